@@ -1,0 +1,476 @@
+#!/usr/bin/env python3
+"""Benchmark of the batched LISA MBHB likelihood on B300 (arXiv:2111.01064, Sec. II-III).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one heterodyned-likelihood batch (Sec. II B; the Module 2/3 workload of
+Sec. III B-C): 8 temperatures x 2048 walkers = 16384 templates perturbed
+1e-3..1e-1 per parameter around a reference on the 1-yr, 15-s grid
+(1,051,920 frequencies), 256 log-spaced bins x 3 channels, mixed precision.
+`value` = heterodyned lnL evaluations per second over all ranks.  The same run
+also measures the direct likelihood (Sec. II, Eqs. 2-3; Sec. III A): the stored-
+template streaming reduction against the HBM roofline and the fused
+generate-and-reduce pass over the 4096-template brute-force batch.
+
+Inputs are synthetic and seeded (mbh_inputs): the LDC-1A data are not available,
+so an injection with SNR drawn in 100-1000, in Gaussian noise from the analytic
+A/E/T PSD, stands in for them.  L2 (126 MB) is flushed between heterodyne steps
+with a 512 MiB write outside the timed events; the direct-path inputs are larger
+than L2.  Multi-GPU: walkers are independent, so each rank runs its own batch
+(weak scaling, no collective on the data path); rank 0 prints max-over-ranks
+timing.  `--impl reference` times the FP64 CPU oracle (the method as the paper
+defines it) on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import mbh_inputs as I  # noqa: E402
+
+METRIC = ("heterodyned lnL evals/sec at |ΔlnL|≤1e-3 vs FP64 oracle; "
+          "direct lnL HBM GB/s; p99 ms")
+UNIT = "lnL evals/s"
+W_TEMPS, W_PER_TEMP, N_BINS = 8, 2048, 256
+N_WALKERS = W_TEMPS * W_PER_TEMP
+N_DIRECT = 4096
+N_STORED = 96
+WORKLOAD = ("heterodyne PE batch: 8 temperatures x 2048 walkers = 16384 templates, 256 bins x 3 "
+            "channels (A,E,T), 1 yr @ 15 s grid (1,051,920 freqs); direct: 4096 prior templates "
+            "on the same grid")
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6400.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+# FP64 peak of B300: 148 SMs x 2 DFMA per SM per clock (measured 566 G DFMA/s at 1935 MHz,
+# i.e. 1.98 per SM per clock) x 2 flop x max SM clock.
+def fp64_peak_gflops(sm_mhz: float) -> float:
+    return 148 * 2 * 2 * sm_mhz * 1e-3
+
+
+# FP64 operations per edge evaluation of the mixed heterodyne kernel (phase chain of
+# phase_mixed + the 2 pi reduction of dPhi), counted from the source: v, 1/v, ln v (3),
+# two degree-7 Horner chains (14), powers of 1/v (4), Psi_PN and its derivative (6), t(f)
+# and the support tests (5), orbit-angle offset and the two float64 corrections (4), k.c
+# (3), Phi (7), the reduction (3): 49 instructions, of which 26 FMA -> 75 flop.
+HET_MIXED_FP64_FLOP_PER_EDGE = 75
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[tuple[float, str]] = []
+        self.window = (0.0, float("inf"))
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def wait_for_samples(self, n: int = 2, timeout: float = 5.0):
+        t0 = time.time()
+        while self.proc is not None and len(self.lines) < n and time.time() - t0 < timeout:
+            time.sleep(0.02)
+
+    def mark(self, t0: float, t1: float):
+        self.window = (t0, t1)
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        t0, t1 = self.window
+        inside = [ln for ts, ln in self.lines if t0 - 0.06 <= ts <= t1 + 0.06]
+        where = "timed region"
+        if len(inside) < 2:   # fewer samples than the sampling period allows: widen to the run
+            inside = [ln for _, ln in self.lines]
+            where = "whole GPU run (timed region shorter than two samples)"
+        for ln in inside:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "samples": len(sm), "window": where, "reasons": sorted(reasons)}
+
+
+def flush_l2(buf):
+    buf.add_(1.0)
+
+
+def run_ours(args) -> dict | None:
+    import torch
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    from paper_2111_01064_b300 import mbhlike as M
+    from paper_2111_01064_b300 import workloads as WL
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    peaks, peak_src = _measured_peaks()
+
+    # ---- workload (per rank: its own source, weak scaling) ----
+    g = I.grid_year()
+    src = WL.source_for(2, g, source=rank)
+    ref = M.het_prepare_reference(src.data, src.theta_inj, N_BINS)
+    th_np = WL.walkers(src.theta_inj, N_WALKERS, 2, source=rank)
+    theta = WL.to_dev(th_np)
+    out = torch.empty((3, N_WALKERS), dtype=torch.float64, device=dev)
+    flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)  # 512 MiB > L2
+    offs = [0, N_WALKERS]
+
+    def het_step(prec="mixed"):
+        M.het_loglike_batch([ref], offs, theta, prec, out=out)
+
+    # ---- timed heterodyne steps ----
+    clk = ClockSampler(local).__enter__()
+    for _ in range(args.warmup):
+        het_step()
+        flush_l2(flush)
+    torch.cuda.synchronize()
+    clk.wait_for_samples()
+    if ws > 1:
+        torch.distributed.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    t_start = time.time()
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        het_step()
+        ev[i][1].record(stream)
+        flush_l2(flush)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    clk.mark(t_start, time.time())
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if ws > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = ws * N_WALKERS * args.steps / (total_ms * 1e-3)
+    mixed_out = out.cpu().numpy().copy()
+
+    # ---- float64 heterodyne kernel on the same batch (baseline) ----
+    het_step("fp64")
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f64_ms = []
+    for _ in range(3):
+        flush_l2(flush)
+        e0.record(stream)
+        het_step("fp64")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        f64_ms.append(e0.elapsed_time(e1))
+    fp64_out = out.cpu().numpy().copy()
+    fp64_rate = N_WALKERS / (statistics.median(f64_ms) * 1e-3)
+    scale = 0.5 * (src.data.dd + np.abs(fp64_out[2]) + 2 * np.abs(fp64_out[1]))
+    dmix = np.abs(mixed_out[0] - fp64_out[0])
+
+    # ---- e2e: host theta in, host lnL out, through the same C-ABI call ----
+    th_host = torch.from_numpy(th_np).pin_memory()
+    out_host = torch.empty((3, N_WALKERS), dtype=torch.float64).pin_memory()
+    theta_e2e = torch.empty_like(theta)
+    for _ in range(2):
+        theta_e2e.copy_(th_host, non_blocking=True)
+        M.het_loglike_batch([ref], offs, theta_e2e, "mixed", out=out)
+        out_host.copy_(out, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush_l2(flush)
+        e2e_ev[i][0].record(stream)
+        theta_e2e.copy_(th_host, non_blocking=True)
+        M.het_loglike_batch([ref], offs, theta_e2e, "mixed", out=out)
+        out_host.copy_(out, non_blocking=True)
+        e2e_ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev)
+    e2e_value = ws * N_WALKERS * args.steps / (e2e_ms * 1e-3)
+
+    # ---- direct likelihood: stored templates (HBM roofline) ----
+    del flush
+    torch.cuda.synchronize()
+    th_dir = I.draw_prior_batch(I.rng(1, 300 + rank), N_DIRECT, g["t_obs"])
+    th_dir_dev = WL.to_dev(th_dir)
+    h64 = M.template_batch(g, WL.to_dev(th_dir[:, :N_STORED]), "fp64")
+    dout = torch.empty((3, N_STORED), dtype=torch.float64, device=dev)
+    for _ in range(2):
+        M.direct_loglike_stored(src.data, h64, "fp64", out=dout)
+    torch.cuda.synchronize()
+    st_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+             for _ in range(5)]
+    for a, b in st_ev:
+        a.record(stream)
+        M.direct_loglike_stored(src.data, h64, "fp64", out=dout)
+        b.record(stream)
+    torch.cuda.synchronize()
+    st_ms = statistics.median(a.elapsed_time(b) for a, b in st_ev)
+    n = g["n"]
+    stored_bytes = N_STORED * 3 * n * 16 + 3 * n * (16 + 8)
+    stored_gbs = stored_bytes / (st_ms * 1e-3) / 1e9
+    del h64
+    h32 = M.template_batch(g, WL.to_dev(th_dir[:, :2 * N_STORED]), "mixed")
+    dout32 = torch.empty((3, 2 * N_STORED), dtype=torch.float64, device=dev)
+    M.direct_loglike_stored(src.data, h32, "mixed", out=dout32)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    M.direct_loglike_stored(src.data, h32, "mixed", out=dout32)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    st32_ms = e0.elapsed_time(e1)
+    stored32_gbs = (2 * N_STORED * 3 * n * 8 + 3 * n * 24) / (st32_ms * 1e-3) / 1e9
+    del h32
+
+    # ---- direct likelihood: fused generate + reduce over the brute-force batch ----
+    dfused = torch.empty((3, N_DIRECT), dtype=torch.float64, device=dev)
+    M.direct_loglike_batch(src.data, th_dir_dev[:, :64].contiguous(), "mixed")
+    torch.cuda.synchronize()
+    e0.record(stream)
+    M.direct_loglike_batch(src.data, th_dir_dev, "mixed", out=dfused)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fused_mixed_ms = e0.elapsed_time(e1)
+    n64 = 256
+    d64 = torch.empty((3, n64), dtype=torch.float64, device=dev)
+    e0.record(stream)
+    M.direct_loglike_batch(src.data, th_dir_dev[:, :n64].contiguous(), "fp64", out=d64)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fused_fp64_ms = e0.elapsed_time(e1)
+    dm = dfused[:, :n64].cpu().numpy()
+    d6 = d64.cpu().numpy()
+    dscale = 0.5 * (src.data.dd + np.abs(d6[2]) + 2 * np.abs(d6[1]))
+
+    clk.__exit__(None, None, None)
+    clocks = clk.summary()
+    sm_for_peak = peaks.get("sm_max_mhz", 2032.0)
+    fp64_peak = fp64_peak_gflops(sm_for_peak)
+    E = ref.bins
+    flop = N_WALKERS * (E + 1) * HET_MIXED_FP64_FLOP_PER_EDGE
+    achieved = flop / (ms_per_step * 1e-3) / 1e9
+    roof_traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof):
+        with open(prof) as fh:
+            roof_traffic = json.load(fh).get("het_mixed_kernel_bytes_per_launch")
+
+    res = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64 phases + f32 response (mixed)",
+        "data": "synthetic (seeded injection in Gaussian noise from the analytic A/E/T PSD; LDC-1A "
+                "not available)",
+        "config": {"workload": WORKLOAD, "walkers": N_WALKERS, "temperatures": W_TEMPS,
+                   "bins_requested": N_BINS, "bins": E, "channels": 3, "grid_points": n,
+                   "precision": "mixed", "l2": "flushed between steps (512 MiB write, outside the "
+                   "timed events)", "parallelism": f"walker batches per rank x{ws}"},
+        "gpu_launches": args.steps * 1,
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
+                       "p99": float(np.percentile(step_ms, 99))},
+        "p99_ms": float(np.percentile(step_ms, 99)),
+        "wall_ms_per_step_incl_flush": t_wall * 1e3 / args.steps,
+        "fp64_het": {"value": fp64_rate, "unit": UNIT, "speedup_mixed_over_fp64": value / ws / fp64_rate},
+        "accuracy_mixed_vs_fp64_kernel": {
+            "abs_dlnL_p50": float(np.median(dmix)), "abs_dlnL_p99": float(np.quantile(dmix, 0.99)),
+            "abs_dlnL_max": float(dmix.max()), "frac_le_1e-3": float(np.mean(dmix <= 1e-3)),
+            "rel_to_terms_max": float((dmix / scale).max()),
+            "lnL_range": [float(fp64_out[0].min()), float(fp64_out[0].max())]},
+        "direct": {
+            "stored_fp64": {"templates": N_STORED, "ms": st_ms, "GB_per_s": stored_gbs,
+                            "frac_of_hbm": stored_gbs / peaks["hbm_gbs"]},
+            "stored_fp32": {"templates": 2 * N_STORED, "ms": st32_ms, "GB_per_s": stored32_gbs,
+                            "frac_of_hbm": stored32_gbs / peaks["hbm_gbs"]},
+            "fused_mixed": {"templates": N_DIRECT, "ms": fused_mixed_ms,
+                            "templates_per_s": N_DIRECT / (fused_mixed_ms * 1e-3)},
+            "fused_fp64": {"templates": n64, "ms": fused_fp64_ms,
+                           "templates_per_s": n64 / (fused_fp64_ms * 1e-3)},
+            "fused_mixed_vs_fp64_rel_max": float((np.abs(dm[0] - d6[0]) / dscale).max()),
+            "fused_mixed_vs_fp64_abs_max": float(np.abs(dm[0] - d6[0]).max()),
+        },
+        "direct_hbm_gbs": stored_gbs,
+        "roofline": {"bound": "alu", "pipe": "fp64", "achieved": achieved, "peak": fp64_peak,
+                     "unit": "GFLOP/s", "frac": achieved / fp64_peak, "traffic": roof_traffic,
+                     "kernel": "het_mixed_kernel",
+                     "peak_note": f"148 SM x 2 DFMA/clk x 2 flop x {sm_for_peak:.0f} MHz "
+                                  "(2 DFMA/clk/SM measured on this B300)",
+                     "flop_per_edge": HET_MIXED_FP64_FLOP_PER_EDGE},
+        "roofline_direct_stored": {"bound": "hbm", "achieved": stored_gbs, "peak": peaks["hbm_gbs"],
+                                   "unit": "GB/s", "frac": stored_gbs / peaks["hbm_gbs"],
+                                   "traffic": None, "kernel": "direct_stored_kernel<double2,4>",
+                                   "peak_source": f"{peak_src} hbm_gbs"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": th_np.nbytes,
+                "d2h_bytes_per_step": out_host.numel() * 8},
+        "clocks": clocks,
+        "_mixed_lnl": mixed_out[0],
+        "_fp64_lnl": fp64_out[0],
+    }
+    if ws > 1:
+        torch.distributed.barrier()
+    return res if rank == 0 else None
+
+
+def oracle_workload(walkers: int = N_WALKERS) -> dict:
+    """The oracle's own copy of the workload (its data, 256-bin reference and walkers,
+    from the same draws as rank 0); built once, not timed."""
+    from oracle import oracle as O
+    g = I.grid_year()
+    th_raw, snr = I.draw_source(I.rng(2, 0), g["t_obs"])
+    f = O.freqs(g)
+    S = O.psd(f)
+    th = I.with_distance(th_raw, O.snr_distance(th_raw, g, snr, S))
+    z = I.noise_normals(I.rng(2, 100), g["n"])
+    d, _ = O.make_data(th, g, z, S)
+    ref = O.het_prepare(th, g, d, S, N_BINS)
+    walk = I.perturb(th, I.perturbation(I.rng(2, 200), N_WALKERS, 1e-3, 1e-1))
+    idx = np.linspace(0, N_WALKERS - 1, walkers).astype(int)
+    return {"O": O, "ref": ref, "idx": idx, "sub": np.ascontiguousarray(walk[:, idx])}
+
+
+def time_oracle(wl: dict, seconds: float) -> tuple[float, int, float, np.ndarray]:
+    """Heterodyned lnL of the sampled walkers, repeated until `seconds` have passed."""
+    O = wl["O"]
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        out = O.het_loglike(wl["sub"], wl["ref"])
+        reps += 1
+        dt = time.perf_counter() - t0
+        if dt >= seconds:
+            break
+    return reps * wl["sub"].shape[1] / dt, reps, dt, out
+
+
+def cpu_baseline(seconds: float) -> dict:
+    """The FP64 oracle, as it stands, on a bounded sample of the same workload."""
+    wl = oracle_workload()
+    rate, reps, dt, out = time_oracle(wl, seconds)
+    return {"value": rate, "unit": UNIT, "cores": wl["O"].threads(), "kind": "oracle",
+            "sample": f"all 16384 walkers x {reps} repetitions ({dt:.1f} s), 256-bin reference on "
+                      "the 1-yr grid (reference preparation not timed, as on the GPU)",
+            "_idx": wl["idx"], "_out": out}
+
+
+def run_reference(args) -> dict | None:
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return None
+    walkers = 1024
+    wl = oracle_workload(walkers)
+    per_step = max(0.2, 60.0 / (args.warmup + args.steps))
+    rates = []
+    for i in range(args.warmup + args.steps):
+        rate, reps, dt, _ = time_oracle(wl, per_step)
+        if i >= args.warmup:
+            rates.append(rate)
+    value = statistics.median(rates)
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": walkers / value * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "walkers_per_step": walkers},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": wl["O"].threads(), "kind": "oracle",
+                             "sample": f"{walkers} evenly spaced walkers of the 16384 per step, "
+                                       f"each step >= {per_step:.2f} s of CPU work"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=10.0,
+                    help="CPU work of the oracle baseline (0: skip)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        res = run_reference(args)
+    else:
+        res = run_ours(args)
+        ws, rank, _ = _dist()
+        if res is not None and rank == 0 and ws == 1 and args.cpu_seconds > 0:
+            cb = cpu_baseline(args.cpu_seconds)
+            res["cpu_baseline"] = {k: v for k, v in cb.items() if not k.startswith("_")}
+            idx, ora = cb["_idx"], cb["_out"][0]
+            for key, name in (("_mixed_lnl", "accuracy_mixed_vs_oracle"),
+                              ("_fp64_lnl", "accuracy_fp64_vs_oracle")):
+                d = np.abs(res[key][idx] - ora)
+                res[name] = {"walkers": int(idx.size), "abs_dlnL_p50": float(np.median(d)),
+                             "abs_dlnL_p99": float(np.quantile(d, 0.99)),
+                             "abs_dlnL_max": float(d.max()), "frac_le_1e-3": float(np.mean(d <= 1e-3))}
+    if res is not None:
+        for k in [k for k in res if k.startswith("_")]:
+            res.pop(k)
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

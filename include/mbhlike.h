@@ -1,0 +1,161 @@
+/*
+ * mbhlike — batched LISA likelihood for massive-black-hole-binary templates on
+ * one NVIDIA B300 (sm_103a).  C ABI of libmbhlike.so.
+ *
+ * The method is the one of Katz, arXiv:2111.01064, Sec. II: frequency-domain
+ * (2,2)-mode templates A(f) e^{-i phi(f)} (Eq. 7) put through the LISA TDI A/E/T
+ * response at the SPA time t(f) (Eqs. 8-9), the noise-weighted inner product
+ * <a|b> = 4 Re sum_{A,E,T} sum_f a* b / S_n df (Eq. 3), the log-likelihood
+ * lnL = -1/2 (<d|d> + <h|h> - 2 <d|h>) (Eq. 2), and the heterodyned
+ * (relative-binning) likelihood of Sec. II B (Eqs. 10-19) over log-spaced bins
+ * covering the band where the reference template is non-zero (Sec. III B).
+ * The amplitude/phase model is the stand-in "W0" (TaylorF2 3.5PN phase with
+ * aligned-spin terms, Gaussian-tapered f^{-7/6} amplitude, t_ref and phi_ref
+ * pinned at f_max = argmax f^2 A) and the response the stand-in "R0" (rigid
+ * equal-arm constellation, one-link kernel, first-generation TDI).
+ *
+ * Conventions shared by every call
+ *  - Parameters theta are float64, structure-of-arrays [11][W]:
+ *    M_T (solar masses, detector frame), q = m2/m1 in (0, 1], a1, a2 (aligned
+ *    spins), D_L (Gpc), phi_ref, iota, lambda, beta, psi (rad, SSB frame),
+ *    t_ref (s, time at f_max).
+ *  - Frequency grid f_k = f0 + k df, k in [0, n), f0 > 0; a template is zero
+ *    above f_cut = 0.2/M and where its track t(f) leaves [0, t_obs].
+ *  - Channels are A, E, T in that order; a complex value is two consecutive
+ *    numbers (re, im); "complex128" = 2 x float64, "complex64" = 2 x float32.
+ *  - Every *_dev pointer is a device pointer owned by the caller; it must stay
+ *    valid until the work queued on `stream` has finished.  Handles (mbh_data,
+ *    mbh_ref, mbh_server) are owned by the library and released only by their
+ *    *_free call.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls queue
+ *    work asynchronously and return without synchronising, except where a
+ *    call says it synchronises.
+ *  - Argument errors are detected on the host before anything is queued and
+ *    return MBH_EINVAL; CUDA launch/allocation failures return MBH_ECUDA or
+ *    MBH_ENOMEM.  mbh_last_error() gives a message for the calling thread.
+ *  - There is no host fallback: without a usable CUDA device every compute
+ *    call returns MBH_ECUDA.
+ */
+#ifndef MBHLIKE_H
+#define MBHLIKE_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MBH_API __attribute__((visibility("default")))
+#else
+#define MBH_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MBH_OK = 0,
+    MBH_EINVAL = 1,   /* bad argument (checked on the host, nothing queued) */
+    MBH_ENOMEM = 2,   /* device allocation failed */
+    MBH_ECUDA = 3,    /* CUDA error (no device, launch failure, ...) */
+    MBH_ETIMEOUT = 4, /* a bounded wait gave up (serving loop) */
+    MBH_EBUSY = 5     /* admission refused: over the memory budget or queue full */
+} mbh_status;
+
+typedef enum {
+    MBH_FP64 = 0,  /* every step in float64 */
+    MBH_MIXED = 1  /* large phases (Psi, 2 pi f k.c, t(f)) in float64, amplitudes,
+                      response, ratios and products in float32, sums in float64 */
+} mbh_precision;
+
+typedef struct {
+    double f0;     /* first grid frequency (Hz), > 0 */
+    double df;     /* spacing (Hz), > 0 */
+    int64_t n;     /* number of grid points, >= 2 */
+    double t_obs;  /* observation window [0, t_obs] (s) */
+} mbh_grid;
+
+typedef struct mbh_data mbh_data; /* data d~ and noise weights on one grid */
+typedef struct mbh_ref mbh_ref;   /* one heterodyne reference (summary data) */
+
+/* Message for the last failing call on this thread ("" if none). */
+MBH_API const char* mbh_last_error(void);
+
+/* Analytic noise PSD S_n of A, E, T on the grid (Sec. II, remark under Eq. 3:
+ * A and E identical, T different; acceleration 3e-15 m/s^2/rtHz, OMS
+ * 15e-12 m/rtHz, L = 2.5e9 m).  psd_dev: float64 [3][n], written. */
+MBH_API mbh_status mbh_psd_aet(const mbh_grid* grid, double* psd_dev, void* stream);
+
+/* Gaussian noise realisation from standard normals (Sec. II: <n~ n~*> = S/2 per
+ * unit bandwidth): noise[c][k] = sqrt(S[c][k] / (4 df)) (z[c][k][0] + i z[c][k][1]).
+ * z_dev: float64 [3][n][2]; psd_dev: float64 [3][n]; noise_dev: complex128
+ * [3][n], written.  With accumulate != 0 the noise is added to noise_dev. */
+MBH_API mbh_status mbh_noise_aet(const mbh_grid* grid, const double* z_dev, const double* psd_dev,
+                         int32_t accumulate, void* noise_dev, void* stream);
+
+/* Templates h~^{A,E,T}(f_k) = T^{A,E,T}(f, t(f)) A(f) e^{-i phi(f)} on the grid
+ * (Sec. II A, Eqs. 7-9).  theta_dev: float64 [11][W]; h_out_dev: [W][3][n]
+ * complex128 (MBH_FP64) or complex64 (MBH_MIXED: the float64 phase is rounded
+ * once to float32 storage), written. */
+MBH_API mbh_status template_batch(const mbh_grid* grid, const double* theta_dev, int64_t W,
+                          mbh_precision precision, void* h_out_dev, void* stream);
+
+/* Bind data to a grid (Sec. II, Eq. 3).  d_dev: complex128 [3][n]; psd_dev:
+ * float64 [3][n] (all > 0).  The library keeps its own device copies (the
+ * caller's buffers may be released once the stream has passed this call) in
+ * the form 4 df d/S (complex128) and 4 df/S (float64), and computes <d|d>.
+ * Synchronises `stream` once (to read <d|d>). */
+MBH_API mbh_status mbh_data_create(const mbh_grid* grid, const void* d_dev, const double* psd_dev,
+                           void* stream, mbh_data** out);
+/* <d|d> of the data (host value, computed at creation). */
+MBH_API double mbh_data_dd(const mbh_data* data);
+MBH_API void mbh_data_free(mbh_data* data);
+
+/* Direct likelihood, templates generated on the device and reduced in the same
+ * pass (Sec. II, Eqs. 2-3; Sec. III A).  out_dev: float64 [3][W]: lnL, <d|h>,
+ * <h|h>.  MBH_MIXED evaluates the response in float32 around float64 phases;
+ * sums are float64 in both modes. */
+MBH_API mbh_status direct_loglike_batch(const mbh_data* data, const double* theta_dev, int64_t W,
+                                mbh_precision precision, double* out_dev, void* stream);
+
+/* Direct likelihood of stored templates h_dev [W][3][n] (complex128 for
+ * MBH_FP64, complex64 for MBH_MIXED), e.g. from template_batch.  Float64
+ * accumulation.  out_dev as above. */
+MBH_API mbh_status direct_loglike_stored(const mbh_data* data, const void* h_dev, int64_t W,
+                                 mbh_precision precision, double* out_dev, void* stream);
+
+/* Heterodyne reference (Sec. II B, Eqs. 15-16 and 18-19; Sec. III B).
+ * theta0_host: float64 [11] on the host.  Band = first..last grid index where
+ * h0 != 0; n_bins + 1 log-spaced edge targets from f(band start) to f(band end)
+ * rounded to the nearest grid index, endpoints exact, duplicates dropped.  Bin
+ * b holds k in [e_b, e_{b+1}), the last bin also e_E; f_b is the bin centre.
+ * Stores per bin and channel A0, A1 (complex), B0, B1 (real), h0 at the edges
+ * and <d|d>.  The handle is independent of `data` afterwards.  Synchronises
+ * `stream` (edge bookkeeping on the host).  MBH_EINVAL if the band has fewer
+ * than two grid points or n_bins is outside [1, 4096]. */
+MBH_API mbh_status het_prepare_reference(const mbh_data* data, const double* theta0_host,
+                                 int32_t n_bins, void* stream, mbh_ref** out);
+/* Number of bins E actually used (<= n_bins). */
+MBH_API int32_t mbh_ref_bins(const mbh_ref* ref);
+/* Copies (host, blocking): edges int64 [E+1]; summary float64 [E][3][6] =
+ * Re A0, Im A0, Re A1, Im A1, B0, B1; h0 at the edges complex128 [E+1][3];
+ * any pointer may be NULL. */
+MBH_API mbh_status mbh_ref_read(const mbh_ref* ref, int64_t* edges_host, double* summary_host,
+                        double* h0_edges_host, double* dd_host);
+MBH_API void mbh_ref_free(mbh_ref* ref);
+
+/* Heterodyned likelihood for walkers of several sources in one launch
+ * (Sec. II B, Eqs. 14 and 17): the template is evaluated at the E_s + 1 bin
+ * edges of its source, r = h/h0, r0 = (r_lo + r_hi)/2, r1 = (r_hi - r_lo)/(f_hi -
+ * f_lo), and contracted with the summary data.  Walkers [offsets[s],
+ * offsets[s+1]) belong to refs[s]; theta_dev: float64 [11][W] with W =
+ * offsets[n_sources]; offsets_host: int64 [n_sources + 1] on the host,
+ * non-decreasing, offsets[0] = 0.  out_dev: float64 [3][W]: lnL, <d|h>, <h|h>.
+ * MBH_MIXED: float64 phase difference, float32 ratios in the delta = r - 1
+ * form, float32 products accumulated in float64. */
+MBH_API mbh_status het_loglike_batch(const mbh_ref* const* refs, const int64_t* offsets_host,
+                             int32_t n_sources, const double* theta_dev,
+                             mbh_precision precision, double* out_dev, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MBHLIKE_H */

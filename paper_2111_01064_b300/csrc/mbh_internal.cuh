@@ -1,0 +1,159 @@
+// Internal types shared by the translation units of libmbhlike (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <mutex>
+#include <vector>
+
+#include "../../include/mbhlike.h"
+
+namespace mbh {
+
+constexpr int kMaxBins = 4096;
+constexpr int kMaxSrc = 96;   // sources per launch (descriptors travel as kernel parameters)
+
+// Edge record of the mixed-precision heterodyne: the frequency tables that make the float64
+// phase chain free of cbrt/log, the reference's float64 large phase Phi0 and 1/H0 of the
+// float32 transfer part (h0 = H0 e^{-i Phi0}).
+struct MixEdge {
+    double f, f3, fm3, lnf3, phi0;
+    float2 h0inv[3];
+};
+// Bin record of the mixed-precision heterodyne: float32 summary data and 1/(f_hi - f_lo).
+struct MixBin {
+    float q[18];
+    float invw;
+    float pad;
+};
+
+struct MixTables {
+    const MixEdge* edge;   // [E+1]
+    const MixBin* bin;     // [E]
+    double sumA0;          // sum_b sum_c Re A0
+    double sumB0;          // sum_b sum_c B0
+};
+
+struct PrepItem {
+    int32_t bin;
+    int64_t k0, k1;   // grid range [k0, k1)
+};
+
+struct SrcDesc {
+    const double* summary;   // [E][3][6]
+    const double2* h0inv;    // [E+1][3]
+    const double* fe;        // [E+1]
+    const double* invw;      // [E]
+    MixTables mix;
+    double dd, t_obs;
+    int64_t w_begin, w_end;  // walker range in theta/out
+    int32_t E;
+    int32_t tile_begin;      // first tile of this source
+};
+
+struct HetLaunch {
+    const double* theta;
+    double* out;
+    int64_t W;
+    int32_t n_src;
+    int32_t n_tiles;
+    SrcDesc src[kMaxSrc];
+};
+
+mbh_status fail(mbh_status s, const char* fmt, ...);
+mbh_status cuda_fail(cudaError_t e, const char* where);
+mbh_status check_grid(const mbh_grid* g);
+mbh_status check_device();
+mbh_status check_het_args(const mbh_ref* const* refs, const int64_t* offsets, int32_t n_src,
+                          const double* theta, double* out);
+mbh_status build_launch(const mbh_ref* const* refs, const int64_t* offsets, int32_t n_src,
+                        int64_t first, int32_t count, int wpb, const double* theta, int64_t W,
+                        double* out, HetLaunch& L);
+void direct_chunks(int64_t n, int64_t tiles, int64_t max_chunk, int64_t& chunk, int& nchunks);
+mbh_status direct_finish(double2* part, int nchunks, int64_t W, double dd, double* out,
+                         cudaStream_t st);
+std::mutex& launch_mutex();
+
+// mixed-precision entry points (mbh_mixed.cu)
+mbh_status launch_template_mixed(const mbh_grid* g, const double* theta, int64_t W, float2* h,
+                                 cudaStream_t st);
+mbh_status launch_direct_fused_mixed(const mbh_data* data, const double* theta, int64_t W,
+                                     double* out, cudaStream_t st);
+cudaError_t alloc_ref_tables(mbh_ref* R);
+void free_ref_tables(mbh_ref* R);
+cudaError_t prepare_mixed_tables(mbh_ref* R, cudaStream_t st);
+struct HetTuning {
+    int threads_per_walker;   // 1, 2, 4, 8, 16 or 32
+    int block;                // threads per block (multiple of 32)
+    int persistent_blocks;    // 0: one block per tile; else grid size of the persistent loop
+};
+mbh_status run_het_mixed(const mbh_ref* const* refs, const int64_t* offsets, int32_t n_src,
+                         const double* theta, int64_t W, double* out, cudaStream_t st,
+                         const HetTuning* tuning);
+
+// ------------------------------------------------------------------------------------------
+// reductions
+// ------------------------------------------------------------------------------------------
+// Block-wide sum of N doubles per thread; result valid in thread 0.  blockDim.x must be a
+// multiple of 32 and <= 1024.  Fixed order.
+template <int N>
+__device__ void block_sum(double (&v)[N], double* smem /* >= 32*N */)
+{
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_down_sync(0xffffffffu, v[j], o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int j = 0; j < N; ++j) smem[j * 32 + warp] = v[j];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            double x = lane < nw ? smem[j * 32 + lane] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+            v[j] = x;
+        }
+    }
+}
+
+}  // namespace mbh
+
+struct mbh_data {
+    mbh_grid grid;
+    int device = -1;
+    double2* wd = nullptr;   // [3][n] 4 df d/S
+    double* wv = nullptr;    // [3][n] 4 df/S
+    float2* wd32 = nullptr;  // [3][n] sigma 4 df d/S (mixed path)
+    float* wv32 = nullptr;   // [3][n] sigma^2 4 df/S (mixed path)
+    float4* wsp = nullptr;   // [3][n] float pairs of 2^shift 4 df d/S: (re hi, im hi, re lo, im lo)
+    float2* vsp = nullptr;   // [3][n] float pair of 2^(2 shift) 4 df/S
+    double sigma = 1.0;      // scale of the float32 copies: h/sigma is O(1)
+    int shift = 0;           // round(log2 sigma): templates are split as h 2^-shift
+    double dd = 0.0;         // <d|d>
+};
+
+struct mbh_ref {
+    int device = -1;
+    mbh_grid grid;
+    int32_t E = 0;
+    int64_t band[2] = {0, 0};
+    double theta0[11];
+    double dd = 0.0;
+    std::vector<int64_t> edges_host;
+    double* theta0_dev = nullptr;
+    int64_t* edges = nullptr;      // [E+1]
+    double* fe = nullptr;          // [E+1]
+    double* invw = nullptr;        // [E]
+    double* summary = nullptr;     // [E][3][6]
+    double2* h0e = nullptr;        // [E+1][3]
+    double2* h0inv = nullptr;      // [E+1][3]
+    mbh::MixEdge* mix_edge = nullptr;
+    mbh::MixBin* mix_bin = nullptr;
+    double* mix_sums = nullptr;    // device [2]
+    mbh::MixTables mix{};
+};

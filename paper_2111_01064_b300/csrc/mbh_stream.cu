@@ -1,0 +1,168 @@
+// Direct likelihood of stored templates (Katz, arXiv:2111.01064, Sec. II, Eqs. 2-3): the
+// HBM-bound streaming reduction <d|h> = sum Re(conj(4 df d/S) h), <h|h> = sum 4 df/S |h|^2
+// over 3 channels x n frequencies per template.
+//
+//   direct_stored_df_kernel   complex128 templates, float64-class accuracy from double-float
+//                             arithmetic on the float32/integer pipes (mbh_df.cuh): B300's
+//                             float64 pipe (2 FMA/SM/clock) would cap this reduction at
+//                             ~1.8 TB/s, the double-float form leaves it HBM-bound.
+//   direct_stored_f32_kernel  complex64 templates, float32 products on O(1)-scaled operands,
+//                             float64 sums.
+// Block = (walker tile of T templates, frequency chunk); the data of a chunk is read once per
+// block and reused by its T templates, and walker tiles vary fastest in launch order so the
+// tiles sharing a chunk run together and find the data in L2.  Per-block partial sums go to a
+// scratch array, added in chunk order by direct_finalize_kernel (deterministic).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "mbh_df.cuh"
+#include "mbh_internal.cuh"
+
+using namespace mbh;
+
+constexpr int kStreamThreads = 256;
+
+template <int T>
+__global__ void __launch_bounds__(kStreamThreads)
+    direct_stored_df_kernel(const float4* __restrict__ wsp, const float2* __restrict__ vsp,
+                            const double2* __restrict__ h, int64_t n, int64_t W, int64_t chunk,
+                            int nchunks, int shift, double2* __restrict__ part)
+{
+    __shared__ double sm[32 * 2 * T];
+    const int64_t w0 = (int64_t)blockIdx.x * T;
+    const int ch = blockIdx.y;
+    const int64_t kb = (int64_t)ch * chunk, ke = std::min<int64_t>(n, kb + chunk);
+    f2 adh[T], ahh[T];
+#pragma unroll
+    for (int t = 0; t < T; ++t) adh[t] = ahh[t] = {0.0f, 0.0f};
+    for (int c = 0; c < 3; ++c) {
+        const float4* wc = wsp + (int64_t)c * n;
+        const float2* vc = vsp + (int64_t)c * n;
+#pragma unroll 2
+        for (int64_t k = kb + threadIdx.x; k < ke; k += kStreamThreads) {
+            const float4 d = __ldg(wc + k);
+            const float2 v2 = __ldg(vc + k);
+            const f2 dre = {d.x, d.z}, dim = {d.y, d.w}, v = {v2.x, v2.y};
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+                if (w0 + t < W) {
+                    const double2 x = __ldcs(h + ((w0 + t) * 3 + c) * n + k);
+                    const f2 xr = split_f64(x.x, shift), xi = split_f64(x.y, shift);
+                    df_acc(adh[t], df_mul(dre, xr));
+                    df_acc(adh[t], df_mul(dim, xi));
+                    df_acc(ahh[t], df_mul(v, df_add(df_sqr(xr), df_sqr(xi))));
+                }
+            }
+        }
+    }
+    double acc[2 * T];
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        acc[2 * t] = df_to_double(adh[t]);
+        acc[2 * t + 1] = df_to_double(ahh[t]);
+    }
+    block_sum<2 * T>(acc, sm);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int t = 0; t < T; ++t)
+            if (w0 + t < W) part[(w0 + t) * nchunks + ch] = make_double2(acc[2 * t], acc[2 * t + 1]);
+}
+
+template <int T>
+__global__ void __launch_bounds__(kStreamThreads)
+    direct_stored_f32_kernel(const float2* __restrict__ wd, const float* __restrict__ wv,
+                             const float2* __restrict__ h, int64_t n, int64_t W, int64_t chunk,
+                             int nchunks, float inv_sigma, double2* __restrict__ part)
+{
+    __shared__ double sm[32 * 2 * T];
+    const int64_t w0 = (int64_t)blockIdx.x * T;
+    const int ch = blockIdx.y;
+    const int64_t kb = (int64_t)ch * chunk, ke = std::min<int64_t>(n, kb + chunk);
+    double acc[2 * T];
+#pragma unroll
+    for (int t = 0; t < 2 * T; ++t) acc[t] = 0.0;
+    for (int c = 0; c < 3; ++c) {
+        const float2* wc = wd + (int64_t)c * n;
+        const float* vc = wv + (int64_t)c * n;
+        float pd[T], ph[T];
+#pragma unroll
+        for (int t = 0; t < T; ++t) pd[t] = ph[t] = 0.0f;
+#pragma unroll 4
+        for (int64_t k = kb + threadIdx.x; k < ke; k += kStreamThreads) {
+            const float2 d = __ldg(wc + k);
+            const float v = __ldg(vc + k);
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+                if (w0 + t < W) {
+                    const float2 x = __ldcs(h + ((w0 + t) * 3 + c) * n + k);
+                    const float xr = x.x * inv_sigma, xi = x.y * inv_sigma;
+                    pd[t] = fmaf(d.x, xr, fmaf(d.y, xi, pd[t]));
+                    ph[t] = fmaf(v, fmaf(xr, xr, xi * xi), ph[t]);
+                }
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            acc[2 * t] += (double)pd[t];
+            acc[2 * t + 1] += (double)ph[t];
+        }
+    }
+    block_sum<2 * T>(acc, sm);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int t = 0; t < T; ++t)
+            if (w0 + t < W) part[(w0 + t) * nchunks + ch] = make_double2(acc[2 * t], acc[2 * t + 1]);
+}
+
+namespace mbh {
+// Launch the stored-template reduction into caller-provided partial sums part[W][nchunks].
+mbh_status launch_stored(const mbh_data* data, const void* h, int64_t W, mbh_precision p,
+                         double2* part, int64_t chunk, int nchunks, cudaStream_t st)
+{
+    constexpr int T = 4;
+    const int64_t tiles = (W + T - 1) / T;
+    dim3 grid((unsigned)tiles, (unsigned)nchunks);
+    if (p == MBH_FP64)
+        direct_stored_df_kernel<T><<<grid, kStreamThreads, 0, st>>>(
+            data->wsp, data->vsp, (const double2*)h, data->grid.n, W, chunk, nchunks, data->shift, part);
+    else
+        direct_stored_f32_kernel<T><<<grid, kStreamThreads, 0, st>>>(
+            data->wd32, data->wv32, (const float2*)h, data->grid.n, W, chunk, nchunks,
+            (float)(1.0 / data->sigma), part);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MBH_OK : cuda_fail(e, "direct_stored kernel");
+}
+
+mbh_status stored_plan(const mbh_data* data, int64_t W, int64_t& chunk, int& nchunks)
+{
+    constexpr int T = 4;
+    const int64_t tiles = (W + T - 1) / T;
+    if (tiles > 0x7fffffff) return fail(MBH_EINVAL, "W too large");
+    direct_chunks(data->grid.n, tiles, 1 << 16, chunk, nchunks);
+    return MBH_OK;
+}
+}  // namespace mbh
+
+extern "C" mbh_status direct_loglike_stored(const mbh_data* data, const void* h_dev, int64_t W,
+                                            mbh_precision precision, double* out_dev, void* stream)
+{
+    if (!data) return fail(MBH_EINVAL, "data is NULL");
+    if (W < 0) return fail(MBH_EINVAL, "W < 0");
+    if (W == 0) return MBH_OK;
+    if (!h_dev || !out_dev) return fail(MBH_EINVAL, "NULL buffer");
+    if (precision != MBH_FP64 && precision != MBH_MIXED)
+        return fail(MBH_EINVAL, "unknown precision %d", (int)precision);
+    cudaStream_t st = (cudaStream_t)stream;
+    int64_t chunk;
+    int nchunks;
+    if (mbh_status s = stored_plan(data, W, chunk, nchunks)) return s;
+    double2* part = nullptr;
+    cudaError_t e = cudaMallocAsync(&part, sizeof(double2) * W * nchunks, st);
+    if (e != cudaSuccess) return cuda_fail(e, "direct_loglike_stored alloc");
+    if (mbh_status s = launch_stored(data, h_dev, W, precision, part, chunk, nchunks, st)) {
+        cudaFreeAsync(part, st);
+        return s;
+    }
+    return direct_finish(part, nchunks, W, data->dd, out_dev, st);
+}

@@ -1,0 +1,266 @@
+"""ctypes binding of libmbhlike (include/mbhlike.h), argument marshalling only.
+
+Every compute step runs in the library's CUDA kernels; this module turns torch
+tensors into device pointers and the current torch stream into a cudaStream_t.
+There is no CPU fallback: a missing library or device raises MBHError.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Sequence
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmbhlike.so")
+
+FP64, MIXED = 0, 1
+_PREC = {"fp64": FP64, "mixed": MIXED, FP64: FP64, MIXED: MIXED}
+STATUS = {0: "MBH_OK", 1: "MBH_EINVAL", 2: "MBH_ENOMEM", 3: "MBH_ECUDA", 4: "MBH_ETIMEOUT",
+          5: "MBH_EBUSY"}
+
+
+class MBHError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Grid(C.Structure):
+    _fields_ = [("f0", C.c_double), ("df", C.c_double), ("n", C.c_int64), ("t_obs", C.c_double)]
+
+
+def grid_struct(g: dict) -> Grid:
+    return Grid(float(g["f0"]), float(g["df"]), int(g["n"]), float(g["t_obs"]))
+
+
+_lib = None
+vp, dp, i64, i32 = C.c_void_p, C.POINTER(C.c_double), C.c_int64, C.c_int32
+
+
+def lib() -> C.CDLL:
+    """Load libmbhlike.so (built in-tree by paper_2111_01064_b300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise MBHError(3, f"{LIB_PATH} not built: run `python -m paper_2111_01064_b300.build`")
+    L = C.CDLL(LIB_PATH)
+    gp = C.POINTER(Grid)
+    sigs = {
+        "mbh_last_error": (C.c_char_p, []),
+        "mbh_psd_aet": (C.c_int, [gp, vp, vp]),
+        "mbh_noise_aet": (C.c_int, [gp, vp, vp, i32, vp, vp]),
+        "template_batch": (C.c_int, [gp, vp, i64, C.c_int, vp, vp]),
+        "mbh_data_create": (C.c_int, [gp, vp, vp, vp, C.POINTER(vp)]),
+        "mbh_data_dd": (C.c_double, [vp]),
+        "mbh_data_free": (None, [vp]),
+        "direct_loglike_batch": (C.c_int, [vp, vp, i64, C.c_int, vp, vp]),
+        "direct_loglike_stored": (C.c_int, [vp, vp, i64, C.c_int, vp, vp]),
+        "het_prepare_reference": (C.c_int, [vp, dp, i32, vp, C.POINTER(vp)]),
+        "mbh_ref_bins": (i32, [vp]),
+        "mbh_ref_read": (C.c_int, [vp, C.POINTER(C.c_int64), dp, dp, dp]),
+        "mbh_ref_free": (None, [vp]),
+        "het_loglike_batch": (C.c_int, [C.POINTER(vp), C.POINTER(C.c_int64), i32, vp, C.c_int, vp,
+                                        vp]),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(status: int):
+    if status != 0:
+        raise MBHError(status, lib().mbh_last_error().decode())
+
+
+def _require_cuda():
+    if not torch.cuda.is_available():
+        raise MBHError(3, "no CUDA device: the mbhlike kernels have no CPU fallback")
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _dev(t: torch.Tensor, dtype, shape=None, name="tensor") -> int:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise MBHError(1, f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise MBHError(1, f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise MBHError(1, f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise MBHError(1, f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return t.data_ptr()
+
+
+def _prec(p) -> int:
+    try:
+        return _PREC[p]
+    except KeyError:
+        raise MBHError(1, f"unknown precision {p!r}") from None
+
+
+# ---- PSD, noise, templates ----------------------------------------------------------
+def mbh_psd_aet(grid: dict, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    _require_cuda()
+    if out is None:
+        out = torch.empty((3, int(grid["n"])), dtype=torch.float64, device="cuda")
+    g = grid_struct(grid)
+    _check(lib().mbh_psd_aet(C.byref(g), _dev(out, torch.float64, (3, g.n), "out"), _stream(stream)))
+    return out
+
+
+def mbh_noise_aet(grid: dict, z: torch.Tensor, psd: torch.Tensor, out: torch.Tensor | None = None,
+                  accumulate: bool = False, stream=None) -> torch.Tensor:
+    _require_cuda()
+    n = int(grid["n"])
+    if out is None:
+        out = torch.zeros((3, n), dtype=torch.complex128, device="cuda")
+    g = grid_struct(grid)
+    _check(lib().mbh_noise_aet(C.byref(g), _dev(z, torch.float64, (3, n, 2), "z"),
+                               _dev(psd, torch.float64, (3, n), "psd"), 1 if accumulate else 0,
+                               _dev(out, torch.complex128, (3, n), "out"), _stream(stream)))
+    return out
+
+
+def template_batch(grid: dict, theta: torch.Tensor, precision="fp64", out: torch.Tensor | None = None,
+                   stream=None) -> torch.Tensor:
+    _require_cuda()
+    p = _prec(precision)
+    W = theta.shape[1]
+    n = int(grid["n"])
+    dt = torch.complex128 if p == FP64 else torch.complex64
+    if out is None:
+        out = torch.empty((W, 3, n), dtype=dt, device="cuda")
+    g = grid_struct(grid)
+    _check(lib().template_batch(C.byref(g), _dev(theta, torch.float64, (11, W), "theta"), W, p,
+                                _dev(out, dt, (W, 3, n), "out"), _stream(stream)))
+    return out
+
+
+# ---- data and the direct likelihood ----------------------------------------------------
+class Data:
+    """mbh_data handle: the data d (3, n) complex128 and PSD (3, n) on one grid."""
+
+    def __init__(self, grid: dict, d: torch.Tensor, psd: torch.Tensor, stream=None):
+        _require_cuda()
+        self.grid = dict(grid)
+        n = int(grid["n"])
+        h = vp()
+        g = grid_struct(grid)
+        _check(lib().mbh_data_create(C.byref(g), _dev(d, torch.complex128, (3, n), "d"),
+                                     _dev(psd, torch.float64, (3, n), "psd"), _stream(stream),
+                                     C.byref(h)))
+        self.handle = h
+
+    @property
+    def dd(self) -> float:
+        return lib().mbh_data_dd(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().mbh_data_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mbh_data_create(grid: dict, d: torch.Tensor, psd: torch.Tensor, stream=None) -> Data:
+    return Data(grid, d, psd, stream)
+
+
+def direct_loglike_batch(data: Data, theta: torch.Tensor, precision="fp64",
+                         out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    W = theta.shape[1]
+    if out is None:
+        out = torch.empty((3, W), dtype=torch.float64, device="cuda")
+    _check(lib().direct_loglike_batch(data.handle, _dev(theta, torch.float64, (11, W), "theta"), W,
+                                      _prec(precision), _dev(out, torch.float64, (3, W), "out"),
+                                      _stream(stream)))
+    return out
+
+
+def direct_loglike_stored(data: Data, h: torch.Tensor, precision="fp64",
+                          out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    p = _prec(precision)
+    W = h.shape[0]
+    dt = torch.complex128 if p == FP64 else torch.complex64
+    if out is None:
+        out = torch.empty((3, W), dtype=torch.float64, device="cuda")
+    _check(lib().direct_loglike_stored(data.handle, _dev(h, dt, (W, 3, data.grid["n"]), "h"), W, p,
+                                       _dev(out, torch.float64, (3, W), "out"), _stream(stream)))
+    return out
+
+
+# ---- heterodyne ---------------------------------------------------------------------------
+class Ref:
+    """mbh_ref handle: one heterodyne reference (summary data resident on the device)."""
+
+    def __init__(self, data: Data, theta0, n_bins: int, stream=None):
+        th = np.ascontiguousarray(np.asarray(theta0, dtype=np.float64).reshape(11))
+        h = vp()
+        _check(lib().het_prepare_reference(data.handle, th.ctypes.data_as(dp), int(n_bins),
+                                           _stream(stream), C.byref(h)))
+        self.handle = h
+        self.grid = dict(data.grid)
+        self.theta0 = th.copy()
+
+    @property
+    def bins(self) -> int:
+        return int(lib().mbh_ref_bins(self.handle))
+
+    def read(self) -> dict:
+        E = self.bins
+        edges = np.empty(E + 1, dtype=np.int64)
+        summ = np.empty((E, 3, 6))
+        h0e = np.empty((E + 1, 3), dtype=np.complex128)
+        dd = np.empty(1)
+        _check(lib().mbh_ref_read(self.handle, edges.ctypes.data_as(C.POINTER(C.c_int64)),
+                                  summ.ctypes.data_as(dp), h0e.view(np.float64).ctypes.data_as(dp),
+                                  dd.ctypes.data_as(dp)))
+        return dict(E=E, edges=edges, summary=summ, h0e=h0e, dd=float(dd[0]))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().mbh_ref_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def het_prepare_reference(data: Data, theta0, n_bins: int, stream=None) -> Ref:
+    return Ref(data, theta0, n_bins, stream)
+
+
+def het_loglike_batch(refs: Sequence[Ref], offsets, theta: torch.Tensor, precision="mixed",
+                      out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Walkers offsets[s]..offsets[s+1] of theta (11, W) use refs[s]."""
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    ns = len(refs)
+    if off.shape != (ns + 1,):
+        raise MBHError(1, f"offsets must have {ns + 1} entries")
+    W = int(off[-1])
+    if out is None:
+        out = torch.empty((3, W), dtype=torch.float64, device="cuda")
+    arr = (vp * max(ns, 1))(*[r.handle for r in refs])
+    _check(lib().het_loglike_batch(arr, off.ctypes.data_as(C.POINTER(C.c_int64)), ns,
+                                   _dev(theta, torch.float64, (11, W), "theta"), _prec(precision),
+                                   _dev(out, torch.float64, (3, W), "out"), _stream(stream)))
+    return out

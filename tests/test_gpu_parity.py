@@ -1,0 +1,300 @@
+"""GPU (CUDA, through the C ABI) against the FP64 CPU oracle on the same seeded
+inputs.  Each side builds its own data from the shared draws (mbh_inputs): its own
+PSD, injection template, noise scaling and SNR distance; the tests compare the
+results element by element.
+
+Tolerances (floating point):
+  * float64 path: |dlnL| <= 1e-6 * scale with scale = (<d|d> + <h|h> + 2|<d|h>|)/2
+    (relative 1e-6 is ill-conditioned near lnL ~ 0, so it is taken against the
+    size of the terms that cancel); templates within 1e-8 of max|h| (phases of up
+    to ~1e7 rad are reproduced to ~1e-9 rad);
+  * mixed path: heterodyne |dlnL| <= 1e-3 absolute for walkers near the reference
+    (the sampler's regime), and within 1e-6 * scale for every walker;
+  * integer bookkeeping (band, edges) bit-exact.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import mbh_inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def _lnl_err(gpu, ora, dd):
+    scale = 0.5 * (dd + np.abs(ora[2]) + 2 * np.abs(ora[1]))
+    return np.abs(gpu[0] - ora[0]), scale
+
+
+@pytest.fixture(scope="module")
+def M():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2111_01064_b300 import mbhlike
+    mbhlike.lib()
+    return mbhlike
+
+
+@pytest.fixture(scope="module")
+def WL(M):
+    from paper_2111_01064_b300 import workloads
+    return workloads
+
+
+@pytest.fixture(scope="module")
+def month(oracle, M, WL):
+    g = I.grid_month()
+    th_raw, snr = I.draw_source(I.rng(0), g["t_obs"])
+    z = I.noise_normals(I.rng(0, 100), g["n"])
+    src = WL.build_source(g, th_raw, snr, z)
+    f = oracle.freqs(g)
+    S = oracle.psd(f)
+    th_o = I.with_distance(th_raw, oracle.snr_distance(th_raw, g, snr, S))
+    d_o, _ = oracle.make_data(th_o, g, z, S)
+    walk_g = WL.walkers(src.theta_inj, 64, 0, lo=1e-4, hi=1e-3)
+    walk_o = WL.walkers(th_o, 64, 0, lo=1e-4, hi=1e-3)
+    return dict(g=g, src=src, S=S, f=f, th_o=th_o, d_o=d_o, walk_g=walk_g, walk_o=walk_o,
+                dd_o=oracle.inner(d_o, d_o, S, g["df"]))
+
+
+def test_psd(month, M):
+    S_g = M.mbh_psd_aet(month["g"]).cpu().numpy()
+    np.testing.assert_allclose(S_g, month["S"], rtol=1e-13)
+
+
+def test_snr_distance(month):
+    dg, do = month["src"].theta_inj[I.I_DL], month["th_o"][I.I_DL]
+    assert abs(dg / do - 1) < 1e-12
+
+
+def test_data_dd(month):
+    assert month["src"].data.dd == pytest.approx(month["dd_o"], rel=1e-12)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-8), ("mixed", 2e-5)])
+def test_template(month, M, WL, oracle, prec, tol):
+    g = month["g"]
+    th = month["walk_o"][:, :6]
+    h_g = M.template_batch(g, WL.to_dev(th), prec).cpu().numpy()
+    h_o = oracle.template_batch(th, g)
+    for w in range(th.shape[1]):
+        for c in range(3):
+            ref = np.abs(h_o[w, c]).max()
+            err = np.abs(h_g[w, c] - h_o[w, c]).max()
+            assert err <= tol * ref, (prec, w, c, err / ref)
+    # support bookkeeping is bit-exact
+    np.testing.assert_array_equal(h_g[:, 0] == 0, h_o[:, 0] == 0)
+
+
+def test_template_ragged_and_empty(month, M, WL, oracle):
+    g = I.grid_small(n=1000 + 37)
+    th = month["walk_o"][:, :3]
+    h_g = M.template_batch(g, WL.to_dev(th), "fp64").cpu().numpy()
+    h_o = oracle.template_batch(th, g)
+    np.testing.assert_allclose(h_g, h_o, rtol=0, atol=1e-8 * np.abs(h_o).max())
+    e = M.template_batch(g, WL.to_dev(np.zeros((11, 0))), "fp64")
+    assert e.shape == (0, 3, g["n"])
+
+
+def test_direct_fp64(month, M, WL, oracle):
+    g, src = month["g"], month["src"]
+    out_g = M.direct_loglike_batch(src.data, WL.to_dev(month["walk_g"]), "fp64").cpu().numpy()
+    out_o = oracle.direct(month["walk_o"], g, month["d_o"], month["S"])
+    err, scale = _lnl_err(out_g, out_o, month["dd_o"])
+    print("direct fp64 max rel", (err / scale).max(), "abs", err.max())
+    assert np.all(err <= 1e-6 * scale)
+    np.testing.assert_allclose(out_g[2], out_o[2], rtol=1e-9)
+
+
+def test_direct_stored_matches_fused(month, M, WL):
+    src = month["src"]
+    th = WL.to_dev(month["walk_g"][:, :13])   # ragged against the 4-template tile
+    h = M.template_batch(month["g"], th, "fp64")
+    a = M.direct_loglike_stored(src.data, h, "fp64").cpu().numpy()
+    b = M.direct_loglike_batch(src.data, th, "fp64").cpu().numpy()
+    np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-9)
+    h32 = M.template_batch(month["g"], th, "mixed")
+    c = M.direct_loglike_stored(src.data, h32, "mixed").cpu().numpy()
+    scale = 0.5 * (src.data.dd + np.abs(b[2]) + 2 * np.abs(b[1]))
+    print("stored fp32 vs fp64 max rel", (np.abs(c[0] - b[0]) / scale).max())
+    assert np.all(np.abs(c[0] - b[0]) <= 1e-5 * scale)
+
+
+def test_direct_mixed(month, M, WL, oracle):
+    g, src = month["g"], month["src"]
+    out_g = M.direct_loglike_batch(src.data, WL.to_dev(month["walk_g"]), "mixed").cpu().numpy()
+    out_o = oracle.direct(month["walk_o"], g, month["d_o"], month["S"])
+    err, scale = _lnl_err(out_g, out_o, month["dd_o"])
+    print("direct mixed max rel", (err / scale).max(), "abs p50/max", np.median(err), err.max())
+    assert np.all(err <= 1e-5 * scale)
+
+
+@pytest.fixture(scope="module")
+def refs(month, M, oracle):
+    g = month["g"]
+    ref_g = M.het_prepare_reference(month["src"].data, month["src"].theta_inj, 128)
+    ref_o = oracle.het_prepare(month["th_o"], g, month["d_o"], month["S"], 128)
+    return ref_g, ref_o
+
+
+def test_het_prepare(refs):
+    ref_g, ref_o = refs
+    r = ref_g.read()
+    assert r["E"] == ref_o["E"]
+    np.testing.assert_array_equal(r["edges"], ref_o["edges"])
+    for m in range(6):
+        x, y = r["summary"][:, :, m], ref_o["summary"][:, :, m]
+        np.testing.assert_allclose(x, y, rtol=0, atol=1e-9 * np.abs(y).max())
+    np.testing.assert_allclose(r["h0e"], ref_o["h0e"], rtol=0, atol=1e-8 * np.abs(ref_o["h0e"]).max())
+    assert r["dd"] == pytest.approx(ref_o["dd"], rel=1e-12)
+
+
+def test_het_fp64(month, refs, M, WL, oracle):
+    ref_g, ref_o = refs
+    W = month["walk_g"].shape[1]
+    out_g = M.het_loglike_batch([ref_g], [0, W], WL.to_dev(month["walk_g"]), "fp64").cpu().numpy()
+    out_o = oracle.het_loglike(month["walk_o"], ref_o)
+    err, scale = _lnl_err(out_g, out_o, ref_o["dd"])
+    print("het fp64 max rel", (err / scale).max(), "abs max", err.max())
+    assert np.all(err <= 1e-6 * scale)
+
+
+def test_het_mixed(month, refs, M, WL, oracle):
+    ref_g, ref_o = refs
+    th_g = WL.walkers(month["src"].theta_inj, 64, 0, lo=1e-6, hi=1e-4)
+    th_o = WL.walkers(month["th_o"], 64, 0, lo=1e-6, hi=1e-4)
+    out_g = M.het_loglike_batch([ref_g], [0, 64], WL.to_dev(th_g), "mixed").cpu().numpy()
+    out_o = oracle.het_loglike(th_o, ref_o)
+    err, scale = _lnl_err(out_g, out_o, ref_o["dd"])
+    print("het mixed near: abs p50/p99/max", np.median(err), np.quantile(err, 0.99), err.max())
+    assert err.max() <= 1e-3
+    far_g = month["walk_g"]
+    far = M.het_loglike_batch([ref_g], [0, far_g.shape[1]], WL.to_dev(far_g), "mixed").cpu().numpy()
+    far_o = oracle.het_loglike(month["walk_o"], ref_o)
+    err, scale = _lnl_err(far, far_o, ref_o["dd"])
+    print("het mixed 1e-4..1e-3: abs p50/max", np.median(err), err.max(), "rel max", (err / scale).max())
+    assert np.all(err <= 1e-6 * scale)
+
+
+def test_het_exact_at_reference(month, refs, M, WL):
+    ref_g, _ = refs
+    th = WL.to_dev(month["src"].theta_inj.reshape(11, 1))
+    het = M.het_loglike_batch([ref_g], [0, 1], th, "fp64").cpu().numpy()
+    dr = M.direct_loglike_batch(month["src"].data, th, "fp64").cpu().numpy()
+    scale = 0.5 * (month["src"].data.dd + abs(dr[2, 0]) + 2 * abs(dr[1, 0]))
+    assert abs(het[0, 0] - dr[0, 0]) <= 1e-11 * scale
+    mix = M.het_loglike_batch([ref_g], [0, 1], th, "mixed").cpu().numpy()
+    assert abs(mix[0, 0] - dr[0, 0]) <= 1e-3
+
+
+def test_het_multi_source_equals_single(month, M, WL):
+    """Walkers of several sources in one launch give the same results as one
+    launch per source (deterministic per-walker reduction)."""
+    g = month["g"]
+    srcs, refs, ths = [], [], []
+    for s, nb in enumerate((128, 7, 300)):
+        src = WL.source_for(3, g, source=s)
+        srcs.append(src)
+        refs.append(M.het_prepare_reference(src.data, src.theta_inj, nb))
+        ths.append(WL.walkers(src.theta_inj, (33, 1, 70)[s], 3, s, 1e-5, 1e-3))
+    off = np.concatenate([[0], np.cumsum([t.shape[1] for t in ths])])
+    th = WL.to_dev(np.concatenate(ths, axis=1))
+    for prec in ("fp64", "mixed"):
+        allg = M.het_loglike_batch(refs, off, th, prec).cpu().numpy()
+        for s in range(3):
+            one = M.het_loglike_batch([refs[s]], [0, ths[s].shape[1]], WL.to_dev(ths[s]), prec).cpu().numpy()
+            np.testing.assert_array_equal(allg[:, off[s]:off[s + 1]], one)
+
+
+def test_het_edge_cases(month, M, WL, oracle):
+    src = month["src"]
+    r1 = M.het_prepare_reference(src.data, src.theta_inj, 1)
+    assert r1.bins == 1
+    out = M.het_loglike_batch([r1], [0, 0], WL.to_dev(np.zeros((11, 0))), "mixed")
+    assert out.shape == (3, 0)
+    # a walker whose support misses most edges (10x the mass): finite, matches the oracle
+    far = src.theta_inj.copy()
+    far[I.I_MT] *= 10
+    ref_o = oracle.het_prepare(month["th_o"], month["g"], month["d_o"], month["S"], 1)
+    far_o = month["th_o"].copy()
+    far_o[I.I_MT] *= 10
+    a = M.het_loglike_batch([r1], [0, 1], WL.to_dev(far.reshape(11, 1)), "fp64").cpu().numpy()
+    b = oracle.het_loglike(far_o, ref_o)
+    assert np.all(np.isfinite(a))
+    assert abs(a[0, 0] - b[0, 0]) <= 1e-6 * (ref_o["dd"] + abs(b[2, 0]) + 2 * abs(b[1, 0]))
+
+
+def test_invalid_arguments(month, M, WL):
+    src = month["src"]
+    with pytest.raises(M.MBHError) as e:
+        M.het_prepare_reference(src.data, src.theta_inj, 0)
+    assert e.value.status == 1
+    with pytest.raises(M.MBHError):
+        M.mbh_psd_aet(dict(f0=-1.0, df=1e-6, n=10, t_obs=1e6))
+    ref = M.het_prepare_reference(src.data, src.theta_inj, 16)
+    th = WL.to_dev(month["walk_g"][:, :4])
+    with pytest.raises(M.MBHError):
+        M.het_loglike_batch([ref, ref], [0, 3, 2], th, "fp64")   # decreasing offsets
+    with pytest.raises(M.MBHError):
+        M.het_loglike_batch([ref], [0, 4], th, "half")
+
+
+# ---- full-size cases, sampled against the oracle ---------------------------------------
+@pytest.fixture(scope="module")
+def year(oracle, M, WL):
+    g = I.grid_year()
+    th_raw, snr = I.draw_source(I.rng(1), g["t_obs"])
+    z = I.noise_normals(I.rng(1, 100), g["n"])
+    src = WL.build_source(g, th_raw, snr, z)
+    f = oracle.freqs(g)
+    S = oracle.psd(f)
+    th_o = I.with_distance(th_raw, oracle.snr_distance(th_raw, g, snr, S))
+    d_o, _ = oracle.make_data(th_o, g, z, S)
+    return dict(g=g, src=src, S=S, th_o=th_o, d_o=d_o)
+
+
+def test_direct_full_size_sampled(year, M, WL, oracle):
+    """4096 prior-drawn templates on the 1-yr grid (the brute-force search batch),
+    in the launch configuration of the benchmark; 3 sampled templates against the
+    oracle, the rest through the fp64-vs-mixed agreement."""
+    g = year["g"]
+    th = I.draw_prior_batch(I.rng(1, 300), 4096, g["t_obs"])
+    # put a few templates near the injection so that lnL is not just -<d|d>/2
+    th[:, :8] = WL.walkers(year["src"].theta_inj, 8, 1, lo=1e-6, hi=1e-5)
+    out64 = M.direct_loglike_batch(year["src"].data, WL.to_dev(th), "fp64").cpu().numpy()
+    outm = M.direct_loglike_batch(year["src"].data, WL.to_dev(th), "mixed").cpu().numpy()
+    sample = [0, 3, 1234]
+    tho = th[:, sample].copy()
+    tho[:, :2] = WL.walkers(year["th_o"], 8, 1, lo=1e-6, hi=1e-5)[:, [0, 3]]
+    out_o = oracle.direct(tho, g, year["d_o"], year["S"])
+    err, scale = _lnl_err(out64[:, sample], out_o, year["src"].data.dd)
+    print("year direct fp64 sampled rel", err / scale)
+    assert np.all(err <= 1e-6 * scale)
+    scale_all = 0.5 * (year["src"].data.dd + np.abs(out64[2]) + 2 * np.abs(out64[1]))
+    rel = np.abs(outm[0] - out64[0]) / scale_all
+    print("year direct mixed vs fp64 rel max", rel.max(), "abs max", np.abs(outm[0] - out64[0]).max())
+    assert np.all(rel <= 1e-5)
+
+
+def test_het_full_size_sampled(year, M, WL, oracle):
+    """16384 walkers (8 temperatures x 2048) perturbed 1e-3..1e-1, 256 bins on the
+    1-yr grid; 32 sampled walkers against the oracle."""
+    g = year["g"]
+    ref_g = M.het_prepare_reference(year["src"].data, year["src"].theta_inj, 256)
+    ref_o = oracle.het_prepare(year["th_o"], g, year["d_o"], year["S"], 256)
+    r = ref_g.read()
+    np.testing.assert_array_equal(r["edges"], ref_o["edges"])
+    W = 16384
+    th_g = WL.walkers(year["src"].theta_inj, W, 2)
+    th_o = WL.walkers(year["th_o"], W, 2)
+    o64 = M.het_loglike_batch([ref_g], [0, W], WL.to_dev(th_g), "fp64").cpu().numpy()
+    omx = M.het_loglike_batch([ref_g], [0, W], WL.to_dev(th_g), "mixed").cpu().numpy()
+    sample = np.arange(0, W, W // 32)
+    out_o = oracle.het_loglike(np.ascontiguousarray(th_o[:, sample]), ref_o)
+    err, scale = _lnl_err(o64[:, sample], out_o, ref_o["dd"])
+    assert np.all(err <= 1e-6 * scale)
+    err, scale = _lnl_err(omx[:, sample], out_o, ref_o["dd"])
+    print("year het mixed sampled: abs p50/max", np.median(err), err.max(), "rel max", (err / scale).max())
+    assert np.all(err <= 1e-6 * scale)
