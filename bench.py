@@ -175,11 +175,14 @@ def run_ours(args) -> dict | None:
     g = I.grid_year()
     src = WL.source_for(2, g, source=rank)
     ref = M.het_prepare_reference(src.data, src.theta_inj, N_BINS)
-    th_np = WL.walkers(src.theta_inj, N_WALKERS, 2, source=rank)
+    nw = args.walkers
+    th_np = WL.walkers(src.theta_inj, nw, 2, source=rank)
     theta = WL.to_dev(th_np)
-    out = torch.empty((3, N_WALKERS), dtype=torch.float64, device=dev)
+    out = torch.empty((3, nw), dtype=torch.float64, device=dev)
     flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)  # 512 MiB > L2
-    offs = [0, N_WALKERS]
+    offs = [0, nw]
+    if args.only == "direct":
+        return run_direct_only(args, M, WL, g, src, rank, dev, stream, peaks, peak_src)
 
     def het_step(prec="mixed"):
         M.het_loglike_batch([ref], offs, theta, prec, out=out)
@@ -213,8 +216,12 @@ def run_ours(args) -> dict | None:
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total_ms = float(t.item())
     ms_per_step = total_ms / args.steps
-    value = ws * N_WALKERS * args.steps / (total_ms * 1e-3)
+    value = ws * nw * args.steps / (total_ms * 1e-3)
     mixed_out = out.cpu().numpy().copy()
+    if args.only == "het":
+        clk.__exit__(None, None, None)
+        return {"profile_case": "het", "walkers": nw, "value": value, "unit": UNIT,
+                "ms_per_step": ms_per_step} if rank == 0 else None
 
     # ---- float64 heterodyne kernel on the same batch (baseline) ----
     het_step("fp64")
@@ -229,13 +236,13 @@ def run_ours(args) -> dict | None:
         torch.cuda.synchronize()
         f64_ms.append(e0.elapsed_time(e1))
     fp64_out = out.cpu().numpy().copy()
-    fp64_rate = N_WALKERS / (statistics.median(f64_ms) * 1e-3)
+    fp64_rate = nw / (statistics.median(f64_ms) * 1e-3)
     scale = 0.5 * (src.data.dd + np.abs(fp64_out[2]) + 2 * np.abs(fp64_out[1]))
     dmix = np.abs(mixed_out[0] - fp64_out[0])
 
     # ---- e2e: host theta in, host lnL out, through the same C-ABI call ----
     th_host = torch.from_numpy(th_np).pin_memory()
-    out_host = torch.empty((3, N_WALKERS), dtype=torch.float64).pin_memory()
+    out_host = torch.empty((3, nw), dtype=torch.float64).pin_memory()
     theta_e2e = torch.empty_like(theta)
     for _ in range(2):
         theta_e2e.copy_(th_host, non_blocking=True)
@@ -253,7 +260,7 @@ def run_ours(args) -> dict | None:
         e2e_ev[i][1].record(stream)
     torch.cuda.synchronize()
     e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev)
-    e2e_value = ws * N_WALKERS * args.steps / (e2e_ms * 1e-3)
+    e2e_value = ws * nw * args.steps / (e2e_ms * 1e-3)
 
     # ---- direct likelihood: stored templates (HBM roofline) ----
     del flush
@@ -314,7 +321,7 @@ def run_ours(args) -> dict | None:
     sm_for_peak = peaks.get("sm_max_mhz", 2032.0)
     fp64_peak = fp64_peak_gflops(sm_for_peak)
     E = ref.bins
-    flop = N_WALKERS * (E + 1) * HET_MIXED_FP64_FLOP_PER_EDGE
+    flop = nw * (E + 1) * HET_MIXED_FP64_FLOP_PER_EDGE
     achieved = flop / (ms_per_step * 1e-3) / 1e9
     roof_traffic = None
     prof = os.path.join(ROOT, "profiles", "traffic.json")
@@ -328,7 +335,7 @@ def run_ours(args) -> dict | None:
         "scaling": "weak", "vs_baseline": None, "dtype": "f64 phases + f32 response (mixed)",
         "data": "synthetic (seeded injection in Gaussian noise from the analytic A/E/T PSD; LDC-1A "
                 "not available)",
-        "config": {"workload": WORKLOAD, "walkers": N_WALKERS, "temperatures": W_TEMPS,
+        "config": {"workload": WORKLOAD, "walkers": nw, "temperatures": W_TEMPS,
                    "bins_requested": N_BINS, "bins": E, "channels": 3, "grid_points": n,
                    "precision": "mixed", "l2": "flushed between steps (512 MiB write, outside the "
                    "timed events)", "parallelism": f"walker batches per rank x{ws}"},
@@ -375,6 +382,28 @@ def run_ours(args) -> dict | None:
     if ws > 1:
         torch.distributed.barrier()
     return res if rank == 0 else None
+
+
+def run_direct_only(args, M, WL, g, src, rank, dev, stream, peaks, peak_src) -> dict | None:
+    """Profiling case: the stored-template reduction alone (args.stored fp64 templates)."""
+    import torch
+    th = I.draw_prior_batch(I.rng(1, 300 + rank), args.stored, g["t_obs"])
+    h64 = M.template_batch(g, WL.to_dev(th), "fp64")
+    dout = torch.empty((3, args.stored), dtype=torch.float64, device=dev)
+    for _ in range(args.warmup):
+        M.direct_loglike_stored(src.data, h64, "fp64", out=dout)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        M.direct_loglike_stored(src.data, h64, "fp64", out=dout)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    n = g["n"]
+    gbs = (args.stored * 3 * n * 16 + 3 * n * 24) / (ms * 1e-3) / 1e9
+    return {"profile_case": "direct", "templates": args.stored, "ms": ms, "GB_per_s": gbs,
+            "frac_of_hbm": gbs / peaks["hbm_gbs"]} if rank == 0 else None
 
 
 def oracle_workload(walkers: int = N_WALKERS) -> dict:
@@ -448,6 +477,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="CPU work of the oracle baseline (0: skip)")
+    ap.add_argument("--only", default="all", choices=["all", "het", "direct"],
+                    help="profiling cases: time only the heterodyne steps or only the direct path")
+    ap.add_argument("--walkers", type=int, default=N_WALKERS, help="heterodyne batch (profiling)")
+    ap.add_argument("--stored", type=int, default=N_STORED, help="stored templates (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -456,7 +489,7 @@ def main():
     else:
         res = run_ours(args)
         ws, rank, _ = _dist()
-        if res is not None and rank == 0 and ws == 1 and args.cpu_seconds > 0:
+        if res is not None and rank == 0 and ws == 1 and args.cpu_seconds > 0 and args.only == "all":
             cb = cpu_baseline(args.cpu_seconds)
             res["cpu_baseline"] = {k: v for k, v in cb.items() if not k.startswith("_")}
             idx, ora = cb["_idx"], cb["_out"][0]
