@@ -122,6 +122,27 @@ MBH_API mbh_status direct_loglike_batch(const mbh_data* data, const double* thet
 MBH_API mbh_status direct_loglike_stored(const mbh_data* data, const void* h_dev, int64_t W,
                                  mbh_precision precision, double* out_dev, void* stream);
 
+/* direct_loglike_stored without device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory while they
+ * evaluate likelihoods (a fixed memory budget owned by another framework, a host
+ * callback that must not enter the allocator, a service that reserves all device
+ * memory up front).  Same arguments, layout and result as direct_loglike_stored; the
+ * partial sums live in one static 8 MiB device buffer held by every device that loads
+ * the library until the process exits.
+ *  - Size limit: W x (number of grid chunks) x 16 bytes must fit in 8 MiB (e.g. W up
+ *    to ~15,000 templates on a 1,051,920-point grid, more on shorter grids); larger
+ *    batches return MBH_EINVAL with the required size in mbh_last_error(), checked
+ *    before anything is queued.
+ *  - The first call on a device looks up the buffer's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call before
+ *    any stream capture.
+ *  - All calls on a device share the buffer: calls whose work overlaps on the GPU
+ *    (different streams, or different host threads) race and give wrong results;
+ *    serialise them, e.g. on one stream.
+ *  - Calls no cudaMalloc, cudaFree or other allocating routine. */
+MBH_API mbh_status direct_loglike_stored_noalloc(const mbh_data* data, const void* h_dev, int64_t W,
+                                         mbh_precision precision, double* out_dev, void* stream);
+
 /* Heterodyne reference (Sec. II B, Eqs. 15-16 and 18-19; Sec. III B).
  * theta0_host: float64 [11] on the host.  Band = first..last grid index where
  * h0 != 0; n_bins + 1 log-spaced edge targets from f(band start) to f(band end)

@@ -74,6 +74,11 @@ void direct_chunks(int64_t n, int64_t tiles, int64_t max_chunk, int64_t& chunk, 
 mbh_status direct_finish(double2* part, int nchunks, int64_t W, double dd, double* out,
                          cudaStream_t st);
 std::mutex& launch_mutex();
+mbh_status launch_direct_finalize(const double2* part, int nchunks, int64_t W, double dd, double* out,
+                                  cudaStream_t st);
+mbh_status stored_plan(const mbh_data* data, int64_t W, int64_t& chunk, int& nchunks);
+mbh_status launch_stored(const mbh_data* data, const void* h, int64_t W, mbh_precision p,
+                         double2* part, int64_t chunk, int nchunks, cudaStream_t st);
 
 // mixed-precision entry points (mbh_mixed.cu)
 mbh_status launch_template_mixed(const mbh_grid* g, const double* theta, int64_t W, float2* h,

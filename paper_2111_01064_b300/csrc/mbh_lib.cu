@@ -417,6 +417,18 @@ mbh_status direct_finish(double2* part, int nchunks, int64_t W, double dd, doubl
 }
 }  // namespace mbh
 
+namespace mbh {
+// Final pass of the direct reduction (lnL from the chunk partial sums) into `out`, without
+// releasing the partial-sum buffer (for callers that own it).
+mbh_status launch_direct_finalize(const double2* part, int nchunks, int64_t W, double dd, double* out,
+                                  cudaStream_t st)
+{
+    direct_finalize_kernel<<<(unsigned)((W + 255) / 256), 256, 0, st>>>(part, nchunks, W, dd, out);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MBH_OK : cuda_fail(e, "direct finalize");
+}
+}  // namespace mbh
+
 extern "C" mbh_status direct_loglike_batch(const mbh_data* data, const double* theta_dev, int64_t W,
                                            mbh_precision precision, double* out_dev, void* stream)
 {

@@ -59,6 +59,7 @@ def lib() -> C.CDLL:
         "mbh_data_free": (None, [vp]),
         "direct_loglike_batch": (C.c_int, [vp, vp, i64, C.c_int, vp, vp]),
         "direct_loglike_stored": (C.c_int, [vp, vp, i64, C.c_int, vp, vp]),
+        "direct_loglike_stored_noalloc": (C.c_int, [vp, vp, i64, C.c_int, vp, vp]),
         "het_prepare_reference": (C.c_int, [vp, dp, i32, vp, C.POINTER(vp)]),
         "mbh_ref_bins": (i32, [vp]),
         "mbh_ref_read": (C.c_int, [vp, C.POINTER(C.c_int64), dp, dp, dp]),
@@ -202,6 +203,20 @@ def direct_loglike_stored(data: Data, h: torch.Tensor, precision="fp64",
         out = torch.empty((3, W), dtype=torch.float64, device="cuda")
     _check(lib().direct_loglike_stored(data.handle, _dev(h, dt, (W, 3, data.grid["n"]), "h"), W, p,
                                        _dev(out, torch.float64, (3, W), "out"), _stream(stream)))
+    return out
+
+
+def direct_loglike_stored_noalloc(data: Data, h: torch.Tensor, precision="fp64", *,
+                                  out: torch.Tensor, stream=None) -> torch.Tensor:
+    """direct_loglike_stored for callers that cannot allocate device memory: the C
+    call allocates nothing (static 8 MiB scratch shared by all calls on a device, so
+    calls must not overlap on the GPU); `out` must be preallocated by the caller."""
+    p = _prec(precision)
+    W = h.shape[0]
+    dt = torch.complex128 if p == FP64 else torch.complex64
+    _check(lib().direct_loglike_stored_noalloc(data.handle, _dev(h, dt, (W, 3, data.grid["n"]), "h"),
+                                               W, p, _dev(out, torch.float64, (3, W), "out"),
+                                               _stream(stream)))
     return out
 
 
