@@ -25,8 +25,8 @@
  *    numbers (re, im); "complex128" = 2 x float64, "complex64" = 2 x float32.
  *  - Every *_dev pointer is a device pointer owned by the caller; it must stay
  *    valid until the work queued on `stream` has finished.  Handles (mbh_data,
- *    mbh_ref, mbh_server) are owned by the library and released only by their
- *    *_free call.
+ *    mbh_ref, mbh_het_graph, mbh_server) are owned by the library and released
+ *    only by their *_free call.
  *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls queue
  *    work asynchronously and return without synchronising, except where a
  *    call says it synchronises.
@@ -57,7 +57,8 @@ typedef enum {
     MBH_ENOMEM = 2,   /* device allocation failed */
     MBH_ECUDA = 3,    /* CUDA error (no device, launch failure, ...) */
     MBH_ETIMEOUT = 4, /* a bounded wait gave up (serving loop) */
-    MBH_EBUSY = 5     /* admission refused: over the memory budget or queue full */
+    MBH_EBUSY = 5,    /* admission refused: over the memory budget or queue full */
+    MBH_ECANCELED = 6 /* request cancelled before it was launched */
 } mbh_status;
 
 typedef enum {
@@ -129,10 +130,10 @@ MBH_API mbh_status direct_loglike_stored(const mbh_data* data, const void* h_dev
  * memory up front).  Same arguments, layout and result as direct_loglike_stored; the
  * partial sums live in one static 8 MiB device buffer held by every device that loads
  * the library until the process exits.
- *  - Size limit: W x (number of grid chunks) x 16 bytes must fit in 8 MiB (e.g. W up
- *    to ~15,000 templates on a 1,051,920-point grid, more on shorter grids); larger
- *    batches return MBH_EINVAL with the required size in mbh_last_error(), checked
- *    before anything is queued.
+ *  - Size limit: W x (number of grid chunks) x 16 bytes must fit in 8 MiB; large
+ *    batches use at least n / 262144 chunks, so on a 1,051,920-point grid W can
+ *    reach ~100,000 templates.  Larger batches return MBH_EINVAL with the required
+ *    size in mbh_last_error(), checked before anything is queued.
  *  - The first call on a device looks up the buffer's device address
  *    (cudaGetSymbolAddress) with that device current; make that first call before
  *    any stream capture.
@@ -175,6 +176,106 @@ MBH_API void mbh_ref_free(mbh_ref* ref);
 MBH_API mbh_status het_loglike_batch(const mbh_ref* const* refs, const int64_t* offsets_host,
                              int32_t n_sources, const double* theta_dev,
                              mbh_precision precision, double* out_dev, void* stream);
+
+/* Launch configuration of the heterodyne kernels.  A walker is handled by
+ * threads_per_walker threads (1, 2, 4, 8, 16 or 32) that deal its bin edges
+ * round-robin (each round covers threads_per_walker bins); a block of `block`
+ * threads (64, 128 or 256) holds block/threads_per_walker walkers of one source.
+ * persistent = 0: one block per walker tile; 1: a grid of (SMs x resident blocks)
+ * looping over the tiles, sources ordered by bin count (largest first).  For a
+ * given threads_per_walker the results are bitwise reproducible and independent of
+ * the block size, the persistent mode, the other walkers and sources in the launch
+ * and their order; threads_per_walker sets the order in which a walker's bins are
+ * summed, so changing it changes results in the last bits only. */
+typedef struct {
+    int32_t threads_per_walker;
+    int32_t block;
+    int32_t persistent;
+} mbh_het_config;
+
+/* het_loglike_batch with an explicit launch configuration (NULL = default). */
+MBH_API mbh_status het_loglike_batch_cfg(const mbh_ref* const* refs, const int64_t* offsets_host,
+                                 int32_t n_sources, const double* theta_dev,
+                                 mbh_precision precision, const mbh_het_config* cfg,
+                                 double* out_dev, void* stream);
+
+/* Autotuner for a given batch (same arguments as het_loglike_batch): times every
+ * configuration (reps launches each after one warm-up, CUDA events on `stream`),
+ * writes the fastest to *best and its time per batch to *best_ms.  out_dev is
+ * overwritten.  Synchronises `stream`. */
+MBH_API mbh_status mbh_het_autotune(const mbh_ref* const* refs, const int64_t* offsets_host,
+                            int32_t n_sources, const double* theta_dev, mbh_precision precision,
+                            double* out_dev, int32_t reps, void* stream, mbh_het_config* best,
+                            double* best_ms);
+
+/* A heterodyne batch captured once in a CUDA graph (on a private stream) and
+ * replayed with mbh_het_graph_launch: the refs, offsets, theta_dev and out_dev
+ * pointers are fixed at creation; the caller rewrites theta_dev in place between
+ * replays (e.g. one sampler step per replay).  The refs must outlive the graph. */
+typedef struct mbh_het_graph mbh_het_graph;
+MBH_API mbh_status mbh_het_graph_create(const mbh_ref* const* refs, const int64_t* offsets_host,
+                                int32_t n_sources, const double* theta_dev, mbh_precision precision,
+                                const mbh_het_config* cfg, double* out_dev, void* stream,
+                                mbh_het_graph** out);
+MBH_API mbh_status mbh_het_graph_launch(mbh_het_graph* graph, void* stream);
+MBH_API void mbh_het_graph_free(mbh_het_graph* graph);
+
+/* ---- serving loop --------------------------------------------------------------
+ * Continuous batching of heterodyned-likelihood requests from many concurrent
+ * samplers (the batched evaluations of Sec. III B-C) on the current device.
+ * Sources (prepared references) stay resident on the device and are admitted while
+ * their footprint fits hbm_budget_bytes.  A request = one source and W walkers;
+ * submit copies theta (the caller may reuse its buffer on return) and queues it; a
+ * worker thread packs queued requests of any sources into one multi-source launch
+ * whenever one of max_inflight_batches slots (fixed device buffers for
+ * max_batch_walkers walkers, counted in the budget, one stream each) is free, so a
+ * new batch's copies and kernel overlap those in flight.  A request's results are
+ * the same alone and in a batch. */
+typedef struct mbh_server mbh_server;
+typedef struct {
+    int64_t hbm_budget_bytes;       /* device memory for slots + resident sources */
+    int32_t max_batch_walkers;      /* walkers per launch (and per request) */
+    int32_t max_inflight_batches;   /* slots */
+    int32_t max_queue;              /* queued requests before submit returns MBH_EBUSY */
+    mbh_precision precision;
+    mbh_het_config config;          /* threads_per_walker = 0: default configuration */
+} mbh_server_opts;
+typedef struct {
+    int64_t completed, walkers, batches, rejected, queued;
+    double mean_batch_walkers;
+    double p50_ms, p99_ms, max_ms;  /* submit -> results written, completed requests */
+    double walkers_per_s;           /* walkers completed / (first submit .. last completion) */
+    int64_t source_bytes, slot_bytes;
+} mbh_server_report;
+
+/* Starts the worker thread.  MBH_EBUSY if the slots alone exceed the budget. */
+MBH_API mbh_status mbh_server_create(const mbh_server_opts* opts, mbh_server** out);
+/* Registers a prepared reference (which must outlive the server or its removal);
+ * MBH_EBUSY if it does not fit the budget. */
+MBH_API mbh_status mbh_server_add_source(mbh_server* server, const mbh_ref* ref, int32_t* source_id);
+/* Evicts a source: its queued requests complete with MBH_EINVAL, batches in flight
+ * finish first (the call blocks until then). */
+MBH_API mbh_status mbh_server_remove_source(mbh_server* server, int32_t source_id);
+/* theta_host: float64 [11][W]; out_host: float64 [3][W] (lnL, <d|h>, <h|h>), written
+ * on completion and owned by the caller until mbh_server_wait returns.  MBH_EBUSY
+ * when the queue is full, MBH_EINVAL for an unknown source or W outside
+ * [1, max_batch_walkers]. */
+MBH_API mbh_status mbh_server_submit(mbh_server* server, int32_t source_id, const double* theta_host,
+                             int64_t W, double* out_host, uint64_t* request_id);
+/* Waits up to timeout_ms (< 0: no limit); MBH_ETIMEOUT if the request is not done.
+ * *request_status: MBH_OK, MBH_ECANCELED, MBH_EINVAL (source evicted) or a CUDA
+ * error of its batch.  A request can be waited for once. */
+MBH_API mbh_status mbh_server_wait(mbh_server* server, uint64_t request_id, int32_t timeout_ms,
+                           mbh_status* request_status);
+/* paused != 0: keep admitting and queueing requests but launch nothing (batches
+ * already in flight finish); 0: resume. */
+MBH_API mbh_status mbh_server_pause(mbh_server* server, int32_t paused);
+/* Cancels a request that has not been launched (MBH_EBUSY once it has). */
+MBH_API mbh_status mbh_server_cancel(mbh_server* server, uint64_t request_id);
+MBH_API mbh_status mbh_server_stats(mbh_server* server, mbh_server_report* out);
+MBH_API mbh_status mbh_server_reset_stats(mbh_server* server);
+/* Cancels queued requests, waits for batches in flight, stops the worker. */
+MBH_API void mbh_server_free(mbh_server* server);
 
 #ifdef __cplusplus
 }

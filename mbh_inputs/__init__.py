@@ -126,6 +126,25 @@ def perturb(theta0: np.ndarray, eps: np.ndarray) -> np.ndarray:
     return th
 
 
+def draw_uneven_batch(g: np.random.Generator, n_sources: int, bins=(64, 512),
+                      walkers=(128, 4096)) -> tuple[np.ndarray, np.ndarray]:
+    """Per-source bin counts U{bins[0]..bins[1]} and walker counts log-uniform in
+    [walkers[0], walkers[1]) (the uneven multi-source batch)."""
+    nb = g.integers(bins[0], bins[1] + 1, n_sources)
+    nw = np.round(np.exp(g.uniform(math.log(walkers[0]), math.log(walkers[1]), n_sources))).astype(np.int64)
+    return nb.astype(np.int64), nw
+
+
+def draw_requests(g: np.random.Generator, n: int, size=(64, 4096), pool: int = 4096,
+                  rate: float = 1.0) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """Serving requests: sizes log-uniform in [size[0], size[1]], start offsets inside a
+    per-source pool of `pool` walkers, and Poisson inter-arrival gaps at `rate` (per s)."""
+    sz = np.round(np.exp(g.uniform(math.log(size[0]), math.log(size[1]), n))).astype(np.int64)
+    start = (g.uniform(size=n) * (pool - sz + 1)).astype(np.int64)
+    gaps = g.exponential(1.0 / rate, n)
+    return sz, start, gaps
+
+
 def noise_normals(g: np.random.Generator, n: int, channels: int = 3) -> np.ndarray:
     """Standard normals of shape (channels, n, 2): real and imaginary parts."""
     return g.standard_normal((channels, n, 2))

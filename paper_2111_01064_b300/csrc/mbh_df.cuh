@@ -1,11 +1,11 @@
-// Double-float ("df") helpers: float64-class arithmetic on B300's float32 and integer pipes.
+// Double-float ("df") arithmetic: float64-class results on B300's float32 and integer pipes.
 //
-// B300 executes float64 FMA at 2 per SM per clock (1/64 of float32), so even a streaming
-// reduction that does five float64 operations per complex element is bound by the float64
-// pipe at ~1.8 TB/s, far below HBM.  Here a float64 input x is split exactly, with integer
-// operations only, into floats hi + lo = x * 2^-sh (hi: sign, exponent and the top 23
-// mantissa bits; lo: the remaining 29 bits, rounded to 24); products use the FMA two-product
-// and sums the two-sum, so results carry ~47 bits without touching the float64 unit.
+// B300 executes float64 FMA at 2 per SM per clock, 1/64 of float32 (measured 566 G/s against
+// 34.6 T/s), and its float64 pipe also carries conversions, compares and rounding.  A value is
+// kept as an unevaluated sum hi + lo of two floats (~48 significant bits); products use the
+// FMA two-product, sums Knuth's two-sum.  All primitives use the _rn intrinsics so that the
+// compiler cannot contract a product into a following add, which would break the error-free
+// transformations.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -17,8 +17,15 @@ struct f2 {
     float hi, lo;
 };
 
-// x * 2^-sh as hi + lo (relative error <= 2^-47).  Zero, denormals and magnitudes below
-// 2^-75 (after scaling) map to 0; the caller picks sh so that |x| 2^-sh stays below 2^127.
+// exact split of a double constant (host or device, compile time)
+__host__ __device__ constexpr f2 df_const(double x)
+{
+    return {(float)x, (float)(x - (double)(float)x)};
+}
+
+// x * 2^-sh as hi + lo (relative error <= 2^-47) with integer operations only.  Zero,
+// denormals and magnitudes below 2^-75 (after scaling) map to 0; the caller picks sh so that
+// |x| 2^-sh stays below 2^127.
 __device__ __forceinline__ f2 split_f64(double x, int sh)
 {
     const unsigned long long u = (unsigned long long)__double_as_longlong(x);
@@ -29,34 +36,89 @@ __device__ __forceinline__ f2 split_f64(double x, int sh)
     const unsigned long long mant = u & 0xFFFFFFFFFFFFFull;
     const unsigned hib = sign | ((unsigned)fe << 23) | (unsigned)(mant >> 29);
     const unsigned rem = (unsigned)(mant & 0x1FFFFFFFull);
-    const float lo = __uint2float_rn(rem) * __int_as_float((fe - 52) << 23);   // rem 2^(fe-179)
+    const float lo = __fmul_rn(__uint2float_rn(rem), __int_as_float((fe - 52) << 23));  // rem 2^(fe-179)
     return {__int_as_float((int)hib), __int_as_float(__float_as_int(lo) | (int)sign)};
 }
 
-// a * b with a, b as (hi, lo): hi*hi exactly as p + e (FMA), plus the cross terms.
+// s + e = a + b exactly
+__device__ __forceinline__ f2 two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+// s + e = a + b exactly when |a| >= |b|
+__device__ __forceinline__ f2 fast_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ f2 dd_add(f2 a, f2 b)
+{
+    f2 s = two_sum(a.hi, b.hi);
+    s.lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+    return fast_two_sum(s.hi, s.lo);
+}
+
+__device__ __forceinline__ f2 dd_neg(f2 a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ f2 dd_sub(f2 a, f2 b) { return dd_add(a, dd_neg(b)); }
+
+__device__ __forceinline__ f2 dd_add_f(f2 a, float b)
+{
+    f2 s = two_sum(a.hi, b);
+    s.lo = __fadd_rn(s.lo, a.lo);
+    return fast_two_sum(s.hi, s.lo);
+}
+
+__device__ __forceinline__ f2 dd_mul(f2 a, f2 b)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+    return fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ f2 dd_mul_f(f2 a, float b)
+{
+    const float p = __fmul_rn(a.hi, b);
+    float e = __fmaf_rn(a.hi, b, -p);
+    e = __fmaf_rn(a.lo, b, e);
+    return fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ f2 dd_fma(f2 a, f2 b, f2 c) { return dd_add(dd_mul(a, b), c); }
+
+__device__ __forceinline__ float dd_to_float(f2 a) { return __fadd_rn(a.hi, a.lo); }
+
+// sign test of a (normalised) df value
+__device__ __forceinline__ bool dd_le0(f2 a) { return a.hi < 0.0f || (a.hi == 0.0f && a.lo <= 0.0f); }
+__device__ __forceinline__ bool dd_lt0(f2 a) { return a.hi < 0.0f || (a.hi == 0.0f && a.lo < 0.0f); }
+
+// ---- unnormalised accumulation used by the streaming reduction --------------------------
+// a * b with a, b as (hi, lo): hi*hi exactly as p + e, plus the cross terms (not normalised).
 __device__ __forceinline__ f2 df_mul(f2 a, f2 b)
 {
-    const float p = a.hi * b.hi;
-    const float e = fmaf(a.hi, b.hi, -p);
-    return {p, e + fmaf(a.hi, b.lo, a.lo * b.hi)};
+    const float p = __fmul_rn(a.hi, b.hi);
+    const float e = __fmaf_rn(a.hi, b.hi, -p);
+    return {p, __fadd_rn(e, __fmaf_rn(a.hi, b.lo, __fmul_rn(a.lo, b.hi)))};
 }
 
 __device__ __forceinline__ f2 df_sqr(f2 a)
 {
-    const float p = a.hi * a.hi;
-    const float e = fmaf(a.hi, a.hi, -p);
-    return {p, fmaf(2.0f * a.hi, a.lo, e)};
+    const float p = __fmul_rn(a.hi, a.hi);
+    const float e = __fmaf_rn(a.hi, a.hi, -p);
+    return {p, __fmaf_rn(2.0f * a.hi, a.lo, e)};
 }
 
-// s += x with Knuth's two-sum on the high parts; low parts and the rounding error are
-// collected in s.lo.
+// s += x with the two-sum on the high parts; low parts and the rounding error go to s.lo.
 __device__ __forceinline__ void df_acc(f2& s, f2 x)
 {
-    const float t = s.hi + x.hi;
-    const float bp = t - s.hi;
-    const float err = (s.hi - (t - bp)) + (x.hi - bp);
-    s.hi = t;
-    s.lo += err + x.lo;
+    const f2 t = two_sum(s.hi, x.hi);
+    s.hi = t.hi;
+    s.lo = __fadd_rn(s.lo, __fadd_rn(t.lo, x.lo));
 }
 
 __device__ __forceinline__ f2 df_add(f2 a, f2 b)

@@ -14,11 +14,12 @@ namespace mbh {
 constexpr int kMaxBins = 4096;
 constexpr int kMaxSrc = 96;   // sources per launch (descriptors travel as kernel parameters)
 
-// Edge record of the mixed-precision heterodyne: the frequency tables that make the float64
-// phase chain free of cbrt/log, the reference's float64 large phase Phi0 and 1/H0 of the
-// float32 transfer part (h0 = H0 e^{-i Phi0}).
+// Edge record of the mixed-precision heterodyne: the frequency tables that make the
+// double-float phase chain free of cbrt/log (f, f^{1/3}, f^{-1/3}, ln f / 3 as float pairs),
+// the reference's large phase Phi0 (float pair) and 1/H0 of the float32 transfer part
+// (h0 = H0 e^{-i Phi0}).
 struct MixEdge {
-    double f, f3, fm3, lnf3, phi0;
+    float2 f, f3, fm3, lnf3, phi0;
     float2 h0inv[3];
 };
 // Bin record of the mixed-precision heterodyne: float32 summary data and 1/(f_hi - f_lo).
@@ -65,15 +66,9 @@ mbh_status fail(mbh_status s, const char* fmt, ...);
 mbh_status cuda_fail(cudaError_t e, const char* where);
 mbh_status check_grid(const mbh_grid* g);
 mbh_status check_device();
-mbh_status check_het_args(const mbh_ref* const* refs, const int64_t* offsets, int32_t n_src,
-                          const double* theta, double* out);
-mbh_status build_launch(const mbh_ref* const* refs, const int64_t* offsets, int32_t n_src,
-                        int64_t first, int32_t count, int wpb, const double* theta, int64_t W,
-                        double* out, HetLaunch& L);
 void direct_chunks(int64_t n, int64_t tiles, int64_t max_chunk, int64_t& chunk, int& nchunks);
 mbh_status direct_finish(double2* part, int nchunks, int64_t W, double dd, double* out,
                          cudaStream_t st);
-std::mutex& launch_mutex();
 mbh_status launch_direct_finalize(const double2* part, int nchunks, int64_t W, double dd, double* out,
                                   cudaStream_t st);
 mbh_status stored_plan(const mbh_data* data, int64_t W, int64_t& chunk, int& nchunks);
@@ -86,16 +81,17 @@ mbh_status launch_template_mixed(const mbh_grid* g, const double* theta, int64_t
 mbh_status launch_direct_fused_mixed(const mbh_data* data, const double* theta, int64_t W,
                                      double* out, cudaStream_t st);
 cudaError_t alloc_ref_tables(mbh_ref* R);
+mbh_status make_freq_tables(mbh_data* D, cudaStream_t st);
 void free_ref_tables(mbh_ref* R);
 cudaError_t prepare_mixed_tables(mbh_ref* R, cudaStream_t st);
-struct HetTuning {
-    int threads_per_walker;   // 1, 2, 4, 8, 16 or 32
-    int block;                // threads per block (multiple of 32)
-    int persistent_blocks;    // 0: one block per tile; else grid size of the persistent loop
+// heterodyne kernel instantiations: launcher and kernel address (for occupancy queries)
+using HetLauncher = cudaError_t (*)(const HetLaunch&, int, cudaStream_t);
+struct HetKernel {
+    HetLauncher launch;
+    const void* fn;
 };
-mbh_status run_het_mixed(const mbh_ref* const* refs, const int64_t* offsets, int32_t n_src,
-                         const double* theta, int64_t W, double* out, cudaStream_t st,
-                         const HetTuning* tuning);
+HetKernel het_kernel_f64(int G, int block);
+HetKernel het_kernel_mixed(int G, int block);
 
 // ------------------------------------------------------------------------------------------
 // reductions
@@ -137,6 +133,8 @@ struct mbh_data {
     float* wv32 = nullptr;   // [3][n] sigma^2 4 df/S (mixed path)
     float4* wsp = nullptr;   // [3][n] float pairs of 2^shift 4 df d/S: (re hi, im hi, re lo, im lo)
     float2* vsp = nullptr;   // [3][n] float pair of 2^(2 shift) 4 df/S
+    float4* ftab = nullptr;  // [n] (f hi, f lo, f^{1/3} hi, f^{1/3} lo) of the grid
+    float4* ftab2 = nullptr; // [n] (f^{-1/3} hi, lo, ln(f)/3 hi, lo)
     double sigma = 1.0;      // scale of the float32 copies: h/sigma is O(1)
     int shift = 0;           // round(log2 sigma): templates are split as h 2^-shift
     double dd = 0.0;         // <d|d>

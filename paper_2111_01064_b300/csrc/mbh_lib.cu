@@ -296,6 +296,12 @@ extern "C" mbh_status mbh_data_create(const mbh_grid* grid, const void* d_dev, c
     data_kernel<<<nb, kDataThreads, 0, st>>>((const double2*)d_dev, psd_dev, m, grid->df, D->sigma,
                                              D->shift, D->wd, D->wv, D->wd32, D->wv32, D->wsp,
                                              D->vsp, part);
+    if (mbh_status s = make_freq_tables(D, st)) {
+        cudaFreeAsync(part, st);
+        cudaStreamSynchronize(st);
+        mbh_data_free(D);
+        return s;
+    }
     sum_partials_kernel<<<1, 32, 0, st>>>(part, nb, dd_dev);
     e = cudaMemcpyAsync(&D->dd, dd_dev, sizeof(double), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaFreeAsync(part, st);
@@ -320,6 +326,8 @@ extern "C" void mbh_data_free(mbh_data* data)
     if (data->wv32) cudaFree(data->wv32);
     if (data->wsp) cudaFree(data->wsp);
     if (data->vsp) cudaFree(data->vsp);
+    if (data->ftab) cudaFree(data->ftab);
+    if (data->ftab2) cudaFree(data->ftab2);
     delete data;
 }
 
@@ -790,88 +798,27 @@ __global__ void __launch_bounds__(BLOCK)
     }
 }
 
+namespace {
+template <int G, int BLOCK>
+cudaError_t launch_het_f64(const HetLaunch& L, int grid, cudaStream_t st)
+{
+    het_f64_kernel<G, BLOCK><<<grid, BLOCK, 0, st>>>(L);
+    return cudaGetLastError();
+}
+}  // namespace
+
 namespace mbh {
-mbh_status build_launch(const mbh_ref* const* refs, const int64_t* offsets, int32_t n_src,
-                        int64_t first, int32_t count, int wpb, const double* theta, int64_t W,
-                        double* out, HetLaunch& L)
+HetKernel het_kernel_f64(int G, int block)
 {
-    L.theta = theta;
-    L.W = W;
-    L.out = out;
-    L.n_src = count;
-    int tiles = 0;
-    for (int32_t j = 0; j < count; ++j) {
-        const int32_t s = (int32_t)first + j;
-        const mbh_ref* R = refs[s];
-        SrcDesc& S = L.src[j];
-        S.summary = R->summary;
-        S.h0inv = R->h0inv;
-        S.fe = R->fe;
-        S.invw = R->invw;
-        S.mix = R->mix;
-        S.dd = R->dd;
-        S.t_obs = R->grid.t_obs;
-        S.E = R->E;
-        S.w_begin = offsets[s];
-        S.w_end = offsets[s + 1];
-        S.tile_begin = tiles;
-        const int64_t nt = (S.w_end - S.w_begin + wpb - 1) / wpb;
-        if (tiles + nt > 0x7fffffff) return fail(MBH_EINVAL, "too many walker tiles");
-        tiles += (int)nt;
-    }
-    L.n_tiles = tiles;
-    (void)n_src;
-    return MBH_OK;
-}
-
-template <int G>
-static mbh_status run_het_f64(const mbh_ref* const* refs, const int64_t* offsets, int32_t n_src,
-                              const double* theta, int64_t W, double* out, cudaStream_t st)
-{
-    constexpr int BLOCK = 128;
-    constexpr int WPB = BLOCK / G;
-    static HetLaunch L;  // large: keep off the stack; filled and consumed under the host lock
-    std::lock_guard<std::mutex> lk(launch_mutex());
-    for (int32_t first = 0; first < n_src; first += kMaxSrc) {
-        const int32_t count = std::min<int32_t>(kMaxSrc, n_src - first);
-        if (mbh_status s = build_launch(refs, offsets, n_src, first, count, WPB, theta, W, out, L)) return s;
-        if (L.n_tiles == 0) continue;
-        het_f64_kernel<G, BLOCK><<<L.n_tiles, BLOCK, 0, st>>>(L);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return cuda_fail(e, "het_f64_kernel");
-    }
-    return MBH_OK;
-}
-
-mbh_status check_het_args(const mbh_ref* const* refs, const int64_t* offsets, int32_t n_src,
-                          const double* theta, double* out)
-{
-    if (n_src < 0) return fail(MBH_EINVAL, "n_sources < 0");
-    if (n_src == 0) return MBH_OK;
-    if (!refs || !offsets) return fail(MBH_EINVAL, "NULL refs/offsets");
-    if (offsets[0] != 0) return fail(MBH_EINVAL, "offsets[0] must be 0");
-    int dev = -1;
-    cudaGetDevice(&dev);
-    for (int32_t s = 0; s < n_src; ++s) {
-        if (!refs[s]) return fail(MBH_EINVAL, "refs[%d] is NULL", s);
-        if (offsets[s + 1] < offsets[s]) return fail(MBH_EINVAL, "offsets must be non-decreasing");
-        if (refs[s]->device != dev) return fail(MBH_EINVAL, "refs[%d] lives on another device", s);
-    }
-    if (offsets[n_src] > 0 && (!theta || !out)) return fail(MBH_EINVAL, "NULL theta/out");
-    return MBH_OK;
+#define MBH_CASE(g, b) \
+    if (G == g && block == b) return {&launch_het_f64<g, b>, (const void*)&het_f64_kernel<g, b>};
+    MBH_CASE(1, 64) MBH_CASE(1, 128) MBH_CASE(1, 256)
+    MBH_CASE(2, 64) MBH_CASE(2, 128) MBH_CASE(2, 256)
+    MBH_CASE(4, 64) MBH_CASE(4, 128) MBH_CASE(4, 256)
+    MBH_CASE(8, 64) MBH_CASE(8, 128) MBH_CASE(8, 256)
+    MBH_CASE(16, 64) MBH_CASE(16, 128) MBH_CASE(16, 256)
+    MBH_CASE(32, 64) MBH_CASE(32, 128) MBH_CASE(32, 256)
+#undef MBH_CASE
+    return {nullptr, nullptr};
 }
 }  // namespace mbh
-
-extern "C" mbh_status het_loglike_batch(const mbh_ref* const* refs, const int64_t* offsets_host,
-                                        int32_t n_sources, const double* theta_dev,
-                                        mbh_precision precision, double* out_dev, void* stream)
-{
-    if (mbh_status s = check_het_args(refs, offsets_host, n_sources, theta_dev, out_dev)) return s;
-    if (n_sources == 0 || offsets_host[n_sources] == 0) return MBH_OK;
-    const int64_t W = offsets_host[n_sources];
-    cudaStream_t st = (cudaStream_t)stream;
-    if (precision == MBH_MIXED)
-        return run_het_mixed(refs, offsets_host, n_sources, theta_dev, W, out_dev, st, nullptr);
-    if (precision != MBH_FP64) return fail(MBH_EINVAL, "unknown precision %d", (int)precision);
-    return run_het_f64<8>(refs, offsets_host, n_sources, theta_dev, W, out_dev, st);
-}

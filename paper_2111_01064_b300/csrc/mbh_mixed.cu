@@ -1,37 +1,34 @@
-// Mixed-precision path of libmbhlike (Katz, arXiv:2111.01064, Sec. II): the large phases
-// Phi(f) = Psi(f) + 2 pi f k.c(t(f)) (up to ~1e7 rad) and t(f) stay float64; amplitudes, the
-// response, ratios and products are float32; sums are float64.
+// Mixed-precision path of libmbhlike (Katz, arXiv:2111.01064, Sec. II): the large phase
+// Phi(f) = Psi(f) + 2 pi f k.c(t(f)) (up to ~1e7 rad) and t(f) are carried in double-float
+// (float pairs, ~48 bits, mbh_df.cuh); amplitudes, the response, ratios and products are
+// float32; sums are double-float or float64.
 //
-// B300 runs float64 FMA at ~1/61 of the float32 rate and float64 sin/log far slower still,
-// so the float64 part is cut to multiply-adds:
+// B300 runs float64 FMA at 1/64 of the float32 rate, and its float64 pipe also carries
+// conversions, compares and rounding; a float64 phase chain left this kernel bound by that
+// pipe (84% busy, float32 pipe 12%).  The chain therefore runs on the float32 pipe:
 //  - v = (pi M f)^{1/3} and ln v come from per-frequency tables (f^{1/3}, f^{-1/3}, ln f / 3)
-//    times per-walker constants, so no float64 cbrt/log per point;
+//    times per-walker constants, so there is no cbrt/log per point;
 //  - the orbital angle alpha(t) = alpha(t_ref) + dalpha with dalpha = 2 pi (t - t_ref)/yr:
-//    sin/cos alpha(t_ref) are float64 per walker and the correction
+//    sin/cos alpha(t_ref) are double-float per walker and the correction
 //    (cos dalpha - 1, sin dalpha) is float32 from the half angle, accurate relative to its
-//    own (small) size, then added in float64;
-//  - the phase is reduced modulo 2 pi in float64 and only then rounded to float32.
+//    own (small) size;
+//  - the phase is reduced modulo 2 pi in double-float and only then rounded to float32.
 // The heterodyne works in delta = r - 1 = (rho - 1) e^{-i dPhi} + (e^{-i dPhi} - 1), with
-// rho = H/H0 the float32 ratio of the transfer parts and dPhi = Phi - Phi0 in float64, and
-// contracts the "1" part once in float64 (sum Re A0, sum B0).
+// rho = H/H0 the float32 ratio of the transfer parts and dPhi = Phi - Phi0 in double-float,
+// and contracts the "1" part once in float64 (sum Re A0, sum B0).
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <mutex>
 
+#include "mbh_df.cuh"
 #include "mbh_internal.cuh"
 #include "mbh_model.cuh"
 
 using namespace mbh;
 
 namespace mbh {
-
-std::mutex& launch_mutex()
-{
-    static std::mutex m;
-    return m;
-}
 
 struct cf { float re, im; };
 __device__ __forceinline__ cf fmul(cf a, cf b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
@@ -44,25 +41,6 @@ struct WalkerF {
     float k[3], Pp[6], Pc[6], Kp[2], Kc[2];
     float sa_ref, ca_ref, amp, inv_fc2;
 };
-
-__device__ inline void walker_f32(const Walker& w, WalkerF& m)
-{
-#pragma unroll
-    for (int j = 0; j < 3; ++j) m.k[j] = (float)w.k[j];
-#pragma unroll
-    for (int j = 0; j < 6; ++j) {
-        m.Pp[j] = (float)w.Pp[j];
-        m.Pc[j] = (float)w.Pc[j];
-    }
-    m.Kp[0] = (float)w.Kp[0];
-    m.Kp[1] = (float)w.Kp[1];
-    m.Kc[0] = (float)w.Kc[0];
-    m.Kc[1] = (float)w.Kc[1];
-    m.sa_ref = (float)w.sa_ref;
-    m.ca_ref = (float)w.ca_ref;
-    m.amp = (float)w.amp;
-    m.inv_fc2 = (float)w.inv_fc2;
-}
 
 __device__ __forceinline__ float nPnf(const float* P, const float* n)
 {
@@ -149,73 +127,224 @@ __device__ inline void transfer_f32(const WalkerF& w, float f, float sa, float c
     T[2] = fscale(fmul(fmul(W2, W1), tsum), (float)(1.0 / kSqrt3));
 }
 
-// Float64 large phase Phi(f) and float32 amplitude, orbit angle, from the frequency tables.
-// Returns false outside the support (f > f_cut or t(f) outside [0, t_obs]).
-__device__ __forceinline__ bool phase_mixed(const Walker& w, const WalkerF& wf, double f, double f3,
-                                            double fm3, double lnf3, double t_obs, double& Phi,
-                                            float& sa, float& ca, float& amp)
+constexpr f2 kTwoPiDF = df_const(kTwoPi);
+constexpr f2 kInvTwoPiDF = df_const(kInvTwoPi);
+constexpr f2 kAUSecDF = df_const(kAUSec);
+
+// Per-walker constants of the phase chain as float pairs.
+struct WalkerDF {
+    f2 c[8], d[8], cl5, cl6, dl6;
+    f2 cbrt_piM, icbrt_piM, ln_cbrt_piM;
+    f2 tref, fmax, fcut, psi_max, dpsi_max;
+    f2 sa_ref, ca_ref, kx, ky;
+};
+
+__device__ __forceinline__ f2 split_d(double x)
 {
-    const double v = w.cbrt_piM * f3;
-    const double iv = w.icbrt_piM * fm3;
-    const double lnv = w.ln_cbrt_piM + lnf3;
-    double P = w.c[7], Q = w.d[7];
+    const float hi = (float)x;
+    return {hi, (float)(x - (double)hi)};
+}
+
+// v and ln v at f_max: pi M f_max = 0.05 pi sqrt(5/12) for every mass (f_max = f_c sqrt(5/12),
+// f_c = 0.05/M), so v(f_max) = (0.05 pi sqrt(5/12))^{1/3} is a constant.
+constexpr double kPiMfmax = 0.10139446689934029;   // 0.05 pi sqrt(5/12)
+
+// Per-walker constants of the mixed path (Sec. II A parameter derivation), in float64: the
+// large-phase constants (PN coefficients, the v and ln v scales, t_ref and the f_max
+// references, the orbital angle at t_ref, the in-plane propagation components) are split
+// into float pairs with integer operations (split_f64); the amplitude, polarisation and mode
+// factors are rounded once to float32.  One thread per walker; the caller spreads walkers
+// over full warps (a float64 warp instruction costs the same with 4 or 32 active lanes).
+__device__ inline void walker_setup_mixed(const double* __restrict__ theta, int64_t W, int64_t i,
+                                          WalkerDF& m, WalkerF& wf)
+{
+    const double mt = theta[kMT * W + i], q = theta[kQ * W + i];
+    const double a1 = theta[kA1 * W + i], a2 = theta[kA2 * W + i];
+    const double tref = theta[kTref * W + i];
+    const double lam = theta[kLam * W + i], bet = theta[kBeta * W + i];
+    const double dl = theta[kDL * W + i], phi = theta[kPhi * W + i];
+    const double iota = theta[kIota * W + i], pol = theta[kPsi * W + i];
+
+    const double opq = 1.0 + q;
+    const double eta = q / (opq * opq);
+    const double x1 = 1.0 / opq, x2 = q / opq;
+    const double M = mt * kMsunSec;
+    const double so = (113.0 / 12.0 * x1 * x1 + 25.0 / 4.0 * eta) * a1 +
+                      (113.0 / 12.0 * x2 * x2 + 25.0 / 4.0 * eta) * a2;
+    const double ss = 79.0 / 8.0 * eta * a1 * a2;
+    const double pi2 = kPi * kPi;
+    double al[8];
+    al[0] = 1.0;
+    al[1] = 0.0;
+    al[2] = 3715.0 / 756.0 + 55.0 / 9.0 * eta;
+    al[3] = -16.0 * kPi + 4.0 * so;
+    al[4] = 15293365.0 / 508032.0 + 27145.0 / 504.0 * eta + 3085.0 / 72.0 * eta * eta - 10.0 * ss;
+    al[5] = kPi * (38645.0 / 756.0 - 65.0 / 9.0 * eta);
+    const double alog5 = 3.0 * al[5];
+    al[6] = 11583231236531.0 / 4694215680.0 - 640.0 / 3.0 * pi2 - 6848.0 / 21.0 * kEulerGamma -
+            6848.0 / 21.0 * 1.386294361119890618834464242916353136 +
+            eta * (-15737765635.0 / 3048192.0 + 2255.0 / 12.0 * pi2) + 76055.0 / 1728.0 * eta * eta -
+            127825.0 / 1296.0 * eta * eta * eta;
+    const double alog6 = -6848.0 / 21.0;
+    al[7] = kPi * (77096675.0 / 254016.0 + 378515.0 / 1512.0 * eta - 74045.0 / 756.0 * eta * eta);
+    const double pre = 3.0 / (128.0 * eta), dpre = kPi * M / (128.0 * eta);
+    double c[8], d[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        c[k] = pre * al[k];
+        d[k] = dpre * ((k - 5) * al[k]);
+    }
+    d[5] += dpre * alog5;
+    d[6] += dpre * alog6;
+    const double cl5 = pre * alog5, cl6 = pre * alog6, dl6 = dpre * alog6;
+    // Psi_PN and its derivative at f_max (v = constant)
+    const double vm = cbrt(kPiMfmax), lvm = log(vm);
+    double P = c[7], Q = d[7];
 #pragma unroll
     for (int k = 6; k >= 0; --k) {
-        P = fma(P, v, w.c[k]);
-        Q = fma(Q, v, w.d[k]);
+        P = fma(P, vm, c[k]);
+        Q = fma(Q, vm, d[k]);
     }
-    const double iv2 = iv * iv, iv4 = iv2 * iv2, iv5 = iv4 * iv, iv8 = iv4 * iv4;
-    const double psi_pn = fma(P, iv5, lnv * fma(w.cl6, v, w.cl5));
-    const double dpsi = fma(Q, iv8, lnv * w.dl6 * iv2);
-    const double dt = (dpsi - w.dpsi_max) * kInvTwoPi;
-    const double t = w.tref + dt;
-    if (!(f <= w.fcut) || t < 0.0 || t > t_obs) return false;
+    const double vm2 = vm * vm, vm5 = vm2 * vm2 * vm, vm6 = vm5 * vm, vm8 = vm6 * vm2;
+    const double psi_max = (P + lvm * (cl5 * vm5 + cl6 * vm6)) / vm5;
+    const double dpsi_max = (Q + lvm * dl6 * vm6) / vm8;
+    const double piM = kPi * M;
+    const double cb = cbrt(piM);
+    double sa, ca, sl, cl, sb, cbt;
+    sincos(kTwoPi * tref / kYear, &sa, &ca);
+    sincos(lam, &sl, &cl);
+    sincos(bet, &sb, &cbt);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        m.c[k] = split_f64(c[k], 0);
+        m.d[k] = split_f64(d[k], 0);
+    }
+    m.cl5 = split_f64(cl5, 0);
+    m.cl6 = split_f64(cl6, 0);
+    m.dl6 = split_f64(dl6, 0);
+    m.cbrt_piM = split_f64(cb, 0);
+    m.icbrt_piM = split_f64(1.0 / cb, 0);
+    m.ln_cbrt_piM = split_f64(log(piM) / 3.0, 0);
+    m.tref = split_f64(tref, 0);
+    m.fmax = split_f64(0.05 * 0.6454972243679028 / M, 0);   // f_c sqrt(5/12)
+    m.fcut = split_f64(0.2 / M, 0);
+    m.psi_max = split_f64(psi_max, 0);
+    m.dpsi_max = split_f64(dpsi_max, 0);
+    m.sa_ref = split_f64(sa, 0);
+    m.ca_ref = split_f64(ca, 0);
+    m.kx = split_f64(-cbt * cl, 0);
+    m.ky = split_f64(-cbt * sl, 0);
+
+    // Float32 constants (amplitude, taper, wave frame, mode factors), computed in float64 and
+    // rounded once: the heterodyne ratio h/h0 of a nearby walker cancels their common part,
+    // so their rounding error enters the likelihood directly.
+    // A = sqrt(2 pi/3) pi^{-2/3} M^{5/6} eta^{1/2} (pi M)^{7/6} / D v^{-7/2} exp(-(f/fc)^2)
+    //   = pi sqrt(2/3) M^2 sqrt(eta) / D v^{-7/2} exp(-(f/fc)^2)
+    const double dist = (double)dl * (1e9 * kParsec / kClight);
+    wf.amp = (float)(kPi * 0.816496580927726 /* sqrt(2/3) */ * M * M * sqrt(eta) / dist);
+    const double fc = 0.05 / M;
+    wf.inv_fc2 = (float)(1.0 / (fc * fc));
+    wf.sa_ref = (float)sa;
+    wf.ca_ref = (float)ca;
+    double s2p, c2p, s2f, c2f;
+    sincos(2.0 * (double)pol, &s2p, &c2p);
+    sincos(2.0 * (double)phi, &s2f, &c2f);
+    const double u[3] = {sl, -cl, 0.0};
+    const double vv[3] = {-sb * cl, -sb * sl, cbt};
+    wf.k[0] = (float)(-cbt * cl);
+    wf.k[1] = (float)(-cbt * sl);
+    wf.k[2] = (float)(-sb);
+    const int ii[6] = {0, 0, 0, 1, 1, 2}, jj[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+    for (int n = 0; n < 6; ++n) {
+        const double ep = u[ii[n]] * u[jj[n]] - vv[ii[n]] * vv[jj[n]];
+        const double ec = u[ii[n]] * vv[jj[n]] + vv[ii[n]] * u[jj[n]];
+        wf.Pp[n] = (float)(c2p * ep + s2p * ec);
+        wf.Pc[n] = (float)(-s2p * ep + c2p * ec);
+    }
+    const double ylm = 0.15769578262626002 /* sqrt(5/(64 pi)) */;
+    const double ci = cos((double)iota);
+    const double ap = ylm * (1.0 + ci * ci), ac = 2.0 * ylm * ci;
+    wf.Kp[0] = (float)(ap * c2f);
+    wf.Kp[1] = (float)(ap * s2f);
+    wf.Kc[0] = (float)(-ac * s2f);
+    wf.Kc[1] = (float)(ac * c2f);
+}
+
+// frequency tables of one grid point: f, f^{1/3}, f^{-1/3}, ln(f)/3 as float pairs
+struct FreqDF {
+    f2 f, f3, fm3, lnf3;
+};
+
+__device__ __forceinline__ FreqDF freq_tables(double f)
+{
+    const double f3 = cbrt(f);
+    return {split_d(f), split_d(f3), split_d(1.0 / f3), split_d(log(f) * (1.0 / 3.0))};
+}
+
+__device__ __forceinline__ f2 ld_f2(float2 v) { return {v.x, v.y}; }
+
+// Large phase Phi(f) (double-float) and float32 amplitude and orbit angle from the
+// frequency tables.  Returns false outside the support (f > f_cut or t(f) outside [0, t_obs]).
+__device__ __forceinline__ bool phase_df(const WalkerDF& w, const WalkerF& wf, const FreqDF& q,
+                                         f2 t_obs, f2& Phi, float& sa, float& ca, float& amp)
+{
+    const f2 v = dd_mul(w.cbrt_piM, q.f3);
+    const f2 iv = dd_mul(w.icbrt_piM, q.fm3);
+    const f2 lnv = dd_add(w.ln_cbrt_piM, q.lnf3);
+    f2 P = w.c[7], Q = w.d[7];
+#pragma unroll
+    for (int k = 6; k >= 0; --k) {
+        P = dd_fma(P, v, w.c[k]);
+        Q = dd_fma(Q, v, w.d[k]);
+    }
+    const f2 iv2 = dd_mul(iv, iv), iv4 = dd_mul(iv2, iv2);
+    const f2 iv5 = dd_mul(iv4, iv), iv8 = dd_mul(iv4, iv4);
+    const f2 psi_pn = dd_add(dd_mul(P, iv5), dd_mul(lnv, dd_fma(w.cl6, v, w.cl5)));
+    const f2 dpsi = dd_add(dd_mul(Q, iv8), dd_mul(dd_mul(lnv, w.dl6), iv2));
+    const f2 dt = dd_mul(dd_sub(dpsi, w.dpsi_max), kInvTwoPiDF);
+    const f2 t = dd_add(w.tref, dt);
+    if (!dd_le0(dd_sub(q.f, w.fcut)) || dd_lt0(t) || !dd_le0(dd_sub(t, t_obs))) return false;
     // orbit angle alpha(t) = alpha(t_ref) + da
-    const float da = (float)(dt * (kTwoPi / kYear));
+    const float da = dt.hi * (float)(kTwoPi / kYear);
     float sh, ch;
     sincosf(0.5f * da, &sh, &ch);
     const float sd = 2.0f * sh * ch, omc = 2.0f * sh * sh;   // sin da, 1 - cos da
-    const double sa_d = w.sa_ref + (double)(wf.ca_ref * sd - wf.sa_ref * omc);
-    const double ca_d = w.ca_ref - (double)(wf.ca_ref * omc + wf.sa_ref * sd);
-    const double kc = kAUSec * (w.k[0] * ca_d + w.k[1] * sa_d);
-    Phi = kTwoPi * f * (w.tref + kc) + (psi_pn - w.psi_max) - (f - w.fmax) * w.dpsi_max;
-    sa = (float)sa_d;
-    ca = (float)ca_d;
-    const float ivf = (float)iv, ff = (float)f;
+    const f2 sa_d = dd_add_f(w.sa_ref, wf.ca_ref * sd - wf.sa_ref * omc);
+    const f2 ca_d = dd_add_f(w.ca_ref, -(wf.ca_ref * omc + wf.sa_ref * sd));
+    const f2 kc = dd_mul(dd_add(dd_mul(w.kx, ca_d), dd_mul(w.ky, sa_d)), kAUSecDF);
+    const f2 lin = dd_sub(dd_mul(kTwoPiDF, dd_mul(q.f, dd_add(w.tref, kc))),
+                          dd_mul(dd_sub(q.f, w.fmax), w.dpsi_max));
+    Phi = dd_add(lin, dd_sub(psi_pn, w.psi_max));
+    sa = dd_to_float(sa_d);
+    ca = dd_to_float(ca_d);
+    const float ivf = iv.hi, ff = q.f.hi;
     amp = wf.amp * ivf * ivf * ivf * sqrtf(ivf) * expf(-ff * ff * wf.inv_fc2);
     return true;
 }
 
-// phase modulo 2 pi in float64, then float32
-__device__ __forceinline__ float reduce_phase(double p)
+// phase modulo 2 pi in double-float, then float32
+__device__ __forceinline__ float reduce_phase(f2 p)
 {
-    return (float)fma(-rint(p * kInvTwoPi), kTwoPi, p);
+    const float n = rintf(p.hi * (float)kInvTwoPi);
+    return dd_to_float(dd_sub(p, dd_mul_f(kTwoPiDF, n)));
 }
 
-// Mixed template at f: h = amp e^{-i Phi} T (float32 result).
-__device__ __forceinline__ bool point_mixed(const Walker& w, const WalkerF& wf, double f, double f3,
-                                            double fm3, double lnf3, double t_obs, float scale,
-                                            cf h[3])
+// Mixed template at one grid point: h = amp e^{-i Phi} T (float32 result, times `scale`).
+__device__ __forceinline__ bool point_mixed(const WalkerDF& w, const WalkerF& wf, const FreqDF& q,
+                                            f2 t_obs, float scale, cf h[3])
 {
-    double Phi;
+    f2 Phi;
     float sa, ca, amp;
-    if (!phase_mixed(w, wf, f, f3, fm3, lnf3, t_obs, Phi, sa, ca, amp)) return false;
+    if (!phase_df(w, wf, q, t_obs, Phi, sa, ca, amp)) return false;
     float sp, cp;
     sincosf(reduce_phase(Phi), &sp, &cp);
     cf T[3];
-    transfer_f32(wf, (float)f, sa, ca, T);
+    transfer_f32(wf, q.f.hi, sa, ca, T);
     const cf e = {amp * scale * cp, -amp * scale * sp};
 #pragma unroll
     for (int c = 0; c < 3; ++c) h[c] = fmul(e, T[c]);
     return true;
-}
-
-// frequency tables (float64): f^{1/3}, f^{-1/3}, ln(f)/3
-__device__ __forceinline__ void freq_tables(double f, double& f3, double& fm3, double& lnf3)
-{
-    f3 = cbrt(f);
-    fm3 = 1.0 / f3;
-    lnf3 = log(f) * (1.0 / 3.0);
 }
 
 }  // namespace mbh
@@ -230,25 +359,21 @@ __global__ void __launch_bounds__(kTplThreadsM)
     template_mixed_kernel(const double* __restrict__ theta, int64_t W, double f0, double df,
                           int64_t n, double t_obs, float2* __restrict__ h)
 {
-    __shared__ Walker ws;
     __shared__ WalkerF wsf;
+    __shared__ WalkerDF wsd;
+    const f2 tob = split_d(t_obs);
     for (int64_t wi = blockIdx.y; wi < W; wi += gridDim.y) {
         __syncthreads();
-        if (threadIdx.x == 0) {
-            walker_setup(theta, W, wi, ws);
-            walker_f32(ws, wsf);
-        }
+        if (threadIdx.x == 0) walker_setup_mixed(theta, W, wi, wsd, wsf);
         __syncthreads();
         const int64_t base = (int64_t)blockIdx.x * kTplThreadsM * kTplPerThreadM + threadIdx.x;
 #pragma unroll
         for (int j = 0; j < kTplPerThreadM; ++j) {
             const int64_t k = base + (int64_t)j * kTplThreadsM;
             if (k < n) {
-                const double f = f0 + (double)k * df;
-                double f3, fm3, lnf3;
-                freq_tables(f, f3, fm3, lnf3);
+                const FreqDF q = freq_tables(f0 + (double)k * df);
                 cf v[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-                point_mixed(ws, wsf, f, f3, fm3, lnf3, t_obs, 1.0f, v);
+                point_mixed(wsd, wsf, q, tob, 1.0f, v);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) h[((int64_t)wi * 3 + c) * n + k] = make_float2(v[c].re, v[c].im);
             }
@@ -276,29 +401,27 @@ constexpr int kDirThreadsM = 256;
 // units where h/sigma is O(1) (float32 range); per-point products are float32, sums float64.
 template <int T>
 __global__ void __launch_bounds__(kDirThreadsM)
-    direct_fused_mixed_kernel(const double* __restrict__ theta, int64_t W, double f0, double df,
-                              double t_obs, const float2* __restrict__ wd, const float* __restrict__ wv,
+    direct_fused_mixed_kernel(const double* __restrict__ theta, int64_t W, const float4* __restrict__ ft1,
+                              const float4* __restrict__ ft2, double t_obs,
+                              const float2* __restrict__ wd, const float* __restrict__ wv,
                               int64_t n, int64_t chunk, int nchunks, float inv_sigma,
                               double2* __restrict__ part)
 {
-    __shared__ Walker ws[T];
+    __shared__ WalkerDF wsd[T];
     __shared__ WalkerF wsf[T];
     __shared__ double sm[32 * 2 * T];
     const int64_t w0 = (int64_t)blockIdx.x * T;
     const int ch = blockIdx.y;
-    if (threadIdx.x < T && w0 + threadIdx.x < W) {
-        walker_setup(theta, W, w0 + threadIdx.x, ws[threadIdx.x]);
-        walker_f32(ws[threadIdx.x], wsf[threadIdx.x]);
-    }
+    if (threadIdx.x < T && w0 + threadIdx.x < W) walker_setup_mixed(theta, W, w0 + threadIdx.x, wsd[threadIdx.x], wsf[threadIdx.x]);
+    const f2 tob = split_d(t_obs);
     __syncthreads();
     const int64_t kb = (int64_t)ch * chunk, ke = std::min<int64_t>(n, kb + chunk);
     double acc[2 * T];
 #pragma unroll
     for (int t = 0; t < 2 * T; ++t) acc[t] = 0.0;
     for (int64_t k = kb + threadIdx.x; k < ke; k += kDirThreadsM) {
-        const double f = f0 + (double)k * df;
-        double f3, fm3, lnf3;
-        freq_tables(f, f3, fm3, lnf3);
+        const float4 a = __ldg(ft1 + k), b = __ldg(ft2 + k);
+        const FreqDF q = {{a.x, a.y}, {a.z, a.w}, {b.x, b.y}, {b.z, b.w}};
         float2 d[3];
         float v[3];
 #pragma unroll
@@ -309,7 +432,7 @@ __global__ void __launch_bounds__(kDirThreadsM)
         for (int t = 0; t < T; ++t) {
             if (w0 + t < W) {
                 cf h[3];
-                if (point_mixed(ws[t], wsf[t], f, f3, fm3, lnf3, t_obs, inv_sigma, h)) {
+                if (point_mixed(wsd[t], wsf[t], q, tob, inv_sigma, h)) {
                     float pd = 0.0f, ph = 0.0f;
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
@@ -329,6 +452,29 @@ __global__ void __launch_bounds__(kDirThreadsM)
             if (w0 + t < W) part[(w0 + t) * nchunks + ch] = make_double2(acc[2 * t], acc[2 * t + 1]);
 }
 
+__global__ void freq_table_kernel(double f0, double df, int64_t n, float4* __restrict__ t1,
+                                  float4* __restrict__ t2)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const FreqDF q = freq_tables(f0 + (double)k * df);
+        t1[k] = make_float4(q.f.hi, q.f.lo, q.f3.hi, q.f3.lo);
+        t2[k] = make_float4(q.fm3.hi, q.fm3.lo, q.lnf3.hi, q.lnf3.lo);
+    }
+}
+
+mbh_status mbh::make_freq_tables(mbh_data* D, cudaStream_t st)
+{
+    const int64_t n = D->grid.n;
+    cudaError_t e = cudaMalloc(&D->ftab, sizeof(float4) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&D->ftab2, sizeof(float4) * n);
+    if (e != cudaSuccess) return cuda_fail(e, "frequency tables");
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 148 * 32);
+    freq_table_kernel<<<blocks, 256, 0, st>>>(D->grid.f0, D->grid.df, n, D->ftab, D->ftab2);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? MBH_OK : cuda_fail(e, "frequency tables");
+}
+
 mbh_status mbh::launch_direct_fused_mixed(const mbh_data* data, const double* theta, int64_t W,
                                           double* out, cudaStream_t st)
 {
@@ -343,7 +489,7 @@ mbh_status mbh::launch_direct_fused_mixed(const mbh_data* data, const double* th
     if (e != cudaSuccess) return cuda_fail(e, "direct_loglike_batch alloc");
     dim3 grid((unsigned)tiles, (unsigned)nchunks);
     direct_fused_mixed_kernel<T><<<grid, kDirThreadsM, 0, st>>>(
-        theta, W, data->grid.f0, data->grid.df, data->grid.t_obs, data->wd32, data->wv32,
+        theta, W, data->ftab, data->ftab2, data->grid.t_obs, data->wd32, data->wv32,
         data->grid.n, chunk, nchunks, (float)(1.0 / data->sigma), part);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "direct_fused_mixed_kernel");
@@ -386,26 +532,24 @@ void mbh::free_ref_tables(mbh_ref* R)
 __global__ void edge_mixed_kernel(const double* __restrict__ theta0, double t_obs,
                                   const double* __restrict__ fe, int n_edges, MixEdge* __restrict__ out)
 {
-    __shared__ Walker w;
+    __shared__ WalkerDF wd;
     __shared__ WalkerF wf;
-    if (threadIdx.x == 0) {
-        walker_setup(theta0, 1, 0, w);
-        walker_f32(w, wf);
-    }
+    if (threadIdx.x == 0) walker_setup_mixed(theta0, 1, 0, wd, wf);
     __syncthreads();
+    const f2 tob = split_d(t_obs);
     for (int e = threadIdx.x; e < n_edges; e += blockDim.x) {
+        const FreqDF q = freq_tables(fe[e]);
         MixEdge m;
-        m.f = fe[e];
-        freq_tables(m.f, m.f3, m.fm3, m.lnf3);
-        double Phi = 0.0;
+        m.f = make_float2(q.f.hi, q.f.lo);
+        m.f3 = make_float2(q.f3.hi, q.f3.lo);
+        m.fm3 = make_float2(q.fm3.hi, q.fm3.lo);
+        m.lnf3 = make_float2(q.lnf3.hi, q.lnf3.lo);
+        f2 Phi = {0.0f, 0.0f};
         float sa, ca, amp;
-        m.phi0 = 0.0;
-        bool in = phase_mixed(w, wf, m.f, m.f3, m.fm3, m.lnf3, t_obs, Phi, sa, ca, amp);
+        const bool in = phase_df(wd, wf, q, tob, Phi, sa, ca, amp);
         cf T[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-        if (in) {
-            m.phi0 = Phi;
-            transfer_f32(wf, (float)m.f, sa, ca, T);
-        }
+        if (in) transfer_f32(wf, q.f.hi, sa, ca, T);
+        m.phi0 = in ? make_float2(Phi.hi, Phi.lo) : make_float2(0.f, 0.f);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             // 1/H0 in float64: |H0| is ~1e-20..1e-30 in strain units, so |H0|^2 underflows
@@ -469,23 +613,25 @@ __global__ void __launch_bounds__(BLOCK)
     het_mixed_kernel(const __grid_constant__ HetLaunch L)
 {
     constexpr int WPB = BLOCK / G;
-    __shared__ Walker ws[WPB];
+    __shared__ WalkerDF wsd[WPB];
     __shared__ WalkerF wsf[WPB];
     const int lw = threadIdx.x / G, lane = threadIdx.x % G;
     for (int tile = blockIdx.x; tile < L.n_tiles; tile += gridDim.x) {
         int s = 0;
         while (s + 1 < L.n_src && L.src[s + 1].tile_begin <= tile) ++s;
         const SrcDesc& S = L.src[s];
-        const int64_t wi = S.w_begin + (int64_t)(tile - S.tile_begin) * WPB + lw;
+        const int64_t w0 = S.w_begin + (int64_t)(tile - S.tile_begin) * WPB;
+        const int64_t wi = w0 + lw;
         const bool active = wi < S.w_end;
         __syncthreads();
-        if (lane == 0 && active) {
-            walker_setup(L.theta, L.W, wi, ws[lw]);
-            walker_f32(ws[lw], wsf[lw]);
-        }
+        // setup with consecutive threads (full warps): a float64 warp instruction costs the
+        // same whether 4 or 32 of its lanes are active
+        for (int j = threadIdx.x; j < WPB; j += BLOCK)
+            if (w0 + j < S.w_end) walker_setup_mixed(L.theta, L.W, w0 + j, wsd[j], wsf[j]);
         __syncthreads();
         const int E = S.E;
-        double adh = 0.0, ahh = 0.0;
+        const f2 tob = split_d(S.t_obs);
+        f2 adh = {0.0f, 0.0f}, ahh = {0.0f, 0.0f};
         cf carry[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
         const int rounds = (E + 1 + G - 1) / G;
         for (int r = 0; r < rounds; ++r) {
@@ -493,14 +639,15 @@ __global__ void __launch_bounds__(BLOCK)
             cf dl[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
             if (active && e <= E) {
                 const MixEdge me = S.mix.edge[e];
-                double Phi;
+                const FreqDF q = {ld_f2(me.f), ld_f2(me.f3), ld_f2(me.fm3), ld_f2(me.lnf3)};
+                f2 Phi;
                 float sa, ca, amp;
-                if (phase_mixed(ws[lw], wsf[lw], me.f, me.f3, me.fm3, me.lnf3, S.t_obs, Phi, sa, ca, amp)) {
+                if (phase_df(wsd[lw], wsf[lw], q, tob, Phi, sa, ca, amp)) {
                     float sh, ch;
-                    sincosf(0.5f * reduce_phase(Phi - me.phi0), &sh, &ch);
+                    sincosf(0.5f * reduce_phase(dd_sub(Phi, ld_f2(me.phi0))), &sh, &ch);
                     const cf em1 = {-2.0f * sh * sh, -2.0f * sh * ch};   // e^{-i dPhi} - 1
                     cf T[3];
-                    transfer_f32(wsf[lw], (float)me.f, sa, ca, T);
+                    transfer_f32(wsf[lw], q.f.hi, sa, ca, T);
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         const cf rho = fmul(fscale(T[c], amp), {me.h0inv[c].x, me.h0inv[c].y});
@@ -534,18 +681,20 @@ __global__ void __launch_bounds__(BLOCK)
                     bh += q[4] * (2.0f * d0r + d0r * d0r + d0i * d0i) +
                           2.0f * q[5] * (d1r + d0r * d1r + d0i * d1i);
                 }
-                adh += (double)bd;
-                ahh += (double)bh;
+                df_acc(adh, {bd, 0.0f});
+                df_acc(ahh, {bh, 0.0f});
             }
         }
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) {
-            adh += __shfl_down_sync(0xffffffffu, adh, o, G);
-            ahh += __shfl_down_sync(0xffffffffu, ahh, o, G);
+            const f2 odh = {__shfl_down_sync(0xffffffffu, adh.hi, o, G), __shfl_down_sync(0xffffffffu, adh.lo, o, G)};
+            const f2 ohh = {__shfl_down_sync(0xffffffffu, ahh.hi, o, G), __shfl_down_sync(0xffffffffu, ahh.lo, o, G)};
+            df_acc(adh, odh);
+            df_acc(ahh, ohh);
         }
         if (active && lane == 0) {
-            const double dh = 4.0 * (S.mix.sumA0 + adh);
-            const double hh = 4.0 * (S.mix.sumB0 + ahh);
+            const double dh = 4.0 * (S.mix.sumA0 + df_to_double(adh));
+            const double hh = 4.0 * (S.mix.sumB0 + df_to_double(ahh));
             L.out[wi] = -0.5 * (S.dd + hh - 2.0 * dh);
             L.out[L.W + wi] = dh;
             L.out[2 * L.W + wi] = hh;
@@ -560,13 +709,13 @@ cudaError_t launch_het_mixed(const HetLaunch& L, int grid, cudaStream_t st)
     het_mixed_kernel<G, BLOCK><<<grid, BLOCK, 0, st>>>(L);
     return cudaGetLastError();
 }
+}  // namespace
 
-using HetFn = cudaError_t (*)(const HetLaunch&, int, cudaStream_t);
-
-HetFn pick(int G, int block)
+namespace mbh {
+HetKernel het_kernel_mixed(int G, int block)
 {
 #define MBH_CASE(g, b) \
-    if (G == g && block == b) return &launch_het_mixed<g, b>;
+    if (G == g && block == b) return {&launch_het_mixed<g, b>, (const void*)&het_mixed_kernel<g, b>};
     MBH_CASE(1, 64) MBH_CASE(1, 128) MBH_CASE(1, 256)
     MBH_CASE(2, 64) MBH_CASE(2, 128) MBH_CASE(2, 256)
     MBH_CASE(4, 64) MBH_CASE(4, 128) MBH_CASE(4, 256)
@@ -574,27 +723,6 @@ HetFn pick(int G, int block)
     MBH_CASE(16, 64) MBH_CASE(16, 128) MBH_CASE(16, 256)
     MBH_CASE(32, 64) MBH_CASE(32, 128) MBH_CASE(32, 256)
 #undef MBH_CASE
-    return nullptr;
+    return {nullptr, nullptr};
 }
-}  // namespace
-
-mbh_status mbh::run_het_mixed(const mbh_ref* const* refs, const int64_t* offsets, int32_t n_src,
-                              const double* theta, int64_t W, double* out, cudaStream_t st,
-                              const HetTuning* tuning)
-{
-    HetTuning t = tuning ? *tuning : HetTuning{8, 128, 0};
-    HetFn fn = pick(t.threads_per_walker, t.block);
-    if (!fn) return fail(MBH_EINVAL, "unsupported tuning G=%d block=%d", t.threads_per_walker, t.block);
-    const int wpb = t.block / t.threads_per_walker;
-    static HetLaunch L;
-    std::lock_guard<std::mutex> lk(launch_mutex());
-    for (int32_t first = 0; first < n_src; first += kMaxSrc) {
-        const int32_t count = std::min<int32_t>(kMaxSrc, n_src - first);
-        if (mbh_status s = build_launch(refs, offsets, n_src, first, count, wpb, theta, W, out, L)) return s;
-        if (L.n_tiles == 0) continue;
-        const int grid = t.persistent_blocks > 0 ? std::min(L.n_tiles, t.persistent_blocks) : L.n_tiles;
-        cudaError_t e = fn(L, grid, st);
-        if (e != cudaSuccess) return cuda_fail(e, "het_mixed_kernel");
-    }
-    return MBH_OK;
-}
+}  // namespace mbh

@@ -1,0 +1,286 @@
+// Heterodyne launch planning (Katz, arXiv:2111.01064, Sec. II B; the batched evaluations of
+// Sec. III B-C): walkers of many sources, each with its own bin count, in one launch.
+//
+//  - A plan packs up to kMaxSrc source descriptors per launch as __grid_constant__ kernel
+//    parameters (no host-to-device copy, so a plan can be captured in a CUDA graph).
+//  - Tiles of BLOCK/G walkers of one source; G threads per walker deal the edges round-robin
+//    (a round covers G bins of a walker).
+//  - Persistent mode: grid = SMs x resident blocks, each block loops over tiles; sources are
+//    ordered by bin count (largest first) so that the round-robin tile assignment mixes costs.
+//    A walker's result does not depend on the order or on the tile that computes it (for a
+//    given G, which fixes the order in which its bins are summed).
+//  - mbh_het_autotune times the candidate configurations with CUDA events; mbh_het_graph_*
+//    capture a plan once and replay it.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <cmath>
+#include <memory>
+#include <numeric>
+#include <vector>
+
+#include "mbh_internal.cuh"
+
+using namespace mbh;
+
+namespace {
+
+struct HetPlan {
+    std::vector<HetLaunch> launches;   // heap-allocated: each ~13 KB
+    std::vector<int> grids;
+    HetKernel kernel{nullptr, nullptr};
+};
+
+mbh_status check_cfg(const mbh_het_config& c)
+{
+    const int g = c.threads_per_walker;
+    if (!(g == 1 || g == 2 || g == 4 || g == 8 || g == 16 || g == 32))
+        return fail(MBH_EINVAL, "threads_per_walker %d not in {1,2,4,8,16,32}", g);
+    if (!(c.block == 64 || c.block == 128 || c.block == 256))
+        return fail(MBH_EINVAL, "block %d not in {64,128,256}", c.block);
+    return MBH_OK;
+}
+
+mbh_status check_het_args(const mbh_ref* const* refs, const int64_t* offsets, int32_t n_src,
+                          const double* theta, double* out)
+{
+    if (n_src < 0) return fail(MBH_EINVAL, "n_sources < 0");
+    if (n_src == 0) return MBH_OK;
+    if (!refs || !offsets) return fail(MBH_EINVAL, "NULL refs/offsets");
+    if (offsets[0] != 0) return fail(MBH_EINVAL, "offsets[0] must be 0");
+    int dev = -1;
+    cudaGetDevice(&dev);
+    for (int32_t s = 0; s < n_src; ++s) {
+        if (!refs[s]) return fail(MBH_EINVAL, "refs[%d] is NULL", s);
+        if (offsets[s + 1] < offsets[s]) return fail(MBH_EINVAL, "offsets must be non-decreasing");
+        if (refs[s]->device != dev) return fail(MBH_EINVAL, "refs[%d] lives on another device", s);
+    }
+    if (offsets[n_src] > 0 && (!theta || !out)) return fail(MBH_EINVAL, "NULL theta/out");
+    return MBH_OK;
+}
+
+mbh_status make_plan(const mbh_ref* const* refs, const int64_t* offsets, int32_t n_src,
+                     const double* theta, double* out, mbh_precision prec,
+                     const mbh_het_config& cfg, HetPlan& plan)
+{
+    if (mbh_status s = check_cfg(cfg)) return s;
+    if (prec != MBH_FP64 && prec != MBH_MIXED) return fail(MBH_EINVAL, "unknown precision %d", (int)prec);
+    plan.kernel = prec == MBH_FP64 ? het_kernel_f64(cfg.threads_per_walker, cfg.block)
+                                   : het_kernel_mixed(cfg.threads_per_walker, cfg.block);
+    if (!plan.kernel.launch) return fail(MBH_EINVAL, "no kernel for this configuration");
+    const int wpb = cfg.block / cfg.threads_per_walker;
+    const int64_t W = offsets[n_src];
+    std::vector<int32_t> order(n_src);
+    std::iota(order.begin(), order.end(), 0);
+    if (cfg.persistent)   // largest bin counts first
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int32_t a, int32_t b) { return refs[a]->E > refs[b]->E; });
+    int resident = 0;
+    if (cfg.persistent) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        int per_sm = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan.kernel.fn, cfg.block, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+        resident = std::max(1, per_sm) * sms;
+    }
+    for (int32_t first = 0; first < n_src; first += kMaxSrc) {
+        const int32_t count = std::min<int32_t>(kMaxSrc, n_src - first);
+        plan.launches.emplace_back();
+        HetLaunch& L = plan.launches.back();
+        std::memset(&L, 0, sizeof L);
+        L.theta = theta;
+        L.W = W;
+        L.out = out;
+        int64_t tiles = 0;
+        int32_t j = 0;
+        for (int32_t q = 0; q < count; ++q) {
+            const int32_t s = order[first + q];
+            const int64_t nw = offsets[s + 1] - offsets[s];
+            if (nw == 0) continue;
+            const mbh_ref* R = refs[s];
+            SrcDesc& S = L.src[j++];
+            S.summary = R->summary;
+            S.h0inv = R->h0inv;
+            S.fe = R->fe;
+            S.invw = R->invw;
+            S.mix = R->mix;
+            S.dd = R->dd;
+            S.t_obs = R->grid.t_obs;
+            S.E = R->E;
+            S.w_begin = offsets[s];
+            S.w_end = offsets[s + 1];
+            S.tile_begin = (int32_t)tiles;
+            tiles += (nw + wpb - 1) / wpb;
+            if (tiles > 0x7fffffff) return fail(MBH_EINVAL, "too many walker tiles");
+        }
+        L.n_src = j;
+        L.n_tiles = (int32_t)tiles;
+        if (tiles == 0) {
+            plan.launches.pop_back();
+            continue;
+        }
+        plan.grids.push_back(cfg.persistent ? (int)std::min<int64_t>(tiles, resident) : (int)tiles);
+    }
+    return MBH_OK;
+}
+
+mbh_status run_plan(const HetPlan& plan, cudaStream_t st)
+{
+    for (size_t i = 0; i < plan.launches.size(); ++i) {
+        cudaError_t e = plan.kernel.launch(plan.launches[i], plan.grids[i], st);
+        if (e != cudaSuccess) return cuda_fail(e, "heterodyne kernel");
+    }
+    return MBH_OK;
+}
+
+mbh_het_config default_cfg(mbh_precision p)
+{
+    (void)p;
+    return mbh_het_config{8, 128, 0};
+}
+
+}  // namespace
+
+struct mbh_het_graph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int device = -1;
+};
+
+extern "C" mbh_status het_loglike_batch_cfg(const mbh_ref* const* refs, const int64_t* offsets_host,
+                                            int32_t n_sources, const double* theta_dev,
+                                            mbh_precision precision, const mbh_het_config* cfg,
+                                            double* out_dev, void* stream)
+{
+    if (mbh_status s = check_het_args(refs, offsets_host, n_sources, theta_dev, out_dev)) return s;
+    if (n_sources == 0 || offsets_host[n_sources] == 0) return MBH_OK;
+    const mbh_het_config c = cfg ? *cfg : default_cfg(precision);
+    HetPlan plan;
+    if (mbh_status s = make_plan(refs, offsets_host, n_sources, theta_dev, out_dev, precision, c, plan)) return s;
+    return run_plan(plan, (cudaStream_t)stream);
+}
+
+extern "C" mbh_status het_loglike_batch(const mbh_ref* const* refs, const int64_t* offsets_host,
+                                        int32_t n_sources, const double* theta_dev,
+                                        mbh_precision precision, double* out_dev, void* stream)
+{
+    return het_loglike_batch_cfg(refs, offsets_host, n_sources, theta_dev, precision, nullptr, out_dev,
+                                 stream);
+}
+
+extern "C" mbh_status mbh_het_autotune(const mbh_ref* const* refs, const int64_t* offsets_host,
+                                       int32_t n_sources, const double* theta_dev,
+                                       mbh_precision precision, double* out_dev, int32_t reps,
+                                       void* stream, mbh_het_config* best, double* best_ms)
+{
+    if (!best) return fail(MBH_EINVAL, "best is NULL");
+    if (mbh_status s = check_het_args(refs, offsets_host, n_sources, theta_dev, out_dev)) return s;
+    if (n_sources == 0 || offsets_host[n_sources] == 0) {
+        *best = default_cfg(precision);
+        if (best_ms) *best_ms = 0.0;
+        return MBH_OK;
+    }
+    reps = std::max(1, reps);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) return cuda_fail(e, "autotune events");
+    double best_t = INFINITY;
+    mbh_het_config best_c = default_cfg(precision);
+    const int gs[] = {1, 2, 4, 8, 16, 32};
+    const int bs[] = {64, 128, 256};
+    mbh_status status = MBH_OK;
+    for (int g : gs)
+        for (int b : bs)
+            for (int pers = 0; pers < 2 && status == MBH_OK; ++pers) {
+                if (b < g) continue;
+                const mbh_het_config c{g, b, pers};
+                HetPlan plan;
+                status = make_plan(refs, offsets_host, n_sources, theta_dev, out_dev, precision, c, plan);
+                if (status != MBH_OK) break;
+                status = run_plan(plan, st);   // warm-up
+                if (status != MBH_OK) break;
+                cudaEventRecord(e0, st);
+                for (int r = 0; r < reps && status == MBH_OK; ++r) status = run_plan(plan, st);
+                cudaEventRecord(e1, st);
+                e = cudaEventSynchronize(e1);
+                if (e != cudaSuccess) {
+                    status = cuda_fail(e, "autotune");
+                    break;
+                }
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                const double t = ms / reps;
+                if (t < best_t) {
+                    best_t = t;
+                    best_c = c;
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (status != MBH_OK) return status;
+    *best = best_c;
+    if (best_ms) *best_ms = best_t;
+    return MBH_OK;
+}
+
+extern "C" mbh_status mbh_het_graph_create(const mbh_ref* const* refs, const int64_t* offsets_host,
+                                           int32_t n_sources, const double* theta_dev,
+                                           mbh_precision precision, const mbh_het_config* cfg,
+                                           double* out_dev, void* stream, mbh_het_graph** out)
+{
+    if (!out) return fail(MBH_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (mbh_status s = check_het_args(refs, offsets_host, n_sources, theta_dev, out_dev)) return s;
+    const mbh_het_config c = cfg ? *cfg : default_cfg(precision);
+    HetPlan plan;
+    if (n_sources > 0)
+        if (mbh_status s = make_plan(refs, offsets_host, n_sources, theta_dev, out_dev, precision, c, plan)) return s;
+    // capture on a private stream so that the caller's stream is never in capture mode
+    cudaStream_t cs;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "graph stream");
+    auto G = std::make_unique<mbh_het_graph>();
+    cudaGetDevice(&G->device);
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    mbh_status status = MBH_OK;
+    if (e == cudaSuccess) {
+        status = run_plan(plan, cs);
+        cudaError_t e2 = cudaStreamEndCapture(cs, &G->graph);
+        if (status == MBH_OK && e2 != cudaSuccess) status = cuda_fail(e2, "end capture");
+    } else {
+        status = cuda_fail(e, "begin capture");
+    }
+    if (status == MBH_OK) {
+        e = cudaGraphInstantiate(&G->exec, G->graph, 0);
+        if (e != cudaSuccess) status = cuda_fail(e, "graph instantiate");
+    }
+    cudaStreamDestroy(cs);
+    if (status != MBH_OK) {
+        if (G->exec) cudaGraphExecDestroy(G->exec);
+        if (G->graph) cudaGraphDestroy(G->graph);
+        return status;
+    }
+    (void)stream;
+    *out = G.release();
+    return MBH_OK;
+}
+
+extern "C" mbh_status mbh_het_graph_launch(mbh_het_graph* g, void* stream)
+{
+    if (!g || !g->exec) return fail(MBH_EINVAL, "graph is NULL");
+    cudaError_t e = cudaGraphLaunch(g->exec, (cudaStream_t)stream);
+    return e == cudaSuccess ? MBH_OK : cuda_fail(e, "graph launch");
+}
+
+extern "C" void mbh_het_graph_free(mbh_het_graph* g)
+{
+    if (!g) return;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+}

@@ -23,13 +23,40 @@ using namespace mbh;
 
 constexpr int kStreamThreads = 256;
 
+// Block-wide double-float sum of N values (shuffles of hi/lo with the two-sum); the result,
+// converted to float64, is valid in thread 0.  No float64 arithmetic per thread.
+template <int N>
+__device__ void block_sum_df(f2 (&v)[N], double (&out)[N])
+{
+    __shared__ float2 sm[N][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            df_acc(v[j], {__shfl_down_sync(0xffffffffu, v[j].hi, o), __shfl_down_sync(0xffffffffu, v[j].lo, o)});
+    if (lane == 0)
+#pragma unroll
+        for (int j = 0; j < N; ++j) sm[j][warp] = make_float2(v[j].hi, v[j].lo);
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            f2 x = lane < nw ? f2{sm[j][lane].x, sm[j][lane].y} : f2{0.0f, 0.0f};
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                df_acc(x, {__shfl_down_sync(0xffffffffu, x.hi, o), __shfl_down_sync(0xffffffffu, x.lo, o)});
+            out[j] = df_to_double(x);
+        }
+    }
+}
+
 template <int T>
 __global__ void __launch_bounds__(kStreamThreads)
     direct_stored_df_kernel(const float4* __restrict__ wsp, const float2* __restrict__ vsp,
                             const double2* __restrict__ h, int64_t n, int64_t W, int64_t chunk,
                             int nchunks, int shift, double2* __restrict__ part)
 {
-    __shared__ double sm[32 * 2 * T];
     const int64_t w0 = (int64_t)blockIdx.x * T;
     const int ch = blockIdx.y;
     const int64_t kb = (int64_t)ch * chunk, ke = std::min<int64_t>(n, kb + chunk);
@@ -56,13 +83,14 @@ __global__ void __launch_bounds__(kStreamThreads)
             }
         }
     }
-    double acc[2 * T];
+    f2 v[2 * T];
 #pragma unroll
     for (int t = 0; t < T; ++t) {
-        acc[2 * t] = df_to_double(adh[t]);
-        acc[2 * t + 1] = df_to_double(ahh[t]);
+        v[2 * t] = adh[t];
+        v[2 * t + 1] = ahh[t];
     }
-    block_sum<2 * T>(acc, sm);
+    double acc[2 * T];
+    block_sum_df<2 * T>(v, acc);
     if (threadIdx.x == 0)
 #pragma unroll
         for (int t = 0; t < T; ++t)
@@ -139,7 +167,15 @@ mbh_status stored_plan(const mbh_data* data, int64_t W, int64_t& chunk, int& nch
     constexpr int T = 4;
     const int64_t tiles = (W + T - 1) / T;
     if (tiles > 0x7fffffff) return fail(MBH_EINVAL, "W too large");
-    direct_chunks(data->grid.n, tiles, 1 << 16, chunk, nchunks);
+    // about two waves of (tile, chunk) blocks, each thread reducing >= 16 points per channel
+    const int64_t min_chunk = 16 * kStreamThreads;
+    int64_t nc = std::max<int64_t>(1, (148 * 16) / std::max<int64_t>(1, tiles));
+    nc = std::min<int64_t>(nc, std::max<int64_t>(1, data->grid.n / min_chunk));
+    nc = std::max<int64_t>(nc, (data->grid.n + (1 << 18) - 1) / (1 << 18));
+    nc = std::min<int64_t>(nc, 65535);
+    chunk = (data->grid.n + nc - 1) / nc;
+    chunk = (chunk + 31) / 32 * 32;
+    nchunks = (int)((data->grid.n + chunk - 1) / chunk);
     return MBH_OK;
 }
 }  // namespace mbh

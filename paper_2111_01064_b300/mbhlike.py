@@ -32,6 +32,35 @@ class Grid(C.Structure):
     _fields_ = [("f0", C.c_double), ("df", C.c_double), ("n", C.c_int64), ("t_obs", C.c_double)]
 
 
+class HetConfig(C.Structure):
+    """mbh_het_config: threads per walker (1..32), block (64/128/256), persistent (0/1)."""
+    _fields_ = [("threads_per_walker", C.c_int32), ("block", C.c_int32), ("persistent", C.c_int32)]
+
+    def as_dict(self) -> dict:
+        return dict(threads_per_walker=self.threads_per_walker, block=self.block,
+                    persistent=self.persistent)
+
+
+def het_config(threads_per_walker=8, block=128, persistent=0) -> HetConfig:
+    return HetConfig(int(threads_per_walker), int(block), int(persistent))
+
+
+class ServerOpts(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_int64), ("max_batch_walkers", C.c_int32),
+                ("max_inflight_batches", C.c_int32), ("max_queue", C.c_int32),
+                ("precision", C.c_int), ("config", HetConfig)]
+
+
+class ServerReport(C.Structure):
+    _fields_ = [("completed", C.c_int64), ("walkers", C.c_int64), ("batches", C.c_int64),
+                ("rejected", C.c_int64), ("queued", C.c_int64), ("mean_batch_walkers", C.c_double),
+                ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("max_ms", C.c_double),
+                ("walkers_per_s", C.c_double), ("source_bytes", C.c_int64), ("slot_bytes", C.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 def grid_struct(g: dict) -> Grid:
     return Grid(float(g["f0"]), float(g["df"]), int(g["n"]), float(g["t_obs"]))
 
@@ -66,6 +95,24 @@ def lib() -> C.CDLL:
         "mbh_ref_free": (None, [vp]),
         "het_loglike_batch": (C.c_int, [C.POINTER(vp), C.POINTER(C.c_int64), i32, vp, C.c_int, vp,
                                         vp]),
+        "het_loglike_batch_cfg": (C.c_int, [C.POINTER(vp), C.POINTER(C.c_int64), i32, vp, C.c_int,
+                                            C.POINTER(HetConfig), vp, vp]),
+        "mbh_het_autotune": (C.c_int, [C.POINTER(vp), C.POINTER(C.c_int64), i32, vp, C.c_int, vp, i32,
+                                       vp, C.POINTER(HetConfig), C.POINTER(C.c_double)]),
+        "mbh_het_graph_create": (C.c_int, [C.POINTER(vp), C.POINTER(C.c_int64), i32, vp, C.c_int,
+                                           C.POINTER(HetConfig), vp, vp, C.POINTER(vp)]),
+        "mbh_het_graph_launch": (C.c_int, [vp, vp]),
+        "mbh_het_graph_free": (None, [vp]),
+        "mbh_server_create": (C.c_int, [C.POINTER(ServerOpts), C.POINTER(vp)]),
+        "mbh_server_add_source": (C.c_int, [vp, vp, C.POINTER(C.c_int32)]),
+        "mbh_server_remove_source": (C.c_int, [vp, i32]),
+        "mbh_server_submit": (C.c_int, [vp, i32, vp, i64, vp, C.POINTER(C.c_uint64)]),
+        "mbh_server_wait": (C.c_int, [vp, C.c_uint64, i32, C.POINTER(C.c_int)]),
+        "mbh_server_cancel": (C.c_int, [vp, C.c_uint64]),
+        "mbh_server_pause": (C.c_int, [vp, i32]),
+        "mbh_server_stats": (C.c_int, [vp, C.POINTER(ServerReport)]),
+        "mbh_server_reset_stats": (C.c_int, [vp]),
+        "mbh_server_free": (None, [vp]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(L, name)
@@ -279,3 +326,139 @@ def het_loglike_batch(refs: Sequence[Ref], offsets, theta: torch.Tensor, precisi
                                    _dev(theta, torch.float64, (11, W), "theta"), _prec(precision),
                                    _dev(out, torch.float64, (3, W), "out"), _stream(stream)))
     return out
+
+
+def _het_args(refs, offsets, theta):
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    ns = len(refs)
+    if off.shape != (ns + 1,):
+        raise MBHError(1, f"offsets must have {ns + 1} entries")
+    W = int(off[-1])
+    arr = (vp * max(ns, 1))(*[r.handle for r in refs])
+    return off, ns, W, arr
+
+
+def het_loglike_batch_cfg(refs: Sequence[Ref], offsets, theta: torch.Tensor, precision="mixed",
+                          cfg: HetConfig | None = None, out: torch.Tensor | None = None,
+                          stream=None) -> torch.Tensor:
+    off, ns, W, arr = _het_args(refs, offsets, theta)
+    if out is None:
+        out = torch.empty((3, W), dtype=torch.float64, device="cuda")
+    _check(lib().het_loglike_batch_cfg(arr, off.ctypes.data_as(C.POINTER(C.c_int64)), ns,
+                                       _dev(theta, torch.float64, (11, W), "theta"), _prec(precision),
+                                       C.byref(cfg) if cfg is not None else None,
+                                       _dev(out, torch.float64, (3, W), "out"), _stream(stream)))
+    return out
+
+
+def mbh_het_autotune(refs: Sequence[Ref], offsets, theta: torch.Tensor, precision="mixed",
+                     reps: int = 3, out: torch.Tensor | None = None, stream=None):
+    """Fastest launch configuration for this batch: (HetConfig, ms per batch)."""
+    off, ns, W, arr = _het_args(refs, offsets, theta)
+    if out is None:
+        out = torch.empty((3, W), dtype=torch.float64, device="cuda")
+    best = HetConfig()
+    ms = C.c_double()
+    _check(lib().mbh_het_autotune(arr, off.ctypes.data_as(C.POINTER(C.c_int64)), ns,
+                                  _dev(theta, torch.float64, (11, W), "theta"), _prec(precision),
+                                  _dev(out, torch.float64, (3, W), "out"), int(reps), _stream(stream),
+                                  C.byref(best), C.byref(ms)))
+    return best, ms.value
+
+
+class HetGraph:
+    """A heterodyne batch captured in a CUDA graph: theta and out are fixed buffers; rewrite
+    theta in place and call launch() for each evaluation."""
+
+    def __init__(self, refs: Sequence[Ref], offsets, theta: torch.Tensor, out: torch.Tensor,
+                 precision="mixed", cfg: HetConfig | None = None, stream=None):
+        off, ns, W, arr = _het_args(refs, offsets, theta)
+        self.refs, self.theta, self.out = list(refs), theta, out   # keep them alive
+        h = vp()
+        _check(lib().mbh_het_graph_create(arr, off.ctypes.data_as(C.POINTER(C.c_int64)), ns,
+                                          _dev(theta, torch.float64, (11, W), "theta"), _prec(precision),
+                                          C.byref(cfg) if cfg is not None else None,
+                                          _dev(out, torch.float64, (3, W), "out"), _stream(stream),
+                                          C.byref(h)))
+        self.handle = h
+
+    def launch(self, stream=None):
+        _check(lib().mbh_het_graph_launch(self.handle, _stream(stream)))
+        return self.out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().mbh_het_graph_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """mbh_server: continuous batching of heterodyne requests (see include/mbhlike.h)."""
+
+    def __init__(self, hbm_budget_bytes: int, max_batch_walkers: int = 16384, max_inflight_batches: int = 3,
+                 max_queue: int = 4096, precision="mixed", cfg: HetConfig | None = None):
+        _require_cuda()
+        opts = ServerOpts(int(hbm_budget_bytes), int(max_batch_walkers), int(max_inflight_batches),
+                          int(max_queue), _prec(precision), cfg if cfg is not None else HetConfig(0, 0, 0))
+        h = vp()
+        _check(lib().mbh_server_create(C.byref(opts), C.byref(h)))
+        self.handle = h
+        self.refs = {}
+        self._out = {}
+
+    def add_source(self, ref: Ref) -> int:
+        sid = C.c_int32()
+        _check(lib().mbh_server_add_source(self.handle, ref.handle, C.byref(sid)))
+        self.refs[sid.value] = ref
+        return sid.value
+
+    def remove_source(self, sid: int):
+        _check(lib().mbh_server_remove_source(self.handle, int(sid)))
+        self.refs.pop(sid, None)
+
+    def submit(self, sid: int, theta: np.ndarray) -> int:
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        W = th.shape[1]
+        out = np.empty((3, W))
+        rid = C.c_uint64()
+        _check(lib().mbh_server_submit(self.handle, int(sid), th.ctypes.data, W, out.ctypes.data,
+                                       C.byref(rid)))
+        self._out[rid.value] = out
+        return rid.value
+
+    def wait(self, rid: int, timeout_ms: int = -1) -> tuple[int, np.ndarray]:
+        """(request status, results (3, W)); raises MBHError(MBH_ETIMEOUT) on timeout."""
+        st = C.c_int()
+        _check(lib().mbh_server_wait(self.handle, C.c_uint64(rid), int(timeout_ms), C.byref(st)))
+        return st.value, self._out.pop(rid)
+
+    def cancel(self, rid: int):
+        _check(lib().mbh_server_cancel(self.handle, C.c_uint64(rid)))
+
+    def pause(self, paused: bool = True):
+        _check(lib().mbh_server_pause(self.handle, 1 if paused else 0))
+
+    def stats(self) -> dict:
+        r = ServerReport()
+        _check(lib().mbh_server_stats(self.handle, C.byref(r)))
+        return r.as_dict()
+
+    def reset_stats(self):
+        _check(lib().mbh_server_reset_stats(self.handle))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().mbh_server_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -81,3 +81,34 @@ def walkers(theta0: np.ndarray, W: int, workload: int, source: int = 0, lo: floa
 
 def to_dev(theta: np.ndarray) -> torch.Tensor:
     return torch.from_numpy(np.ascontiguousarray(theta, dtype=np.float64)).cuda()
+
+
+@dataclasses.dataclass
+class UnevenBatch:
+    sources: list
+    refs: list
+    bins: np.ndarray
+    walkers: np.ndarray
+    offsets: np.ndarray
+    theta: np.ndarray          # (11, W) walkers of all sources, grouped by source
+
+
+def uneven_batch(n_sources: int = 64, grid: dict | None = None, workload: int = 3,
+                 lo: float = 1e-5, hi: float = 1e-3, walkers=(128, 4096)) -> UnevenBatch:
+    """Sources with distinct seeds (injection, noise) on the 30-day grid, bins U{64..512},
+    walkers log-uniform 128-4096 per source, perturbed lo..hi around each injection."""
+    g = grid or I.grid_month()
+    nb, nw = I.draw_uneven_batch(I.rng(workload, 999), n_sources, walkers=walkers)
+    sources, refs, thetas = [], [], []
+    for s in range(n_sources):
+        src = source_for(workload, g, source=s)
+        sources.append(src)
+        refs.append(M.het_prepare_reference(src.data, src.theta_inj, int(nb[s])))
+        thetas.append(walkers_for(src.theta_inj, int(nw[s]), workload, s, lo, hi))
+    offsets = np.concatenate([[0], np.cumsum(nw)]).astype(np.int64)
+    return UnevenBatch(sources=sources, refs=refs, bins=nb, walkers=nw, offsets=offsets,
+                       theta=np.ascontiguousarray(np.concatenate(thetas, axis=1)))
+
+
+def walkers_for(theta0, W, workload, source, lo, hi):
+    return walkers(theta0, W, workload, source, lo, hi)
