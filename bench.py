@@ -70,15 +70,35 @@ def _measured_peaks():
 # FP64 peak of B300: 148 SMs x 2 DFMA per SM per clock (measured 566 G DFMA/s at 1935 MHz,
 # i.e. 1.98 per SM per clock) x 2 flop x max SM clock.
 def fp64_peak_gflops(sm_mhz: float) -> float:
-    return 148 * 2 * 2 * sm_mhz * 1e-3
+    return 148 * 2 * 2 * sm_mhz * 1e-3  # noqa: E501  (reported for the float64 kernel)
 
 
-# FP64 operations per edge evaluation of the mixed heterodyne kernel (phase chain of
-# phase_mixed + the 2 pi reduction of dPhi), counted from the source: v, 1/v, ln v (3),
-# two degree-7 Horner chains (14), powers of 1/v (4), Psi_PN and its derivative (6), t(f)
-# and the support tests (5), orbit-angle offset and the two float64 corrections (4), k.c
-# (3), Phi (7), the reduction (3): 49 instructions, of which 26 FMA -> 75 flop.
-HET_MIXED_FP64_FLOP_PER_EDGE = 75
+# The mixed heterodyne kernel is bound by the float32 (FMA) pipe: per edge evaluation it
+# issues 1399 FMA-pipe thread instructions (double-float phase chain, float32 response,
+# ratio and contraction), counted by ncu on het_mixed_kernel<8,128> (FMA-pipe utilisation x
+# peak x elapsed cycles / edges).  Peak: 148 SMs x 128 FP32 lanes x SM clock.
+HET_MIXED_FMA_INST_PER_EDGE = 1399
+
+
+def fma_peak_tinst(sm_mhz: float) -> float:
+    return 148 * 128 * sm_mhz * 1e-6
+
+
+def max_over_ranks(value: float, device=None) -> float:
+    """Largest value over the ranks of the default process group (value itself when
+    torch.distributed is not initialised)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_rate(world_size: int, units_per_rank: int, steps: int, max_total_ms: float) -> float:
+    """Whole-job throughput: units processed by all ranks over the slowest rank's time."""
+    return world_size * units_per_rank * steps / (max_total_ms * 1e-3)
 
 
 class ClockSampler:
@@ -183,6 +203,8 @@ def run_ours(args) -> dict | None:
     offs = [0, nw]
     if args.only == "direct":
         return run_direct_only(args, M, WL, g, src, rank, dev, stream, peaks, peak_src)
+    if args.only == "fused":
+        return run_fused_only(args, M, WL, g, src, rank, dev, stream)
 
     def het_step(prec="mixed"):
         M.het_loglike_batch([ref], offs, theta, prec, out=out)
@@ -210,13 +232,9 @@ def run_ours(args) -> dict | None:
     t_wall = time.perf_counter() - t_wall
     clk.mark(t_start, time.time())
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if ws > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), dev)
     ms_per_step = total_ms / args.steps
-    value = ws * nw * args.steps / (total_ms * 1e-3)
+    value = weak_scaling_rate(ws, nw, args.steps, total_ms)
     mixed_out = out.cpu().numpy().copy()
     if args.only == "het":
         clk.__exit__(None, None, None)
@@ -259,8 +277,8 @@ def run_ours(args) -> dict | None:
         out_host.copy_(out, non_blocking=True)
         e2e_ev[i][1].record(stream)
     torch.cuda.synchronize()
-    e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev)
-    e2e_value = ws * nw * args.steps / (e2e_ms * 1e-3)
+    e2e_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in e2e_ev), dev)
+    e2e_value = weak_scaling_rate(ws, nw, args.steps, e2e_ms)
 
     # ---- direct likelihood: stored templates (HBM roofline) ----
     del flush
@@ -323,10 +341,10 @@ def run_ours(args) -> dict | None:
     clk.__exit__(None, None, None)
     clocks = clk.summary()
     sm_for_peak = peaks.get("sm_max_mhz", 2032.0)
-    fp64_peak = fp64_peak_gflops(sm_for_peak)
+    fma_peak = fma_peak_tinst(sm_for_peak)
     E = ref.bins
-    flop = nw * (E + 1) * HET_MIXED_FP64_FLOP_PER_EDGE
-    achieved = flop / (ms_per_step * 1e-3) / 1e9
+    inst = nw * (E + 1) * HET_MIXED_FMA_INST_PER_EDGE
+    achieved = inst / (ms_per_step * 1e-3) / 1e12
     roof_traffic = None
     prof = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(prof):
@@ -369,15 +387,14 @@ def run_ours(args) -> dict | None:
         "direct_hbm_gbs": stored_gbs,
         "uneven": uneven,
         "serving": serving,
-        "roofline": {"bound": "alu", "pipe": "fp64", "achieved": achieved, "peak": fp64_peak,
-                     "unit": "GFLOP/s", "frac": achieved / fp64_peak, "traffic": roof_traffic,
-                     "kernel": "het_mixed_kernel",
-                     "peak_note": f"148 SM x 2 DFMA/clk x 2 flop x {sm_for_peak:.0f} MHz "
-                                  "(2 DFMA/clk/SM measured on this B300)",
-                     "flop_per_edge": HET_MIXED_FP64_FLOP_PER_EDGE},
+        "roofline": {"bound": "alu", "pipe": "fp32 (FMA pipe)", "achieved": achieved, "peak": fma_peak,
+                     "unit": "T fp32-pipe inst/s", "frac": achieved / fma_peak, "traffic": roof_traffic,
+                     "kernel": "het_mixed_kernel<8,128>",
+                     "peak_note": f"148 SM x 128 FP32 lanes x {sm_for_peak:.0f} MHz",
+                     "inst_per_edge": HET_MIXED_FMA_INST_PER_EDGE},
         "roofline_direct_stored": {"bound": "hbm", "achieved": stored_gbs, "peak": peaks["hbm_gbs"],
                                    "unit": "GB/s", "frac": stored_gbs / peaks["hbm_gbs"],
-                                   "traffic": None, "kernel": "direct_stored_kernel<double2,4>",
+                                   "traffic": None, "kernel": "direct_stored_df_kernel<4,4>",
                                    "peak_source": f"{peak_src} hbm_gbs"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": th_np.nbytes,
                 "d2h_bytes_per_step": out_host.numel() * 8},
@@ -444,22 +461,25 @@ def run_serving(M, WL, cfg=None, n_sources: int = 32, seconds: float = 1.0,
         srv.reset_stats()
         rids = [[] for _ in range(n_sources)]
 
-        def sampler(s):
+        # requests of each sampler, drawn and laid out (contiguous theta) before the clock starts
+        plans = []
+        for s in range(n_sources):
             sz, st, gaps = I.draw_requests(I.rng(4, 1000 * ri + s), int(rate * seconds / n_sources * 2) + 4,
                                            rate=rate / n_sources)
+            at = np.cumsum(gaps)
+            keep = at <= seconds
+            plans.append([(float(a), np.ascontiguousarray(pools[s][:, b:b + n]), int(b), int(n))
+                          for a, b, n in zip(at[keep], st[keep], sz[keep])])
+
+        def sampler(s):
             t0 = time.perf_counter()
-            t = 0.0
-            for k in range(len(sz)):
-                t += gaps[k]
-                if t > seconds:
-                    break
+            for t, th, b, n in plans[s]:
                 dt = t0 + t - time.perf_counter()
                 if dt > 0:
                     time.sleep(dt)
-                th = pools[s][:, st[k]:st[k] + sz[k]]
                 while True:
                     try:
-                        rids[s].append((srv.submit(ids[s], th), s, int(st[k]), int(sz[k])))
+                        rids[s].append((srv.submit(ids[s], th), s, b, n))
                         break
                     except M.MBHError as exc:   # queue full: back off
                         if exc.status != 5:
@@ -501,6 +521,26 @@ def run_serving(M, WL, cfg=None, n_sources: int = 32, seconds: float = 1.0,
             "rates": steps, "peak_walkers_per_s": best["walkers_per_s"],
             "abs_dlnL_vs_fp64_kernel": {"p50": float(np.median(e)), "p99": float(np.quantile(e, 0.99)),
                                         "max": float(e.max()), "walkers": int(e.size)}}
+
+
+def run_fused_only(args, M, WL, g, src, rank, dev, stream) -> dict | None:
+    """Profiling case: the fused generate-and-reduce direct path, mixed precision, on
+    args.stored prior templates of the 1-yr grid."""
+    import torch
+    th = WL.to_dev(I.draw_prior_batch(I.rng(1, 300 + rank), args.stored, g["t_obs"]))
+    out = torch.empty((3, args.stored), dtype=torch.float64, device=dev)
+    for _ in range(args.warmup):
+        M.direct_loglike_batch(src.data, th, "mixed", out=out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        M.direct_loglike_batch(src.data, th, "mixed", out=out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    return {"profile_case": "fused", "templates": args.stored, "ms": ms,
+            "templates_per_s": args.stored / (ms * 1e-3)} if rank == 0 else None
 
 
 def run_direct_only(args, M, WL, g, src, rank, dev, stream, peaks, peak_src) -> dict | None:
@@ -596,7 +636,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="CPU work of the oracle baseline (0: skip)")
-    ap.add_argument("--only", default="all", choices=["all", "het", "direct"],
+    ap.add_argument("--only", default="all", choices=["all", "het", "direct", "fused"],
                     help="profiling cases: time only the heterodyne steps or only the direct path")
     ap.add_argument("--walkers", type=int, default=N_WALKERS, help="heterodyne batch (profiling)")
     ap.add_argument("--stored", type=int, default=N_STORED, help="stored templates (profiling)")

@@ -336,7 +336,8 @@ extern "C" void mbh_data_free(mbh_data* data)
 // ------------------------------------------------------------------------------------------
 constexpr int kDirThreads = 256;
 
-// Fused generation + reduction, float64.
+// Fused generation + reduction, float64.  A grid point's data is loaded once for the T
+// walkers; per-thread per-walker sums live in shared memory.
 template <int T>
 __global__ void __launch_bounds__(kDirThreads)
     direct_fused_f64_kernel(const double* __restrict__ theta, int64_t W, double f0, double df,
@@ -345,15 +346,16 @@ __global__ void __launch_bounds__(kDirThreads)
                             double2* __restrict__ part)
 {
     __shared__ Walker ws[T];
-    __shared__ double sm[32 * 2 * T];
+    __shared__ double2 acc[T][kDirThreads];
+    __shared__ double sm[32 * 2];
     const int64_t w0 = (int64_t)blockIdx.x * T;
     const int ch = blockIdx.y;
-    if (threadIdx.x < T && w0 + threadIdx.x < W) walker_setup(theta, W, w0 + threadIdx.x, ws[threadIdx.x]);
+    const int nt = (int)std::min<int64_t>(T, W - w0);
+    if (threadIdx.x < nt) walker_setup(theta, W, w0 + threadIdx.x, ws[threadIdx.x]);
+#pragma unroll
+    for (int t = 0; t < T; ++t) acc[t][threadIdx.x] = make_double2(0.0, 0.0);
     __syncthreads();
     const int64_t kb = (int64_t)ch * chunk, ke = std::min<int64_t>(n, kb + chunk);
-    double acc[2 * T];
-#pragma unroll
-    for (int t = 0; t < 2 * T; ++t) acc[t] = 0.0;
     for (int64_t k = kb + threadIdx.x; k < ke; k += kDirThreads) {
         const double f = f0 + (double)k * df;
         double2 d[3];
@@ -363,24 +365,24 @@ __global__ void __launch_bounds__(kDirThreads)
             d[c] = __ldg(wd + (int64_t)c * n + k);
             v[c] = __ldg(wv + (int64_t)c * n + k);
         }
-        for (int t = 0; t < T; ++t) {
-            if (w0 + t < W) {
-                cd h[3];
-                if (point_f64(ws[t], f, t_obs, h)) {
+        for (int t = 0; t < nt; ++t) {
+            cd h[3];
+            if (point_f64(ws[t], f, t_obs, h)) {
+                double2 s2 = acc[t][threadIdx.x];
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        acc[2 * t] += d[c].x * h[c].re + d[c].y * h[c].im;
-                        acc[2 * t + 1] += v[c] * (h[c].re * h[c].re + h[c].im * h[c].im);
-                    }
+                for (int c = 0; c < 3; ++c) {
+                    s2.x += d[c].x * h[c].re + d[c].y * h[c].im;
+                    s2.y += v[c] * (h[c].re * h[c].re + h[c].im * h[c].im);
                 }
+                acc[t][threadIdx.x] = s2;
             }
         }
     }
-    block_sum<2 * T>(acc, sm);
-    if (threadIdx.x == 0)
-#pragma unroll
-        for (int t = 0; t < T; ++t)
-            if (w0 + t < W) part[(w0 + t) * nchunks + ch] = make_double2(acc[2 * t], acc[2 * t + 1]);
+    for (int t = 0; t < nt; ++t) {
+        double r[2] = {acc[t][threadIdx.x].x, acc[t][threadIdx.x].y};
+        block_sum<2>(r, sm);
+        if (threadIdx.x == 0) part[(w0 + t) * nchunks + ch] = make_double2(r[0], r[1]);
+    }
 }
 
 // lnL = -1/2 (<d|d> + <h|h> - 2 <d|h>), partial sums added in chunk order.

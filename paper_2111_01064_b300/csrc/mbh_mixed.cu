@@ -397,10 +397,12 @@ mbh_status mbh::launch_template_mixed(const mbh_grid* g, const double* theta, in
 constexpr int kDirThreadsM = 256;
 
 // block (walker tile of T, frequency chunk).  The frequency tables and the float32 data of a
-// grid point are computed/loaded once and reused by the T walkers.  Data and templates are in
-// units where h/sigma is O(1) (float32 range); per-point products are float32, sums float64.
+// grid point are loaded once and reused by the T walkers; each thread keeps its per-walker
+// float64 sums in shared memory (a dynamically indexed register array would go to local
+// memory), reduced per walker at the end.  Data and templates are in units where h/sigma is
+// O(1) (float32 range); per-point products are float32, sums float64.
 template <int T>
-__global__ void __launch_bounds__(kDirThreadsM)
+__global__ void __launch_bounds__(kDirThreadsM, 2)
     direct_fused_mixed_kernel(const double* __restrict__ theta, int64_t W, const float4* __restrict__ ft1,
                               const float4* __restrict__ ft2, double t_obs,
                               const float2* __restrict__ wd, const float* __restrict__ wv,
@@ -409,16 +411,17 @@ __global__ void __launch_bounds__(kDirThreadsM)
 {
     __shared__ WalkerDF wsd[T];
     __shared__ WalkerF wsf[T];
-    __shared__ double sm[32 * 2 * T];
+    __shared__ double2 acc[T][kDirThreadsM];
+    __shared__ double sm[32 * 2];
     const int64_t w0 = (int64_t)blockIdx.x * T;
     const int ch = blockIdx.y;
-    if (threadIdx.x < T && w0 + threadIdx.x < W) walker_setup_mixed(theta, W, w0 + threadIdx.x, wsd[threadIdx.x], wsf[threadIdx.x]);
+    const int nt = (int)std::min<int64_t>(T, W - w0);
+    if (threadIdx.x < nt) walker_setup_mixed(theta, W, w0 + threadIdx.x, wsd[threadIdx.x], wsf[threadIdx.x]);
+#pragma unroll
+    for (int t = 0; t < T; ++t) acc[t][threadIdx.x] = make_double2(0.0, 0.0);
     const f2 tob = split_d(t_obs);
     __syncthreads();
     const int64_t kb = (int64_t)ch * chunk, ke = std::min<int64_t>(n, kb + chunk);
-    double acc[2 * T];
-#pragma unroll
-    for (int t = 0; t < 2 * T; ++t) acc[t] = 0.0;
     for (int64_t k = kb + threadIdx.x; k < ke; k += kDirThreadsM) {
         const float4 a = __ldg(ft1 + k), b = __ldg(ft2 + k);
         const FreqDF q = {{a.x, a.y}, {a.z, a.w}, {b.x, b.y}, {b.z, b.w}};
@@ -429,27 +432,27 @@ __global__ void __launch_bounds__(kDirThreadsM)
             d[c] = __ldg(wd + (int64_t)c * n + k);
             v[c] = __ldg(wv + (int64_t)c * n + k);
         }
-        for (int t = 0; t < T; ++t) {
-            if (w0 + t < W) {
-                cf h[3];
-                if (point_mixed(wsd[t], wsf[t], q, tob, inv_sigma, h)) {
-                    float pd = 0.0f, ph = 0.0f;
+        for (int t = 0; t < nt; ++t) {
+            cf h[3];
+            if (point_mixed(wsd[t], wsf[t], q, tob, inv_sigma, h)) {
+                float pd = 0.0f, ph = 0.0f;
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        pd += d[c].x * h[c].re + d[c].y * h[c].im;
-                        ph += v[c] * (h[c].re * h[c].re + h[c].im * h[c].im);
-                    }
-                    acc[2 * t] += (double)pd;
-                    acc[2 * t + 1] += (double)ph;
+                for (int c = 0; c < 3; ++c) {
+                    pd += d[c].x * h[c].re + d[c].y * h[c].im;
+                    ph += v[c] * (h[c].re * h[c].re + h[c].im * h[c].im);
                 }
+                double2 s2 = acc[t][threadIdx.x];
+                s2.x += (double)pd;
+                s2.y += (double)ph;
+                acc[t][threadIdx.x] = s2;
             }
         }
     }
-    block_sum<2 * T>(acc, sm);
-    if (threadIdx.x == 0)
-#pragma unroll
-        for (int t = 0; t < T; ++t)
-            if (w0 + t < W) part[(w0 + t) * nchunks + ch] = make_double2(acc[2 * t], acc[2 * t + 1]);
+    for (int t = 0; t < nt; ++t) {
+        double r[2] = {acc[t][threadIdx.x].x, acc[t][threadIdx.x].y};
+        block_sum<2>(r, sm);
+        if (threadIdx.x == 0) part[(w0 + t) * nchunks + ch] = make_double2(r[0], r[1]);
+    }
 }
 
 __global__ void freq_table_kernel(double f0, double df, int64_t n, float4* __restrict__ t1,

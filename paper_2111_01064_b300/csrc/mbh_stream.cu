@@ -51,7 +51,9 @@ __device__ void block_sum_df(f2 (&v)[N], double (&out)[N])
     }
 }
 
-template <int T>
+// U grid points per thread per step, loads for all of them (data pair + T templates) issued
+// before any arithmetic, so that enough bytes are in flight to cover HBM latency.
+template <int T, int U>
 __global__ void __launch_bounds__(kStreamThreads)
     direct_stored_df_kernel(const float4* __restrict__ wsp, const float2* __restrict__ vsp,
                             const double2* __restrict__ h, int64_t n, int64_t W, int64_t chunk,
@@ -60,22 +62,34 @@ __global__ void __launch_bounds__(kStreamThreads)
     const int64_t w0 = (int64_t)blockIdx.x * T;
     const int ch = blockIdx.y;
     const int64_t kb = (int64_t)ch * chunk, ke = std::min<int64_t>(n, kb + chunk);
+    const int nt = (int)std::min<int64_t>(T, W - w0);
     f2 adh[T], ahh[T];
 #pragma unroll
     for (int t = 0; t < T; ++t) adh[t] = ahh[t] = {0.0f, 0.0f};
     for (int c = 0; c < 3; ++c) {
         const float4* wc = wsp + (int64_t)c * n;
         const float2* vc = vsp + (int64_t)c * n;
-#pragma unroll 2
-        for (int64_t k = kb + threadIdx.x; k < ke; k += kStreamThreads) {
-            const float4 d = __ldg(wc + k);
-            const float2 v2 = __ldg(vc + k);
-            const f2 dre = {d.x, d.z}, dim = {d.y, d.w}, v = {v2.x, v2.y};
+        const double2* hc = h + (w0 * 3 + c) * n;
+        for (int64_t k0 = kb + threadIdx.x; k0 < ke; k0 += (int64_t)U * kStreamThreads) {
+            float4 d[U];
+            float2 v2[U];
+            double2 x[U][T];
 #pragma unroll
-            for (int t = 0; t < T; ++t) {
-                if (w0 + t < W) {
-                    const double2 x = __ldcs(h + ((w0 + t) * 3 + c) * n + k);
-                    const f2 xr = split_f64(x.x, shift), xi = split_f64(x.y, shift);
+            for (int u = 0; u < U; ++u) {
+                const int64_t k = k0 + (int64_t)u * kStreamThreads;
+                const bool ok = k < ke;
+                d[u] = ok ? __ldg(wc + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+                v2[u] = ok ? __ldg(vc + k) : make_float2(0.f, 0.f);
+#pragma unroll
+                for (int t = 0; t < T; ++t)
+                    x[u][t] = (ok && t < nt) ? __ldcs(hc + (int64_t)t * 3 * n + k) : make_double2(0.0, 0.0);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const f2 dre = {d[u].x, d[u].z}, dim = {d[u].y, d[u].w}, v = {v2[u].x, v2[u].y};
+#pragma unroll
+                for (int t = 0; t < T; ++t) {
+                    const f2 xr = split_f64(x[u][t].x, shift), xi = split_f64(x[u][t].y, shift);
                     df_acc(adh[t], df_mul(dre, xr));
                     df_acc(adh[t], df_mul(dim, xi));
                     df_acc(ahh[t], df_mul(v, df_add(df_sqr(xr), df_sqr(xi))));
@@ -83,18 +97,18 @@ __global__ void __launch_bounds__(kStreamThreads)
             }
         }
     }
-    f2 v[2 * T];
+    f2 vals[2 * T];
 #pragma unroll
     for (int t = 0; t < T; ++t) {
-        v[2 * t] = adh[t];
-        v[2 * t + 1] = ahh[t];
+        vals[2 * t] = adh[t];
+        vals[2 * t + 1] = ahh[t];
     }
     double acc[2 * T];
-    block_sum_df<2 * T>(v, acc);
+    block_sum_df<2 * T>(vals, acc);
     if (threadIdx.x == 0)
 #pragma unroll
         for (int t = 0; t < T; ++t)
-            if (w0 + t < W) part[(w0 + t) * nchunks + ch] = make_double2(acc[2 * t], acc[2 * t + 1]);
+            if (t < nt) part[(w0 + t) * nchunks + ch] = make_double2(acc[2 * t], acc[2 * t + 1]);
 }
 
 template <int T>
@@ -152,7 +166,7 @@ mbh_status launch_stored(const mbh_data* data, const void* h, int64_t W, mbh_pre
     const int64_t tiles = (W + T - 1) / T;
     dim3 grid((unsigned)tiles, (unsigned)nchunks);
     if (p == MBH_FP64)
-        direct_stored_df_kernel<T><<<grid, kStreamThreads, 0, st>>>(
+        direct_stored_df_kernel<T, 4><<<grid, kStreamThreads, 0, st>>>(
             data->wsp, data->vsp, (const double2*)h, data->grid.n, W, chunk, nchunks, data->shift, part);
     else
         direct_stored_f32_kernel<T><<<grid, kStreamThreads, 0, st>>>(
