@@ -74,10 +74,13 @@ def fp64_peak_gflops(sm_mhz: float) -> float:
 
 
 # The mixed heterodyne kernel is bound by the float32 (FMA) pipe: per edge evaluation it
-# issues 1399 FMA-pipe thread instructions (double-float phase chain, float32 response,
+# issues 1279 FMA-pipe thread instructions (double-float phase chain, float32 response,
 # ratio and contraction), counted by ncu on het_mixed_kernel<8,128> (FMA-pipe utilisation x
 # peak x elapsed cycles / edges).  Peak: 148 SMs x 128 FP32 lanes x SM clock.
-HET_MIXED_FMA_INST_PER_EDGE = 1399
+HET_MIXED_FMA_INST_PER_EDGE = 1279
+HET_MIXED_DRAM_BYTES = 1.57824e6           # read + write per 16384-walker launch (ncu)
+STORED_DATA_BYTES = 75.74e6                # data pairs, read once per launch (ncu: 883.66 MB
+STORED_BYTES_PER_TEMPLATE = 50.4945e6      # for 16 templates = 75.74 MB + 16 x 50.49 MB)
 
 
 def fma_peak_tinst(sm_mhz: float) -> float:
@@ -345,11 +348,11 @@ def run_ours(args) -> dict | None:
     E = ref.bins
     inst = nw * (E + 1) * HET_MIXED_FMA_INST_PER_EDGE
     achieved = inst / (ms_per_step * 1e-3) / 1e12
-    roof_traffic = None
-    prof = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(prof):
-        with open(prof) as fh:
-            roof_traffic = json.load(fh).get("het_mixed_kernel_bytes_per_launch")
+    # DRAM traffic per launch from ncu captures (profiles/het_mixed_kernel_16384w_256b_1yr.md,
+    # profiles/direct_stored_df_kernel_16tpl_1yr.md; the stored-template launch scaled from
+    # 16 to N_STORED templates by the templates processed)
+    roof_traffic = HET_MIXED_DRAM_BYTES if nw == N_WALKERS else None
+    stored_traffic = STORED_DATA_BYTES + N_STORED * STORED_BYTES_PER_TEMPLATE
 
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -394,7 +397,7 @@ def run_ours(args) -> dict | None:
                      "inst_per_edge": HET_MIXED_FMA_INST_PER_EDGE},
         "roofline_direct_stored": {"bound": "hbm", "achieved": stored_gbs, "peak": peaks["hbm_gbs"],
                                    "unit": "GB/s", "frac": stored_gbs / peaks["hbm_gbs"],
-                                   "traffic": None, "kernel": "direct_stored_df_kernel<4,4>",
+                                   "traffic": stored_traffic, "kernel": "direct_stored_df_kernel<4,4>",
                                    "peak_source": f"{peak_src} hbm_gbs"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": th_np.nbytes,
                 "d2h_bytes_per_step": out_host.numel() * 8},

@@ -177,6 +177,14 @@ MBH_API mbh_status het_loglike_batch(const mbh_ref* const* refs, const int64_t* 
                              int32_t n_sources, const double* theta_dev,
                              mbh_precision precision, double* out_dev, void* stream);
 
+/* Test support: evaluates the library's own float32 device math on n inputs
+ * (float32 device arrays) so that it can be checked against CUDA's functions and
+ * float64 references.  kind 0: sin and cos of x (o1, o2; Cody-Waite reduction and
+ * Taylor polynomials, |x| up to ~100); kind 1: sin(x)/x (o1); kind 2:
+ * sinc(x(1+y)) - sinc(x(1-y)) without cancellation (o1). */
+MBH_API mbh_status mbh_selftest_math(int32_t kind, const float* x_dev, const float* y_dev, int64_t n,
+                             float* o1_dev, float* o2_dev, void* stream);
+
 /* Launch configuration of the heterodyne kernels.  A walker is handled by
  * threads_per_walker threads (1, 2, 4, 8, 16 or 32) that deal its bin edges
  * round-robin (each round covers threads_per_walker bins); a block of `block`
@@ -256,6 +264,13 @@ MBH_API mbh_status mbh_server_add_source(mbh_server* server, const mbh_ref* ref,
 /* Evicts a source: its queued requests complete with MBH_EINVAL, batches in flight
  * finish first (the call blocks until then). */
 MBH_API mbh_status mbh_server_remove_source(mbh_server* server, int32_t source_id);
+/* Reference refresh (Sec. III B: the reference is replaced by the best walker every
+ * few thousand sampler iterations): every request of the source launched after the
+ * call uses `ref` (prepared, e.g., around the best walker, with its band re-selected
+ * by het_prepare_reference); requests already queued but not launched use it too.
+ * Returns once the batches in flight on the previous reference have finished, so the
+ * caller may then free it.  MBH_EBUSY if the new reference does not fit the budget. */
+MBH_API mbh_status mbh_server_replace_source(mbh_server* server, int32_t source_id, const mbh_ref* ref);
 /* theta_host: float64 [11][W]; out_host: float64 [3][W] (lnL, <d|h>, <h|h>), written
  * on completion and owned by the caller until mbh_server_wait returns.  MBH_EBUSY
  * when the queue is full, MBH_EINVAL for an unknown source or W outside

@@ -89,7 +89,15 @@ __device__ __forceinline__ f2 dd_mul_f(f2 a, float b)
     return fast_two_sum(p, e);
 }
 
-__device__ __forceinline__ f2 dd_fma(f2 a, f2 b, f2 c) { return dd_add(dd_mul(a, b), c); }
+// a * b + c; the product is left unnormalised (p + e with |e| <= ulp(p)), which the
+// two-sum at the start of dd_add absorbs.
+__device__ __forceinline__ f2 dd_fma(f2 a, f2 b, f2 c)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+    return dd_add({p, e}, c);
+}
 
 __device__ __forceinline__ float dd_to_float(f2 a) { return __fadd_rn(a.hi, a.lo); }
 

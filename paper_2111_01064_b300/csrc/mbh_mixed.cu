@@ -48,22 +48,61 @@ __device__ __forceinline__ float nPnf(const float* P, const float* n)
            2.0f * (P[1] * n[0] * n[1] + P[2] * n[0] * n[2] + P[4] * n[1] * n[2]);
 }
 
-__device__ __forceinline__ float sincf(float x) { return x == 0.0f ? 1.0f : sinf(x) / x; }
+// sin x / x: Taylor series in x^2 up to x^14/15! for |x| < 2 (truncation < 2e-10), else sinf/x.
+__device__ __forceinline__ float sincf(float x)
+{
+    if (fabsf(x) >= 2.0f) return sinf(x) / x;
+    const float u2 = x * x;
+    float p = -1.0f / 1307674368000.0f;
+    p = fmaf(p, u2, 1.0f / 6227020800.0f);
+    p = fmaf(p, u2, -1.0f / 39916800.0f);
+    p = fmaf(p, u2, 1.0f / 362880.0f);
+    p = fmaf(p, u2, -1.0f / 5040.0f);
+    p = fmaf(p, u2, 1.0f / 120.0f);
+    p = fmaf(p, u2, -1.0f / 6.0f);
+    return fmaf(p, u2, 1.0f);
+}
 
-// sinc(x (1 + k)) - sinc(x (1 - k)) without cancellation: for arguments below 1 as
+// sin and cos of |x| <~ 100: Cody-Waite reduction by pi/2 (two-term split of pi/2, the first
+// product exact inside the FMA), then the Taylor polynomials of sin (to r^9/9!) and cos (to
+// r^10/10!) on |r| <= pi/4 (truncation < 2e-9), rotated by the quadrant.
+__device__ __forceinline__ void sincos_small(float x, float* s, float* c)
+{
+    const float q = rintf(x * 0.636619772f);                 // 2/pi
+    float r = fmaf(-q, 1.57079637f, x);                       // float(pi/2)
+    r = fmaf(-q, -4.37113883e-8f, r);                         // pi/2 - float(pi/2)
+    const float r2 = r * r;
+    float sp = fmaf(r2, 1.0f / 362880.0f, -1.0f / 5040.0f);
+    sp = fmaf(sp, r2, 1.0f / 120.0f);
+    sp = fmaf(sp, r2, -1.0f / 6.0f);
+    const float sr = fmaf(sp * r2, r, r);
+    float cp = fmaf(r2, -1.0f / 3628800.0f, 1.0f / 40320.0f);
+    cp = fmaf(cp, r2, -1.0f / 720.0f);
+    cp = fmaf(cp, r2, 1.0f / 24.0f);
+    cp = fmaf(cp, r2, -0.5f);
+    const float cr = fmaf(cp, r2, 1.0f);
+    const int iq = (int)q;
+    const bool swap = iq & 1;
+    const float s0 = swap ? cr : sr, c0 = swap ? sr : cr;
+    *s = (iq & 2) ? -s0 : s0;
+    *c = ((iq + 1) & 2) ? -c0 : c0;
+}
+
+// sinc(x (1 + k)) - sinc(x (1 - k)) without cancellation: for arguments below 2 as
 // (a^2 - b^2) sum_{j>=1} (-1)^j P_j / (2j+1)!, P_1 = 1, P_{j+1} = a^2 P_j + b^{2j}
 // (a^{2j} - b^{2j} = (a^2 - b^2) P_j), with a^2 - b^2 = 4 x^2 k; directly above.
 __device__ __forceinline__ float sinc_diff(float x, float k)
 {
     const float a = x * (1.0f + k), b = x * (1.0f - k);
-    if (fmaxf(fabsf(a), fabsf(b)) >= 1.0f) return sincf(a) - sincf(b);
+    if (fmaxf(fabsf(a), fabsf(b)) >= 2.0f) return sincf(a) - sincf(b);
     const float a2 = a * a, b2 = b * b;
-    // 1/(2j+1)! for j = 1..7
-    const float inv_fact[7] = {1.0f / 6.0f, 1.0f / 120.0f, 1.0f / 5040.0f, 1.0f / 362880.0f,
-                               1.0f / 39916800.0f, 1.0f / 6227020800.0f, 1.0f / 1307674368000.0f};
+    // 1/(2j+1)! for j = 1..9 (terms beyond are below 5e-12 relative for arguments < 2)
+    const float inv_fact[9] = {1.0f / 6.0f, 1.0f / 120.0f, 1.0f / 5040.0f, 1.0f / 362880.0f,
+                               1.0f / 39916800.0f, 1.0f / 6227020800.0f, 1.0f / 1307674368000.0f,
+                               1.0f / 355687428096000.0f, 1.0f / 121645100408832000.0f};
     float P = 1.0f, bp = 1.0f, sum = 0.0f, sign = -1.0f;
 #pragma unroll
-    for (int j = 0; j < 7; ++j) {
+    for (int j = 0; j < 9; ++j) {
         sum += sign * P * inv_fact[j];
         sign = -sign;
         bp *= b2;
@@ -106,7 +145,7 @@ __device__ inline void transfer_f32(const WalkerF& w, float f, float sa, float c
         const float np = nPnf(w.Pp, n), nc = nPnf(w.Pc, n);
         const cf F = {np * w.Kp[0] + nc * w.Kc[0], np * w.Kp[1] + nc * w.Kc[1]};
         float sph, cph;
-        sincosf((float)kPi * f * (armS + ko), &sph, &cph);
+        sincos_small((float)kPi * f * (armS + ko), &sph, &cph);
         const cf g = fmul({-x * sph, -x * cph}, F);
         yf[a] = fscale(g, sincf(x * (1.0f - kn)));
         yb[a] = fscale(g, sincf(x * (1.0f + kn)));
@@ -114,7 +153,7 @@ __device__ inline void transfer_f32(const WalkerF& w, float f, float sa, float c
     }
     const cf y12 = yf[0], y21 = yb[0], y23 = yf[1], y32 = yb[1], y31 = yf[2], y13 = yb[2];
     float s1, c1;
-    sincosf(x, &s1, &c1);
+    sincos_small(x, &s1, &c1);
     const float s2 = 2.0f * s1 * c1, c2 = 1.0f - 2.0f * s1 * s1;   // sin 2x, cos 2x
     const cf D = {c2, -s2};
     const cf W1 = {2.0f * s1 * s1, 2.0f * s1 * c1};                 // 1 - D
@@ -308,7 +347,7 @@ __device__ __forceinline__ bool phase_df(const WalkerDF& w, const WalkerF& wf, c
     // orbit angle alpha(t) = alpha(t_ref) + da
     const float da = dt.hi * (float)(kTwoPi / kYear);
     float sh, ch;
-    sincosf(0.5f * da, &sh, &ch);
+    sincos_small(0.5f * da, &sh, &ch);
     const float sd = 2.0f * sh * ch, omc = 2.0f * sh * sh;   // sin da, 1 - cos da
     const f2 sa_d = dd_add_f(w.sa_ref, wf.ca_ref * sd - wf.sa_ref * omc);
     const f2 ca_d = dd_add_f(w.ca_ref, -(wf.ca_ref * omc + wf.sa_ref * sd));
@@ -338,7 +377,7 @@ __device__ __forceinline__ bool point_mixed(const WalkerDF& w, const WalkerF& wf
     float sa, ca, amp;
     if (!phase_df(w, wf, q, t_obs, Phi, sa, ca, amp)) return false;
     float sp, cp;
-    sincosf(reduce_phase(Phi), &sp, &cp);
+    sincos_small(reduce_phase(Phi), &sp, &cp);
     cf T[3];
     transfer_f32(wf, q.f.hi, sa, ca, T);
     const cf e = {amp * scale * cp, -amp * scale * sp};
@@ -348,6 +387,42 @@ __device__ __forceinline__ bool point_mixed(const WalkerDF& w, const WalkerF& wf
 }
 
 }  // namespace mbh
+
+// ------------------------------------------------------------------------------------------
+// self-test of the float32 device math
+// ------------------------------------------------------------------------------------------
+__global__ void selftest_math_kernel(int kind, const float* __restrict__ x, const float* __restrict__ y,
+                                     int64_t n, float* __restrict__ o1, float* __restrict__ o2)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (kind == 0) {
+            float s, c;
+            sincos_small(x[i], &s, &c);
+            o1[i] = s;
+            o2[i] = c;
+        } else if (kind == 1) {
+            o1[i] = sincf(x[i]);
+        } else {
+            o1[i] = sinc_diff(x[i], y[i]);
+        }
+    }
+}
+
+extern "C" mbh_status mbh_selftest_math(int32_t kind, const float* x_dev, const float* y_dev, int64_t n,
+                                        float* o1_dev, float* o2_dev, void* stream)
+{
+    if (kind < 0 || kind > 2) return fail(MBH_EINVAL, "kind must be 0, 1 or 2");
+    if (n < 0) return fail(MBH_EINVAL, "n < 0");
+    if (n == 0) return MBH_OK;
+    if (!x_dev || !o1_dev || (kind == 0 && !o2_dev) || (kind == 2 && !y_dev))
+        return fail(MBH_EINVAL, "NULL buffer");
+    if (mbh_status s = check_device()) return s;
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 148 * 32);
+    selftest_math_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(kind, x_dev, y_dev, n, o1_dev, o2_dev);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MBH_OK : cuda_fail(e, "mbh_selftest_math");
+}
 
 // ------------------------------------------------------------------------------------------
 // templates (complex64 storage)
@@ -647,7 +722,7 @@ __global__ void __launch_bounds__(BLOCK)
                 float sa, ca, amp;
                 if (phase_df(wsd[lw], wsf[lw], q, tob, Phi, sa, ca, amp)) {
                     float sh, ch;
-                    sincosf(0.5f * reduce_phase(dd_sub(Phi, ld_f2(me.phi0))), &sh, &ch);
+                    sincos_small(0.5f * reduce_phase(dd_sub(Phi, ld_f2(me.phi0))), &sh, &ch);
                     const cf em1 = {-2.0f * sh * sh, -2.0f * sh * ch};   // e^{-i dPhi} - 1
                     cf T[3];
                     transfer_f32(wsf[lw], q.f.hi, sa, ca, T);

@@ -53,6 +53,7 @@ struct Source {
     const mbh_ref* ref = nullptr;
     size_t bytes = 0;
     int64_t pending = 0;   // requests queued or in flight
+    int64_t inflight = 0;  // requests in batches on the GPU (using `ref`)
 };
 
 struct Slot {
@@ -133,7 +134,10 @@ void finish_slot(mbh_server* S, Slot& sl, mbh_status st)
         r->t_done = now;
         r->done = true;
         auto it = S->sources.find(r->source);
-        if (it != S->sources.end()) --it->second.pending;
+        if (it != S->sources.end()) {
+            --it->second.pending;
+            --it->second.inflight;
+        }
         if (r->status == MBH_OK) {
             S->latencies_ms.push_back(std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count());
             ++S->completed;
@@ -185,7 +189,9 @@ bool launch_one(mbh_server* S, std::unique_lock<std::mutex>& lk)
     std::vector<const mbh_ref*> refs;
     std::vector<int64_t> offsets{0};
     for (auto& r : batch) {
-        refs.push_back(S->sources[r->source].ref);
+        Source& src = S->sources[r->source];
+        refs.push_back(src.ref);
+        ++src.inflight;
         offsets.push_back(offsets.back() + r->W);
     }
     ++S->batches;
@@ -319,6 +325,31 @@ extern "C" mbh_status mbh_server_remove_source(mbh_server* S, int32_t source_id)
     it = S->sources.find(source_id);   // the map may have been rehashed meanwhile
     S->source_bytes -= it->second.bytes;
     S->sources.erase(it);
+    return MBH_OK;
+}
+
+extern "C" mbh_status mbh_server_replace_source(mbh_server* S, int32_t source_id, const mbh_ref* ref)
+{
+    if (!S || !ref) return fail(MBH_EINVAL, "NULL argument");
+    if (ref->device != S->device) return fail(MBH_EINVAL, "reference lives on another device");
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->sources.find(source_id);
+    if (it == S->sources.end()) return fail(MBH_EINVAL, "unknown source %d", source_id);
+    const size_t b = ref_bytes(ref);
+    const size_t used = S->source_bytes - it->second.bytes + S->slot_bytes * S->slots.size();
+    if (used + b > (size_t)S->opts.hbm_budget_bytes) {
+        ++S->rejected;
+        return fail(MBH_EBUSY, "replacement needs %zu bytes; %zu of the %lld-byte budget are in use", b,
+                    used, (long long)S->opts.hbm_budget_bytes);
+    }
+    // batches launched from now on use the new reference; wait for those in flight on the old
+    S->source_bytes += b - it->second.bytes;
+    it->second.bytes = b;
+    it->second.ref = ref;
+    S->cv_done.wait(lk, [&] {
+        auto jt = S->sources.find(source_id);
+        return jt == S->sources.end() || jt->second.inflight <= 0;
+    });
     return MBH_OK;
 }
 

@@ -106,6 +106,7 @@ def lib() -> C.CDLL:
         "mbh_server_create": (C.c_int, [C.POINTER(ServerOpts), C.POINTER(vp)]),
         "mbh_server_add_source": (C.c_int, [vp, vp, C.POINTER(C.c_int32)]),
         "mbh_server_remove_source": (C.c_int, [vp, i32]),
+        "mbh_server_replace_source": (C.c_int, [vp, i32, vp]),
         "mbh_server_submit": (C.c_int, [vp, i32, vp, i64, vp, C.POINTER(C.c_uint64)]),
         "mbh_server_wait": (C.c_int, [vp, C.c_uint64, i32, C.POINTER(C.c_int)]),
         "mbh_server_cancel": (C.c_int, [vp, C.c_uint64]),
@@ -113,6 +114,7 @@ def lib() -> C.CDLL:
         "mbh_server_stats": (C.c_int, [vp, C.POINTER(ServerReport)]),
         "mbh_server_reset_stats": (C.c_int, [vp]),
         "mbh_server_free": (None, [vp]),
+        "mbh_selftest_math": (C.c_int, [i32, vp, vp, i64, vp, vp, vp]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(L, name)
@@ -422,6 +424,12 @@ class Server:
         _check(lib().mbh_server_remove_source(self.handle, int(sid)))
         self.refs.pop(sid, None)
 
+    def replace_source(self, sid: int, ref: Ref):
+        """Hot swap of a source's reference (reference refresh); the previous Ref may be
+        freed once this returns."""
+        _check(lib().mbh_server_replace_source(self.handle, int(sid), ref.handle))
+        self.refs[sid] = ref
+
     def submit(self, sid: int, theta: np.ndarray) -> int:
         th = np.ascontiguousarray(theta, dtype=np.float64)
         W = th.shape[1]
@@ -462,3 +470,17 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def mbh_selftest_math(kind: int, x: torch.Tensor, y: torch.Tensor | None = None, stream=None):
+    """Library float32 device math on x (and y): kind 0 -> (sin, cos), 1 -> sinc,
+    2 -> sinc(x(1+y)) - sinc(x(1-y))."""
+    n = x.numel()
+    o1 = torch.empty_like(x)
+    o2 = torch.empty_like(x) if kind == 0 else None
+    _check(lib().mbh_selftest_math(int(kind), _dev(x, torch.float32, None, "x"),
+                                   _dev(y, torch.float32, None, "y") if y is not None else None, n,
+                                   _dev(o1, torch.float32, None, "o1"),
+                                   _dev(o2, torch.float32, None, "o2") if o2 is not None else None,
+                                   _stream(stream)))
+    return (o1, o2) if kind == 0 else o1

@@ -1,0 +1,61 @@
+"""The library's own float32 device math (used on the mixed-precision hot path) against
+float64 references of the same float32 inputs and against CUDA's sin/cos."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def M():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2111_01064_b300 import mbhlike
+    mbhlike.lib()
+    return mbhlike
+
+
+def test_sincos_small(M):
+    import torch
+    rng = np.random.default_rng(1)
+    x = np.concatenate([rng.uniform(-8, 8, 1 << 20), rng.uniform(-1e-3, 1e-3, 1 << 16),
+                        np.float32([0.0, np.pi / 4, -np.pi / 2, np.pi, 3 * np.pi / 2, 6.0])]).astype(np.float32)
+    xt = torch.from_numpy(x).cuda()
+    s, c = M.mbh_selftest_math(0, xt)
+    s, c = s.cpu().numpy().astype(np.float64), c.cpu().numpy().astype(np.float64)
+    xd = x.astype(np.float64)
+    assert np.max(np.abs(s - np.sin(xd))) <= 3e-7
+    assert np.max(np.abs(c - np.cos(xd))) <= 3e-7
+    small = np.abs(xd) < 1e-3
+    assert np.max(np.abs(s[small] - np.sin(xd[small])) / np.maximum(np.abs(xd[small]), 1e-30)) <= 2e-7
+    # as close to the float64 values as CUDA's own sinf/cosf
+    ts, tc = torch.sin(xt).double().cpu().numpy(), torch.cos(xt).double().cpu().numpy()
+    assert np.max(np.abs(s - np.sin(xd))) <= 3.0 * np.max(np.abs(ts - np.sin(xd))) + 1e-8
+    assert np.max(np.abs(c - np.cos(xd))) <= 3.0 * np.max(np.abs(tc - np.cos(xd))) + 1e-8
+
+
+def test_sinc(M):
+    import torch
+    x = np.linspace(-3.0, 3.0, 600001).astype(np.float32)
+    got = M.mbh_selftest_math(1, torch.from_numpy(x).cuda()).cpu().numpy().astype(np.float64)
+    xd = x.astype(np.float64)
+    ref = np.where(xd == 0, 1.0, np.sin(xd) / np.where(xd == 0, 1.0, xd))
+    assert np.max(np.abs(got - ref)) <= 2e-7
+
+
+def test_sinc_difference_relative(M):
+    import mpmath as mp
+    import torch
+    rng = np.random.default_rng(2)
+    x = rng.uniform(1e-5, 1.9, 2000).astype(np.float32)
+    k = rng.uniform(-1, 1, 2000).astype(np.float32)
+    got = M.mbh_selftest_math(2, torch.from_numpy(x).cuda(), torch.from_numpy(k).cuda()).cpu().numpy()
+    mp.mp.dps = 40
+    for i in range(0, 2000, 10):
+        X, K = mp.mpf(float(x[i])), mp.mpf(float(k[i]))
+        ref = float(mp.sinc(X * (1 + K)) - mp.sinc(X * (1 - K)))
+        if max(abs(X * (1 + K)), abs(X * (1 - K))) < 2:     # series branch: relative accuracy
+            assert abs(got[i] - ref) <= 1e-6 * abs(ref) + 1e-12, (x[i], k[i], got[i], ref)
+        else:                                                  # plain difference of O(1) values
+            assert abs(got[i] - ref) <= 3e-7, (x[i], k[i], got[i], ref)

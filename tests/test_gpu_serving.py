@@ -138,3 +138,39 @@ def test_slow_producer_and_shutdown(env):
     srv.pause(True)
     pending = srv.submit(sid, _req(ub, 3, 4))
     srv.close()                                      # cancels what was never launched
+
+
+def test_reference_refresh_hot_swap(env):
+    """Reference refresh: re-prepare around the best walker of a batch (band re-selected)
+    and swap it into the running server; later requests use the new reference and give
+    the results of a direct launch with it."""
+    import torch
+    M, WL, ub = env
+    cfg = M.het_config(8, 128, 0)
+    src = ub.sources[4]
+    srv = M.Server(1 << 30, max_batch_walkers=4096, max_inflight_batches=2, cfg=cfg)
+    sid = srv.add_source(ub.refs[4])
+    th = _req(ub, 4)
+    st, out = srv.wait(srv.submit(sid, th))
+    assert st == 0
+    best = int(np.argmax(out[0]))
+    new_ref = M.het_prepare_reference(src.data, th[:, best], int(ub.bins[4]))
+    pending = [srv.submit(sid, th) for _ in range(3)]
+    srv.replace_source(sid, new_ref)
+    after = srv.submit(sid, th)
+    direct_new = M.het_loglike_batch_cfg([new_ref], [0, th.shape[1]], torch.from_numpy(th).cuda(),
+                                         "mixed", cfg).cpu().numpy()
+    st, got = srv.wait(after)
+    assert st == 0
+    np.testing.assert_array_equal(got, direct_new)
+    # requests submitted before the swap were evaluated with one of the two references
+    direct_old = M.het_loglike_batch_cfg([ub.refs[4]], [0, th.shape[1]], torch.from_numpy(th).cuda(),
+                                         "mixed", cfg).cpu().numpy()
+    for rid in pending:
+        st, o = srv.wait(rid)
+        assert st == 0
+        assert np.array_equal(o, direct_old) or np.array_equal(o, direct_new)
+    # at the new reference (r = 1) the heterodyne equals the direct lnL to the mixed bound
+    dr = M.direct_loglike_batch(src.data, torch.from_numpy(th).cuda(), "fp64").cpu().numpy()
+    assert abs(got[0, best] - dr[0, best]) <= 1e-3
+    srv.close()
