@@ -111,7 +111,9 @@ __global__ void __launch_bounds__(kStreamThreads)
             if (t < nt) part[(w0 + t) * nchunks + ch] = make_double2(acc[2 * t], acc[2 * t + 1]);
 }
 
-template <int T>
+// complex64 templates: loads of U grid points issued before the arithmetic; float32 products
+// on O(1)-scaled operands, float32 sums per channel pass, float64 across passes.
+template <int T, int U>
 __global__ void __launch_bounds__(kStreamThreads)
     direct_stored_f32_kernel(const float2* __restrict__ wd, const float* __restrict__ wv,
                              const float2* __restrict__ h, int64_t n, int64_t W, int64_t chunk,
@@ -121,28 +123,39 @@ __global__ void __launch_bounds__(kStreamThreads)
     const int64_t w0 = (int64_t)blockIdx.x * T;
     const int ch = blockIdx.y;
     const int64_t kb = (int64_t)ch * chunk, ke = std::min<int64_t>(n, kb + chunk);
+    const int nt = (int)std::min<int64_t>(T, W - w0);
     double acc[2 * T];
 #pragma unroll
     for (int t = 0; t < 2 * T; ++t) acc[t] = 0.0;
     for (int c = 0; c < 3; ++c) {
         const float2* wc = wd + (int64_t)c * n;
         const float* vc = wv + (int64_t)c * n;
+        const float2* hc = h + (w0 * 3 + c) * n;
         float pd[T], ph[T];
 #pragma unroll
         for (int t = 0; t < T; ++t) pd[t] = ph[t] = 0.0f;
-#pragma unroll 4
-        for (int64_t k = kb + threadIdx.x; k < ke; k += kStreamThreads) {
-            const float2 d = __ldg(wc + k);
-            const float v = __ldg(vc + k);
+        for (int64_t k0 = kb + threadIdx.x; k0 < ke; k0 += (int64_t)U * kStreamThreads) {
+            float2 d[U];
+            float v[U];
+            float2 x[U][T];
 #pragma unroll
-            for (int t = 0; t < T; ++t) {
-                if (w0 + t < W) {
-                    const float2 x = __ldcs(h + ((w0 + t) * 3 + c) * n + k);
-                    const float xr = x.x * inv_sigma, xi = x.y * inv_sigma;
-                    pd[t] = fmaf(d.x, xr, fmaf(d.y, xi, pd[t]));
-                    ph[t] = fmaf(v, fmaf(xr, xr, xi * xi), ph[t]);
-                }
+            for (int u = 0; u < U; ++u) {
+                const int64_t k = k0 + (int64_t)u * kStreamThreads;
+                const bool ok = k < ke;
+                d[u] = ok ? __ldg(wc + k) : make_float2(0.f, 0.f);
+                v[u] = ok ? __ldg(vc + k) : 0.0f;
+#pragma unroll
+                for (int t = 0; t < T; ++t)
+                    x[u][t] = (ok && t < nt) ? __ldcs(hc + (int64_t)t * 3 * n + k) : make_float2(0.f, 0.f);
             }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int t = 0; t < T; ++t) {
+                    const float xr = x[u][t].x * inv_sigma, xi = x[u][t].y * inv_sigma;
+                    pd[t] = fmaf(d[u].x, xr, fmaf(d[u].y, xi, pd[t]));
+                    ph[t] = fmaf(v[u], fmaf(xr, xr, xi * xi), ph[t]);
+                }
         }
 #pragma unroll
         for (int t = 0; t < T; ++t) {
@@ -154,7 +167,7 @@ __global__ void __launch_bounds__(kStreamThreads)
     if (threadIdx.x == 0)
 #pragma unroll
         for (int t = 0; t < T; ++t)
-            if (w0 + t < W) part[(w0 + t) * nchunks + ch] = make_double2(acc[2 * t], acc[2 * t + 1]);
+            if (t < nt) part[(w0 + t) * nchunks + ch] = make_double2(acc[2 * t], acc[2 * t + 1]);
 }
 
 namespace mbh {
@@ -169,7 +182,7 @@ mbh_status launch_stored(const mbh_data* data, const void* h, int64_t W, mbh_pre
         direct_stored_df_kernel<T, 4><<<grid, kStreamThreads, 0, st>>>(
             data->wsp, data->vsp, (const double2*)h, data->grid.n, W, chunk, nchunks, data->shift, part);
     else
-        direct_stored_f32_kernel<T><<<grid, kStreamThreads, 0, st>>>(
+        direct_stored_f32_kernel<T, 4><<<grid, kStreamThreads, 0, st>>>(
             data->wd32, data->wv32, (const float2*)h, data->grid.n, W, chunk, nchunks,
             (float)(1.0 / data->sigma), part);
     cudaError_t e = cudaGetLastError();
