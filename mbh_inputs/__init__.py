@@ -155,3 +155,37 @@ def with_distance(theta: np.ndarray, dl_gpc) -> np.ndarray:
     th = np.array(theta, dtype=np.float64, copy=True)
     th[I_DL] = dl_gpc
     return th
+
+
+# ---- parallel-tempered sampler inputs (Sec. III) -----------------------------
+# The sampler moves x = [ln M_T, q, a1, a2, D_L, phi_ref, cos iota, lambda,
+# sin beta, psi, t_ref]; its prior is uniform in x on the box of Table I.
+PT_PROBS = (0.85, 0.04, 0.03, 0.08)   # stretch, all 8 sky modes, longitudinal, latitudinal
+
+
+def prior_box(t_obs: float) -> tuple[np.ndarray, np.ndarray]:
+    """Lower and upper bounds of x from Table I (t_ref in [0, t_obs])."""
+    lo = np.array([math.log(1e5), 5e-2, -1.0, -1.0, 1e-2, 0.0, -1.0, 0.0, -1.0, 0.0, 0.0])
+    hi = np.array([math.log(1e8), 1.0, 1.0, 1.0, 1e3, 2 * math.pi, 1.0, 2 * math.pi, 1.0,
+                   math.pi, t_obs])
+    return lo, hi
+
+
+def pt_betas(T: int, t_max: float = 100.0) -> np.ndarray:
+    """Inverse temperatures: 1, geometric up to 1/t_max, and 0 (the prior) last."""
+    if T == 1:
+        return np.ones(1)
+    b = np.zeros(T)
+    if T > 2:
+        b[:T - 1] = t_max ** (-np.arange(T - 1) / (T - 2))
+    else:
+        b[0] = 1.0
+    return b
+
+
+def draw_pt_ensemble(g: np.random.Generator, x0: np.ndarray, T: int, W: int, scale: np.ndarray,
+                     lo: np.ndarray, hi: np.ndarray) -> np.ndarray:
+    """T*W sampler positions (11, T*W) around x0: x0 + scale * N(0, 1), clipped
+    into the prior box."""
+    x = x0[:, None] + scale[:, None] * g.standard_normal((N_PARAMS, T * W))
+    return np.clip(x, lo[:, None], hi[:, None])

@@ -28,6 +28,7 @@ def lib():
         L = C.CDLL(path)
         dp = C.POINTER(C.c_double)
         lp = C.POINTER(C.c_long)
+        u32p = C.POINTER(C.c_uint32)
         sig = {
             "oracle_w0": (None, [dp, C.c_double, dp, C.c_long, dp, dp, dp]),
             "oracle_w0_info": (None, [dp, dp]),
@@ -52,6 +53,18 @@ def lib():
                                            C.c_double, dp, C.c_long, dp]),
             "oracle_het_loglike": (None, [dp, C.c_long, C.c_long, lp, C.c_double, C.c_double,
                                           C.c_double, dp, dp, C.c_double, dp]),
+            "oracle_philox4x32_10": (None, [u32p, u32p, u32p]),
+            "oracle_pt_theta": (None, [dp, C.c_long, dp]),
+            "oracle_pt_choice": (None, [C.c_uint64, C.c_uint64, C.c_int, C.c_long, C.c_long, dp,
+                                        C.c_double, dp]),
+            "oracle_pt_sky": (None, [dp, C.c_int, C.c_int]),
+            "oracle_pt_run_het": (None, [dp, dp, C.c_long, C.c_long, dp, dp, dp, dp, C.c_double,
+                                         C.c_uint64, C.c_uint64, C.c_long, C.c_long, lp,
+                                         C.c_double, C.c_double, C.c_double, dp, dp, C.c_double,
+                                         lp]),
+            "oracle_pt_run_gauss": (None, [dp, dp, C.c_long, C.c_long, dp, dp, dp, dp, C.c_double,
+                                           C.c_uint64, C.c_uint64, C.c_long, dp, dp, lp, dp]),
+            "oracle_pt_gauss_loglike": (None, [dp, C.c_long, dp, dp, dp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -277,3 +290,76 @@ def het_loglike(theta, ref: dict) -> np.ndarray:
 
 def threads() -> int:
     return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+# ---- parallel-tempered ensemble sampler (Sec. III) ------------------------------
+PT_KINDS = ("stretch", "sky_all", "sky_lon", "sky_lat")
+
+
+def philox(ctr, key) -> np.ndarray:
+    """Philox4x32-10 of counters ctr (n, 4) uint32 under key (2,) uint32: (n, 4) uint32."""
+    ctr = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32).reshape(-1, 4))
+    key = np.ascontiguousarray(np.asarray(key, dtype=np.uint32).reshape(2))
+    out = np.empty_like(ctr)
+    u32p = C.POINTER(C.c_uint32)
+    for i in range(ctr.shape[0]):
+        lib().oracle_philox4x32_10(ctr[i].ctypes.data_as(u32p), key.ctypes.data_as(u32p),
+                                   out[i].ctypes.data_as(u32p))
+    return out
+
+
+def pt_theta(x) -> np.ndarray:
+    """theta (11, n) of sampler coordinates x (11, n)."""
+    x = np.ascontiguousarray(_f64(x))
+    th = np.empty_like(x)
+    lib().oracle_pt_theta(_d(x), x.shape[1], _d(th))
+    return th
+
+
+def pt_choice(seed, step, half, item, W, probs, a=2.0) -> dict:
+    out = np.empty(5)
+    lib().oracle_pt_choice(seed, step, half, item, W, _d(_f64(probs)), a, _d(out))
+    return dict(kind=int(out[0]), j=int(out[1]), z=float(out[2]), n=int(out[3]), m=int(out[4]))
+
+
+def pt_sky(x, n, m) -> np.ndarray:
+    v = _f64(x).copy()
+    lib().oracle_pt_sky(_d(v), int(n), int(m))
+    return v
+
+
+def _pt_common(x, out, betas, lo, hi, probs):
+    x = np.ascontiguousarray(_f64(x)).copy()
+    out = np.ascontiguousarray(_f64(out)).copy()
+    return x, out, _f64(betas), _f64(lo), _f64(hi), _f64(probs)
+
+
+def pt_run_het(x, out, T, W, betas, lo, hi, probs, a, seed, step0, n_iter, ref: dict):
+    """n_iter sampler iterations with the heterodyned likelihood; returns (x, out, counters)."""
+    x, out, betas, lo, hi, probs = _pt_common(x, out, betas, lo, hi, probs)
+    cnt = np.zeros(10 * T, dtype=np.int64)
+    g = ref["grid"]
+    lib().oracle_pt_run_het(_d(x), _d(out), T, W, _d(betas), _d(lo), _d(hi), _d(probs), a,
+                            seed, step0, n_iter, ref["E"], _l(ref["edges"]), g["f0"], g["df"],
+                            g["t_obs"], _d(_f64(ref["summary"]).ravel()),
+                            _d(_c128(ref["h0e"]).view(np.float64)), ref["dd"], _l(cnt))
+    return x, out, cnt
+
+
+def pt_run_gauss(x, out, T, W, betas, lo, hi, probs, a, seed, step0, n_iter, mu, sigma,
+                 trace=False):
+    """The sampler on a diagonal Gaussian target in x; returns (x, out, counters, trace)."""
+    x, out, betas, lo, hi, probs = _pt_common(x, out, betas, lo, hi, probs)
+    cnt = np.zeros(10 * T, dtype=np.int64)
+    tr = np.empty((n_iter, 11, T * W)) if trace else None
+    lib().oracle_pt_run_gauss(_d(x), _d(out), T, W, _d(betas), _d(lo), _d(hi), _d(probs), a,
+                              seed, step0, n_iter, _d(_f64(mu)), _d(_f64(sigma)), _l(cnt),
+                              _d(tr) if trace else None)
+    return x, out, cnt, tr
+
+
+def pt_gauss_loglike(x, mu, sigma) -> np.ndarray:
+    x = np.ascontiguousarray(_f64(x))
+    out = np.empty(3 * x.shape[1])
+    lib().oracle_pt_gauss_loglike(_d(x), x.shape[1], _d(_f64(mu)), _d(_f64(sigma)), _d(out))
+    return out.reshape(3, -1)
