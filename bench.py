@@ -341,6 +341,9 @@ def run_ours(args) -> dict | None:
     d6 = d64.cpu().numpy()
     dscale = 0.5 * (src.data.dd + np.abs(d6[2]) + 2 * np.abs(d6[1]))
 
+    # ---- device parallel-tempered sampler on the same source (Sec. III) ----
+    sampler = run_sampler(M, WL, g, src, ref, stream, value / ws) if args.only == "all" else None
+
     # ---- uneven multi-source batch: autotuned, one launch, CUDA-graph replay ----
     uneven = run_uneven(M, WL, stream) if args.only == "all" else None
     serving = run_serving(M, WL, cfg=None) if args.only == "all" else None
@@ -392,6 +395,7 @@ def run_ours(args) -> dict | None:
             "fused_mixed_vs_fp64_abs_max": float(np.abs(dm[0] - d6[0]).max()),
         },
         "direct_hbm_gbs": stored_gbs,
+        "sampler": sampler,
         "uneven": uneven,
         "serving": serving,
         "roofline": {"bound": "alu", "pipe": "fp32 (FMA pipe)", "achieved": achieved, "peak": fma_peak,
@@ -412,6 +416,44 @@ def run_ours(args) -> dict | None:
     if ws > 1:
         torch.distributed.barrier()
     return res if rank == 0 else None
+
+
+def run_sampler(M, WL, g, src, ref, stream, het_rate: float, iters: int = 20) -> dict:
+    """Parallel-tempered ensemble sampler iterations on the device (Sec. III) with the
+    heterodyned likelihood of the benchmark's source: 8 temperatures x 2048 walkers, 256 bins,
+    1-yr grid, mixed precision; one iteration = both half-step moves (2 x 8192 likelihood
+    evaluations), the acceptances and the temperature swaps, replayed from a CUDA graph."""
+    import torch
+    T, W = W_TEMPS, N_WALKERS // W_TEMPS
+    lo, hi = I.prior_box(g["t_obs"])
+    th = src.theta_inj
+    x0 = th.copy()
+    x0[0], x0[6], x0[8] = math.log(th[0]), math.cos(th[6]), math.sin(th[8])
+    scale = np.abs(x0) * 1e-6 + 1e-5 * (hi - lo) * (np.abs(x0) < 1e-3)
+    x = WL.to_dev(I.draw_pt_ensemble(I.rng(2, 300), x0, T, W, scale, lo, hi))
+    betas = I.pt_betas(T, 100.0)
+    res = {}
+    for name, cfg in (("default", None), ("threads_per_walker_16", M.het_config(16, 128, 0))):
+        pt = M.PTSampler(x, betas, lo, hi, ref=ref, walkers=W, seed=1, precision="mixed", cfg=cfg)
+        pt.run(3)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pt.run(iters)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / iters
+        cnt, step = pt.counters()
+        pt.close()
+        prop, acc = cnt[:4 * T].reshape(T, 4), cnt[4 * T:8 * T].reshape(T, 4)
+        res[name] = {"ms_per_iteration": ms, "iterations_per_s": 1e3 / ms,
+                     "lnL_evals_per_s": T * W / (ms * 1e-3),
+                     "overhead_vs_het_only": 1.0 - (T * W / (ms * 1e-3)) / het_rate,
+                     "acceptance_by_temperature": (acc.sum(1) / np.maximum(prop.sum(1), 1)).round(4).tolist(),
+                     "swap_acceptance_by_level": (cnt[8 * T + 1:9 * T] / np.maximum(cnt[9 * T + 1:10 * T], 1)).round(4).tolist(),
+                     "iterations_run": step}
+    return {"temperatures": T, "walkers_per_temperature": W, "bins": ref.bins,
+            "launches_per_iteration": 8, "graph": True, **res}
 
 
 def run_uneven(M, WL, stream, reps: int = 20) -> dict:

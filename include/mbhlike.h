@@ -292,6 +292,75 @@ MBH_API mbh_status mbh_server_reset_stats(mbh_server* server);
 /* Cancels queued requests, waits for batches in flight, stops the worker. */
 MBH_API void mbh_server_free(mbh_server* server);
 
+/* ---- Parallel-tempered ensemble sampler iteration (Sec. III) -------------
+ * The sampler shared by the paper's three pipeline modules, run on the device:
+ * T temperatures (inverse temperatures beta_t, target L^beta_t x prior) of W
+ * walkers.  Walkers move in x = (ln M_T, q, a1, a2, D_L, phi_ref, cos iota,
+ * lambda, sin beta, psi, t_ref), whose prior (Table I) is uniform on the box
+ * [lo, hi].  One iteration: the two halves of every temperature move in turn,
+ * each against the other half (stretch move, Goodman & Weare 2010, with
+ * probability probs[0]; otherwise a sky-mode hop of Sec. III: all eight modes
+ * (probs[1]), a longitudinal change (probs[2]) or the latitudinal flip
+ * (probs[3])), every proposal batch is scored with het_loglike_batch (ref) or
+ * direct_loglike_batch (data), tempered Metropolis acceptance; then swaps
+ * between adjacent temperatures, hottest pair first, walkers paired by a random
+ * permutation (parallel tempering, Vousden, Farr & Mandel 2016).  Random numbers
+ * are Philox4x32-10 (Salmon et al. 2011) with key = seed and counter = (item,
+ * purpose, iteration): a run is reproducible and independent of launch
+ * configuration, and positions are bit-exact functions of (seed, start state)
+ * for a given likelihood.  The iteration counter lives on the device, so
+ * iterations replay from a CUDA graph without host work.
+ *
+ * Ownership: the handle owns the ensemble state (device), the scratch and a
+ * captured graph; it keeps pointers to ref/data, which must outlive it (or be
+ * replaced with mbh_pt_set_ref first).  Counters (int64, 10 T): [0, 4T)
+ * proposals per (temperature, kind), [4T, 8T) accepted per (temperature, kind),
+ * kinds in the order of probs; [8T, 9T) accepted swaps per level i (pair i,
+ * i-1; entry 0 unused); [9T, 10T) proposed swaps per level.
+ * Errors: MBH_EINVAL for bad options (T not in [1, 64], W odd or not in
+ * [4, 8192], a <= 1, negative probabilities or a sum outside (0, 1], lo > hi,
+ * negative or non-finite betas, not exactly one of ref/data). */
+typedef struct mbh_pt mbh_pt;
+typedef struct {
+    int32_t ntemps;          /* T */
+    int32_t walkers;         /* W per temperature */
+    double a;                /* stretch scale (2 in Goodman & Weare) */
+    double probs[4];         /* stretch, all 8 sky modes, longitudinal, latitudinal */
+    double lo[11], hi[11];   /* prior box in x */
+    uint64_t seed;
+    mbh_precision precision;           /* of the likelihood */
+    mbh_het_config het_config;         /* threads_per_walker 0 = default */
+} mbh_pt_opts;
+
+/* x_dev: float64 [11][T W] start positions in x, slot t W + k = walker k of
+ * temperature t (inside the prior box: outside it, cos iota and sin beta are
+ * clamped to [-1, 1] for scoring); betas_host: [T].  Scores the start state
+ * and synchronises `stream` before returning. */
+MBH_API mbh_status mbh_pt_create(const mbh_pt_opts* opts, const mbh_ref* ref, const mbh_data* data,
+                                 const double* betas_host, const double* x_dev, void* stream,
+                                 mbh_pt** out);
+/* Queues n_iter iterations on `stream` (use_graph != 0: replays of one
+ * captured iteration). */
+MBH_API mbh_status mbh_pt_run(mbh_pt* pt, int64_t n_iter, int32_t use_graph, void* stream);
+/* Copies the state in slot order: x_dev [11][T W], out_dev [3][T W] (lnL,
+ * <d|h>, <h|h>); either may be NULL. */
+MBH_API mbh_status mbh_pt_state(const mbh_pt* pt, double* x_dev, double* out_dev, void* stream);
+/* Replaces the positions (slot order) and rescores them. */
+MBH_API mbh_status mbh_pt_set_state(mbh_pt* pt, const double* x_dev, void* stream);
+/* Reference refresh (Sec. III B): later iterations use `ref`; every walker is
+ * rescored against it. */
+MBH_API mbh_status mbh_pt_set_ref(mbh_pt* pt, const mbh_ref* ref, void* stream);
+/* New inverse temperatures (synchronises `stream`). */
+MBH_API mbh_status mbh_pt_set_betas(mbh_pt* pt, const double* betas_host, void* stream);
+/* Reads the counters and the iteration counter (synchronises `stream`). */
+MBH_API mbh_status mbh_pt_counters(const mbh_pt* pt, int64_t* counters_host, uint64_t* step_host,
+                                   void* stream);
+/* Walker of temperature `temp` with the largest lnL (lowest slot on ties):
+ * x_host [11], out_host [3] (synchronises `stream`). */
+MBH_API mbh_status mbh_pt_best(const mbh_pt* pt, int32_t temp, double* x_host, double* out_host,
+                               void* stream);
+MBH_API void mbh_pt_free(mbh_pt* pt);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,698 @@
+// Parallel-tempered ensemble sampler iteration on the device (Katz, arXiv:2111.01064, Sec. III,
+// the sampler shared by all pipeline modules): stretch moves (Goodman & Weare 2010) for most
+// proposals, sky-mode hops (the eight LISA-frame sky modes of Sec. III, three varieties),
+// tempered Metropolis acceptance against L^beta pi, and swaps between adjacent temperatures,
+// hottest pair first (Vousden, Farr & Mandel 2016).  The likelihood of every proposal batch is
+// the library's heterodyned (Sec. II B) or direct (Sec. II) likelihood.
+//
+// One iteration = 8 launches on the caller's stream, no host synchronisation, captured once in
+// a CUDA graph:
+//   pt_perm_kernel     random permutations of every swap level (state-independent; one block
+//                      per level, bitonic sort of 48-bit Philox keys in shared memory)
+//   for each half h:   pt_propose_kernel -> likelihood of the T*W/2 proposals -> pt_accept_kernel
+//   pt_swap_kernel     the swap levels in order, hottest first (one block; the two temperatures
+//                      of a level are held in shared memory), then the step counter advances.
+//
+// Layout: positions x[11][N] and (lnL, <d|h>, <h|h>) out[3][N] stay in physical columns; a map
+// slot -> column (slot = t W + k, walker k of temperature t) makes a swap an exchange of two
+// map entries instead of 2 x 14 doubles.  Walkers are read and written through the map.
+//
+// Random numbers: Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11), key = seed, counter =
+// (item, purpose, step low, step high), so every draw is fixed by (seed, step, purpose, item)
+// and independent of launch configuration.  The proposal arithmetic uses explicitly rounded
+// float64 operations (no contraction), so positions are reproducible bit for bit.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "mbh_internal.cuh"
+
+using namespace mbh;
+
+namespace {
+
+constexpr int kPar = 11;
+constexpr int kMaxTemps = 64;
+constexpr int kMaxWalkers = 8192;   // per temperature (16-bit walker index in the swap keys)
+constexpr int kThreads = 256;
+constexpr int kSortThreads = 1024;
+
+enum { K_STRETCH = 0, K_SKY_ALL = 1, K_SKY_LON = 2, K_SKY_LAT = 3 };
+enum : uint32_t { P_PROPOSE = 0x10, P_ACCEPT = 0x20, P_SWAP_KEY = 0x100, P_SWAP_ACC = 0x200 };
+
+constexpr double kPi = 3.141592653589793;
+constexpr double kHalfPi = 1.5707963267948966;
+constexpr double kTwoPi = 6.283185307179586;
+
+struct PtArgs {
+    double* x;              // [11][N] positions, physical columns
+    double* out;            // [3][N] lnL, <d|h>, <h|h>
+    int32_t* map;           // [N] slot -> column
+    double* y;              // [11][M] proposals of the moving half
+    double* theta;          // [11][N] likelihood input (first M columns during a half step)
+    double* out_p;          // [3][M] likelihood of the proposals
+    double* fac;            // [M] log acceptance factor (d-1) ln z of stretch moves
+    int32_t* flag;          // [M] inside-prior bit | kind << 1
+    int32_t* perm;          // [T][W] hot partner of cold walker k at level i
+    const double* betas;    // [T]
+    unsigned long long* counters;   // [10 T]
+    unsigned long long* step;       // iteration counter
+    double lo[kPar], hi[kPar];
+    double c1, c2, c3;      // cumulative proposal probabilities
+    double a, am1;          // stretch scale and a - 1
+    uint64_t seed;
+    int32_t T, W;
+};
+
+// ---- Philox4x32-10 -------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                        uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
+__device__ __forceinline__ uint4 draw(uint64_t seed, uint32_t item, uint32_t purpose, uint64_t step)
+{
+    return philox(item, purpose, (uint32_t)step, (uint32_t)(step >> 32), (uint32_t)seed,
+                  (uint32_t)(seed >> 32));
+}
+
+// 53-bit uniform in [0, 1); every operation is exact
+__device__ __forceinline__ double u53(uint32_t a, uint32_t b)
+{
+    return ((double)(a >> 5) * 67108864.0 + (double)(b >> 6)) * (1.0 / 9007199254740992.0);
+}
+
+// v mod P for v in [-2P, 4P) (a coordinate of the prior box plus at most 3 quarter turns);
+// the bounded loops leave values outside that range outside [0, P), i.e. outside the prior.
+__device__ __forceinline__ double reduce_period(double v, double P)
+{
+    for (int i = 0; i < 4 && v >= P; ++i) v = __dsub_rn(v, P);
+    for (int i = 0; i < 2 && v < 0.0; ++i) v = __dadd_rn(v, P);
+    return v;
+}
+
+__device__ __forceinline__ void theta_of_x(const double (&x)[kPar], double (&th)[kPar])
+{
+#pragma unroll
+    for (int p = 0; p < kPar; ++p) th[p] = x[p];
+    th[0] = exp(fmin(x[0], 700.0));
+    th[6] = acos(fmin(fmax(x[6], -1.0), 1.0));   // clamps act only outside the prior box
+    th[8] = asin(fmin(fmax(x[8], -1.0), 1.0));
+}
+
+// ---- kernels -------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) pt_propose_kernel(const PtArgs A, int half)
+{
+    const int32_t Wh = A.W / 2, M = A.T * Wh, N = A.T * A.W;
+    const int32_t item = blockIdx.x * blockDim.x + threadIdx.x;
+    if (item >= M) return;
+    const uint64_t step = *A.step;
+    const int32_t t = item / Wh, kp = item - t * Wh;
+    const int32_t col = A.map[t * A.W + half * Wh + kp];
+    const uint4 r = draw(A.seed, (uint32_t)item, P_PROPOSE + (uint32_t)half, step);
+    const double u = (double)r.x * (1.0 / 4294967296.0);
+    const int kind = u < A.c1 ? K_STRETCH : u < A.c2 ? K_SKY_ALL : u < A.c3 ? K_SKY_LON : K_SKY_LAT;
+    double v[kPar], xk[kPar];
+#pragma unroll
+    for (int p = 0; p < kPar; ++p) xk[p] = v[p] = A.x[(int64_t)p * N + col];
+    double fac = 0.0;
+    if (kind == K_STRETCH) {
+        const int32_t j = (1 - half) * Wh + (int32_t)(((uint64_t)r.y * (uint64_t)Wh) >> 32);
+        const int32_t colj = A.map[t * A.W + j];
+        const double s = __dadd_rn(__dmul_rn(A.am1, u53(r.z, r.w)), 1.0);
+        const double z = __ddiv_rn(__dmul_rn(s, s), A.a);
+#pragma unroll
+        for (int p = 0; p < kPar; ++p) {
+            const double xj = A.x[(int64_t)p * N + colj];
+            v[p] = __dadd_rn(xj, __dmul_rn(z, __dsub_rn(v[p], xj)));
+        }
+        fac = (double)(kPar - 1) * log(z);
+    } else {
+        int n = 0, m = 0;
+        if (kind == K_SKY_ALL) {
+            n = (int)(r.z >> 30);
+            m = (int)(r.w >> 31);
+        } else if (kind == K_SKY_LON) {
+            n = 1 + (int)(((uint64_t)r.z * 3u) >> 32);
+        } else {
+            m = 1;
+        }
+        const double shift = __dmul_rn((double)n, kHalfPi);
+        v[7] = reduce_period(__dadd_rn(v[7], shift), kTwoPi);
+        v[9] = reduce_period(__dadd_rn(v[9], shift), kPi);
+        if (m) {
+            v[8] = -v[8];
+            v[6] = -v[6];
+            v[9] = __dsub_rn(kPi, v[9]);
+        }
+    }
+    bool ok = true;
+#pragma unroll
+    for (int p = 0; p < kPar; ++p) ok = ok && (v[p] >= A.lo[p] && v[p] <= A.hi[p]);
+    double th[kPar];
+    theta_of_x(ok ? v : xk, th);   // outside the prior: score the current point (rejected anyway)
+#pragma unroll
+    for (int p = 0; p < kPar; ++p) {
+        A.y[(int64_t)p * M + item] = v[p];
+        A.theta[(int64_t)p * M + item] = th[p];
+    }
+    A.fac[item] = fac;
+    A.flag[item] = (ok ? 1 : 0) | (kind << 1);
+}
+
+__global__ void __launch_bounds__(kThreads) pt_accept_kernel(const PtArgs A, int half)
+{
+    __shared__ unsigned int cnt[kMaxTemps * 8];
+    for (int i = threadIdx.x; i < A.T * 8; i += blockDim.x) cnt[i] = 0;
+    __syncthreads();
+    const int32_t Wh = A.W / 2, M = A.T * Wh, N = A.T * A.W;
+    const int32_t item = blockIdx.x * blockDim.x + threadIdx.x;
+    if (item < M) {
+        const uint64_t step = *A.step;
+        const int32_t t = item / Wh, kp = item - t * Wh;
+        const int32_t col = A.map[t * A.W + half * Wh + kp];
+        const uint4 r = draw(A.seed, (uint32_t)item, P_ACCEPT + (uint32_t)half, step);
+        const double lnu = log(u53(r.x, r.y));
+        const double dl = __dsub_rn(A.out_p[item], A.out[col]);
+        const double la = __dadd_rn(A.fac[item], __dmul_rn(A.betas[t], dl));
+        const int32_t f = A.flag[item];
+        const int kind = f >> 1;
+        const bool acc = (f & 1) && lnu < la;
+        atomicAdd(&cnt[t * 8 + kind], 1u);
+        if (acc) {
+            atomicAdd(&cnt[t * 8 + 4 + kind], 1u);
+#pragma unroll
+            for (int p = 0; p < kPar; ++p) A.x[(int64_t)p * N + col] = A.y[(int64_t)p * M + item];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) A.out[(int64_t)q * N + col] = A.out_p[(int64_t)q * M + item];
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < A.T * 8; i += blockDim.x) {
+        const unsigned int c = cnt[i];
+        if (c == 0) continue;
+        const int t = i / 8, j = i % 8;
+        // counters: [0, 4T) proposals per (t, kind), [4T, 8T) accepted per (t, kind)
+        const int dst = j < 4 ? t * 4 + j : 4 * A.T + t * 4 + (j - 4);
+        atomicAdd(&A.counters[dst], (unsigned long long)c);
+    }
+}
+
+// One block per swap level i = blockIdx.x + 1: sort the keys (48 random bits, then the walker
+// index) of the hot temperature's walkers; perm[i][k] = hot partner of cold walker k.
+__global__ void __launch_bounds__(kSortThreads) pt_perm_kernel(const PtArgs A, int Wp)
+{
+    extern __shared__ unsigned long long keys[];
+    const int i = blockIdx.x + 1;
+    const uint64_t step = *A.step;
+    for (int k = threadIdx.x; k < Wp; k += blockDim.x) {
+        if (k < A.W) {
+            const uint4 r = draw(A.seed, (uint32_t)k, P_SWAP_KEY + (uint32_t)i, step);
+            keys[k] = ((unsigned long long)r.x << 32) | (unsigned long long)(r.y & 0xFFFF0000u) |
+                      (unsigned long long)k;
+        } else {
+            keys[k] = ~0ull;
+        }
+    }
+    __syncthreads();
+    for (int size = 2; size <= Wp; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int q = threadIdx.x; q < Wp / 2; q += blockDim.x) {
+                const int lo = 2 * q - (q & (stride - 1)), hi = lo + stride;
+                const bool up = (lo & size) == 0;
+                const unsigned long long a = keys[lo], b = keys[hi];
+                if ((a > b) == up) {
+                    keys[lo] = b;
+                    keys[hi] = a;
+                }
+            }
+            __syncthreads();
+        }
+    for (int k = threadIdx.x; k < A.W; k += blockDim.x)
+        A.perm[(int64_t)i * A.W + k] = (int32_t)(keys[k] & 0xFFFFull);
+}
+
+// Swap levels in order, hottest first; the hot and cold temperatures of a level are held in
+// shared memory (lnL and map entries).  Thread 0 advances the step counter at the end.
+__global__ void __launch_bounds__(kSortThreads) pt_swap_kernel(const PtArgs A)
+{
+    extern __shared__ double sm[];
+    const int W = A.W, T = A.T;
+    double* lnl = sm;                                   // [2][W]
+    int32_t* mp = reinterpret_cast<int32_t*>(sm + 2 * W);   // [2][W]
+    __shared__ unsigned int acc_level;
+    const uint64_t step = *A.step;
+    if (T > 1) {
+        int hot = 0;
+        for (int k = threadIdx.x; k < W; k += blockDim.x) {
+            const int32_t c = A.map[(T - 1) * W + k];
+            mp[k] = c;
+            lnl[k] = A.out[c];
+        }
+        for (int i = T - 1; i >= 1; --i) {
+            const int cold = hot ^ 1;
+            if (threadIdx.x == 0) acc_level = 0;
+            for (int k = threadIdx.x; k < W; k += blockDim.x) {
+                const int32_t c = A.map[(i - 1) * W + k];
+                mp[cold * W + k] = c;
+                lnl[cold * W + k] = A.out[c];
+            }
+            __syncthreads();
+            const double db = __dsub_rn(A.betas[i - 1], A.betas[i]);
+            unsigned int mine = 0;
+            for (int k = threadIdx.x; k < W; k += blockDim.x) {
+                const int h = A.perm[(int64_t)i * W + k];
+                const uint4 r = draw(A.seed, (uint32_t)k, P_SWAP_ACC + (uint32_t)i, step);
+                const double lnu = log(u53(r.x, r.y));
+                const double la = __dmul_rn(db, __dsub_rn(lnl[hot * W + h], lnl[cold * W + k]));
+                if (lnu < la) {
+                    const double l = lnl[hot * W + h];
+                    lnl[hot * W + h] = lnl[cold * W + k];
+                    lnl[cold * W + k] = l;
+                    const int32_t c = mp[hot * W + h];
+                    mp[hot * W + h] = mp[cold * W + k];
+                    mp[cold * W + k] = c;
+                    ++mine;
+                }
+            }
+            if (mine) atomicAdd(&acc_level, mine);
+            __syncthreads();
+            for (int k = threadIdx.x; k < W; k += blockDim.x) A.map[i * W + k] = mp[hot * W + k];
+            if (threadIdx.x == 0) {
+                A.counters[8 * T + i] += acc_level;
+                A.counters[9 * T + i] += (unsigned long long)W;
+            }
+            __syncthreads();
+            hot = cold;
+        }
+        for (int k = threadIdx.x; k < W; k += blockDim.x) A.map[k] = mp[hot * W + k];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *A.step = step + 1;
+}
+
+// theta(x) of every physical column (rescoring)
+__global__ void pt_theta_kernel(const double* __restrict__ x, int64_t N, double* __restrict__ th)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    double v[kPar], t[kPar];
+#pragma unroll
+    for (int p = 0; p < kPar; ++p) v[p] = x[p * N + c];
+    theta_of_x(v, t);
+#pragma unroll
+    for (int p = 0; p < kPar; ++p) th[p * N + c] = t[p];
+}
+
+// slot-ordered copy of the state; or, with scatter != 0, load positions in slot order
+__global__ void pt_gather_kernel(const PtArgs A, const double* __restrict__ xs, double* __restrict__ xo,
+                                 double* __restrict__ oo, int scatter)
+{
+    const int64_t N = (int64_t)A.T * A.W;
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    if (scatter) {
+        A.map[s] = (int32_t)s;
+#pragma unroll
+        for (int p = 0; p < kPar; ++p) A.x[p * N + s] = xs[p * N + s];
+        return;
+    }
+    const int32_t c = A.map[s];
+    if (xo)
+#pragma unroll
+        for (int p = 0; p < kPar; ++p) xo[p * N + s] = A.x[p * N + c];
+    if (oo)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) oo[q * N + s] = A.out[q * N + c];
+}
+
+// best (largest lnL, lowest slot on ties) walker of temperature t -> res[14] (x, out)
+__global__ void __launch_bounds__(kSortThreads) pt_best_kernel(const PtArgs A, int t, double* res)
+{
+    __shared__ double bv[32];
+    __shared__ int bs[32];
+    const int64_t N = (int64_t)A.T * A.W;
+    double best = -INFINITY;
+    int slot = -1;
+    for (int k = threadIdx.x; k < A.W; k += blockDim.x) {
+        const double v = A.out[A.map[t * A.W + k]];
+        if (slot < 0 || v > best) {
+            best = v;
+            slot = k;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_down_sync(0xffffffffu, best, o);
+        const int os = __shfl_down_sync(0xffffffffu, slot, o);
+        if (os >= 0 && (slot < 0 || ov > best || (ov == best && os < slot))) {
+            best = ov;
+            slot = os;
+        }
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (lane == 0) {
+        bv[warp] = best;
+        bs[warp] = slot;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < nw; ++w)
+            if (bs[w] >= 0 && (slot < 0 || bv[w] > best || (bv[w] == best && bs[w] < slot))) {
+                best = bv[w];
+                slot = bs[w];
+            }
+        const int32_t c = A.map[t * A.W + (slot < 0 ? 0 : slot)];
+        for (int p = 0; p < kPar; ++p) res[p] = A.x[p * N + c];
+        for (int q = 0; q < 3; ++q) res[kPar + q] = A.out[q * N + c];
+    }
+}
+
+}  // namespace
+
+struct mbh_pt {
+    int device = -1;
+    PtArgs A{};
+    mbh_precision precision = MBH_MIXED;
+    const mbh_ref* ref = nullptr;
+    const mbh_data* data = nullptr;
+    mbh_het_config cfg{8, 128, 0};
+    int Wp = 0;
+    double* res = nullptr;   // device [14] for mbh_pt_best
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;
+};
+
+namespace {
+
+void free_pt(mbh_pt* P)
+{
+    if (P->exec) cudaGraphExecDestroy(P->exec);
+    if (P->graph) cudaGraphDestroy(P->graph);
+    PtArgs& A = P->A;
+    void* bufs[] = {A.x, A.out, A.map, A.y, A.theta, A.out_p, A.fac, A.flag, A.perm,
+                    (void*)A.betas, A.counters, A.step, P->res};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    delete P;
+}
+
+// likelihood of the first n columns of A.theta into dst [3][n]
+mbh_status likelihood(mbh_pt* P, int64_t n, double* dst, cudaStream_t st)
+{
+    if (P->ref) {
+        const int64_t off[2] = {0, n};
+        return het_loglike_batch_cfg(&P->ref, off, 1, P->A.theta, P->precision, &P->cfg, dst, st);
+    }
+    return direct_loglike_batch(P->data, P->A.theta, n, P->precision, dst, st);
+}
+
+mbh_status rescore(mbh_pt* P, cudaStream_t st)
+{
+    const int64_t N = (int64_t)P->A.T * P->A.W;
+    pt_theta_kernel<<<(unsigned)((N + kThreads - 1) / kThreads), kThreads, 0, st>>>(P->A.x, N, P->A.theta);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "pt_theta_kernel");
+    return likelihood(P, N, P->A.out, st);
+}
+
+mbh_status queue_iteration(mbh_pt* P, cudaStream_t st)
+{
+    const PtArgs& A = P->A;
+    const int32_t M = A.T * (A.W / 2);
+    const unsigned gM = (unsigned)((M + kThreads - 1) / kThreads);
+    cudaError_t e = cudaSuccess;
+    if (A.T > 1) {
+        pt_perm_kernel<<<A.T - 1, kSortThreads, sizeof(unsigned long long) * P->Wp, st>>>(A, P->Wp);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "pt_perm_kernel");
+    }
+    for (int half = 0; half < 2; ++half) {
+        pt_propose_kernel<<<gM, kThreads, 0, st>>>(A, half);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "pt_propose_kernel");
+        if (mbh_status s = likelihood(P, M, A.out_p, st)) return s;
+        pt_accept_kernel<<<gM, kThreads, 0, st>>>(A, half);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "pt_accept_kernel");
+    }
+    pt_swap_kernel<<<1, kSortThreads, (sizeof(double) + sizeof(int32_t)) * 2 * A.W, st>>>(A);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "pt_swap_kernel");
+    return MBH_OK;
+}
+
+void drop_graph(mbh_pt* P)
+{
+    if (P->exec) cudaGraphExecDestroy(P->exec);
+    if (P->graph) cudaGraphDestroy(P->graph);
+    P->exec = nullptr;
+    P->graph = nullptr;
+}
+
+mbh_status build_graph(mbh_pt* P)
+{
+    cudaStream_t cs = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "graph stream");
+    mbh_status status = MBH_OK;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        status = queue_iteration(P, cs);
+        cudaGraph_t g = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+        if (status == MBH_OK && e2 != cudaSuccess) status = cuda_fail(e2, "graph capture");
+        if (status == MBH_OK) {
+            e2 = cudaGraphInstantiate(&P->exec, g, 0);
+            if (e2 != cudaSuccess) status = cuda_fail(e2, "graph instantiate");
+            P->graph = g;
+        } else if (g) {
+            cudaGraphDestroy(g);
+        }
+    } else {
+        status = cuda_fail(e, "begin capture");
+    }
+    cudaStreamDestroy(cs);
+    if (status != MBH_OK) drop_graph(P);
+    return status;
+}
+
+}  // namespace
+
+extern "C" mbh_status mbh_pt_create(const mbh_pt_opts* o, const mbh_ref* ref, const mbh_data* data,
+                                    const double* betas_host, const double* x_dev, void* stream,
+                                    mbh_pt** out)
+{
+    if (!out) return fail(MBH_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!o || !betas_host || !x_dev) return fail(MBH_EINVAL, "NULL opts/betas/x");
+    if ((ref == nullptr) == (data == nullptr)) return fail(MBH_EINVAL, "give exactly one of ref and data");
+    if (o->ntemps < 1 || o->ntemps > kMaxTemps) return fail(MBH_EINVAL, "ntemps %d not in [1, %d]", o->ntemps, kMaxTemps);
+    if (o->walkers < 4 || o->walkers > kMaxWalkers || (o->walkers & 1))
+        return fail(MBH_EINVAL, "walkers %d: even, in [4, %d]", o->walkers, kMaxWalkers);
+    if (!(o->a > 1.0)) return fail(MBH_EINVAL, "stretch scale a must be > 1");
+    double csum = 0.0;
+    for (int i = 0; i < 4; ++i) {
+        if (!(o->probs[i] >= 0.0)) return fail(MBH_EINVAL, "negative proposal probability");
+        csum += o->probs[i];
+    }
+    if (!(csum > 0.0 && csum <= 1.0 + 1e-12)) return fail(MBH_EINVAL, "proposal probabilities must sum to (0, 1]");
+    for (int p = 0; p < kPar; ++p)
+        if (!(o->lo[p] <= o->hi[p])) return fail(MBH_EINVAL, "prior box: lo[%d] > hi[%d]", p, p);
+    for (int t = 0; t < o->ntemps; ++t)
+        if (!(betas_host[t] >= 0.0) || !std::isfinite(betas_host[t])) return fail(MBH_EINVAL, "betas must be finite and >= 0");
+    if (o->precision != MBH_FP64 && o->precision != MBH_MIXED) return fail(MBH_EINVAL, "unknown precision");
+    if (mbh_status s = check_device()) return s;
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (ref && ref->device != dev) return fail(MBH_EINVAL, "ref lives on another device");
+    if (data && data->device != dev) return fail(MBH_EINVAL, "data lives on another device");
+
+    mbh_pt* P = new (std::nothrow) mbh_pt;
+    if (!P) return fail(MBH_ENOMEM, "host allocation");
+    P->device = dev;
+    P->ref = ref;
+    P->data = data;
+    P->precision = o->precision;
+    if (o->het_config.threads_per_walker) P->cfg = o->het_config;
+    PtArgs& A = P->A;
+    A.T = o->ntemps;
+    A.W = o->walkers;
+    A.seed = o->seed;
+    A.a = o->a;
+    A.am1 = o->a - 1.0;
+    A.c1 = o->probs[0];
+    A.c2 = A.c1 + o->probs[1];
+    A.c3 = A.c2 + o->probs[2];
+    std::memcpy(A.lo, o->lo, sizeof A.lo);
+    std::memcpy(A.hi, o->hi, sizeof A.hi);
+    P->Wp = 1;
+    while (P->Wp < A.W) P->Wp <<= 1;
+    const int64_t N = (int64_t)A.T * A.W, M = N / 2;
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](void** p, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+    };
+    alloc((void**)&A.x, sizeof(double) * kPar * N);
+    alloc((void**)&A.out, sizeof(double) * 3 * N);
+    alloc((void**)&A.map, sizeof(int32_t) * N);
+    alloc((void**)&A.y, sizeof(double) * kPar * M);
+    alloc((void**)&A.theta, sizeof(double) * kPar * N);
+    alloc((void**)&A.out_p, sizeof(double) * 3 * M);
+    alloc((void**)&A.fac, sizeof(double) * M);
+    alloc((void**)&A.flag, sizeof(int32_t) * M);
+    alloc((void**)&A.perm, sizeof(int32_t) * N);
+    alloc((void**)&A.betas, sizeof(double) * A.T);
+    alloc((void**)&A.counters, sizeof(unsigned long long) * 10 * A.T);
+    alloc((void**)&A.step, sizeof(unsigned long long));
+    alloc((void**)&P->res, sizeof(double) * 14);
+    if (e != cudaSuccess) {
+        free_pt(P);
+        return e == cudaErrorMemoryAllocation ? fail(MBH_ENOMEM, "sampler buffers") : cuda_fail(e, "sampler buffers");
+    }
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(pt_perm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(unsigned long long) * kMaxWalkers));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(pt_swap_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)((sizeof(double) + sizeof(int32_t)) * 2 * kMaxWalkers));
+    cudaStream_t st = (cudaStream_t)stream;
+    const unsigned long long zero = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync((void*)A.betas, betas_host, sizeof(double) * A.T, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(A.counters, 0, sizeof(unsigned long long) * 10 * A.T, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(A.step, &zero, sizeof zero, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(A.perm, 0, sizeof(int32_t) * N, st);
+    if (e != cudaSuccess) {
+        free_pt(P);
+        return cuda_fail(e, "sampler setup");
+    }
+    pt_gather_kernel<<<(unsigned)((N + kThreads - 1) / kThreads), kThreads, 0, st>>>(A, x_dev, nullptr, nullptr, 1);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        free_pt(P);
+        return cuda_fail(e, "pt_gather_kernel");
+    }
+    if (mbh_status s = rescore(P, st)) {
+        free_pt(P);
+        return s;
+    }
+    // the host-to-device copies above read host memory that the caller may release on return
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        free_pt(P);
+        return cuda_fail(e, "sampler setup");
+    }
+    *out = P;
+    return MBH_OK;
+}
+
+extern "C" mbh_status mbh_pt_run(mbh_pt* P, int64_t n_iter, int32_t use_graph, void* stream)
+{
+    if (!P) return fail(MBH_EINVAL, "sampler is NULL");
+    if (n_iter < 0) return fail(MBH_EINVAL, "n_iter < 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (use_graph && !P->exec)
+        if (mbh_status s = build_graph(P)) return s;
+    for (int64_t i = 0; i < n_iter; ++i) {
+        if (use_graph) {
+            cudaError_t e = cudaGraphLaunch(P->exec, st);
+            if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+        } else if (mbh_status s = queue_iteration(P, st)) {
+            return s;
+        }
+    }
+    return MBH_OK;
+}
+
+extern "C" mbh_status mbh_pt_state(const mbh_pt* P, double* x_dev, double* out_dev, void* stream)
+{
+    if (!P) return fail(MBH_EINVAL, "sampler is NULL");
+    const int64_t N = (int64_t)P->A.T * P->A.W;
+    pt_gather_kernel<<<(unsigned)((N + kThreads - 1) / kThreads), kThreads, 0, (cudaStream_t)stream>>>(
+        P->A, nullptr, x_dev, out_dev, 0);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MBH_OK : cuda_fail(e, "pt_gather_kernel");
+}
+
+extern "C" mbh_status mbh_pt_set_state(mbh_pt* P, const double* x_dev, void* stream)
+{
+    if (!P || !x_dev) return fail(MBH_EINVAL, "NULL sampler/x");
+    const int64_t N = (int64_t)P->A.T * P->A.W;
+    cudaStream_t st = (cudaStream_t)stream;
+    pt_gather_kernel<<<(unsigned)((N + kThreads - 1) / kThreads), kThreads, 0, st>>>(P->A, x_dev, nullptr, nullptr, 1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "pt_gather_kernel");
+    return rescore(P, st);
+}
+
+extern "C" mbh_status mbh_pt_set_ref(mbh_pt* P, const mbh_ref* ref, void* stream)
+{
+    if (!P || !ref) return fail(MBH_EINVAL, "NULL sampler/ref");
+    if (!P->ref) return fail(MBH_EINVAL, "sampler uses the direct likelihood");
+    if (ref->device != P->device) return fail(MBH_EINVAL, "ref lives on another device");
+    P->ref = ref;
+    drop_graph(P);   // the reference's tables are baked into the captured launches
+    return rescore(P, (cudaStream_t)stream);
+}
+
+extern "C" mbh_status mbh_pt_set_betas(mbh_pt* P, const double* betas_host, void* stream)
+{
+    if (!P || !betas_host) return fail(MBH_EINVAL, "NULL sampler/betas");
+    for (int t = 0; t < P->A.T; ++t)
+        if (!(betas_host[t] >= 0.0) || !std::isfinite(betas_host[t])) return fail(MBH_EINVAL, "betas must be finite and >= 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync((void*)P->A.betas, betas_host, sizeof(double) * P->A.T,
+                                    cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? MBH_OK : cuda_fail(e, "set betas");
+}
+
+extern "C" mbh_status mbh_pt_counters(const mbh_pt* P, int64_t* counters_host, uint64_t* step_host,
+                                      void* stream)
+{
+    if (!P) return fail(MBH_EINVAL, "sampler is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (counters_host)
+        e = cudaMemcpyAsync(counters_host, P->A.counters, sizeof(int64_t) * 10 * P->A.T,
+                            cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && step_host)
+        e = cudaMemcpyAsync(step_host, P->A.step, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? MBH_OK : cuda_fail(e, "read counters");
+}
+
+extern "C" mbh_status mbh_pt_best(const mbh_pt* P, int32_t temp, double* x_host, double* out_host,
+                                  void* stream)
+{
+    if (!P) return fail(MBH_EINVAL, "sampler is NULL");
+    if (temp < 0 || temp >= P->A.T) return fail(MBH_EINVAL, "temperature %d out of range", temp);
+    cudaStream_t st = (cudaStream_t)stream;
+    pt_best_kernel<<<1, kSortThreads, 0, st>>>(P->A, temp, P->res);
+    cudaError_t e = cudaGetLastError();
+    double r[14];
+    if (e == cudaSuccess) e = cudaMemcpyAsync(r, P->res, sizeof r, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "pt_best");
+    if (x_host) std::memcpy(x_host, r, sizeof(double) * kPar);
+    if (out_host) std::memcpy(out_host, r + kPar, sizeof(double) * 3);
+    return MBH_OK;
+}
+
+extern "C" void mbh_pt_free(mbh_pt* P)
+{
+    if (P) free_pt(P);
+}

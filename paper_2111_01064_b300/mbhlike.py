@@ -61,6 +61,13 @@ class ServerReport(C.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class PTOpts(C.Structure):
+    """mbh_pt_opts (see include/mbhlike.h)."""
+    _fields_ = [("ntemps", C.c_int32), ("walkers", C.c_int32), ("a", C.c_double),
+                ("probs", C.c_double * 4), ("lo", C.c_double * 11), ("hi", C.c_double * 11),
+                ("seed", C.c_uint64), ("precision", C.c_int), ("het_config", HetConfig)]
+
+
 def grid_struct(g: dict) -> Grid:
     return Grid(float(g["f0"]), float(g["df"]), int(g["n"]), float(g["t_obs"]))
 
@@ -115,6 +122,15 @@ def lib() -> C.CDLL:
         "mbh_server_reset_stats": (C.c_int, [vp]),
         "mbh_server_free": (None, [vp]),
         "mbh_selftest_math": (C.c_int, [i32, vp, vp, i64, vp, vp, vp]),
+        "mbh_pt_create": (C.c_int, [C.POINTER(PTOpts), vp, vp, dp, vp, vp, C.POINTER(vp)]),
+        "mbh_pt_run": (C.c_int, [vp, i64, i32, vp]),
+        "mbh_pt_state": (C.c_int, [vp, vp, vp, vp]),
+        "mbh_pt_set_state": (C.c_int, [vp, vp, vp]),
+        "mbh_pt_set_ref": (C.c_int, [vp, vp, vp]),
+        "mbh_pt_set_betas": (C.c_int, [vp, dp, vp]),
+        "mbh_pt_counters": (C.c_int, [vp, C.POINTER(C.c_int64), C.POINTER(C.c_uint64), vp]),
+        "mbh_pt_best": (C.c_int, [vp, i32, dp, dp, vp]),
+        "mbh_pt_free": (None, [vp]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(L, name)
@@ -484,3 +500,83 @@ def mbh_selftest_math(kind: int, x: torch.Tensor, y: torch.Tensor | None = None,
                                    _dev(o2, torch.float32, None, "o2") if o2 is not None else None,
                                    _stream(stream)))
     return (o1, o2) if kind == 0 else o1
+
+
+class PTSampler:
+    """mbh_pt: parallel-tempered ensemble sampler iterations on the device (Sec. III).
+
+    Exactly one of ``ref`` (heterodyned likelihood) and ``data`` (direct likelihood).
+    ``x``: CUDA float64 (11, T*W) start positions in the sampler coordinates
+    (ln M_T, q, a1, a2, D_L, phi_ref, cos iota, lambda, sin beta, psi, t_ref)."""
+
+    def __init__(self, x: torch.Tensor, betas, lo, hi, *, ref: Ref | None = None,
+                 data: Data | None = None, walkers: int, a: float = 2.0,
+                 probs=(0.85, 0.04, 0.03, 0.08), seed: int = 0, precision="mixed",
+                 cfg: HetConfig | None = None, stream=None):
+        _require_cuda()
+        betas = np.ascontiguousarray(np.asarray(betas, dtype=np.float64))
+        T = betas.size
+        o = PTOpts()
+        o.ntemps, o.walkers, o.a = T, int(walkers), float(a)
+        o.probs[:] = [float(p) for p in probs]
+        o.lo[:] = [float(v) for v in lo]
+        o.hi[:] = [float(v) for v in hi]
+        o.seed, o.precision = int(seed), _prec(precision)
+        o.het_config = cfg if cfg is not None else HetConfig(0, 0, 0)
+        self.T, self.W = T, int(walkers)
+        self.ref, self.data = ref, data   # keep them alive
+        h = vp()
+        _check(lib().mbh_pt_create(C.byref(o), ref.handle if ref else None,
+                                   data.handle if data else None,
+                                   betas.ctypes.data_as(dp),
+                                   _dev(x, torch.float64, (11, T * self.W), "x"), _stream(stream),
+                                   C.byref(h)))
+        self.handle = h
+
+    def run(self, n_iter: int, graph: bool = True, stream=None):
+        _check(lib().mbh_pt_run(self.handle, int(n_iter), 1 if graph else 0, _stream(stream)))
+
+    def state(self, stream=None) -> tuple[torch.Tensor, torch.Tensor]:
+        N = self.T * self.W
+        x = torch.empty((11, N), dtype=torch.float64, device="cuda")
+        out = torch.empty((3, N), dtype=torch.float64, device="cuda")
+        _check(lib().mbh_pt_state(self.handle, x.data_ptr(), out.data_ptr(), _stream(stream)))
+        return x, out
+
+    def set_state(self, x: torch.Tensor, stream=None):
+        _check(lib().mbh_pt_set_state(self.handle, _dev(x, torch.float64, (11, self.T * self.W), "x"),
+                                      _stream(stream)))
+
+    def set_ref(self, ref: Ref, stream=None):
+        _check(lib().mbh_pt_set_ref(self.handle, ref.handle, _stream(stream)))
+        self.ref = ref
+
+    def set_betas(self, betas, stream=None):
+        b = np.ascontiguousarray(np.asarray(betas, dtype=np.float64))
+        if b.size != self.T:
+            raise MBHError(1, f"need {self.T} betas")
+        _check(lib().mbh_pt_set_betas(self.handle, b.ctypes.data_as(dp), _stream(stream)))
+
+    def counters(self, stream=None) -> tuple[np.ndarray, int]:
+        c = np.zeros(10 * self.T, dtype=np.int64)
+        step = C.c_uint64(0)
+        _check(lib().mbh_pt_counters(self.handle, c.ctypes.data_as(C.POINTER(C.c_int64)),
+                                     C.byref(step), _stream(stream)))
+        return c, int(step.value)
+
+    def best(self, temp: int = 0, stream=None) -> tuple[np.ndarray, np.ndarray]:
+        x, o = np.zeros(11), np.zeros(3)
+        _check(lib().mbh_pt_best(self.handle, int(temp), x.ctypes.data_as(dp), o.ctypes.data_as(dp),
+                                 _stream(stream)))
+        return x, o
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().mbh_pt_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -154,3 +154,23 @@ def test_het_sampler_bookkeeping(oracle):
     assert np.array_equal(out1, oracle.het_loglike(oracle.pt_theta(x1), ref))
     assert cnt[:4 * T].sum() == 3 * T * W and cnt[4 * T:8 * T].sum() > 0
     assert not np.array_equal(x1, x)
+
+
+def test_direct_sampler_bookkeeping(oracle):
+    """Module 1 form (direct likelihood): stored values match the state."""
+    g = I.grid_small(n=1024)
+    th, snr = I.draw_source(I.rng(0), g["t_obs"])
+    f = oracle.freqs(g)
+    S = oracle.psd(f)
+    th[I.I_DL] = oracle.snr_distance(th, g, snr, S)
+    d, _ = oracle.make_data(th, g, I.noise_normals(I.rng(0, 100), g["n"]), S)
+    lo, hi = I.prior_box(g["t_obs"])
+    x0 = th.copy()
+    x0[0], x0[6], x0[8] = math.log(th[0]), math.cos(th[6]), math.sin(th[8])
+    T, W = 2, 8
+    x = I.draw_pt_ensemble(I.rng(62), x0, T, W, 1e-4 * (hi - lo), lo, hi)
+    out = oracle.direct(oracle.pt_theta(x), g, d, S)
+    x1, out1, cnt = oracle.pt_run_direct(x, out, T, W, I.pt_betas(T), lo, hi, PROBS, 2.0, 4, 0, 2,
+                                         g, d, S)
+    assert np.array_equal(out1, oracle.direct(oracle.pt_theta(x1), g, d, S))
+    assert cnt[:4 * T].sum() == 2 * T * W
