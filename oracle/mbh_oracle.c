@@ -35,6 +35,16 @@
  *   heterodyne        Sec. II B, Eqs. 10-19 and Sec. III B (log-spaced bins over
  *                     the band where h0 != 0): summary data A0, A1, B0, B1 per bin
  *                     and channel, bin centre f_b, r = h/h0 linear in each bin.
+ *   higher harmonics  Sec. II A, Eqs. 7-9 (template = sum over (l,m) of the transfer at
+ *                     t_lm(f) times h_lm): the stand-in "W0-HM" for PhenomHM with the
+ *                     modes (2,2), (3,3), (4,4), (2,1), (3,2), (4,3).  Mode (l,m) takes
+ *                     the (2,2) phase at 2f/m scaled by m/2 (so t_lm(f) = t_22(2f/m),
+ *                     Eq. 8), the (2,2) amplitude at 2f/m times sqrt(2/m) (the SPA
+ *                     factor of a harmonic m of the same orbital phase) and the
+ *                     leading post-Newtonian mode factor H_lm(x) of Blanchet, Faye, Iyer
+ *                     & Sinha (2008); polarisations from the spin-weighted harmonics
+ *                     -2Y_lm (Goldberg et al. 1967).  Parity with PhenomHM itself is
+ *                     unpinned.
  */
 #include <complex.h>
 #include <math.h>
@@ -372,9 +382,141 @@ static void template_point(const w0_t* w, const double* k, const double* Pp, con
     if (xyz_out) for (int c = 0; c < 3; ++c) xyz_out[c] = xyz[c];
 }
 
-/* Template h[c*n + i] (complex, interleaved re/im) at frequencies f[0..n). */
-static void template_eval(const double* th, double t_obs, const double* f, long n, cplx* h,
-                          cplx* xyz)
+/* ---- higher harmonics ("W0-HM") ------------------------------------------ */
+/* Mode b of a mode mask: bit b selects (l, m) = (HM_L[b], HM_M[b]); mask 1 = (2,2) only. */
+static const int HM_L[6] = { 2, 3, 4, 2, 3, 4 };
+static const int HM_M[6] = { 2, 3, 4, 1, 2, 3 };
+
+static double factorial(int n)
+{
+    double r = 1.0;
+    for (int i = 2; i <= n; ++i) r *= i;
+    return r;
+}
+
+static double binomial(int n, int k)
+{
+    if (k < 0 || k > n) return 0.0;
+    return factorial(n) / (factorial(k) * factorial(n - k));
+}
+
+/* Spin-weighted spherical harmonic sY_lm(theta, phi), Goldberg et al. (1967):
+   (-1)^m sqrt[(l+m)!(l-m)!(2l+1) / (4 pi (l+s)!(l-s)!)] sin^{2l}(theta/2)
+   sum_r C(l-s, r) C(l+s, r+s-m) (-1)^{l-r-s} cot^{2r+s-m}(theta/2) e^{i m phi},
+   written with cos and sin of theta/2 so that the poles need no special case. */
+static cplx sylm(int s, int l, int m, double theta, double phi)
+{
+    double c = cos(0.5 * theta), sn = sin(0.5 * theta);
+    double pre = ((m % 2) ? -1.0 : 1.0)
+               * sqrt(factorial(l + m) * factorial(l - m) * (2 * l + 1)
+                      / (4.0 * O_PI * factorial(l + s) * factorial(l - s)));
+    double sum = 0.0;
+    for (int r = 0; r <= l - s; ++r) {
+        int j = r + s - m;
+        if (j < 0 || j > l + s) continue;
+        int pc = 2 * r + s - m;            /* power of cos(theta/2) */
+        int ps = 2 * l - pc;               /* power of sin(theta/2) */
+        double sign = ((l - r - s) % 2) ? -1.0 : 1.0;
+        sum += binomial(l - s, r) * binomial(l + s, j) * sign * pow(c, pc) * pow(sn, ps);
+    }
+    return pre * sum * cexp(I * m * phi);
+}
+
+void oracle_sylm(int s, int l, int m, double theta, double phi, double* out)
+{
+    cplx y = sylm(s, l, m, theta, phi);
+    out[0] = creal(y); out[1] = cimag(y);
+}
+
+/* Leading post-Newtonian mode factor H_lm(x) relative to the (2,2) mode (Blanchet, Faye,
+   Iyer & Sinha 2008), x = (pi M f_orb 2)^{2/3}, delta = (m1 - m2)/M. */
+static cplx hm_hhat(int b, double eta, double delta, double x)
+{
+    switch (b) {
+    case 0: return 1.0;
+    case 1: return -0.75 * I * sqrt(15.0 / 14.0) * delta * sqrt(x);
+    case 2: return -8.0 / 9.0 * sqrt(5.0 / 7.0) * (1.0 - 3.0 * eta) * x;
+    case 3: return I / 3.0 * delta * sqrt(x);
+    case 4: return 1.0 / 3.0 * sqrt(5.0 / 7.0) * (1.0 - 3.0 * eta) * x;
+    default: return -9.0 * I / (4.0 * sqrt(70.0)) * delta * (1.0 - 2.0 * eta) * pow(x, 1.5);
+    }
+}
+
+/* Polarisation factors of mode b (positive frequencies, in the convention of the (2,2)
+   factors above): K+ = (Y_lm + (-1)^l conj(Y_{l,-m}))/2, Kx = i (Y_lm - (-1)^l conj(Y_{l,-m}))/2,
+   Y = -2Y(iota, phi_ref). */
+static void hm_factors(int b, double iota, double phi, cplx* Kp, cplx* Kc)
+{
+    int l = HM_L[b], m = HM_M[b];
+    cplx y = sylm(-2, l, m, iota, phi), ym = conj(sylm(-2, l, -m, iota, phi));
+    double sg = (l % 2) ? -1.0 : 1.0;
+    *Kp = 0.5 * (y + sg * ym);
+    *Kc = 0.5 * I * (y - sg * ym);
+}
+
+/* Mode b alone: |h_lm|, Psi_lm and t_lm at f (zero amplitude outside its support). */
+static void hm_mode(const w0_t* w, double eta, double delta, int b, double t_obs, double f,
+                    double* amp, double* psi, double* t, cplx* H)
+{
+    int m = HM_M[b];
+    double f2 = 2.0 * f / m;
+    *t = w0_time(w, f2);
+    double a = w0_amp(w, f2, *t, t_obs);
+    double x = pow(O_PI * w->M * f2, 2.0 / 3.0);
+    *H = hm_hhat(b, eta, delta, x);
+    *amp = a * sqrt(2.0 / m);
+    *psi = 0.5 * m * w0_phase(w, f2);
+}
+
+/* Template of the selected modes at f: per mode the transfer at t_lm(f) (orbit positions
+   at t_lm), summed over modes link by link; TDI is linear, so it is applied once. */
+static void template_point_hm(const w0_t* w, const double* th, const double* k, const double* Pp,
+                              const double* Pc, unsigned modes, double t_obs, double f, cplx* h,
+                              cplx* xyz_out)
+{
+    double q = th[P_Q];
+    double eta = q / ((1.0 + q) * (1.0 + q)), delta = (1.0 - q) / (1.0 + q);
+    cplx y[6] = { 0, 0, 0, 0, 0, 0 };
+    int any = 0;
+    for (int b = 0; b < 6; ++b) {
+        if (!(modes & (1u << b))) continue;
+        double amp, psi, t;
+        cplx H;
+        hm_mode(w, eta, delta, b, t_obs, f, &amp, &psi, &t, &H);
+        if (amp == 0.0) continue;
+        any = 1;
+        cplx Kp, Kc;
+        hm_factors(b, th[P_IOTA], th[P_PHI], &Kp, &Kc);
+        cplx hlm = amp * H * cexp(-I * psi);
+        double p[9];
+        oracle_orbit(t, p);
+        for (int l = 0; l < 6; ++l) {
+            const double* ps = p + 3 * LINK_S[l];
+            const double* pr = p + 3 * LINK_R[l];
+            double L = O_LARM / O_C, n[3];
+            for (int j = 0; j < 3; ++j) n[j] = (pr[j] - ps[j]) / L;
+            double nPpn = 0.0, nPcn = 0.0;
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) {
+                    nPpn += n[i] * Pp[3 * i + j] * n[j];
+                    nPcn += n[i] * Pc[3 * i + j] * n[j];
+                }
+            y[l] += link_kernel(f, k, ps, pr) * (nPpn * Kp + nPcn * Kc) * hlm;
+        }
+    }
+    if (!any) {
+        for (int c = 0; c < 3; ++c) { h[c] = 0.0; if (xyz_out) xyz_out[c] = 0.0; }
+        return;
+    }
+    cplx xyz[3];
+    tdi(f, y, xyz, h);
+    if (xyz_out) for (int c = 0; c < 3; ++c) xyz_out[c] = xyz[c];
+}
+
+/* Template h[c*n + i] (complex, interleaved re/im) at frequencies f[0..n) for the modes
+   of the mask (1 = the (2,2) mode: W0). */
+static void template_eval_modes(const double* th, double t_obs, const double* f, long n,
+                                unsigned modes, cplx* h, cplx* xyz)
 {
     w0_t w;
     w0_setup(th, &w);
@@ -383,12 +525,43 @@ static void template_eval(const double* th, double t_obs, const double* f, long 
     cplx Kp = kp[0] + I * kp[1], Kc = kc[0] + I * kc[1];
     for (long i = 0; i < n; ++i) {
         cplx hh[3], xx[3];
-        template_point(&w, k, Pp, Pc, Kp, Kc, t_obs, f[i], hh, xx);
+        if (modes == 1u)
+            template_point(&w, k, Pp, Pc, Kp, Kc, t_obs, f[i], hh, xx);
+        else
+            template_point_hm(&w, th, k, Pp, Pc, modes, t_obs, f[i], hh, xx);
         for (int c = 0; c < 3; ++c) {
             h[c * n + i] = hh[c];
             if (xyz) xyz[c * n + i] = xx[c];
         }
     }
+}
+
+static void template_eval(const double* th, double t_obs, const double* f, long n, cplx* h,
+                          cplx* xyz)
+{
+    template_eval_modes(th, t_obs, f, n, 1u, h, xyz);
+}
+
+/* Mode b alone on frequencies f: amp, psi, t (the SPA relations are pinned with these). */
+void oracle_hm_mode(const double* th, double t_obs, const double* f, long n, int b, double* amp,
+                    double* psi, double* tf, double* hre, double* him)
+{
+    w0_t w;
+    w0_setup(th, &w);
+    double q = th[P_Q];
+    double eta = q / ((1.0 + q) * (1.0 + q)), delta = (1.0 - q) / (1.0 + q);
+    for (long i = 0; i < n; ++i) {
+        cplx H;
+        hm_mode(&w, eta, delta, b, t_obs, f[i], amp + i, psi + i, tf + i, &H);
+        hre[i] = creal(H);
+        him[i] = cimag(H);
+    }
+}
+
+void oracle_template_hm(const double* th, double t_obs, const double* f, long n, unsigned modes,
+                        double* h)
+{
+    template_eval_modes(th, t_obs, f, n, modes, (cplx*)h, NULL);
 }
 
 void oracle_template(const double* th, double t_obs, const double* f, long n, double* h)
@@ -408,9 +581,9 @@ static void theta_col(const double* th, long W, long i, double* out)
     for (int j = 0; j < 11; ++j) out[j] = th[j * W + i];
 }
 
-/* Batch on the grid f_k = f0 + k df: h[(w*3 + c)*n + k]. */
-void oracle_template_batch(const double* th, long W, double f0, double df, long n,
-                           double t_obs, double* h)
+/* Batch on the grid f_k = f0 + k df: h[(w*3 + c)*n + k], modes of the mask. */
+void oracle_template_batch_hm(const double* th, long W, double f0, double df, long n,
+                              double t_obs, unsigned modes, double* h)
 {
     double* f = malloc(sizeof(double) * n);
     for (long k = 0; k < n; ++k) f[k] = f0 + k * df;
@@ -418,9 +591,15 @@ void oracle_template_batch(const double* th, long W, double f0, double df, long 
     for (long i = 0; i < W; ++i) {
         double t[11];
         theta_col(th, W, i, t);
-        template_eval(t, t_obs, f, n, (cplx*)h + i * 3 * n, NULL);
+        template_eval_modes(t, t_obs, f, n, modes, (cplx*)h + i * 3 * n, NULL);
     }
     free(f);
+}
+
+void oracle_template_batch(const double* th, long W, double f0, double df, long n,
+                           double t_obs, double* h)
+{
+    oracle_template_batch_hm(th, W, f0, df, n, t_obs, 1u, h);
 }
 
 /* ========================================================================== */
@@ -480,8 +659,8 @@ double oracle_inner(const double* a, const double* b, const double* S, long n, d
 /* Direct likelihood for W templates against data d ([3][n] complex) on the grid
    f_k = f0 + k df, k in [0, n): out[0*W + i] = lnL, out[W + i] = <d|h>,
    out[2W + i] = <h|h>, with lnL = -1/2 (<d|d> + <h|h> - 2 <d|h>). */
-void oracle_direct(const double* th, long W, double f0, double df, long n, double t_obs,
-                   const double* d, const double* S, double* out)
+void oracle_direct_hm(const double* th, long W, double f0, double df, long n, double t_obs,
+                      unsigned modes, const double* d, const double* S, double* out)
 {
     double dd = oracle_inner(d, d, S, n, df, 0);
     double* f = malloc(sizeof(double) * n);
@@ -491,7 +670,7 @@ void oracle_direct(const double* th, long W, double f0, double df, long n, doubl
         double t[11];
         theta_col(th, W, i, t);
         cplx* h = malloc(sizeof(cplx) * 3 * n);
-        template_eval(t, t_obs, f, n, h, NULL);
+        template_eval_modes(t, t_obs, f, n, modes, h, NULL);
         double dh = oracle_inner(d, (const double*)h, S, n, df, 0);
         double hh = oracle_inner((const double*)h, (const double*)h, S, n, df, 0);
         out[i] = -0.5 * (dd + hh - 2.0 * dh);
@@ -500,6 +679,12 @@ void oracle_direct(const double* th, long W, double f0, double df, long n, doubl
         free(h);
     }
     free(f);
+}
+
+void oracle_direct(const double* th, long W, double f0, double df, long n, double t_obs,
+                   const double* d, const double* S, double* out)
+{
+    oracle_direct_hm(th, W, f0, df, n, t_obs, 1u, d, S, out);
 }
 
 /* ========================================================================== */
@@ -511,15 +696,21 @@ void oracle_direct(const double* th, long W, double f0, double df, long n, doubl
    f(kmax), rounded to the nearest grid index, endpoints exact, duplicates
    dropped.  Returns the number of bins (edges has that + 1 entries) or -1 when
    the band has fewer than two points. */
-long oracle_het_edges(const double* th0, double f0, double df, long n, double t_obs, int nbins,
-                      long* edges, long* band)
+long oracle_het_edges_hm(const double* th0, double f0, double df, long n, double t_obs,
+                         unsigned modes, int nbins, long* edges, long* band)
 {
     w0_t w;
     w0_setup(th0, &w);
     long kmin = -1, kmax = -1;
     for (long k = 0; k < n; ++k) {
         double f = f0 + k * df;
-        if (w0_amp(&w, f, w0_time(&w, f), t_obs) != 0.0) {
+        int on = 0;   /* some selected mode of h0 is non-zero at f */
+        for (int b = 0; b < 6 && !on; ++b) {
+            if (!(modes & (1u << b))) continue;
+            double f2 = 2.0 * f / HM_M[b];
+            on = w0_amp(&w, f2, w0_time(&w, f2), t_obs) != 0.0;
+        }
+        if (on) {
             if (kmin < 0) kmin = k;
             kmax = k;
         }
@@ -543,6 +734,12 @@ long oracle_het_edges(const double* th0, double f0, double df, long n, double t_
     return m - 1;
 }
 
+long oracle_het_edges(const double* th0, double f0, double df, long n, double t_obs, int nbins,
+                      long* edges, long* band)
+{
+    return oracle_het_edges_hm(th0, f0, df, n, t_obs, 1u, nbins, edges, band);
+}
+
 /* Summary data for the reference th0 (Eqs. 15, 16, 18, 19), per bin b and channel c,
    sum[(b*3 + c)*6 + {0..5}] = Re A0, Im A0, Re A1, Im A1, B0, B1, with
    A0 = sum_{k in b} d conj(h0)/S df, A1 = sum d conj(h0)/S (f - f_b) df,
@@ -550,12 +747,12 @@ long oracle_het_edges(const double* th0, double f0, double df, long n, double t_
    Bin b holds k in [e_b, e_{b+1}), the last bin also holds e_E.
    h0e[(e*3 + c)] = h0 at edge e (complex interleaved).
    Returns the number of bins E (or -1); edges needs nbins+1 entries. */
-long oracle_het_prepare(const double* th0, double f0, double df, long n, double t_obs,
-                        const double* d, const double* S, int nbins,
-                        long* edges, double* sum, double* h0e, double* dd_out)
+long oracle_het_prepare_hm(const double* th0, double f0, double df, long n, double t_obs,
+                           unsigned modes, const double* d, const double* S, int nbins,
+                           long* edges, double* sum, double* h0e, double* dd_out)
 {
     long band[2];
-    long E = oracle_het_edges(th0, f0, df, n, t_obs, nbins, edges, band);
+    long E = oracle_het_edges_hm(th0, f0, df, n, t_obs, modes, nbins, edges, band);
     *dd_out = oracle_inner(d, d, S, n, df, 0);
     if (E < 1) return -1;
     const cplx* cd = (const cplx*)d;
@@ -564,7 +761,7 @@ long oracle_het_prepare(const double* th0, double f0, double df, long n, double 
     double* f = malloc(sizeof(double) * nb);
     for (long i = 0; i < nb; ++i) f[i] = f0 + (kmin + i) * df;
     cplx* h0 = malloc(sizeof(cplx) * 3 * nb);
-    template_eval(th0, t_obs, f, nb, h0, NULL);
+    template_eval_modes(th0, t_obs, f, nb, modes, h0, NULL);
     for (long b = 0; b < E; ++b) {
         long klo = edges[b], khi = edges[b + 1];
         long kend = (b == E - 1) ? khi + 1 : khi;
@@ -596,6 +793,13 @@ long oracle_het_prepare(const double* th0, double f0, double df, long n, double 
     free(h0);
     free(f);
     return E;
+}
+
+long oracle_het_prepare(const double* th0, double f0, double df, long n, double t_obs,
+                        const double* d, const double* S, int nbins,
+                        long* edges, double* sum, double* h0e, double* dd_out)
+{
+    return oracle_het_prepare_hm(th0, f0, df, n, t_obs, 1u, d, S, nbins, edges, sum, h0e, dd_out);
 }
 
 /* Contraction from template values at the edges (Eqs. 14 and 17): he is
@@ -633,10 +837,11 @@ void oracle_het_contract(long E, const long* edges, double f0, double df, const 
     }
 }
 
-/* Heterodyned likelihood of W walkers (SoA [11][W]) against a prepared reference. */
-void oracle_het_loglike(const double* th, long W, long E, const long* edges, double f0,
-                        double df, double t_obs, const double* sum, const double* h0e,
-                        double dd, double* out)
+/* Heterodyned likelihood of W walkers (SoA [11][W]) against a prepared reference, templates
+   of the modes of the mask (the reference's). */
+void oracle_het_loglike_hm(const double* th, long W, long E, const long* edges, double f0,
+                           double df, double t_obs, unsigned modes, const double* sum,
+                           const double* h0e, double dd, double* out)
 {
     double* fe = malloc(sizeof(double) * (E + 1));
     for (long e = 0; e <= E; ++e) fe[e] = f0 + edges[e] * df;
@@ -646,7 +851,7 @@ void oracle_het_loglike(const double* th, long W, long E, const long* edges, dou
         double t[11];
         theta_col(th, W, i, t);
         cplx* tmp = malloc(sizeof(cplx) * 3 * (E + 1));
-        template_eval(t, t_obs, fe, E + 1, tmp, NULL);
+        template_eval_modes(t, t_obs, fe, E + 1, modes, tmp, NULL);
         for (long e = 0; e <= E; ++e)
             for (int c = 0; c < 3; ++c) he[(i * (E + 1) + e) * 3 + c] = tmp[c * (E + 1) + e];
         free(tmp);
@@ -654,4 +859,11 @@ void oracle_het_loglike(const double* th, long W, long E, const long* edges, dou
     oracle_het_contract(E, edges, f0, df, sum, h0e, dd, (const double*)he, W, out);
     free(he);
     free(fe);
+}
+
+void oracle_het_loglike(const double* th, long W, long E, const long* edges, double f0,
+                        double df, double t_obs, const double* sum, const double* h0e,
+                        double dd, double* out)
+{
+    oracle_het_loglike_hm(th, W, E, edges, f0, df, t_obs, 1u, sum, h0e, dd, out);
 }

@@ -54,6 +54,19 @@ def lib():
             "oracle_het_loglike": (None, [dp, C.c_long, C.c_long, lp, C.c_double, C.c_double,
                                           C.c_double, dp, dp, C.c_double, dp]),
             "oracle_philox4x32_10": (None, [u32p, u32p, u32p]),
+            "oracle_sylm": (None, [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, dp]),
+            "oracle_hm_mode": (None, [dp, C.c_double, dp, C.c_long, C.c_int, dp, dp, dp, dp, dp]),
+            "oracle_template_hm": (None, [dp, C.c_double, dp, C.c_long, C.c_uint, dp]),
+            "oracle_template_batch_hm": (None, [dp, C.c_long, C.c_double, C.c_double, C.c_long,
+                                                C.c_double, C.c_uint, dp]),
+            "oracle_direct_hm": (None, [dp, C.c_long, C.c_double, C.c_double, C.c_long, C.c_double,
+                                        C.c_uint, dp, dp, dp]),
+            "oracle_het_edges_hm": (C.c_long, [dp, C.c_double, C.c_double, C.c_long, C.c_double,
+                                               C.c_uint, C.c_int, lp, lp]),
+            "oracle_het_prepare_hm": (C.c_long, [dp, C.c_double, C.c_double, C.c_long, C.c_double,
+                                                 C.c_uint, dp, dp, C.c_int, lp, dp, dp, dp]),
+            "oracle_het_loglike_hm": (None, [dp, C.c_long, C.c_long, lp, C.c_double, C.c_double,
+                                             C.c_double, C.c_uint, dp, dp, C.c_double, dp]),
             "oracle_pt_theta": (None, [dp, C.c_long, dp]),
             "oracle_pt_choice": (None, [C.c_uint64, C.c_uint64, C.c_int, C.c_long, C.c_long, dp,
                                         C.c_double, dp]),
@@ -173,14 +186,43 @@ def template_xyz(theta, f, t_obs):
     return h, x
 
 
-def template_batch(theta, grid) -> np.ndarray:
+def template_batch(theta, grid, modes: int = 1) -> np.ndarray:
     """Templates on the grid for SoA theta (11, W): shape (W, 3, n) complex128."""
-    th = _f64(theta)
+    th = np.ascontiguousarray(_f64(theta))
     W = th.shape[1]
     h = np.empty((W, 3, grid["n"]), dtype=np.complex128)
-    lib().oracle_template_batch(_d(th), W, grid["f0"], grid["df"], grid["n"], grid["t_obs"],
-                                _d(h.view(np.float64)))
+    lib().oracle_template_batch_hm(_d(th), W, grid["f0"], grid["df"], grid["n"], grid["t_obs"],
+                                   int(modes), _d(h.view(np.float64)))
     return h
+
+
+# ---- higher harmonics (W0-HM) ---------------------------------------------------
+HM_MODES = ((2, 2), (3, 3), (4, 4), (2, 1), (3, 2), (4, 3))   # bit b of a mode mask
+HM_ALL = 0x3F
+
+
+def template_hm(theta, f, t_obs, modes: int) -> np.ndarray:
+    f = _f64(f)
+    h = np.empty((3, f.size), dtype=np.complex128)
+    lib().oracle_template_hm(_d(_f64(theta)), t_obs, _d(f), f.size, int(modes),
+                             _d(h.view(np.float64)))
+    return h
+
+
+def hm_mode(theta, f, t_obs, b: int):
+    """Mode b alone: (|h_lm| without the mode factor, Psi_lm, t_lm, H_lm complex)."""
+    f = _f64(f)
+    n = f.size
+    amp, psi, tf, hr, hi = (np.empty(n) for _ in range(5))
+    lib().oracle_hm_mode(_d(_f64(theta)), t_obs, _d(f), n, int(b), _d(amp), _d(psi), _d(tf),
+                         _d(hr), _d(hi))
+    return amp, psi, tf, hr + 1j * hi
+
+
+def sylm(s: int, l: int, m: int, theta: float, phi: float) -> complex:
+    out = np.empty(2)
+    lib().oracle_sylm(s, l, m, float(theta), float(phi), _d(out))
+    return complex(out[0], out[1])
 
 
 # ---- PSD, noise, inner products ---------------------------------------------
@@ -227,42 +269,42 @@ def make_data(theta_inj, grid, z=None, S=None):
     return np.ascontiguousarray(d), S
 
 
-def direct(theta, grid, d, S) -> np.ndarray:
-    """(3, W): lnL, <d|h>, <h|h> (Eqs. 2-3)."""
+def direct(theta, grid, d, S, modes: int = 1) -> np.ndarray:
+    """(3, W): lnL, <d|h>, <h|h> (Eqs. 2-3); templates of the modes of the mask."""
     th = _f64(theta)
     if th.ndim == 1:
         th = th[:, None]
     th = np.ascontiguousarray(th)
     W = th.shape[1]
     out = np.empty(3 * W)
-    lib().oracle_direct(_d(th), W, grid["f0"], grid["df"], grid["n"], grid["t_obs"],
-                        _d(_c128(d).view(np.float64)), _d(_f64(S)), _d(out))
+    lib().oracle_direct_hm(_d(th), W, grid["f0"], grid["df"], grid["n"], grid["t_obs"],
+                           int(modes), _d(_c128(d).view(np.float64)), _d(_f64(S)), _d(out))
     return out.reshape(3, W)
 
 
 # ---- heterodyne ---------------------------------------------------------------
-def het_edges(theta0, grid, nbins):
+def het_edges(theta0, grid, nbins, modes: int = 1):
     edges = np.empty(nbins + 1, dtype=np.int64)
     band = np.empty(2, dtype=np.int64)
-    E = lib().oracle_het_edges(_d(_f64(theta0)), grid["f0"], grid["df"], grid["n"],
-                               grid["t_obs"], nbins, _l(edges), _l(band))
+    E = lib().oracle_het_edges_hm(_d(_f64(theta0)), grid["f0"], grid["df"], grid["n"],
+                                  grid["t_obs"], int(modes), nbins, _l(edges), _l(band))
     return (edges[:E + 1].copy() if E > 0 else edges[:0].copy()), band
 
 
-def het_prepare(theta0, grid, d, S, nbins) -> dict:
+def het_prepare(theta0, grid, d, S, nbins, modes: int = 1) -> dict:
     edges = np.empty(nbins + 1, dtype=np.int64)
     summ = np.empty(nbins * 3 * 6)
     h0e = np.empty((nbins + 1) * 3 * 2)
     dd = np.empty(1)
-    E = lib().oracle_het_prepare(_d(_f64(theta0)), grid["f0"], grid["df"], grid["n"],
-                                 grid["t_obs"], _d(_c128(d).view(np.float64)), _d(_f64(S)),
-                                 nbins, _l(edges), _d(summ), _d(h0e), _d(dd))
+    E = lib().oracle_het_prepare_hm(_d(_f64(theta0)), grid["f0"], grid["df"], grid["n"],
+                                    grid["t_obs"], int(modes), _d(_c128(d).view(np.float64)),
+                                    _d(_f64(S)), nbins, _l(edges), _d(summ), _d(h0e), _d(dd))
     if E < 1:
         raise ValueError("empty heterodyne band")
     return dict(E=int(E), edges=edges[:E + 1].copy(),
                 summary=summ[:E * 18].reshape(E, 3, 6).copy(),
                 h0e=h0e[:(E + 1) * 6].view(np.complex128).reshape(E + 1, 3).copy(),
-                dd=float(dd[0]), grid=dict(grid))
+                dd=float(dd[0]), grid=dict(grid), modes=int(modes))
 
 
 def het_contract(ref: dict, he: np.ndarray) -> np.ndarray:
@@ -285,9 +327,10 @@ def het_loglike(theta, ref: dict) -> np.ndarray:
     W = th.shape[1]
     out = np.empty(3 * W)
     g = ref["grid"]
-    lib().oracle_het_loglike(_d(th), W, ref["E"], _l(ref["edges"]), g["f0"], g["df"], g["t_obs"],
-                             _d(_f64(ref["summary"]).ravel()),
-                             _d(_c128(ref["h0e"]).view(np.float64)), ref["dd"], _d(out))
+    lib().oracle_het_loglike_hm(_d(th), W, ref["E"], _l(ref["edges"]), g["f0"], g["df"],
+                                g["t_obs"], int(ref.get("modes", 1)),
+                                _d(_f64(ref["summary"]).ravel()),
+                                _d(_c128(ref["h0e"]).view(np.float64)), ref["dd"], _d(out))
     return out.reshape(3, W)
 
 
