@@ -453,7 +453,7 @@ def run_sampler(M, WL, g, src, ref, stream, het_rate: float, iters: int = 20) ->
                      "swap_acceptance_by_level": (cnt[8 * T + 1:9 * T] / np.maximum(cnt[9 * T + 1:10 * T], 1)).round(4).tolist(),
                      "iterations_run": step}
     return {"temperatures": T, "walkers_per_temperature": W, "bins": ref.bins,
-            "launches_per_iteration": 8, "graph": True, **res}
+            "launches_per_iteration": 9, "graph": True, **res}
 
 
 def run_uneven(M, WL, stream, reps: int = 20) -> dict:

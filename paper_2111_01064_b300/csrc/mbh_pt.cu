@@ -5,10 +5,12 @@
 // hottest pair first (Vousden, Farr & Mandel 2016).  The likelihood of every proposal batch is
 // the library's heterodyned (Sec. II B) or direct (Sec. II) likelihood.
 //
-// One iteration = 8 launches on the caller's stream, no host synchronisation, captured once in
-// a CUDA graph:
+// One iteration = 9 launches, no host synchronisation, captured once in a CUDA graph:
+//   pt_draws_kernel    ln u of every acceptance and swap test (state-independent)
 //   pt_perm_kernel     random permutations of every swap level (state-independent; one block
-//                      per level, bitonic sort of 48-bit Philox keys in shared memory)
+//                      per level, bitonic sort of 48-bit Philox keys in shared memory); both
+//                      on a side stream forked at the start of the iteration, joined before the
+//                      first acceptance and before the swaps, so they overlap the half steps
 //   for each half h:   pt_propose_kernel -> likelihood of the T*W/2 proposals -> pt_accept_kernel
 //   pt_swap_kernel     the swap levels in order, hottest first (one block; the two temperatures
 //                      of a level are held in shared memory), then the step counter advances.
@@ -37,7 +39,8 @@ namespace {
 constexpr int kPar = 11;
 constexpr int kMaxTemps = 64;
 constexpr int kMaxWalkers = 8192;   // per temperature (16-bit walker index in the swap keys)
-constexpr int kThreads = 256;
+constexpr int kThreads = 256;      // rescoring and gathers
+constexpr int kStepThreads = 64;   // propose/accept: 8192 walkers -> 128 blocks
 constexpr int kSortThreads = 1024;
 
 enum { K_STRETCH = 0, K_SKY_ALL = 1, K_SKY_LON = 2, K_SKY_LAT = 3 };
@@ -57,6 +60,8 @@ struct PtArgs {
     double* fac;            // [M] log acceptance factor (d-1) ln z of stretch moves
     int32_t* flag;          // [M] inside-prior bit | kind << 1
     int32_t* perm;          // [T][W] hot partner of cold walker k at level i
+    double* lnu_acc;        // [2][M] ln u of the acceptance tests of both half steps
+    double* lnu_swap;       // [T][W] ln u of the swap tests (level 0 unused)
     const double* betas;    // [T]
     unsigned long long* counters;   // [10 T]
     unsigned long long* step;       // iteration counter
@@ -119,7 +124,7 @@ __device__ __forceinline__ void theta_of_x(const double (&x)[kPar], double (&th)
 }
 
 // ---- kernels -------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) pt_propose_kernel(const PtArgs A, int half)
+__global__ void __launch_bounds__(kStepThreads) pt_propose_kernel(const PtArgs A, int half)
 {
     const int32_t Wh = A.W / 2, M = A.T * Wh, N = A.T * A.W;
     const int32_t item = blockIdx.x * blockDim.x + threadIdx.x;
@@ -178,7 +183,7 @@ __global__ void __launch_bounds__(kThreads) pt_propose_kernel(const PtArgs A, in
     A.flag[item] = (ok ? 1 : 0) | (kind << 1);
 }
 
-__global__ void __launch_bounds__(kThreads) pt_accept_kernel(const PtArgs A, int half)
+__global__ void __launch_bounds__(kStepThreads) pt_accept_kernel(const PtArgs A, int half)
 {
     __shared__ unsigned int cnt[kMaxTemps * 8];
     for (int i = threadIdx.x; i < A.T * 8; i += blockDim.x) cnt[i] = 0;
@@ -186,16 +191,13 @@ __global__ void __launch_bounds__(kThreads) pt_accept_kernel(const PtArgs A, int
     const int32_t Wh = A.W / 2, M = A.T * Wh, N = A.T * A.W;
     const int32_t item = blockIdx.x * blockDim.x + threadIdx.x;
     if (item < M) {
-        const uint64_t step = *A.step;
         const int32_t t = item / Wh, kp = item - t * Wh;
         const int32_t col = A.map[t * A.W + half * Wh + kp];
-        const uint4 r = draw(A.seed, (uint32_t)item, P_ACCEPT + (uint32_t)half, step);
-        const double lnu = log(u53(r.x, r.y));
         const double dl = __dsub_rn(A.out_p[item], A.out[col]);
         const double la = __dadd_rn(A.fac[item], __dmul_rn(A.betas[t], dl));
         const int32_t f = A.flag[item];
         const int kind = f >> 1;
-        const bool acc = (f & 1) && lnu < la;
+        const bool acc = (f & 1) && A.lnu_acc[(int64_t)half * M + item] < la;
         atomicAdd(&cnt[t * 8 + kind], 1u);
         if (acc) {
             atomicAdd(&cnt[t * 8 + 4 + kind], 1u);
@@ -213,6 +215,29 @@ __global__ void __launch_bounds__(kThreads) pt_accept_kernel(const PtArgs A, int
         // counters: [0, 4T) proposals per (t, kind), [4T, 8T) accepted per (t, kind)
         const int dst = j < 4 ? t * 4 + j : 4 * A.T + t * 4 + (j - 4);
         atomicAdd(&A.counters[dst], (unsigned long long)c);
+    }
+}
+
+// ln u of every acceptance and swap test of the iteration (state-independent, float64 log on
+// the whole GPU): items [0, 2M) acceptance tests of half 0 and 1, then [2M, 2M + (T-1) W) swaps.
+__global__ void __launch_bounds__(kThreads) pt_draws_kernel(const PtArgs A)
+{
+    const int32_t M = A.T * (A.W / 2);
+    const int64_t n = 2 * (int64_t)M + (int64_t)(A.T - 1) * A.W;
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const uint64_t step = *A.step;
+    if (q < 2 * M) {
+        const int half = (int)(q / M);
+        const int32_t item = (int32_t)(q - (int64_t)half * M);
+        const uint4 r = draw(A.seed, (uint32_t)item, P_ACCEPT + (uint32_t)half, step);
+        A.lnu_acc[q] = log(u53(r.x, r.y));
+    } else {
+        const int64_t s = q - 2 * M;
+        const int i = 1 + (int)(s / A.W);
+        const int32_t k = (int32_t)(s - (int64_t)(i - 1) * A.W);
+        const uint4 r = draw(A.seed, (uint32_t)k, P_SWAP_ACC + (uint32_t)i, step);
+        A.lnu_swap[(int64_t)i * A.W + k] = log(u53(r.x, r.y));
     }
 }
 
@@ -280,10 +305,8 @@ __global__ void __launch_bounds__(kSortThreads) pt_swap_kernel(const PtArgs A)
             unsigned int mine = 0;
             for (int k = threadIdx.x; k < W; k += blockDim.x) {
                 const int h = A.perm[(int64_t)i * W + k];
-                const uint4 r = draw(A.seed, (uint32_t)k, P_SWAP_ACC + (uint32_t)i, step);
-                const double lnu = log(u53(r.x, r.y));
                 const double la = __dmul_rn(db, __dsub_rn(lnl[hot * W + h], lnl[cold * W + k]));
-                if (lnu < la) {
+                if (A.lnu_swap[(int64_t)i * W + k] < la) {
                     const double l = lnl[hot * W + h];
                     lnl[hot * W + h] = lnl[cold * W + k];
                     lnl[cold * W + k] = l;
@@ -398,6 +421,8 @@ struct mbh_pt {
     double* res = nullptr;   // device [14] for mbh_pt_best
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
+    cudaStream_t side = nullptr;   // permutation sorts, concurrent with the half steps
+    cudaEvent_t fork = nullptr, join = nullptr, join_draws = nullptr;
 };
 
 namespace {
@@ -406,8 +431,15 @@ void free_pt(mbh_pt* P)
 {
     if (P->exec) cudaGraphExecDestroy(P->exec);
     if (P->graph) cudaGraphDestroy(P->graph);
+    if (P->side) {
+        cudaStreamSynchronize(P->side);
+        cudaStreamDestroy(P->side);
+    }
+    if (P->fork) cudaEventDestroy(P->fork);
+    if (P->join) cudaEventDestroy(P->join);
+    if (P->join_draws) cudaEventDestroy(P->join_draws);
     PtArgs& A = P->A;
-    void* bufs[] = {A.x, A.out, A.map, A.y, A.theta, A.out_p, A.fac, A.flag, A.perm,
+    void* bufs[] = {A.x, A.out, A.map, A.y, A.theta, A.out_p, A.fac, A.flag, A.perm, A.lnu_acc, A.lnu_swap,
                     (void*)A.betas, A.counters, A.step, P->res};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -437,19 +469,32 @@ mbh_status queue_iteration(mbh_pt* P, cudaStream_t st)
 {
     const PtArgs& A = P->A;
     const int32_t M = A.T * (A.W / 2);
-    const unsigned gM = (unsigned)((M + kThreads - 1) / kThreads);
+    const unsigned gM = (unsigned)((M + kStepThreads - 1) / kStepThreads);
     cudaError_t e = cudaSuccess;
+    // state-independent work on a side stream while the first half step runs: ln u of every
+    // test of the iteration, then the permutations of the swap levels
+    e = cudaEventRecord(P->fork, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(P->side, P->fork, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "fork");
+    const int64_t nd = 2 * (int64_t)M + (int64_t)(A.T - 1) * A.W;
+    pt_draws_kernel<<<(unsigned)((nd + kThreads - 1) / kThreads), kThreads, 0, P->side>>>(A);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "pt_draws_kernel");
+    if ((e = cudaEventRecord(P->join_draws, P->side)) != cudaSuccess) return cuda_fail(e, "join");
     if (A.T > 1) {
-        pt_perm_kernel<<<A.T - 1, kSortThreads, sizeof(unsigned long long) * P->Wp, st>>>(A, P->Wp);
+        pt_perm_kernel<<<A.T - 1, kSortThreads, sizeof(unsigned long long) * P->Wp, P->side>>>(A, P->Wp);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "pt_perm_kernel");
     }
+    if ((e = cudaEventRecord(P->join, P->side)) != cudaSuccess) return cuda_fail(e, "join");
     for (int half = 0; half < 2; ++half) {
-        pt_propose_kernel<<<gM, kThreads, 0, st>>>(A, half);
+        pt_propose_kernel<<<gM, kStepThreads, 0, st>>>(A, half);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "pt_propose_kernel");
         if (mbh_status s = likelihood(P, M, A.out_p, st)) return s;
-        pt_accept_kernel<<<gM, kThreads, 0, st>>>(A, half);
+        if (half == 0 && (e = cudaStreamWaitEvent(st, P->join_draws, 0)) != cudaSuccess)
+            return cuda_fail(e, "join");
+        pt_accept_kernel<<<gM, kStepThreads, 0, st>>>(A, half);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "pt_accept_kernel");
     }
+    if ((e = cudaStreamWaitEvent(st, P->join, 0)) != cudaSuccess) return cuda_fail(e, "join");
     pt_swap_kernel<<<1, kSortThreads, (sizeof(double) + sizeof(int32_t)) * 2 * A.W, st>>>(A);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "pt_swap_kernel");
     return MBH_OK;
@@ -555,10 +600,16 @@ extern "C" mbh_status mbh_pt_create(const mbh_pt_opts* o, const mbh_ref* ref, co
     alloc((void**)&A.fac, sizeof(double) * M);
     alloc((void**)&A.flag, sizeof(int32_t) * M);
     alloc((void**)&A.perm, sizeof(int32_t) * N);
+    alloc((void**)&A.lnu_acc, sizeof(double) * 2 * M);
+    alloc((void**)&A.lnu_swap, sizeof(double) * N);
     alloc((void**)&A.betas, sizeof(double) * A.T);
     alloc((void**)&A.counters, sizeof(unsigned long long) * 10 * A.T);
     alloc((void**)&A.step, sizeof(unsigned long long));
     alloc((void**)&P->res, sizeof(double) * 14);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->join_draws, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         free_pt(P);
         return e == cudaErrorMemoryAllocation ? fail(MBH_ENOMEM, "sampler buffers") : cuda_fail(e, "sampler buffers");
