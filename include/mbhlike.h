@@ -157,6 +157,8 @@ MBH_API mbh_status het_prepare_reference(const mbh_data* data, const double* the
                                  int32_t n_bins, void* stream, mbh_ref** out);
 /* Number of bins E actually used (<= n_bins). */
 MBH_API int32_t mbh_ref_bins(const mbh_ref* ref);
+/* Mode mask the reference was prepared with (see the higher-harmonic calls). */
+MBH_API uint32_t mbh_ref_modes(const mbh_ref* ref);
 /* Copies (host, blocking): edges int64 [E+1]; summary float64 [E][3][6] =
  * Re A0, Im A0, Re A1, Im A1, B0, B1; h0 at the edges complex128 [E+1][3];
  * any pointer may be NULL. */
@@ -292,6 +294,30 @@ MBH_API mbh_status mbh_server_reset_stats(mbh_server* server);
 /* Cancels queued requests, waits for batches in flight, stops the worker. */
 MBH_API void mbh_server_free(mbh_server* server);
 
+/* ---- Higher harmonics (Sec. II A, Eqs. 7-9) ------------------------------
+ * Templates summed over harmonic modes (l, m), each with its own time-frequency
+ * map t_lm(f) (Eq. 8) and its own response at t_lm (Eq. 9).  The model is the
+ * stand-in "W0-HM" (PhenomHM's coefficients are not available): mode (l, m) takes
+ * the W0 (2,2) phase at f2 = 2f/m scaled by m/2, so t_lm(f) = t_22(2f/m), and the
+ * (2,2) amplitude at f2 times sqrt(2/m) and the leading post-Newtonian mode factor
+ * H_lm(x), x = (pi M f2)^{2/3}; polarisations from the spin-weighted harmonics
+ * -2Y_lm(iota, phi_ref).  Mode mask: bit 0 (2,2), bit 1 (3,3), bit 2 (4,4),
+ * bit 3 (2,1), bit 4 (3,2), bit 5 (4,3); mask 1 is W0 and these calls then do
+ * exactly what the (2,2) calls do.  Masks with higher modes are evaluated in
+ * float64 only (MBH_MIXED returns MBH_EINVAL).  Layouts, ownership and errors as
+ * in the (2,2) calls; an empty mask or bits above 5 return MBH_EINVAL. */
+MBH_API mbh_status template_batch_hm(const mbh_grid* grid, const double* theta_dev, int64_t W,
+                                     uint32_t modes, mbh_precision precision, void* h_out_dev,
+                                     void* stream);
+MBH_API mbh_status direct_loglike_batch_hm(const mbh_data* data, const double* theta_dev, int64_t W,
+                                           uint32_t modes, mbh_precision precision, double* out_dev,
+                                           void* stream);
+/* The band is where some selected mode of h0 is non-zero; het_loglike_batch then
+ * evaluates every walker of this reference with the same modes (MBH_FP64). */
+MBH_API mbh_status het_prepare_reference_hm(const mbh_data* data, const double* theta0_host,
+                                            int32_t n_bins, uint32_t modes, void* stream,
+                                            mbh_ref** out);
+
 /* ---- Parallel-tempered ensemble sampler iteration (Sec. III) -------------
  * The sampler shared by the paper's three pipeline modules, run on the device:
  * T temperatures (inverse temperatures beta_t, target L^beta_t x prior) of W
@@ -330,6 +356,8 @@ typedef struct {
     uint64_t seed;
     mbh_precision precision;           /* of the likelihood */
     mbh_het_config het_config;         /* threads_per_walker 0 = default */
+    uint32_t modes;                    /* direct likelihood: harmonic mode mask (0 = (2,2));
+                                          a reference brings its own */
 } mbh_pt_opts;
 
 /* x_dev: float64 [11][T W] start positions in x, slot t W + k = walker k of

@@ -80,7 +80,8 @@ def lib():
             "oracle_pt_gauss_loglike": (None, [dp, C.c_long, dp, dp, dp]),
             "oracle_pt_run_direct": (None, [dp, dp, C.c_long, C.c_long, dp, dp, dp, dp, C.c_double,
                                             C.c_uint64, C.c_uint64, C.c_long, C.c_double,
-                                            C.c_double, C.c_long, C.c_double, dp, dp, lp]),
+                                            C.c_double, C.c_long, C.c_double, C.c_uint, dp, dp,
+                                            lp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -392,13 +393,15 @@ def pt_run_het(x, out, T, W, betas, lo, hi, probs, a, seed, step0, n_iter, ref: 
     return x, out, cnt
 
 
-def pt_run_direct(x, out, T, W, betas, lo, hi, probs, a, seed, step0, n_iter, grid, d, S):
+def pt_run_direct(x, out, T, W, betas, lo, hi, probs, a, seed, step0, n_iter, grid, d, S,
+                  modes: int = 1):
     """n_iter sampler iterations with the direct likelihood; returns (x, out, counters)."""
     x, out, betas, lo, hi, probs = _pt_common(x, out, betas, lo, hi, probs)
     cnt = np.zeros(10 * T, dtype=np.int64)
     lib().oracle_pt_run_direct(_d(x), _d(out), T, W, _d(betas), _d(lo), _d(hi), _d(probs), a,
                                seed, step0, n_iter, grid["f0"], grid["df"], grid["n"],
-                               grid["t_obs"], _d(_c128(d).view(np.float64)), _d(_f64(S)), _l(cnt))
+                               grid["t_obs"], int(modes), _d(_c128(d).view(np.float64)),
+                               _d(_f64(S)), _l(cnt))
     return x, out, cnt
 
 

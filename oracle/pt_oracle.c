@@ -52,8 +52,8 @@
 void oracle_het_loglike(const double* th, long W, long E, const long* edges, double f0,
                         double df, double t_obs, const double* sum, const double* h0e,
                         double dd, double* out);
-void oracle_direct(const double* th, long W, double f0, double df, long n, double t_obs,
-                   const double* d, const double* S, double* out);
+void oracle_direct_hm(const double* th, long W, double f0, double df, long n, double t_obs,
+                      unsigned modes, const double* d, const double* S, double* out);
 
 enum { NPAR = 11 };
 enum { K_STRETCH = 0, K_SKY_ALL = 1, K_SKY_LON = 2, K_SKY_LAT = 3 };
@@ -204,6 +204,7 @@ typedef struct {
     const double *mu, *sigma;
     long n;                    /* direct: grid size, data d [3][n] complex, PSD S [3][n] */
     const double *d, *S;
+    unsigned modes;            /* direct: harmonic mode mask of the templates */
 } like_t;
 
 /* out[3][n] (lnL, <d|h>, <h|h>) for n points x[11][n] */
@@ -216,7 +217,7 @@ static void loglike(const like_t* L, const double* x, long n, double* out)
             oracle_het_loglike(th, n, L->E, L->edges, L->f0, L->df, L->t_obs, L->sum, L->h0e,
                                L->dd, out);
         else
-            oracle_direct(th, n, L->f0, L->df, L->n, L->t_obs, L->d, L->S, out);
+            oracle_direct_hm(th, n, L->f0, L->df, L->n, L->t_obs, L->modes, L->d, L->S, out);
         free(th);
         return;
     }
@@ -341,19 +342,21 @@ void oracle_pt_run_het(double* x, double* out, long T, long W, const double* bet
                        double f0, double df, double t_obs, const double* sum, const double* h0e,
                        double dd, long* counters)
 {
-    like_t L = {0, E, edges, f0, df, t_obs, sum, h0e, dd, NULL, NULL, 0, NULL, NULL};
+    like_t L = {0, E, edges, f0, df, t_obs, sum, h0e, dd, NULL, NULL, 0, NULL, NULL, 1u};
     for (long s = 0; s < n_iter; ++s)
         iteration(x, out, T, W, betas, lo, hi, probs, a, seed, step0 + (uint64_t)s, &L, counters);
 }
 
 /* n_iter iterations with the direct likelihood (Module 1 of Sec. III) on the grid
-   f_k = f0 + k df, k < n, data d [3][n] complex and PSD S [3][n]. */
+   f_k = f0 + k df, k < n, data d [3][n] complex and PSD S [3][n], templates of the
+   harmonic modes of the mask (the higher-mode posterior of Sec. III C uses this form). */
 void oracle_pt_run_direct(double* x, double* out, long T, long W, const double* betas,
                           const double* lo, const double* hi, const double* probs, double a,
                           uint64_t seed, uint64_t step0, long n_iter, double f0, double df,
-                          long n, double t_obs, const double* d, const double* S, long* counters)
+                          long n, double t_obs, unsigned modes, const double* d, const double* S,
+                          long* counters)
 {
-    like_t L = {2, 0, NULL, f0, df, t_obs, NULL, NULL, 0, NULL, NULL, n, d, S};
+    like_t L = {2, 0, NULL, f0, df, t_obs, NULL, NULL, 0, NULL, NULL, n, d, S, modes};
     for (long s = 0; s < n_iter; ++s)
         iteration(x, out, T, W, betas, lo, hi, probs, a, seed, step0 + (uint64_t)s, &L, counters);
 }
@@ -366,7 +369,7 @@ void oracle_pt_run_gauss(double* x, double* out, long T, long W, const double* b
                          uint64_t seed, uint64_t step0, long n_iter, const double* mu,
                          const double* sigma, long* counters, double* trace)
 {
-    like_t L = {1, 0, NULL, 0, 0, 0, NULL, NULL, 0, mu, sigma, 0, NULL, NULL};
+    like_t L = {1, 0, NULL, 0, 0, 0, NULL, NULL, 0, mu, sigma, 0, NULL, NULL, 1u};
     const long N = T * W;
     for (long s = 0; s < n_iter; ++s) {
         iteration(x, out, T, W, betas, lo, hi, probs, a, seed, step0 + (uint64_t)s, &L, counters);
@@ -378,6 +381,6 @@ void oracle_pt_run_gauss(double* x, double* out, long T, long W, const double* b
 void oracle_pt_gauss_loglike(const double* x, long n, const double* mu, const double* sigma,
                              double* out)
 {
-    like_t L = {1, 0, NULL, 0, 0, 0, NULL, NULL, 0, mu, sigma, 0, NULL, NULL};
+    like_t L = {1, 0, NULL, 0, 0, 0, NULL, NULL, 0, mu, sigma, 0, NULL, NULL, 1u};
     loglike(&L, x, n, out);
 }

@@ -51,6 +51,7 @@ struct SrcDesc {
     int64_t w_begin, w_end;  // walker range in theta/out
     int32_t E;
     int32_t tile_begin;      // first tile of this source
+    uint32_t modes;          // mode mask of the reference (1 = (2,2) only)
 };
 
 struct HetLaunch {
@@ -66,6 +67,7 @@ mbh_status fail(mbh_status s, const char* fmt, ...);
 mbh_status cuda_fail(cudaError_t e, const char* where);
 mbh_status check_grid(const mbh_grid* g);
 mbh_status check_device();
+mbh_status check_modes(uint32_t modes, mbh_precision precision);
 void direct_chunks(int64_t n, int64_t tiles, int64_t max_chunk, int64_t& chunk, int& nchunks);
 mbh_status direct_finish(double2* part, int nchunks, int64_t W, double dd, double* out,
                          cudaStream_t st);
@@ -142,6 +144,7 @@ struct mbh_data {
 
 struct mbh_ref {
     int device = -1;
+    uint32_t modes = 1u;             // harmonics of h0 and of the walkers' templates
     mbh_grid grid;
     int32_t E = 0;
     int64_t band[2] = {0, 0};

@@ -163,12 +163,12 @@ constexpr int kTplPerThread = 4;
 // kTplPerThread grid points, coalesced per channel.
 __global__ void __launch_bounds__(kTplThreads)
     template_f64_kernel(const double* __restrict__ theta, int64_t W, double f0, double df,
-                        int64_t n, double t_obs, double2* __restrict__ h)
+                        int64_t n, double t_obs, uint32_t modes, double2* __restrict__ h)
 {
     __shared__ Walker ws;
     for (int64_t wi = blockIdx.y; wi < W; wi += gridDim.y) {
         __syncthreads();
-        if (threadIdx.x == 0) walker_setup(theta, W, wi, ws);
+        if (threadIdx.x == 0) walker_setup(theta, W, wi, ws, modes);
         __syncthreads();
         const int64_t base = (int64_t)blockIdx.x * kTplThreads * kTplPerThread + threadIdx.x;
 #pragma unroll
@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(kTplThreads)
             const int64_t k = base + (int64_t)j * kTplThreads;
             if (k < n) {
                 cd v[3];
-                point_f64(ws, f0 + (double)k * df, t_obs, v);
+                point_model_f64(ws, f0 + (double)k * df, t_obs, v);
 #pragma unroll
                 for (int c = 0; c < 3; ++c)
                     h[((int64_t)wi * 3 + c) * n + k] = make_double2(v[c].re, v[c].im);
@@ -187,11 +187,11 @@ __global__ void __launch_bounds__(kTplThreads)
 
 namespace mbh {
 mbh_status launch_template_f64(const mbh_grid* g, const double* theta, int64_t W, double2* h,
-                               cudaStream_t st)
+                               cudaStream_t st, uint32_t modes = 1u)
 {
     const int64_t per_block = (int64_t)kTplThreads * kTplPerThread;
     dim3 grid((unsigned)((g->n + per_block - 1) / per_block), (unsigned)std::min<int64_t>(W, 65535));
-    template_f64_kernel<<<grid, kTplThreads, 0, st>>>(theta, W, g->f0, g->df, g->n, g->t_obs, h);
+    template_f64_kernel<<<grid, kTplThreads, 0, st>>>(theta, W, g->f0, g->df, g->n, g->t_obs, modes, h);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? MBH_OK : cuda_fail(e, "template kernel");
 }
@@ -210,6 +210,31 @@ extern "C" mbh_status template_batch(const mbh_grid* grid, const double* theta_d
     if (precision == MBH_MIXED)
         return launch_template_mixed(grid, theta_dev, W, (float2*)h_out_dev, (cudaStream_t)stream);
     return fail(MBH_EINVAL, "unknown precision %d", (int)precision);
+}
+
+namespace mbh {
+mbh_status check_modes(uint32_t modes, mbh_precision precision)
+{
+    if (modes == 0u || (modes & ~kHmAll)) return fail(MBH_EINVAL, "mode mask 0x%x: bits 0-5, not empty", modes);
+    if (modes != 1u && precision != MBH_FP64)
+        return fail(MBH_EINVAL, "higher modes are evaluated in float64 only (MBH_FP64)");
+    if (precision != MBH_FP64 && precision != MBH_MIXED) return fail(MBH_EINVAL, "unknown precision %d", (int)precision);
+    return MBH_OK;
+}
+}  // namespace mbh
+
+extern "C" mbh_status template_batch_hm(const mbh_grid* grid, const double* theta_dev, int64_t W,
+                                        uint32_t modes, mbh_precision precision, void* h_out_dev,
+                                        void* stream)
+{
+    if (mbh_status s = check_modes(modes, precision)) return s;
+    if (modes == 1u) return template_batch(grid, theta_dev, W, precision, h_out_dev, stream);
+    if (mbh_status s = check_grid(grid)) return s;
+    if (W < 0) return fail(MBH_EINVAL, "W < 0");
+    if (W == 0) return MBH_OK;
+    if (!theta_dev || !h_out_dev) return fail(MBH_EINVAL, "NULL buffer");
+    if (mbh_status s = check_device()) return s;
+    return launch_template_f64(grid, theta_dev, W, (double2*)h_out_dev, (cudaStream_t)stream, modes);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -343,7 +368,7 @@ __global__ void __launch_bounds__(kDirThreads)
     direct_fused_f64_kernel(const double* __restrict__ theta, int64_t W, double f0, double df,
                             double t_obs, const double2* __restrict__ wd,
                             const double* __restrict__ wv, int64_t n, int64_t chunk, int nchunks,
-                            double2* __restrict__ part)
+                            uint32_t modes, double2* __restrict__ part)
 {
     __shared__ Walker ws[T];
     __shared__ double2 acc[T][kDirThreads];
@@ -351,7 +376,7 @@ __global__ void __launch_bounds__(kDirThreads)
     const int64_t w0 = (int64_t)blockIdx.x * T;
     const int ch = blockIdx.y;
     const int nt = (int)std::min<int64_t>(T, W - w0);
-    if (threadIdx.x < nt) walker_setup(theta, W, w0 + threadIdx.x, ws[threadIdx.x]);
+    if (threadIdx.x < nt) walker_setup(theta, W, w0 + threadIdx.x, ws[threadIdx.x], modes);
 #pragma unroll
     for (int t = 0; t < T; ++t) acc[t][threadIdx.x] = make_double2(0.0, 0.0);
     __syncthreads();
@@ -367,7 +392,7 @@ __global__ void __launch_bounds__(kDirThreads)
         }
         for (int t = 0; t < nt; ++t) {
             cd h[3];
-            if (point_f64(ws[t], f, t_obs, h)) {
+            if (point_model_f64(ws[t], f, t_obs, h)) {
                 double2 s2 = acc[t][threadIdx.x];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
@@ -439,6 +464,24 @@ mbh_status launch_direct_finalize(const double2* part, int nchunks, int64_t W, d
 }
 }  // namespace mbh
 
+namespace {
+mbh_status direct_f64(const mbh_data* data, const double* theta_dev, int64_t W, uint32_t modes,
+                      double* out_dev, cudaStream_t st);
+}
+
+extern "C" mbh_status direct_loglike_batch_hm(const mbh_data* data, const double* theta_dev, int64_t W,
+                                              uint32_t modes, mbh_precision precision, double* out_dev,
+                                              void* stream)
+{
+    if (mbh_status s = check_modes(modes, precision)) return s;
+    if (modes == 1u) return direct_loglike_batch(data, theta_dev, W, precision, out_dev, stream);
+    if (!data) return fail(MBH_EINVAL, "data is NULL");
+    if (W < 0) return fail(MBH_EINVAL, "W < 0");
+    if (W == 0) return MBH_OK;
+    if (!theta_dev || !out_dev) return fail(MBH_EINVAL, "NULL buffer");
+    return direct_f64(data, theta_dev, W, modes, out_dev, (cudaStream_t)stream);
+}
+
 extern "C" mbh_status direct_loglike_batch(const mbh_data* data, const double* theta_dev, int64_t W,
                                            mbh_precision precision, double* out_dev, void* stream)
 {
@@ -449,6 +492,13 @@ extern "C" mbh_status direct_loglike_batch(const mbh_data* data, const double* t
     cudaStream_t st = (cudaStream_t)stream;
     if (precision == MBH_MIXED) return launch_direct_fused_mixed(data, theta_dev, W, out_dev, st);
     if (precision != MBH_FP64) return fail(MBH_EINVAL, "unknown precision %d", (int)precision);
+    return direct_f64(data, theta_dev, W, 1u, out_dev, st);
+}
+
+namespace {
+mbh_status direct_f64(const mbh_data* data, const double* theta_dev, int64_t W, uint32_t modes,
+                      double* out_dev, cudaStream_t st)
+{
     constexpr int T = 4;
     const int64_t tiles = (W + T - 1) / T;
     if (tiles > 0x7fffffff) return fail(MBH_EINVAL, "W too large");
@@ -461,11 +511,12 @@ extern "C" mbh_status direct_loglike_batch(const mbh_data* data, const double* t
     dim3 grid((unsigned)tiles, (unsigned)nchunks);
     direct_fused_f64_kernel<T><<<grid, kDirThreads, 0, st>>>(theta_dev, W, data->grid.f0, data->grid.df,
                                                             data->grid.t_obs, data->wd, data->wv,
-                                                            data->grid.n, chunk, nchunks, part);
+                                                            data->grid.n, chunk, nchunks, modes, part);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "direct_loglike_batch");
     return direct_finish(part, nchunks, W, data->dd, out_dev, st);
 }
+}  // namespace
 
 // ------------------------------------------------------------------------------------------
 // heterodyne: reference preparation
@@ -474,16 +525,16 @@ constexpr int kPrepThreads = 256;
 constexpr int64_t kPrepItem = 2048;   // grid points per (bin, sub-range) item
 
 __global__ void band_kernel(const double* __restrict__ theta0, double f0, double df, int64_t n,
-                            double t_obs, unsigned long long* __restrict__ kminmax)
+                            double t_obs, uint32_t modes, unsigned long long* __restrict__ kminmax)
 {
     __shared__ Walker w;
-    if (threadIdx.x == 0) walker_setup(theta0, 1, 0, w);
+    if (threadIdx.x == 0) walker_setup(theta0, 1, 0, w, modes);
     __syncthreads();
     unsigned long long lo = ~0ull, hi = 0ull;
     bool any = false;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
          k += (int64_t)gridDim.x * blockDim.x) {
-        if (support_f64(w, f0 + (double)k * df, t_obs)) {
+        if (support_model_f64(w, f0 + (double)k * df, t_obs)) {
             lo = std::min<unsigned long long>(lo, (unsigned long long)k);
             hi = std::max<unsigned long long>(hi, (unsigned long long)k);
             any = true;
@@ -503,11 +554,11 @@ __global__ void __launch_bounds__(kPrepThreads)
     prep_items_kernel(const double* __restrict__ theta0, double f0, double df, int64_t n,
                       double t_obs, const double2* __restrict__ wd, const double* __restrict__ wv,
                       const PrepItem* __restrict__ items, const double* __restrict__ fb,
-                      double* __restrict__ part)
+                      uint32_t modes, double* __restrict__ part)
 {
     __shared__ Walker w;
     __shared__ double sm[32 * 18];
-    if (threadIdx.x == 0) walker_setup(theta0, 1, 0, w);
+    if (threadIdx.x == 0) walker_setup(theta0, 1, 0, w, modes);
     __syncthreads();
     const PrepItem it = items[blockIdx.x];
     const double fbin = fb[it.bin];
@@ -517,7 +568,7 @@ __global__ void __launch_bounds__(kPrepThreads)
     for (int64_t k = it.k0 + threadIdx.x; k < it.k1; k += kPrepThreads) {
         const double f = f0 + (double)k * df;
         cd h[3];
-        if (!point_f64(w, f, t_obs, h)) continue;
+        if (!point_model_f64(w, f, t_obs, h)) continue;
         const double x = f - fbin;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -556,15 +607,15 @@ __global__ void prep_finalize_kernel(const double* __restrict__ part,
 // Reference template at the bin edges: h0 and 1/h0 (0 where h0 = 0), plus the factored form
 // used by the mixed kernel (float64 large phase and the float32 transfer).
 __global__ void edge_ref_kernel(const double* __restrict__ theta0, double t_obs,
-                                const double* __restrict__ fe, int n_edges,
+                                const double* __restrict__ fe, int n_edges, uint32_t modes,
                                 double2* __restrict__ h0e, double2* __restrict__ h0inv)
 {
     __shared__ Walker w;
-    if (threadIdx.x == 0) walker_setup(theta0, 1, 0, w);
+    if (threadIdx.x == 0) walker_setup(theta0, 1, 0, w, modes);
     __syncthreads();
     for (int e = threadIdx.x; e < n_edges; e += blockDim.x) {
         cd h[3];
-        point_f64(w, fe[e], t_obs, h);
+        point_model_f64(w, fe[e], t_obs, h);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             h0e[e * 3 + c] = make_double2(h[c].re, h[c].im);
@@ -602,7 +653,15 @@ std::vector<int64_t> make_edges(int64_t kmin, int64_t kmax, int nbins, double f0
 extern "C" mbh_status het_prepare_reference(const mbh_data* data, const double* theta0_host,
                                             int32_t n_bins, void* stream, mbh_ref** out)
 {
+    return het_prepare_reference_hm(data, theta0_host, n_bins, 1u, stream, out);
+}
+
+extern "C" mbh_status het_prepare_reference_hm(const mbh_data* data, const double* theta0_host,
+                                               int32_t n_bins, uint32_t modes, void* stream,
+                                               mbh_ref** out)
+{
     if (!out) return fail(MBH_EINVAL, "out is NULL");
+    if (modes == 0u || (modes & ~kHmAll)) return fail(MBH_EINVAL, "mode mask 0x%x: bits 0-5, not empty", modes);
     *out = nullptr;
     if (!data || !theta0_host) return fail(MBH_EINVAL, "NULL argument");
     if (n_bins < 1 || n_bins > kMaxBins) return fail(MBH_EINVAL, "n_bins %d outside [1, %d]", n_bins, kMaxBins);
@@ -613,6 +672,7 @@ extern "C" mbh_status het_prepare_reference(const mbh_data* data, const double* 
     cudaStream_t st = (cudaStream_t)stream;
     const mbh_grid& g = data->grid;
     mbh_ref* R = new mbh_ref();
+    R->modes = modes;
     R->grid = g;
     R->dd = data->dd;
     std::memcpy(R->theta0, theta0_host, sizeof(R->theta0));
@@ -629,7 +689,7 @@ extern "C" mbh_status het_prepare_reference(const mbh_data* data, const double* 
     if (e == cudaSuccess) e = cudaMemsetAsync(kmm, 0xff, sizeof(unsigned long long), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(kmm + 1, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return bail(e, "prepare setup");
-    band_kernel<<<grid_blocks(g.n, 256), 256, 0, st>>>(R->theta0_dev, g.f0, g.df, g.n, g.t_obs, kmm);
+    band_kernel<<<grid_blocks(g.n, 256), 256, 0, st>>>(R->theta0_dev, g.f0, g.df, g.n, g.t_obs, modes, kmm);
     unsigned long long h_kmm[2];
     e = cudaMemcpyAsync(h_kmm, kmm, sizeof h_kmm, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaFreeAsync(kmm, st);
@@ -682,11 +742,12 @@ extern "C" mbh_status het_prepare_reference(const mbh_data* data, const double* 
     if (e != cudaSuccess) return bail(e, "prepare upload");
 
     prep_items_kernel<<<nitems, kPrepThreads, 0, st>>>(R->theta0_dev, g.f0, g.df, g.n, g.t_obs, data->wd,
-                                                        data->wv, d_items, d_fb, d_part);
+                                                        data->wv, d_items, d_fb, modes, d_part);
     prep_finalize_kernel<<<(E * 18 + 255) / 256, 256, 0, st>>>(d_part, d_ib, E, R->summary);
-    edge_ref_kernel<<<1, 256, 0, st>>>(R->theta0_dev, g.t_obs, R->fe, E + 1, R->h0e, R->h0inv);
+    edge_ref_kernel<<<1, 256, 0, st>>>(R->theta0_dev, g.t_obs, R->fe, E + 1, modes, R->h0e, R->h0inv);
     e = cudaGetLastError();
-    if (e == cudaSuccess) e = prepare_mixed_tables(R, st);
+    // the mixed kernel's factored reference is a (2,2)-mode construction
+    if (e == cudaSuccess && modes == 1u) e = prepare_mixed_tables(R, st);
     if (e == cudaSuccess) e = cudaFreeAsync(d_items, st);
     if (e == cudaSuccess) e = cudaFreeAsync(d_ib, st);
     if (e == cudaSuccess) e = cudaFreeAsync(d_fb, st);
@@ -699,6 +760,7 @@ extern "C" mbh_status het_prepare_reference(const mbh_data* data, const double* 
 }
 
 extern "C" int32_t mbh_ref_bins(const mbh_ref* ref) { return ref ? ref->E : -1; }
+extern "C" uint32_t mbh_ref_modes(const mbh_ref* ref) { return ref ? ref->modes : 0u; }
 
 extern "C" mbh_status mbh_ref_read(const mbh_ref* ref, int64_t* edges_host, double* summary_host,
                                    double* h0_edges_host, double* dd_host)
@@ -742,7 +804,7 @@ __global__ void __launch_bounds__(BLOCK)
         const int64_t wi = S.w_begin + (int64_t)(tile - S.tile_begin) * WPB + lw;
         const bool active = wi < S.w_end;
         __syncthreads();
-        if (lane == 0 && active) walker_setup(L.theta, L.W, wi, ws[lw]);
+        if (lane == 0 && active) walker_setup(L.theta, L.W, wi, ws[lw], S.modes);
         __syncthreads();
         const int E = S.E;
         double dh = 0.0, hh = 0.0;
@@ -753,7 +815,7 @@ __global__ void __launch_bounds__(BLOCK)
             cd rr[3] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
             if (active && e <= E) {
                 cd h[3];
-                if (point_f64(ws[lw], S.fe[e], S.t_obs, h)) {
+                if (point_model_f64(ws[lw], S.fe[e], S.t_obs, h)) {
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         const double2 iv = S.h0inv[e * 3 + c];

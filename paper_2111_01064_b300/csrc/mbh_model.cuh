@@ -50,7 +50,19 @@ struct Walker {
     double k[3];            // propagation direction
     double Pp[6], Pc[6];    // polarisation tensors (xx, xy, xz, yy, yz, zz)
     double Kp[2], Kc[2];    // mode factors of h+ and hx (complex)
+    uint32_t modes;         // bit b: mode (kHmL[b], kHmM[b]); 1 = the (2,2) mode alone (W0)
+    double hk[6][4];        // per mode: K+ and Kx (re, im) times H_lm's constant and sqrt(2/m)
 };
+
+// Higher harmonics ("W0-HM", Sec. II A, Eqs. 7-9): mode (l, m) uses the (2,2) phase at
+// f2 = 2f/m scaled by m/2, so t_lm(f) = t_22(f2) (Eq. 8), the (2,2) amplitude at f2 times
+// sqrt(2/m) (stationary phase for harmonic m of the same orbital phase) times the leading
+// post-Newtonian mode factor H_lm = c_lm x^{p_lm} (Blanchet, Faye, Iyer & Sinha 2008),
+// x = v^2 with v = (pi M f2)^{1/3}; each mode has its own response at t_lm (Eq. 9).
+constexpr int kHmModes = 6;
+__host__ __device__ constexpr int hm_m(int b) { return b == 0 ? 2 : b == 1 ? 3 : b == 2 ? 4 : b == 3 ? 1 : b == 4 ? 2 : 3; }
+__host__ __device__ constexpr int hm_vpow(int b) { return b == 0 ? 0 : b == 1 ? 1 : b == 2 ? 2 : b == 3 ? 1 : b == 4 ? 2 : 3; }
+constexpr uint32_t kHmAll = 0x3Fu;
 
 // TaylorF2-type phase and its frequency derivative from v and ln v (Horner form).
 __device__ __forceinline__ void pn_phase_f64(const Walker& w, double v, double lnv, double& psi,
@@ -70,8 +82,10 @@ __device__ __forceinline__ void pn_phase_f64(const Walker& w, double v, double l
 // Parameter derivation (Sec. II A): masses, PN coefficients with the 1.5PN spin-orbit and
 // 2PN spin-spin terms, taper/cut frequencies, f_max = argmax f^2 A, distance scaling,
 // wave frame and mode factors.  theta is SoA [11][W].
+__device__ inline void hm_setup(Walker& w, double q, double iota, double phi);
+
 __device__ inline void walker_setup(const double* __restrict__ theta, int64_t W, int64_t i,
-                                    Walker& w)
+                                    Walker& w, uint32_t modes = 1u)
 {
     const double mt = theta[kMT * W + i], q = theta[kQ * W + i];
     const double a1 = theta[kA1 * W + i], a2 = theta[kA2 * W + i];
@@ -168,6 +182,82 @@ __device__ inline void walker_setup(const double* __restrict__ theta, int64_t W,
     w.Kp[1] = ap * s2f;
     w.Kc[0] = -ac * s2f;
     w.Kc[1] = ac * c2f;
+    w.modes = modes;
+    if (modes != 1u) hm_setup(w, q, iota, phi);
+}
+
+// Spin-weighted harmonics -2Y_{l,+-m}(iota, .) without the e^{+-i m phi} factor, written out in
+// C = cos(iota/2), S = sin(iota/2) for the six modes: y[0] = -2Y_{l,m}, y[1] = -2Y_{l,-m}.
+__device__ inline void hm_ylm(int b, double C, double S, double y[2])
+{
+    const double rpi = 0.564189583547756286948079451560772586;   // 1/sqrt(pi)
+    const double C2 = C * C, S2 = S * S;
+    switch (b) {
+    case 0:   // (2, +-2)
+        y[0] = 0.5 * 2.236067977499789696 * rpi * C2 * C2;
+        y[1] = 0.5 * 2.236067977499789696 * rpi * S2 * S2;
+        break;
+    case 1:   // (3, +-3)
+        y[0] = -0.5 * 6.480740698407860230 * rpi * C2 * C2 * C * S;
+        y[1] = 0.5 * 6.480740698407860230 * rpi * C * S * S2 * S2;
+        break;
+    case 2:   // (4, +-4)
+        y[0] = 3.0 * 2.645751311064590590 * rpi * C2 * C2 * C2 * S2;
+        y[1] = 3.0 * 2.645751311064590590 * rpi * C2 * S2 * S2 * S2;
+        break;
+    case 3:   // (2, +-1)
+        y[0] = 2.236067977499789696 * rpi * C2 * C * S;
+        y[1] = 2.236067977499789696 * rpi * C * S2 * S;
+        break;
+    case 4:   // (3, +-2)
+        y[0] = 0.5 * 2.645751311064590590 * rpi * C2 * C2 * (C2 - 5.0 * S2);
+        y[1] = 0.5 * 2.645751311064590590 * rpi * S2 * S2 * (5.0 * C2 - S2);
+        break;
+    default:  // (4, +-3)
+        y[0] = -1.5 * 3.741657386773941386 * rpi * C2 * C2 * C * S * (C2 - 3.0 * S2);
+        y[1] = 1.5 * 3.741657386773941386 * rpi * C * S * S2 * S2 * (3.0 * C2 - S2);
+        break;
+    }
+}
+
+// Per-mode polarisation factors, positive frequencies, in the convention of the (2,2) factors
+// above: K+ = (Y_lm + (-1)^l conj(Y_{l,-m}))/2, Kx = i (Y_lm - (-1)^l conj(Y_{l,-m}))/2, both
+// proportional to e^{i m phi}; folded with H_lm's constant c_lm and sqrt(2/m).
+__device__ inline void hm_setup(Walker& w, double q, double iota, double phi)
+{
+    const double eta = q / ((1.0 + q) * (1.0 + q)), delta = (1.0 - q) / (1.0 + q);
+    double S, C;
+    sincos(0.5 * iota, &S, &C);
+#pragma unroll
+    for (int b = 0; b < kHmModes; ++b) {
+        const int m = hm_m(b), l = (b == 0 || b == 3) ? 2 : (b == 1 || b == 4) ? 3 : 4;
+        double y[2];
+        hm_ylm(b, C, S, y);
+        const double sg = (l & 1) ? -1.0 : 1.0;
+        const double a = 0.5 * (y[0] + sg * y[1]), bx = 0.5 * (y[0] - sg * y[1]);
+        // c_lm: 22: 1; 33: -(3i/4) sqrt(15/14) delta; 44: -(8/9) sqrt(5/7)(1 - 3 eta);
+        // 21: (i/3) delta; 32: (1/3) sqrt(5/7)(1 - 3 eta); 43: -(9i/(4 sqrt 70)) delta (1 - 2 eta)
+        double cr = 0.0, cim = 0.0;
+        switch (b) {
+        case 0: cr = 1.0; break;
+        case 1: cim = -0.75 * 1.035098339013531 * delta; break;
+        case 2: cr = -8.0 / 9.0 * 0.845154254728516 * (1.0 - 3.0 * eta); break;
+        case 3: cim = delta / 3.0; break;
+        case 4: cr = 1.0 / 3.0 * 0.845154254728516 * (1.0 - 3.0 * eta); break;
+        default: cim = -9.0 / (4.0 * 8.366600265340756) * delta * (1.0 - 2.0 * eta); break;
+        }
+        const double sc = sqrt(2.0 / m);
+        cr *= sc;
+        cim *= sc;
+        double sm, cm;
+        sincos(m * phi, &sm, &cm);
+        // K+ = a e^{i m phi} c, Kx = i bx e^{i m phi} c
+        const double er = cm * cr - sm * cim, ei = cm * cim + sm * cr;
+        w.hk[b][0] = a * er;
+        w.hk[b][1] = a * ei;
+        w.hk[b][2] = -bx * ei;
+        w.hk[b][3] = bx * er;
+    }
 }
 
 struct cd { double re, im; };
@@ -191,7 +281,8 @@ __device__ __forceinline__ double nPn(const double* P, const double* n)
 // (i, j) contributes g = -i x e^{-i pi f (L + k.(o_i + o_j))} F with x = pi f L and
 // F = n.(P+ K+ + Px Kx).n; link i->j adds sinc(x (1 - k.n)), link j->i sinc(x (1 + k.n)).
 // First-generation TDI with D = e^{-2 i x}, then A, E, T.
-__device__ inline void transfer_f64(const Walker& w, double f, double sa, double ca, cd T[3])
+__device__ inline void transfer_f64(const Walker& w, double f, double sa, double ca, const double* Kp,
+                                    const double* Kc, cd T[3])
 {
     const double rho = kArmSec / kSqrt3;
     // sin/cos(alpha - 2 pi i/3): cos(2pi/3) = -1/2, sin(2pi/3) = sqrt3/2
@@ -217,7 +308,7 @@ __device__ inline void transfer_f64(const Walker& w, double f, double sa, double
             ko += w.k[m] * (o[i][m] + o[j][m]);
         }
         const double np = nPn(w.Pp, n), nc = nPn(w.Pc, n);
-        cd F = {np * w.Kp[0] + nc * w.Kc[0], np * w.Kp[1] + nc * w.Kc[1]};
+        cd F = {np * Kp[0] + nc * Kc[0], np * Kp[1] + nc * Kc[1]};
         double sph, cph;
         sincos(kPi * f * (kArmSec + ko), &sph, &cph);
         // -i x e^{-i ph} = -x (sin ph + i cos ph)
@@ -260,12 +351,53 @@ __device__ inline bool point_f64(const Walker& w, double f, double t_obs, cd h[3
     double sP, cP;
     sincos(Phi, &sP, &cP);
     cd T[3];
-    transfer_f64(w, f, sa, ca, T);
+    transfer_f64(w, f, sa, ca, w.Kp, w.Kc, T);
     const cd e = {amp * cP, -amp * sP};
     h[0] = cmul(e, T[0]);
     h[1] = cmul(e, T[1]);
     h[2] = cmul(e, T[2]);
     return true;
+}
+
+// Template of the walker's modes at f, float64: per mode the (2,2) model at f2 = 2f/m (phase
+// scaled by m/2, amplitude by v^{p_lm}), the orbit and the transfer at t_lm(f), summed.
+// Returns false (and zeros) when no mode is in its support.
+__device__ inline bool point_hm_f64(const Walker& w, double f, double t_obs, cd h[3])
+{
+    h[0] = h[1] = h[2] = {0.0, 0.0};
+    bool any = false;
+    for (int b = 0; b < kHmModes; ++b) {
+        if (!(w.modes & (1u << b))) continue;
+        const int m = hm_m(b);
+        const double f2 = 2.0 * f / m;
+        const double v = cbrt(w.piM * f2);
+        double psi_pn, dpsi_pn;
+        pn_phase_f64(w, v, log(v), psi_pn, dpsi_pn);
+        const double t = w.tref + (dpsi_pn - w.dpsi_max) * kInvTwoPi;
+        if (!(f2 <= w.fcut) || t < 0.0 || t > t_obs) continue;
+        any = true;
+        double amp = w.amp * exp(-f2 * f2 * w.inv_fc2) / (v * v * v * sqrt(v));
+        for (int j = 0; j < hm_vpow(b); ++j) amp *= v;
+        double sa, ca;
+        sincos(kTwoPi * t / kYear, &sa, &ca);
+        const double kc = kAUSec * (w.k[0] * ca + w.k[1] * sa);
+        const double Phi = 0.5 * m * (kTwoPi * f2 * w.tref + psi_pn - w.psi_max - (f2 - w.fmax) * w.dpsi_max) +
+                           kTwoPi * f * kc;
+        double sP, cP;
+        sincos(Phi, &sP, &cP);
+        cd T[3];
+        transfer_f64(w, f, sa, ca, &w.hk[b][0], &w.hk[b][2], T);
+        const cd e = {amp * cP, -amp * sP};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) h[c] = cadd(h[c], cmul(e, T[c]));
+    }
+    return any;
+}
+
+// The walker's template, whatever its modes (W0 for the (2,2) mode alone).
+__device__ __forceinline__ bool point_model_f64(const Walker& w, double f, double t_obs, cd h[3])
+{
+    return w.modes == 1u ? point_f64(w, f, t_obs, h) : point_hm_f64(w, f, t_obs, h);
 }
 
 // Support test alone (band search): t(f) and the cut, float64.
@@ -276,6 +408,15 @@ __device__ inline bool support_f64(const Walker& w, double f, double t_obs)
     pn_phase_f64(w, v, log(v), psi_pn, dpsi_pn);
     const double t = w.tref + (dpsi_pn - w.dpsi_max) * kInvTwoPi;
     return (f <= w.fcut) && t >= 0.0 && t <= t_obs;
+}
+
+// Some mode of the walker is in its support at f (the (2,2) mode at f2 = 2f/m).
+__device__ inline bool support_model_f64(const Walker& w, double f, double t_obs)
+{
+    if (w.modes == 1u) return support_f64(w, f, t_obs);
+    for (int b = 0; b < kHmModes; ++b)
+        if ((w.modes & (1u << b)) && support_f64(w, 2.0 * f / hm_m(b), t_obs)) return true;
+    return false;
 }
 
 }  // namespace mbh

@@ -417,6 +417,7 @@ struct mbh_pt {
     const mbh_ref* ref = nullptr;
     const mbh_data* data = nullptr;
     mbh_het_config cfg{8, 128, 0};
+    uint32_t modes = 1u;     // direct likelihood: harmonic modes of the templates
     int Wp = 0;
     double* res = nullptr;   // device [14] for mbh_pt_best
     cudaGraphExec_t exec = nullptr;
@@ -453,7 +454,7 @@ mbh_status likelihood(mbh_pt* P, int64_t n, double* dst, cudaStream_t st)
         const int64_t off[2] = {0, n};
         return het_loglike_batch_cfg(&P->ref, off, 1, P->A.theta, P->precision, &P->cfg, dst, st);
     }
-    return direct_loglike_batch(P->data, P->A.theta, n, P->precision, dst, st);
+    return direct_loglike_batch_hm(P->data, P->A.theta, n, P->modes, P->precision, dst, st);
 }
 
 mbh_status rescore(mbh_pt* P, cudaStream_t st)
@@ -560,6 +561,11 @@ extern "C" mbh_status mbh_pt_create(const mbh_pt_opts* o, const mbh_ref* ref, co
     for (int t = 0; t < o->ntemps; ++t)
         if (!(betas_host[t] >= 0.0) || !std::isfinite(betas_host[t])) return fail(MBH_EINVAL, "betas must be finite and >= 0");
     if (o->precision != MBH_FP64 && o->precision != MBH_MIXED) return fail(MBH_EINVAL, "unknown precision");
+    const uint32_t modes = o->modes ? o->modes : 1u;
+    if (data)
+        if (mbh_status s = check_modes(modes, o->precision)) return s;
+    if (ref && ref->modes != 1u && o->precision != MBH_FP64)
+        return fail(MBH_EINVAL, "higher-mode reference: MBH_FP64 only");
     if (mbh_status s = check_device()) return s;
     int dev = -1;
     cudaGetDevice(&dev);
@@ -572,6 +578,7 @@ extern "C" mbh_status mbh_pt_create(const mbh_pt_opts* o, const mbh_ref* ref, co
     P->ref = ref;
     P->data = data;
     P->precision = o->precision;
+    P->modes = modes;
     if (o->het_config.threads_per_walker) P->cfg = o->het_config;
     PtArgs& A = P->A;
     A.T = o->ntemps;

@@ -110,6 +110,9 @@ mbh_status make_plan(const mbh_ref* const* refs, const int64_t* offsets, int32_t
             S.dd = R->dd;
             S.t_obs = R->grid.t_obs;
             S.E = R->E;
+            S.modes = R->modes;
+            if (R->modes != 1u && prec != MBH_FP64)
+                return fail(MBH_EINVAL, "source %d has higher modes: MBH_FP64 only", s);
             S.w_begin = offsets[s];
             S.w_end = offsets[s + 1];
             S.tile_begin = (int32_t)tiles;

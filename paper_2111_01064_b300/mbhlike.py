@@ -65,7 +65,8 @@ class PTOpts(C.Structure):
     """mbh_pt_opts (see include/mbhlike.h)."""
     _fields_ = [("ntemps", C.c_int32), ("walkers", C.c_int32), ("a", C.c_double),
                 ("probs", C.c_double * 4), ("lo", C.c_double * 11), ("hi", C.c_double * 11),
-                ("seed", C.c_uint64), ("precision", C.c_int), ("het_config", HetConfig)]
+                ("seed", C.c_uint64), ("precision", C.c_int), ("het_config", HetConfig),
+                ("modes", C.c_uint32)]
 
 
 def grid_struct(g: dict) -> Grid:
@@ -122,6 +123,10 @@ def lib() -> C.CDLL:
         "mbh_server_reset_stats": (C.c_int, [vp]),
         "mbh_server_free": (None, [vp]),
         "mbh_selftest_math": (C.c_int, [i32, vp, vp, i64, vp, vp, vp]),
+        "mbh_ref_modes": (C.c_uint32, [vp]),
+        "template_batch_hm": (C.c_int, [gp, vp, i64, C.c_uint32, C.c_int, vp, vp]),
+        "direct_loglike_batch_hm": (C.c_int, [vp, vp, i64, C.c_uint32, C.c_int, vp, vp]),
+        "het_prepare_reference_hm": (C.c_int, [vp, dp, i32, C.c_uint32, vp, C.POINTER(vp)]),
         "mbh_pt_create": (C.c_int, [C.POINTER(PTOpts), vp, vp, dp, vp, vp, C.POINTER(vp)]),
         "mbh_pt_run": (C.c_int, [vp, i64, i32, vp]),
         "mbh_pt_state": (C.c_int, [vp, vp, vp, vp]),
@@ -199,7 +204,8 @@ def mbh_noise_aet(grid: dict, z: torch.Tensor, psd: torch.Tensor, out: torch.Ten
 
 
 def template_batch(grid: dict, theta: torch.Tensor, precision="fp64", out: torch.Tensor | None = None,
-                   stream=None) -> torch.Tensor:
+                   stream=None, modes: int = 1) -> torch.Tensor:
+    """Templates (W, 3, n) on the grid; `modes` selects harmonic modes (1 = the (2,2) mode)."""
     _require_cuda()
     p = _prec(precision)
     W = theta.shape[1]
@@ -208,8 +214,8 @@ def template_batch(grid: dict, theta: torch.Tensor, precision="fp64", out: torch
     if out is None:
         out = torch.empty((W, 3, n), dtype=dt, device="cuda")
     g = grid_struct(grid)
-    _check(lib().template_batch(C.byref(g), _dev(theta, torch.float64, (11, W), "theta"), W, p,
-                                _dev(out, dt, (W, 3, n), "out"), _stream(stream)))
+    _check(lib().template_batch_hm(C.byref(g), _dev(theta, torch.float64, (11, W), "theta"), W,
+                                   int(modes), p, _dev(out, dt, (W, 3, n), "out"), _stream(stream)))
     return out
 
 
@@ -259,6 +265,18 @@ def direct_loglike_batch(data: Data, theta: torch.Tensor, precision="fp64",
     return out
 
 
+def direct_loglike_batch_hm(data: Data, theta: torch.Tensor, modes: int, precision="fp64",
+                            out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Direct likelihood of templates summed over the harmonic modes of the mask."""
+    W = theta.shape[1]
+    if out is None:
+        out = torch.empty((3, W), dtype=torch.float64, device="cuda")
+    _check(lib().direct_loglike_batch_hm(data.handle, _dev(theta, torch.float64, (11, W), "theta"), W,
+                                         int(modes), _prec(precision),
+                                         _dev(out, torch.float64, (3, W), "out"), _stream(stream)))
+    return out
+
+
 def direct_loglike_stored(data: Data, h: torch.Tensor, precision="fp64",
                           out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     p = _prec(precision)
@@ -289,11 +307,11 @@ def direct_loglike_stored_noalloc(data: Data, h: torch.Tensor, precision="fp64",
 class Ref:
     """mbh_ref handle: one heterodyne reference (summary data resident on the device)."""
 
-    def __init__(self, data: Data, theta0, n_bins: int, stream=None):
+    def __init__(self, data: Data, theta0, n_bins: int, stream=None, modes: int = 1):
         th = np.ascontiguousarray(np.asarray(theta0, dtype=np.float64).reshape(11))
         h = vp()
-        _check(lib().het_prepare_reference(data.handle, th.ctypes.data_as(dp), int(n_bins),
-                                           _stream(stream), C.byref(h)))
+        _check(lib().het_prepare_reference_hm(data.handle, th.ctypes.data_as(dp), int(n_bins),
+                                              int(modes), _stream(stream), C.byref(h)))
         self.handle = h
         self.grid = dict(data.grid)
         self.theta0 = th.copy()
@@ -301,6 +319,10 @@ class Ref:
     @property
     def bins(self) -> int:
         return int(lib().mbh_ref_bins(self.handle))
+
+    @property
+    def modes(self) -> int:
+        return int(lib().mbh_ref_modes(self.handle))
 
     def read(self) -> dict:
         E = self.bins
@@ -325,8 +347,8 @@ class Ref:
             pass
 
 
-def het_prepare_reference(data: Data, theta0, n_bins: int, stream=None) -> Ref:
-    return Ref(data, theta0, n_bins, stream)
+def het_prepare_reference(data: Data, theta0, n_bins: int, stream=None, modes: int = 1) -> Ref:
+    return Ref(data, theta0, n_bins, stream, modes)
 
 
 def het_loglike_batch(refs: Sequence[Ref], offsets, theta: torch.Tensor, precision="mixed",
@@ -512,7 +534,7 @@ class PTSampler:
     def __init__(self, x: torch.Tensor, betas, lo, hi, *, ref: Ref | None = None,
                  data: Data | None = None, walkers: int, a: float = 2.0,
                  probs=(0.85, 0.04, 0.03, 0.08), seed: int = 0, precision="mixed",
-                 cfg: HetConfig | None = None, stream=None):
+                 cfg: HetConfig | None = None, modes: int = 1, stream=None):
         _require_cuda()
         betas = np.ascontiguousarray(np.asarray(betas, dtype=np.float64))
         T = betas.size
@@ -523,6 +545,7 @@ class PTSampler:
         o.hi[:] = [float(v) for v in hi]
         o.seed, o.precision = int(seed), _prec(precision)
         o.het_config = cfg if cfg is not None else HetConfig(0, 0, 0)
+        o.modes = int(modes)
         self.T, self.W = T, int(walkers)
         self.ref, self.data = ref, data   # keep them alive
         h = vp()

@@ -1,0 +1,152 @@
+"""Higher harmonics (Sec. II A, Eqs. 7-9; stand-in "W0-HM") on the GPU against the oracle:
+templates, the direct likelihood, the heterodyne reference (band, edges, summary data) and
+likelihood, and the Module-1 sampler with higher-mode templates, all float64.  Tolerances as
+in the (2,2) parity tests: templates within 1e-8 of max|h|; lnL within 1e-6 of the size of
+the terms; edges bit-exact.  Mixed precision with higher modes is refused (MBH_EINVAL)."""
+import math
+
+import numpy as np
+import pytest
+
+import mbh_inputs as I
+
+pytestmark = pytest.mark.gpu
+ALL = 0x3F
+
+
+@pytest.fixture(scope="module")
+def M():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2111_01064_b300 import mbhlike
+    mbhlike.lib()
+    return mbhlike
+
+
+@pytest.fixture(scope="module")
+def WL(M):
+    from paper_2111_01064_b300 import workloads
+    return workloads
+
+
+@pytest.fixture(scope="module")
+def case(oracle, M, WL):
+    """Higher-mode injection (q = 0.35, M_T = 5e5) in noise on the 30-day record; each side
+    builds its own data from the shared draws."""
+    import torch
+    g = I.grid_month()
+    th_raw, snr = I.draw_source(I.rng(0), g["t_obs"], mt_range=(5e5, 5e5))
+    th_raw[I.I_Q] = 0.35
+    z = I.noise_normals(I.rng(0, 100), g["n"])
+    S = oracle.psd(oracle.freqs(g))
+    th_o = I.with_distance(th_raw, oracle.snr_distance(th_raw, g, snr, S))
+    d_o = oracle.template_hm(th_o, oracle.freqs(g), g["t_obs"], ALL) + oracle.noise(S, g["df"], z)
+    psd = M.mbh_psd_aet(g)
+    th_g = th_o.copy()   # the same injection parameters on both sides
+    d_g = M.template_batch(g, WL.to_dev(th_g.reshape(11, 1)), "fp64", modes=ALL)[0].contiguous()
+    M.mbh_noise_aet(g, torch.from_numpy(np.ascontiguousarray(z)).cuda(), psd, out=d_g, accumulate=True)
+    data = M.Data(g, d_g, psd)
+    walk = WL.walkers(th_o, 24, 0, lo=1e-5, hi=1e-3)
+    return dict(g=g, S=S, th=th_o, d_o=d_o, data=data, walk=walk,
+                dd_o=oracle.inner(d_o, d_o, S, g["df"]))
+
+
+def _close(gpu, ora, dd, rel=1e-6):
+    scale = 0.5 * (dd + np.abs(ora[2]) + 2 * np.abs(ora[1]))
+    err = np.abs(gpu[0] - ora[0])
+    assert np.all(err <= rel * scale), (err / scale).max()
+
+
+@pytest.mark.parametrize("modes", [ALL, 0x2, 0x20, 0x9])
+def test_templates(M, WL, oracle, case, modes):
+    g, th = case["g"], case["walk"][:, :4]
+    h_g = M.template_batch(g, WL.to_dev(th), "fp64", modes=modes).cpu().numpy()
+    h_o = oracle.template_batch(th, g, modes)
+    assert np.abs(h_o).max() > 0
+    assert np.abs(h_g - h_o).max() <= 1e-8 * np.abs(h_o).max()
+
+
+def test_single_mode_mask_is_w0(M, WL, case):
+    g, th = case["g"], WL.to_dev(case["walk"][:, :3])
+    a = M.template_batch(g, th, "fp64", modes=1).cpu().numpy()
+    b = M.template_batch(g, th, "fp64").cpu().numpy()
+    assert np.array_equal(a, b)
+
+
+def test_direct(M, WL, oracle, case):
+    th = case["walk"]
+    out_g = M.direct_loglike_batch_hm(case["data"], WL.to_dev(th), ALL).cpu().numpy()
+    out_o = oracle.direct(th, case["g"], case["d_o"], case["S"], ALL)
+    _close(out_g, out_o, case["dd_o"])
+    # the (2,2)-only model fits this data worse than the full one at the injection
+    o22 = M.direct_loglike_batch_hm(case["data"], WL.to_dev(case["th"].reshape(11, 1)), 1).cpu().numpy()
+    oall = M.direct_loglike_batch_hm(case["data"], WL.to_dev(case["th"].reshape(11, 1)), ALL).cpu().numpy()
+    assert o22[0, 0] < oall[0, 0] - 1.0
+
+
+def test_het_reference_and_likelihood(M, WL, oracle, case):
+    ref_g = M.het_prepare_reference(case["data"], case["th"], 64, modes=ALL)
+    ref_o = oracle.het_prepare(case["th"], case["g"], case["d_o"], case["S"], 64, ALL)
+    assert ref_g.modes == ALL
+    rg = ref_g.read()
+    assert np.array_equal(rg["edges"], ref_o["edges"])
+    np.testing.assert_allclose(rg["summary"], ref_o["summary"], rtol=1e-7,
+                               atol=1e-9 * np.abs(ref_o["summary"]).max())
+    th = case["walk"]
+    out_g = M.het_loglike_batch([ref_g], [0, th.shape[1]], WL.to_dev(th), "fp64").cpu().numpy()
+    out_o = oracle.het_loglike(th, ref_o)
+    _close(out_g, out_o, case["dd_o"])
+    # band of all modes covers the (2,2) band
+    _, band22 = oracle.het_edges(case["th"], case["g"], 64)
+    assert rg["edges"][0] <= band22[0] and rg["edges"][-1] >= band22[1]
+
+
+def test_mixed_with_higher_modes_refused(M, WL, case):
+    th = WL.to_dev(case["walk"][:, :2])
+    with pytest.raises(M.MBHError):
+        M.template_batch(case["g"], th, "mixed", modes=ALL)
+    with pytest.raises(M.MBHError):
+        M.direct_loglike_batch_hm(case["data"], th, ALL, "mixed")
+    ref = M.het_prepare_reference(case["data"], case["th"], 16, modes=ALL)
+    with pytest.raises(M.MBHError):
+        M.het_loglike_batch([ref], [0, 2], th, "mixed")
+    srv = M.Server(1 << 30, precision="mixed")
+    with pytest.raises(M.MBHError):
+        srv.add_source(ref)
+    srv.close()
+    with pytest.raises(M.MBHError):
+        M.template_batch(case["g"], th, "fp64", modes=0x40)
+
+
+def test_sampler_direct_higher_modes(M, WL, oracle):
+    """Module-1 sampler with higher-mode templates (the Sec. III C higher-mode posterior is
+    sampled this way): positions bit-identical to the oracle's sampler."""
+    import torch
+    g = I.grid_small(n=1536)
+    th_raw, snr = I.draw_source(I.rng(0), g["t_obs"], mt_range=(4e5, 4e5))
+    th_raw[I.I_Q] = 0.4
+    S = oracle.psd(oracle.freqs(g))
+    th = I.with_distance(th_raw, oracle.snr_distance(th_raw, g, snr, S))
+    z = I.noise_normals(I.rng(0, 100), g["n"])
+    d_o = oracle.template_hm(th, oracle.freqs(g), g["t_obs"], ALL) + oracle.noise(S, g["df"], z)
+    psd = M.mbh_psd_aet(g)
+    d_g = M.template_batch(g, WL.to_dev(th.reshape(11, 1)), "fp64", modes=ALL)[0].contiguous()
+    M.mbh_noise_aet(g, torch.from_numpy(np.ascontiguousarray(z)).cuda(), psd, out=d_g, accumulate=True)
+    data = M.Data(g, d_g, psd)
+    lo, hi = I.prior_box(g["t_obs"])
+    x0 = th.copy()
+    x0[0], x0[6], x0[8] = math.log(th[0]), math.cos(th[6]), math.sin(th[8])
+    T, W = 2, 8
+    x = I.draw_pt_ensemble(I.rng(65), x0, T, W, np.abs(x0) * 1e-5 + 1e-4 * (hi - lo) * (x0 == 0), lo, hi)
+    betas = I.pt_betas(T)
+    probs = np.array(I.PT_PROBS)
+    pt = M.PTSampler(WL.to_dev(x), betas, lo, hi, data=data, walkers=W, probs=probs, seed=3,
+                     precision="fp64", modes=ALL)
+    pt.run(2)
+    xg, og = (t.cpu().numpy() for t in pt.state())
+    cg, _ = pt.counters()
+    out0 = oracle.direct(oracle.pt_theta(x), g, d_o, S, ALL)
+    xo, oo, co = oracle.pt_run_direct(x, out0, T, W, betas, lo, hi, probs, 2.0, 3, 0, 2, g, d_o, S, ALL)
+    assert np.array_equal(cg, co) and np.array_equal(xg, xo)
+    _close(og, oo, oracle.inner(d_o, d_o, S, g["df"]))
