@@ -303,9 +303,12 @@ MBH_API void mbh_server_free(mbh_server* server);
  * H_lm(x), x = (pi M f2)^{2/3}; polarisations from the spin-weighted harmonics
  * -2Y_lm(iota, phi_ref).  Mode mask: bit 0 (2,2), bit 1 (3,3), bit 2 (4,4),
  * bit 3 (2,1), bit 4 (3,2), bit 5 (4,3); mask 1 is W0 and these calls then do
- * exactly what the (2,2) calls do.  Masks with higher modes are evaluated in
- * float64 only (MBH_MIXED returns MBH_EINVAL).  Layouts, ownership and errors as
- * in the (2,2) calls; an empty mask or bits above 5 return MBH_EINVAL. */
+ * exactly what the (2,2) calls do.  template_batch_hm and direct_loglike_batch_hm
+ * evaluate masks with higher modes in float64 only (MBH_MIXED returns
+ * MBH_EINVAL); the heterodyned likelihood of a higher-mode reference runs in both
+ * precisions (mixed: the delta form per mode, each mode's large phase difference in
+ * double-float).  Layouts, ownership and errors as in the (2,2) calls; an empty
+ * mask or bits above 5 return MBH_EINVAL. */
 MBH_API mbh_status template_batch_hm(const mbh_grid* grid, const double* theta_dev, int64_t W,
                                      uint32_t modes, mbh_precision precision, void* h_out_dev,
                                      void* stream);
@@ -313,7 +316,8 @@ MBH_API mbh_status direct_loglike_batch_hm(const mbh_data* data, const double* t
                                            uint32_t modes, mbh_precision precision, double* out_dev,
                                            void* stream);
 /* The band is where some selected mode of h0 is non-zero; het_loglike_batch then
- * evaluates every walker of this reference with the same modes (MBH_FP64). */
+ * evaluates every walker of this reference with the same modes (either precision;
+ * a launch mixing (2,2) and higher-mode references runs one kernel per kind). */
 MBH_API mbh_status het_prepare_reference_hm(const mbh_data* data, const double* theta0_host,
                                             int32_t n_bins, uint32_t modes, void* stream,
                                             mbh_ref** out);

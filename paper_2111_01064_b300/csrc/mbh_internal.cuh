@@ -29,11 +29,21 @@ struct MixBin {
     float pad;
 };
 
+// per (edge, mode) of a higher-mode reference: Phi0_lm (float pair), u = h0_lm/h0 and
+// g = e^{-i Phi0_lm}/h0 per channel (float32 complex)
+struct MixModeHM {
+    float2 phi0;
+    float2 u[3];
+    float2 g[3];
+};
+
 struct MixTables {
     const MixEdge* edge;   // [E+1]
     const MixBin* bin;     // [E]
     double sumA0;          // sum_b sum_c Re A0
     double sumB0;          // sum_b sum_c B0
+    const MixModeHM* hm;   // [E+1][6] (higher-mode references)
+    const float* hm_base;  // [E+1][3]: -1 where h0 = 0, else 0
 };
 
 struct PrepItem {
@@ -94,6 +104,7 @@ struct HetKernel {
 };
 HetKernel het_kernel_f64(int G, int block);
 HetKernel het_kernel_mixed(int G, int block);
+HetKernel het_kernel_mixed_hm(int G, int block);
 
 // ------------------------------------------------------------------------------------------
 // reductions
@@ -161,5 +172,7 @@ struct mbh_ref {
     mbh::MixEdge* mix_edge = nullptr;
     mbh::MixBin* mix_bin = nullptr;
     double* mix_sums = nullptr;    // device [2]
+    mbh::MixModeHM* mix_hm = nullptr;   // higher-mode references: [E+1][6]
+    float* mix_hm_base = nullptr;       // [E+1][3]
     mbh::MixTables mix{};
 };

@@ -217,7 +217,7 @@ mbh_status check_modes(uint32_t modes, mbh_precision precision)
 {
     if (modes == 0u || (modes & ~kHmAll)) return fail(MBH_EINVAL, "mode mask 0x%x: bits 0-5, not empty", modes);
     if (modes != 1u && precision != MBH_FP64)
-        return fail(MBH_EINVAL, "higher modes are evaluated in float64 only (MBH_FP64)");
+        return fail(MBH_EINVAL, "templates and direct likelihoods with higher modes are float64 only");
     if (precision != MBH_FP64 && precision != MBH_MIXED) return fail(MBH_EINVAL, "unknown precision %d", (int)precision);
     return MBH_OK;
 }
@@ -746,8 +746,7 @@ extern "C" mbh_status het_prepare_reference_hm(const mbh_data* data, const doubl
     prep_finalize_kernel<<<(E * 18 + 255) / 256, 256, 0, st>>>(d_part, d_ib, E, R->summary);
     edge_ref_kernel<<<1, 256, 0, st>>>(R->theta0_dev, g.t_obs, R->fe, E + 1, modes, R->h0e, R->h0inv);
     e = cudaGetLastError();
-    // the mixed kernel's factored reference is a (2,2)-mode construction
-    if (e == cudaSuccess && modes == 1u) e = prepare_mixed_tables(R, st);
+    if (e == cudaSuccess) e = prepare_mixed_tables(R, st);
     if (e == cudaSuccess) e = cudaFreeAsync(d_items, st);
     if (e == cudaSuccess) e = cudaFreeAsync(d_ib, st);
     if (e == cudaSuccess) e = cudaFreeAsync(d_fb, st);

@@ -116,7 +116,8 @@ __device__ __forceinline__ float sinc_diff(float x, float k)
 //   1 - D = 2i sin x e^{-ix}, 1 - D^2 = 2i sin 2x e^{-2ix} (no 1 - cos), and
 //   X + Y + Z = (1 - D^2)(1 - D) sum_arms g_a [sinc(x(1 + k.n)) - sinc(x(1 - k.n))],
 // so T = (X + Y + Z)/sqrt3 is formed from sinc differences computed without cancellation.
-__device__ inline void transfer_f32(const WalkerF& w, float f, float sa, float ca, cf T[3])
+__device__ inline void transfer_f32(const WalkerF& w, const float* Kp, const float* Kc, float f, float sa,
+                                    float ca, cf T[3])
 {
     constexpr float armS = (float)kArmSec;
     constexpr float rho = (float)(kArmSec / kSqrt3);
@@ -143,7 +144,7 @@ __device__ inline void transfer_f32(const WalkerF& w, float f, float sa, float c
             ko += w.k[m] * (o[i][m] + o[j][m]);
         }
         const float np = nPnf(w.Pp, n), nc = nPnf(w.Pc, n);
-        const cf F = {np * w.Kp[0] + nc * w.Kc[0], np * w.Kp[1] + nc * w.Kc[1]};
+        const cf F = {np * Kp[0] + nc * Kc[0], np * Kp[1] + nc * Kc[1]};
         float sph, cph;
         sincos_small((float)kPi * f * (armS + ko), &sph, &cph);
         const cf g = fmul({-x * sph, -x * cph}, F);
@@ -324,7 +325,9 @@ __device__ __forceinline__ FreqDF freq_tables(double f)
 __device__ __forceinline__ f2 ld_f2(float2 v) { return {v.x, v.y}; }
 
 // Large phase Phi(f) (double-float) and float32 amplitude and orbit angle from the
-// frequency tables.  Returns false outside the support (f > f_cut or t(f) outside [0, t_obs]).
+// frequency tables.  Returns false outside the support (f > f_cut or t(f) outside [0, t_obs]);
+// with kAlways the phase is computed there as well (a reference phase defined at every edge).
+template <bool kAlways = false>
 __device__ __forceinline__ bool phase_df(const WalkerDF& w, const WalkerF& wf, const FreqDF& q,
                                          f2 t_obs, f2& Phi, float& sa, float& ca, float& amp)
 {
@@ -343,7 +346,8 @@ __device__ __forceinline__ bool phase_df(const WalkerDF& w, const WalkerF& wf, c
     const f2 dpsi = dd_add(dd_mul(Q, iv8), dd_mul(dd_mul(lnv, w.dl6), iv2));
     const f2 dt = dd_mul(dd_sub(dpsi, w.dpsi_max), kInvTwoPiDF);
     const f2 t = dd_add(w.tref, dt);
-    if (!dd_le0(dd_sub(q.f, w.fcut)) || dd_lt0(t) || !dd_le0(dd_sub(t, t_obs))) return false;
+    const bool in = dd_le0(dd_sub(q.f, w.fcut)) && !dd_lt0(t) && dd_le0(dd_sub(t, t_obs));
+    if (!kAlways && !in) return false;
     // orbit angle alpha(t) = alpha(t_ref) + da
     const float da = dt.hi * (float)(kTwoPi / kYear);
     float sh, ch;
@@ -359,7 +363,61 @@ __device__ __forceinline__ bool phase_df(const WalkerDF& w, const WalkerF& wf, c
     ca = dd_to_float(ca_d);
     const float ivf = iv.hi, ff = q.f.hi;
     amp = wf.amp * ivf * ivf * ivf * sqrtf(ivf) * expf(-ff * ff * wf.inv_fc2);
-    return true;
+    return in;
+}
+
+// ---- higher harmonics, mixed precision ---------------------------------------------------
+// Mode (l, m) is the (2,2) chain at f2 = 2f/m (so its tables are the grid's scaled by
+// constants) with the phase scaled by m/2; the amplitude gains v^{p_lm} and the response uses
+// the mode's polarisation factors (float32, folded with H_lm's constant and sqrt(2/m)).
+struct WalkerHMF {
+    float hk[kHmModes][4];   // K+ (re, im), Kx (re, im) per mode
+};
+
+// tables of f2 = r f, r = 2/m: f2, f2^{1/3}, f2^{-1/3}, ln(f2)/3
+__device__ __forceinline__ FreqDF mode_tables(const FreqDF& q, int b)
+{
+    constexpr f2 r[kHmModes] = {df_const(1.0), df_const(2.0 / 3.0), df_const(0.5), df_const(2.0),
+                                df_const(1.0), df_const(2.0 / 3.0)};
+    constexpr f2 r3[kHmModes] = {df_const(1.0), df_const(0.87358046473629952), df_const(0.79370052598409974),
+                                 df_const(1.2599210498948732), df_const(1.0), df_const(0.87358046473629952)};
+    constexpr f2 rm3[kHmModes] = {df_const(1.0), df_const(1.1447142425533319), df_const(1.2599210498948732),
+                                  df_const(0.79370052598409974), df_const(1.0), df_const(1.1447142425533319)};
+    constexpr f2 ln3[kHmModes] = {df_const(0.0), df_const(-0.13515503603605479), df_const(-0.23104906018664842),
+                                  df_const(0.23104906018664842), df_const(0.0), df_const(-0.13515503603605479)};
+    if (hm_m(b) == 2) return q;
+    return {dd_mul(q.f, r[b]), dd_mul(q.f3, r3[b]), dd_mul(q.fm3, rm3[b]), dd_add(q.lnf3, ln3[b])};
+}
+
+// Phi_lm = (m/2) Phi_22(f2) in double-float (exact for m = 1, 2, 4)
+__device__ __forceinline__ f2 mode_phase(f2 p, int b)
+{
+    const int m = hm_m(b);
+    if (m == 2) return p;
+    if (m == 4) return {2.0f * p.hi, 2.0f * p.lo};
+    if (m == 1) return {0.5f * p.hi, 0.5f * p.lo};
+    return dd_mul_f(p, 1.5f);
+}
+
+// Folded per-mode factors of one walker (float64, rounded once), as in the float64 model.
+__device__ inline void walker_setup_hm(const double* __restrict__ theta, int64_t W, int64_t i,
+                                       WalkerHMF& h)
+{
+    const double q = theta[kQ * W + i], iota = theta[kIota * W + i], phi = theta[kPhi * W + i];
+    Walker tmp;
+    hm_setup(tmp, q, iota, phi);
+#pragma unroll
+    for (int b = 0; b < kHmModes; ++b)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) h.hk[b][j] = (float)tmp.hk[b][j];
+}
+
+// v^{p_lm} in float32 from f2^{1/3} and (pi M)^{1/3}
+__device__ __forceinline__ float mode_vpow(const WalkerDF& w, const FreqDF& q2, int b)
+{
+    const float v = w.cbrt_piM.hi * q2.f3.hi;
+    const int p = hm_vpow(b);
+    return p == 0 ? 1.0f : p == 1 ? v : p == 2 ? v * v : v * v * v;
 }
 
 // phase modulo 2 pi in double-float, then float32
@@ -379,7 +437,7 @@ __device__ __forceinline__ bool point_mixed(const WalkerDF& w, const WalkerF& wf
     float sp, cp;
     sincos_small(reduce_phase(Phi), &sp, &cp);
     cf T[3];
-    transfer_f32(wf, q.f.hi, sa, ca, T);
+    transfer_f32(wf, wf.Kp, wf.Kc, q.f.hi, sa, ca, T);
     const cf e = {amp * scale * cp, -amp * scale * sp};
 #pragma unroll
     for (int c = 0; c < 3; ++c) h[c] = fmul(e, T[c]);
@@ -603,6 +661,8 @@ void mbh::free_ref_tables(mbh_ref* R)
     cudaFree(R->mix_edge);
     cudaFree(R->mix_bin);
     cudaFree(R->mix_sums);
+    if (R->mix_hm) cudaFree(R->mix_hm);
+    if (R->mix_hm_base) cudaFree(R->mix_hm_base);
 }
 
 // Edge records of the reference, using the same mixed-precision functions as the walkers so
@@ -626,7 +686,7 @@ __global__ void edge_mixed_kernel(const double* __restrict__ theta0, double t_ob
         float sa, ca, amp;
         const bool in = phase_df(wd, wf, q, tob, Phi, sa, ca, amp);
         cf T[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-        if (in) transfer_f32(wf, q.f.hi, sa, ca, T);
+        if (in) transfer_f32(wf, wf.Kp, wf.Kc, q.f.hi, sa, ca, T);
         m.phi0 = in ? make_float2(Phi.hi, Phi.lo) : make_float2(0.f, 0.f);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -638,6 +698,80 @@ __global__ void edge_mixed_kernel(const double* __restrict__ theta0, double t_ob
             m.h0inv[c] = m2 > 0.0 ? make_float2((float)(hr / m2), (float)(-hi / m2)) : make_float2(0.f, 0.f);
         }
         out[e] = m;
+    }
+}
+
+// Higher-mode reference: per edge and mode the mode's large phase Phi0_lm (double-float,
+// defined also outside the mode's support), and per channel u = h0_lm/h0 and g = e^{-i Phi0_lm}/h0
+// (formed in float64 from the same mixed-precision chain as the walkers'); base = -1 where
+// h0 = 0 (r = 0 there).  A walker's delta = r - 1 is then
+//   base + sum_lm [a + a (e^{-i dPhi_lm} - 1) + u (e^{-i dPhi_lm} - 1)],  a = H_lm g - u,
+// with H_lm its float32 mode template without the large phase; a mode outside the walker's
+// support contributes -u.
+__global__ void edge_mixed_hm_kernel(const double* __restrict__ theta0, double t_obs, uint32_t modes,
+                                     const double* __restrict__ fe, int n_edges, MixEdge* __restrict__ out,
+                                     MixModeHM* __restrict__ hm, float* __restrict__ base)
+{
+    __shared__ WalkerDF wd;
+    __shared__ WalkerF wf;
+    __shared__ WalkerHMF wh;
+    if (threadIdx.x == 0) {
+        walker_setup_mixed(theta0, 1, 0, wd, wf);
+        walker_setup_hm(theta0, 1, 0, wh);
+    }
+    __syncthreads();
+    const f2 tob = split_d(t_obs);
+    for (int e = threadIdx.x; e < n_edges; e += blockDim.x) {
+        const FreqDF q = freq_tables(fe[e]);
+        MixEdge me{};
+        me.f = make_float2(q.f.hi, q.f.lo);
+        me.f3 = make_float2(q.f3.hi, q.f3.lo);
+        me.fm3 = make_float2(q.fm3.hi, q.fm3.lo);
+        me.lnf3 = make_float2(q.lnf3.hi, q.lnf3.lo);
+        out[e] = me;
+        double h0r[3] = {0, 0, 0}, h0i[3] = {0, 0, 0};
+        double hr[kHmModes][3], hi[kHmModes][3], er[kHmModes], ei[kHmModes];
+        for (int b = 0; b < kHmModes; ++b) {
+            for (int c = 0; c < 3; ++c) hr[b][c] = hi[b][c] = 0.0;
+            er[b] = ei[b] = 0.0;
+            MixModeHM mm{};
+            if (modes & (1u << b)) {
+                const FreqDF q2 = mode_tables(q, b);
+                f2 Phi;
+                float sa, ca, amp;
+                const bool in = phase_df<true>(wd, wf, q2, tob, Phi, sa, ca, amp);
+                const f2 P = mode_phase(Phi, b);
+                mm.phi0 = make_float2(P.hi, P.lo);
+                const double ph = fmod((double)P.hi + (double)P.lo, kTwoPi);
+                sincos(-ph, &ei[b], &er[b]);   // e^{-i Phi0_lm}
+                if (in) {
+                    cf T[3];
+                    transfer_f32(wf, &wh.hk[b][0], &wh.hk[b][2], q.f.hi, sa, ca, T);
+                    const float a = amp * mode_vpow(wd, q2, b);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const double Hr = (double)(a * T[c].re), Hi = (double)(a * T[c].im);
+                        hr[b][c] = Hr * er[b] - Hi * ei[b];
+                        hi[b][c] = Hr * ei[b] + Hi * er[b];
+                        h0r[c] += hr[b][c];
+                        h0i[c] += hi[b][c];
+                    }
+                }
+            }
+            hm[(int64_t)e * kHmModes + b] = mm;
+        }
+        for (int c = 0; c < 3; ++c) {
+            const double m2 = h0r[c] * h0r[c] + h0i[c] * h0i[c];
+            base[e * 3 + c] = m2 > 0.0 ? 0.0f : -1.0f;
+            if (!(m2 > 0.0)) continue;
+            const double ir = h0r[c] / m2, ii = -h0i[c] / m2;   // 1/h0
+            for (int b = 0; b < kHmModes; ++b) {
+                if (!(modes & (1u << b))) continue;
+                MixModeHM& mm = hm[(int64_t)e * kHmModes + b];
+                mm.u[c] = make_float2((float)(hr[b][c] * ir - hi[b][c] * ii), (float)(hr[b][c] * ii + hi[b][c] * ir));
+                mm.g[c] = make_float2((float)(er[b] * ir - ei[b] * ii), (float)(er[b] * ii + ei[b] * ir));
+            }
+        }
     }
 }
 
@@ -668,7 +802,15 @@ __global__ void bin_mixed_kernel(const double* __restrict__ summary, const doubl
 cudaError_t mbh::prepare_mixed_tables(mbh_ref* R, cudaStream_t st)
 {
     const int E = R->E;
-    edge_mixed_kernel<<<1, 256, 0, st>>>(R->theta0_dev, R->grid.t_obs, R->fe, E + 1, R->mix_edge);
+    if (R->modes == 1u) {
+        edge_mixed_kernel<<<1, 256, 0, st>>>(R->theta0_dev, R->grid.t_obs, R->fe, E + 1, R->mix_edge);
+    } else {
+        cudaError_t e = cudaMalloc(&R->mix_hm, sizeof(MixModeHM) * kHmModes * (E + 1));
+        if (e == cudaSuccess) e = cudaMalloc(&R->mix_hm_base, sizeof(float) * 3 * (E + 1));
+        if (e != cudaSuccess) return e;
+        edge_mixed_hm_kernel<<<1, 128, 0, st>>>(R->theta0_dev, R->grid.t_obs, R->modes, R->fe, E + 1,
+                                                R->mix_edge, R->mix_hm, R->mix_hm_base);
+    }
     bin_mixed_kernel<<<(E + 127) / 128, 128, 0, st>>>(R->summary, R->invw, E, R->mix_bin, R->mix_sums);
     cudaError_t e = cudaGetLastError();
     double sums[2];
@@ -679,6 +821,8 @@ cudaError_t mbh::prepare_mixed_tables(mbh_ref* R, cudaStream_t st)
         R->mix.bin = R->mix_bin;
         R->mix.sumA0 = sums[0];
         R->mix.sumB0 = sums[1];
+        R->mix.hm = R->mix_hm;
+        R->mix.hm_base = R->mix_hm_base;
     }
     return e;
 }
@@ -725,7 +869,7 @@ __global__ void __launch_bounds__(BLOCK)
                     sincos_small(0.5f * reduce_phase(dd_sub(Phi, ld_f2(me.phi0))), &sh, &ch);
                     const cf em1 = {-2.0f * sh * sh, -2.0f * sh * ch};   // e^{-i dPhi} - 1
                     cf T[3];
-                    transfer_f32(wsf[lw], q.f.hi, sa, ca, T);
+                    transfer_f32(wsf[lw], wsf[lw].Kp, wsf[lw].Kc, q.f.hi, sa, ca, T);
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         const cf rho = fmul(fscale(T[c], amp), {me.h0inv[c].x, me.h0inv[c].y});
@@ -780,11 +924,127 @@ __global__ void __launch_bounds__(BLOCK)
     }
 }
 
+
+// Higher-mode heterodyne (Sec. II B with the template of Eq. 9 summed over modes before the
+// ratio), mixed precision; layout and reductions as het_mixed_kernel, delta from the
+// per-mode reference tables (edge_mixed_hm_kernel).
+template <int G, int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+    het_mixed_hm_kernel(const __grid_constant__ HetLaunch L)
+{
+    constexpr int WPB = BLOCK / G;
+    __shared__ WalkerDF wsd[WPB];
+    __shared__ WalkerF wsf[WPB];
+    __shared__ WalkerHMF wsh[WPB];
+    const int lw = threadIdx.x / G, lane = threadIdx.x % G;
+    for (int tile = blockIdx.x; tile < L.n_tiles; tile += gridDim.x) {
+        int s = 0;
+        while (s + 1 < L.n_src && L.src[s + 1].tile_begin <= tile) ++s;
+        const SrcDesc& S = L.src[s];
+        const int64_t w0 = S.w_begin + (int64_t)(tile - S.tile_begin) * WPB;
+        const int64_t wi = w0 + lw;
+        const bool active = wi < S.w_end;
+        __syncthreads();
+        for (int j = threadIdx.x; j < WPB; j += BLOCK)
+            if (w0 + j < S.w_end) {
+                walker_setup_mixed(L.theta, L.W, w0 + j, wsd[j], wsf[j]);
+                walker_setup_hm(L.theta, L.W, w0 + j, wsh[j]);
+            }
+        __syncthreads();
+        const int E = S.E;
+        const uint32_t modes = S.modes;
+        const f2 tob = split_d(S.t_obs);
+        f2 adh = {0.0f, 0.0f}, ahh = {0.0f, 0.0f};
+        cf carry[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+        const int rounds = (E + 1 + G - 1) / G;
+        for (int r = 0; r < rounds; ++r) {
+            const int e = r * G + lane;
+            cf dl[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+            if (active && e <= E) {
+                const MixEdge me = S.mix.edge[e];
+                const FreqDF q = {ld_f2(me.f), ld_f2(me.f3), ld_f2(me.fm3), ld_f2(me.lnf3)};
+#pragma unroll
+                for (int c = 0; c < 3; ++c) dl[c].re = S.mix.hm_base[e * 3 + c];
+                for (int b = 0; b < kHmModes; ++b) {
+                    if (!(modes & (1u << b))) continue;
+                    const MixModeHM mm = S.mix.hm[(int64_t)e * kHmModes + b];
+                    const FreqDF q2 = mode_tables(q, b);
+                    f2 Phi;
+                    float sa, ca, amp;
+                    if (phase_df(wsd[lw], wsf[lw], q2, tob, Phi, sa, ca, amp)) {
+                        float sh, ch;
+                        sincos_small(0.5f * reduce_phase(dd_sub(mode_phase(Phi, b), ld_f2(mm.phi0))), &sh, &ch);
+                        const cf em1 = {-2.0f * sh * sh, -2.0f * sh * ch};   // e^{-i dPhi} - 1
+                        cf T[3];
+                        transfer_f32(wsf[lw], &wsh[lw].hk[b][0], &wsh[lw].hk[b][2], q.f.hi, sa, ca, T);
+                        const float a = amp * mode_vpow(wsd[lw], q2, b);
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            const cf u = {mm.u[c].x, mm.u[c].y};
+                            const cf ac = fsub(fmul(fscale(T[c], a), {mm.g[c].x, mm.g[c].y}), u);
+                            dl[c] = fadd(dl[c], fadd(fadd(ac, fmul(ac, em1)), fmul(u, em1)));
+                        }
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) dl[c] = fsub(dl[c], {mm.u[c].x, mm.u[c].y});
+                    }
+                }
+            }
+            cf dp[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                dp[c].re = __shfl_up_sync(0xffffffffu, dl[c].re, 1, G);
+                dp[c].im = __shfl_up_sync(0xffffffffu, dl[c].im, 1, G);
+                if (lane == 0) dp[c] = carry[c];
+                carry[c].re = __shfl_sync(0xffffffffu, dl[c].re, G - 1, G);
+                carry[c].im = __shfl_sync(0xffffffffu, dl[c].im, G - 1, G);
+            }
+            if (active && e >= 1 && e <= E) {
+                const MixBin& mb = S.mix.bin[e - 1];
+                const float iw = mb.invw;
+                float bd = 0.0f, bh = 0.0f;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float d0r = 0.5f * (dp[c].re + dl[c].re), d0i = 0.5f * (dp[c].im + dl[c].im);
+                    const float d1r = (dl[c].re - dp[c].re) * iw, d1i = (dl[c].im - dp[c].im) * iw;
+                    const float* qq = mb.q + 6 * c;
+                    bd += qq[0] * d0r + qq[1] * d0i + qq[2] * d1r + qq[3] * d1i;
+                    bh += qq[4] * (2.0f * d0r + d0r * d0r + d0i * d0i) +
+                          2.0f * qq[5] * (d1r + d0r * d1r + d0i * d1i);
+                }
+                df_acc(adh, {bd, 0.0f});
+                df_acc(ahh, {bh, 0.0f});
+            }
+        }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+            const f2 odh = {__shfl_down_sync(0xffffffffu, adh.hi, o, G), __shfl_down_sync(0xffffffffu, adh.lo, o, G)};
+            const f2 ohh = {__shfl_down_sync(0xffffffffu, ahh.hi, o, G), __shfl_down_sync(0xffffffffu, ahh.lo, o, G)};
+            df_acc(adh, odh);
+            df_acc(ahh, ohh);
+        }
+        if (active && lane == 0) {
+            const double dh = 4.0 * (S.mix.sumA0 + df_to_double(adh));
+            const double hh = 4.0 * (S.mix.sumB0 + df_to_double(ahh));
+            L.out[wi] = -0.5 * (S.dd + hh - 2.0 * dh);
+            L.out[L.W + wi] = dh;
+            L.out[2 * L.W + wi] = hh;
+        }
+    }
+}
+
 namespace {
 template <int G, int BLOCK>
 cudaError_t launch_het_mixed(const HetLaunch& L, int grid, cudaStream_t st)
 {
     het_mixed_kernel<G, BLOCK><<<grid, BLOCK, 0, st>>>(L);
+    return cudaGetLastError();
+}
+
+template <int G, int BLOCK>
+cudaError_t launch_het_mixed_hm(const HetLaunch& L, int grid, cudaStream_t st)
+{
+    het_mixed_hm_kernel<G, BLOCK><<<grid, BLOCK, 0, st>>>(L);
     return cudaGetLastError();
 }
 }  // namespace
@@ -794,6 +1054,22 @@ HetKernel het_kernel_mixed(int G, int block)
 {
 #define MBH_CASE(g, b) \
     if (G == g && block == b) return {&launch_het_mixed<g, b>, (const void*)&het_mixed_kernel<g, b>};
+    MBH_CASE(1, 64) MBH_CASE(1, 128) MBH_CASE(1, 256)
+    MBH_CASE(2, 64) MBH_CASE(2, 128) MBH_CASE(2, 256)
+    MBH_CASE(4, 64) MBH_CASE(4, 128) MBH_CASE(4, 256)
+    MBH_CASE(8, 64) MBH_CASE(8, 128) MBH_CASE(8, 256)
+    MBH_CASE(16, 64) MBH_CASE(16, 128) MBH_CASE(16, 256)
+    MBH_CASE(32, 64) MBH_CASE(32, 128) MBH_CASE(32, 256)
+#undef MBH_CASE
+    return {nullptr, nullptr};
+}
+}  // namespace mbh
+
+namespace mbh {
+HetKernel het_kernel_mixed_hm(int G, int block)
+{
+#define MBH_CASE(g, b) \
+    if (G == g && block == b) return {&launch_het_mixed_hm<g, b>, (const void*)&het_mixed_hm_kernel<g, b>};
     MBH_CASE(1, 64) MBH_CASE(1, 128) MBH_CASE(1, 256)
     MBH_CASE(2, 64) MBH_CASE(2, 128) MBH_CASE(2, 256)
     MBH_CASE(4, 64) MBH_CASE(4, 128) MBH_CASE(4, 256)

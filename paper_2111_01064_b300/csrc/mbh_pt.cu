@@ -564,8 +564,6 @@ extern "C" mbh_status mbh_pt_create(const mbh_pt_opts* o, const mbh_ref* ref, co
     const uint32_t modes = o->modes ? o->modes : 1u;
     if (data)
         if (mbh_status s = check_modes(modes, o->precision)) return s;
-    if (ref && ref->modes != 1u && o->precision != MBH_FP64)
-        return fail(MBH_EINVAL, "higher-mode reference: MBH_FP64 only");
     if (mbh_status s = check_device()) return s;
     int dev = -1;
     cudaGetDevice(&dev);

@@ -29,7 +29,7 @@ namespace {
 struct HetPlan {
     std::vector<HetLaunch> launches;   // heap-allocated: each ~13 KB
     std::vector<int> grids;
-    HetKernel kernel{nullptr, nullptr};
+    std::vector<HetKernel> kernels;    // per launch
 };
 
 mbh_status check_cfg(const mbh_het_config& c)
@@ -66,66 +66,78 @@ mbh_status make_plan(const mbh_ref* const* refs, const int64_t* offsets, int32_t
 {
     if (mbh_status s = check_cfg(cfg)) return s;
     if (prec != MBH_FP64 && prec != MBH_MIXED) return fail(MBH_EINVAL, "unknown precision %d", (int)prec);
-    plan.kernel = prec == MBH_FP64 ? het_kernel_f64(cfg.threads_per_walker, cfg.block)
-                                   : het_kernel_mixed(cfg.threads_per_walker, cfg.block);
-    if (!plan.kernel.launch) return fail(MBH_EINVAL, "no kernel for this configuration");
     const int wpb = cfg.block / cfg.threads_per_walker;
     const int64_t W = offsets[n_src];
-    std::vector<int32_t> order(n_src);
-    std::iota(order.begin(), order.end(), 0);
-    if (cfg.persistent)   // largest bin counts first
-        std::stable_sort(order.begin(), order.end(),
-                         [&](int32_t a, int32_t b) { return refs[a]->E > refs[b]->E; });
-    int resident = 0;
-    if (cfg.persistent) {
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        int per_sm = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan.kernel.fn, cfg.block, 0);
-        if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
-        resident = std::max(1, per_sm) * sms;
-    }
-    for (int32_t first = 0; first < n_src; first += kMaxSrc) {
-        const int32_t count = std::min<int32_t>(kMaxSrc, n_src - first);
-        plan.launches.emplace_back();
-        HetLaunch& L = plan.launches.back();
-        std::memset(&L, 0, sizeof L);
-        L.theta = theta;
-        L.W = W;
-        L.out = out;
-        int64_t tiles = 0;
-        int32_t j = 0;
-        for (int32_t q = 0; q < count; ++q) {
-            const int32_t s = order[first + q];
-            const int64_t nw = offsets[s + 1] - offsets[s];
-            if (nw == 0) continue;
-            const mbh_ref* R = refs[s];
-            SrcDesc& S = L.src[j++];
-            S.summary = R->summary;
-            S.h0inv = R->h0inv;
-            S.fe = R->fe;
-            S.invw = R->invw;
-            S.mix = R->mix;
-            S.dd = R->dd;
-            S.t_obs = R->grid.t_obs;
-            S.E = R->E;
-            S.modes = R->modes;
-            if (R->modes != 1u && prec != MBH_FP64)
-                return fail(MBH_EINVAL, "source %d has higher modes: MBH_FP64 only", s);
-            S.w_begin = offsets[s];
-            S.w_end = offsets[s + 1];
-            S.tile_begin = (int32_t)tiles;
-            tiles += (nw + wpb - 1) / wpb;
-            if (tiles > 0x7fffffff) return fail(MBH_EINVAL, "too many walker tiles");
+    // kernel per source: float64 (any modes), mixed (2,2), or mixed with higher modes;
+    // a launch holds sources of one kernel
+    auto kernel_of = [&](int32_t s) {
+        if (prec == MBH_FP64) return het_kernel_f64(cfg.threads_per_walker, cfg.block);
+        return refs[s]->modes == 1u ? het_kernel_mixed(cfg.threads_per_walker, cfg.block)
+                                    : het_kernel_mixed_hm(cfg.threads_per_walker, cfg.block);
+    };
+    for (int group = 0; group < 2; ++group) {
+        std::vector<int32_t> order;
+        for (int32_t s = 0; s < n_src; ++s) {
+            const bool hm = prec == MBH_MIXED && refs[s]->modes != 1u;
+            if ((group == 1) == hm) order.push_back(s);
         }
-        L.n_src = j;
-        L.n_tiles = (int32_t)tiles;
-        if (tiles == 0) {
-            plan.launches.pop_back();
-            continue;
+        if (order.empty()) continue;
+        const HetKernel kernel = kernel_of(order[0]);
+        if (!kernel.launch) return fail(MBH_EINVAL, "no kernel for this configuration");
+        if (cfg.persistent)   // largest bin counts first
+            std::stable_sort(order.begin(), order.end(),
+                             [&](int32_t a, int32_t b) { return refs[a]->E > refs[b]->E; });
+        int resident = 0;
+        if (cfg.persistent) {
+            int dev = 0, sms = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            int per_sm = 0;
+            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel.fn, cfg.block, 0);
+            if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+            resident = std::max(1, per_sm) * sms;
         }
-        plan.grids.push_back(cfg.persistent ? (int)std::min<int64_t>(tiles, resident) : (int)tiles);
+        const int32_t ng = (int32_t)order.size();
+        for (int32_t first = 0; first < ng; first += kMaxSrc) {
+            const int32_t count = std::min<int32_t>(kMaxSrc, ng - first);
+            plan.launches.emplace_back();
+            HetLaunch& L = plan.launches.back();
+            std::memset(&L, 0, sizeof L);
+            L.theta = theta;
+            L.W = W;
+            L.out = out;
+            int64_t tiles = 0;
+            int32_t j = 0;
+            for (int32_t q = 0; q < count; ++q) {
+                const int32_t s = order[first + q];
+                const int64_t nw = offsets[s + 1] - offsets[s];
+                if (nw == 0) continue;
+                const mbh_ref* R = refs[s];
+                SrcDesc& S = L.src[j++];
+                S.summary = R->summary;
+                S.h0inv = R->h0inv;
+                S.fe = R->fe;
+                S.invw = R->invw;
+                S.mix = R->mix;
+                S.dd = R->dd;
+                S.t_obs = R->grid.t_obs;
+                S.E = R->E;
+                S.modes = R->modes;
+                S.w_begin = offsets[s];
+                S.w_end = offsets[s + 1];
+                S.tile_begin = (int32_t)tiles;
+                tiles += (nw + wpb - 1) / wpb;
+                if (tiles > 0x7fffffff) return fail(MBH_EINVAL, "too many walker tiles");
+            }
+            L.n_src = j;
+            L.n_tiles = (int32_t)tiles;
+            if (tiles == 0) {
+                plan.launches.pop_back();
+                continue;
+            }
+            plan.kernels.push_back(kernel);
+            plan.grids.push_back(cfg.persistent ? (int)std::min<int64_t>(tiles, resident) : (int)tiles);
+        }
     }
     return MBH_OK;
 }
@@ -133,7 +145,7 @@ mbh_status make_plan(const mbh_ref* const* refs, const int64_t* offsets, int32_t
 mbh_status run_plan(const HetPlan& plan, cudaStream_t st)
 {
     for (size_t i = 0; i < plan.launches.size(); ++i) {
-        cudaError_t e = plan.kernel.launch(plan.launches[i], plan.grids[i], st);
+        cudaError_t e = plan.kernels[i].launch(plan.launches[i], plan.grids[i], st);
         if (e != cudaSuccess) return cuda_fail(e, "heterodyne kernel");
     }
     return MBH_OK;

@@ -286,8 +286,6 @@ extern "C" mbh_status mbh_server_add_source(mbh_server* S, const mbh_ref* ref, i
 {
     if (!S || !ref || !source_id) return fail(MBH_EINVAL, "NULL argument");
     if (ref->device != S->device) return fail(MBH_EINVAL, "reference lives on another device");
-    if (ref->modes != 1u && S->opts.precision != MBH_FP64)
-        return fail(MBH_EINVAL, "higher-mode references need a float64 server");
     std::lock_guard<std::mutex> lk(S->mu);
     const size_t b = ref_bytes(ref);
     const size_t used = S->source_bytes + S->slot_bytes * S->slots.size();
@@ -334,8 +332,6 @@ extern "C" mbh_status mbh_server_replace_source(mbh_server* S, int32_t source_id
 {
     if (!S || !ref) return fail(MBH_EINVAL, "NULL argument");
     if (ref->device != S->device) return fail(MBH_EINVAL, "reference lives on another device");
-    if (ref->modes != 1u && S->opts.precision != MBH_FP64)
-        return fail(MBH_EINVAL, "higher-mode references need a float64 server");
     std::unique_lock<std::mutex> lk(S->mu);
     auto it = S->sources.find(source_id);
     if (it == S->sources.end()) return fail(MBH_EINVAL, "unknown source %d", source_id);

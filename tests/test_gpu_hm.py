@@ -2,7 +2,8 @@
 templates, the direct likelihood, the heterodyne reference (band, edges, summary data) and
 likelihood, and the Module-1 sampler with higher-mode templates, all float64.  Tolerances as
 in the (2,2) parity tests: templates within 1e-8 of max|h|; lnL within 1e-6 of the size of
-the terms; edges bit-exact.  Mixed precision with higher modes is refused (MBH_EINVAL)."""
+the terms; edges bit-exact.  The heterodyne also runs in mixed precision (per-mode delta
+form); templates and the direct likelihood with higher modes are float64 only."""
 import math
 
 import numpy as np
@@ -102,19 +103,46 @@ def test_het_reference_and_likelihood(M, WL, oracle, case):
     assert rg["edges"][0] <= band22[0] and rg["edges"][-1] >= band22[1]
 
 
-def test_mixed_with_higher_modes_refused(M, WL, case):
+def test_het_mixed_higher_modes(M, WL, oracle, case):
+    """Mixed-precision heterodyne of a higher-mode reference: per-mode delta form (each
+    mode's large phase difference in double-float); near the reference |dlnL| ~ 1e-4 as for
+    the (2,2) kernel, and within 1e-6 of the terms for every walker."""
+    ref_g = M.het_prepare_reference(case["data"], case["th"], 64, modes=ALL)
+    ref_o = oracle.het_prepare(case["th"], case["g"], case["d_o"], case["S"], 64, ALL)
+    near = WL.walkers(case["th"], 64, 0, source=7, lo=1e-6, hi=1e-4)
+    far = case["walk"]
+    for th, tol in ((near, 2e-3), (far, None)):
+        out_m = M.het_loglike_batch([ref_g], [0, th.shape[1]], WL.to_dev(th), "mixed").cpu().numpy()
+        out_o = oracle.het_loglike(th, ref_o)
+        _close(out_m, out_o, case["dd_o"])
+        if tol is not None:
+            d = np.abs(out_m[0] - out_o[0])
+            assert np.median(d) < 1e-3 and d.max() < tol, (np.median(d), d.max())
+    # the reference itself: delta = 0 up to rounding
+    out_m = M.het_loglike_batch([ref_g], [0, 1], WL.to_dev(case["th"].reshape(11, 1)), "mixed").cpu().numpy()
+    out_f = M.het_loglike_batch([ref_g], [0, 1], WL.to_dev(case["th"].reshape(11, 1)), "fp64").cpu().numpy()
+    assert abs(out_m[0, 0] - out_f[0, 0]) < 1e-3
+
+
+def test_mixed_batch_of_both_kinds(M, WL, case):
+    """A mixed launch holding a (2,2) and a higher-mode source gives each the result it gets
+    alone (the plan splits them by kernel)."""
+    ref_hm = M.het_prepare_reference(case["data"], case["th"], 32, modes=ALL)
+    ref_22 = M.het_prepare_reference(case["data"], case["th"], 32)
+    th = case["walk"][:, :10]
+    both = np.concatenate([th, th], 1)
+    out = M.het_loglike_batch([ref_22, ref_hm], [0, 10, 20], WL.to_dev(both), "mixed").cpu().numpy()
+    a = M.het_loglike_batch([ref_22], [0, 10], WL.to_dev(th), "mixed").cpu().numpy()
+    b = M.het_loglike_batch([ref_hm], [0, 10], WL.to_dev(th), "mixed").cpu().numpy()
+    assert np.array_equal(out[:, :10], a) and np.array_equal(out[:, 10:], b)
+
+
+def test_mixed_templates_with_higher_modes_refused(M, WL, case):
     th = WL.to_dev(case["walk"][:, :2])
     with pytest.raises(M.MBHError):
         M.template_batch(case["g"], th, "mixed", modes=ALL)
     with pytest.raises(M.MBHError):
         M.direct_loglike_batch_hm(case["data"], th, ALL, "mixed")
-    ref = M.het_prepare_reference(case["data"], case["th"], 16, modes=ALL)
-    with pytest.raises(M.MBHError):
-        M.het_loglike_batch([ref], [0, 2], th, "mixed")
-    srv = M.Server(1 << 30, precision="mixed")
-    with pytest.raises(M.MBHError):
-        srv.add_source(ref)
-    srv.close()
     with pytest.raises(M.MBHError):
         M.template_batch(case["g"], th, "fp64", modes=0x40)
 
