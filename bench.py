@@ -208,6 +208,12 @@ def run_ours(args) -> dict | None:
         return run_direct_only(args, M, WL, g, src, rank, dev, stream, peaks, peak_src)
     if args.only == "fused":
         return run_fused_only(args, M, WL, g, src, rank, dev, stream)
+    if args.only == "sampler":   # profiling case: sampler iterations alone
+        r = run_sampler(M, WL, g, src, ref, stream, 1.0, iters=args.steps)
+        return {"profile_case": "sampler", **r} if rank == 0 else None
+    if args.only == "hm":        # profiling case: higher-mode heterodyne alone
+        r = run_higher_modes(M, WL, g, stream, reps=args.steps)
+        return {"profile_case": "hm", **r} if rank == 0 else None
 
     def het_step(prec="mixed"):
         M.het_loglike_batch([ref], offs, theta, prec, out=out)
@@ -732,8 +738,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="CPU work of the oracle baseline (0: skip)")
-    ap.add_argument("--only", default="all", choices=["all", "het", "direct", "fused"],
-                    help="profiling cases: time only the heterodyne steps or only the direct path")
+    ap.add_argument("--only", default="all", choices=["all", "het", "direct", "fused", "sampler", "hm"],
+                    help="profiling cases: time only the heterodyne steps, the direct path, the "
+                         "sampler or the higher-mode heterodyne")
     ap.add_argument("--walkers", type=int, default=N_WALKERS, help="heterodyne batch (profiling)")
     ap.add_argument("--stored", type=int, default=N_STORED, help="stored templates (profiling)")
     args = ap.parse_args()

@@ -40,7 +40,7 @@ constexpr int kPar = 11;
 constexpr int kMaxTemps = 64;
 constexpr int kMaxWalkers = 8192;   // per temperature (16-bit walker index in the swap keys)
 constexpr int kThreads = 256;      // rescoring and gathers
-constexpr int kStepThreads = 64;   // propose/accept: 8192 walkers -> 128 blocks
+constexpr int kStepThreads = 32;   // propose/accept: 8192 walkers -> 256 blocks over all SMs
 constexpr int kSortThreads = 1024;
 
 enum { K_STRETCH = 0, K_SKY_ALL = 1, K_SKY_LON = 2, K_SKY_LAT = 3 };
@@ -276,37 +276,76 @@ __global__ void __launch_bounds__(kSortThreads) pt_perm_kernel(const PtArgs A, i
 }
 
 // Swap levels in order, hottest first; the hot and cold temperatures of a level are held in
-// shared memory (lnL and map entries).  Thread 0 advances the step counter at the end.
+// shared memory (lnL and map entries).  Thread t handles walkers k = t + j blockDim (j < J);
+// while level i is decided, the next level's inputs (the colder temperature's map entries and
+// then their lnL, the permutation, ln u) are already being loaded into registers, so each
+// level costs its arithmetic and barriers rather than two dependent global round trips.
+// Thread 0 advances the step counter at the end.
+template <int J>
 __global__ void __launch_bounds__(kSortThreads) pt_swap_kernel(const PtArgs A)
 {
     extern __shared__ double sm[];
     const int W = A.W, T = A.T;
-    double* lnl = sm;                                   // [2][W]
+    double* lnl = sm;                                       // [2][W]
     int32_t* mp = reinterpret_cast<int32_t*>(sm + 2 * W);   // [2][W]
     __shared__ unsigned int acc_level;
     const uint64_t step = *A.step;
     if (T > 1) {
+        int32_t pm[J], pp[J];
+        double pl[J], pu[J];
+        // level i's inputs: map and lnL of temperature i-1, permutation and ln u of level i
+        auto issue = [&](int i) {
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+                const int k = threadIdx.x + j * blockDim.x;
+                if (k < W) {
+                    pm[j] = A.map[(i - 1) * W + k];
+                    pp[j] = A.perm[(int64_t)i * W + k];
+                    pu[j] = A.lnu_swap[(int64_t)i * W + k];
+                }
+            }
+        };
+        auto gather = [&]() {
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+                const int k = threadIdx.x + j * blockDim.x;
+                if (k < W) pl[j] = A.out[pm[j]];
+            }
+        };
         int hot = 0;
         for (int k = threadIdx.x; k < W; k += blockDim.x) {
             const int32_t c = A.map[(T - 1) * W + k];
             mp[k] = c;
             lnl[k] = A.out[c];
         }
+        issue(T - 1);
+        gather();
         for (int i = T - 1; i >= 1; --i) {
             const int cold = hot ^ 1;
-            if (threadIdx.x == 0) acc_level = 0;
-            for (int k = threadIdx.x; k < W; k += blockDim.x) {
-                const int32_t c = A.map[(i - 1) * W + k];
-                mp[cold * W + k] = c;
-                lnl[cold * W + k] = A.out[c];
+            int32_t cp[J];
+            double cu[J];
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+                const int k = threadIdx.x + j * blockDim.x;
+                if (k < W) {
+                    mp[cold * W + k] = pm[j];
+                    lnl[cold * W + k] = pl[j];
+                    cp[j] = pp[j];
+                    cu[j] = pu[j];
+                }
             }
+            if (threadIdx.x == 0) acc_level = 0;
             __syncthreads();
+            if (i > 1) issue(i - 1);   // in flight while this level is decided
             const double db = __dsub_rn(A.betas[i - 1], A.betas[i]);
             unsigned int mine = 0;
-            for (int k = threadIdx.x; k < W; k += blockDim.x) {
-                const int h = A.perm[(int64_t)i * W + k];
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+                const int k = threadIdx.x + j * blockDim.x;
+                if (k >= W) continue;
+                const int h = cp[j];
                 const double la = __dmul_rn(db, __dsub_rn(lnl[hot * W + h], lnl[cold * W + k]));
-                if (A.lnu_swap[(int64_t)i * W + k] < la) {
+                if (cu[j] < la) {
                     const double l = lnl[hot * W + h];
                     lnl[hot * W + h] = lnl[cold * W + k];
                     lnl[cold * W + k] = l;
@@ -316,6 +355,7 @@ __global__ void __launch_bounds__(kSortThreads) pt_swap_kernel(const PtArgs A)
                     ++mine;
                 }
             }
+            if (i > 1) gather();
             if (mine) atomicAdd(&acc_level, mine);
             __syncthreads();
             for (int k = threadIdx.x; k < W; k += blockDim.x) A.map[i * W + k] = mp[hot * W + k];
@@ -496,7 +536,12 @@ mbh_status queue_iteration(mbh_pt* P, cudaStream_t st)
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "pt_accept_kernel");
     }
     if ((e = cudaStreamWaitEvent(st, P->join, 0)) != cudaSuccess) return cuda_fail(e, "join");
-    pt_swap_kernel<<<1, kSortThreads, (sizeof(double) + sizeof(int32_t)) * 2 * A.W, st>>>(A);
+    const size_t swap_smem = (sizeof(double) + sizeof(int32_t)) * 2 * A.W;
+    const int J = (A.W + kSortThreads - 1) / kSortThreads;
+    if (J <= 1) pt_swap_kernel<1><<<1, kSortThreads, swap_smem, st>>>(A);
+    else if (J <= 2) pt_swap_kernel<2><<<1, kSortThreads, swap_smem, st>>>(A);
+    else if (J <= 4) pt_swap_kernel<4><<<1, kSortThreads, swap_smem, st>>>(A);
+    else pt_swap_kernel<8><<<1, kSortThreads, swap_smem, st>>>(A);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "pt_swap_kernel");
     return MBH_OK;
 }
@@ -622,9 +667,11 @@ extern "C" mbh_status mbh_pt_create(const mbh_pt_opts* o, const mbh_ref* ref, co
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(pt_perm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(sizeof(unsigned long long) * kMaxWalkers));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(pt_swap_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)((sizeof(double) + sizeof(int32_t)) * 2 * kMaxWalkers));
+    const int swap_max = (int)((sizeof(double) + sizeof(int32_t)) * 2 * kMaxWalkers);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(pt_swap_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, swap_max);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(pt_swap_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, swap_max);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(pt_swap_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, swap_max);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(pt_swap_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, swap_max);
     cudaStream_t st = (cudaStream_t)stream;
     const unsigned long long zero = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync((void*)A.betas, betas_host, sizeof(double) * A.T, cudaMemcpyHostToDevice, st);

@@ -57,7 +57,7 @@ def case(oracle, M, WL):
     scale = np.abs(x0) * 2e-6 + 1e-5 * (hi - lo) * np.array([0, 0, 1, 1, 0, 1, 1, 1, 1, 1, 0])
     x = I.draw_pt_ensemble(I.rng(63), x0, T, W, scale, lo, hi)
     return dict(g=g, src=src, S=S, d_o=d_o, ref_g=ref_g, ref_o=ref_o, lo=lo, hi=hi, T=T, W=W,
-                x=x, betas=I.pt_betas(T, 50.0))
+                x=x, x0=x0, scale=scale, betas=I.pt_betas(T, 50.0))
 
 
 def _gpu_run(M, WL, c, n_iter, precision="fp64", seed=5, graph=True, ref=None):
@@ -185,3 +185,27 @@ def test_pt_invalid_arguments(M, WL, case):
                     probs=(1.1, -0.1, 0, 0))
     with pytest.raises(M.MBHError):   # a <= 1
         M.PTSampler(xd, c["betas"], c["lo"], c["hi"], ref=c["ref_g"], walkers=c["W"], a=1.0)
+
+
+@pytest.mark.parametrize("W", [1500, 3000, 5000])
+def test_pt_large_ensembles_match_oracle(M, WL, oracle, case, W):
+    """Ensembles with several walkers per swap-kernel thread (the swap kernel's register
+    prefetch of 2, 4 and 8 walkers per thread): one iteration, float64, against the oracle."""
+    T = 3
+    lo, hi = case["lo"], case["hi"]
+    th_o = case["x0"].copy()   # reference at the ensemble's centre
+    th_o[0], th_o[6], th_o[8] = math.exp(th_o[0]), math.acos(th_o[6]), math.asin(th_o[8])
+    ref_o = oracle.het_prepare(th_o, case["g"], case["d_o"], case["S"], 16)
+    ref_g = M.het_prepare_reference(case["src"].data, th_o, 16)
+    x = I.draw_pt_ensemble(I.rng(66, W), case["x0"], T, W, case["scale"], lo, hi)
+    betas = I.pt_betas(T, 20.0)
+    pt = M.PTSampler(WL.to_dev(x), betas, lo, hi, ref=ref_g, walkers=W, probs=PROBS, seed=11,
+                     precision="fp64")
+    pt.run(1)
+    xg, og = (t.cpu().numpy() for t in pt.state())
+    cg, _ = pt.counters()
+    out0 = oracle.het_loglike(oracle.pt_theta(x), ref_o)
+    xo, oo, co = oracle.pt_run_het(x, out0, T, W, betas, lo, hi, PROBS, 2.0, 11, 0, 1, ref_o)
+    assert np.array_equal(cg, co)
+    assert np.array_equal(xg, xo)
+    assert co[8 * T + 1:9 * T].sum() > 0
