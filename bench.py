@@ -462,6 +462,19 @@ def run_higher_modes(M, WL, g, stream, reps: int = 5) -> dict:
         ms = e0.elapsed_time(e1) / n
         res[prec] = {"ms": ms, "lnL_evals_per_s": nw / (ms * 1e-3)}
         outs[prec] = out.cpu().numpy().copy()
+    # brute-force (direct) likelihood with the six modes, mixed precision, full 1-yr grid
+    nd = 512
+    thd = theta[:, :nd].contiguous()
+    outd = torch.empty((3, nd), dtype=torch.float64, device="cuda")
+    M.direct_loglike_batch_hm(data, thd[:, :8].contiguous(), 0x3F, "mixed")
+    torch.cuda.synchronize()
+    e0.record(stream)
+    M.direct_loglike_batch_hm(data, thd, 0x3F, "mixed", out=outd)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    msd = e0.elapsed_time(e1)
+    res["direct_mixed"] = {"templates": nd, "grid_points": int(g["n"]), "ms": msd,
+                           "templates_per_s": nd / (msd * 1e-3)}
     dmix = np.abs(outs["mixed"][0] - outs["fp64"][0])
     res["accuracy_mixed_vs_fp64_kernel"] = {"abs_dlnL_p50": float(np.median(dmix)),
                                             "abs_dlnL_p99": float(np.quantile(dmix, 0.99)),

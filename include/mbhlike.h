@@ -303,12 +303,10 @@ MBH_API void mbh_server_free(mbh_server* server);
  * H_lm(x), x = (pi M f2)^{2/3}; polarisations from the spin-weighted harmonics
  * -2Y_lm(iota, phi_ref).  Mode mask: bit 0 (2,2), bit 1 (3,3), bit 2 (4,4),
  * bit 3 (2,1), bit 4 (3,2), bit 5 (4,3); mask 1 is W0 and these calls then do
- * exactly what the (2,2) calls do.  template_batch_hm and direct_loglike_batch_hm
- * evaluate masks with higher modes in float64 only (MBH_MIXED returns
- * MBH_EINVAL); the heterodyned likelihood of a higher-mode reference runs in both
- * precisions (mixed: the delta form per mode, each mode's large phase difference in
- * double-float).  Layouts, ownership and errors as in the (2,2) calls; an empty
- * mask or bits above 5 return MBH_EINVAL. */
+ * exactly what the (2,2) calls do.  Both precisions: the mixed path evaluates each
+ * mode's large phase in double-float and its response in float32 (heterodyne: the
+ * delta form per mode).  Layouts, ownership and errors as in the (2,2) calls (mixed
+ * templates are complex64); an empty mask or bits above 5 return MBH_EINVAL. */
 MBH_API mbh_status template_batch_hm(const mbh_grid* grid, const double* theta_dev, int64_t W,
                                      uint32_t modes, mbh_precision precision, void* h_out_dev,
                                      void* stream);

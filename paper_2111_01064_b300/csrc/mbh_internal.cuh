@@ -89,9 +89,9 @@ mbh_status launch_stored(const mbh_data* data, const void* h, int64_t W, mbh_pre
 
 // mixed-precision entry points (mbh_mixed.cu)
 mbh_status launch_template_mixed(const mbh_grid* g, const double* theta, int64_t W, float2* h,
-                                 cudaStream_t st);
+                                 cudaStream_t st, uint32_t modes = 1u);
 mbh_status launch_direct_fused_mixed(const mbh_data* data, const double* theta, int64_t W,
-                                     double* out, cudaStream_t st);
+                                     double* out, cudaStream_t st, uint32_t modes = 1u);
 cudaError_t alloc_ref_tables(mbh_ref* R);
 mbh_status make_freq_tables(mbh_data* D, cudaStream_t st);
 void free_ref_tables(mbh_ref* R);

@@ -216,8 +216,6 @@ namespace mbh {
 mbh_status check_modes(uint32_t modes, mbh_precision precision)
 {
     if (modes == 0u || (modes & ~kHmAll)) return fail(MBH_EINVAL, "mode mask 0x%x: bits 0-5, not empty", modes);
-    if (modes != 1u && precision != MBH_FP64)
-        return fail(MBH_EINVAL, "templates and direct likelihoods with higher modes are float64 only");
     if (precision != MBH_FP64 && precision != MBH_MIXED) return fail(MBH_EINVAL, "unknown precision %d", (int)precision);
     return MBH_OK;
 }
@@ -234,6 +232,8 @@ extern "C" mbh_status template_batch_hm(const mbh_grid* grid, const double* thet
     if (W == 0) return MBH_OK;
     if (!theta_dev || !h_out_dev) return fail(MBH_EINVAL, "NULL buffer");
     if (mbh_status s = check_device()) return s;
+    if (precision == MBH_MIXED)
+        return launch_template_mixed(grid, theta_dev, W, (float2*)h_out_dev, (cudaStream_t)stream, modes);
     return launch_template_f64(grid, theta_dev, W, (double2*)h_out_dev, (cudaStream_t)stream, modes);
 }
 
@@ -479,6 +479,8 @@ extern "C" mbh_status direct_loglike_batch_hm(const mbh_data* data, const double
     if (W < 0) return fail(MBH_EINVAL, "W < 0");
     if (W == 0) return MBH_OK;
     if (!theta_dev || !out_dev) return fail(MBH_EINVAL, "NULL buffer");
+    if (precision == MBH_MIXED)
+        return launch_direct_fused_mixed(data, theta_dev, W, out_dev, (cudaStream_t)stream, modes);
     return direct_f64(data, theta_dev, W, modes, out_dev, (cudaStream_t)stream);
 }
 

@@ -420,6 +420,8 @@ __device__ __forceinline__ float mode_vpow(const WalkerDF& w, const FreqDF& q2, 
     return p == 0 ? 1.0f : p == 1 ? v : p == 2 ? v * v : v * v * v;
 }
 
+
+
 // phase modulo 2 pi in double-float, then float32
 __device__ __forceinline__ float reduce_phase(f2 p)
 {
@@ -442,6 +444,34 @@ __device__ __forceinline__ bool point_mixed(const WalkerDF& w, const WalkerF& wf
 #pragma unroll
     for (int c = 0; c < 3; ++c) h[c] = fmul(e, T[c]);
     return true;
+}
+
+// Mixed template of the walker's modes at one grid point (times `scale`): per mode the (2,2)
+// chain at f2, the phase scaled by m/2 and reduced modulo 2 pi in double-float, the response
+// at t_lm with the mode's factors; summed.  Returns false when no mode is in its support.
+__device__ __forceinline__ bool point_mixed_hm(const WalkerDF& w, const WalkerF& wf, const WalkerHMF& wh,
+                                               const FreqDF& q, f2 t_obs, float scale, uint32_t modes,
+                                               cf h[3])
+{
+    h[0] = h[1] = h[2] = {0.0f, 0.0f};
+    bool any = false;
+    for (int b = 0; b < kHmModes; ++b) {
+        if (!(modes & (1u << b))) continue;
+        const FreqDF q2 = mode_tables(q, b);
+        f2 Phi;
+        float sa, ca, amp;
+        if (!phase_df(w, wf, q2, t_obs, Phi, sa, ca, amp)) continue;
+        any = true;
+        float sp, cp;
+        sincos_small(reduce_phase(mode_phase(Phi, b)), &sp, &cp);
+        cf T[3];
+        transfer_f32(wf, &wh.hk[b][0], &wh.hk[b][2], q.f.hi, sa, ca, T);
+        const float a = amp * mode_vpow(w, q2, b) * scale;
+        const cf e = {a * cp, -a * sp};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) h[c] = fadd(h[c], fmul(e, T[c]));
+    }
+    return any;
 }
 
 }  // namespace mbh
@@ -488,16 +518,21 @@ extern "C" mbh_status mbh_selftest_math(int32_t kind, const float* x_dev, const 
 constexpr int kTplThreadsM = 128;
 constexpr int kTplPerThreadM = 4;
 
+template <bool kHM>
 __global__ void __launch_bounds__(kTplThreadsM)
     template_mixed_kernel(const double* __restrict__ theta, int64_t W, double f0, double df,
-                          int64_t n, double t_obs, float2* __restrict__ h)
+                          int64_t n, double t_obs, uint32_t modes, float2* __restrict__ h)
 {
     __shared__ WalkerF wsf;
     __shared__ WalkerDF wsd;
+    __shared__ WalkerHMF wsh;
     const f2 tob = split_d(t_obs);
     for (int64_t wi = blockIdx.y; wi < W; wi += gridDim.y) {
         __syncthreads();
-        if (threadIdx.x == 0) walker_setup_mixed(theta, W, wi, wsd, wsf);
+        if (threadIdx.x == 0) {
+            walker_setup_mixed(theta, W, wi, wsd, wsf);
+            if (kHM) walker_setup_hm(theta, W, wi, wsh);
+        }
         __syncthreads();
         const int64_t base = (int64_t)blockIdx.x * kTplThreadsM * kTplPerThreadM + threadIdx.x;
 #pragma unroll
@@ -506,7 +541,10 @@ __global__ void __launch_bounds__(kTplThreadsM)
             if (k < n) {
                 const FreqDF q = freq_tables(f0 + (double)k * df);
                 cf v[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-                point_mixed(wsd, wsf, q, tob, 1.0f, v);
+                if (kHM)
+                    point_mixed_hm(wsd, wsf, wsh, q, tob, 1.0f, modes, v);
+                else
+                    point_mixed(wsd, wsf, q, tob, 1.0f, v);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) h[((int64_t)wi * 3 + c) * n + k] = make_float2(v[c].re, v[c].im);
             }
@@ -515,11 +553,14 @@ __global__ void __launch_bounds__(kTplThreadsM)
 }
 
 mbh_status mbh::launch_template_mixed(const mbh_grid* g, const double* theta, int64_t W, float2* h,
-                                      cudaStream_t st)
+                                      cudaStream_t st, uint32_t modes)
 {
     const int64_t per_block = (int64_t)kTplThreadsM * kTplPerThreadM;
     dim3 grid((unsigned)((g->n + per_block - 1) / per_block), (unsigned)std::min<int64_t>(W, 65535));
-    template_mixed_kernel<<<grid, kTplThreadsM, 0, st>>>(theta, W, g->f0, g->df, g->n, g->t_obs, h);
+    if (modes == 1u)
+        template_mixed_kernel<false><<<grid, kTplThreadsM, 0, st>>>(theta, W, g->f0, g->df, g->n, g->t_obs, modes, h);
+    else
+        template_mixed_kernel<true><<<grid, kTplThreadsM, 0, st>>>(theta, W, g->f0, g->df, g->n, g->t_obs, modes, h);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? MBH_OK : cuda_fail(e, "template_mixed_kernel");
 }
@@ -534,22 +575,26 @@ constexpr int kDirThreadsM = 256;
 // float64 sums in shared memory (a dynamically indexed register array would go to local
 // memory), reduced per walker at the end.  Data and templates are in units where h/sigma is
 // O(1) (float32 range); per-point products are float32, sums float64.
-template <int T>
+template <int T, bool kHM>
 __global__ void __launch_bounds__(kDirThreadsM, 2)
     direct_fused_mixed_kernel(const double* __restrict__ theta, int64_t W, const float4* __restrict__ ft1,
                               const float4* __restrict__ ft2, double t_obs,
                               const float2* __restrict__ wd, const float* __restrict__ wv,
-                              int64_t n, int64_t chunk, int nchunks, float inv_sigma,
+                              int64_t n, int64_t chunk, int nchunks, float inv_sigma, uint32_t modes,
                               double2* __restrict__ part)
 {
     __shared__ WalkerDF wsd[T];
     __shared__ WalkerF wsf[T];
+    __shared__ WalkerHMF wsh[kHM ? T : 1];
     __shared__ double2 acc[T][kDirThreadsM];
     __shared__ double sm[32 * 2];
     const int64_t w0 = (int64_t)blockIdx.x * T;
     const int ch = blockIdx.y;
     const int nt = (int)std::min<int64_t>(T, W - w0);
-    if (threadIdx.x < nt) walker_setup_mixed(theta, W, w0 + threadIdx.x, wsd[threadIdx.x], wsf[threadIdx.x]);
+    if (threadIdx.x < nt) {
+        walker_setup_mixed(theta, W, w0 + threadIdx.x, wsd[threadIdx.x], wsf[threadIdx.x]);
+        if (kHM) walker_setup_hm(theta, W, w0 + threadIdx.x, wsh[threadIdx.x]);
+    }
 #pragma unroll
     for (int t = 0; t < T; ++t) acc[t][threadIdx.x] = make_double2(0.0, 0.0);
     const f2 tob = split_d(t_obs);
@@ -567,7 +612,9 @@ __global__ void __launch_bounds__(kDirThreadsM, 2)
         }
         for (int t = 0; t < nt; ++t) {
             cf h[3];
-            if (point_mixed(wsd[t], wsf[t], q, tob, inv_sigma, h)) {
+            const bool in = kHM ? point_mixed_hm(wsd[t], wsf[t], wsh[t], q, tob, inv_sigma, modes, h)
+                                : point_mixed(wsd[t], wsf[t], q, tob, inv_sigma, h);
+            if (in) {
                 float pd = 0.0f, ph = 0.0f;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
@@ -612,7 +659,7 @@ mbh_status mbh::make_freq_tables(mbh_data* D, cudaStream_t st)
 }
 
 mbh_status mbh::launch_direct_fused_mixed(const mbh_data* data, const double* theta, int64_t W,
-                                          double* out, cudaStream_t st)
+                                          double* out, cudaStream_t st, uint32_t modes)
 {
     constexpr int T = 8;
     const int64_t tiles = (W + T - 1) / T;
@@ -624,9 +671,14 @@ mbh_status mbh::launch_direct_fused_mixed(const mbh_data* data, const double* th
     cudaError_t e = cudaMallocAsync(&part, sizeof(double2) * W * nchunks, st);
     if (e != cudaSuccess) return cuda_fail(e, "direct_loglike_batch alloc");
     dim3 grid((unsigned)tiles, (unsigned)nchunks);
-    direct_fused_mixed_kernel<T><<<grid, kDirThreadsM, 0, st>>>(
-        theta, W, data->ftab, data->ftab2, data->grid.t_obs, data->wd32, data->wv32,
-        data->grid.n, chunk, nchunks, (float)(1.0 / data->sigma), part);
+    if (modes == 1u)
+        direct_fused_mixed_kernel<T, false><<<grid, kDirThreadsM, 0, st>>>(
+            theta, W, data->ftab, data->ftab2, data->grid.t_obs, data->wd32, data->wv32,
+            data->grid.n, chunk, nchunks, (float)(1.0 / data->sigma), modes, part);
+    else
+        direct_fused_mixed_kernel<T, true><<<grid, kDirThreadsM, 0, st>>>(
+            theta, W, data->ftab, data->ftab2, data->grid.t_obs, data->wd32, data->wv32,
+            data->grid.n, chunk, nchunks, (float)(1.0 / data->sigma), modes, part);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "direct_fused_mixed_kernel");
     return direct_finish(part, nchunks, W, data->dd, out, st);

@@ -2,8 +2,8 @@
 templates, the direct likelihood, the heterodyne reference (band, edges, summary data) and
 likelihood, and the Module-1 sampler with higher-mode templates, all float64.  Tolerances as
 in the (2,2) parity tests: templates within 1e-8 of max|h|; lnL within 1e-6 of the size of
-the terms; edges bit-exact.  The heterodyne also runs in mixed precision (per-mode delta
-form); templates and the direct likelihood with higher modes are float64 only."""
+the terms; edges bit-exact.  The mixed-precision paths (templates, the fused direct
+likelihood, the heterodyne's per-mode delta form) are held to the (2,2) mixed tolerances."""
 import math
 
 import numpy as np
@@ -137,14 +137,32 @@ def test_mixed_batch_of_both_kinds(M, WL, case):
     assert np.array_equal(out[:, :10], a) and np.array_equal(out[:, 10:], b)
 
 
-def test_mixed_templates_with_higher_modes_refused(M, WL, case):
+def test_mixed_templates_and_direct(M, WL, oracle, case):
+    """Mixed-precision higher-mode templates (complex64) and fused direct likelihood, with the
+    (2,2) mixed path's tolerances: templates within 2e-5 of max|h| per channel, lnL within
+    1e-5 of the terms; supports bit-exact."""
+    g, th = case["g"], case["walk"][:, :4]
+    h_g = M.template_batch(g, WL.to_dev(th), "mixed", modes=ALL).cpu().numpy()
+    h_o = oracle.template_batch(th, g, ALL)
+    for w in range(th.shape[1]):
+        for c in range(3):
+            ref = np.abs(h_o[w, c]).max()
+            assert np.abs(h_g[w, c] - h_o[w, c]).max() <= 2e-5 * ref
+    np.testing.assert_array_equal(h_g[:, 0] == 0, h_o[:, 0] == 0)
+    out_g = M.direct_loglike_batch_hm(case["data"], WL.to_dev(case["walk"]), ALL, "mixed").cpu().numpy()
+    out_o = oracle.direct(case["walk"], g, case["d_o"], case["S"], ALL)
+    _close(out_g, out_o, case["dd_o"], rel=1e-5)
+
+
+def test_invalid_mode_masks(M, WL, case):
     th = WL.to_dev(case["walk"][:, :2])
-    with pytest.raises(M.MBHError):
-        M.template_batch(case["g"], th, "mixed", modes=ALL)
-    with pytest.raises(M.MBHError):
-        M.direct_loglike_batch_hm(case["data"], th, ALL, "mixed")
-    with pytest.raises(M.MBHError):
-        M.template_batch(case["g"], th, "fp64", modes=0x40)
+    for bad in (0x40, 0x0):
+        with pytest.raises(M.MBHError):
+            M.template_batch(case["g"], th, "fp64", modes=bad)
+        with pytest.raises(M.MBHError):
+            M.direct_loglike_batch_hm(case["data"], th, bad)
+        with pytest.raises(M.MBHError):
+            M.het_prepare_reference(case["data"], case["th"], 16, modes=bad)
 
 
 def test_sampler_direct_higher_modes(M, WL, oracle):
