@@ -629,11 +629,27 @@ def run_serving(M, WL, cfg=None, n_sources: int = 32, seconds: float = 1.0,
         ref = M.het_loglike_batch([ub.refs[s]], [0, n], th, "fp64").cpu().numpy()
         errs.append(np.abs(out[0] - ref[0]))
     e = np.concatenate(errs) if errs else np.zeros(1)
+    # the same sources driven by native client threads (the server's own capacity: the Python
+    # clients above saturate first)
+    native = []
+    rate = 1600.0
+    P = min(p.shape[1] for p in pools)
+    npools = [np.ascontiguousarray(p[:, :P]) for p in pools]
+    while rate <= 409600.0:
+        r = srv.loadgen(ids, npools, rate, seconds, 64, min(4096, P), seed=int(rate))
+        native.append(r)
+        if (r["completed_per_s"] < 0.8 * rate or r["p99_ms"] > 100.0
+                or r["rejected"] > 0.01 * max(1, r["submitted"])):
+            break
+        rate *= 2
     srv.close()
     best = max(steps, key=lambda d: d["walkers_per_s"])
+    best_native = max(native, key=lambda d: d["walkers_per_s"])
     return {"sources": n_sources, "samplers": n_sources, "request_walkers": [64, 4096],
             "bins_range": [int(ub.bins.min()), int(ub.bins.max())], "seconds_per_rate": seconds,
             "rates": steps, "peak_walkers_per_s": best["walkers_per_s"],
+            "native_clients": {"rates": native, "peak_walkers_per_s": best_native["walkers_per_s"],
+                               "peak_completed_req_per_s": best_native["completed_per_s"]},
             "abs_dlnL_vs_fp64_kernel": {"p50": float(np.median(e)), "p99": float(np.quantile(e, 0.99)),
                                         "max": float(e.max()), "walkers": int(e.size)}}
 

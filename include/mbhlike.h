@@ -294,6 +294,32 @@ MBH_API mbh_status mbh_server_reset_stats(mbh_server* server);
 /* Cancels queued requests, waits for batches in flight, stops the worker. */
 MBH_API void mbh_server_free(mbh_server* server);
 
+/* Load generator for measuring a server (no counterpart in the paper; the
+ * "sampler threads" of a serving benchmark): n_clients threads, client c submits
+ * requests for source_ids[c] at Poisson arrival times with total rate
+ * rate_per_s for `seconds` (open loop), sizes log-uniform in
+ * [min_walkers, max_walkers], walkers copied from pools_host[c] (host float64
+ * [11][pool], SoA); results are reaped as they complete.  Resets the server's
+ * statistics first; blocks until every accepted request has completed.  Requests
+ * refused by a full queue count as rejected.  MBH_EINVAL for bad options. */
+typedef struct {
+    double rate_per_s;
+    double seconds;
+    int32_t min_walkers, max_walkers;
+    uint64_t seed;
+} mbh_loadgen_opts;
+typedef struct {
+    double offered_per_s;
+    int64_t submitted, completed, rejected, failed;
+    double wall_seconds, completed_per_s, walkers_per_s;
+    double p50_ms, p99_ms, max_ms;        /* submit -> results written, server side */
+    int64_t batches;
+    double mean_batch_walkers;
+} mbh_loadgen_report;
+MBH_API mbh_status mbh_server_loadgen(mbh_server* server, const int32_t* source_ids, int32_t n_clients,
+                                      const double* const* pools_host, int64_t pool,
+                                      const mbh_loadgen_opts* opts, mbh_loadgen_report* out);
+
 /* ---- Higher harmonics (Sec. II A, Eqs. 7-9) ------------------------------
  * Templates summed over harmonic modes (l, m), each with its own time-frequency
  * map t_lm(f) (Eq. 8) and its own response at t_lm (Eq. 9).  The model is the

@@ -26,6 +26,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <random>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -502,4 +503,96 @@ extern "C" void mbh_server_free(mbh_server* S)
         cudaFreeHost(sl->out_host);
     }
     delete S;
+}
+
+// ------------------------------------------------------------------------------------------
+// Load generator: n_clients sampler threads, each submitting requests of its own source at
+// Poisson arrival times (open loop: a client does not wait for a result before its next
+// arrival), request sizes log-uniform in [min_walkers, max_walkers], walkers taken from the
+// client's pool; results are collected as they complete.  The server's statistics are reset
+// at the start, so its latency percentiles describe this run.
+// ------------------------------------------------------------------------------------------
+extern "C" mbh_status mbh_server_loadgen(mbh_server* S, const int32_t* source_ids, int32_t n_clients,
+                                         const double* const* pools_host, int64_t pool,
+                                         const mbh_loadgen_opts* o, mbh_loadgen_report* out)
+{
+    if (!S || !source_ids || !pools_host || !o || !out) return fail(MBH_EINVAL, "NULL argument");
+    if (n_clients < 1 || pool < 1) return fail(MBH_EINVAL, "need n_clients >= 1 and pool >= 1");
+    if (!(o->rate_per_s > 0.0) || !(o->seconds > 0.0)) return fail(MBH_EINVAL, "rate and seconds must be > 0");
+    if (o->min_walkers < 1 || o->max_walkers < o->min_walkers || o->max_walkers > pool ||
+        o->max_walkers > S->opts.max_batch_walkers)
+        return fail(MBH_EINVAL, "request sizes must satisfy 1 <= min <= max <= min(pool, max_batch_walkers)");
+    for (int32_t c = 0; c < n_clients; ++c)
+        if (!pools_host[c]) return fail(MBH_EINVAL, "pool %d is NULL", c);
+    mbh_server_reset_stats(S);
+    std::atomic<int64_t> submitted{0}, completed{0}, rejected{0}, failed{0}, walkers{0};
+    const auto t0 = Clock::now() + std::chrono::milliseconds(5);
+    auto client = [&](int32_t c) {
+        std::mt19937_64 rng(o->seed * 1000003ull + (uint64_t)c);
+        std::exponential_distribution<double> gap(o->rate_per_s / n_clients);
+        std::uniform_real_distribution<double> lsz(std::log((double)o->min_walkers), std::log((double)o->max_walkers + 1.0));
+        struct Out {
+            uint64_t id;
+            int64_t W;
+            std::vector<double> res;
+        };
+        std::deque<Out> outstanding;
+        std::vector<double> th;
+        auto reap = [&](bool block) {
+            while (!outstanding.empty()) {
+                mbh_status rs = MBH_OK;
+                const mbh_status w = mbh_server_wait(S, outstanding.front().id, block ? -1 : 0, &rs);
+                if (w == MBH_ETIMEOUT) return;
+                if (w == MBH_OK && rs == MBH_OK) {
+                    ++completed;
+                    walkers += outstanding.front().W;
+                } else {
+                    ++failed;
+                }
+                outstanding.pop_front();
+            }
+        };
+        double t = 0.0;
+        while (true) {
+            t += gap(rng);
+            if (t > o->seconds) break;
+            const int64_t W = std::min<int64_t>(o->max_walkers, std::max<int64_t>(o->min_walkers, (int64_t)std::exp(lsz(rng))));
+            const int64_t off = (int64_t)(rng() % (uint64_t)(pool - W + 1));
+            th.resize(11 * W);
+            for (int j = 0; j < 11; ++j)
+                std::memcpy(th.data() + (int64_t)j * W, pools_host[c] + (int64_t)j * pool + off, sizeof(double) * W);
+            std::this_thread::sleep_until(t0 + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(t)));
+            Out rec{0, W, std::vector<double>(3 * W)};
+            const mbh_status st = mbh_server_submit(S, source_ids[c], th.data(), W, rec.res.data(), &rec.id);
+            if (st == MBH_OK) {
+                ++submitted;
+                outstanding.push_back(std::move(rec));
+            } else {
+                ++rejected;
+            }
+            reap(false);
+        }
+        reap(true);
+    };
+    std::vector<std::thread> threads;
+    for (int32_t c = 0; c < n_clients; ++c) threads.emplace_back(client, c);
+    for (auto& th : threads) th.join();
+    const double wall = std::chrono::duration<double>(Clock::now() - t0).count();
+    mbh_server_report rep{};
+    mbh_server_stats(S, &rep);
+    std::memset(out, 0, sizeof *out);
+    out->offered_per_s = o->rate_per_s;
+    out->submitted = submitted.load();
+    out->completed = completed.load();
+    out->rejected = rejected.load();
+    out->failed = failed.load();
+    out->wall_seconds = wall;
+    out->completed_per_s = completed.load() / wall;
+    out->walkers_per_s = walkers.load() / wall;
+    out->p50_ms = rep.p50_ms;
+    out->p99_ms = rep.p99_ms;
+    out->max_ms = rep.max_ms;
+    out->batches = rep.batches;
+    out->mean_batch_walkers = rep.mean_batch_walkers;
+    return MBH_OK;
 }

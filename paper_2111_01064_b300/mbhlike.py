@@ -69,6 +69,22 @@ class PTOpts(C.Structure):
                 ("modes", C.c_uint32)]
 
 
+class LoadgenOpts(C.Structure):
+    _fields_ = [("rate_per_s", C.c_double), ("seconds", C.c_double), ("min_walkers", C.c_int32),
+                ("max_walkers", C.c_int32), ("seed", C.c_uint64)]
+
+
+class LoadgenReport(C.Structure):
+    _fields_ = [("offered_per_s", C.c_double), ("submitted", C.c_int64), ("completed", C.c_int64),
+                ("rejected", C.c_int64), ("failed", C.c_int64), ("wall_seconds", C.c_double),
+                ("completed_per_s", C.c_double), ("walkers_per_s", C.c_double), ("p50_ms", C.c_double),
+                ("p99_ms", C.c_double), ("max_ms", C.c_double), ("batches", C.c_int64),
+                ("mean_batch_walkers", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 def grid_struct(g: dict) -> Grid:
     return Grid(float(g["f0"]), float(g["df"]), int(g["n"]), float(g["t_obs"]))
 
@@ -128,6 +144,8 @@ def lib() -> C.CDLL:
         "direct_loglike_batch_hm": (C.c_int, [vp, vp, i64, C.c_uint32, C.c_int, vp, vp]),
         "het_prepare_reference_hm": (C.c_int, [vp, dp, i32, C.c_uint32, vp, C.POINTER(vp)]),
         "mbh_pt_create": (C.c_int, [C.POINTER(PTOpts), vp, vp, dp, vp, vp, C.POINTER(vp)]),
+        "mbh_server_loadgen": (C.c_int, [vp, C.POINTER(C.c_int32), i32, C.POINTER(dp), i64,
+                                         C.POINTER(LoadgenOpts), C.POINTER(LoadgenReport)]),
         "mbh_pt_run": (C.c_int, [vp, i64, i32, vp]),
         "mbh_pt_state": (C.c_int, [vp, vp, vp, vp]),
         "mbh_pt_set_state": (C.c_int, [vp, vp, vp]),
@@ -494,6 +512,22 @@ class Server:
         r = ServerReport()
         _check(lib().mbh_server_stats(self.handle, C.byref(r)))
         return r.as_dict()
+
+    def loadgen(self, source_ids, pools, rate_per_s: float, seconds: float, min_walkers: int = 64,
+                max_walkers: int = 4096, seed: int = 0) -> dict:
+        """Native load generator (one C++ client thread per source, Poisson arrivals, open
+        loop); pools: one float64 (11, P) host array per client."""
+        n = len(source_ids)
+        pools = [np.ascontiguousarray(np.asarray(p, dtype=np.float64)) for p in pools]
+        P = pools[0].shape[1]
+        if any(p.shape != (11, P) for p in pools):
+            raise MBHError(1, "pools must all be (11, P)")
+        ids = (C.c_int32 * n)(*[int(i) for i in source_ids])
+        ptrs = (dp * n)(*[p.ctypes.data_as(dp) for p in pools])
+        o = LoadgenOpts(float(rate_per_s), float(seconds), int(min_walkers), int(max_walkers), int(seed))
+        rep = LoadgenReport()
+        _check(lib().mbh_server_loadgen(self.handle, ids, n, ptrs, P, C.byref(o), C.byref(rep)))
+        return rep.as_dict()
 
     def reset_stats(self):
         _check(lib().mbh_server_reset_stats(self.handle))

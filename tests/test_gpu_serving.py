@@ -174,3 +174,22 @@ def test_reference_refresh_hot_swap(env):
     dr = M.direct_loglike_batch(src.data, torch.from_numpy(th).cuda(), "fp64").cpu().numpy()
     assert abs(got[0, best] - dr[0, best]) <= 1e-3
     srv.close()
+
+
+def test_native_load_generator(env):
+    """Client threads in the library drive the server at Poisson arrival times: every accepted
+    request completes, the latency statistics cover them, and invalid options are refused."""
+    M, WL, ub = env
+    srv = M.Server(1 << 30, max_batch_walkers=16384, max_inflight_batches=3, precision="mixed")
+    ids = [srv.add_source(r) for r in ub.refs[:4]]
+    P = int(min(ub.offsets[s + 1] - ub.offsets[s] for s in range(4)))
+    pools = [np.ascontiguousarray(ub.theta[:, ub.offsets[s]:ub.offsets[s] + P]) for s in range(4)]
+    rep = srv.loadgen(ids, pools, 400.0, 0.5, 1, P, seed=3)
+    assert rep["submitted"] > 100 and rep["completed"] == rep["submitted"] and rep["failed"] == 0
+    assert 0 < rep["p50_ms"] <= rep["p99_ms"] <= rep["max_ms"]
+    assert srv.stats()["completed"] == rep["completed"]
+    with pytest.raises(M.MBHError):
+        srv.loadgen(ids, pools, 400.0, 0.5, 1, P + 1)    # larger than the pools
+    with pytest.raises(M.MBHError):
+        srv.loadgen(ids, pools, 0.0, 0.5, 1, P)
+    srv.close()
