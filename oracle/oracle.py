@@ -74,9 +74,10 @@ def lib():
             "oracle_pt_run_het": (None, [dp, dp, C.c_long, C.c_long, dp, dp, dp, dp, C.c_double,
                                          C.c_uint64, C.c_uint64, C.c_long, C.c_long, lp,
                                          C.c_double, C.c_double, C.c_double, dp, dp, C.c_double,
-                                         lp]),
+                                         lp, C.c_double, C.c_double]),
             "oracle_pt_run_gauss": (None, [dp, dp, C.c_long, C.c_long, dp, dp, dp, dp, C.c_double,
-                                           C.c_uint64, C.c_uint64, C.c_long, dp, dp, lp, dp]),
+                                           C.c_uint64, C.c_uint64, C.c_long, dp, dp, lp, dp,
+                                           C.c_double, C.c_double, dp]),
             "oracle_pt_gauss_loglike": (None, [dp, C.c_long, dp, dp, dp]),
             "oracle_pt_run_direct": (None, [dp, dp, C.c_long, C.c_long, dp, dp, dp, dp, C.c_double,
                                             C.c_uint64, C.c_uint64, C.c_long, C.c_double,
@@ -378,19 +379,23 @@ def pt_sky(x, n, m) -> np.ndarray:
 def _pt_common(x, out, betas, lo, hi, probs):
     x = np.ascontiguousarray(_f64(x)).copy()
     out = np.ascontiguousarray(_f64(out)).copy()
-    return x, out, _f64(betas), _f64(lo), _f64(hi), _f64(probs)
+    return x, out, _f64(betas).copy(), _f64(lo), _f64(hi), _f64(probs)
 
 
-def pt_run_het(x, out, T, W, betas, lo, hi, probs, a, seed, step0, n_iter, ref: dict):
-    """n_iter sampler iterations with the heterodyned likelihood; returns (x, out, counters)."""
+def pt_run_het(x, out, T, W, betas, lo, hi, probs, a, seed, step0, n_iter, ref: dict,
+               adapt=None, return_betas=False):
+    """n_iter sampler iterations with the heterodyned likelihood; returns (x, out, counters)
+    (and the final ladder with return_betas).  adapt = (nu, n0) adapts the ladder."""
     x, out, betas, lo, hi, probs = _pt_common(x, out, betas, lo, hi, probs)
     cnt = np.zeros(10 * T, dtype=np.int64)
     g = ref["grid"]
+    nu, n0 = adapt if adapt else (0.0, 0.0)
     lib().oracle_pt_run_het(_d(x), _d(out), T, W, _d(betas), _d(lo), _d(hi), _d(probs), a,
                             seed, step0, n_iter, ref["E"], _l(ref["edges"]), g["f0"], g["df"],
                             g["t_obs"], _d(_f64(ref["summary"]).ravel()),
-                            _d(_c128(ref["h0e"]).view(np.float64)), ref["dd"], _l(cnt))
-    return x, out, cnt
+                            _d(_c128(ref["h0e"]).view(np.float64)), ref["dd"], _l(cnt),
+                            float(nu), float(n0))
+    return (x, out, cnt, betas) if return_betas else (x, out, cnt)
 
 
 def pt_run_direct(x, out, T, W, betas, lo, hi, probs, a, seed, step0, n_iter, grid, d, S,
@@ -406,15 +411,19 @@ def pt_run_direct(x, out, T, W, betas, lo, hi, probs, a, seed, step0, n_iter, gr
 
 
 def pt_run_gauss(x, out, T, W, betas, lo, hi, probs, a, seed, step0, n_iter, mu, sigma,
-                 trace=False):
-    """The sampler on a diagonal Gaussian target in x; returns (x, out, counters, trace)."""
+                 trace=False, adapt=None, beta_trace=False):
+    """The sampler on a diagonal Gaussian target in x; returns (x, out, counters, trace),
+    plus the ladder after every iteration with beta_trace.  adapt = (nu, n0)."""
     x, out, betas, lo, hi, probs = _pt_common(x, out, betas, lo, hi, probs)
     cnt = np.zeros(10 * T, dtype=np.int64)
     tr = np.empty((n_iter, 11, T * W)) if trace else None
+    bt = np.empty((n_iter, T)) if beta_trace else None
+    nu, n0 = adapt if adapt else (0.0, 0.0)
     lib().oracle_pt_run_gauss(_d(x), _d(out), T, W, _d(betas), _d(lo), _d(hi), _d(probs), a,
                               seed, step0, n_iter, _d(_f64(mu)), _d(_f64(sigma)), _l(cnt),
-                              _d(tr) if trace else None)
-    return x, out, cnt, tr
+                              _d(tr) if trace else None, float(nu), float(n0),
+                              _d(bt) if beta_trace else None)
+    return (x, out, cnt, tr, bt) if beta_trace else (x, out, cnt, tr)
 
 
 def pt_gauss_loglike(x, mu, sigma) -> np.ndarray:

@@ -36,6 +36,12 @@
  *                 cold walker k is paired with hot walker sigma_i(k), sigma_i a
  *                 random permutation, and the pair exchanges states iff
  *                 ln u < (beta_{i-1} - beta_i)(lnL_hot - lnL_cold).
+ *   ladder        optionally adapted after every iteration (Vousden, Farr & Mandel 2016):
+ *                 with T_t = 1/beta_t, S_t = ln(T_t - T_{t-1}) for the intermediate
+ *                 temperatures 1 <= t <= T-2 moves by kappa(n) (A_t - A_{t+1}), A_t the
+ *                 fraction of accepted swaps of pair (t, t-1) in this iteration and
+ *                 kappa(n) = (1/nu) n0/(n + n0) at iteration n; the coldest and the hottest
+ *                 temperatures stay fixed, the others are rebuilt from T_0 upwards.
  *   randomness    Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11), key = the
  *                 64-bit seed, counter = (item, purpose, step low, step high); 53-bit
  *                 uniforms from two words; permutations by sorting 48-bit random
@@ -245,9 +251,30 @@ static int cmp_u64(const void* a, const void* b)
    place.  counters (int64, 10 T): [0, 4T) proposals per (t, kind), [4T, 8T) accepted
    per (t, kind), [8T, 9T) accepted swaps per level i (pair i, i-1; entry 0 unused),
    [9T, 10T) proposed swaps per level. */
-static void iteration(double* x, double* out, long T, long W, const double* betas,
+static void adapt_ladder(double* betas, long T, const long* acc_now, long W, uint64_t step, double nu,
+                         double n0)
+{
+    if (T < 3) return;
+    const double kappa = (1.0 / nu) * n0 / ((double)step + n0);
+    double* Tt = malloc(sizeof(double) * T);
+    double* S = malloc(sizeof(double) * T);
+    for (long t = 0; t < T; ++t) Tt[t] = 1.0 / betas[t];
+    for (long t = 1; t <= T - 2; ++t) {
+        const double A = (double)acc_now[t] / (double)W, A1 = (double)acc_now[t + 1] / (double)W;
+        S[t] = log(Tt[t] - Tt[t - 1]) + kappa * (A - A1);
+    }
+    for (long t = 1; t <= T - 2; ++t) {
+        Tt[t] = Tt[t - 1] + exp(S[t]);
+        betas[t] = 1.0 / Tt[t];
+    }
+    free(S);
+    free(Tt);
+}
+
+static void iteration(double* x, double* out, long T, long W, double* betas,
                       const double* lo, const double* hi, const double* probs, double a,
-                      uint64_t seed, uint64_t step, const like_t* L, long* counters)
+                      uint64_t seed, uint64_t step, const like_t* L, long* counters,
+                      double adapt_nu, double adapt_n0)
 {
     const long N = T * W, Wh = W / 2, M = T * Wh;
     double* y = malloc(sizeof(double) * NPAR * M);
@@ -298,6 +325,7 @@ static void iteration(double* x, double* out, long T, long W, const double* beta
     }
     /* temperature swaps, hottest pair first */
     uint64_t* keys = malloc(sizeof(uint64_t) * W);
+    long* acc_now = calloc((size_t)T, sizeof(long));
     for (long i = T - 1; i >= 1; --i) {
         for (long k = 0; k < W; ++k) {
             uint32_t r[4];
@@ -314,6 +342,7 @@ static void iteration(double* x, double* out, long T, long W, const double* beta
             counters[9 * T + i] += 1;
             if (lnu < la) {
                 counters[8 * T + i] += 1;
+                acc_now[i] += 1;
                 for (int p = 0; p < NPAR; ++p) {
                     const double s = x[p * N + hot];
                     x[p * N + hot] = x[p * N + cold];
@@ -327,6 +356,8 @@ static void iteration(double* x, double* out, long T, long W, const double* beta
             }
         }
     }
+    if (adapt_nu > 0.0) adapt_ladder(betas, T, acc_now, W, step, adapt_nu, adapt_n0);
+    free(acc_now);
     free(keys);
     free(oy);
     free(kind);
@@ -336,21 +367,23 @@ static void iteration(double* x, double* out, long T, long W, const double* beta
 }
 
 /* n_iter iterations from step step0 with the heterodyned likelihood. */
-void oracle_pt_run_het(double* x, double* out, long T, long W, const double* betas,
+/* betas (in/out): the ladder, adapted in place when adapt_nu > 0 (adapt_n0 the lag). */
+void oracle_pt_run_het(double* x, double* out, long T, long W, double* betas,
                        const double* lo, const double* hi, const double* probs, double a,
                        uint64_t seed, uint64_t step0, long n_iter, long E, const long* edges,
                        double f0, double df, double t_obs, const double* sum, const double* h0e,
-                       double dd, long* counters)
+                       double dd, long* counters, double adapt_nu, double adapt_n0)
 {
     like_t L = {0, E, edges, f0, df, t_obs, sum, h0e, dd, NULL, NULL, 0, NULL, NULL, 1u};
     for (long s = 0; s < n_iter; ++s)
-        iteration(x, out, T, W, betas, lo, hi, probs, a, seed, step0 + (uint64_t)s, &L, counters);
+        iteration(x, out, T, W, betas, lo, hi, probs, a, seed, step0 + (uint64_t)s, &L, counters,
+                  adapt_nu, adapt_n0);
 }
 
 /* n_iter iterations with the direct likelihood (Module 1 of Sec. III) on the grid
    f_k = f0 + k df, k < n, data d [3][n] complex and PSD S [3][n], templates of the
    harmonic modes of the mask (the higher-mode posterior of Sec. III C uses this form). */
-void oracle_pt_run_direct(double* x, double* out, long T, long W, const double* betas,
+void oracle_pt_run_direct(double* x, double* out, long T, long W, double* betas,
                           const double* lo, const double* hi, const double* probs, double a,
                           uint64_t seed, uint64_t step0, long n_iter, double f0, double df,
                           long n, double t_obs, unsigned modes, const double* d, const double* S,
@@ -358,21 +391,25 @@ void oracle_pt_run_direct(double* x, double* out, long T, long W, const double* 
 {
     like_t L = {2, 0, NULL, f0, df, t_obs, NULL, NULL, 0, NULL, NULL, n, d, S, modes};
     for (long s = 0; s < n_iter; ++s)
-        iteration(x, out, T, W, betas, lo, hi, probs, a, seed, step0 + (uint64_t)s, &L, counters);
+        iteration(x, out, T, W, betas, lo, hi, probs, a, seed, step0 + (uint64_t)s, &L, counters,
+                  0.0, 0.0);
 }
 
 /* The same sampler on lnL = -1/2 sum_p ((x_p - mu_p)/sigma_p)^2 (sigma_p = 0: x_p
    unconstrained); the chain of every sample is appended to trace[n_iter][T][11]
    (the state after each iteration, for moment checks). */
-void oracle_pt_run_gauss(double* x, double* out, long T, long W, const double* betas,
+void oracle_pt_run_gauss(double* x, double* out, long T, long W, double* betas,
                          const double* lo, const double* hi, const double* probs, double a,
                          uint64_t seed, uint64_t step0, long n_iter, const double* mu,
-                         const double* sigma, long* counters, double* trace)
+                         const double* sigma, long* counters, double* trace, double adapt_nu,
+                         double adapt_n0, double* beta_trace)
 {
     like_t L = {1, 0, NULL, 0, 0, 0, NULL, NULL, 0, mu, sigma, 0, NULL, NULL, 1u};
     const long N = T * W;
     for (long s = 0; s < n_iter; ++s) {
-        iteration(x, out, T, W, betas, lo, hi, probs, a, seed, step0 + (uint64_t)s, &L, counters);
+        iteration(x, out, T, W, betas, lo, hi, probs, a, seed, step0 + (uint64_t)s, &L, counters,
+                  adapt_nu, adapt_n0);
+        if (beta_trace) memcpy(beta_trace + s * T, betas, sizeof(double) * T);
         if (trace) memcpy(trace + s * NPAR * N, x, sizeof(double) * NPAR * N);
     }
 }

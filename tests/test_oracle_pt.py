@@ -174,3 +174,30 @@ def test_direct_sampler_bookkeeping(oracle):
                                          g, d, S)
     assert np.array_equal(out1, oracle.direct(oracle.pt_theta(x1), g, d, S))
     assert cnt[:4 * T].sum() == 2 * T * W
+
+
+def test_ladder_adaptation_equalises_swap_rates(oracle):
+    """Vousden et al. adaptation: from a poor ladder (three temperatures crowded near 1 and the
+    prior last) the swap acceptance rates of all adjacent pairs become nearly equal, the
+    coldest and hottest temperatures stay fixed and the ladder stays ordered; without
+    adaptation the same ladder leaves the top pair almost never swapping."""
+    lo, hi, mu, sig = _gauss_setup()
+    T, W = 5, 32
+    b0 = np.array([1.0, 0.9, 0.8, 0.7, 0.0])
+
+    def rates(adapt):
+        g = I.rng(61)
+        x = lo[:, None] + (hi - lo)[:, None] * g.random((11, T * W))
+        out = oracle.pt_gauss_loglike(x, mu, sig)
+        x, out, _, _, bt = oracle.pt_run_gauss(x, out, T, W, b0, lo, hi, PROBS, 2.0, 11, 0, 3000, mu,
+                                               sig, adapt=adapt, beta_trace=True)
+        _, _, cnt, _, bt2 = oracle.pt_run_gauss(x, out, T, W, bt[-1], lo, hi, PROBS, 2.0, 11, 3000,
+                                                1000, mu, sig, adapt=adapt, beta_trace=True)
+        return cnt[8 * T + 1:9 * T] / cnt[9 * T + 1:10 * T], np.concatenate([bt, bt2])
+
+    r0, _ = rates(None)
+    assert r0[-1] < 0.05 and r0[:-1].min() > 0.8
+    r, bt = rates((10.0, 200.0))
+    assert r.min() > 0.1 and r.max() - r.min() < 0.06, r
+    assert np.all(bt[:, 0] == 1.0) and np.all(bt[:, -1] == 0.0)
+    assert np.all(np.diff(bt, axis=1) < 0)
