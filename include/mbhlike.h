@@ -386,6 +386,12 @@ typedef struct {
     mbh_het_config het_config;         /* threads_per_walker 0 = default */
     uint32_t modes;                    /* direct likelihood: harmonic mode mask (0 = (2,2));
                                           a reference brings its own */
+    double adapt_time;                 /* > 0: adapt the ladder every iteration (Vousden et
+                                          al. 2016): ln(T_t - T_{t-1}) moves by kappa (A_t -
+                                          A_{t+1}), kappa = n0/(adapt_time (n + n0)), A_t this
+                                          iteration's swap acceptance of pair (t, t-1); the
+                                          coldest and hottest temperatures stay fixed */
+    double adapt_lag;                  /* n0 (> 0 when adapting) */
 } mbh_pt_opts;
 
 /* x_dev: float64 [11][T W] start positions in x, slot t W + k = walker k of
@@ -406,6 +412,8 @@ MBH_API mbh_status mbh_pt_set_state(mbh_pt* pt, const double* x_dev, void* strea
 /* Reference refresh (Sec. III B): later iterations use `ref`; every walker is
  * rescored against it. */
 MBH_API mbh_status mbh_pt_set_ref(mbh_pt* pt, const mbh_ref* ref, void* stream);
+/* Current inverse temperatures (after any adaptation; synchronises `stream`). */
+MBH_API mbh_status mbh_pt_get_betas(const mbh_pt* pt, double* betas_host, void* stream);
 /* New inverse temperatures (synchronises `stream`). */
 MBH_API mbh_status mbh_pt_set_betas(mbh_pt* pt, const double* betas_host, void* stream);
 /* Reads the counters and the iteration counter (synchronises `stream`). */

@@ -62,12 +62,13 @@ struct PtArgs {
     int32_t* perm;          // [T][W] hot partner of cold walker k at level i
     double* lnu_acc;        // [2][M] ln u of the acceptance tests of both half steps
     double* lnu_swap;       // [T][W] ln u of the swap tests (level 0 unused)
-    const double* betas;    // [T]
+    double* betas;          // [T] (adapted in place when adapt_nu > 0)
     unsigned long long* counters;   // [10 T]
     unsigned long long* step;       // iteration counter
     double lo[kPar], hi[kPar];
     double c1, c2, c3;      // cumulative proposal probabilities
     double a, am1;          // stretch scale and a - 1
+    double adapt_nu, adapt_n0;   // ladder adaptation (nu > 0 enables)
     uint64_t seed;
     int32_t T, W;
 };
@@ -289,6 +290,7 @@ __global__ void __launch_bounds__(kSortThreads) pt_swap_kernel(const PtArgs A)
     double* lnl = sm;                                       // [2][W]
     int32_t* mp = reinterpret_cast<int32_t*>(sm + 2 * W);   // [2][W]
     __shared__ unsigned int acc_level;
+    __shared__ unsigned int acc_now[kMaxTemps];
     const uint64_t step = *A.step;
     if (T > 1) {
         int32_t pm[J], pp[J];
@@ -362,6 +364,7 @@ __global__ void __launch_bounds__(kSortThreads) pt_swap_kernel(const PtArgs A)
             if (threadIdx.x == 0) {
                 A.counters[8 * T + i] += acc_level;
                 A.counters[9 * T + i] += (unsigned long long)W;
+                acc_now[i] = acc_level;
             }
             __syncthreads();
             hot = cold;
@@ -369,7 +372,26 @@ __global__ void __launch_bounds__(kSortThreads) pt_swap_kernel(const PtArgs A)
         for (int k = threadIdx.x; k < W; k += blockDim.x) A.map[k] = mp[hot * W + k];
     }
     __syncthreads();
-    if (threadIdx.x == 0) *A.step = step + 1;
+    if (threadIdx.x == 0) {
+        // ladder adaptation (Vousden, Farr & Mandel 2016): S_t = ln(T_t - T_{t-1}) moves by
+        // kappa (A_t - A_{t+1}), kappa = (1/nu) n0/(n + n0); coldest and hottest fixed
+        if (A.adapt_nu > 0.0 && T >= 3) {
+            const double kappa = __ddiv_rn(__dmul_rn(__ddiv_rn(1.0, A.adapt_nu), A.adapt_n0),
+                                           __dadd_rn((double)step, A.adapt_n0));
+            double Tt[kMaxTemps], S[kMaxTemps];
+            for (int t = 0; t < T; ++t) Tt[t] = __ddiv_rn(1.0, A.betas[t]);
+            for (int t = 1; t <= T - 2; ++t) {
+                const double a0 = __ddiv_rn((double)acc_now[t], (double)W);
+                const double a1 = __ddiv_rn((double)acc_now[t + 1], (double)W);
+                S[t] = __dadd_rn(log(__dsub_rn(Tt[t], Tt[t - 1])), __dmul_rn(kappa, __dsub_rn(a0, a1)));
+            }
+            for (int t = 1; t <= T - 2; ++t) {
+                Tt[t] = __dadd_rn(Tt[t - 1], exp(S[t]));
+                A.betas[t] = __ddiv_rn(1.0, Tt[t]);
+            }
+        }
+        *A.step = step + 1;
+    }
 }
 
 // theta(x) of every physical column (rescoring)
@@ -481,7 +503,7 @@ void free_pt(mbh_pt* P)
     if (P->join_draws) cudaEventDestroy(P->join_draws);
     PtArgs& A = P->A;
     void* bufs[] = {A.x, A.out, A.map, A.y, A.theta, A.out_p, A.fac, A.flag, A.perm, A.lnu_acc, A.lnu_swap,
-                    (void*)A.betas, A.counters, A.step, P->res};
+                    A.betas, A.counters, A.step, P->res};
     for (void* b : bufs)
         if (b) cudaFree(b);
     delete P;
@@ -603,6 +625,7 @@ extern "C" mbh_status mbh_pt_create(const mbh_pt_opts* o, const mbh_ref* ref, co
     if (!(csum > 0.0 && csum <= 1.0 + 1e-12)) return fail(MBH_EINVAL, "proposal probabilities must sum to (0, 1]");
     for (int p = 0; p < kPar; ++p)
         if (!(o->lo[p] <= o->hi[p])) return fail(MBH_EINVAL, "prior box: lo[%d] > hi[%d]", p, p);
+    if (o->adapt_time > 0.0 && !(o->adapt_lag > 0.0)) return fail(MBH_EINVAL, "adapt_lag must be > 0");
     for (int t = 0; t < o->ntemps; ++t)
         if (!(betas_host[t] >= 0.0) || !std::isfinite(betas_host[t])) return fail(MBH_EINVAL, "betas must be finite and >= 0");
     if (o->precision != MBH_FP64 && o->precision != MBH_MIXED) return fail(MBH_EINVAL, "unknown precision");
@@ -629,6 +652,8 @@ extern "C" mbh_status mbh_pt_create(const mbh_pt_opts* o, const mbh_ref* ref, co
     A.seed = o->seed;
     A.a = o->a;
     A.am1 = o->a - 1.0;
+    A.adapt_nu = o->adapt_time > 0.0 ? o->adapt_time : 0.0;
+    A.adapt_n0 = o->adapt_lag;
     A.c1 = o->probs[0];
     A.c2 = A.c1 + o->probs[1];
     A.c3 = A.c2 + o->probs[2];
@@ -674,7 +699,7 @@ extern "C" mbh_status mbh_pt_create(const mbh_pt_opts* o, const mbh_ref* ref, co
     if (e == cudaSuccess) e = cudaFuncSetAttribute(pt_swap_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, swap_max);
     cudaStream_t st = (cudaStream_t)stream;
     const unsigned long long zero = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync((void*)A.betas, betas_host, sizeof(double) * A.T, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(A.betas, betas_host, sizeof(double) * A.T, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(A.counters, 0, sizeof(unsigned long long) * 10 * A.T, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(A.step, &zero, sizeof zero, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(A.perm, 0, sizeof(int32_t) * N, st);
@@ -757,10 +782,19 @@ extern "C" mbh_status mbh_pt_set_betas(mbh_pt* P, const double* betas_host, void
     for (int t = 0; t < P->A.T; ++t)
         if (!(betas_host[t] >= 0.0) || !std::isfinite(betas_host[t])) return fail(MBH_EINVAL, "betas must be finite and >= 0");
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = cudaMemcpyAsync((void*)P->A.betas, betas_host, sizeof(double) * P->A.T,
+    cudaError_t e = cudaMemcpyAsync(P->A.betas, betas_host, sizeof(double) * P->A.T,
                                     cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return e == cudaSuccess ? MBH_OK : cuda_fail(e, "set betas");
+}
+
+extern "C" mbh_status mbh_pt_get_betas(const mbh_pt* P, double* betas_host, void* stream)
+{
+    if (!P || !betas_host) return fail(MBH_EINVAL, "NULL sampler/betas");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(betas_host, P->A.betas, sizeof(double) * P->A.T, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? MBH_OK : cuda_fail(e, "get betas");
 }
 
 extern "C" mbh_status mbh_pt_counters(const mbh_pt* P, int64_t* counters_host, uint64_t* step_host,

@@ -66,7 +66,7 @@ class PTOpts(C.Structure):
     _fields_ = [("ntemps", C.c_int32), ("walkers", C.c_int32), ("a", C.c_double),
                 ("probs", C.c_double * 4), ("lo", C.c_double * 11), ("hi", C.c_double * 11),
                 ("seed", C.c_uint64), ("precision", C.c_int), ("het_config", HetConfig),
-                ("modes", C.c_uint32)]
+                ("modes", C.c_uint32), ("adapt_time", C.c_double), ("adapt_lag", C.c_double)]
 
 
 class LoadgenOpts(C.Structure):
@@ -151,6 +151,7 @@ def lib() -> C.CDLL:
         "mbh_pt_set_state": (C.c_int, [vp, vp, vp]),
         "mbh_pt_set_ref": (C.c_int, [vp, vp, vp]),
         "mbh_pt_set_betas": (C.c_int, [vp, dp, vp]),
+        "mbh_pt_get_betas": (C.c_int, [vp, dp, vp]),
         "mbh_pt_counters": (C.c_int, [vp, C.POINTER(C.c_int64), C.POINTER(C.c_uint64), vp]),
         "mbh_pt_best": (C.c_int, [vp, i32, dp, dp, vp]),
         "mbh_pt_free": (None, [vp]),
@@ -568,7 +569,7 @@ class PTSampler:
     def __init__(self, x: torch.Tensor, betas, lo, hi, *, ref: Ref | None = None,
                  data: Data | None = None, walkers: int, a: float = 2.0,
                  probs=(0.85, 0.04, 0.03, 0.08), seed: int = 0, precision="mixed",
-                 cfg: HetConfig | None = None, modes: int = 1, stream=None):
+                 cfg: HetConfig | None = None, modes: int = 1, adapt=None, stream=None):
         _require_cuda()
         betas = np.ascontiguousarray(np.asarray(betas, dtype=np.float64))
         T = betas.size
@@ -580,6 +581,8 @@ class PTSampler:
         o.seed, o.precision = int(seed), _prec(precision)
         o.het_config = cfg if cfg is not None else HetConfig(0, 0, 0)
         o.modes = int(modes)
+        if adapt is not None:   # (nu, n0): ladder adaptation
+            o.adapt_time, o.adapt_lag = float(adapt[0]), float(adapt[1])
         self.T, self.W = T, int(walkers)
         self.ref, self.data = ref, data   # keep them alive
         h = vp()
@@ -613,6 +616,11 @@ class PTSampler:
         if b.size != self.T:
             raise MBHError(1, f"need {self.T} betas")
         _check(lib().mbh_pt_set_betas(self.handle, b.ctypes.data_as(dp), _stream(stream)))
+
+    def betas(self, stream=None) -> np.ndarray:
+        b = np.zeros(self.T)
+        _check(lib().mbh_pt_get_betas(self.handle, b.ctypes.data_as(dp), _stream(stream)))
+        return b
 
     def counters(self, stream=None) -> tuple[np.ndarray, int]:
         c = np.zeros(10 * self.T, dtype=np.int64)

@@ -209,3 +209,23 @@ def test_pt_large_ensembles_match_oracle(M, WL, oracle, case, W):
     assert np.array_equal(cg, co)
     assert np.array_equal(xg, xo)
     assert co[8 * T + 1:9 * T].sum() > 0
+
+
+def test_pt_ladder_adaptation_matches_oracle(M, WL, oracle, case):
+    """Ladder adaptation on the device against the oracle: the ladder after 12 iterations to
+    float64 rounding (the logarithm and exponential of the two libraries may differ in the
+    last bit), positions and counters exactly."""
+    c = case
+    b0 = np.array([1.0, 0.9, 0.8, 0.0])
+    pt = M.PTSampler(WL.to_dev(c["x"]), b0, c["lo"], c["hi"], ref=c["ref_g"], walkers=c["W"],
+                     probs=PROBS, seed=5, precision="fp64", adapt=(10.0, 200.0))
+    pt.run(12)
+    xg, og = (t.cpu().numpy() for t in pt.state())
+    cg, _ = pt.counters()
+    bg = pt.betas()
+    out0 = oracle.het_loglike(oracle.pt_theta(c["x"]), c["ref_o"])
+    xo, oo, co, bo = oracle.pt_run_het(c["x"], out0, c["T"], c["W"], b0, c["lo"], c["hi"], PROBS, 2.0,
+                                       5, 0, 12, c["ref_o"], adapt=(10.0, 200.0), return_betas=True)
+    assert np.array_equal(cg, co) and np.array_equal(xg, xo)
+    np.testing.assert_allclose(bg, bo, rtol=1e-13)
+    assert not np.allclose(bo, b0) and bo[0] == 1.0 and bo[-1] == 0.0
