@@ -301,7 +301,8 @@ MBH_API void mbh_server_free(mbh_server* server);
  * [min_walkers, max_walkers], walkers copied from pools_host[c] (host float64
  * [11][pool], SoA); results are reaped as they complete.  Resets the server's
  * statistics first; blocks until every accepted request has completed.  Requests
- * refused by a full queue count as rejected.  MBH_EINVAL for bad options. */
+ * refused by a full queue count as rejected.  MBH_EINVAL for bad options (including more
+ * than 1e7 arrivals in total). */
 typedef struct {
     double rate_per_s;
     double seconds;

@@ -32,6 +32,7 @@
 #include <vector>
 
 #include "mbh_internal.cuh"
+#include "mbh_model.cuh"
 
 using namespace mbh;
 using Clock = std::chrono::steady_clock;
@@ -73,9 +74,12 @@ struct Slot {
 size_t ref_bytes(const mbh_ref* R)
 {
     const size_t E = (size_t)R->E;
-    return E * (18 * sizeof(double) + sizeof(double) + sizeof(MixBin)) +
-           (E + 1) * (sizeof(int64_t) + sizeof(double) + 2 * 3 * sizeof(double2) + sizeof(MixEdge)) +
-           11 * sizeof(double) + 2 * sizeof(double);
+    size_t b = E * (18 * sizeof(double) + sizeof(double) + sizeof(MixBin)) +
+               (E + 1) * (sizeof(int64_t) + sizeof(double) + 2 * 3 * sizeof(double2) + sizeof(MixEdge)) +
+               11 * sizeof(double) + 2 * sizeof(double);
+    if (R->modes != 1u)   // per-mode reference tables of a higher-mode reference
+        b += (E + 1) * (kHmModes * sizeof(MixModeHM) + 3 * sizeof(float));
+    return b;
 }
 
 }  // namespace
@@ -519,6 +523,7 @@ extern "C" mbh_status mbh_server_loadgen(mbh_server* S, const int32_t* source_id
     if (!S || !source_ids || !pools_host || !o || !out) return fail(MBH_EINVAL, "NULL argument");
     if (n_clients < 1 || pool < 1) return fail(MBH_EINVAL, "need n_clients >= 1 and pool >= 1");
     if (!(o->rate_per_s > 0.0) || !(o->seconds > 0.0)) return fail(MBH_EINVAL, "rate and seconds must be > 0");
+    if (o->rate_per_s * o->seconds > 1e7) return fail(MBH_EINVAL, "more than 1e7 arrivals requested");
     if (o->min_walkers < 1 || o->max_walkers < o->min_walkers || o->max_walkers > pool ||
         o->max_walkers > S->opts.max_batch_walkers)
         return fail(MBH_EINVAL, "request sizes must satisfy 1 <= min <= max <= min(pool, max_batch_walkers)");
