@@ -393,6 +393,10 @@ typedef struct {
                                           iteration's swap acceptance of pair (t, t-1); the
                                           coldest and hottest temperatures stay fixed */
     double adapt_lag;                  /* n0 (> 0 when adapting) */
+    int32_t no_fuse;                   /* != 0: keep proposal, likelihood and acceptance as
+                                          separate launches (by default a mixed-precision
+                                          (2,2) reference runs each half step as one fused
+                                          heterodyne launch) */
 } mbh_pt_opts;
 
 /* x_dev: float64 [11][T W] start positions in x, slot t W + k = walker k of

@@ -67,6 +67,8 @@ struct SrcDesc {
 struct HetLaunch {
     const double* theta;
     double* out;
+    const void* pt;          // fused sampler half step: the sampler's device state (else null)
+    int32_t pt_half;
     int64_t W;
     int32_t n_src;
     int32_t n_tiles;
@@ -105,6 +107,9 @@ struct HetKernel {
 HetKernel het_kernel_f64(int G, int block);
 HetKernel het_kernel_mixed(int G, int block);
 HetKernel het_kernel_mixed_hm(int G, int block);
+HetKernel het_kernel_mixed_pt(int G, int block);
+mbh_status het_launch_fused_pt(const mbh_ref* ref, int64_t M, const mbh_het_config& cfg, const void* pt_dev,
+                               int half, cudaStream_t st);
 
 // ------------------------------------------------------------------------------------------
 // reductions

@@ -25,6 +25,7 @@
 #include "mbh_df.cuh"
 #include "mbh_internal.cuh"
 #include "mbh_model.cuh"
+#include "mbh_pt.cuh"
 
 using namespace mbh;
 
@@ -1085,6 +1086,129 @@ __global__ void __launch_bounds__(BLOCK)
     }
 }
 
+
+// Sampler half step fused with the heterodyne likelihood (the sampler of Sec. III driving the
+// likelihood of Sec. II B): the walker setup builds moving walker w's proposal from the
+// ensemble state (pt::propose_item) and sets the walker up from theta(Y); the edge loop is
+// het_mixed_kernel's; the epilogue applies the tempered acceptance (pt::accept_test) and
+// updates the state and counters.  Walker index w = the half step's item t W/2 + k'.
+template <int G, int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+    het_mixed_pt_kernel(const __grid_constant__ HetLaunch L)
+{
+    constexpr int WPB = BLOCK / G;
+    __shared__ WalkerDF wsd[WPB];
+    __shared__ WalkerF wsf[WPB];
+    __shared__ double ys[WPB][pt::kPar];
+    __shared__ double facs[WPB];
+    __shared__ int32_t flags[WPB];
+    const pt::PtArgs& A = *static_cast<const pt::PtArgs*>(L.pt);
+    const int half = L.pt_half;
+    const int lw = threadIdx.x / G, lane = threadIdx.x % G;
+    for (int tile = blockIdx.x; tile < L.n_tiles; tile += gridDim.x) {
+        const SrcDesc& S = L.src[0];
+        const int64_t w0 = (int64_t)(tile - S.tile_begin) * WPB;
+        const int64_t wi = w0 + lw;
+        const bool active = wi < S.w_end;
+        __syncthreads();
+        for (int j = threadIdx.x; j < WPB; j += BLOCK)
+            if (w0 + j < S.w_end) {
+                double v[pt::kPar], th[pt::kPar], fac;
+                int32_t flag;
+                pt::propose_item(A, half, (int32_t)(w0 + j), *A.step, v, th, fac, flag);
+#pragma unroll
+                for (int p = 0; p < pt::kPar; ++p) ys[j][p] = v[p];
+                facs[j] = fac;
+                flags[j] = flag;
+                walker_setup_mixed(th, 1, 0, wsd[j], wsf[j]);
+            }
+        __syncthreads();
+        const int E = S.E;
+        const f2 tob = split_d(S.t_obs);
+        f2 adh = {0.0f, 0.0f}, ahh = {0.0f, 0.0f};
+        cf carry[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+        const int rounds = (E + 1 + G - 1) / G;
+        for (int r = 0; r < rounds; ++r) {
+            const int e = r * G + lane;
+            cf dl[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+            if (active && e <= E) {
+                const MixEdge me = S.mix.edge[e];
+                const FreqDF q = {ld_f2(me.f), ld_f2(me.f3), ld_f2(me.fm3), ld_f2(me.lnf3)};
+                f2 Phi;
+                float sa, ca, amp;
+                if (phase_df(wsd[lw], wsf[lw], q, tob, Phi, sa, ca, amp)) {
+                    float sh, ch;
+                    sincos_small(0.5f * reduce_phase(dd_sub(Phi, ld_f2(me.phi0))), &sh, &ch);
+                    const cf em1 = {-2.0f * sh * sh, -2.0f * sh * ch};
+                    cf T[3];
+                    transfer_f32(wsf[lw], wsf[lw].Kp, wsf[lw].Kc, q.f.hi, sa, ca, T);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const cf rho = fmul(fscale(T[c], amp), {me.h0inv[c].x, me.h0inv[c].y});
+                        const cf rm1 = {rho.re - 1.0f, rho.im};
+                        dl[c] = fadd(fadd(rm1, fmul(rm1, em1)), em1);
+                    }
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) dl[c] = {-1.0f, 0.0f};
+                }
+            }
+            cf dp[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                dp[c].re = __shfl_up_sync(0xffffffffu, dl[c].re, 1, G);
+                dp[c].im = __shfl_up_sync(0xffffffffu, dl[c].im, 1, G);
+                if (lane == 0) dp[c] = carry[c];
+                carry[c].re = __shfl_sync(0xffffffffu, dl[c].re, G - 1, G);
+                carry[c].im = __shfl_sync(0xffffffffu, dl[c].im, G - 1, G);
+            }
+            if (active && e >= 1 && e <= E) {
+                const MixBin& mb = S.mix.bin[e - 1];
+                const float iw = mb.invw;
+                float bd = 0.0f, bh = 0.0f;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float d0r = 0.5f * (dp[c].re + dl[c].re), d0i = 0.5f * (dp[c].im + dl[c].im);
+                    const float d1r = (dl[c].re - dp[c].re) * iw, d1i = (dl[c].im - dp[c].im) * iw;
+                    const float* qq = mb.q + 6 * c;
+                    bd += qq[0] * d0r + qq[1] * d0i + qq[2] * d1r + qq[3] * d1i;
+                    bh += qq[4] * (2.0f * d0r + d0r * d0r + d0i * d0i) +
+                          2.0f * qq[5] * (d1r + d0r * d1r + d0i * d1i);
+                }
+                df_acc(adh, {bd, 0.0f});
+                df_acc(ahh, {bh, 0.0f});
+            }
+        }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+            const f2 odh = {__shfl_down_sync(0xffffffffu, adh.hi, o, G), __shfl_down_sync(0xffffffffu, adh.lo, o, G)};
+            const f2 ohh = {__shfl_down_sync(0xffffffffu, ahh.hi, o, G), __shfl_down_sync(0xffffffffu, ahh.lo, o, G)};
+            df_acc(adh, odh);
+            df_acc(ahh, ohh);
+        }
+        if (active && lane == 0) {
+            const double dh = 4.0 * (S.mix.sumA0 + df_to_double(adh));
+            const double hh = 4.0 * (S.mix.sumB0 + df_to_double(ahh));
+            const double lnl = -0.5 * (S.dd + hh - 2.0 * dh);
+            int32_t col;
+            int t;
+            const int32_t flag = flags[lw];
+            const int kind = flag >> 1;
+            const bool acc = pt::accept_test(A, half, (int32_t)wi, lnl, facs[lw], flag, col, t);
+            atomicAdd(&A.counters[t * 4 + kind], 1ull);
+            if (acc) {
+                atomicAdd(&A.counters[4 * A.T + t * 4 + kind], 1ull);
+                const int64_t N = (int64_t)A.T * A.W;
+#pragma unroll
+                for (int p = 0; p < pt::kPar; ++p) A.x[p * N + col] = ys[lw][p];
+                A.out[col] = lnl;
+                A.out[N + col] = dh;
+                A.out[2 * N + col] = hh;
+            }
+        }
+    }
+}
+
 namespace {
 template <int G, int BLOCK>
 cudaError_t launch_het_mixed(const HetLaunch& L, int grid, cudaStream_t st)
@@ -1097,6 +1221,13 @@ template <int G, int BLOCK>
 cudaError_t launch_het_mixed_hm(const HetLaunch& L, int grid, cudaStream_t st)
 {
     het_mixed_hm_kernel<G, BLOCK><<<grid, BLOCK, 0, st>>>(L);
+    return cudaGetLastError();
+}
+
+template <int G, int BLOCK>
+cudaError_t launch_het_mixed_pt(const HetLaunch& L, int grid, cudaStream_t st)
+{
+    het_mixed_pt_kernel<G, BLOCK><<<grid, BLOCK, 0, st>>>(L);
     return cudaGetLastError();
 }
 }  // namespace
@@ -1122,6 +1253,22 @@ HetKernel het_kernel_mixed_hm(int G, int block)
 {
 #define MBH_CASE(g, b) \
     if (G == g && block == b) return {&launch_het_mixed_hm<g, b>, (const void*)&het_mixed_hm_kernel<g, b>};
+    MBH_CASE(1, 64) MBH_CASE(1, 128) MBH_CASE(1, 256)
+    MBH_CASE(2, 64) MBH_CASE(2, 128) MBH_CASE(2, 256)
+    MBH_CASE(4, 64) MBH_CASE(4, 128) MBH_CASE(4, 256)
+    MBH_CASE(8, 64) MBH_CASE(8, 128) MBH_CASE(8, 256)
+    MBH_CASE(16, 64) MBH_CASE(16, 128) MBH_CASE(16, 256)
+    MBH_CASE(32, 64) MBH_CASE(32, 128) MBH_CASE(32, 256)
+#undef MBH_CASE
+    return {nullptr, nullptr};
+}
+}  // namespace mbh
+
+namespace mbh {
+HetKernel het_kernel_mixed_pt(int G, int block)
+{
+#define MBH_CASE(g, b) \
+    if (G == g && block == b) return {&launch_het_mixed_pt<g, b>, (const void*)&het_mixed_pt_kernel<g, b>};
     MBH_CASE(1, 64) MBH_CASE(1, 128) MBH_CASE(1, 256)
     MBH_CASE(2, 64) MBH_CASE(2, 128) MBH_CASE(2, 256)
     MBH_CASE(4, 64) MBH_CASE(4, 128) MBH_CASE(4, 256)

@@ -31,157 +31,33 @@
 #include <new>
 
 #include "mbh_internal.cuh"
+#include "mbh_pt.cuh"
 
 using namespace mbh;
 
 namespace {
 
-constexpr int kPar = 11;
-constexpr int kMaxTemps = 64;
-constexpr int kMaxWalkers = 8192;   // per temperature (16-bit walker index in the swap keys)
+using namespace mbh::pt;
 constexpr int kThreads = 256;      // rescoring and gathers
 constexpr int kStepThreads = 32;   // propose/accept: 8192 walkers -> 256 blocks over all SMs
 constexpr int kSortThreads = 1024;
 
-enum { K_STRETCH = 0, K_SKY_ALL = 1, K_SKY_LON = 2, K_SKY_LAT = 3 };
-enum : uint32_t { P_PROPOSE = 0x10, P_ACCEPT = 0x20, P_SWAP_KEY = 0x100, P_SWAP_ACC = 0x200 };
-
-constexpr double kPi = 3.141592653589793;
-constexpr double kHalfPi = 1.5707963267948966;
-constexpr double kTwoPi = 6.283185307179586;
-
-struct PtArgs {
-    double* x;              // [11][N] positions, physical columns
-    double* out;            // [3][N] lnL, <d|h>, <h|h>
-    int32_t* map;           // [N] slot -> column
-    double* y;              // [11][M] proposals of the moving half
-    double* theta;          // [11][N] likelihood input (first M columns during a half step)
-    double* out_p;          // [3][M] likelihood of the proposals
-    double* fac;            // [M] log acceptance factor (d-1) ln z of stretch moves
-    int32_t* flag;          // [M] inside-prior bit | kind << 1
-    int32_t* perm;          // [T][W] hot partner of cold walker k at level i
-    double* lnu_acc;        // [2][M] ln u of the acceptance tests of both half steps
-    double* lnu_swap;       // [T][W] ln u of the swap tests (level 0 unused)
-    double* betas;          // [T] (adapted in place when adapt_nu > 0)
-    unsigned long long* counters;   // [10 T]
-    unsigned long long* step;       // iteration counter
-    double lo[kPar], hi[kPar];
-    double c1, c2, c3;      // cumulative proposal probabilities
-    double a, am1;          // stretch scale and a - 1
-    double adapt_nu, adapt_n0;   // ladder adaptation (nu > 0 enables)
-    uint64_t seed;
-    int32_t T, W;
-};
-
-// ---- Philox4x32-10 -------------------------------------------------------------------------
-__device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
-                                        uint32_t k0, uint32_t k1)
-{
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        if (r > 0) {
-            k0 += 0x9E3779B9u;
-            k1 += 0xBB67AE85u;
-        }
-        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
-        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
-        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
-        c0 = n0;
-        c1 = lo1;
-        c2 = n2;
-        c3 = lo0;
-    }
-    return make_uint4(c0, c1, c2, c3);
-}
-
-__device__ __forceinline__ uint4 draw(uint64_t seed, uint32_t item, uint32_t purpose, uint64_t step)
-{
-    return philox(item, purpose, (uint32_t)step, (uint32_t)(step >> 32), (uint32_t)seed,
-                  (uint32_t)(seed >> 32));
-}
-
-// 53-bit uniform in [0, 1); every operation is exact
-__device__ __forceinline__ double u53(uint32_t a, uint32_t b)
-{
-    return ((double)(a >> 5) * 67108864.0 + (double)(b >> 6)) * (1.0 / 9007199254740992.0);
-}
-
-// v mod P for v in [-2P, 4P) (a coordinate of the prior box plus at most 3 quarter turns);
-// the bounded loops leave values outside that range outside [0, P), i.e. outside the prior.
-__device__ __forceinline__ double reduce_period(double v, double P)
-{
-    for (int i = 0; i < 4 && v >= P; ++i) v = __dsub_rn(v, P);
-    for (int i = 0; i < 2 && v < 0.0; ++i) v = __dadd_rn(v, P);
-    return v;
-}
-
-__device__ __forceinline__ void theta_of_x(const double (&x)[kPar], double (&th)[kPar])
-{
-#pragma unroll
-    for (int p = 0; p < kPar; ++p) th[p] = x[p];
-    th[0] = exp(fmin(x[0], 700.0));
-    th[6] = acos(fmin(fmax(x[6], -1.0), 1.0));   // clamps act only outside the prior box
-    th[8] = asin(fmin(fmax(x[8], -1.0), 1.0));
-}
-
 // ---- kernels -------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kStepThreads) pt_propose_kernel(const PtArgs A, int half)
 {
-    const int32_t Wh = A.W / 2, M = A.T * Wh, N = A.T * A.W;
+    const int32_t M = A.T * (A.W / 2);
     const int32_t item = blockIdx.x * blockDim.x + threadIdx.x;
     if (item >= M) return;
-    const uint64_t step = *A.step;
-    const int32_t t = item / Wh, kp = item - t * Wh;
-    const int32_t col = A.map[t * A.W + half * Wh + kp];
-    const uint4 r = draw(A.seed, (uint32_t)item, P_PROPOSE + (uint32_t)half, step);
-    const double u = (double)r.x * (1.0 / 4294967296.0);
-    const int kind = u < A.c1 ? K_STRETCH : u < A.c2 ? K_SKY_ALL : u < A.c3 ? K_SKY_LON : K_SKY_LAT;
-    double v[kPar], xk[kPar];
-#pragma unroll
-    for (int p = 0; p < kPar; ++p) xk[p] = v[p] = A.x[(int64_t)p * N + col];
-    double fac = 0.0;
-    if (kind == K_STRETCH) {
-        const int32_t j = (1 - half) * Wh + (int32_t)(((uint64_t)r.y * (uint64_t)Wh) >> 32);
-        const int32_t colj = A.map[t * A.W + j];
-        const double s = __dadd_rn(__dmul_rn(A.am1, u53(r.z, r.w)), 1.0);
-        const double z = __ddiv_rn(__dmul_rn(s, s), A.a);
-#pragma unroll
-        for (int p = 0; p < kPar; ++p) {
-            const double xj = A.x[(int64_t)p * N + colj];
-            v[p] = __dadd_rn(xj, __dmul_rn(z, __dsub_rn(v[p], xj)));
-        }
-        fac = (double)(kPar - 1) * log(z);
-    } else {
-        int n = 0, m = 0;
-        if (kind == K_SKY_ALL) {
-            n = (int)(r.z >> 30);
-            m = (int)(r.w >> 31);
-        } else if (kind == K_SKY_LON) {
-            n = 1 + (int)(((uint64_t)r.z * 3u) >> 32);
-        } else {
-            m = 1;
-        }
-        const double shift = __dmul_rn((double)n, kHalfPi);
-        v[7] = reduce_period(__dadd_rn(v[7], shift), kTwoPi);
-        v[9] = reduce_period(__dadd_rn(v[9], shift), kPi);
-        if (m) {
-            v[8] = -v[8];
-            v[6] = -v[6];
-            v[9] = __dsub_rn(kPi, v[9]);
-        }
-    }
-    bool ok = true;
-#pragma unroll
-    for (int p = 0; p < kPar; ++p) ok = ok && (v[p] >= A.lo[p] && v[p] <= A.hi[p]);
-    double th[kPar];
-    theta_of_x(ok ? v : xk, th);   // outside the prior: score the current point (rejected anyway)
+    double v[kPar], th[kPar], fac;
+    int32_t flag;
+    propose_item(A, half, item, *A.step, v, th, fac, flag);
 #pragma unroll
     for (int p = 0; p < kPar; ++p) {
         A.y[(int64_t)p * M + item] = v[p];
         A.theta[(int64_t)p * M + item] = th[p];
     }
     A.fac[item] = fac;
-    A.flag[item] = (ok ? 1 : 0) | (kind << 1);
+    A.flag[item] = flag;
 }
 
 __global__ void __launch_bounds__(kStepThreads) pt_accept_kernel(const PtArgs A, int half)
@@ -192,13 +68,11 @@ __global__ void __launch_bounds__(kStepThreads) pt_accept_kernel(const PtArgs A,
     const int32_t Wh = A.W / 2, M = A.T * Wh, N = A.T * A.W;
     const int32_t item = blockIdx.x * blockDim.x + threadIdx.x;
     if (item < M) {
-        const int32_t t = item / Wh, kp = item - t * Wh;
-        const int32_t col = A.map[t * A.W + half * Wh + kp];
-        const double dl = __dsub_rn(A.out_p[item], A.out[col]);
-        const double la = __dadd_rn(A.fac[item], __dmul_rn(A.betas[t], dl));
+        int32_t col;
+        int t;
         const int32_t f = A.flag[item];
         const int kind = f >> 1;
-        const bool acc = (f & 1) && A.lnu_acc[(int64_t)half * M + item] < la;
+        const bool acc = accept_test(A, half, item, A.out_p[item], A.fac[item], f, col, t);
         atomicAdd(&cnt[t * 8 + kind], 1u);
         if (acc) {
             atomicAdd(&cnt[t * 8 + 4 + kind], 1u);
@@ -480,6 +354,9 @@ struct mbh_pt {
     const mbh_data* data = nullptr;
     mbh_het_config cfg{8, 128, 0};
     uint32_t modes = 1u;     // direct likelihood: harmonic modes of the templates
+    bool fused = false;      // half steps as one fused heterodyne launch each
+    bool fuse_ok = false;    // the caller allows fusion (mixed precision, not opted out)
+    PtArgs* A_dev = nullptr; // device copy of A for the fused kernel
     int Wp = 0;
     double* res = nullptr;   // device [14] for mbh_pt_best
     cudaGraphExec_t exec = nullptr;
@@ -503,7 +380,7 @@ void free_pt(mbh_pt* P)
     if (P->join_draws) cudaEventDestroy(P->join_draws);
     PtArgs& A = P->A;
     void* bufs[] = {A.x, A.out, A.map, A.y, A.theta, A.out_p, A.fac, A.flag, A.perm, A.lnu_acc, A.lnu_swap,
-                    A.betas, A.counters, A.step, P->res};
+                    A.betas, A.counters, A.step, P->res, P->A_dev};
     for (void* b : bufs)
         if (b) cudaFree(b);
     delete P;
@@ -549,6 +426,12 @@ mbh_status queue_iteration(mbh_pt* P, cudaStream_t st)
     }
     if ((e = cudaEventRecord(P->join, P->side)) != cudaSuccess) return cuda_fail(e, "join");
     for (int half = 0; half < 2; ++half) {
+        if (P->fused) {   // proposal, likelihood and acceptance in one launch
+            if (half == 0 && (e = cudaStreamWaitEvent(st, P->join_draws, 0)) != cudaSuccess)
+                return cuda_fail(e, "join");
+            if (mbh_status s = het_launch_fused_pt(P->ref, M, P->cfg, P->A_dev, half, st)) return s;
+            continue;
+        }
         pt_propose_kernel<<<gM, kStepThreads, 0, st>>>(A, half);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "pt_propose_kernel");
         if (mbh_status s = likelihood(P, M, A.out_p, st)) return s;
@@ -681,6 +564,7 @@ extern "C" mbh_status mbh_pt_create(const mbh_pt_opts* o, const mbh_ref* ref, co
     alloc((void**)&A.counters, sizeof(unsigned long long) * 10 * A.T);
     alloc((void**)&A.step, sizeof(unsigned long long));
     alloc((void**)&P->res, sizeof(double) * 14);
+    alloc((void**)&P->A_dev, sizeof(PtArgs));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->join, cudaEventDisableTiming);
@@ -703,6 +587,9 @@ extern "C" mbh_status mbh_pt_create(const mbh_pt_opts* o, const mbh_ref* ref, co
     if (e == cudaSuccess) e = cudaMemsetAsync(A.counters, 0, sizeof(unsigned long long) * 10 * A.T, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(A.step, &zero, sizeof zero, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(A.perm, 0, sizeof(int32_t) * N, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(P->A_dev, &A, sizeof(PtArgs), cudaMemcpyHostToDevice, st);
+    P->fuse_ok = o->precision == MBH_MIXED && !o->no_fuse;
+    P->fused = P->fuse_ok && ref != nullptr && ref->modes == 1u;
     if (e != cudaSuccess) {
         free_pt(P);
         return cuda_fail(e, "sampler setup");
@@ -772,6 +659,7 @@ extern "C" mbh_status mbh_pt_set_ref(mbh_pt* P, const mbh_ref* ref, void* stream
     if (!P->ref) return fail(MBH_EINVAL, "sampler uses the direct likelihood");
     if (ref->device != P->device) return fail(MBH_EINVAL, "ref lives on another device");
     P->ref = ref;
+    P->fused = P->fuse_ok && ref->modes == 1u;
     drop_graph(P);   // the reference's tables are baked into the captured launches
     return rescore(P, (cudaStream_t)stream);
 }

@@ -17,6 +17,7 @@
 #include <cstring>
 #include <cmath>
 #include <memory>
+#include <new>
 #include <numeric>
 #include <vector>
 
@@ -299,3 +300,49 @@ extern "C" void mbh_het_graph_free(mbh_het_graph* g)
     if (g->graph) cudaGraphDestroy(g->graph);
     delete g;
 }
+
+namespace mbh {
+// One fused sampler half step (het_mixed_pt_kernel) over the M moving walkers of a (2,2)
+// reference: a single-source launch whose walker constants come from the sampler's proposals.
+mbh_status het_launch_fused_pt(const mbh_ref* ref, int64_t M, const mbh_het_config& cfg, const void* pt_dev,
+                               int half, cudaStream_t st)
+{
+    if (mbh_status s = check_cfg(cfg)) return s;
+    const HetKernel k = het_kernel_mixed_pt(cfg.threads_per_walker, cfg.block);
+    if (!k.launch) return fail(MBH_EINVAL, "no kernel for this configuration");
+    const int wpb = cfg.block / cfg.threads_per_walker;
+    HetLaunch* L = new (std::nothrow) HetLaunch;
+    if (!L) return fail(MBH_ENOMEM, "host allocation");
+    std::memset(L, 0, sizeof *L);
+    L->W = M;
+    L->pt = pt_dev;
+    L->pt_half = half;
+    L->n_src = 1;
+    SrcDesc& S = L->src[0];
+    S.summary = ref->summary;
+    S.h0inv = ref->h0inv;
+    S.fe = ref->fe;
+    S.invw = ref->invw;
+    S.mix = ref->mix;
+    S.dd = ref->dd;
+    S.t_obs = ref->grid.t_obs;
+    S.E = ref->E;
+    S.modes = ref->modes;
+    S.w_begin = 0;
+    S.w_end = M;
+    S.tile_begin = 0;
+    const int64_t tiles = (M + wpb - 1) / wpb;
+    L->n_tiles = (int32_t)tiles;
+    int grid = (int)tiles;
+    if (cfg.persistent) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k.fn, cfg.block, 0) == cudaSuccess)
+            grid = (int)std::min<int64_t>(tiles, (int64_t)std::max(1, per_sm) * sms);
+    }
+    const cudaError_t e = k.launch(*L, grid, st);
+    delete L;
+    return e == cudaSuccess ? MBH_OK : cuda_fail(e, "fused sampler half step");
+}
+}  // namespace mbh

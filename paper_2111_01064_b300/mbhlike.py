@@ -66,7 +66,8 @@ class PTOpts(C.Structure):
     _fields_ = [("ntemps", C.c_int32), ("walkers", C.c_int32), ("a", C.c_double),
                 ("probs", C.c_double * 4), ("lo", C.c_double * 11), ("hi", C.c_double * 11),
                 ("seed", C.c_uint64), ("precision", C.c_int), ("het_config", HetConfig),
-                ("modes", C.c_uint32), ("adapt_time", C.c_double), ("adapt_lag", C.c_double)]
+                ("modes", C.c_uint32), ("adapt_time", C.c_double), ("adapt_lag", C.c_double),
+                ("no_fuse", C.c_int32)]
 
 
 class LoadgenOpts(C.Structure):
@@ -569,7 +570,8 @@ class PTSampler:
     def __init__(self, x: torch.Tensor, betas, lo, hi, *, ref: Ref | None = None,
                  data: Data | None = None, walkers: int, a: float = 2.0,
                  probs=(0.85, 0.04, 0.03, 0.08), seed: int = 0, precision="mixed",
-                 cfg: HetConfig | None = None, modes: int = 1, adapt=None, stream=None):
+                 cfg: HetConfig | None = None, modes: int = 1, adapt=None, fuse: bool = True,
+                 stream=None):
         _require_cuda()
         betas = np.ascontiguousarray(np.asarray(betas, dtype=np.float64))
         T = betas.size
@@ -583,6 +585,7 @@ class PTSampler:
         o.modes = int(modes)
         if adapt is not None:   # (nu, n0): ladder adaptation
             o.adapt_time, o.adapt_lag = float(adapt[0]), float(adapt[1])
+        o.no_fuse = 0 if fuse else 1
         self.T, self.W = T, int(walkers)
         self.ref, self.data = ref, data   # keep them alive
         h = vp()

@@ -229,3 +229,25 @@ def test_pt_ladder_adaptation_matches_oracle(M, WL, oracle, case):
     assert np.array_equal(cg, co) and np.array_equal(xg, xo)
     np.testing.assert_allclose(bg, bo, rtol=1e-13)
     assert not np.allclose(bo, b0) and bo[0] == 1.0 and bo[-1] == 0.0
+
+
+def test_pt_fused_half_steps_equal_separate_launches(M, WL, case):
+    """Mixed precision: a half step as one fused heterodyne launch (proposal in the walker
+    setup, acceptance in the epilogue) against proposal, likelihood and acceptance as separate
+    launches.  The likelihood arithmetic is the same; the walker constants are compiled into two
+    kernels, so a last-bit difference may flip a decision sitting on its threshold."""
+    c = case
+    runs = []
+    for fuse in (True, False):
+        pt = M.PTSampler(WL.to_dev(c["x"]), c["betas"], c["lo"], c["hi"], ref=c["ref_g"], walkers=c["W"],
+                         probs=PROBS, seed=21, precision="mixed", fuse=fuse)
+        pt.run(4)
+        x, out = (t.cpu().numpy() for t in pt.state())
+        cnt, step = pt.counters()
+        runs.append((x, out, cnt, step))
+    (xa, oa, ca, sa), (xb, ob, cb, sb) = runs
+    same = np.all(xa == xb, axis=0)
+    assert sa == sb == 4 and same.mean() >= 0.97, same.mean()
+    assert np.abs(ca - cb).sum() <= 4
+    d = np.abs(oa[0] - ob[0])[same]
+    assert d.max() < 1e-6 * np.abs(ob[0][same]).max() + 1e-6
