@@ -551,8 +551,27 @@ def run_sampler(M, WL, g, src, ref, stream, het_rate: float, iters: int = 20) ->
                      "acceptance_by_temperature": (acc.sum(1) / np.maximum(prop.sum(1), 1)).round(4).tolist(),
                      "swap_acceptance_by_level": (cnt[8 * T + 1:9 * T] / np.maximum(cnt[9 * T + 1:10 * T], 1)).round(4).tolist(),
                      "iterations_run": step}
+    # four ensembles stepping together (references around four nearby points of the same
+    # data): each half step is one 32768-walker likelihood batch
+    n_ens = 4
+    ths = [th] + [I.perturb(th, np.full((11, 1), 10.0 ** (-5 - e)))[:, 0] for e in range(1, n_ens)]
+    refs = [ref] + [M.het_prepare_reference(src.data, t_, ref.bins) for t_ in ths[1:]]
+    xs = [I.draw_pt_ensemble(I.rng(2, 310 + e), x0, T, W, scale, lo, hi) for e in range(n_ens)]
+    pt = M.PTSampler(WL.to_dev(np.concatenate(xs, 1)), betas, lo, hi, refs=refs, walkers=W, seed=1,
+                     precision="mixed")
+    pt.run(3)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    pt.run(iters)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / iters
+    pt.close()
+    res["four_ensembles"] = {"ensembles": n_ens, "walkers": n_ens * T * W, "ms_per_iteration": ms,
+                             "iterations_per_s": 1e3 / ms, "lnL_evals_per_s": n_ens * T * W / (ms * 1e-3)}
     return {"temperatures": T, "walkers_per_temperature": W, "bins": ref.bins,
-            "launches_per_iteration": 9, "graph": True, **res}
+            "launches_per_iteration": 5, "fused_half_steps": True, "graph": True, **res}
 
 
 def run_uneven(M, WL, stream, reps: int = 20) -> dict:

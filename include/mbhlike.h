@@ -406,20 +406,31 @@ typedef struct {
 MBH_API mbh_status mbh_pt_create(const mbh_pt_opts* opts, const mbh_ref* ref, const mbh_data* data,
                                  const double* betas_host, const double* x_dev, void* stream,
                                  mbh_pt** out);
+/* Several independent ensembles stepping together (one per source, or independent
+ * chains of one source): ensemble e uses refs[e] (or, with data, the direct
+ * likelihood of the common data), seed seed + e 0x9E3779B97F4A7C15, ladder
+ * betas_host[e T .. e T + T) and slots [e T W, (e+1) T W) of x_dev [11][n_ens T W];
+ * it is exactly a single-ensemble sampler with that seed.  A half step of all
+ * ensembles is one likelihood batch, which fills the GPU where one ensemble's half
+ * step does not.  Counters are [n_ens][10 T].  n_ens in [1, 1024]. */
+MBH_API mbh_status mbh_pt_create_multi(const mbh_pt_opts* opts, const mbh_ref* const* refs, int32_t n_ens,
+                                       const mbh_data* data, const double* betas_host, const double* x_dev,
+                                       void* stream, mbh_pt** out);
 /* Queues n_iter iterations on `stream` (use_graph != 0: replays of one
  * captured iteration). */
 MBH_API mbh_status mbh_pt_run(mbh_pt* pt, int64_t n_iter, int32_t use_graph, void* stream);
-/* Copies the state in slot order: x_dev [11][T W], out_dev [3][T W] (lnL,
- * <d|h>, <h|h>); either may be NULL. */
+/* Copies the state in slot order: x_dev [11][n_ens T W], out_dev [3][n_ens T W]
+ * (lnL, <d|h>, <h|h>); either may be NULL. */
 MBH_API mbh_status mbh_pt_state(const mbh_pt* pt, double* x_dev, double* out_dev, void* stream);
 /* Replaces the positions (slot order) and rescores them. */
 MBH_API mbh_status mbh_pt_set_state(mbh_pt* pt, const double* x_dev, void* stream);
 /* Reference refresh (Sec. III B): later iterations use `ref`; every walker is
- * rescored against it. */
+ * rescored against it (single-ensemble samplers; mbh_pt_set_ref_at for ensemble e). */
 MBH_API mbh_status mbh_pt_set_ref(mbh_pt* pt, const mbh_ref* ref, void* stream);
-/* Current inverse temperatures (after any adaptation; synchronises `stream`). */
+MBH_API mbh_status mbh_pt_set_ref_at(mbh_pt* pt, int32_t ensemble, const mbh_ref* ref, void* stream);
+/* Current inverse temperatures [n_ens][T] (after any adaptation; synchronises `stream`). */
 MBH_API mbh_status mbh_pt_get_betas(const mbh_pt* pt, double* betas_host, void* stream);
-/* New inverse temperatures (synchronises `stream`). */
+/* New inverse temperatures [n_ens][T] (synchronises `stream`). */
 MBH_API mbh_status mbh_pt_set_betas(mbh_pt* pt, const double* betas_host, void* stream);
 /* Reads the counters and the iteration counter (synchronises `stream`). */
 MBH_API mbh_status mbh_pt_counters(const mbh_pt* pt, int64_t* counters_host, uint64_t* step_host,
@@ -428,6 +439,9 @@ MBH_API mbh_status mbh_pt_counters(const mbh_pt* pt, int64_t* counters_host, uin
  * x_host [11], out_host [3] (synchronises `stream`). */
 MBH_API mbh_status mbh_pt_best(const mbh_pt* pt, int32_t temp, double* x_host, double* out_host,
                                void* stream);
+/* The same for ensemble `ensemble`. */
+MBH_API mbh_status mbh_pt_best_at(const mbh_pt* pt, int32_t ensemble, int32_t temp, double* x_host,
+                                  double* out_host, void* stream);
 MBH_API void mbh_pt_free(mbh_pt* pt);
 
 #ifdef __cplusplus

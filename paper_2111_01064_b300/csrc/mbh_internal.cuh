@@ -108,8 +108,8 @@ HetKernel het_kernel_f64(int G, int block);
 HetKernel het_kernel_mixed(int G, int block);
 HetKernel het_kernel_mixed_hm(int G, int block);
 HetKernel het_kernel_mixed_pt(int G, int block);
-mbh_status het_launch_fused_pt(const mbh_ref* ref, int64_t M, const mbh_het_config& cfg, const void* pt_dev,
-                               int half, cudaStream_t st);
+mbh_status het_launch_fused_pt(const mbh_ref* const* refs, int n_ens, int64_t M, const mbh_het_config& cfg,
+                               const void* pt_dev, int half, cudaStream_t st);
 
 // ------------------------------------------------------------------------------------------
 // reductions

@@ -1106,8 +1106,10 @@ __global__ void __launch_bounds__(BLOCK)
     const int half = L.pt_half;
     const int lw = threadIdx.x / G, lane = threadIdx.x % G;
     for (int tile = blockIdx.x; tile < L.n_tiles; tile += gridDim.x) {
-        const SrcDesc& S = L.src[0];
-        const int64_t w0 = (int64_t)(tile - S.tile_begin) * WPB;
+        int s = 0;   // ensemble of this tile
+        while (s + 1 < L.n_src && L.src[s + 1].tile_begin <= tile) ++s;
+        const SrcDesc& S = L.src[s];
+        const int64_t w0 = S.w_begin + (int64_t)(tile - S.tile_begin) * WPB;
         const int64_t wi = w0 + lw;
         const bool active = wi < S.w_end;
         __syncthreads();
@@ -1191,14 +1193,14 @@ __global__ void __launch_bounds__(BLOCK)
             const double hh = 4.0 * (S.mix.sumB0 + df_to_double(ahh));
             const double lnl = -0.5 * (S.dd + hh - 2.0 * dh);
             int32_t col;
-            int t;
+            int t, cb;
             const int32_t flag = flags[lw];
             const int kind = flag >> 1;
-            const bool acc = pt::accept_test(A, half, (int32_t)wi, lnl, facs[lw], flag, col, t);
-            atomicAdd(&A.counters[t * 4 + kind], 1ull);
+            const bool acc = pt::accept_test(A, half, (int32_t)wi, lnl, facs[lw], flag, col, t, cb);
+            atomicAdd(&A.counters[cb + t * 4 + kind], 1ull);
             if (acc) {
-                atomicAdd(&A.counters[4 * A.T + t * 4 + kind], 1ull);
-                const int64_t N = (int64_t)A.T * A.W;
+                atomicAdd(&A.counters[cb + 4 * A.T + t * 4 + kind], 1ull);
+                const int64_t N = (int64_t)A.n_ens * A.T * A.W;
 #pragma unroll
                 for (int p = 0; p < pt::kPar; ++p) A.x[p * N + col] = ys[lw][p];
                 A.out[col] = lnl;

@@ -29,6 +29,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "mbh_internal.cuh"
 #include "mbh_pt.cuh"
@@ -45,7 +46,7 @@ constexpr int kSortThreads = 1024;
 // ---- kernels -------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kStepThreads) pt_propose_kernel(const PtArgs A, int half)
 {
-    const int32_t M = A.T * (A.W / 2);
+    const int32_t M = A.n_ens * A.T * (A.W / 2);   // moving walkers of all ensembles
     const int32_t item = blockIdx.x * blockDim.x + threadIdx.x;
     if (item >= M) return;
     double v[kPar], th[kPar], fac;
@@ -62,70 +63,64 @@ __global__ void __launch_bounds__(kStepThreads) pt_propose_kernel(const PtArgs A
 
 __global__ void __launch_bounds__(kStepThreads) pt_accept_kernel(const PtArgs A, int half)
 {
-    __shared__ unsigned int cnt[kMaxTemps * 8];
-    for (int i = threadIdx.x; i < A.T * 8; i += blockDim.x) cnt[i] = 0;
-    __syncthreads();
-    const int32_t Wh = A.W / 2, M = A.T * Wh, N = A.T * A.W;
+    const int32_t M = A.n_ens * A.T * (A.W / 2);
+    const int64_t N = (int64_t)A.n_ens * A.T * A.W;
     const int32_t item = blockIdx.x * blockDim.x + threadIdx.x;
-    if (item < M) {
-        int32_t col;
-        int t;
-        const int32_t f = A.flag[item];
-        const int kind = f >> 1;
-        const bool acc = accept_test(A, half, item, A.out_p[item], A.fac[item], f, col, t);
-        atomicAdd(&cnt[t * 8 + kind], 1u);
-        if (acc) {
-            atomicAdd(&cnt[t * 8 + 4 + kind], 1u);
+    if (item >= M) return;
+    int32_t col;
+    int t, cb;
+    const int32_t f = A.flag[item];
+    const int kind = f >> 1;
+    const bool acc = accept_test(A, half, item, A.out_p[item], A.fac[item], f, col, t, cb);
+    // counters of ensemble e at cb: [0, 4T) proposals per (t, kind), [4T, 8T) accepted
+    atomicAdd(&A.counters[cb + t * 4 + kind], 1ull);
+    if (acc) {
+        atomicAdd(&A.counters[cb + 4 * A.T + t * 4 + kind], 1ull);
 #pragma unroll
-            for (int p = 0; p < kPar; ++p) A.x[(int64_t)p * N + col] = A.y[(int64_t)p * M + item];
+        for (int p = 0; p < kPar; ++p) A.x[(int64_t)p * N + col] = A.y[(int64_t)p * M + item];
 #pragma unroll
-            for (int q = 0; q < 3; ++q) A.out[(int64_t)q * N + col] = A.out_p[(int64_t)q * M + item];
-        }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < A.T * 8; i += blockDim.x) {
-        const unsigned int c = cnt[i];
-        if (c == 0) continue;
-        const int t = i / 8, j = i % 8;
-        // counters: [0, 4T) proposals per (t, kind), [4T, 8T) accepted per (t, kind)
-        const int dst = j < 4 ? t * 4 + j : 4 * A.T + t * 4 + (j - 4);
-        atomicAdd(&A.counters[dst], (unsigned long long)c);
+        for (int q = 0; q < 3; ++q) A.out[(int64_t)q * N + col] = A.out_p[(int64_t)q * M + item];
     }
 }
 
 // ln u of every acceptance and swap test of the iteration (state-independent, float64 log on
-// the whole GPU): items [0, 2M) acceptance tests of half 0 and 1, then [2M, 2M + (T-1) W) swaps.
+// the whole GPU): items [0, 2 Mt) acceptance tests of half 0 and 1 (Mt = n_ens M), then
+// n_ens (T-1) W swap tests.
 __global__ void __launch_bounds__(kThreads) pt_draws_kernel(const PtArgs A)
 {
-    const int32_t M = A.T * (A.W / 2);
-    const int64_t n = 2 * (int64_t)M + (int64_t)(A.T - 1) * A.W;
+    const int32_t M = A.T * (A.W / 2), Mt = A.n_ens * M;
+    const int64_t per = (int64_t)(A.T - 1) * A.W;
+    const int64_t n = 2 * (int64_t)Mt + (int64_t)A.n_ens * per;
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n) return;
     const uint64_t step = *A.step;
-    if (q < 2 * M) {
-        const int half = (int)(q / M);
-        const int32_t item = (int32_t)(q - (int64_t)half * M);
-        const uint4 r = draw(A.seed, (uint32_t)item, P_ACCEPT + (uint32_t)half, step);
+    if (q < 2 * (int64_t)Mt) {
+        const int half = (int)(q / Mt);
+        const int32_t item = (int32_t)(q - (int64_t)half * Mt);
+        const int32_t e = item / M, li = item - e * M;
+        const uint4 r = draw(ens_seed(A, e), (uint32_t)li, P_ACCEPT + (uint32_t)half, step);
         A.lnu_acc[q] = log(u53(r.x, r.y));
     } else {
-        const int64_t s = q - 2 * M;
-        const int i = 1 + (int)(s / A.W);
-        const int32_t k = (int32_t)(s - (int64_t)(i - 1) * A.W);
-        const uint4 r = draw(A.seed, (uint32_t)k, P_SWAP_ACC + (uint32_t)i, step);
-        A.lnu_swap[(int64_t)i * A.W + k] = log(u53(r.x, r.y));
+        const int64_t s = q - 2 * (int64_t)Mt;
+        const int e = (int)(s / per);
+        const int64_t r0 = s - (int64_t)e * per;
+        const int i = 1 + (int)(r0 / A.W);
+        const int32_t k = (int32_t)(r0 - (int64_t)(i - 1) * A.W);
+        const uint4 r = draw(ens_seed(A, e), (uint32_t)k, P_SWAP_ACC + (uint32_t)i, step);
+        A.lnu_swap[((int64_t)e * A.T + i) * A.W + k] = log(u53(r.x, r.y));
     }
 }
 
-// One block per swap level i = blockIdx.x + 1: sort the keys (48 random bits, then the walker
-// index) of the hot temperature's walkers; perm[i][k] = hot partner of cold walker k.
+// One block per (ensemble e, swap level i): sort the keys (48 random bits, then the walker
+// index) of the hot temperature's walkers; perm[e][i][k] = hot partner of cold walker k.
 __global__ void __launch_bounds__(kSortThreads) pt_perm_kernel(const PtArgs A, int Wp)
 {
     extern __shared__ unsigned long long keys[];
-    const int i = blockIdx.x + 1;
+    const int e = blockIdx.x / (A.T - 1), i = blockIdx.x % (A.T - 1) + 1;
     const uint64_t step = *A.step;
     for (int k = threadIdx.x; k < Wp; k += blockDim.x) {
         if (k < A.W) {
-            const uint4 r = draw(A.seed, (uint32_t)k, P_SWAP_KEY + (uint32_t)i, step);
+            const uint4 r = draw(ens_seed(A, e), (uint32_t)k, P_SWAP_KEY + (uint32_t)i, step);
             keys[k] = ((unsigned long long)r.x << 32) | (unsigned long long)(r.y & 0xFFFF0000u) |
                       (unsigned long long)k;
         } else {
@@ -147,7 +142,7 @@ __global__ void __launch_bounds__(kSortThreads) pt_perm_kernel(const PtArgs A, i
             __syncthreads();
         }
     for (int k = threadIdx.x; k < A.W; k += blockDim.x)
-        A.perm[(int64_t)i * A.W + k] = (int32_t)(keys[k] & 0xFFFFull);
+        A.perm[((int64_t)e * A.T + i) * A.W + k] = (int32_t)(keys[k] & 0xFFFFull);
 }
 
 // Swap levels in order, hottest first; the hot and cold temperatures of a level are held in
@@ -161,10 +156,17 @@ __global__ void __launch_bounds__(kSortThreads) pt_swap_kernel(const PtArgs A)
 {
     extern __shared__ double sm[];
     const int W = A.W, T = A.T;
+    const int e = blockIdx.x;                               // one block per ensemble
+    int32_t* map = A.map + (int64_t)e * T * W;
+    const int32_t* perm = A.perm + (int64_t)e * T * W;
+    const double* lnu_swap = A.lnu_swap + (int64_t)e * T * W;
+    double* betas = A.betas + (int64_t)e * T;
+    unsigned long long* counters = A.counters + (int64_t)e * 10 * T;
     double* lnl = sm;                                       // [2][W]
     int32_t* mp = reinterpret_cast<int32_t*>(sm + 2 * W);   // [2][W]
     __shared__ unsigned int acc_level;
     __shared__ unsigned int acc_now[kMaxTemps];
+    __shared__ bool last;
     const uint64_t step = *A.step;
     if (T > 1) {
         int32_t pm[J], pp[J];
@@ -175,9 +177,9 @@ __global__ void __launch_bounds__(kSortThreads) pt_swap_kernel(const PtArgs A)
             for (int j = 0; j < J; ++j) {
                 const int k = threadIdx.x + j * blockDim.x;
                 if (k < W) {
-                    pm[j] = A.map[(i - 1) * W + k];
-                    pp[j] = A.perm[(int64_t)i * W + k];
-                    pu[j] = A.lnu_swap[(int64_t)i * W + k];
+                    pm[j] = map[(i - 1) * W + k];
+                    pp[j] = perm[(int64_t)i * W + k];
+                    pu[j] = lnu_swap[(int64_t)i * W + k];
                 }
             }
         };
@@ -190,7 +192,7 @@ __global__ void __launch_bounds__(kSortThreads) pt_swap_kernel(const PtArgs A)
         };
         int hot = 0;
         for (int k = threadIdx.x; k < W; k += blockDim.x) {
-            const int32_t c = A.map[(T - 1) * W + k];
+            const int32_t c = map[(T - 1) * W + k];
             mp[k] = c;
             lnl[k] = A.out[c];
         }
@@ -213,7 +215,7 @@ __global__ void __launch_bounds__(kSortThreads) pt_swap_kernel(const PtArgs A)
             if (threadIdx.x == 0) acc_level = 0;
             __syncthreads();
             if (i > 1) issue(i - 1);   // in flight while this level is decided
-            const double db = __dsub_rn(A.betas[i - 1], A.betas[i]);
+            const double db = __dsub_rn(betas[i - 1], betas[i]);
             unsigned int mine = 0;
 #pragma unroll
             for (int j = 0; j < J; ++j) {
@@ -234,16 +236,16 @@ __global__ void __launch_bounds__(kSortThreads) pt_swap_kernel(const PtArgs A)
             if (i > 1) gather();
             if (mine) atomicAdd(&acc_level, mine);
             __syncthreads();
-            for (int k = threadIdx.x; k < W; k += blockDim.x) A.map[i * W + k] = mp[hot * W + k];
+            for (int k = threadIdx.x; k < W; k += blockDim.x) map[i * W + k] = mp[hot * W + k];
             if (threadIdx.x == 0) {
-                A.counters[8 * T + i] += acc_level;
-                A.counters[9 * T + i] += (unsigned long long)W;
+                counters[8 * T + i] += acc_level;
+                counters[9 * T + i] += (unsigned long long)W;
                 acc_now[i] = acc_level;
             }
             __syncthreads();
             hot = cold;
         }
-        for (int k = threadIdx.x; k < W; k += blockDim.x) A.map[k] = mp[hot * W + k];
+        for (int k = threadIdx.x; k < W; k += blockDim.x) map[k] = mp[hot * W + k];
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -253,7 +255,7 @@ __global__ void __launch_bounds__(kSortThreads) pt_swap_kernel(const PtArgs A)
             const double kappa = __ddiv_rn(__dmul_rn(__ddiv_rn(1.0, A.adapt_nu), A.adapt_n0),
                                            __dadd_rn((double)step, A.adapt_n0));
             double Tt[kMaxTemps], S[kMaxTemps];
-            for (int t = 0; t < T; ++t) Tt[t] = __ddiv_rn(1.0, A.betas[t]);
+            for (int t = 0; t < T; ++t) Tt[t] = __ddiv_rn(1.0, betas[t]);
             for (int t = 1; t <= T - 2; ++t) {
                 const double a0 = __ddiv_rn((double)acc_now[t], (double)W);
                 const double a1 = __ddiv_rn((double)acc_now[t + 1], (double)W);
@@ -261,10 +263,16 @@ __global__ void __launch_bounds__(kSortThreads) pt_swap_kernel(const PtArgs A)
             }
             for (int t = 1; t <= T - 2; ++t) {
                 Tt[t] = __dadd_rn(Tt[t - 1], exp(S[t]));
-                A.betas[t] = __ddiv_rn(1.0, Tt[t]);
+                betas[t] = __ddiv_rn(1.0, Tt[t]);
             }
         }
-        *A.step = step + 1;
+        // the last ensemble block to finish advances the step: every block has read it by then
+        __threadfence();
+        last = atomicAdd(A.done, 1u) == (unsigned int)(A.n_ens - 1);
+        if (last) {
+            *A.done = 0u;
+            *A.step = step + 1;
+        }
     }
 }
 
@@ -285,7 +293,7 @@ __global__ void pt_theta_kernel(const double* __restrict__ x, int64_t N, double*
 __global__ void pt_gather_kernel(const PtArgs A, const double* __restrict__ xs, double* __restrict__ xo,
                                  double* __restrict__ oo, int scatter)
 {
-    const int64_t N = (int64_t)A.T * A.W;
+    const int64_t N = (int64_t)A.n_ens * A.T * A.W;
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= N) return;
     if (scatter) {
@@ -303,16 +311,17 @@ __global__ void pt_gather_kernel(const PtArgs A, const double* __restrict__ xs, 
         for (int q = 0; q < 3; ++q) oo[q * N + s] = A.out[q * N + c];
 }
 
-// best (largest lnL, lowest slot on ties) walker of temperature t -> res[14] (x, out)
-__global__ void __launch_bounds__(kSortThreads) pt_best_kernel(const PtArgs A, int t, double* res)
+// best (largest lnL, lowest slot on ties) walker of temperature t of ensemble e -> res[14]
+__global__ void __launch_bounds__(kSortThreads) pt_best_kernel(const PtArgs A, int e, int t, double* res)
 {
     __shared__ double bv[32];
     __shared__ int bs[32];
-    const int64_t N = (int64_t)A.T * A.W;
+    const int64_t N = (int64_t)A.n_ens * A.T * A.W;
+    const int32_t* map = A.map + (int64_t)e * A.T * A.W;
     double best = -INFINITY;
     int slot = -1;
     for (int k = threadIdx.x; k < A.W; k += blockDim.x) {
-        const double v = A.out[A.map[t * A.W + k]];
+        const double v = A.out[map[t * A.W + k]];
         if (slot < 0 || v > best) {
             best = v;
             slot = k;
@@ -338,7 +347,7 @@ __global__ void __launch_bounds__(kSortThreads) pt_best_kernel(const PtArgs A, i
                 best = bv[w];
                 slot = bs[w];
             }
-        const int32_t c = A.map[t * A.W + (slot < 0 ? 0 : slot)];
+        const int32_t c = map[t * A.W + (slot < 0 ? 0 : slot)];
         for (int p = 0; p < kPar; ++p) res[p] = A.x[p * N + c];
         for (int q = 0; q < 3; ++q) res[kPar + q] = A.out[q * N + c];
     }
@@ -350,8 +359,8 @@ struct mbh_pt {
     int device = -1;
     PtArgs A{};
     mbh_precision precision = MBH_MIXED;
-    const mbh_ref* ref = nullptr;
-    const mbh_data* data = nullptr;
+    std::vector<const mbh_ref*> refs;   // one per ensemble (heterodyned likelihood)
+    const mbh_data* data = nullptr;      // or the data of the direct likelihood
     mbh_het_config cfg{8, 128, 0};
     uint32_t modes = 1u;     // direct likelihood: harmonic modes of the templates
     bool fused = false;      // half steps as one fused heterodyne launch each
@@ -380,25 +389,28 @@ void free_pt(mbh_pt* P)
     if (P->join_draws) cudaEventDestroy(P->join_draws);
     PtArgs& A = P->A;
     void* bufs[] = {A.x, A.out, A.map, A.y, A.theta, A.out_p, A.fac, A.flag, A.perm, A.lnu_acc, A.lnu_swap,
-                    A.betas, A.counters, A.step, P->res, P->A_dev};
+                    A.betas, A.counters, A.step, A.done, P->res, P->A_dev};
     for (void* b : bufs)
         if (b) cudaFree(b);
     delete P;
 }
 
-// likelihood of the first n columns of A.theta into dst [3][n]
+// likelihood of the first n columns of A.theta into dst [3][n]; the columns are n/n_ens per
+// ensemble, in ensemble order
 mbh_status likelihood(mbh_pt* P, int64_t n, double* dst, cudaStream_t st)
 {
-    if (P->ref) {
-        const int64_t off[2] = {0, n};
-        return het_loglike_batch_cfg(&P->ref, off, 1, P->A.theta, P->precision, &P->cfg, dst, st);
+    if (!P->refs.empty()) {
+        const int ne = (int)P->refs.size();
+        std::vector<int64_t> off(ne + 1);
+        for (int e = 0; e <= ne; ++e) off[e] = n / ne * e;
+        return het_loglike_batch_cfg(P->refs.data(), off.data(), ne, P->A.theta, P->precision, &P->cfg, dst, st);
     }
     return direct_loglike_batch_hm(P->data, P->A.theta, n, P->modes, P->precision, dst, st);
 }
 
 mbh_status rescore(mbh_pt* P, cudaStream_t st)
 {
-    const int64_t N = (int64_t)P->A.T * P->A.W;
+    const int64_t N = (int64_t)P->A.n_ens * P->A.T * P->A.W;
     pt_theta_kernel<<<(unsigned)((N + kThreads - 1) / kThreads), kThreads, 0, st>>>(P->A.x, N, P->A.theta);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "pt_theta_kernel");
@@ -408,7 +420,7 @@ mbh_status rescore(mbh_pt* P, cudaStream_t st)
 mbh_status queue_iteration(mbh_pt* P, cudaStream_t st)
 {
     const PtArgs& A = P->A;
-    const int32_t M = A.T * (A.W / 2);
+    const int32_t M = A.n_ens * A.T * (A.W / 2);   // moving walkers of all ensembles
     const unsigned gM = (unsigned)((M + kStepThreads - 1) / kStepThreads);
     cudaError_t e = cudaSuccess;
     // state-independent work on a side stream while the first half step runs: ln u of every
@@ -416,12 +428,12 @@ mbh_status queue_iteration(mbh_pt* P, cudaStream_t st)
     e = cudaEventRecord(P->fork, st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(P->side, P->fork, 0);
     if (e != cudaSuccess) return cuda_fail(e, "fork");
-    const int64_t nd = 2 * (int64_t)M + (int64_t)(A.T - 1) * A.W;
+    const int64_t nd = 2 * (int64_t)M + (int64_t)A.n_ens * (A.T - 1) * A.W;
     pt_draws_kernel<<<(unsigned)((nd + kThreads - 1) / kThreads), kThreads, 0, P->side>>>(A);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "pt_draws_kernel");
     if ((e = cudaEventRecord(P->join_draws, P->side)) != cudaSuccess) return cuda_fail(e, "join");
     if (A.T > 1) {
-        pt_perm_kernel<<<A.T - 1, kSortThreads, sizeof(unsigned long long) * P->Wp, P->side>>>(A, P->Wp);
+        pt_perm_kernel<<<A.n_ens * (A.T - 1), kSortThreads, sizeof(unsigned long long) * P->Wp, P->side>>>(A, P->Wp);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "pt_perm_kernel");
     }
     if ((e = cudaEventRecord(P->join, P->side)) != cudaSuccess) return cuda_fail(e, "join");
@@ -429,7 +441,9 @@ mbh_status queue_iteration(mbh_pt* P, cudaStream_t st)
         if (P->fused) {   // proposal, likelihood and acceptance in one launch
             if (half == 0 && (e = cudaStreamWaitEvent(st, P->join_draws, 0)) != cudaSuccess)
                 return cuda_fail(e, "join");
-            if (mbh_status s = het_launch_fused_pt(P->ref, M, P->cfg, P->A_dev, half, st)) return s;
+            if (mbh_status s = het_launch_fused_pt(P->refs.data(), (int)P->refs.size(), M / A.n_ens, P->cfg,
+                                                   P->A_dev, half, st))
+                return s;
             continue;
         }
         pt_propose_kernel<<<gM, kStepThreads, 0, st>>>(A, half);
@@ -443,10 +457,11 @@ mbh_status queue_iteration(mbh_pt* P, cudaStream_t st)
     if ((e = cudaStreamWaitEvent(st, P->join, 0)) != cudaSuccess) return cuda_fail(e, "join");
     const size_t swap_smem = (sizeof(double) + sizeof(int32_t)) * 2 * A.W;
     const int J = (A.W + kSortThreads - 1) / kSortThreads;
-    if (J <= 1) pt_swap_kernel<1><<<1, kSortThreads, swap_smem, st>>>(A);
-    else if (J <= 2) pt_swap_kernel<2><<<1, kSortThreads, swap_smem, st>>>(A);
-    else if (J <= 4) pt_swap_kernel<4><<<1, kSortThreads, swap_smem, st>>>(A);
-    else pt_swap_kernel<8><<<1, kSortThreads, swap_smem, st>>>(A);
+    const unsigned ne = (unsigned)A.n_ens;   // one block per ensemble
+    if (J <= 1) pt_swap_kernel<1><<<ne, kSortThreads, swap_smem, st>>>(A);
+    else if (J <= 2) pt_swap_kernel<2><<<ne, kSortThreads, swap_smem, st>>>(A);
+    else if (J <= 4) pt_swap_kernel<4><<<ne, kSortThreads, swap_smem, st>>>(A);
+    else pt_swap_kernel<8><<<ne, kSortThreads, swap_smem, st>>>(A);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "pt_swap_kernel");
     return MBH_OK;
 }
@@ -488,14 +503,18 @@ mbh_status build_graph(mbh_pt* P)
 
 }  // namespace
 
-extern "C" mbh_status mbh_pt_create(const mbh_pt_opts* o, const mbh_ref* ref, const mbh_data* data,
-                                    const double* betas_host, const double* x_dev, void* stream,
-                                    mbh_pt** out)
+extern "C" mbh_status mbh_pt_create_multi(const mbh_pt_opts* o, const mbh_ref* const* refs, int32_t n_ens,
+                                          const mbh_data* data, const double* betas_host, const double* x_dev,
+                                          void* stream, mbh_pt** out)
 {
     if (!out) return fail(MBH_EINVAL, "out is NULL");
     *out = nullptr;
     if (!o || !betas_host || !x_dev) return fail(MBH_EINVAL, "NULL opts/betas/x");
-    if ((ref == nullptr) == (data == nullptr)) return fail(MBH_EINVAL, "give exactly one of ref and data");
+    if ((refs == nullptr) == (data == nullptr)) return fail(MBH_EINVAL, "give exactly one of refs and data");
+    if (n_ens < 1 || n_ens > 1024) return fail(MBH_EINVAL, "n_ens %d not in [1, 1024]", n_ens);
+    if (refs)
+        for (int32_t e = 0; e < n_ens; ++e)
+            if (!refs[e]) return fail(MBH_EINVAL, "refs[%d] is NULL", e);
     if (o->ntemps < 1 || o->ntemps > kMaxTemps) return fail(MBH_EINVAL, "ntemps %d not in [1, %d]", o->ntemps, kMaxTemps);
     if (o->walkers < 4 || o->walkers > kMaxWalkers || (o->walkers & 1))
         return fail(MBH_EINVAL, "walkers %d: even, in [4, %d]", o->walkers, kMaxWalkers);
@@ -509,7 +528,8 @@ extern "C" mbh_status mbh_pt_create(const mbh_pt_opts* o, const mbh_ref* ref, co
     for (int p = 0; p < kPar; ++p)
         if (!(o->lo[p] <= o->hi[p])) return fail(MBH_EINVAL, "prior box: lo[%d] > hi[%d]", p, p);
     if (o->adapt_time > 0.0 && !(o->adapt_lag > 0.0)) return fail(MBH_EINVAL, "adapt_lag must be > 0");
-    for (int t = 0; t < o->ntemps; ++t)
+    if ((int64_t)n_ens * o->ntemps * o->walkers > 0x3fffffff) return fail(MBH_EINVAL, "ensemble too large");
+    for (int64_t t = 0; t < (int64_t)n_ens * o->ntemps; ++t)
         if (!(betas_host[t] >= 0.0) || !std::isfinite(betas_host[t])) return fail(MBH_EINVAL, "betas must be finite and >= 0");
     if (o->precision != MBH_FP64 && o->precision != MBH_MIXED) return fail(MBH_EINVAL, "unknown precision");
     const uint32_t modes = o->modes ? o->modes : 1u;
@@ -518,13 +538,18 @@ extern "C" mbh_status mbh_pt_create(const mbh_pt_opts* o, const mbh_ref* ref, co
     if (mbh_status s = check_device()) return s;
     int dev = -1;
     cudaGetDevice(&dev);
-    if (ref && ref->device != dev) return fail(MBH_EINVAL, "ref lives on another device");
+    bool all22 = true;
+    if (refs)
+        for (int32_t e = 0; e < n_ens; ++e) {
+            if (refs[e]->device != dev) return fail(MBH_EINVAL, "refs[%d] lives on another device", e);
+            all22 = all22 && refs[e]->modes == 1u;
+        }
     if (data && data->device != dev) return fail(MBH_EINVAL, "data lives on another device");
 
     mbh_pt* P = new (std::nothrow) mbh_pt;
     if (!P) return fail(MBH_ENOMEM, "host allocation");
     P->device = dev;
-    P->ref = ref;
+    if (refs) P->refs.assign(refs, refs + n_ens);
     P->data = data;
     P->precision = o->precision;
     P->modes = modes;
@@ -532,6 +557,7 @@ extern "C" mbh_status mbh_pt_create(const mbh_pt_opts* o, const mbh_ref* ref, co
     PtArgs& A = P->A;
     A.T = o->ntemps;
     A.W = o->walkers;
+    A.n_ens = n_ens;
     A.seed = o->seed;
     A.a = o->a;
     A.am1 = o->a - 1.0;
@@ -544,7 +570,8 @@ extern "C" mbh_status mbh_pt_create(const mbh_pt_opts* o, const mbh_ref* ref, co
     std::memcpy(A.hi, o->hi, sizeof A.hi);
     P->Wp = 1;
     while (P->Wp < A.W) P->Wp <<= 1;
-    const int64_t N = (int64_t)A.T * A.W, M = N / 2;
+    const int64_t N = (int64_t)n_ens * A.T * A.W, M = N / 2;
+    const int64_t NT = (int64_t)n_ens * A.T;
     cudaError_t e = cudaSuccess;
     auto alloc = [&](void** p, size_t bytes) {
         if (e == cudaSuccess) e = cudaMalloc(p, bytes);
@@ -560,9 +587,10 @@ extern "C" mbh_status mbh_pt_create(const mbh_pt_opts* o, const mbh_ref* ref, co
     alloc((void**)&A.perm, sizeof(int32_t) * N);
     alloc((void**)&A.lnu_acc, sizeof(double) * 2 * M);
     alloc((void**)&A.lnu_swap, sizeof(double) * N);
-    alloc((void**)&A.betas, sizeof(double) * A.T);
-    alloc((void**)&A.counters, sizeof(unsigned long long) * 10 * A.T);
+    alloc((void**)&A.betas, sizeof(double) * NT);
+    alloc((void**)&A.counters, sizeof(unsigned long long) * 10 * NT);
     alloc((void**)&A.step, sizeof(unsigned long long));
+    alloc((void**)&A.done, sizeof(unsigned int));
     alloc((void**)&P->res, sizeof(double) * 14);
     alloc((void**)&P->A_dev, sizeof(PtArgs));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking);
@@ -583,13 +611,14 @@ extern "C" mbh_status mbh_pt_create(const mbh_pt_opts* o, const mbh_ref* ref, co
     if (e == cudaSuccess) e = cudaFuncSetAttribute(pt_swap_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, swap_max);
     cudaStream_t st = (cudaStream_t)stream;
     const unsigned long long zero = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(A.betas, betas_host, sizeof(double) * A.T, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(A.counters, 0, sizeof(unsigned long long) * 10 * A.T, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(A.betas, betas_host, sizeof(double) * NT, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(A.counters, 0, sizeof(unsigned long long) * 10 * NT, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(A.step, &zero, sizeof zero, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(A.done, 0, sizeof(unsigned int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(A.perm, 0, sizeof(int32_t) * N, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(P->A_dev, &A, sizeof(PtArgs), cudaMemcpyHostToDevice, st);
     P->fuse_ok = o->precision == MBH_MIXED && !o->no_fuse;
-    P->fused = P->fuse_ok && ref != nullptr && ref->modes == 1u;
+    P->fused = P->fuse_ok && refs != nullptr && all22;
     if (e != cudaSuccess) {
         free_pt(P);
         return cuda_fail(e, "sampler setup");
@@ -614,6 +643,13 @@ extern "C" mbh_status mbh_pt_create(const mbh_pt_opts* o, const mbh_ref* ref, co
     return MBH_OK;
 }
 
+extern "C" mbh_status mbh_pt_create(const mbh_pt_opts* o, const mbh_ref* ref, const mbh_data* data,
+                                    const double* betas_host, const double* x_dev, void* stream,
+                                    mbh_pt** out)
+{
+    return mbh_pt_create_multi(o, ref ? &ref : nullptr, 1, data, betas_host, x_dev, stream, out);
+}
+
 extern "C" mbh_status mbh_pt_run(mbh_pt* P, int64_t n_iter, int32_t use_graph, void* stream)
 {
     if (!P) return fail(MBH_EINVAL, "sampler is NULL");
@@ -635,7 +671,7 @@ extern "C" mbh_status mbh_pt_run(mbh_pt* P, int64_t n_iter, int32_t use_graph, v
 extern "C" mbh_status mbh_pt_state(const mbh_pt* P, double* x_dev, double* out_dev, void* stream)
 {
     if (!P) return fail(MBH_EINVAL, "sampler is NULL");
-    const int64_t N = (int64_t)P->A.T * P->A.W;
+    const int64_t N = (int64_t)P->A.n_ens * P->A.T * P->A.W;
     pt_gather_kernel<<<(unsigned)((N + kThreads - 1) / kThreads), kThreads, 0, (cudaStream_t)stream>>>(
         P->A, nullptr, x_dev, out_dev, 0);
     cudaError_t e = cudaGetLastError();
@@ -645,7 +681,7 @@ extern "C" mbh_status mbh_pt_state(const mbh_pt* P, double* x_dev, double* out_d
 extern "C" mbh_status mbh_pt_set_state(mbh_pt* P, const double* x_dev, void* stream)
 {
     if (!P || !x_dev) return fail(MBH_EINVAL, "NULL sampler/x");
-    const int64_t N = (int64_t)P->A.T * P->A.W;
+    const int64_t N = (int64_t)P->A.n_ens * P->A.T * P->A.W;
     cudaStream_t st = (cudaStream_t)stream;
     pt_gather_kernel<<<(unsigned)((N + kThreads - 1) / kThreads), kThreads, 0, st>>>(P->A, x_dev, nullptr, nullptr, 1);
     cudaError_t e = cudaGetLastError();
@@ -653,24 +689,34 @@ extern "C" mbh_status mbh_pt_set_state(mbh_pt* P, const double* x_dev, void* str
     return rescore(P, st);
 }
 
-extern "C" mbh_status mbh_pt_set_ref(mbh_pt* P, const mbh_ref* ref, void* stream)
+extern "C" mbh_status mbh_pt_set_ref_at(mbh_pt* P, int32_t ensemble, const mbh_ref* ref, void* stream)
 {
     if (!P || !ref) return fail(MBH_EINVAL, "NULL sampler/ref");
-    if (!P->ref) return fail(MBH_EINVAL, "sampler uses the direct likelihood");
+    if (P->refs.empty()) return fail(MBH_EINVAL, "sampler uses the direct likelihood");
+    if (ensemble < 0 || ensemble >= (int32_t)P->refs.size()) return fail(MBH_EINVAL, "ensemble %d out of range", ensemble);
     if (ref->device != P->device) return fail(MBH_EINVAL, "ref lives on another device");
-    P->ref = ref;
-    P->fused = P->fuse_ok && ref->modes == 1u;
+    P->refs[ensemble] = ref;
+    bool all22 = true;
+    for (const mbh_ref* r : P->refs) all22 = all22 && r->modes == 1u;
+    P->fused = P->fuse_ok && all22;
     drop_graph(P);   // the reference's tables are baked into the captured launches
     return rescore(P, (cudaStream_t)stream);
+}
+
+extern "C" mbh_status mbh_pt_set_ref(mbh_pt* P, const mbh_ref* ref, void* stream)
+{
+    if (P && P->A.n_ens != 1) return fail(MBH_EINVAL, "several ensembles: use mbh_pt_set_ref_at");
+    return mbh_pt_set_ref_at(P, 0, ref, stream);
 }
 
 extern "C" mbh_status mbh_pt_set_betas(mbh_pt* P, const double* betas_host, void* stream)
 {
     if (!P || !betas_host) return fail(MBH_EINVAL, "NULL sampler/betas");
-    for (int t = 0; t < P->A.T; ++t)
+    const int64_t NT = (int64_t)P->A.n_ens * P->A.T;
+    for (int64_t t = 0; t < NT; ++t)
         if (!(betas_host[t] >= 0.0) || !std::isfinite(betas_host[t])) return fail(MBH_EINVAL, "betas must be finite and >= 0");
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = cudaMemcpyAsync(P->A.betas, betas_host, sizeof(double) * P->A.T,
+    cudaError_t e = cudaMemcpyAsync(P->A.betas, betas_host, sizeof(double) * NT,
                                     cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return e == cudaSuccess ? MBH_OK : cuda_fail(e, "set betas");
@@ -680,7 +726,8 @@ extern "C" mbh_status mbh_pt_get_betas(const mbh_pt* P, double* betas_host, void
 {
     if (!P || !betas_host) return fail(MBH_EINVAL, "NULL sampler/betas");
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = cudaMemcpyAsync(betas_host, P->A.betas, sizeof(double) * P->A.T, cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaMemcpyAsync(betas_host, P->A.betas, sizeof(double) * P->A.n_ens * P->A.T,
+                                    cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return e == cudaSuccess ? MBH_OK : cuda_fail(e, "get betas");
 }
@@ -692,7 +739,7 @@ extern "C" mbh_status mbh_pt_counters(const mbh_pt* P, int64_t* counters_host, u
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaSuccess;
     if (counters_host)
-        e = cudaMemcpyAsync(counters_host, P->A.counters, sizeof(int64_t) * 10 * P->A.T,
+        e = cudaMemcpyAsync(counters_host, P->A.counters, sizeof(int64_t) * 10 * P->A.n_ens * P->A.T,
                             cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess && step_host)
         e = cudaMemcpyAsync(step_host, P->A.step, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
@@ -700,13 +747,14 @@ extern "C" mbh_status mbh_pt_counters(const mbh_pt* P, int64_t* counters_host, u
     return e == cudaSuccess ? MBH_OK : cuda_fail(e, "read counters");
 }
 
-extern "C" mbh_status mbh_pt_best(const mbh_pt* P, int32_t temp, double* x_host, double* out_host,
-                                  void* stream)
+extern "C" mbh_status mbh_pt_best_at(const mbh_pt* P, int32_t ensemble, int32_t temp, double* x_host,
+                                     double* out_host, void* stream)
 {
     if (!P) return fail(MBH_EINVAL, "sampler is NULL");
     if (temp < 0 || temp >= P->A.T) return fail(MBH_EINVAL, "temperature %d out of range", temp);
+    if (ensemble < 0 || ensemble >= P->A.n_ens) return fail(MBH_EINVAL, "ensemble %d out of range", ensemble);
     cudaStream_t st = (cudaStream_t)stream;
-    pt_best_kernel<<<1, kSortThreads, 0, st>>>(P->A, temp, P->res);
+    pt_best_kernel<<<1, kSortThreads, 0, st>>>(P->A, ensemble, temp, P->res);
     cudaError_t e = cudaGetLastError();
     double r[14];
     if (e == cudaSuccess) e = cudaMemcpyAsync(r, P->res, sizeof r, cudaMemcpyDeviceToHost, st);
@@ -715,6 +763,12 @@ extern "C" mbh_status mbh_pt_best(const mbh_pt* P, int32_t temp, double* x_host,
     if (x_host) std::memcpy(x_host, r, sizeof(double) * kPar);
     if (out_host) std::memcpy(out_host, r + kPar, sizeof(double) * 3);
     return MBH_OK;
+}
+
+extern "C" mbh_status mbh_pt_best(const mbh_pt* P, int32_t temp, double* x_host, double* out_host,
+                                  void* stream)
+{
+    return mbh_pt_best_at(P, 0, temp, x_host, out_host, stream);
 }
 
 extern "C" void mbh_pt_free(mbh_pt* P)

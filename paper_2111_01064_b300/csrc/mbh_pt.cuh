@@ -21,8 +21,12 @@ constexpr double kPtPi = 3.141592653589793;
 constexpr double kPtHalfPi = 1.5707963267948966;
 constexpr double kPtTwoPi = 6.283185307179586;
 
+// Several independent ensembles (one per source, or independent chains of one source) step
+// together: ensemble e owns slots [e T W, (e+1) T W) and half-step items [e M, (e+1) M),
+// M = T W/2, and draws its random numbers with the key seed_e = seed + e 0x9E3779B97F4A7C15,
+// so each ensemble is exactly a single-ensemble sampler with seed seed_e.
 struct PtArgs {
-    double* x;              // [11][N] positions, physical columns
+    double* x;              // [11][N] positions, physical columns (N = n_ens T W)
     double* out;            // [3][N] lnL, <d|h>, <h|h>
     int32_t* map;           // [N] slot -> column
     double* y;              // [11][M] proposals of the moving half
@@ -31,18 +35,24 @@ struct PtArgs {
     double* fac;            // [M] log acceptance factor (d-1) ln z of stretch moves
     int32_t* flag;          // [M] inside-prior bit | kind << 1
     int32_t* perm;          // [T][W] hot partner of cold walker k at level i
-    double* lnu_acc;        // [2][M] ln u of the acceptance tests of both half steps
-    double* lnu_swap;       // [T][W] ln u of the swap tests (level 0 unused)
-    double* betas;          // [T] (adapted in place when adapt_nu > 0)
-    unsigned long long* counters;   // [10 T]
+    double* lnu_acc;        // [2][n_ens M] ln u of the acceptance tests of both half steps
+    double* lnu_swap;       // [n_ens][T][W] ln u of the swap tests (level 0 unused)
+    double* betas;          // [n_ens][T] (adapted in place when adapt_nu > 0)
+    unsigned long long* counters;   // [n_ens][10 T]
+    unsigned int* done;     // swap-kernel blocks finished in this iteration (last one advances step)
     unsigned long long* step;       // iteration counter
     double lo[kPar], hi[kPar];
     double c1, c2, c3;      // cumulative proposal probabilities
     double a, am1;          // stretch scale and a - 1
     double adapt_nu, adapt_n0;   // ladder adaptation (nu > 0 enables)
     uint64_t seed;
-    int32_t T, W;
+    int32_t T, W, n_ens;
 };
+
+__device__ __forceinline__ uint64_t ens_seed(const PtArgs& A, int e)
+{
+    return A.seed + (uint64_t)e * 0x9E3779B97F4A7C15ull;
+}
 
 // ---- Philox4x32-10 -------------------------------------------------------------------------
 __device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
@@ -95,17 +105,21 @@ __device__ __forceinline__ void theta_of_x(const double (&x)[kPar], double (&th)
     th[8] = asin(fmin(fmax(x[8], -1.0), 1.0));
 }
 
-// Proposal of moving walker `item` (= t W/2 + k') of half `half`: Y (v), theta(Y) or theta of
-// the current point when Y leaves the prior box (th), the log acceptance factor and the flag
-// (inside-prior bit | kind << 1).  Explicitly rounded float64, so Y is reproducible bit for bit.
+// Proposal of moving walker `item` (= e M + t W/2 + k') of half `half`: Y (v), theta(Y) or
+// theta of the current point when Y leaves the prior box (th), the log acceptance factor and the
+// flag (inside-prior bit | kind << 1).  Explicitly rounded float64, so Y is reproducible bit for
+// bit.  The ensemble's own walkers and draws only: ensembles are independent.
 __device__ __forceinline__ void propose_item(const PtArgs& A, int half, int32_t item, uint64_t step,
                                              double (&v)[kPar], double (&th)[kPar], double& fac,
                                              int32_t& flag)
 {
-    const int32_t Wh = A.W / 2, N = A.T * A.W;
-    const int32_t t = item / Wh, kp = item - t * Wh;
-    const int32_t col = A.map[t * A.W + half * Wh + kp];
-    const uint4 r = draw(A.seed, (uint32_t)item, P_PROPOSE + (uint32_t)half, step);
+    const int32_t Wh = A.W / 2, M = A.T * Wh;
+    const int64_t N = (int64_t)A.n_ens * A.T * A.W;
+    const int32_t e = item / M, li = item - e * M;
+    const int32_t base = e * A.T * A.W;
+    const int32_t t = li / Wh, kp = li - t * Wh;
+    const int32_t col = A.map[base + t * A.W + half * Wh + kp];
+    const uint4 r = draw(ens_seed(A, e), (uint32_t)li, P_PROPOSE + (uint32_t)half, step);
     const double u = (double)r.x * (1.0 / 4294967296.0);
     const int kind = u < A.c1 ? K_STRETCH : u < A.c2 ? K_SKY_ALL : u < A.c3 ? K_SKY_LON : K_SKY_LAT;
     double xk[kPar];
@@ -114,7 +128,7 @@ __device__ __forceinline__ void propose_item(const PtArgs& A, int half, int32_t 
     fac = 0.0;
     if (kind == K_STRETCH) {
         const int32_t j = (1 - half) * Wh + (int32_t)(((uint64_t)r.y * (uint64_t)Wh) >> 32);
-        const int32_t colj = A.map[t * A.W + j];
+        const int32_t colj = A.map[base + t * A.W + j];
         const double s = __dadd_rn(__dmul_rn(A.am1, u53(r.z, r.w)), 1.0);
         const double z = __ddiv_rn(__dmul_rn(s, s), A.a);
 #pragma unroll
@@ -150,17 +164,20 @@ __device__ __forceinline__ void propose_item(const PtArgs& A, int half, int32_t 
 }
 
 // Tempered Metropolis test of moving walker `item` with proposal lnL lnl_p; returns the
-// decision (the column and temperature come back for the update).
+// decision (the column, and the ensemble's counter offset plus temperature, come back for the
+// update: counters of (e, t) start at e 10 T, the temperature index is t).
 __device__ __forceinline__ bool accept_test(const PtArgs& A, int half, int32_t item, double lnl_p, double fac,
-                                            int32_t flag, int32_t& col, int& t)
+                                            int32_t flag, int32_t& col, int& t, int& cbase)
 {
     const int32_t Wh = A.W / 2, M = A.T * Wh;
-    t = item / Wh;
-    const int32_t kp = item - t * Wh;
-    col = A.map[t * A.W + half * Wh + kp];
+    const int32_t e = item / M, li = item - e * M;
+    t = li / Wh;
+    const int32_t kp = li - t * Wh;
+    col = A.map[e * A.T * A.W + t * A.W + half * Wh + kp];
+    cbase = e * 10 * A.T;
     const double dl = __dsub_rn(lnl_p, A.out[col]);
-    const double la = __dadd_rn(fac, __dmul_rn(A.betas[t], dl));
-    return (flag & 1) && A.lnu_acc[(int64_t)half * M + item] < la;
+    const double la = __dadd_rn(fac, __dmul_rn(A.betas[e * A.T + t], dl));
+    return (flag & 1) && A.lnu_acc[(int64_t)half * A.n_ens * M + item] < la;
 }
 
 }  // namespace pt

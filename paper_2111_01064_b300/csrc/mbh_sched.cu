@@ -302,47 +302,57 @@ extern "C" void mbh_het_graph_free(mbh_het_graph* g)
 }
 
 namespace mbh {
-// One fused sampler half step (het_mixed_pt_kernel) over the M moving walkers of a (2,2)
-// reference: a single-source launch whose walker constants come from the sampler's proposals.
-mbh_status het_launch_fused_pt(const mbh_ref* ref, int64_t M, const mbh_het_config& cfg, const void* pt_dev,
-                               int half, cudaStream_t st)
+// One fused sampler half step (het_mixed_pt_kernel) over the moving walkers of n_ens ensembles,
+// M of each, ensemble e against refs[e] ((2,2) references): multi-source launches (up to
+// kMaxSrc ensembles each) whose walker constants come from the sampler's proposals.
+mbh_status het_launch_fused_pt(const mbh_ref* const* refs, int n_ens, int64_t M, const mbh_het_config& cfg,
+                               const void* pt_dev, int half, cudaStream_t st)
 {
     if (mbh_status s = check_cfg(cfg)) return s;
     const HetKernel k = het_kernel_mixed_pt(cfg.threads_per_walker, cfg.block);
     if (!k.launch) return fail(MBH_EINVAL, "no kernel for this configuration");
     const int wpb = cfg.block / cfg.threads_per_walker;
-    HetLaunch* L = new (std::nothrow) HetLaunch;
+    std::unique_ptr<HetLaunch> L(new (std::nothrow) HetLaunch);
     if (!L) return fail(MBH_ENOMEM, "host allocation");
-    std::memset(L, 0, sizeof *L);
-    L->W = M;
-    L->pt = pt_dev;
-    L->pt_half = half;
-    L->n_src = 1;
-    SrcDesc& S = L->src[0];
-    S.summary = ref->summary;
-    S.h0inv = ref->h0inv;
-    S.fe = ref->fe;
-    S.invw = ref->invw;
-    S.mix = ref->mix;
-    S.dd = ref->dd;
-    S.t_obs = ref->grid.t_obs;
-    S.E = ref->E;
-    S.modes = ref->modes;
-    S.w_begin = 0;
-    S.w_end = M;
-    S.tile_begin = 0;
-    const int64_t tiles = (M + wpb - 1) / wpb;
-    L->n_tiles = (int32_t)tiles;
-    int grid = (int)tiles;
+    int resident = 0;
     if (cfg.persistent) {
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k.fn, cfg.block, 0) == cudaSuccess)
-            grid = (int)std::min<int64_t>(tiles, (int64_t)std::max(1, per_sm) * sms);
+            resident = std::max(1, per_sm) * sms;
     }
-    const cudaError_t e = k.launch(*L, grid, st);
-    delete L;
-    return e == cudaSuccess ? MBH_OK : cuda_fail(e, "fused sampler half step");
+    for (int first = 0; first < n_ens; first += kMaxSrc) {
+        const int count = std::min(kMaxSrc, n_ens - first);
+        std::memset(L.get(), 0, sizeof(HetLaunch));
+        L->W = M * n_ens;
+        L->pt = pt_dev;
+        L->pt_half = half;
+        int64_t tiles = 0;
+        for (int q = 0; q < count; ++q) {
+            const mbh_ref* R = refs[first + q];
+            SrcDesc& S = L->src[q];
+            S.summary = R->summary;
+            S.h0inv = R->h0inv;
+            S.fe = R->fe;
+            S.invw = R->invw;
+            S.mix = R->mix;
+            S.dd = R->dd;
+            S.t_obs = R->grid.t_obs;
+            S.E = R->E;
+            S.modes = R->modes;
+            S.w_begin = (int64_t)(first + q) * M;
+            S.w_end = S.w_begin + M;
+            S.tile_begin = (int32_t)tiles;
+            tiles += (M + wpb - 1) / wpb;
+        }
+        if (tiles > 0x7fffffff) return fail(MBH_EINVAL, "too many walker tiles");
+        L->n_src = count;
+        L->n_tiles = (int32_t)tiles;
+        const int grid = resident > 0 ? (int)std::min<int64_t>(tiles, resident) : (int)tiles;
+        const cudaError_t e = k.launch(*L, grid, st);
+        if (e != cudaSuccess) return cuda_fail(e, "fused sampler half step");
+    }
+    return MBH_OK;
 }
 }  // namespace mbh

@@ -145,6 +145,10 @@ def lib() -> C.CDLL:
         "direct_loglike_batch_hm": (C.c_int, [vp, vp, i64, C.c_uint32, C.c_int, vp, vp]),
         "het_prepare_reference_hm": (C.c_int, [vp, dp, i32, C.c_uint32, vp, C.POINTER(vp)]),
         "mbh_pt_create": (C.c_int, [C.POINTER(PTOpts), vp, vp, dp, vp, vp, C.POINTER(vp)]),
+        "mbh_pt_create_multi": (C.c_int, [C.POINTER(PTOpts), C.POINTER(vp), i32, vp, dp, vp, vp,
+                                          C.POINTER(vp)]),
+        "mbh_pt_set_ref_at": (C.c_int, [vp, i32, vp, vp]),
+        "mbh_pt_best_at": (C.c_int, [vp, i32, i32, dp, dp, vp]),
         "mbh_server_loadgen": (C.c_int, [vp, C.POINTER(C.c_int32), i32, C.POINTER(dp), i64,
                                          C.POINTER(LoadgenOpts), C.POINTER(LoadgenReport)]),
         "mbh_pt_run": (C.c_int, [vp, i64, i32, vp]),
@@ -563,18 +567,25 @@ def mbh_selftest_math(kind: int, x: torch.Tensor, y: torch.Tensor | None = None,
 class PTSampler:
     """mbh_pt: parallel-tempered ensemble sampler iterations on the device (Sec. III).
 
-    Exactly one of ``ref`` (heterodyned likelihood) and ``data`` (direct likelihood).
-    ``x``: CUDA float64 (11, T*W) start positions in the sampler coordinates
-    (ln M_T, q, a1, a2, D_L, phi_ref, cos iota, lambda, sin beta, psi, t_ref)."""
+    One of ``ref`` (heterodyned likelihood), ``refs`` (one ensemble per reference, stepping
+    together) and ``data`` (direct likelihood; ``n_ens`` independent ensembles of it).
+    ``x``: CUDA float64 (11, n_ens*T*W) start positions in the sampler coordinates
+    (ln M_T, q, a1, a2, D_L, phi_ref, cos iota, lambda, sin beta, psi, t_ref); ``betas``: (T,)
+    for every ensemble or (n_ens, T)."""
 
     def __init__(self, x: torch.Tensor, betas, lo, hi, *, ref: Ref | None = None,
-                 data: Data | None = None, walkers: int, a: float = 2.0,
-                 probs=(0.85, 0.04, 0.03, 0.08), seed: int = 0, precision="mixed",
-                 cfg: HetConfig | None = None, modes: int = 1, adapt=None, fuse: bool = True,
-                 stream=None):
+                 refs: Sequence[Ref] | None = None, data: Data | None = None, n_ens: int = 1,
+                 walkers: int, a: float = 2.0, probs=(0.85, 0.04, 0.03, 0.08), seed: int = 0,
+                 precision="mixed", cfg: HetConfig | None = None, modes: int = 1, adapt=None,
+                 fuse: bool = True, stream=None):
         _require_cuda()
-        betas = np.ascontiguousarray(np.asarray(betas, dtype=np.float64))
-        T = betas.size
+        if ref is not None:
+            refs = [ref]
+        if refs is not None:
+            n_ens = len(refs)
+        betas = np.asarray(betas, dtype=np.float64)
+        T = betas.shape[-1]
+        betas = np.ascontiguousarray(np.broadcast_to(betas, (n_ens, T)))
         o = PTOpts()
         o.ntemps, o.walkers, o.a = T, int(walkers), float(a)
         o.probs[:] = [float(p) for p in probs]
@@ -586,56 +597,58 @@ class PTSampler:
         if adapt is not None:   # (nu, n0): ladder adaptation
             o.adapt_time, o.adapt_lag = float(adapt[0]), float(adapt[1])
         o.no_fuse = 0 if fuse else 1
-        self.T, self.W = T, int(walkers)
-        self.ref, self.data = ref, data   # keep them alive
+        self.T, self.W, self.n_ens = T, int(walkers), int(n_ens)
+        self.refs, self.data = (list(refs) if refs is not None else None), data   # keep them alive
+        arr = (vp * n_ens)(*[r.handle for r in refs]) if refs is not None else None
         h = vp()
-        _check(lib().mbh_pt_create(C.byref(o), ref.handle if ref else None,
-                                   data.handle if data else None,
-                                   betas.ctypes.data_as(dp),
-                                   _dev(x, torch.float64, (11, T * self.W), "x"), _stream(stream),
-                                   C.byref(h)))
+        _check(lib().mbh_pt_create_multi(C.byref(o), arr, n_ens, data.handle if data else None,
+                                         betas.ctypes.data_as(dp),
+                                         _dev(x, torch.float64, (11, n_ens * T * self.W), "x"),
+                                         _stream(stream), C.byref(h)))
         self.handle = h
 
     def run(self, n_iter: int, graph: bool = True, stream=None):
         _check(lib().mbh_pt_run(self.handle, int(n_iter), 1 if graph else 0, _stream(stream)))
 
     def state(self, stream=None) -> tuple[torch.Tensor, torch.Tensor]:
-        N = self.T * self.W
+        N = self.n_ens * self.T * self.W
         x = torch.empty((11, N), dtype=torch.float64, device="cuda")
         out = torch.empty((3, N), dtype=torch.float64, device="cuda")
         _check(lib().mbh_pt_state(self.handle, x.data_ptr(), out.data_ptr(), _stream(stream)))
         return x, out
 
     def set_state(self, x: torch.Tensor, stream=None):
-        _check(lib().mbh_pt_set_state(self.handle, _dev(x, torch.float64, (11, self.T * self.W), "x"),
+        _check(lib().mbh_pt_set_state(self.handle,
+                                      _dev(x, torch.float64, (11, self.n_ens * self.T * self.W), "x"),
                                       _stream(stream)))
 
-    def set_ref(self, ref: Ref, stream=None):
-        _check(lib().mbh_pt_set_ref(self.handle, ref.handle, _stream(stream)))
-        self.ref = ref
+    def set_ref(self, ref: Ref, ensemble: int = 0, stream=None):
+        _check(lib().mbh_pt_set_ref_at(self.handle, int(ensemble), ref.handle, _stream(stream)))
+        self.refs[ensemble] = ref
 
     def set_betas(self, betas, stream=None):
-        b = np.ascontiguousarray(np.asarray(betas, dtype=np.float64))
-        if b.size != self.T:
-            raise MBHError(1, f"need {self.T} betas")
+        b = np.ascontiguousarray(np.broadcast_to(np.asarray(betas, dtype=np.float64),
+                                                 (self.n_ens, self.T)))
         _check(lib().mbh_pt_set_betas(self.handle, b.ctypes.data_as(dp), _stream(stream)))
 
     def betas(self, stream=None) -> np.ndarray:
-        b = np.zeros(self.T)
+        """(T,) for one ensemble, (n_ens, T) otherwise."""
+        b = np.zeros((self.n_ens, self.T))
         _check(lib().mbh_pt_get_betas(self.handle, b.ctypes.data_as(dp), _stream(stream)))
-        return b
+        return b[0] if self.n_ens == 1 else b
 
     def counters(self, stream=None) -> tuple[np.ndarray, int]:
-        c = np.zeros(10 * self.T, dtype=np.int64)
+        """int64 [n_ens * 10 T] (see include/mbhlike.h) and the iteration counter."""
+        c = np.zeros(10 * self.n_ens * self.T, dtype=np.int64)
         step = C.c_uint64(0)
         _check(lib().mbh_pt_counters(self.handle, c.ctypes.data_as(C.POINTER(C.c_int64)),
                                      C.byref(step), _stream(stream)))
         return c, int(step.value)
 
-    def best(self, temp: int = 0, stream=None) -> tuple[np.ndarray, np.ndarray]:
+    def best(self, temp: int = 0, ensemble: int = 0, stream=None) -> tuple[np.ndarray, np.ndarray]:
         x, o = np.zeros(11), np.zeros(3)
-        _check(lib().mbh_pt_best(self.handle, int(temp), x.ctypes.data_as(dp), o.ctypes.data_as(dp),
-                                 _stream(stream)))
+        _check(lib().mbh_pt_best_at(self.handle, int(ensemble), int(temp), x.ctypes.data_as(dp),
+                                    o.ctypes.data_as(dp), _stream(stream)))
         return x, o
 
     def close(self):

@@ -251,3 +251,65 @@ def test_pt_fused_half_steps_equal_separate_launches(M, WL, case):
     assert np.abs(ca - cb).sum() <= 4
     d = np.abs(oa[0] - ob[0])[same]
     assert d.max() < 1e-6 * np.abs(ob[0][same]).max() + 1e-6
+
+
+SEED_STEP = 0x9E3779B97F4A7C15
+
+
+def _ens_refs(M, oracle, c, n):
+    """n references around the case's source (the first at the ensemble centre)."""
+    th0 = c["x0"].copy()
+    th0[0], th0[6], th0[8] = math.exp(th0[0]), math.acos(th0[6]), math.asin(th0[8])
+    ths = [th0] + [I.perturb(th0, np.full((11, 1), 10.0 ** (-4 - e)) * (1 - 2 * (e % 2)))[:, 0]
+                   for e in range(1, n)]
+    refs_g = [M.het_prepare_reference(c["src"].data, th, 32) for th in ths]
+    refs_o = [oracle.het_prepare(th, c["g"], c["d_o"], c["S"], 32) for th in ths]
+    return refs_g, refs_o
+
+
+def test_pt_multi_ensemble_matches_oracle(M, WL, oracle, case):
+    """Three ensembles, one reference each, stepping together: ensemble e equals the oracle's
+    single-ensemble sampler with seed + e 0x9E3779B97F4A7C15 (float64; positions and counters
+    exactly)."""
+    c = case
+    n, T, W = 3, c["T"], c["W"]
+    refs_g, refs_o = _ens_refs(M, oracle, c, n)
+    xs = [I.draw_pt_ensemble(I.rng(68, e), c["x0"], T, W, c["scale"], c["lo"], c["hi"]) for e in range(n)]
+    pt = M.PTSampler(WL.to_dev(np.concatenate(xs, 1)), c["betas"], c["lo"], c["hi"], refs=refs_g,
+                     walkers=W, probs=PROBS, seed=7, precision="fp64")
+    pt.run(5)
+    xg = pt.state()[0].cpu().numpy()
+    cg, step = pt.counters()
+    assert step == 5
+    for e in range(n):
+        out0 = oracle.het_loglike(oracle.pt_theta(xs[e]), refs_o[e])
+        seed_e = (7 + e * SEED_STEP) % (1 << 64)
+        xo, _, co = oracle.pt_run_het(xs[e], out0, T, W, c["betas"], c["lo"], c["hi"], PROBS, 2.0,
+                                      seed_e, 0, 5, refs_o[e])
+        assert np.array_equal(xg[:, e * T * W:(e + 1) * T * W], xo), e
+        assert np.array_equal(cg[e * 10 * T:(e + 1) * 10 * T], co), e
+    xb, ob = pt.best(0, ensemble=2)
+    og = pt.state()[1].cpu().numpy()[0, 2 * T * W:2 * T * W + W]
+    assert ob[0] == og.max()
+
+
+def test_pt_multi_ensemble_fused_equals_alone(M, WL, oracle, case):
+    """Mixed precision, fused half steps: each ensemble of a joint run is bit-identical to the
+    same ensemble run alone (its seed, its walkers, its reference)."""
+    c = case
+    n, T, W = 3, c["T"], c["W"]
+    refs_g, _ = _ens_refs(M, oracle, c, n)
+    xs = [I.draw_pt_ensemble(I.rng(69, e), c["x0"], T, W, c["scale"], c["lo"], c["hi"]) for e in range(n)]
+    pt = M.PTSampler(WL.to_dev(np.concatenate(xs, 1)), c["betas"], c["lo"], c["hi"], refs=refs_g,
+                     walkers=W, probs=PROBS, seed=9, precision="mixed")
+    pt.run(3)
+    xg = pt.state()[0].cpu().numpy()
+    cg, _ = pt.counters()
+    for e in range(n):
+        one = M.PTSampler(WL.to_dev(xs[e]), c["betas"], c["lo"], c["hi"], ref=refs_g[e], walkers=W,
+                          probs=PROBS, seed=(9 + e * SEED_STEP) % (1 << 64), precision="mixed")
+        one.run(3)
+        x1 = one.state()[0].cpu().numpy()
+        c1, _ = one.counters()
+        assert np.array_equal(xg[:, e * T * W:(e + 1) * T * W], x1), e
+        assert np.array_equal(cg[e * 10 * T:(e + 1) * 10 * T], c1), e
