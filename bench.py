@@ -74,11 +74,13 @@ def fp64_peak_gflops(sm_mhz: float) -> float:
 
 
 # The mixed heterodyne kernel is bound by the float32 (FMA) pipe: per edge evaluation it
-# issues 1279 FMA-pipe thread instructions (double-float phase chain, float32 response,
-# ratio and contraction), counted by ncu on het_mixed_kernel<8,128> (FMA-pipe utilisation x
-# peak x elapsed cycles / edges).  Peak: 148 SMs x 128 FP32 lanes x SM clock.
-HET_MIXED_FMA_INST_PER_EDGE = 1279
-HET_MIXED_DRAM_BYTES = 1.57824e6           # read + write per 16384-walker launch (ncu)
+# issues 1296 FMA-pipe thread instructions (double-float phase chain, float32 response,
+# ratio and contraction), counted by ncu on het_mixed_kernel_capped<8,224>, the default launch
+# at 16384 walkers (FMA-pipe utilisation x peak x elapsed cycles / edges).  Peak: 148 SMs x 128
+# FP32 lanes x SM clock.
+HET_MIXED_FMA_INST_PER_EDGE = 1296
+HET_KERNEL = "het_mixed_kernel_capped<8,224>"
+HET_MIXED_DRAM_BYTES = 1.570304e6          # read + write per 16384-walker launch (ncu)
 STORED_DATA_BYTES = 75.74e6                # data pairs, read once per launch (ncu: 883.66 MB
 STORED_BYTES_PER_TEMPLATE = 50.4945e6      # for 16 templates = 75.74 MB + 16 x 50.49 MB)
 
@@ -392,7 +394,7 @@ def run_ours(args) -> dict | None:
     E = ref.bins
     inst = nw * (E + 1) * HET_MIXED_FMA_INST_PER_EDGE
     achieved = inst / (ms_per_step * 1e-3) / 1e12
-    # DRAM traffic per launch from ncu captures (profiles/het_mixed_kernel_16384w_256b_1yr.md,
+    # DRAM traffic per launch from ncu captures (profiles/het_mixed_kernel_capped_16384w_256b_1yr.md,
     # profiles/direct_stored_df_kernel_16tpl_1yr.md; the stored-template launch scaled from
     # 16 to N_STORED templates by the templates processed)
     roof_traffic = HET_MIXED_DRAM_BYTES if nw == N_WALKERS else None
@@ -438,7 +440,7 @@ def run_ours(args) -> dict | None:
         "serving": serving,
         "roofline": {"bound": "alu", "pipe": "fp32 (FMA pipe)", "achieved": achieved, "peak": fma_peak,
                      "unit": "T fp32-pipe inst/s", "frac": achieved / fma_peak, "traffic": roof_traffic,
-                     "kernel": "het_mixed_kernel<8,128>",
+                     "kernel": HET_KERNEL,
                      "peak_note": f"148 SM x 128 FP32 lanes x {sm_for_peak:.0f} MHz",
                      "inst_per_edge": HET_MIXED_FMA_INST_PER_EDGE},
         "roofline_direct_stored": {"bound": "hbm", "achieved": stored_gbs, "peak": peaks["hbm_gbs"],
@@ -532,7 +534,7 @@ def run_sampler(M, WL, g, src, ref, stream, het_rate: float, iters: int = 20) ->
     x = WL.to_dev(I.draw_pt_ensemble(I.rng(2, 300), x0, T, W, scale, lo, hi))
     betas = I.pt_betas(T, 100.0)
     res = {}
-    for name, cfg in (("default", None), ("threads_per_walker_16", M.het_config(16, 128, 0))):
+    for name, cfg in (("default", None), ("threads_per_walker_8_block_128", M.het_config(8, 128, 0))):
         pt = M.PTSampler(x, betas, lo, hi, ref=ref, walkers=W, seed=1, precision="mixed", cfg=cfg)
         pt.run(3)
         torch.cuda.synchronize()

@@ -190,7 +190,15 @@ MBH_API mbh_status mbh_selftest_math(int32_t kind, const float* x_dev, const flo
 /* Launch configuration of the heterodyne kernels.  A walker is handled by
  * threads_per_walker threads (1, 2, 4, 8, 16 or 32) that deal its bin edges
  * round-robin (each round covers threads_per_walker bins); a block of `block`
- * threads (64, 128 or 256) holds block/threads_per_walker walkers of one source.
+ * threads holds block/threads_per_walker walkers of one source.  Every kernel has
+ * blocks of 64, 128 and 256 threads; the mixed-precision (2,2) kernels (and the
+ * fused sampler half step) also 224 for 4, 8 or 16 threads per walker, 96 and 160
+ * for 4 or 8, and 32 for 2 or 4, compiled for ~28 resident warps per SM (72
+ * registers); a (threads_per_walker, block) pair without a kernel is rejected
+ * (MBH_EINVAL).  block = 0 takes the default: 224 for the mixed (2,2) kernels at 4,
+ * 8 or 16 threads per walker when the launch has at least 3 x (SMs) blocks of 224
+ * threads' worth of walkers (16384 walkers at 8 threads per walker on 148 SMs),
+ * else 128.
  * persistent = 0: one block per walker tile; 1: a grid of (SMs x resident blocks)
  * looping over the tiles, sources ordered by bin count (largest first).  For a
  * given threads_per_walker the results are bitwise reproducible and independent of
@@ -384,7 +392,9 @@ typedef struct {
     double lo[11], hi[11];   /* prior box in x */
     uint64_t seed;
     mbh_precision precision;           /* of the likelihood */
-    mbh_het_config het_config;         /* threads_per_walker 0 = default */
+    mbh_het_config het_config;         /* threads_per_walker 0 = default: 16 threads per walker
+                                          when a half step moves <= 12288 walkers (mixed
+                                          precision), else 8; block 0 = default */
     uint32_t modes;                    /* direct likelihood: harmonic mode mask (0 = (2,2));
                                           a reference brings its own */
     double adapt_time;                 /* > 0: adapt the ladder every iteration (Vousden et

@@ -33,14 +33,23 @@ def _stale() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile every source to an object in parallel (one nvcc per file), then link."""
     if not force and not _stale():
         return LIB
-    cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden",
-           "-shared", "-I", INCLUDE, "--expt-relaxed-constexpr", "-o", LIB + ".tmp", *sources(),
-           "-lcudart"]
+    objdir = os.path.join(HERE, "_build")
+    os.makedirs(objdir, exist_ok=True)
+    flags = [*ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden",
+             "-I", INCLUDE, "--expt-relaxed-constexpr"]
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    subprocess.check_call(cmd)
+        flags.insert(0, "-Xptxas=-v")
+    jobs = []
+    for src in sources():
+        obj = os.path.join(objdir, os.path.basename(src) + ".o")
+        jobs.append((obj, subprocess.Popen([NVCC, *flags, "-c", src, "-o", obj])))
+    failed = [obj for obj, p in jobs if p.wait() != 0]
+    if failed:
+        raise subprocess.CalledProcessError(1, f"nvcc ({', '.join(map(os.path.basename, failed))})")
+    subprocess.check_call([NVCC, *ARCH, "-shared", "-o", LIB + ".tmp", *[o for o, _ in jobs], "-lcudart"])
     os.replace(LIB + ".tmp", LIB)
     return LIB
 

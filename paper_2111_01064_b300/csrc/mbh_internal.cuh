@@ -13,6 +13,10 @@ namespace mbh {
 
 constexpr int kMaxBins = 4096;
 constexpr int kMaxSrc = 96;   // sources per launch (descriptors travel as kernel parameters)
+// default heterodyne blocks (mbh_het_config.block = 0): 224 threads for the mixed (2,2) kernels
+// on large batches (the register-capped kernels, 28 resident warps per SM), 128 otherwise
+constexpr int kDefaultBlockMixed = 224;
+constexpr int kDefaultBlock = 128;
 
 // Edge record of the mixed-precision heterodyne: the frequency tables that make the
 // double-float phase chain free of cbrt/log (f, f^{1/3}, f^{-1/3}, ln f / 3 as float pairs),

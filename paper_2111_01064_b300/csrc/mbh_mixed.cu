@@ -186,9 +186,13 @@ __device__ __forceinline__ f2 split_d(double x)
     return {hi, (float)(x - (double)hi)};
 }
 
-// v and ln v at f_max: pi M f_max = 0.05 pi sqrt(5/12) for every mass (f_max = f_c sqrt(5/12),
-// f_c = 0.05/M), so v(f_max) = (0.05 pi sqrt(5/12))^{1/3} is a constant.
-constexpr double kPiMfmax = 0.10139446689934029;   // 0.05 pi sqrt(5/12)
+// v and ln v at f_max: pi M f_max = 0.05 pi sqrt(5/12) = 0.1013944668993403 for every mass
+// (f_max = f_c sqrt(5/12), f_c = 0.05/M), so v(f_max) = (pi M f_max)^{1/3}, ln v(f_max), v^-5
+// and v^-8 are constants (evaluated to 40 digits, then rounded).
+constexpr double kVm = 0.4663064457284195;
+constexpr double kLnVm = -0.7629122521271803;
+constexpr double kVmPow5Inv = 45.35685218040481;
+constexpr double kVmPow8Inv = 447.3306440422728;
 
 // Per-walker constants of the mixed path (Sec. II A parameter derivation), in float64: the
 // large-phase constants (PN coefficients, the v and ln v scales, t_ref and the f_max
@@ -206,10 +210,13 @@ __device__ inline void walker_setup_mixed(const double* __restrict__ theta, int6
     const double dl = theta[kDL * W + i], phi = theta[kPhi * W + i];
     const double iota = theta[kIota * W + i], pol = theta[kPsi * W + i];
 
+    // few float64 divisions and transcendentals: on this path they cost 16 cycles of the SM's
+    // float64 pipe per warp instruction, and the setup runs in every block before its edges
     const double opq = 1.0 + q;
-    const double eta = q / (opq * opq);
-    const double x1 = 1.0 / opq, x2 = q / opq;
+    const double x1 = 1.0 / opq, x2 = q * x1;
+    const double eta = x1 * x2;
     const double M = mt * kMsunSec;
+    const double iM = 1.0 / M;
     const double so = (113.0 / 12.0 * x1 * x1 + 25.0 / 4.0 * eta) * a1 +
                       (113.0 / 12.0 * x2 * x2 + 25.0 / 4.0 * eta) * a2;
     const double ss = 79.0 / 8.0 * eta * a1 * a2;
@@ -228,7 +235,7 @@ __device__ inline void walker_setup_mixed(const double* __restrict__ theta, int6
             127825.0 / 1296.0 * eta * eta * eta;
     const double alog6 = -6848.0 / 21.0;
     al[7] = kPi * (77096675.0 / 254016.0 + 378515.0 / 1512.0 * eta - 74045.0 / 756.0 * eta * eta);
-    const double pre = 3.0 / (128.0 * eta), dpre = kPi * M / (128.0 * eta);
+    const double pre = 3.0 / (128.0 * eta), dpre = pre * (kPi / 3.0) * M;
     double c[8], d[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
@@ -239,18 +246,17 @@ __device__ inline void walker_setup_mixed(const double* __restrict__ theta, int6
     d[6] += dpre * alog6;
     const double cl5 = pre * alog5, cl6 = pre * alog6, dl6 = dpre * alog6;
     // Psi_PN and its derivative at f_max (v = constant)
-    const double vm = cbrt(kPiMfmax), lvm = log(vm);
     double P = c[7], Q = d[7];
 #pragma unroll
     for (int k = 6; k >= 0; --k) {
-        P = fma(P, vm, c[k]);
-        Q = fma(Q, vm, d[k]);
+        P = fma(P, kVm, c[k]);
+        Q = fma(Q, kVm, d[k]);
     }
-    const double vm2 = vm * vm, vm5 = vm2 * vm2 * vm, vm6 = vm5 * vm, vm8 = vm6 * vm2;
-    const double psi_max = (P + lvm * (cl5 * vm5 + cl6 * vm6)) / vm5;
-    const double dpsi_max = (Q + lvm * dl6 * vm6) / vm8;
+    constexpr double vm5 = kVm * kVm * kVm * kVm * kVm, vm6 = vm5 * kVm;
+    const double psi_max = (P + kLnVm * (cl5 * vm5 + cl6 * vm6)) * kVmPow5Inv;
+    const double dpsi_max = (Q + kLnVm * dl6 * vm6) * kVmPow8Inv;
     const double piM = kPi * M;
-    const double cb = cbrt(piM);
+    const double icb = rcbrt(piM), cb = piM * icb * icb;
     double sa, ca, sl, cl, sb, cbt;
     sincos(kTwoPi * tref / kYear, &sa, &ca);
     sincos(lam, &sl, &cl);
@@ -264,11 +270,11 @@ __device__ inline void walker_setup_mixed(const double* __restrict__ theta, int6
     m.cl6 = split_f64(cl6, 0);
     m.dl6 = split_f64(dl6, 0);
     m.cbrt_piM = split_f64(cb, 0);
-    m.icbrt_piM = split_f64(1.0 / cb, 0);
+    m.icbrt_piM = split_f64(icb, 0);
     m.ln_cbrt_piM = split_f64(log(piM) / 3.0, 0);
     m.tref = split_f64(tref, 0);
-    m.fmax = split_f64(0.05 * 0.6454972243679028 / M, 0);   // f_c sqrt(5/12)
-    m.fcut = split_f64(0.2 / M, 0);
+    m.fmax = split_f64((0.05 * 0.6454972243679028) * iM, 0);   // f_c sqrt(5/12)
+    m.fcut = split_f64(0.2 * iM, 0);
     m.psi_max = split_f64(psi_max, 0);
     m.dpsi_max = split_f64(dpsi_max, 0);
     m.sa_ref = split_f64(sa, 0);
@@ -283,8 +289,7 @@ __device__ inline void walker_setup_mixed(const double* __restrict__ theta, int6
     //   = pi sqrt(2/3) M^2 sqrt(eta) / D v^{-7/2} exp(-(f/fc)^2)
     const double dist = (double)dl * (1e9 * kParsec / kClight);
     wf.amp = (float)(kPi * 0.816496580927726 /* sqrt(2/3) */ * M * M * sqrt(eta) / dist);
-    const double fc = 0.05 / M;
-    wf.inv_fc2 = (float)(1.0 / (fc * fc));
+    wf.inv_fc2 = (float)(400.0 * M * M);   // 1/f_c^2, f_c = 0.05/M
     wf.sa_ref = (float)sa;
     wf.ca_ref = (float)ca;
     double s2p, c2p, s2f, c2f;
@@ -883,9 +888,13 @@ cudaError_t mbh::prepare_mixed_tables(mbh_ref* R, cudaStream_t st)
 // ------------------------------------------------------------------------------------------
 // heterodyne likelihood, mixed precision
 // ------------------------------------------------------------------------------------------
+// Each heterodyne kernel comes in two register budgets: het_*_kernel (power-of-two blocks)
+// leaves the register count to the compiler (~96-118), het_*_kernel_capped (blocks of 96,
+// 160, 224) is compiled for about 28 resident warps per SM (72 registers, a few bytes spilled):
+// at 8 threads per walker 16384 walkers then fit in one wave (586 blocks of 224 threads on
+// 148 x 4 slots) instead of the 1.4 waves that 96 registers allow.
 template <int G, int BLOCK>
-__global__ void __launch_bounds__(BLOCK)
-    het_mixed_kernel(const __grid_constant__ HetLaunch L)
+__device__ __forceinline__ void het_mixed_body(const HetLaunch& L)
 {
     constexpr int WPB = BLOCK / G;
     __shared__ WalkerDF wsd[WPB];
@@ -977,6 +986,18 @@ __global__ void __launch_bounds__(BLOCK)
     }
 }
 
+
+template <int G, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) het_mixed_kernel(const __grid_constant__ HetLaunch L)
+{
+    het_mixed_body<G, BLOCK>(L);
+}
+
+template <int G, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 896 / BLOCK) het_mixed_kernel_capped(const __grid_constant__ HetLaunch L)
+{
+    het_mixed_body<G, BLOCK>(L);
+}
 
 // Higher-mode heterodyne (Sec. II B with the template of Eq. 9 summed over modes before the
 // ratio), mixed precision; layout and reductions as het_mixed_kernel, delta from the
@@ -1093,8 +1114,7 @@ __global__ void __launch_bounds__(BLOCK)
 // het_mixed_kernel's; the epilogue applies the tempered acceptance (pt::accept_test) and
 // updates the state and counters.  Walker index w = the half step's item t W/2 + k'.
 template <int G, int BLOCK>
-__global__ void __launch_bounds__(BLOCK)
-    het_mixed_pt_kernel(const __grid_constant__ HetLaunch L)
+__device__ __forceinline__ void het_mixed_pt_body(const HetLaunch& L)
 {
     constexpr int WPB = BLOCK / G;
     __shared__ WalkerDF wsd[WPB];
@@ -1211,12 +1231,45 @@ __global__ void __launch_bounds__(BLOCK)
     }
 }
 
+template <int G, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) het_mixed_pt_kernel(const __grid_constant__ HetLaunch L)
+{
+    het_mixed_pt_body<G, BLOCK>(L);
+}
+
+template <int G, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 896 / BLOCK) het_mixed_pt_kernel_capped(const __grid_constant__ HetLaunch L)
+{
+    het_mixed_pt_body<G, BLOCK>(L);
+}
+
 namespace {
 template <int G, int BLOCK>
 cudaError_t launch_het_mixed(const HetLaunch& L, int grid, cudaStream_t st)
 {
-    het_mixed_kernel<G, BLOCK><<<grid, BLOCK, 0, st>>>(L);
+    if constexpr (BLOCK % 64 == 0)
+        het_mixed_kernel<G, BLOCK><<<grid, BLOCK, 0, st>>>(L);
+    else
+        het_mixed_kernel_capped<G, BLOCK><<<grid, BLOCK, 0, st>>>(L);
     return cudaGetLastError();
+}
+
+template <int G, int BLOCK>
+const void* het_mixed_fn()
+{
+    if constexpr (BLOCK % 64 == 0)
+        return (const void*)&het_mixed_kernel<G, BLOCK>;
+    else
+        return (const void*)&het_mixed_kernel_capped<G, BLOCK>;
+}
+
+template <int G, int BLOCK>
+const void* het_mixed_pt_fn()
+{
+    if constexpr (BLOCK % 64 == 0)
+        return (const void*)&het_mixed_pt_kernel<G, BLOCK>;
+    else
+        return (const void*)&het_mixed_pt_kernel_capped<G, BLOCK>;
 }
 
 template <int G, int BLOCK>
@@ -1229,7 +1282,10 @@ cudaError_t launch_het_mixed_hm(const HetLaunch& L, int grid, cudaStream_t st)
 template <int G, int BLOCK>
 cudaError_t launch_het_mixed_pt(const HetLaunch& L, int grid, cudaStream_t st)
 {
-    het_mixed_pt_kernel<G, BLOCK><<<grid, BLOCK, 0, st>>>(L);
+    if constexpr (BLOCK % 64 == 0)
+        het_mixed_pt_kernel<G, BLOCK><<<grid, BLOCK, 0, st>>>(L);
+    else
+        het_mixed_pt_kernel_capped<G, BLOCK><<<grid, BLOCK, 0, st>>>(L);
     return cudaGetLastError();
 }
 }  // namespace
@@ -1238,12 +1294,13 @@ namespace mbh {
 HetKernel het_kernel_mixed(int G, int block)
 {
 #define MBH_CASE(g, b) \
-    if (G == g && block == b) return {&launch_het_mixed<g, b>, (const void*)&het_mixed_kernel<g, b>};
+    if (G == g && block == b) return {&launch_het_mixed<g, b>, het_mixed_fn<g, b>()};
     MBH_CASE(1, 64) MBH_CASE(1, 128) MBH_CASE(1, 256)
-    MBH_CASE(2, 64) MBH_CASE(2, 128) MBH_CASE(2, 256)
-    MBH_CASE(4, 64) MBH_CASE(4, 128) MBH_CASE(4, 256)
-    MBH_CASE(8, 64) MBH_CASE(8, 128) MBH_CASE(8, 256)
-    MBH_CASE(16, 64) MBH_CASE(16, 128) MBH_CASE(16, 256)
+    MBH_CASE(2, 32) MBH_CASE(2, 64) MBH_CASE(2, 128) MBH_CASE(2, 256)
+    MBH_CASE(4, 32) MBH_CASE(4, 64) MBH_CASE(4, 96) MBH_CASE(4, 128) MBH_CASE(4, 160) MBH_CASE(4, 224)
+    MBH_CASE(4, 256)
+    MBH_CASE(8, 64) MBH_CASE(8, 96) MBH_CASE(8, 128) MBH_CASE(8, 160) MBH_CASE(8, 224) MBH_CASE(8, 256)
+    MBH_CASE(16, 64) MBH_CASE(16, 128) MBH_CASE(16, 224) MBH_CASE(16, 256)
     MBH_CASE(32, 64) MBH_CASE(32, 128) MBH_CASE(32, 256)
 #undef MBH_CASE
     return {nullptr, nullptr};
@@ -1270,12 +1327,13 @@ namespace mbh {
 HetKernel het_kernel_mixed_pt(int G, int block)
 {
 #define MBH_CASE(g, b) \
-    if (G == g && block == b) return {&launch_het_mixed_pt<g, b>, (const void*)&het_mixed_pt_kernel<g, b>};
+    if (G == g && block == b) return {&launch_het_mixed_pt<g, b>, het_mixed_pt_fn<g, b>()};
     MBH_CASE(1, 64) MBH_CASE(1, 128) MBH_CASE(1, 256)
-    MBH_CASE(2, 64) MBH_CASE(2, 128) MBH_CASE(2, 256)
-    MBH_CASE(4, 64) MBH_CASE(4, 128) MBH_CASE(4, 256)
-    MBH_CASE(8, 64) MBH_CASE(8, 128) MBH_CASE(8, 256)
-    MBH_CASE(16, 64) MBH_CASE(16, 128) MBH_CASE(16, 256)
+    MBH_CASE(2, 32) MBH_CASE(2, 64) MBH_CASE(2, 128) MBH_CASE(2, 256)
+    MBH_CASE(4, 32) MBH_CASE(4, 64) MBH_CASE(4, 96) MBH_CASE(4, 128) MBH_CASE(4, 160) MBH_CASE(4, 224)
+    MBH_CASE(4, 256)
+    MBH_CASE(8, 64) MBH_CASE(8, 96) MBH_CASE(8, 128) MBH_CASE(8, 160) MBH_CASE(8, 224) MBH_CASE(8, 256)
+    MBH_CASE(16, 64) MBH_CASE(16, 128) MBH_CASE(16, 224) MBH_CASE(16, 256)
     MBH_CASE(32, 64) MBH_CASE(32, 128) MBH_CASE(32, 256)
 #undef MBH_CASE
     return {nullptr, nullptr};

@@ -361,7 +361,7 @@ struct mbh_pt {
     mbh_precision precision = MBH_MIXED;
     std::vector<const mbh_ref*> refs;   // one per ensemble (heterodyned likelihood)
     const mbh_data* data = nullptr;      // or the data of the direct likelihood
-    mbh_het_config cfg{8, 128, 0};
+    mbh_het_config cfg{8, 0, 0};
     uint32_t modes = 1u;     // direct likelihood: harmonic modes of the templates
     bool fused = false;      // half steps as one fused heterodyne launch each
     bool fuse_ok = false;    // the caller allows fusion (mixed precision, not opted out)
@@ -571,6 +571,11 @@ extern "C" mbh_status mbh_pt_create_multi(const mbh_pt_opts* o, const mbh_ref* c
     P->Wp = 1;
     while (P->Wp < A.W) P->Wp <<= 1;
     const int64_t N = (int64_t)n_ens * A.T * A.W, M = N / 2;
+    // default launch shape of the mixed-precision half steps: enough threads per walker for
+    // about one wave of the register-capped 224-thread blocks (28 warps per SM): 16 threads per
+    // walker up to 12288 moving walkers, 8 above (threads per walker fixes the summation order,
+    // so a sampler keeps the one it was created with)
+    if (!o->het_config.threads_per_walker && P->precision == MBH_MIXED) P->cfg.threads_per_walker = M <= 12288 ? 16 : 8;
     const int64_t NT = (int64_t)n_ens * A.T;
     cudaError_t e = cudaSuccess;
     auto alloc = [&](void** p, size_t bytes) {

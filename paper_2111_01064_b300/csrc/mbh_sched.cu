@@ -38,8 +38,9 @@ mbh_status check_cfg(const mbh_het_config& c)
     const int g = c.threads_per_walker;
     if (!(g == 1 || g == 2 || g == 4 || g == 8 || g == 16 || g == 32))
         return fail(MBH_EINVAL, "threads_per_walker %d not in {1,2,4,8,16,32}", g);
-    if (!(c.block == 64 || c.block == 128 || c.block == 256))
-        return fail(MBH_EINVAL, "block %d not in {64,128,256}", c.block);
+    if (c.block != 0 && (c.block < 32 || c.block > 256 || c.block % 32 != 0 || c.block < g))
+        return fail(MBH_EINVAL, "block %d not 0 or a multiple of 32 in [32, 256] (and >= threads_per_walker)",
+                    c.block);
     return MBH_OK;
 }
 
@@ -61,21 +62,30 @@ mbh_status check_het_args(const mbh_ref* const* refs, const int64_t* offsets, in
     return MBH_OK;
 }
 
+// Default block (mbh_het_config.block = 0) of the mixed-precision (2,2) kernels for a launch of
+// W walkers: 224 threads (the register-capped kernel, 4 blocks of 7 warps per SM) once its
+// tiles fill three quarters of such a wave, else 128 (no register cap; below that the capped
+// kernel's spills cost more than its occupancy gains).  4, 8 and 16 threads per walker.
+int default_block_mixed(int G, int64_t W)
+{
+    if (G != 4 && G != 8 && G != 16) return kDefaultBlock;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return kDefaultBlock;
+    const int64_t wpb = kDefaultBlockMixed / G;
+    const int64_t tiles = (W + wpb - 1) / wpb;
+    return 4 * tiles >= 3 * 4 * (int64_t)sms ? kDefaultBlockMixed : kDefaultBlock;
+}
+
 mbh_status make_plan(const mbh_ref* const* refs, const int64_t* offsets, int32_t n_src,
                      const double* theta, double* out, mbh_precision prec,
                      const mbh_het_config& cfg, HetPlan& plan)
 {
     if (mbh_status s = check_cfg(cfg)) return s;
     if (prec != MBH_FP64 && prec != MBH_MIXED) return fail(MBH_EINVAL, "unknown precision %d", (int)prec);
-    const int wpb = cfg.block / cfg.threads_per_walker;
     const int64_t W = offsets[n_src];
     // kernel per source: float64 (any modes), mixed (2,2), or mixed with higher modes;
-    // a launch holds sources of one kernel
-    auto kernel_of = [&](int32_t s) {
-        if (prec == MBH_FP64) return het_kernel_f64(cfg.threads_per_walker, cfg.block);
-        return refs[s]->modes == 1u ? het_kernel_mixed(cfg.threads_per_walker, cfg.block)
-                                    : het_kernel_mixed_hm(cfg.threads_per_walker, cfg.block);
-    };
+    // a launch holds sources of one kernel.  block 0 takes each kernel's default block.
     for (int group = 0; group < 2; ++group) {
         std::vector<int32_t> order;
         for (int32_t s = 0; s < n_src; ++s) {
@@ -83,7 +93,15 @@ mbh_status make_plan(const mbh_ref* const* refs, const int64_t* offsets, int32_t
             if ((group == 1) == hm) order.push_back(s);
         }
         if (order.empty()) continue;
-        const HetKernel kernel = kernel_of(order[0]);
+        const bool mixed22 = prec == MBH_MIXED && group == 0;
+        int64_t wg = 0;
+        for (int32_t s : order) wg += offsets[s + 1] - offsets[s];
+        const int block = cfg.block ? cfg.block
+                                    : (mixed22 ? default_block_mixed(cfg.threads_per_walker, wg) : kDefaultBlock);
+        const int wpb = block / cfg.threads_per_walker;
+        const HetKernel kernel = prec == MBH_FP64 ? het_kernel_f64(cfg.threads_per_walker, block)
+                                 : mixed22        ? het_kernel_mixed(cfg.threads_per_walker, block)
+                                                  : het_kernel_mixed_hm(cfg.threads_per_walker, block);
         if (!kernel.launch) return fail(MBH_EINVAL, "no kernel for this configuration");
         if (cfg.persistent)   // largest bin counts first
             std::stable_sort(order.begin(), order.end(),
@@ -94,7 +112,7 @@ mbh_status make_plan(const mbh_ref* const* refs, const int64_t* offsets, int32_t
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
             int per_sm = 0;
-            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel.fn, cfg.block, 0);
+            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel.fn, block, 0);
             if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
             resident = std::max(1, per_sm) * sms;
         }
@@ -152,10 +170,22 @@ mbh_status run_plan(const HetPlan& plan, cudaStream_t st)
     return MBH_OK;
 }
 
+// every kernel kind the batch needs exists for this (threads_per_walker, block)
+bool plan_has_kernels(const mbh_ref* const* refs, int32_t n_src, mbh_precision prec, const mbh_het_config& c)
+{
+    for (int32_t s = 0; s < n_src; ++s) {
+        const HetKernel k = prec == MBH_FP64          ? het_kernel_f64(c.threads_per_walker, c.block)
+                            : refs[s]->modes == 1u ? het_kernel_mixed(c.threads_per_walker, c.block)
+                                                   : het_kernel_mixed_hm(c.threads_per_walker, c.block);
+        if (!k.launch) return false;
+    }
+    return true;
+}
+
 mbh_het_config default_cfg(mbh_precision p)
 {
     (void)p;
-    return mbh_het_config{8, 128, 0};
+    return mbh_het_config{8, 0, 0};
 }
 
 }  // namespace
@@ -208,7 +238,7 @@ extern "C" mbh_status mbh_het_autotune(const mbh_ref* const* refs, const int64_t
     double best_t = INFINITY;
     mbh_het_config best_c = default_cfg(precision);
     const int gs[] = {1, 2, 4, 8, 16, 32};
-    const int bs[] = {64, 128, 256};
+    const int bs[] = {32, 64, 96, 128, 160, 224, 256};
     mbh_status status = MBH_OK;
     for (int g : gs)
         for (int b : bs)
@@ -217,6 +247,10 @@ extern "C" mbh_status mbh_het_autotune(const mbh_ref* const* refs, const int64_t
                 const mbh_het_config c{g, b, pers};
                 HetPlan plan;
                 status = make_plan(refs, offsets_host, n_sources, theta_dev, out_dev, precision, c, plan);
+                if (status == MBH_EINVAL && !plan_has_kernels(refs, n_sources, precision, c)) {
+                    status = MBH_OK;   // no kernel compiled for this pair: not a candidate
+                    break;
+                }
                 if (status != MBH_OK) break;
                 status = run_plan(plan, st);   // warm-up
                 if (status != MBH_OK) break;
@@ -309,9 +343,10 @@ mbh_status het_launch_fused_pt(const mbh_ref* const* refs, int n_ens, int64_t M,
                                const void* pt_dev, int half, cudaStream_t st)
 {
     if (mbh_status s = check_cfg(cfg)) return s;
-    const HetKernel k = het_kernel_mixed_pt(cfg.threads_per_walker, cfg.block);
+    const int block = cfg.block ? cfg.block : default_block_mixed(cfg.threads_per_walker, M * n_ens);
+    const HetKernel k = het_kernel_mixed_pt(cfg.threads_per_walker, block);
     if (!k.launch) return fail(MBH_EINVAL, "no kernel for this configuration");
-    const int wpb = cfg.block / cfg.threads_per_walker;
+    const int wpb = block / cfg.threads_per_walker;
     std::unique_ptr<HetLaunch> L(new (std::nothrow) HetLaunch);
     if (!L) return fail(MBH_ENOMEM, "host allocation");
     int resident = 0;
@@ -319,7 +354,7 @@ mbh_status het_launch_fused_pt(const mbh_ref* const* refs, int n_ens, int64_t M,
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k.fn, cfg.block, 0) == cudaSuccess)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k.fn, block, 0) == cudaSuccess)
             resident = std::max(1, per_sm) * sms;
     }
     for (int first = 0; first < n_ens; first += kMaxSrc) {

@@ -33,7 +33,8 @@ class Grid(C.Structure):
 
 
 class HetConfig(C.Structure):
-    """mbh_het_config: threads per walker (1..32), block (64/128/256), persistent (0/1)."""
+    """mbh_het_config: threads per walker (1..32), block (0 = the kernel's default, or a
+    multiple of 32 up to 256 for which a kernel exists), persistent (0/1)."""
     _fields_ = [("threads_per_walker", C.c_int32), ("block", C.c_int32), ("persistent", C.c_int32)]
 
     def as_dict(self) -> dict:
@@ -41,7 +42,7 @@ class HetConfig(C.Structure):
                     persistent=self.persistent)
 
 
-def het_config(threads_per_walker=8, block=128, persistent=0) -> HetConfig:
+def het_config(threads_per_walker=8, block=0, persistent=0) -> HetConfig:
     return HetConfig(int(threads_per_walker), int(block), int(persistent))
 
 

@@ -35,10 +35,11 @@ def test_launch_configurations(M, batch, prec):
     th = torch.from_numpy(batch.theta).cuda()
     ref = M.het_loglike_batch(batch.refs, batch.offsets, th, prec).cpu().numpy()
     scale = np.abs(ref).max(axis=1, keepdims=True)
+    extra = {2: (32,), 4: (32, 96, 160, 224), 8: (96, 160, 224), 16: (224,)} if prec == "mixed" else {}
     for g in (1, 2, 4, 8, 16, 32):
         first = None
-        for b in (64, 128, 256):
-            if b < g:
+        for b in (0, 64, 128, 256) + extra.get(g, ()):
+            if 0 < b < g:
                 continue
             for pers in (0, 1):
                 out = M.het_loglike_batch_cfg(batch.refs, batch.offsets, th, prec,
@@ -123,5 +124,8 @@ def test_bad_configuration_rejected(M, batch):
     th = torch.from_numpy(batch.theta).cuda()
     with pytest.raises(M.MBHError):
         M.het_loglike_batch_cfg(batch.refs, batch.offsets, th, "mixed", M.het_config(3, 128, 0))
-    with pytest.raises(M.MBHError):
-        M.het_loglike_batch_cfg(batch.refs, batch.offsets, th, "mixed", M.het_config(8, 96, 0))
+    for g, b in ((8, 100), (8, 288), (32, 224), (16, 160), (32, 16)):
+        with pytest.raises(M.MBHError):
+            M.het_loglike_batch_cfg(batch.refs, batch.offsets, th, "mixed", M.het_config(g, b, 0))
+    with pytest.raises(M.MBHError):   # the float64 kernel has no 224-thread block
+        M.het_loglike_batch_cfg(batch.refs, batch.offsets, th, "fp64", M.het_config(8, 224, 0))
