@@ -149,9 +149,12 @@ __device__ inline void transfer_f32(const WalkerF& w, const float* Kp, const flo
         float sph, cph;
         sincos_small((float)kPi * f * (armS + ko), &sph, &cph);
         const cf g = fmul({-x * sph, -x * cph}, F);
-        yf[a] = fscale(g, sincf(x * (1.0f - kn)));
-        yb[a] = fscale(g, sincf(x * (1.0f + kn)));
-        tsum = fadd(tsum, fscale(g, sinc_diff(x, kn)));   // y_{j->i} - y_{i->j}
+        // sinc(x(1 + k.n)) = sinc(x(1 - k.n)) + the difference (which T needs on its own);
+        // the sum is off by at most an ulp of the larger term, like a direct evaluation
+        const float sm = sincf(x * (1.0f - kn)), sd = sinc_diff(x, kn);
+        yf[a] = fscale(g, sm);
+        yb[a] = fscale(g, sm + sd);
+        tsum = fadd(tsum, fscale(g, sd));   // y_{j->i} - y_{i->j}
     }
     const cf y12 = yf[0], y21 = yb[0], y23 = yf[1], y32 = yb[1], y31 = yf[2], y13 = yb[2];
     float s1, c1;

@@ -12,8 +12,10 @@
 //                      on a side stream forked at the start of the iteration, joined before the
 //                      first acceptance and before the swaps, so they overlap the half steps
 //   for each half h:   pt_propose_kernel -> likelihood of the T*W/2 proposals -> pt_accept_kernel
-//   pt_swap_kernel     the swap levels in order, hottest first (one block; the two temperatures
-//                      of a level are held in shared memory), then the step counter advances.
+//   pt_swap_kernel     the swap levels in order, hottest first (one block per ensemble; the two
+//                      temperatures of a level are held in shared memory, or every temperature
+//                      when T W (8 + 4) bytes fit: pt_swap_resident_kernel), then the step
+//                      counter advances.
 //
 // Layout: positions x[11][N] and (lnL, <d|h>, <h|h>) out[3][N] stay in physical columns; a map
 // slot -> column (slot = t W + k, walker k of temperature t) makes a swap an exchange of two
@@ -42,6 +44,9 @@ using namespace mbh::pt;
 constexpr int kThreads = 256;      // rescoring and gathers
 constexpr int kStepThreads = 32;   // propose/accept: 8192 walkers -> 256 blocks over all SMs
 constexpr int kSortThreads = 1024;
+// shared memory of pt_swap_resident_kernel: all T x W lnL and map entries (8 x 2048 walkers
+// need 192 KiB), leaving room for the static arrays under the 227 KiB limit
+constexpr size_t kSwapResidentBytes = 200 * 1024;
 
 // ---- kernels -------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kStepThreads) pt_propose_kernel(const PtArgs A, int half)
@@ -145,6 +150,36 @@ __global__ void __launch_bounds__(kSortThreads) pt_perm_kernel(const PtArgs A, i
         A.perm[((int64_t)e * A.T + i) * A.W + k] = (int32_t)(keys[k] & 0xFFFFull);
 }
 
+// After the swap levels (thread 0 of an ensemble's block): ladder adaptation from this
+// iteration's swap acceptances, then the last ensemble block to finish advances the step.
+__device__ void swap_epilogue(const PtArgs& A, double* betas, const unsigned int* acc_now, uint64_t step)
+{
+    const int T = A.T, W = A.W;
+    // ladder adaptation (Vousden, Farr & Mandel 2016): S_t = ln(T_t - T_{t-1}) moves by
+    // kappa (A_t - A_{t+1}), kappa = (1/nu) n0/(n + n0); coldest and hottest fixed
+    if (A.adapt_nu > 0.0 && T >= 3) {
+        const double kappa = __ddiv_rn(__dmul_rn(__ddiv_rn(1.0, A.adapt_nu), A.adapt_n0),
+                                       __dadd_rn((double)step, A.adapt_n0));
+        double Tt[kMaxTemps], S[kMaxTemps];
+        for (int t = 0; t < T; ++t) Tt[t] = __ddiv_rn(1.0, betas[t]);
+        for (int t = 1; t <= T - 2; ++t) {
+            const double a0 = __ddiv_rn((double)acc_now[t], (double)W);
+            const double a1 = __ddiv_rn((double)acc_now[t + 1], (double)W);
+            S[t] = __dadd_rn(log(__dsub_rn(Tt[t], Tt[t - 1])), __dmul_rn(kappa, __dsub_rn(a0, a1)));
+        }
+        for (int t = 1; t <= T - 2; ++t) {
+            Tt[t] = __dadd_rn(Tt[t - 1], exp(S[t]));
+            betas[t] = __ddiv_rn(1.0, Tt[t]);
+        }
+    }
+    // the last ensemble block to finish advances the step: every block has read it by then
+    __threadfence();
+    if (atomicAdd(A.done, 1u) == (unsigned int)(A.n_ens - 1)) {
+        *A.done = 0u;
+        *A.step = step + 1;
+    }
+}
+
 // Swap levels in order, hottest first; the hot and cold temperatures of a level are held in
 // shared memory (lnL and map entries).  Thread t handles walkers k = t + j blockDim (j < J);
 // while level i is decided, the next level's inputs (the colder temperature's map entries and
@@ -166,7 +201,6 @@ __global__ void __launch_bounds__(kSortThreads) pt_swap_kernel(const PtArgs A)
     int32_t* mp = reinterpret_cast<int32_t*>(sm + 2 * W);   // [2][W]
     __shared__ unsigned int acc_level;
     __shared__ unsigned int acc_now[kMaxTemps];
-    __shared__ bool last;
     const uint64_t step = *A.step;
     if (T > 1) {
         int32_t pm[J], pp[J];
@@ -248,32 +282,95 @@ __global__ void __launch_bounds__(kSortThreads) pt_swap_kernel(const PtArgs A)
         for (int k = threadIdx.x; k < W; k += blockDim.x) map[k] = mp[hot * W + k];
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        // ladder adaptation (Vousden, Farr & Mandel 2016): S_t = ln(T_t - T_{t-1}) moves by
-        // kappa (A_t - A_{t+1}), kappa = (1/nu) n0/(n + n0); coldest and hottest fixed
-        if (A.adapt_nu > 0.0 && T >= 3) {
-            const double kappa = __ddiv_rn(__dmul_rn(__ddiv_rn(1.0, A.adapt_nu), A.adapt_n0),
-                                           __dadd_rn((double)step, A.adapt_n0));
-            double Tt[kMaxTemps], S[kMaxTemps];
-            for (int t = 0; t < T; ++t) Tt[t] = __ddiv_rn(1.0, betas[t]);
-            for (int t = 1; t <= T - 2; ++t) {
-                const double a0 = __ddiv_rn((double)acc_now[t], (double)W);
-                const double a1 = __ddiv_rn((double)acc_now[t + 1], (double)W);
-                S[t] = __dadd_rn(log(__dsub_rn(Tt[t], Tt[t - 1])), __dmul_rn(kappa, __dsub_rn(a0, a1)));
+    if (threadIdx.x == 0) swap_epilogue(A, betas, acc_now, step);
+}
+
+// The same swap levels with every temperature's lnL and map entries resident in shared memory
+// (T W (8 + 4) bytes, when that fits): the state is read once at the start and written back
+// once at the end, each level is decided from shared memory with one barrier, and the next
+// level's permutation and ln u (independent of the state) load while the current level is
+// decided.  Decisions, order and counters are those of pt_swap_kernel.
+template <int J>
+__global__ void __launch_bounds__(kSortThreads) pt_swap_resident_kernel(const PtArgs A)
+{
+    extern __shared__ double sm[];
+    const int W = A.W, T = A.T;
+    const int e = blockIdx.x;                               // one block per ensemble
+    const int TW = T * W;
+    int32_t* map = A.map + (int64_t)e * TW;
+    const int32_t* perm = A.perm + (int64_t)e * TW;
+    const double* lnu_swap = A.lnu_swap + (int64_t)e * TW;
+    double* betas = A.betas + (int64_t)e * T;
+    unsigned long long* counters = A.counters + (int64_t)e * 10 * T;
+    double* lnl = sm;                                       // [T][W]
+    int32_t* mp = reinterpret_cast<int32_t*>(sm + TW);      // [T][W]
+    __shared__ unsigned int acc_now[kMaxTemps];
+    __shared__ double bs[kMaxTemps];
+    const uint64_t step = *A.step;
+    for (int t = threadIdx.x; t < T; t += blockDim.x) {
+        acc_now[t] = 0;
+        bs[t] = betas[t];
+    }
+    // map first (independent loads), then the lnL behind each entry (eight in flight a thread)
+#pragma unroll 8
+    for (int s = threadIdx.x; s < TW; s += blockDim.x) mp[s] = map[s];
+#pragma unroll 8
+    for (int s = threadIdx.x; s < TW; s += blockDim.x) lnl[s] = A.out[mp[s]];
+    if (T > 1) {
+        int32_t cp[J], np[J];
+        double cu[J], nu[J];
+        auto load = [&](int i, int32_t (&p)[J], double (&u)[J]) {
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+                const int k = threadIdx.x + j * blockDim.x;
+                if (k < W) {
+                    p[j] = perm[(int64_t)i * W + k];
+                    u[j] = lnu_swap[(int64_t)i * W + k];
+                }
             }
-            for (int t = 1; t <= T - 2; ++t) {
-                Tt[t] = __dadd_rn(Tt[t - 1], exp(S[t]));
-                betas[t] = __ddiv_rn(1.0, Tt[t]);
+        };
+        load(T - 1, cp, cu);
+        __syncthreads();
+        for (int i = T - 1; i >= 1; --i) {
+            if (i > 1) load(i - 1, np, nu);   // in flight while this level is decided
+            const double db = __dsub_rn(bs[i - 1], bs[i]);
+            double* lh = lnl + i * W;
+            double* lc = lnl + (i - 1) * W;
+            int32_t* mh = mp + i * W;
+            int32_t* mc = mp + (i - 1) * W;
+            unsigned int mine = 0;
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+                const int k = threadIdx.x + j * blockDim.x;
+                if (k >= W) continue;
+                const int h = cp[j];
+                const double la = __dmul_rn(db, __dsub_rn(lh[h], lc[k]));
+                if (cu[j] < la) {
+                    const double l = lh[h];
+                    lh[h] = lc[k];
+                    lc[k] = l;
+                    const int32_t c = mh[h];
+                    mh[h] = mc[k];
+                    mc[k] = c;
+                    ++mine;
+                }
             }
-        }
-        // the last ensemble block to finish advances the step: every block has read it by then
-        __threadfence();
-        last = atomicAdd(A.done, 1u) == (unsigned int)(A.n_ens - 1);
-        if (last) {
-            *A.done = 0u;
-            *A.step = step + 1;
+            if (mine) atomicAdd(&acc_now[i], mine);
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+                cp[j] = np[j];
+                cu[j] = nu[j];
+            }
         }
     }
+    for (int s = threadIdx.x; s < TW; s += blockDim.x) map[s] = mp[s];
+    for (int t = 1 + (int)threadIdx.x; t < T; t += blockDim.x) {
+        counters[8 * T + t] += acc_now[t];
+        counters[9 * T + t] += (unsigned long long)W;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) swap_epilogue(A, betas, acc_now, step);
 }
 
 // theta(x) of every physical column (rescoring)
@@ -456,9 +553,13 @@ mbh_status queue_iteration(mbh_pt* P, cudaStream_t st)
     }
     if ((e = cudaStreamWaitEvent(st, P->join, 0)) != cudaSuccess) return cuda_fail(e, "join");
     const size_t swap_smem = (sizeof(double) + sizeof(int32_t)) * 2 * A.W;
+    const size_t resident_smem = (sizeof(double) + sizeof(int32_t)) * (size_t)A.T * A.W;
     const int J = (A.W + kSortThreads - 1) / kSortThreads;
     const unsigned ne = (unsigned)A.n_ens;   // one block per ensemble
-    if (J <= 1) pt_swap_kernel<1><<<ne, kSortThreads, swap_smem, st>>>(A);
+    if (resident_smem <= kSwapResidentBytes && J <= 2) {
+        if (J <= 1) pt_swap_resident_kernel<1><<<ne, kSortThreads, resident_smem, st>>>(A);
+        else pt_swap_resident_kernel<2><<<ne, kSortThreads, resident_smem, st>>>(A);
+    } else if (J <= 1) pt_swap_kernel<1><<<ne, kSortThreads, swap_smem, st>>>(A);
     else if (J <= 2) pt_swap_kernel<2><<<ne, kSortThreads, swap_smem, st>>>(A);
     else if (J <= 4) pt_swap_kernel<4><<<ne, kSortThreads, swap_smem, st>>>(A);
     else pt_swap_kernel<8><<<ne, kSortThreads, swap_smem, st>>>(A);
@@ -614,6 +715,12 @@ extern "C" mbh_status mbh_pt_create_multi(const mbh_pt_opts* o, const mbh_ref* c
     if (e == cudaSuccess) e = cudaFuncSetAttribute(pt_swap_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, swap_max);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(pt_swap_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, swap_max);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(pt_swap_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, swap_max);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(pt_swap_resident_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kSwapResidentBytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(pt_swap_resident_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kSwapResidentBytes);
     cudaStream_t st = (cudaStream_t)stream;
     const unsigned long long zero = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(A.betas, betas_host, sizeof(double) * NT, cudaMemcpyHostToDevice, st);
