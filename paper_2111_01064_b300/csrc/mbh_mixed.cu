@@ -112,43 +112,48 @@ __device__ __forceinline__ float sinc_diff(float x, float k)
     return 4.0f * x * x * k * sum;
 }
 
-// Transfer T_c(f) in float32: the construction of transfer_f64, rearranged so that no
-// step cancels to leading order at small f L (which float32 cannot afford):
+// Transfer T_c(f) in float32, times a real factor `scale` (the caller's amplitude): the
+// construction of transfer_f64, rearranged so that no step cancels to leading order at small
+// f L (which float32 cannot afford):
 //   1 - D = 2i sin x e^{-ix}, 1 - D^2 = 2i sin 2x e^{-2ix} (no 1 - cos), and
 //   X + Y + Z = (1 - D^2)(1 - D) sum_arms g_a [sinc(x(1 + k.n)) - sinc(x(1 - k.n))],
 // so T = (X + Y + Z)/sqrt3 is formed from sinc differences computed without cancellation.
+// Spacecraft offsets from the guiding centre are u_i L/sqrt3 (|u_i - u_j| = sqrt3); the walker
+// carries k/sqrt3 and P/3 (WalkerF), so k.n = (k/sqrt3).(u_j - u_i), n.P.n = (u_j - u_i).(P/3).
+// (u_j - u_i) and pi f (L + k.(p_i + p_j)) = x (1 + (k/sqrt3).(u_i + u_j)).  The common factors
+// (1 - D^2, the one-link -x, scale and the A/E/T normalisations) multiply once at the end:
+//   X = (1 - D^2) [(y21 - y31) + D (y12 - y13)] and cyclic.
 __device__ inline void transfer_f32(const WalkerF& w, const float* Kp, const float* Kc, float f, float sa,
-                                    float ca, cf T[3])
+                                    float ca, float scale, cf T[3])
 {
     constexpr float armS = (float)kArmSec;
-    constexpr float rho = (float)(kArmSec / kSqrt3);
     constexpr float h3 = (float)(0.5 * kSqrt3);
     const float sp[3] = {sa, -0.5f * sa - h3 * ca, -0.5f * sa + h3 * ca};
     const float cp[3] = {ca, -0.5f * ca + h3 * sa, -0.5f * ca - h3 * sa};
-    float o[3][3];
+    float u[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        o[i][0] = rho * (-sp[i] * sa - 0.5f * cp[i] * ca);
-        o[i][1] = rho * (sp[i] * ca - 0.5f * cp[i] * sa);
-        o[i][2] = -rho * h3 * cp[i];
+        u[i][0] = -sp[i] * sa - 0.5f * cp[i] * ca;
+        u[i][1] = sp[i] * ca - 0.5f * cp[i] * sa;
+        u[i][2] = -h3 * cp[i];
     }
     const float x = (float)kPi * armS * f;
     cf yf[3], yb[3], tsum = {0.0f, 0.0f};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const int i = a, j = (a + 1) % 3;
-        float n[3], kn = 0.0f, ko = 0.0f;
+        float d[3], kn = 0.0f, ks = 0.0f;
 #pragma unroll
         for (int m = 0; m < 3; ++m) {
-            n[m] = (o[j][m] - o[i][m]) * (1.0f / armS);
-            kn += w.k[m] * n[m];
-            ko += w.k[m] * (o[i][m] + o[j][m]);
+            d[m] = u[j][m] - u[i][m];
+            kn += w.k[m] * d[m];
+            ks += w.k[m] * (u[i][m] + u[j][m]);
         }
-        const float np = nPnf(w.Pp, n), nc = nPnf(w.Pc, n);
+        const float np = nPnf(w.Pp, d), nc = nPnf(w.Pc, d);
         const cf F = {np * Kp[0] + nc * Kc[0], np * Kp[1] + nc * Kc[1]};
         float sph, cph;
-        sincos_small((float)kPi * f * (armS + ko), &sph, &cph);
-        const cf g = fmul({-x * sph, -x * cph}, F);
+        sincos_small(x * (1.0f + ks), &sph, &cph);
+        const cf g = fmul({sph, cph}, F);
         // sinc(x(1 + k.n)) = sinc(x(1 - k.n)) + the difference (which T needs on its own);
         // the sum is off by at most an ulp of the larger term, like a direct evaluation
         const float sm = sincf(x * (1.0f - kn)), sd = sinc_diff(x, kn);
@@ -162,13 +167,14 @@ __device__ inline void transfer_f32(const WalkerF& w, const float* Kp, const flo
     const float s2 = 2.0f * s1 * c1, c2 = 1.0f - 2.0f * s1 * s1;   // sin 2x, cos 2x
     const cf D = {c2, -s2};
     const cf W1 = {2.0f * s1 * s1, 2.0f * s1 * c1};                 // 1 - D
-    const cf W2 = {2.0f * s2 * s2, 2.0f * s2 * c2};                 // 1 - D^2
-    const cf X = fmul(W2, fsub(fadd(y21, fmul(D, y12)), fadd(y31, fmul(D, y13))));
-    const cf Y = fmul(W2, fsub(fadd(y32, fmul(D, y23)), fadd(y12, fmul(D, y21))));
-    const cf Z = fmul(W2, fsub(fadd(y13, fmul(D, y31)), fadd(y23, fmul(D, y32))));
-    T[0] = fscale(fsub(Z, X), (float)(1.0 / kSqrt2));
-    T[1] = fscale(fadd(fsub(X, fscale(Y, 2.0f)), Z), (float)(1.0 / kSqrt6));
-    T[2] = fscale(fmul(fmul(W2, W1), tsum), (float)(1.0 / kSqrt3));
+    const float w2 = -x * scale * 2.0f * s2;                        // 1 - D^2 = 2 sin 2x (s2, c2)
+    const cf W2 = {w2 * s2, w2 * c2};                               // times -x scale
+    const cf Xp = fadd(fsub(y21, y31), fmul(D, fsub(y12, y13)));
+    const cf Yp = fadd(fsub(y32, y12), fmul(D, fsub(y23, y21)));
+    const cf Zp = fadd(fsub(y13, y23), fmul(D, fsub(y31, y32)));
+    T[0] = fmul(fscale(W2, (float)(1.0 / kSqrt2)), fsub(Zp, Xp));
+    T[1] = fmul(fscale(W2, (float)(1.0 / kSqrt6)), fsub(fadd(Xp, Zp), fscale(Yp, 2.0f)));
+    T[2] = fmul(fscale(fmul(W2, W1), (float)(1.0 / kSqrt3)), tsum);
 }
 
 constexpr f2 kTwoPiDF = df_const(kTwoPi);
@@ -300,16 +306,18 @@ __device__ inline void walker_setup_mixed(const double* __restrict__ theta, int6
     sincos(2.0 * (double)phi, &s2f, &c2f);
     const double u[3] = {sl, -cl, 0.0};
     const double vv[3] = {-sb * cl, -sb * sl, cbt};
-    wf.k[0] = (float)(-cbt * cl);
-    wf.k[1] = (float)(-cbt * sl);
-    wf.k[2] = (float)(-sb);
+    // k/sqrt3 and P/3 (the response works with spacecraft offsets in units of L/sqrt3)
+    constexpr double isq3 = 0.57735026918962576;
+    wf.k[0] = (float)(-cbt * cl * isq3);
+    wf.k[1] = (float)(-cbt * sl * isq3);
+    wf.k[2] = (float)(-sb * isq3);
     const int ii[6] = {0, 0, 0, 1, 1, 2}, jj[6] = {0, 1, 2, 1, 2, 2};
 #pragma unroll
     for (int n = 0; n < 6; ++n) {
         const double ep = u[ii[n]] * u[jj[n]] - vv[ii[n]] * vv[jj[n]];
         const double ec = u[ii[n]] * vv[jj[n]] + vv[ii[n]] * u[jj[n]];
-        wf.Pp[n] = (float)(c2p * ep + s2p * ec);
-        wf.Pc[n] = (float)(-s2p * ep + c2p * ec);
+        wf.Pp[n] = (float)((c2p * ep + s2p * ec) * (1.0 / 3.0));
+        wf.Pc[n] = (float)((-s2p * ep + c2p * ec) * (1.0 / 3.0));
     }
     const double ylm = 0.15769578262626002 /* sqrt(5/(64 pi)) */;
     const double ci = cos((double)iota);
@@ -448,8 +456,8 @@ __device__ __forceinline__ bool point_mixed(const WalkerDF& w, const WalkerF& wf
     float sp, cp;
     sincos_small(reduce_phase(Phi), &sp, &cp);
     cf T[3];
-    transfer_f32(wf, wf.Kp, wf.Kc, q.f.hi, sa, ca, T);
-    const cf e = {amp * scale * cp, -amp * scale * sp};
+    transfer_f32(wf, wf.Kp, wf.Kc, q.f.hi, sa, ca, amp * scale, T);
+    const cf e = {cp, -sp};
 #pragma unroll
     for (int c = 0; c < 3; ++c) h[c] = fmul(e, T[c]);
     return true;
@@ -474,9 +482,8 @@ __device__ __forceinline__ bool point_mixed_hm(const WalkerDF& w, const WalkerF&
         float sp, cp;
         sincos_small(reduce_phase(mode_phase(Phi, b)), &sp, &cp);
         cf T[3];
-        transfer_f32(wf, &wh.hk[b][0], &wh.hk[b][2], q.f.hi, sa, ca, T);
-        const float a = amp * mode_vpow(w, q2, b) * scale;
-        const cf e = {a * cp, -a * sp};
+        transfer_f32(wf, &wh.hk[b][0], &wh.hk[b][2], q.f.hi, sa, ca, amp * mode_vpow(w, q2, b) * scale, T);
+        const cf e = {cp, -sp};
 #pragma unroll
         for (int c = 0; c < 3; ++c) h[c] = fadd(h[c], fmul(e, T[c]));
     }
@@ -747,13 +754,13 @@ __global__ void edge_mixed_kernel(const double* __restrict__ theta0, double t_ob
         float sa, ca, amp;
         const bool in = phase_df(wd, wf, q, tob, Phi, sa, ca, amp);
         cf T[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-        if (in) transfer_f32(wf, wf.Kp, wf.Kc, q.f.hi, sa, ca, T);
+        if (in) transfer_f32(wf, wf.Kp, wf.Kc, q.f.hi, sa, ca, amp, T);
         m.phi0 = in ? make_float2(Phi.hi, Phi.lo) : make_float2(0.f, 0.f);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             // 1/H0 in float64: |H0| is ~1e-20..1e-30 in strain units, so |H0|^2 underflows
             // float32, while 1/H0 itself (~1e20..1e30) is a normal float32
-            const cf H = fscale(T[c], in ? amp : 0.0f);
+            const cf H = in ? T[c] : cf{0.0f, 0.0f};
             const double hr = (double)H.re, hi = (double)H.im;
             const double m2 = hr * hr + hi * hi;
             m.h0inv[c] = m2 > 0.0 ? make_float2((float)(hr / m2), (float)(-hi / m2)) : make_float2(0.f, 0.f);
@@ -807,11 +814,10 @@ __global__ void edge_mixed_hm_kernel(const double* __restrict__ theta0, double t
                 sincos(-ph, &ei[b], &er[b]);   // e^{-i Phi0_lm}
                 if (in) {
                     cf T[3];
-                    transfer_f32(wf, &wh.hk[b][0], &wh.hk[b][2], q.f.hi, sa, ca, T);
-                    const float a = amp * mode_vpow(wd, q2, b);
+                    transfer_f32(wf, &wh.hk[b][0], &wh.hk[b][2], q.f.hi, sa, ca, amp * mode_vpow(wd, q2, b), T);
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
-                        const double Hr = (double)(a * T[c].re), Hi = (double)(a * T[c].im);
+                        const double Hr = (double)T[c].re, Hi = (double)T[c].im;
                         hr[b][c] = Hr * er[b] - Hi * ei[b];
                         hi[b][c] = Hr * ei[b] + Hi * er[b];
                         h0r[c] += hr[b][c];
@@ -934,10 +940,10 @@ __device__ __forceinline__ void het_mixed_body(const HetLaunch& L)
                     sincos_small(0.5f * reduce_phase(dd_sub(Phi, ld_f2(me.phi0))), &sh, &ch);
                     const cf em1 = {-2.0f * sh * sh, -2.0f * sh * ch};   // e^{-i dPhi} - 1
                     cf T[3];
-                    transfer_f32(wsf[lw], wsf[lw].Kp, wsf[lw].Kc, q.f.hi, sa, ca, T);
+                    transfer_f32(wsf[lw], wsf[lw].Kp, wsf[lw].Kc, q.f.hi, sa, ca, amp, T);
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
-                        const cf rho = fmul(fscale(T[c], amp), {me.h0inv[c].x, me.h0inv[c].y});
+                        const cf rho = fmul(T[c], {me.h0inv[c].x, me.h0inv[c].y});
                         const cf rm1 = {rho.re - 1.0f, rho.im};
                         dl[c] = fadd(fadd(rm1, fmul(rm1, em1)), em1);
                     }
@@ -1053,12 +1059,12 @@ __global__ void __launch_bounds__(BLOCK)
                         sincos_small(0.5f * reduce_phase(dd_sub(mode_phase(Phi, b), ld_f2(mm.phi0))), &sh, &ch);
                         const cf em1 = {-2.0f * sh * sh, -2.0f * sh * ch};   // e^{-i dPhi} - 1
                         cf T[3];
-                        transfer_f32(wsf[lw], &wsh[lw].hk[b][0], &wsh[lw].hk[b][2], q.f.hi, sa, ca, T);
-                        const float a = amp * mode_vpow(wsd[lw], q2, b);
+                        transfer_f32(wsf[lw], &wsh[lw].hk[b][0], &wsh[lw].hk[b][2], q.f.hi, sa, ca,
+                                     amp * mode_vpow(wsd[lw], q2, b), T);
 #pragma unroll
                         for (int c = 0; c < 3; ++c) {
                             const cf u = {mm.u[c].x, mm.u[c].y};
-                            const cf ac = fsub(fmul(fscale(T[c], a), {mm.g[c].x, mm.g[c].y}), u);
+                            const cf ac = fsub(fmul(T[c], {mm.g[c].x, mm.g[c].y}), u);
                             dl[c] = fadd(dl[c], fadd(fadd(ac, fmul(ac, em1)), fmul(u, em1)));
                         }
                     } else {
@@ -1166,10 +1172,10 @@ __device__ __forceinline__ void het_mixed_pt_body(const HetLaunch& L)
                     sincos_small(0.5f * reduce_phase(dd_sub(Phi, ld_f2(me.phi0))), &sh, &ch);
                     const cf em1 = {-2.0f * sh * sh, -2.0f * sh * ch};
                     cf T[3];
-                    transfer_f32(wsf[lw], wsf[lw].Kp, wsf[lw].Kc, q.f.hi, sa, ca, T);
+                    transfer_f32(wsf[lw], wsf[lw].Kp, wsf[lw].Kc, q.f.hi, sa, ca, amp, T);
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
-                        const cf rho = fmul(fscale(T[c], amp), {me.h0inv[c].x, me.h0inv[c].y});
+                        const cf rho = fmul(T[c], {me.h0inv[c].x, me.h0inv[c].y});
                         const cf rm1 = {rho.re - 1.0f, rho.im};
                         dl[c] = fadd(fadd(rm1, fmul(rm1, em1)), em1);
                     }
