@@ -25,6 +25,7 @@ constexpr int kDefaultBlock = 128;
 struct MixEdge {
     float2 f, f3, fm3, lnf3, phi0;
     float2 h0inv[3];
+    float4 xs;   // sin x, cos x (x = pi f L/c, the one-link phase), f^{-7/6}, 0
 };
 // Bin record of the mixed-precision heterodyne: float32 summary data and 1/(f_hi - f_lo).
 struct MixBin {

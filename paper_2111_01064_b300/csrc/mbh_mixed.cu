@@ -41,6 +41,7 @@ __device__ __forceinline__ cf fscale(cf a, float s) { return {a.re * s, a.im * s
 struct WalkerF {
     float k[3], Pp[6], Pc[6], Kp[2], Kc[2];
     float sa_ref, ca_ref, amp, inv_fc2;
+    float amp76;   // amp (pi M)^{-7/6}: times f^{-7/6} of an edge table gives amp v^{-7/2}
 };
 
 __device__ __forceinline__ float nPnf(const float* P, const float* n)
@@ -124,7 +125,7 @@ __device__ __forceinline__ float sinc_diff(float x, float k)
 // (1 - D^2, the one-link -x, scale and the A/E/T normalisations) multiply once at the end:
 //   X = (1 - D^2) [(y21 - y31) + D (y12 - y13)] and cyclic.
 __device__ inline void transfer_f32(const WalkerF& w, const float* Kp, const float* Kc, float f, float sa,
-                                    float ca, float scale, cf T[3])
+                                    float ca, float scale, float s1, float c1, cf T[3])
 {
     constexpr float armS = (float)kArmSec;
     constexpr float h3 = (float)(0.5 * kSqrt3);
@@ -162,8 +163,6 @@ __device__ inline void transfer_f32(const WalkerF& w, const float* Kp, const flo
         tsum = fadd(tsum, fscale(g, sd));   // y_{j->i} - y_{i->j}
     }
     const cf y12 = yf[0], y21 = yb[0], y23 = yf[1], y32 = yb[1], y31 = yf[2], y13 = yb[2];
-    float s1, c1;
-    sincos_small(x, &s1, &c1);
     const float s2 = 2.0f * s1 * c1, c2 = 1.0f - 2.0f * s1 * s1;   // sin 2x, cos 2x
     const cf D = {c2, -s2};
     const cf W1 = {2.0f * s1 * s1, 2.0f * s1 * c1};                 // 1 - D
@@ -175,6 +174,15 @@ __device__ inline void transfer_f32(const WalkerF& w, const float* Kp, const flo
     T[0] = fmul(fscale(W2, (float)(1.0 / kSqrt2)), fsub(Zp, Xp));
     T[1] = fmul(fscale(W2, (float)(1.0 / kSqrt6)), fsub(fadd(Xp, Zp), fscale(Yp, 2.0f)));
     T[2] = fmul(fscale(fmul(W2, W1), (float)(1.0 / kSqrt3)), tsum);
+}
+
+// the same with sin x, cos x of the one-link phase x = pi f L/c computed here
+__device__ __forceinline__ void transfer_f32(const WalkerF& w, const float* Kp, const float* Kc, float f,
+                                             float sa, float ca, float scale, cf T[3])
+{
+    float s1, c1;
+    sincos_small((float)kPi * (float)kArmSec * f, &s1, &c1);
+    transfer_f32(w, Kp, Kc, f, sa, ca, scale, s1, c1, T);
 }
 
 constexpr f2 kTwoPiDF = df_const(kTwoPi);
@@ -297,7 +305,9 @@ __device__ inline void walker_setup_mixed(const double* __restrict__ theta, int6
     // A = sqrt(2 pi/3) pi^{-2/3} M^{5/6} eta^{1/2} (pi M)^{7/6} / D v^{-7/2} exp(-(f/fc)^2)
     //   = pi sqrt(2/3) M^2 sqrt(eta) / D v^{-7/2} exp(-(f/fc)^2)
     const double dist = (double)dl * (1e9 * kParsec / kClight);
-    wf.amp = (float)(kPi * 0.816496580927726 /* sqrt(2/3) */ * M * M * sqrt(eta) / dist);
+    const double ampd = kPi * 0.816496580927726 /* sqrt(2/3) */ * M * M * sqrt(eta) / dist;
+    wf.amp = (float)ampd;
+    wf.amp76 = (float)(ampd * (icb * icb * icb) * sqrt(icb));   // (pi M)^{-7/6} = icb^{7/2}
     wf.inv_fc2 = (float)(400.0 * M * M);   // 1/f_c^2, f_c = 0.05/M
     wf.sa_ref = (float)sa;
     wf.ca_ref = (float)ca;
@@ -344,9 +354,10 @@ __device__ __forceinline__ f2 ld_f2(float2 v) { return {v.x, v.y}; }
 // Large phase Phi(f) (double-float) and float32 amplitude and orbit angle from the
 // frequency tables.  Returns false outside the support (f > f_cut or t(f) outside [0, t_obs]);
 // with kAlways the phase is computed there as well (a reference phase defined at every edge).
-template <bool kAlways = false>
+template <bool kAlways = false, bool kTab = false>
 __device__ __forceinline__ bool phase_df(const WalkerDF& w, const WalkerF& wf, const FreqDF& q,
-                                         f2 t_obs, f2& Phi, float& sa, float& ca, float& amp)
+                                         f2 t_obs, f2& Phi, float& sa, float& ca, float& amp,
+                                         float fm76 = 0.0f)
 {
     const f2 v = dd_mul(w.cbrt_piM, q.f3);
     const f2 iv = dd_mul(w.icbrt_piM, q.fm3);
@@ -378,8 +389,13 @@ __device__ __forceinline__ bool phase_df(const WalkerDF& w, const WalkerF& wf, c
     Phi = dd_add(lin, dd_sub(psi_pn, w.psi_max));
     sa = dd_to_float(sa_d);
     ca = dd_to_float(ca_d);
-    const float ivf = iv.hi, ff = q.f.hi;
-    amp = wf.amp * ivf * ivf * ivf * sqrtf(ivf) * expf(-ff * ff * wf.inv_fc2);
+    const float ff = q.f.hi;
+    if (kTab) {   // f^{-7/6} from the edge table
+        amp = wf.amp76 * fm76 * expf(-ff * ff * wf.inv_fc2);
+    } else {
+        const float ivf = iv.hi;
+        amp = wf.amp * ivf * ivf * ivf * sqrtf(ivf) * expf(-ff * ff * wf.inv_fc2);
+    }
     return in;
 }
 
@@ -733,8 +749,18 @@ void mbh::free_ref_tables(mbh_ref* R)
     if (R->mix_hm_base) cudaFree(R->mix_hm_base);
 }
 
-// Edge records of the reference, using the same mixed-precision functions as the walkers so
-// that a walker equal to the reference gets dPhi = 0 and rho = 1 up to one rounding.
+// frequency-only factors of an edge, rounded once from float64: sin and cos of the one-link
+// phase x = pi f L/c, and f^{-7/6}
+__device__ __forceinline__ float4 edge_xs(double f)
+{
+    double s, c;
+    sincos(kPi * kArmSec * f, &s, &c);
+    return make_float4((float)s, (float)c, (float)pow(f, -7.0 / 6.0), 0.0f);
+}
+
+// Edge records of the reference, using the same mixed-precision functions (and the same edge
+// table values) as the walkers so that a walker equal to the reference gets dPhi = 0 and
+// rho = 1 up to one rounding.
 __global__ void edge_mixed_kernel(const double* __restrict__ theta0, double t_obs,
                                   const double* __restrict__ fe, int n_edges, MixEdge* __restrict__ out)
 {
@@ -750,11 +776,12 @@ __global__ void edge_mixed_kernel(const double* __restrict__ theta0, double t_ob
         m.f3 = make_float2(q.f3.hi, q.f3.lo);
         m.fm3 = make_float2(q.fm3.hi, q.fm3.lo);
         m.lnf3 = make_float2(q.lnf3.hi, q.lnf3.lo);
+        m.xs = edge_xs(fe[e]);
         f2 Phi = {0.0f, 0.0f};
         float sa, ca, amp;
-        const bool in = phase_df(wd, wf, q, tob, Phi, sa, ca, amp);
+        const bool in = phase_df<false, true>(wd, wf, q, tob, Phi, sa, ca, amp, m.xs.z);
         cf T[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-        if (in) transfer_f32(wf, wf.Kp, wf.Kc, q.f.hi, sa, ca, amp, T);
+        if (in) transfer_f32(wf, wf.Kp, wf.Kc, q.f.hi, sa, ca, amp, m.xs.x, m.xs.y, T);
         m.phi0 = in ? make_float2(Phi.hi, Phi.lo) : make_float2(0.f, 0.f);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -796,6 +823,7 @@ __global__ void edge_mixed_hm_kernel(const double* __restrict__ theta0, double t
         me.f3 = make_float2(q.f3.hi, q.f3.lo);
         me.fm3 = make_float2(q.fm3.hi, q.fm3.lo);
         me.lnf3 = make_float2(q.lnf3.hi, q.lnf3.lo);
+        me.xs = edge_xs(fe[e]);
         out[e] = me;
         double h0r[3] = {0, 0, 0}, h0i[3] = {0, 0, 0};
         double hr[kHmModes][3], hi[kHmModes][3], er[kHmModes], ei[kHmModes];
@@ -814,7 +842,8 @@ __global__ void edge_mixed_hm_kernel(const double* __restrict__ theta0, double t
                 sincos(-ph, &ei[b], &er[b]);   // e^{-i Phi0_lm}
                 if (in) {
                     cf T[3];
-                    transfer_f32(wf, &wh.hk[b][0], &wh.hk[b][2], q.f.hi, sa, ca, amp * mode_vpow(wd, q2, b), T);
+                    transfer_f32(wf, &wh.hk[b][0], &wh.hk[b][2], q.f.hi, sa, ca, amp * mode_vpow(wd, q2, b),
+                                 me.xs.x, me.xs.y, T);
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         const double Hr = (double)T[c].re, Hi = (double)T[c].im;
@@ -935,12 +964,12 @@ __device__ __forceinline__ void het_mixed_body(const HetLaunch& L)
                 const FreqDF q = {ld_f2(me.f), ld_f2(me.f3), ld_f2(me.fm3), ld_f2(me.lnf3)};
                 f2 Phi;
                 float sa, ca, amp;
-                if (phase_df(wsd[lw], wsf[lw], q, tob, Phi, sa, ca, amp)) {
+                if (phase_df<false, true>(wsd[lw], wsf[lw], q, tob, Phi, sa, ca, amp, me.xs.z)) {
                     float sh, ch;
                     sincos_small(0.5f * reduce_phase(dd_sub(Phi, ld_f2(me.phi0))), &sh, &ch);
                     const cf em1 = {-2.0f * sh * sh, -2.0f * sh * ch};   // e^{-i dPhi} - 1
                     cf T[3];
-                    transfer_f32(wsf[lw], wsf[lw].Kp, wsf[lw].Kc, q.f.hi, sa, ca, amp, T);
+                    transfer_f32(wsf[lw], wsf[lw].Kp, wsf[lw].Kc, q.f.hi, sa, ca, amp, me.xs.x, me.xs.y, T);
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         const cf rho = fmul(T[c], {me.h0inv[c].x, me.h0inv[c].y});
@@ -1060,7 +1089,7 @@ __global__ void __launch_bounds__(BLOCK)
                         const cf em1 = {-2.0f * sh * sh, -2.0f * sh * ch};   // e^{-i dPhi} - 1
                         cf T[3];
                         transfer_f32(wsf[lw], &wsh[lw].hk[b][0], &wsh[lw].hk[b][2], q.f.hi, sa, ca,
-                                     amp * mode_vpow(wsd[lw], q2, b), T);
+                                     amp * mode_vpow(wsd[lw], q2, b), me.xs.x, me.xs.y, T);
 #pragma unroll
                         for (int c = 0; c < 3; ++c) {
                             const cf u = {mm.u[c].x, mm.u[c].y};
@@ -1167,12 +1196,12 @@ __device__ __forceinline__ void het_mixed_pt_body(const HetLaunch& L)
                 const FreqDF q = {ld_f2(me.f), ld_f2(me.f3), ld_f2(me.fm3), ld_f2(me.lnf3)};
                 f2 Phi;
                 float sa, ca, amp;
-                if (phase_df(wsd[lw], wsf[lw], q, tob, Phi, sa, ca, amp)) {
+                if (phase_df<false, true>(wsd[lw], wsf[lw], q, tob, Phi, sa, ca, amp, me.xs.z)) {
                     float sh, ch;
                     sincos_small(0.5f * reduce_phase(dd_sub(Phi, ld_f2(me.phi0))), &sh, &ch);
                     const cf em1 = {-2.0f * sh * sh, -2.0f * sh * ch};
                     cf T[3];
-                    transfer_f32(wsf[lw], wsf[lw].Kp, wsf[lw].Kc, q.f.hi, sa, ca, amp, T);
+                    transfer_f32(wsf[lw], wsf[lw].Kp, wsf[lw].Kc, q.f.hi, sa, ca, amp, me.xs.x, me.xs.y, T);
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         const cf rho = fmul(T[c], {me.h0inv[c].x, me.h0inv[c].y});
