@@ -101,6 +101,10 @@ __device__ __forceinline__ f2 dd_fma(f2 a, f2 b, f2 c)
 
 __device__ __forceinline__ float dd_to_float(f2 a) { return __fadd_rn(a.hi, a.lo); }
 
+// a <= b for df values normalised with round-to-nearest (|lo| <= ulp(hi)/2): the order of
+// the (hi, lo) pairs is the order of the values
+__device__ __forceinline__ bool dd_le(f2 a, f2 b) { return a.hi < b.hi || (a.hi == b.hi && a.lo <= b.lo); }
+
 // sign test of a (normalised) df value
 __device__ __forceinline__ bool dd_le0(f2 a) { return a.hi < 0.0f || (a.hi == 0.0f && a.lo <= 0.0f); }
 __device__ __forceinline__ bool dd_lt0(f2 a) { return a.hi < 0.0f || (a.hi == 0.0f && a.lo < 0.0f); }

@@ -186,14 +186,12 @@ __device__ __forceinline__ void transfer_f32(const WalkerF& w, const float* Kp, 
 }
 
 constexpr f2 kTwoPiDF = df_const(kTwoPi);
-constexpr f2 kInvTwoPiDF = df_const(kInvTwoPi);
-constexpr f2 kAUSecDF = df_const(kAUSec);
 
 // Per-walker constants of the phase chain as float pairs.
 struct WalkerDF {
     f2 c[8], d[8], cl5, cl6, dl6;
     f2 cbrt_piM, icbrt_piM, ln_cbrt_piM;
-    f2 tref, fmax, fcut, psi_max, dpsi_max;
+    f2 tref, fcut, t0, c0, c1;
     f2 sa_ref, ca_ref, kx, ky;
 };
 
@@ -281,23 +279,28 @@ __device__ inline void walker_setup_mixed(const double* __restrict__ theta, int6
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         m.c[k] = split_f64(c[k], 0);
-        m.d[k] = split_f64(d[k], 0);
+        m.d[k] = split_f64(d[k] * kInvTwoPi, 0);   // the derivative chain gives t(f) in seconds
     }
     m.cl5 = split_f64(cl5, 0);
     m.cl6 = split_f64(cl6, 0);
-    m.dl6 = split_f64(dl6, 0);
+    m.dl6 = split_f64(dl6 * kInvTwoPi, 0);
     m.cbrt_piM = split_f64(cb, 0);
     m.icbrt_piM = split_f64(icb, 0);
     m.ln_cbrt_piM = split_f64(log(piM) / 3.0, 0);
+    // the t_ref and f_max pinning folded into per-walker constants:
+    //   t(f) = t_ref + (Psi'(f) - Psi'(f_max))/(2 pi) = Psi'(f)/(2 pi) + t0,
+    //   Phi(f) = 2 pi f (t_ref + k.c(t)) + Psi_PN(f) - Psi_PN(f_max) - (f - f_max) Psi'(f_max)
+    //          = f (c1 + 2 pi (AU/c) k.c(t)) + Psi_PN(f) + c0
+    const double fmax = (0.05 * 0.6454972243679028) * iM;   // f_c sqrt(5/12)
     m.tref = split_f64(tref, 0);
-    m.fmax = split_f64((0.05 * 0.6454972243679028) * iM, 0);   // f_c sqrt(5/12)
-    m.fcut = split_f64(0.2 * iM, 0);
-    m.psi_max = split_f64(psi_max, 0);
-    m.dpsi_max = split_f64(dpsi_max, 0);
+    m.fcut = split_d(0.2 * iM);   // rounded to nearest: compared lexicographically (dd_le)
+    m.t0 = split_f64(tref - dpsi_max * kInvTwoPi, 0);
+    m.c0 = split_f64(fmax * dpsi_max - psi_max, 0);
+    m.c1 = split_f64(kTwoPi * tref - dpsi_max, 0);
     m.sa_ref = split_f64(sa, 0);
     m.ca_ref = split_f64(ca, 0);
-    m.kx = split_f64(-cbt * cl, 0);
-    m.ky = split_f64(-cbt * sl, 0);
+    m.kx = split_f64(kTwoPi * kAUSec * (-cbt * cl), 0);
+    m.ky = split_f64(kTwoPi * kAUSec * (-cbt * sl), 0);
 
     // Float32 constants (amplitude, taper, wave frame, mode factors), computed in float64 and
     // rounded once: the heterodyne ratio h/h0 of a nearby walker cancels their common part,
@@ -371,22 +374,21 @@ __device__ __forceinline__ bool phase_df(const WalkerDF& w, const WalkerF& wf, c
     const f2 iv2 = dd_mul(iv, iv), iv4 = dd_mul(iv2, iv2);
     const f2 iv5 = dd_mul(iv4, iv), iv8 = dd_mul(iv4, iv4);
     const f2 psi_pn = dd_add(dd_mul(P, iv5), dd_mul(lnv, dd_fma(w.cl6, v, w.cl5)));
-    const f2 dpsi = dd_add(dd_mul(Q, iv8), dd_mul(dd_mul(lnv, w.dl6), iv2));
-    const f2 dt = dd_mul(dd_sub(dpsi, w.dpsi_max), kInvTwoPiDF);
-    const f2 t = dd_add(w.tref, dt);
-    const bool in = dd_le0(dd_sub(q.f, w.fcut)) && !dd_lt0(t) && dd_le0(dd_sub(t, t_obs));
+    // t(f) = Psi'(f)/(2 pi) + t0 (the walker's d and dl6 carry the 1/(2 pi))
+    const f2 t = dd_add(dd_add(dd_mul(Q, iv8), dd_mul(dd_mul(lnv, w.dl6), iv2)), w.t0);
+    const bool in = dd_le(q.f, w.fcut) && !dd_lt0(t) && dd_le(t, t_obs);
     if (!kAlways && !in) return false;
-    // orbit angle alpha(t) = alpha(t_ref) + da
-    const float da = dt.hi * (float)(kTwoPi / kYear);
+    // orbit angle alpha(t) = alpha(t_ref) + da, da from t - t_ref in float32
+    const float dt = __fadd_rn(__fsub_rn(t.hi, w.tref.hi), __fsub_rn(t.lo, w.tref.lo));
+    const float da = dt * (float)(kTwoPi / kYear);
     float sh, ch;
     sincos_small(0.5f * da, &sh, &ch);
     const float sd = 2.0f * sh * ch, omc = 2.0f * sh * sh;   // sin da, 1 - cos da
     const f2 sa_d = dd_add_f(w.sa_ref, wf.ca_ref * sd - wf.sa_ref * omc);
     const f2 ca_d = dd_add_f(w.ca_ref, -(wf.ca_ref * omc + wf.sa_ref * sd));
-    const f2 kc = dd_mul(dd_add(dd_mul(w.kx, ca_d), dd_mul(w.ky, sa_d)), kAUSecDF);
-    const f2 lin = dd_sub(dd_mul(kTwoPiDF, dd_mul(q.f, dd_add(w.tref, kc))),
-                          dd_mul(dd_sub(q.f, w.fmax), w.dpsi_max));
-    Phi = dd_add(lin, dd_sub(psi_pn, w.psi_max));
+    // Phi = f (c1 + 2 pi (AU/c) k.c(t)) + Psi_PN(f) + c0 (kx, ky carry 2 pi AU/c)
+    const f2 S = dd_fma(w.ky, sa_d, dd_fma(w.kx, ca_d, w.c1));
+    Phi = dd_add(dd_mul(q.f, S), dd_add(psi_pn, w.c0));
     sa = dd_to_float(sa_d);
     ca = dd_to_float(ca_d);
     const float ff = q.f.hi;
