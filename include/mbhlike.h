@@ -183,7 +183,9 @@ MBH_API mbh_status het_loglike_batch(const mbh_ref* const* refs, const int64_t* 
  * (float32 device arrays) so that it can be checked against CUDA's functions and
  * float64 references.  kind 0: sin and cos of x (o1, o2; Cody-Waite reduction and
  * Taylor polynomials, |x| up to ~100); kind 1: sin(x)/x (o1); kind 2:
- * sinc(x(1+y)) - sinc(x(1-y)) without cancellation (o1). */
+ * sinc(x(1+y)) - sinc(x(1-y)) without cancellation (o1); kinds 3 and 4: the
+ * four-term forms of kinds 1 and 2 that the response uses below x = 0.1 (valid for
+ * |x| < 0.2, and x < 0.1 with |y| <= 1).  MBH_EINVAL for another kind. */
 MBH_API mbh_status mbh_selftest_math(int32_t kind, const float* x_dev, const float* y_dev, int64_t n,
                              float* o1_dev, float* o2_dev, void* stream);
 

@@ -50,19 +50,24 @@ __device__ __forceinline__ float nPnf(const float* P, const float* n)
            2.0f * (P[1] * n[0] * n[1] + P[2] * n[0] * n[2] + P[4] * n[1] * n[2]);
 }
 
-// sin x / x: Taylor series in x^2 up to x^14/15! for |x| < 2 (truncation < 2e-10), else sinf/x.
+// sin x / x as its Taylor series in u2 = x^2 to the term x^{2(N-1)}/(2N-1)!
+template <int N>
+__device__ __forceinline__ float sinc_series(float u2)
+{
+    // (-1)^j/(2j+1)!, j = 0..7
+    constexpr float c[8] = {1.0f, -1.0f / 6.0f, 1.0f / 120.0f, -1.0f / 5040.0f, 1.0f / 362880.0f,
+                            -1.0f / 39916800.0f, 1.0f / 6227020800.0f, -1.0f / 1307674368000.0f};
+    float p = c[N - 1];
+#pragma unroll
+    for (int j = N - 2; j >= 0; --j) p = fmaf(p, u2, c[j]);
+    return p;
+}
+
+// sin x / x: the series to x^14/15! for |x| < 2 (truncation < 2e-10), else sinf/x.
 __device__ __forceinline__ float sincf(float x)
 {
     if (fabsf(x) >= 2.0f) return sinf(x) / x;
-    const float u2 = x * x;
-    float p = -1.0f / 1307674368000.0f;
-    p = fmaf(p, u2, 1.0f / 6227020800.0f);
-    p = fmaf(p, u2, -1.0f / 39916800.0f);
-    p = fmaf(p, u2, 1.0f / 362880.0f);
-    p = fmaf(p, u2, -1.0f / 5040.0f);
-    p = fmaf(p, u2, 1.0f / 120.0f);
-    p = fmaf(p, u2, -1.0f / 6.0f);
-    return fmaf(p, u2, 1.0f);
+    return sinc_series<8>(x * x);
 }
 
 // sin and cos of |x| <~ 100: Cody-Waite reduction by pi/2 (two-term split of pi/2, the first
@@ -93,18 +98,19 @@ __device__ __forceinline__ void sincos_small(float x, float* s, float* c)
 // sinc(x (1 + k)) - sinc(x (1 - k)) without cancellation: for arguments below 2 as
 // (a^2 - b^2) sum_{j>=1} (-1)^j P_j / (2j+1)!, P_1 = 1, P_{j+1} = a^2 P_j + b^{2j}
 // (a^{2j} - b^{2j} = (a^2 - b^2) P_j), with a^2 - b^2 = 4 x^2 k; directly above.
-__device__ __forceinline__ float sinc_diff(float x, float k)
+// the series of sinc(x(1 + k)) - sinc(x(1 - k)) with N terms (j = 1..N)
+template <int N>
+__device__ __forceinline__ float sinc_diff_series(float x, float k)
 {
     const float a = x * (1.0f + k), b = x * (1.0f - k);
-    if (fmaxf(fabsf(a), fabsf(b)) >= 2.0f) return sincf(a) - sincf(b);
     const float a2 = a * a, b2 = b * b;
     // 1/(2j+1)! for j = 1..9 (terms beyond are below 5e-12 relative for arguments < 2)
-    const float inv_fact[9] = {1.0f / 6.0f, 1.0f / 120.0f, 1.0f / 5040.0f, 1.0f / 362880.0f,
-                               1.0f / 39916800.0f, 1.0f / 6227020800.0f, 1.0f / 1307674368000.0f,
-                               1.0f / 355687428096000.0f, 1.0f / 121645100408832000.0f};
+    constexpr float inv_fact[9] = {1.0f / 6.0f, 1.0f / 120.0f, 1.0f / 5040.0f, 1.0f / 362880.0f,
+                                   1.0f / 39916800.0f, 1.0f / 6227020800.0f, 1.0f / 1307674368000.0f,
+                                   1.0f / 355687428096000.0f, 1.0f / 121645100408832000.0f};
     float P = 1.0f, bp = 1.0f, sum = 0.0f, sign = -1.0f;
 #pragma unroll
-    for (int j = 0; j < 9; ++j) {
+    for (int j = 0; j < N; ++j) {
         sum += sign * P * inv_fact[j];
         sign = -sign;
         bp *= b2;
@@ -112,6 +118,17 @@ __device__ __forceinline__ float sinc_diff(float x, float k)
     }
     return 4.0f * x * x * k * sum;
 }
+
+__device__ __forceinline__ float sinc_diff(float x, float k)
+{
+    const float a = x * (1.0f + k), b = x * (1.0f - k);
+    if (fmaxf(fabsf(a), fabsf(b)) >= 2.0f) return sincf(a) - sincf(b);
+    return sinc_diff_series<9>(x, k);
+}
+
+// Below x = 0.1 (both arguments under 0.2, |k| <= 1) four terms of either series reach float32
+// rounding (the next terms are below 1e-11 and 3e-13 of the first): the short forms used there.
+constexpr float kSincShortX = 0.1f;
 
 // Transfer T_c(f) in float32, times a real factor `scale` (the caller's amplitude): the
 // construction of transfer_f64, rearranged so that no step cancels to leading order at small
@@ -157,7 +174,15 @@ __device__ inline void transfer_f32(const WalkerF& w, const float* Kp, const flo
         const cf g = fmul({sph, cph}, F);
         // sinc(x(1 + k.n)) = sinc(x(1 - k.n)) + the difference (which T needs on its own);
         // the sum is off by at most an ulp of the larger term, like a direct evaluation
-        const float sm = sincf(x * (1.0f - kn)), sd = sinc_diff(x, kn);
+        float sm, sd;
+        if (x < kSincShortX) {   // uniform over a warp but for the rounds that straddle 0.1
+            const float b = x * (1.0f - kn);
+            sm = sinc_series<4>(b * b);
+            sd = sinc_diff_series<4>(x, kn);
+        } else {
+            sm = sincf(x * (1.0f - kn));
+            sd = sinc_diff(x, kn);
+        }
         yf[a] = fscale(g, sm);
         yb[a] = fscale(g, sm + sd);
         tsum = fadd(tsum, fscale(g, sd));   // y_{j->i} - y_{i->j}
@@ -525,8 +550,12 @@ __global__ void selftest_math_kernel(int kind, const float* __restrict__ x, cons
             o2[i] = c;
         } else if (kind == 1) {
             o1[i] = sincf(x[i]);
-        } else {
+        } else if (kind == 2) {
             o1[i] = sinc_diff(x[i], y[i]);
+        } else if (kind == 3) {
+            o1[i] = sinc_series<4>(x[i] * x[i]);
+        } else {
+            o1[i] = sinc_diff_series<4>(x[i], y[i]);
         }
     }
 }
@@ -534,10 +563,10 @@ __global__ void selftest_math_kernel(int kind, const float* __restrict__ x, cons
 extern "C" mbh_status mbh_selftest_math(int32_t kind, const float* x_dev, const float* y_dev, int64_t n,
                                         float* o1_dev, float* o2_dev, void* stream)
 {
-    if (kind < 0 || kind > 2) return fail(MBH_EINVAL, "kind must be 0, 1 or 2");
+    if (kind < 0 || kind > 4) return fail(MBH_EINVAL, "kind must be 0..4");
     if (n < 0) return fail(MBH_EINVAL, "n < 0");
     if (n == 0) return MBH_OK;
-    if (!x_dev || !o1_dev || (kind == 0 && !o2_dev) || (kind == 2 && !y_dev))
+    if (!x_dev || !o1_dev || (kind == 0 && !o2_dev) || ((kind == 2 || kind == 4) && !y_dev))
         return fail(MBH_EINVAL, "NULL buffer");
     if (mbh_status s = check_device()) return s;
     const int blocks = (int)std::min<int64_t>((n + 255) / 256, 148 * 32);

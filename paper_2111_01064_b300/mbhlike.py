@@ -553,7 +553,7 @@ class Server:
 
 def mbh_selftest_math(kind: int, x: torch.Tensor, y: torch.Tensor | None = None, stream=None):
     """Library float32 device math on x (and y): kind 0 -> (sin, cos), 1 -> sinc,
-    2 -> sinc(x(1+y)) - sinc(x(1-y))."""
+    2 -> sinc(x(1+y)) - sinc(x(1-y)); 3, 4: the four-term forms of 1 and 2 (small x)."""
     n = x.numel()
     o1 = torch.empty_like(x)
     o2 = torch.empty_like(x) if kind == 0 else None

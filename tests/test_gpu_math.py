@@ -59,3 +59,28 @@ def test_sinc_difference_relative(M):
             assert abs(got[i] - ref) <= 1e-6 * abs(ref) + 1e-12, (x[i], k[i], got[i], ref)
         else:                                                  # plain difference of O(1) values
             assert abs(got[i] - ref) <= 3e-7, (x[i], k[i], got[i], ref)
+
+
+def test_short_sinc_forms(M):
+    """The four-term series used by the response below x = 0.1 agree with the float64
+    values to float32 rounding over their whole range (|x| < 0.2; x < 0.1 with |k| <= 1)."""
+    import mpmath as mp
+    import torch
+    x = np.linspace(-0.2, 0.2, 40001).astype(np.float32)
+    got = M.mbh_selftest_math(3, torch.from_numpy(x).cuda()).cpu().numpy().astype(np.float64)
+    xd = x.astype(np.float64)
+    ref = np.where(xd == 0, 1.0, np.sin(xd) / np.where(xd == 0, 1.0, xd))
+    assert np.max(np.abs(got - ref)) <= 1.2e-7
+    rng = np.random.default_rng(4)
+    xs = np.concatenate([rng.uniform(1e-5, 0.1, 1500), np.full(100, 0.0999999)]).astype(np.float32)
+    ks = np.concatenate([rng.uniform(-1, 1, 1500), rng.choice([-1.0, 1.0], 100)]).astype(np.float32)
+    got = M.mbh_selftest_math(4, torch.from_numpy(xs).cuda(), torch.from_numpy(ks).cuda()).cpu().numpy()
+    full = M.mbh_selftest_math(2, torch.from_numpy(xs).cuda(), torch.from_numpy(ks).cuda()).cpu().numpy()
+    mp.mp.dps = 40
+    for i in range(0, 1600, 4):
+        X, K = mp.mpf(float(xs[i])), mp.mpf(float(ks[i]))
+        ref = float(mp.sinc(X * (1 + K)) - mp.sinc(X * (1 - K)))
+        assert abs(got[i] - ref) <= 1e-6 * abs(ref) + 1e-14, (xs[i], ks[i], got[i], ref)
+        assert abs(got[i] - full[i]) <= 1e-6 * abs(ref) + 1e-14
+    with pytest.raises(M.MBHError):
+        M.mbh_selftest_math(5, torch.from_numpy(xs).cuda())
