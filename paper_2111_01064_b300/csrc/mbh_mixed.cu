@@ -70,6 +70,28 @@ __device__ __forceinline__ float sincf(float x)
     return sinc_series<8>(x * x);
 }
 
+// sin and cos of |r| <= pi/4 without reduction: Taylor polynomials of sin to r^9/9! and cos to
+// r^10/10! (truncation < 2e-9), or with kShort (|r| <= 0.06) to r^5/5! and r^6/6! (< 1e-12)
+template <bool kShort>
+__device__ __forceinline__ void sincos_poly(float r, float* s, float* c)
+{
+    const float r2 = r * r;
+    if (kShort) {
+        *s = fmaf(fmaf(r2, 1.0f / 120.0f, -1.0f / 6.0f) * r2, r, r);
+        *c = fmaf(fmaf(fmaf(r2, -1.0f / 720.0f, 1.0f / 24.0f), r2, -0.5f), r2, 1.0f);
+        return;
+    }
+    float sp = fmaf(r2, 1.0f / 362880.0f, -1.0f / 5040.0f);
+    sp = fmaf(sp, r2, 1.0f / 120.0f);
+    sp = fmaf(sp, r2, -1.0f / 6.0f);
+    *s = fmaf(sp * r2, r, r);
+    float cp = fmaf(r2, -1.0f / 3628800.0f, 1.0f / 40320.0f);
+    cp = fmaf(cp, r2, -1.0f / 720.0f);
+    cp = fmaf(cp, r2, 1.0f / 24.0f);
+    cp = fmaf(cp, r2, -0.5f);
+    *c = fmaf(cp, r2, 1.0f);
+}
+
 // sin and cos of |x| <~ 100: Cody-Waite reduction by pi/2 (two-term split of pi/2, the first
 // product exact inside the FMA), then the Taylor polynomials of sin (to r^9/9!) and cos (to
 // r^10/10!) on |r| <= pi/4 (truncation < 2e-9), rotated by the quadrant.
@@ -136,10 +158,13 @@ constexpr float kSincShortX = 0.1f;
 //   1 - D = 2i sin x e^{-ix}, 1 - D^2 = 2i sin 2x e^{-2ix} (no 1 - cos), and
 //   X + Y + Z = (1 - D^2)(1 - D) sum_arms g_a [sinc(x(1 + k.n)) - sinc(x(1 - k.n))],
 // so T = (X + Y + Z)/sqrt3 is formed from sinc differences computed without cancellation.
-// Spacecraft offsets from the guiding centre are u_i L/sqrt3 (|u_i - u_j| = sqrt3); the walker
-// carries k/sqrt3 and P/3 (WalkerF), so k.n = (k/sqrt3).(u_j - u_i), n.P.n = (u_j - u_i).(P/3).
-// (u_j - u_i) and pi f (L + k.(p_i + p_j)) = x (1 + (k/sqrt3).(u_i + u_j)).  The common factors
-// (1 - D^2, the one-link -x, scale and the A/E/T normalisations) multiply once at the end:
+// Spacecraft offsets from the guiding centre are u_i L/sqrt3 (|u_i - u_j| = sqrt3,
+// u_0 + u_1 + u_2 = 0); the walker carries k/sqrt3 and P/3 (WalkerF), so with
+// kappa_m = (k/sqrt3).u_m: k.n = kappa_j - kappa_i and n.P.n = (u_j - u_i).(P/3).(u_j - u_i) on
+// the arm from i to j, whose one-link phase pi f (L + k.(p_i + p_j)) is x - q_m, q_m = x kappa_m
+// for the third spacecraft m (q_0 + q_1 + q_2 = 0, |q_m| <= x/sqrt3): e^{i q_m} for m = 0, 1
+// from their polynomials, the third the conjugate of their product.  Common factors (1 - D^2,
+// the one-link -x, e^{-ix}, scale and the A/E/T normalisations) multiply once at the end:
 //   X = (1 - D^2) [(y21 - y31) + D (y12 - y13)] and cyclic.
 __device__ inline void transfer_f32(const WalkerF& w, const float* Kp, const float* Kc, float f, float sa,
                                     float ca, float scale, float s1, float c1, cf T[3])
@@ -156,26 +181,39 @@ __device__ inline void transfer_f32(const WalkerF& w, const float* Kp, const flo
         u[i][2] = -h3 * cp[i];
     }
     const float x = (float)kPi * armS * f;
+    float kap[3];
+#pragma unroll
+    for (int m = 0; m < 2; ++m) kap[m] = w.k[0] * u[m][0] + w.k[1] * u[m][1] + w.k[2] * u[m][2];
+    kap[2] = -(kap[0] + kap[1]);
+    const bool shrt = x < kSincShortX;   // uniform over a warp but for the rounds that straddle 0.1
+    cf E[3];                             // e^{i q_m}
+    if (shrt) {
+        sincos_poly<true>(x * kap[0], &E[0].im, &E[0].re);
+        sincos_poly<true>(x * kap[1], &E[1].im, &E[1].re);
+    } else if (x < 1.36f) {              // |q_m| <= x/sqrt3 < pi/4
+        sincos_poly<false>(x * kap[0], &E[0].im, &E[0].re);
+        sincos_poly<false>(x * kap[1], &E[1].im, &E[1].re);
+    } else {
+        sincos_small(x * kap[0], &E[0].im, &E[0].re);
+        sincos_small(x * kap[1], &E[1].im, &E[1].re);
+    }
+    const cf e01 = fmul(E[0], E[1]);
+    E[2] = {e01.re, -e01.im};
     cf yf[3], yb[3], tsum = {0.0f, 0.0f};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const int i = a, j = (a + 1) % 3;
-        float d[3], kn = 0.0f, ks = 0.0f;
+        const int i = a, j = (a + 1) % 3, m = (a + 2) % 3;
+        float d[3];
 #pragma unroll
-        for (int m = 0; m < 3; ++m) {
-            d[m] = u[j][m] - u[i][m];
-            kn += w.k[m] * d[m];
-            ks += w.k[m] * (u[i][m] + u[j][m]);
-        }
+        for (int q = 0; q < 3; ++q) d[q] = u[j][q] - u[i][q];
+        const float kn = kap[j] - kap[i];
         const float np = nPnf(w.Pp, d), nc = nPnf(w.Pc, d);
         const cf F = {np * Kp[0] + nc * Kc[0], np * Kp[1] + nc * Kc[1]};
-        float sph, cph;
-        sincos_small(x * (1.0f + ks), &sph, &cph);
-        const cf g = fmul({sph, cph}, F);
+        const cf g = fmul({-E[m].im, E[m].re}, F);   // i e^{i q_m} F
         // sinc(x(1 + k.n)) = sinc(x(1 - k.n)) + the difference (which T needs on its own);
         // the sum is off by at most an ulp of the larger term, like a direct evaluation
         float sm, sd;
-        if (x < kSincShortX) {   // uniform over a warp but for the rounds that straddle 0.1
+        if (shrt) {
             const float b = x * (1.0f - kn);
             sm = sinc_series<4>(b * b);
             sd = sinc_diff_series<4>(x, kn);
@@ -191,8 +229,9 @@ __device__ inline void transfer_f32(const WalkerF& w, const float* Kp, const flo
     const float s2 = 2.0f * s1 * c1, c2 = 1.0f - 2.0f * s1 * s1;   // sin 2x, cos 2x
     const cf D = {c2, -s2};
     const cf W1 = {2.0f * s1 * s1, 2.0f * s1 * c1};                 // 1 - D
-    const float w2 = -x * scale * 2.0f * s2;                        // 1 - D^2 = 2 sin 2x (s2, c2)
-    const cf W2 = {w2 * s2, w2 * c2};                               // times -x scale
+    // (1 - D^2) (-x) e^{-ix} scale = -2 x scale sin 2x (sin 3x, cos 3x)
+    const float w2 = -x * scale * 2.0f * s2;
+    const cf W2 = {w2 * (s2 * c1 + c2 * s1), w2 * (c2 * c1 - s2 * s1)};
     const cf Xp = fadd(fsub(y21, y31), fmul(D, fsub(y12, y13)));
     const cf Yp = fadd(fsub(y32, y12), fmul(D, fsub(y23, y21)));
     const cf Zp = fadd(fsub(y13, y23), fmul(D, fsub(y31, y32)));
