@@ -27,11 +27,11 @@ struct MixEdge {
     float2 h0inv[3];
     float4 xs;   // sin x, cos x (x = pi f L/c, the one-link phase), f^{-7/6}, 0
 };
-// Bin record of the mixed-precision heterodyne: float32 summary data and 1/(f_hi - f_lo).
+// Bin record of the mixed-precision heterodyne: float32 summary data per channel with the
+// contraction's factors folded in (q0/2, q1/2, q2/w, q3/w, q4/4, q5/w; w = f_hi - f_lo).
 struct MixBin {
     float q[18];
-    float invw;
-    float pad;
+    float pad[2];
 };
 
 // per (edge, mode) of a higher-mode reference: Phi0_lm (float pair), u = h0_lm/h0 and

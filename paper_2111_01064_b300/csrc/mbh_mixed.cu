@@ -941,16 +941,20 @@ __global__ void edge_mixed_hm_kernel(const double* __restrict__ theta0, double t
     }
 }
 
+// Bin records: the summary data of each channel with the contraction's constant factors folded
+// in (float64, rounded once): from (A0, A1, B0, B1) as (q0, q1, q2, q3, q4, q5) and w = f_hi - f_lo,
+// (q0/2, q1/2, q2/w, q3/w, q4/4, q5/w) for contract_bin.
 __global__ void bin_mixed_kernel(const double* __restrict__ summary, const double* __restrict__ invw,
                                  int E, MixBin* __restrict__ out, double* __restrict__ sums)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b < E) {
         MixBin m;
+        const double iw = invw[b];
+        const double fold[6] = {0.5, 0.5, iw, iw, 0.25, iw};
 #pragma unroll
-        for (int j = 0; j < 18; ++j) m.q[j] = (float)summary[(int64_t)b * 18 + j];
-        m.invw = (float)invw[b];
-        m.pad = 0.0f;
+        for (int j = 0; j < 18; ++j) m.q[j] = (float)(summary[(int64_t)b * 18 + j] * fold[j % 6]);
+        m.pad[0] = m.pad[1] = 0.0f;
         out[b] = m;
     }
     if (b == 0) {
@@ -991,6 +995,26 @@ cudaError_t mbh::prepare_mixed_tables(mbh_ref* R, cudaStream_t st)
         R->mix.hm_base = R->mix_hm_base;
     }
     return e;
+}
+
+// Contribution of one bin to <d|h> and <h|h> (Eqs. 14, 17, without the 4 and the "1" parts), from delta at
+// its low (dp) and high (dl) edge: with d0 = (dp + dl)/2, d1 = (dl - dp)/w per channel,
+//   <d|h>: q0 d0r + q1 d0i + q2 d1r + q3 d1i,
+//   <h|h>: q4 (2 d0r + |d0|^2) + 2 q5 (d1r + Re(d0 conj(d1)))   [first order, Eq. 17 as printed]
+// evaluated in s = dp + dl, t = dl - dp with the record's folded factors (bin_mixed_kernel).
+__device__ __forceinline__ void contract_bin(const MixBin& mb, const cf dp[3], const cf dl[3], float& bd,
+                                             float& bh)
+{
+    bd = 0.0f;
+    bh = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float sr = dp[c].re + dl[c].re, si = dp[c].im + dl[c].im;
+        const float tr = dl[c].re - dp[c].re, ti = dl[c].im - dp[c].im;
+        const float* q = mb.q + 6 * c;
+        bd = fmaf(q[0], sr, fmaf(q[1], si, fmaf(q[2], tr, fmaf(q[3], ti, bd))));
+        bh = fmaf(q[4], fmaf(si, si, sr * (4.0f + sr)), fmaf(q[5], fmaf(si, ti, tr * (2.0f + sr)), bh));
+    }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1061,18 +1085,8 @@ __device__ __forceinline__ void het_mixed_body(const HetLaunch& L)
                 carry[c].im = __shfl_sync(0xffffffffu, dl[c].im, G - 1, G);
             }
             if (active && e >= 1 && e <= E) {
-                const MixBin& mb = S.mix.bin[e - 1];
-                const float iw = mb.invw;
-                float bd = 0.0f, bh = 0.0f;
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const float d0r = 0.5f * (dp[c].re + dl[c].re), d0i = 0.5f * (dp[c].im + dl[c].im);
-                    const float d1r = (dl[c].re - dp[c].re) * iw, d1i = (dl[c].im - dp[c].im) * iw;
-                    const float* q = mb.q + 6 * c;
-                    bd += q[0] * d0r + q[1] * d0i + q[2] * d1r + q[3] * d1i;
-                    bh += q[4] * (2.0f * d0r + d0r * d0r + d0i * d0i) +
-                          2.0f * q[5] * (d1r + d0r * d1r + d0i * d1i);
-                }
+                float bd, bh;
+                contract_bin(S.mix.bin[e - 1], dp, dl, bd, bh);
                 df_acc(adh, {bd, 0.0f});
                 df_acc(ahh, {bh, 0.0f});
             }
@@ -1182,18 +1196,8 @@ __global__ void __launch_bounds__(BLOCK)
                 carry[c].im = __shfl_sync(0xffffffffu, dl[c].im, G - 1, G);
             }
             if (active && e >= 1 && e <= E) {
-                const MixBin& mb = S.mix.bin[e - 1];
-                const float iw = mb.invw;
-                float bd = 0.0f, bh = 0.0f;
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const float d0r = 0.5f * (dp[c].re + dl[c].re), d0i = 0.5f * (dp[c].im + dl[c].im);
-                    const float d1r = (dl[c].re - dp[c].re) * iw, d1i = (dl[c].im - dp[c].im) * iw;
-                    const float* qq = mb.q + 6 * c;
-                    bd += qq[0] * d0r + qq[1] * d0i + qq[2] * d1r + qq[3] * d1i;
-                    bh += qq[4] * (2.0f * d0r + d0r * d0r + d0i * d0i) +
-                          2.0f * qq[5] * (d1r + d0r * d1r + d0i * d1i);
-                }
+                float bd, bh;
+                contract_bin(S.mix.bin[e - 1], dp, dl, bd, bh);
                 df_acc(adh, {bd, 0.0f});
                 df_acc(ahh, {bh, 0.0f});
             }
@@ -1293,18 +1297,8 @@ __device__ __forceinline__ void het_mixed_pt_body(const HetLaunch& L)
                 carry[c].im = __shfl_sync(0xffffffffu, dl[c].im, G - 1, G);
             }
             if (active && e >= 1 && e <= E) {
-                const MixBin& mb = S.mix.bin[e - 1];
-                const float iw = mb.invw;
-                float bd = 0.0f, bh = 0.0f;
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const float d0r = 0.5f * (dp[c].re + dl[c].re), d0i = 0.5f * (dp[c].im + dl[c].im);
-                    const float d1r = (dl[c].re - dp[c].re) * iw, d1i = (dl[c].im - dp[c].im) * iw;
-                    const float* qq = mb.q + 6 * c;
-                    bd += qq[0] * d0r + qq[1] * d0i + qq[2] * d1r + qq[3] * d1i;
-                    bh += qq[4] * (2.0f * d0r + d0r * d0r + d0i * d0i) +
-                          2.0f * qq[5] * (d1r + d0r * d1r + d0i * d1i);
-                }
+                float bd, bh;
+                contract_bin(S.mix.bin[e - 1], dp, dl, bd, bh);
                 df_acc(adh, {bd, 0.0f});
                 df_acc(ahh, {bh, 0.0f});
             }
