@@ -25,7 +25,7 @@ constexpr int kDefaultBlock = 128;
 struct MixEdge {
     float2 f, f3, fm3, lnf3, phi0;
     float2 h0inv[3];
-    float4 xs;   // sin x, cos x (x = pi f L/c, the one-link phase), f^{-7/6}, 0
+    float4 xs;   // sin x, cos x (x = pi f L/c, the one-link phase), 0, x
 };
 // Bin record of the mixed-precision heterodyne: float32 summary data per channel with the
 // contraction's factors folded in (q0/2, q1/2, q2/w, q3/w, q4/4, q5/w; w = f_hi - f_lo).
@@ -49,6 +49,7 @@ struct MixTables {
     double sumB0;          // sum_b sum_c B0
     const MixModeHM* hm;   // [E+1][6] (higher-mode references)
     const float* hm_base;  // [E+1][3]: -1 where h0 = 0, else 0
+    double amp_eps0;       // relative rounding of the reference's float32 amplitude factor
 };
 
 struct PrepItem {

@@ -42,6 +42,9 @@ struct WalkerF {
     float k[3], Pp[6], Pc[6], Kp[2], Kc[2];
     float sa_ref, ca_ref, amp, inv_fc2;
     float amp76;   // amp (pi M)^{-7/6}: times f^{-7/6} of an edge table gives amp v^{-7/2}
+    // relative rounding errors (exact/float - 1) of amp and amp76: a pure scale of the whole
+    // template, which the heterodyne kernels undo exactly at the end (amp_fix)
+    float eps_amp, eps_amp76;
 };
 
 __device__ __forceinline__ float nPnf(const float* P, const float* n)
@@ -166,10 +169,15 @@ constexpr float kSincShortX = 0.1f;
 // from their polynomials, the third the conjugate of their product.  Common factors (1 - D^2,
 // the one-link -x, e^{-ix}, scale and the A/E/T normalisations) multiply once at the end:
 //   X = (1 - D^2) [(y21 - y31) + D (y12 - y13)] and cyclic.
-__device__ inline void transfer_f32(const WalkerF& w, const float* Kp, const float* Kc, float f, float sa,
+// With kRaw every factor that depends on the frequency alone is left out (and `scale` is not
+// applied): T_A = Z' - X', T_E = X' + Z' - 2Y', T_T = sum_arms g_a [sinc differences] with
+// X' = X/(1 - D^2) etc.  The heterodyne folds the rest, per edge and channel, into its
+// float64-formed 1/h0 (so that no float32 rounding of a per-edge or constant factor is shared
+// by every walker's template, which would bias the whole batch).
+template <bool kRaw = false>
+__device__ inline void transfer_f32(const WalkerF& w, const float* Kp, const float* Kc, float x, float sa,
                                     float ca, float scale, float s1, float c1, cf T[3])
 {
-    constexpr float armS = (float)kArmSec;
     constexpr float h3 = (float)(0.5 * kSqrt3);
     const float sp[3] = {sa, -0.5f * sa - h3 * ca, -0.5f * sa + h3 * ca};
     const float cp[3] = {ca, -0.5f * ca + h3 * sa, -0.5f * ca - h3 * sa};
@@ -180,7 +188,6 @@ __device__ inline void transfer_f32(const WalkerF& w, const float* Kp, const flo
         u[i][1] = sp[i] * ca - 0.5f * cp[i] * sa;
         u[i][2] = -h3 * cp[i];
     }
-    const float x = (float)kPi * armS * f;
     float kap[3];
 #pragma unroll
     for (int m = 0; m < 2; ++m) kap[m] = w.k[0] * u[m][0] + w.k[1] * u[m][1] + w.k[2] * u[m][2];
@@ -228,25 +235,32 @@ __device__ inline void transfer_f32(const WalkerF& w, const float* Kp, const flo
     const cf y12 = yf[0], y21 = yb[0], y23 = yf[1], y32 = yb[1], y31 = yf[2], y13 = yb[2];
     const float s2 = 2.0f * s1 * c1, c2 = 1.0f - 2.0f * s1 * s1;   // sin 2x, cos 2x
     const cf D = {c2, -s2};
-    const cf W1 = {2.0f * s1 * s1, 2.0f * s1 * c1};                 // 1 - D
-    // (1 - D^2) (-x) e^{-ix} scale = -2 x scale sin 2x (sin 3x, cos 3x)
-    const float w2 = -x * scale * 2.0f * s2;
-    const cf W2 = {w2 * (s2 * c1 + c2 * s1), w2 * (c2 * c1 - s2 * s1)};
     const cf Xp = fadd(fsub(y21, y31), fmul(D, fsub(y12, y13)));
     const cf Yp = fadd(fsub(y32, y12), fmul(D, fsub(y23, y21)));
     const cf Zp = fadd(fsub(y13, y23), fmul(D, fsub(y31, y32)));
-    T[0] = fmul(fscale(W2, (float)(1.0 / kSqrt2)), fsub(Zp, Xp));
-    T[1] = fmul(fscale(W2, (float)(1.0 / kSqrt6)), fsub(fadd(Xp, Zp), fscale(Yp, 2.0f)));
-    T[2] = fmul(fscale(fmul(W2, W1), (float)(1.0 / kSqrt3)), tsum);
+    if (kRaw) {
+        T[0] = fsub(Zp, Xp);
+        T[1] = fsub(fadd(Xp, Zp), fscale(Yp, 2.0f));
+        T[2] = tsum;
+    } else {
+        const cf W1 = {2.0f * s1 * s1, 2.0f * s1 * c1};   // 1 - D
+        // (1 - D^2) (-x) e^{-ix} scale = -2 x scale sin 2x (sin 3x, cos 3x)
+        const float w2 = -x * scale * 2.0f * s2;
+        const cf W2 = {w2 * (s2 * c1 + c2 * s1), w2 * (c2 * c1 - s2 * s1)};
+        T[0] = fmul(fscale(W2, (float)(1.0 / kSqrt2)), fsub(Zp, Xp));
+        T[1] = fmul(fscale(W2, (float)(1.0 / kSqrt6)), fsub(fadd(Xp, Zp), fscale(Yp, 2.0f)));
+        T[2] = fmul(fscale(fmul(W2, W1), (float)(1.0 / kSqrt3)), tsum);
+    }
 }
 
 // the same with sin x, cos x of the one-link phase x = pi f L/c computed here
 __device__ __forceinline__ void transfer_f32(const WalkerF& w, const float* Kp, const float* Kc, float f,
                                              float sa, float ca, float scale, cf T[3])
 {
+    const float x = (float)kPi * (float)kArmSec * f;
     float s1, c1;
-    sincos_small((float)kPi * (float)kArmSec * f, &s1, &c1);
-    transfer_f32(w, Kp, Kc, f, sa, ca, scale, s1, c1, T);
+    sincos_small(x, &s1, &c1);
+    transfer_f32<false>(w, Kp, Kc, x, sa, ca, scale, s1, c1, T);
 }
 
 constexpr f2 kTwoPiDF = df_const(kTwoPi);
@@ -373,8 +387,11 @@ __device__ inline void walker_setup_mixed(const double* __restrict__ theta, int6
     //   = pi sqrt(2/3) M^2 sqrt(eta) / D v^{-7/2} exp(-(f/fc)^2)
     const double dist = (double)dl * (1e9 * kParsec / kClight);
     const double ampd = kPi * 0.816496580927726 /* sqrt(2/3) */ * M * M * sqrt(eta) / dist;
+    const double amp76d = ampd * (icb * icb * icb) * sqrt(icb);   // (pi M)^{-7/6} = icb^{7/2}
     wf.amp = (float)ampd;
-    wf.amp76 = (float)(ampd * (icb * icb * icb) * sqrt(icb));   // (pi M)^{-7/6} = icb^{7/2}
+    wf.amp76 = (float)amp76d;
+    wf.eps_amp = (float)(ampd - (double)wf.amp) / wf.amp;
+    wf.eps_amp76 = (float)(amp76d - (double)wf.amp76) / wf.amp76;
     wf.inv_fc2 = (float)(400.0 * M * M);   // 1/f_c^2, f_c = 0.05/M
     wf.sa_ref = (float)sa;
     wf.ca_ref = (float)ca;
@@ -421,10 +438,11 @@ __device__ __forceinline__ f2 ld_f2(float2 v) { return {v.x, v.y}; }
 // Large phase Phi(f) (double-float) and float32 amplitude and orbit angle from the
 // frequency tables.  Returns false outside the support (f > f_cut or t(f) outside [0, t_obs]);
 // with kAlways the phase is computed there as well (a reference phase defined at every edge).
+// With kTab the amplitude leaves out f^{-7/6} (amp76 e^{-(f/f_c)^2}), which the heterodyne folds
+// into its edge records.
 template <bool kAlways = false, bool kTab = false>
 __device__ __forceinline__ bool phase_df(const WalkerDF& w, const WalkerF& wf, const FreqDF& q,
-                                         f2 t_obs, f2& Phi, float& sa, float& ca, float& amp,
-                                         float fm76 = 0.0f)
+                                         f2 t_obs, f2& Phi, float& sa, float& ca, float& amp)
 {
     const f2 v = dd_mul(w.cbrt_piM, q.f3);
     const f2 iv = dd_mul(w.icbrt_piM, q.fm3);
@@ -456,8 +474,8 @@ __device__ __forceinline__ bool phase_df(const WalkerDF& w, const WalkerF& wf, c
     sa = dd_to_float(sa_d);
     ca = dd_to_float(ca_d);
     const float ff = q.f.hi;
-    if (kTab) {   // f^{-7/6} from the edge table
-        amp = wf.amp76 * fm76 * expf(-ff * ff * wf.inv_fc2);
+    if (kTab) {   // f^{-7/6} is folded into the edge table's 1/h0
+        amp = wf.amp76 * expf(-ff * ff * wf.inv_fc2);
     } else {
         const float ivf = iv.hi;
         amp = wf.amp * ivf * ivf * ivf * sqrtf(ivf) * expf(-ff * ff * wf.inv_fc2);
@@ -800,7 +818,7 @@ cudaError_t mbh::alloc_ref_tables(mbh_ref* R)
     if (e == cudaSuccess) e = cudaMalloc(&R->h0inv, sizeof(double2) * 3 * (E + 1));
     if (e == cudaSuccess) e = cudaMalloc(&R->mix_edge, sizeof(MixEdge) * (E + 1));
     if (e == cudaSuccess) e = cudaMalloc(&R->mix_bin, sizeof(MixBin) * E);
-    if (e == cudaSuccess) e = cudaMalloc(&R->mix_sums, sizeof(double) * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&R->mix_sums, sizeof(double) * 3);
     return e;
 }
 
@@ -819,24 +837,33 @@ void mbh::free_ref_tables(mbh_ref* R)
     if (R->mix_hm_base) cudaFree(R->mix_hm_base);
 }
 
-// frequency-only factors of an edge, rounded once from float64: sin and cos of the one-link
-// phase x = pi f L/c, and f^{-7/6}
+// frequency-only inputs of an edge, rounded once from float64: sin and cos of the one-link
+// phase x = pi f L/c, and x
 __device__ __forceinline__ float4 edge_xs(double f)
 {
+    const double x = kPi * kArmSec * f;
     double s, c;
-    sincos(kPi * kArmSec * f, &s, &c);
-    return make_float4((float)s, (float)c, (float)pow(f, -7.0 / 6.0), 0.0f);
+    sincos(x, &s, &c);
+    return make_float4((float)s, (float)c, 0.0f, (float)x);
 }
 
-// Edge records of the reference, using the same mixed-precision functions (and the same edge
-// table values) as the walkers so that a walker equal to the reference gets dPhi = 0 and
-// rho = 1 up to one rounding.
+// Edge records of the reference: its large phase Phi0 from the same double-float chain and edge
+// tables as the walkers (so that Phi - Phi0 cancels exactly for the reference itself), and
+// 1/H0 with H0 = h0 e^{+i Phi0}, h0 the float64 reference template at the edge: the walkers'
+// ratio r = H e^{-i(Phi - Phi0)}/H0 is then h/h0 with the exact h0.  (An H0 from the walkers'
+// own float32 chain would put its rounding into the ratio of every walker alike: a bias of
+// ~1e-7 of <h|h> shared by the whole batch.)
 __global__ void edge_mixed_kernel(const double* __restrict__ theta0, double t_obs,
-                                  const double* __restrict__ fe, int n_edges, MixEdge* __restrict__ out)
+                                  const double* __restrict__ fe, int n_edges,
+                                  const double2* __restrict__ h0e, MixEdge* __restrict__ out,
+                                  double* __restrict__ eps0)
 {
     __shared__ WalkerDF wd;
     __shared__ WalkerF wf;
-    if (threadIdx.x == 0) walker_setup_mixed(theta0, 1, 0, wd, wf);
+    if (threadIdx.x == 0) {
+        walker_setup_mixed(theta0, 1, 0, wd, wf);
+        *eps0 = 0.0;   // h0 is exact: no float32 amplitude on the reference side
+    }
     __syncthreads();
     const f2 tob = split_d(t_obs);
     for (int e = threadIdx.x; e < n_edges; e += blockDim.x) {
@@ -849,18 +876,33 @@ __global__ void edge_mixed_kernel(const double* __restrict__ theta0, double t_ob
         m.xs = edge_xs(fe[e]);
         f2 Phi = {0.0f, 0.0f};
         float sa, ca, amp;
-        const bool in = phase_df<false, true>(wd, wf, q, tob, Phi, sa, ca, amp, m.xs.z);
-        cf T[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-        if (in) transfer_f32(wf, wf.Kp, wf.Kc, q.f.hi, sa, ca, amp, m.xs.x, m.xs.y, T);
-        m.phi0 = in ? make_float2(Phi.hi, Phi.lo) : make_float2(0.f, 0.f);
+        phase_df<true, true>(wd, wf, q, tob, Phi, sa, ca, amp);   // defined at every edge
+        m.phi0 = make_float2(Phi.hi, Phi.lo);
+        double sp, cp;
+        sincos((double)Phi.hi + (double)Phi.lo, &sp, &cp);
+        // frequency-only factors of the template (transfer_f32<true> and phase_df<.., true>):
+        // W = (1 - D^2)(-x) e^{-ix} = -2 x sin 2x (sin 3x, cos 3x), 1 - D = 2 sin x (sin x, cos x),
+        // K_A = W/sqrt2, K_E = W/sqrt6, K_T = W (1 - D)/sqrt3, all times f^{-7/6}
+        const double x = kPi * kArmSec * fe[e];
+        double s1, c1, s3, c3;
+        sincos(x, &s1, &c1);
+        sincos(3.0 * x, &s3, &c3);
+        const double wm = -2.0 * x * (2.0 * s1 * c1) * pow(fe[e], -7.0 / 6.0);
+        const double wr = wm * s3, wi = wm * c3;
+        const double ar = 2.0 * s1 * s1, ai = 2.0 * s1 * c1;
+        const double2 K[3] = {make_double2(wr / kSqrt2, wi / kSqrt2), make_double2(wr / kSqrt6, wi / kSqrt6),
+                              make_double2((wr * ar - wi * ai) / kSqrt3, (wr * ai + wi * ar) / kSqrt3)};
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             // 1/H0 in float64: |H0| is ~1e-20..1e-30 in strain units, so |H0|^2 underflows
             // float32, while 1/H0 itself (~1e20..1e30) is a normal float32
-            const cf H = in ? T[c] : cf{0.0f, 0.0f};
-            const double hr = (double)H.re, hi = (double)H.im;
+            // times the factors the walkers' raw transfer and amplitude leave out (K below)
+            const double2 h = h0e[e * 3 + c];
+            const double hr = h.x * cp - h.y * sp, hi = h.x * sp + h.y * cp;
             const double m2 = hr * hr + hi * hi;
-            m.h0inv[c] = m2 > 0.0 ? make_float2((float)(hr / m2), (float)(-hi / m2)) : make_float2(0.f, 0.f);
+            const double ir = hr / m2, ii = -hi / m2;
+            m.h0inv[c] = m2 > 0.0 ? make_float2((float)(K[c].x * ir - K[c].y * ii), (float)(K[c].x * ii + K[c].y * ir))
+                                  : make_float2(0.f, 0.f);
         }
         out[e] = m;
     }
@@ -875,7 +917,8 @@ __global__ void edge_mixed_kernel(const double* __restrict__ theta0, double t_ob
 // support contributes -u.
 __global__ void edge_mixed_hm_kernel(const double* __restrict__ theta0, double t_obs, uint32_t modes,
                                      const double* __restrict__ fe, int n_edges, MixEdge* __restrict__ out,
-                                     MixModeHM* __restrict__ hm, float* __restrict__ base)
+                                     MixModeHM* __restrict__ hm, float* __restrict__ base,
+                                     double* __restrict__ eps0)
 {
     __shared__ WalkerDF wd;
     __shared__ WalkerF wf;
@@ -883,6 +926,7 @@ __global__ void edge_mixed_hm_kernel(const double* __restrict__ theta0, double t
     if (threadIdx.x == 0) {
         walker_setup_mixed(theta0, 1, 0, wd, wf);
         walker_setup_hm(theta0, 1, 0, wh);
+        *eps0 = (double)wf.eps_amp;   // the mode records use amp (generic chain)
     }
     __syncthreads();
     const f2 tob = split_d(t_obs);
@@ -912,8 +956,8 @@ __global__ void edge_mixed_hm_kernel(const double* __restrict__ theta0, double t
                 sincos(-ph, &ei[b], &er[b]);   // e^{-i Phi0_lm}
                 if (in) {
                     cf T[3];
-                    transfer_f32(wf, &wh.hk[b][0], &wh.hk[b][2], q.f.hi, sa, ca, amp * mode_vpow(wd, q2, b),
-                                 me.xs.x, me.xs.y, T);
+                    transfer_f32<false>(wf, &wh.hk[b][0], &wh.hk[b][2], me.xs.w, sa, ca, amp * mode_vpow(wd, q2, b),
+                                        me.xs.x, me.xs.y, T);
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         const double Hr = (double)T[c].re, Hi = (double)T[c].im;
@@ -973,17 +1017,18 @@ cudaError_t mbh::prepare_mixed_tables(mbh_ref* R, cudaStream_t st)
 {
     const int E = R->E;
     if (R->modes == 1u) {
-        edge_mixed_kernel<<<1, 256, 0, st>>>(R->theta0_dev, R->grid.t_obs, R->fe, E + 1, R->mix_edge);
+        edge_mixed_kernel<<<1, 256, 0, st>>>(R->theta0_dev, R->grid.t_obs, R->fe, E + 1, R->h0e,
+                                             R->mix_edge, R->mix_sums + 2);
     } else {
         cudaError_t e = cudaMalloc(&R->mix_hm, sizeof(MixModeHM) * kHmModes * (E + 1));
         if (e == cudaSuccess) e = cudaMalloc(&R->mix_hm_base, sizeof(float) * 3 * (E + 1));
         if (e != cudaSuccess) return e;
         edge_mixed_hm_kernel<<<1, 128, 0, st>>>(R->theta0_dev, R->grid.t_obs, R->modes, R->fe, E + 1,
-                                                R->mix_edge, R->mix_hm, R->mix_hm_base);
+                                                R->mix_edge, R->mix_hm, R->mix_hm_base, R->mix_sums + 2);
     }
     bin_mixed_kernel<<<(E + 127) / 128, 128, 0, st>>>(R->summary, R->invw, E, R->mix_bin, R->mix_sums);
     cudaError_t e = cudaGetLastError();
-    double sums[2];
+    double sums[3];
     if (e == cudaSuccess) e = cudaMemcpyAsync(sums, R->mix_sums, sizeof sums, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e == cudaSuccess) {
@@ -993,6 +1038,7 @@ cudaError_t mbh::prepare_mixed_tables(mbh_ref* R, cudaStream_t st)
         R->mix.sumB0 = sums[1];
         R->mix.hm = R->mix_hm;
         R->mix.hm_base = R->mix_hm_base;
+        R->mix.amp_eps0 = sums[2];
     }
     return e;
 }
@@ -1015,6 +1061,15 @@ __device__ __forceinline__ void contract_bin(const MixBin& mb, const cf dp[3], c
         bd = fmaf(q[0], sr, fmaf(q[1], si, fmaf(q[2], tr, fmaf(q[3], ti, bd))));
         bh = fmaf(q[4], fmaf(si, si, sr * (4.0f + sr)), fmaf(q[5], fmaf(si, ti, tr * (2.0f + sr)), bh));
     }
+}
+
+// The float32 amplitude factors of the walker and of the reference scale the whole of h and h0,
+// so their rounding is a common factor of every ratio r = h/h0: <d|h> (linear in r) is off by
+// amp_fix and <h|h> (quadratic) by its square, which the epilogue removes in float64.  Left in,
+// this coherent error dominates |dlnL| for walkers far from the reference.
+__device__ __forceinline__ double amp_fix(float eps_walker, double eps_ref)
+{
+    return (1.0 + (double)eps_walker) / (1.0 + eps_ref);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1058,15 +1113,15 @@ __device__ __forceinline__ void het_mixed_body(const HetLaunch& L)
                 const FreqDF q = {ld_f2(me.f), ld_f2(me.f3), ld_f2(me.fm3), ld_f2(me.lnf3)};
                 f2 Phi;
                 float sa, ca, amp;
-                if (phase_df<false, true>(wsd[lw], wsf[lw], q, tob, Phi, sa, ca, amp, me.xs.z)) {
+                if (phase_df<false, true>(wsd[lw], wsf[lw], q, tob, Phi, sa, ca, amp)) {
                     float sh, ch;
                     sincos_small(0.5f * reduce_phase(dd_sub(Phi, ld_f2(me.phi0))), &sh, &ch);
                     const cf em1 = {-2.0f * sh * sh, -2.0f * sh * ch};   // e^{-i dPhi} - 1
                     cf T[3];
-                    transfer_f32(wsf[lw], wsf[lw].Kp, wsf[lw].Kc, q.f.hi, sa, ca, amp, me.xs.x, me.xs.y, T);
+                    transfer_f32<true>(wsf[lw], wsf[lw].Kp, wsf[lw].Kc, me.xs.w, sa, ca, 1.0f, me.xs.x, me.xs.y, T);
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
-                        const cf rho = fmul(T[c], {me.h0inv[c].x, me.h0inv[c].y});
+                        const cf rho = fmul(fscale(T[c], amp), {me.h0inv[c].x, me.h0inv[c].y});
                         const cf rm1 = {rho.re - 1.0f, rho.im};
                         dl[c] = fadd(fadd(rm1, fmul(rm1, em1)), em1);
                     }
@@ -1099,8 +1154,9 @@ __device__ __forceinline__ void het_mixed_body(const HetLaunch& L)
             df_acc(ahh, ohh);
         }
         if (active && lane == 0) {
-            const double dh = 4.0 * (S.mix.sumA0 + df_to_double(adh));
-            const double hh = 4.0 * (S.mix.sumB0 + df_to_double(ahh));
+            const double fix = amp_fix(wsf[lw].eps_amp76, S.mix.amp_eps0);
+            const double dh = 4.0 * (S.mix.sumA0 + df_to_double(adh)) * fix;
+            const double hh = 4.0 * (S.mix.sumB0 + df_to_double(ahh)) * (fix * fix);
             L.out[wi] = -0.5 * (S.dd + hh - 2.0 * dh);
             L.out[L.W + wi] = dh;
             L.out[2 * L.W + wi] = hh;
@@ -1172,8 +1228,8 @@ __global__ void __launch_bounds__(BLOCK)
                         sincos_small(0.5f * reduce_phase(dd_sub(mode_phase(Phi, b), ld_f2(mm.phi0))), &sh, &ch);
                         const cf em1 = {-2.0f * sh * sh, -2.0f * sh * ch};   // e^{-i dPhi} - 1
                         cf T[3];
-                        transfer_f32(wsf[lw], &wsh[lw].hk[b][0], &wsh[lw].hk[b][2], q.f.hi, sa, ca,
-                                     amp * mode_vpow(wsd[lw], q2, b), me.xs.x, me.xs.y, T);
+                        transfer_f32<false>(wsf[lw], &wsh[lw].hk[b][0], &wsh[lw].hk[b][2], me.xs.w, sa, ca,
+                                            amp * mode_vpow(wsd[lw], q2, b), me.xs.x, me.xs.y, T);
 #pragma unroll
                         for (int c = 0; c < 3; ++c) {
                             const cf u = {mm.u[c].x, mm.u[c].y};
@@ -1210,8 +1266,9 @@ __global__ void __launch_bounds__(BLOCK)
             df_acc(ahh, ohh);
         }
         if (active && lane == 0) {
-            const double dh = 4.0 * (S.mix.sumA0 + df_to_double(adh));
-            const double hh = 4.0 * (S.mix.sumB0 + df_to_double(ahh));
+            const double fix = amp_fix(wsf[lw].eps_amp, S.mix.amp_eps0);   // generic chain: amp
+            const double dh = 4.0 * (S.mix.sumA0 + df_to_double(adh)) * fix;
+            const double hh = 4.0 * (S.mix.sumB0 + df_to_double(ahh)) * (fix * fix);
             L.out[wi] = -0.5 * (S.dd + hh - 2.0 * dh);
             L.out[L.W + wi] = dh;
             L.out[2 * L.W + wi] = hh;
@@ -1270,15 +1327,15 @@ __device__ __forceinline__ void het_mixed_pt_body(const HetLaunch& L)
                 const FreqDF q = {ld_f2(me.f), ld_f2(me.f3), ld_f2(me.fm3), ld_f2(me.lnf3)};
                 f2 Phi;
                 float sa, ca, amp;
-                if (phase_df<false, true>(wsd[lw], wsf[lw], q, tob, Phi, sa, ca, amp, me.xs.z)) {
+                if (phase_df<false, true>(wsd[lw], wsf[lw], q, tob, Phi, sa, ca, amp)) {
                     float sh, ch;
                     sincos_small(0.5f * reduce_phase(dd_sub(Phi, ld_f2(me.phi0))), &sh, &ch);
                     const cf em1 = {-2.0f * sh * sh, -2.0f * sh * ch};
                     cf T[3];
-                    transfer_f32(wsf[lw], wsf[lw].Kp, wsf[lw].Kc, q.f.hi, sa, ca, amp, me.xs.x, me.xs.y, T);
+                    transfer_f32<true>(wsf[lw], wsf[lw].Kp, wsf[lw].Kc, me.xs.w, sa, ca, 1.0f, me.xs.x, me.xs.y, T);
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
-                        const cf rho = fmul(T[c], {me.h0inv[c].x, me.h0inv[c].y});
+                        const cf rho = fmul(fscale(T[c], amp), {me.h0inv[c].x, me.h0inv[c].y});
                         const cf rm1 = {rho.re - 1.0f, rho.im};
                         dl[c] = fadd(fadd(rm1, fmul(rm1, em1)), em1);
                     }
@@ -1311,8 +1368,9 @@ __device__ __forceinline__ void het_mixed_pt_body(const HetLaunch& L)
             df_acc(ahh, ohh);
         }
         if (active && lane == 0) {
-            const double dh = 4.0 * (S.mix.sumA0 + df_to_double(adh));
-            const double hh = 4.0 * (S.mix.sumB0 + df_to_double(ahh));
+            const double fix = amp_fix(wsf[lw].eps_amp76, S.mix.amp_eps0);
+            const double dh = 4.0 * (S.mix.sumA0 + df_to_double(adh)) * fix;
+            const double hh = 4.0 * (S.mix.sumB0 + df_to_double(ahh)) * (fix * fix);
             const double lnl = -0.5 * (S.dd + hh - 2.0 * dh);
             int32_t col;
             int t, cb;
