@@ -178,15 +178,19 @@ template <bool kRaw = false>
 __device__ inline void transfer_f32(const WalkerF& w, const float* Kp, const float* Kc, float x, float sa,
                                     float ca, float scale, float s1, float c1, cf T[3])
 {
+    // sqrt3/2 as a float pair: its float32 rounding alone would shorten the arms by ~2e-8 for
+    // every walker alike (a bias of the whole batch)
     constexpr float h3 = (float)(0.5 * kSqrt3);
-    const float sp[3] = {sa, -0.5f * sa - h3 * ca, -0.5f * sa + h3 * ca};
-    const float cp[3] = {ca, -0.5f * ca + h3 * sa, -0.5f * ca - h3 * sa};
+    constexpr float h3lo = (float)(0.5 * kSqrt3 - (double)h3);
+    const float h3s = fmaf(h3, sa, h3lo * sa), h3c = fmaf(h3, ca, h3lo * ca);
+    const float sp[3] = {sa, -0.5f * sa - h3c, -0.5f * sa + h3c};
+    const float cp[3] = {ca, -0.5f * ca + h3s, -0.5f * ca - h3s};
     float u[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         u[i][0] = -sp[i] * sa - 0.5f * cp[i] * ca;
         u[i][1] = sp[i] * ca - 0.5f * cp[i] * sa;
-        u[i][2] = -h3 * cp[i];
+        u[i][2] = -fmaf(h3, cp[i], h3lo * cp[i]);
     }
     float kap[3];
 #pragma unroll
