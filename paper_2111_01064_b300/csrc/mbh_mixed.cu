@@ -45,6 +45,7 @@ struct WalkerF {
     // relative rounding errors (exact/float - 1) of amp and amp76: a pure scale of the whole
     // template, which the heterodyne kernels undo exactly at the end (amp_fix)
     float eps_amp, eps_amp76;
+    float Klo[4];   // Kp, Kc - their float32 values (the (2,2) mode factors as float pairs)
 };
 
 __device__ __forceinline__ float nPnf(const float* P, const float* n)
@@ -174,9 +175,11 @@ constexpr float kSincShortX = 0.1f;
 // X' = X/(1 - D^2) etc.  The heterodyne folds the rest, per edge and channel, into its
 // float64-formed 1/h0 (so that no float32 rounding of a per-edge or constant factor is shared
 // by every walker's template, which would bias the whole batch).
+// Klo (or nullptr): the low parts of Kp and Kc as float pairs (Kp_lo[2], Kc_lo[2]).
 template <bool kRaw = false>
 __device__ inline void transfer_f32(const WalkerF& w, const float* Kp, const float* Kc, float x, float sa,
-                                    float ca, float scale, float s1, float c1, cf T[3])
+                                    float ca, float scale, float s1, float c1, cf T[3],
+                                    const float* Klo = nullptr)
 {
     // sqrt3/2 as a float pair: its float32 rounding alone would shorten the arms by ~2e-8 for
     // every walker alike (a bias of the whole batch)
@@ -219,7 +222,11 @@ __device__ inline void transfer_f32(const WalkerF& w, const float* Kp, const flo
         for (int q = 0; q < 3; ++q) d[q] = u[j][q] - u[i][q];
         const float kn = kap[j] - kap[i];
         const float np = nPnf(w.Pp, d), nc = nPnf(w.Pc, d);
-        const cf F = {np * Kp[0] + nc * Kc[0], np * Kp[1] + nc * Kc[1]};
+        cf F = {np * Kp[0] + nc * Kc[0], np * Kp[1] + nc * Kc[1]};
+        if (Klo != nullptr) {   // the mode factors' float32 rounding is common to all edges
+            F.re += np * Klo[0] + nc * Klo[2];
+            F.im += np * Klo[1] + nc * Klo[3];
+        }
         const cf g = fmul({-E[m].im, E[m].re}, F);   // i e^{i q_m} F
         // sinc(x(1 + k.n)) = sinc(x(1 - k.n)) + the difference (which T needs on its own);
         // the sum is off by at most an ulp of the larger term, like a direct evaluation
@@ -424,6 +431,10 @@ __device__ inline void walker_setup_mixed(const double* __restrict__ theta, int6
     wf.Kp[1] = (float)(ap * s2f);
     wf.Kc[0] = (float)(-ac * s2f);
     wf.Kc[1] = (float)(ac * c2f);
+    wf.Klo[0] = (float)(ap * c2f - (double)wf.Kp[0]);
+    wf.Klo[1] = (float)(ap * s2f - (double)wf.Kp[1]);
+    wf.Klo[2] = (float)(-ac * s2f - (double)wf.Kc[0]);
+    wf.Klo[3] = (float)(ac * c2f - (double)wf.Kc[1]);
 }
 
 // frequency tables of one grid point: f, f^{1/3}, f^{-1/3}, ln(f)/3 as float pairs
@@ -1122,7 +1133,8 @@ __device__ __forceinline__ void het_mixed_body(const HetLaunch& L)
                     sincos_small(0.5f * reduce_phase(dd_sub(Phi, ld_f2(me.phi0))), &sh, &ch);
                     const cf em1 = {-2.0f * sh * sh, -2.0f * sh * ch};   // e^{-i dPhi} - 1
                     cf T[3];
-                    transfer_f32<true>(wsf[lw], wsf[lw].Kp, wsf[lw].Kc, me.xs.w, sa, ca, 1.0f, me.xs.x, me.xs.y, T);
+                    transfer_f32<true>(wsf[lw], wsf[lw].Kp, wsf[lw].Kc, me.xs.w, sa, ca, 1.0f, me.xs.x, me.xs.y, T,
+                                       wsf[lw].Klo);
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         const cf rho = fmul(fscale(T[c], amp), {me.h0inv[c].x, me.h0inv[c].y});
@@ -1336,7 +1348,8 @@ __device__ __forceinline__ void het_mixed_pt_body(const HetLaunch& L)
                     sincos_small(0.5f * reduce_phase(dd_sub(Phi, ld_f2(me.phi0))), &sh, &ch);
                     const cf em1 = {-2.0f * sh * sh, -2.0f * sh * ch};
                     cf T[3];
-                    transfer_f32<true>(wsf[lw], wsf[lw].Kp, wsf[lw].Kc, me.xs.w, sa, ca, 1.0f, me.xs.x, me.xs.y, T);
+                    transfer_f32<true>(wsf[lw], wsf[lw].Kp, wsf[lw].Kc, me.xs.w, sa, ca, 1.0f, me.xs.x, me.xs.y, T,
+                                       wsf[lw].Klo);
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         const cf rho = fmul(fscale(T[c], amp), {me.h0inv[c].x, me.h0inv[c].y});
