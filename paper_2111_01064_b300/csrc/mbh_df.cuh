@@ -99,6 +99,19 @@ __device__ __forceinline__ f2 dd_fma(f2 a, f2 b, f2 c)
     return dd_add({p, e}, c);
 }
 
+// a * b + c without the final renormalisation: hi is the rounded sum of the product's and c's
+// high parts, lo collects the exact two-sum error and the low-order terms (|lo| may exceed
+// ulp(hi)/2 by a little).  Chained Horner steps accept such operands unchanged (every product
+// and sum of high parts is still exact), and so does dd_mul, which normalises its result.
+__device__ __forceinline__ f2 dd_fma_lazy(f2 a, f2 b, f2 c)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+    const f2 s = two_sum(p, c.hi);
+    return {s.hi, __fadd_rn(s.lo, __fadd_rn(e, c.lo))};
+}
+
 __device__ __forceinline__ float dd_to_float(f2 a) { return __fadd_rn(a.hi, a.lo); }
 
 // a <= b for df values normalised with round-to-nearest (|lo| <= ulp(hi)/2): the order of

@@ -465,9 +465,10 @@ __device__ __forceinline__ bool phase_df(const WalkerDF& w, const WalkerF& wf, c
     f2 P = w.c[7], Q = w.d[7];
 #pragma unroll
     for (int k = 6; k >= 0; --k) {
-        P = dd_fma(P, v, w.c[k]);
-        Q = dd_fma(Q, v, w.d[k]);
+        P = dd_fma_lazy(P, v, w.c[k]);
+        Q = dd_fma_lazy(Q, v, w.d[k]);
     }
+    // (P and Q go straight into dd_mul, which takes unnormalised operands and normalises)
     const f2 iv2 = dd_mul(iv, iv), iv4 = dd_mul(iv2, iv2);
     const f2 iv5 = dd_mul(iv4, iv), iv8 = dd_mul(iv4, iv4);
     const f2 psi_pn = dd_add(dd_mul(P, iv5), dd_mul(lnv, dd_fma(w.cl6, v, w.cl5)));
