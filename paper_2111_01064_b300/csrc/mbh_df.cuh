@@ -112,6 +112,21 @@ __device__ __forceinline__ f2 dd_fma_lazy(f2 a, f2 b, f2 c)
     return {s.hi, __fadd_rn(s.lo, __fadd_rn(e, c.lo))};
 }
 
+// a * b and a + b without the final renormalisation, for operands of further dd_* arithmetic
+// (not for the comparisons dd_le / dd_lt0, which need normalised values)
+__device__ __forceinline__ f2 dd_mul_lazy(f2 a, f2 b)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    const float e = __fmaf_rn(a.hi, b.hi, -p);
+    return {p, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e))};
+}
+
+__device__ __forceinline__ f2 dd_add_lazy(f2 a, f2 b)
+{
+    const f2 s = two_sum(a.hi, b.hi);
+    return {s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo))};
+}
+
 __device__ __forceinline__ float dd_to_float(f2 a) { return __fadd_rn(a.hi, a.lo); }
 
 // a <= b for df values normalised with round-to-nearest (|lo| <= ulp(hi)/2): the order of

@@ -459,21 +459,22 @@ template <bool kAlways = false, bool kTab = false>
 __device__ __forceinline__ bool phase_df(const WalkerDF& w, const WalkerF& wf, const FreqDF& q,
                                          f2 t_obs, f2& Phi, float& sa, float& ca, float& amp)
 {
-    const f2 v = dd_mul(w.cbrt_piM, q.f3);
-    const f2 iv = dd_mul(w.icbrt_piM, q.fm3);
-    const f2 lnv = dd_add(w.ln_cbrt_piM, q.lnf3);
+    // intermediate double-float values stay unnormalised (the *_lazy forms) up to the two that
+    // need it: t(f), compared against the support bounds, and Phi
+    const f2 v = dd_mul_lazy(w.cbrt_piM, q.f3);
+    const f2 iv = dd_mul_lazy(w.icbrt_piM, q.fm3);
+    const f2 lnv = dd_add_lazy(w.ln_cbrt_piM, q.lnf3);
     f2 P = w.c[7], Q = w.d[7];
 #pragma unroll
     for (int k = 6; k >= 0; --k) {
         P = dd_fma_lazy(P, v, w.c[k]);
         Q = dd_fma_lazy(Q, v, w.d[k]);
     }
-    // (P and Q go straight into dd_mul, which takes unnormalised operands and normalises)
-    const f2 iv2 = dd_mul(iv, iv), iv4 = dd_mul(iv2, iv2);
-    const f2 iv5 = dd_mul(iv4, iv), iv8 = dd_mul(iv4, iv4);
-    const f2 psi_pn = dd_add(dd_mul(P, iv5), dd_mul(lnv, dd_fma(w.cl6, v, w.cl5)));
+    const f2 iv2 = dd_mul_lazy(iv, iv), iv4 = dd_mul_lazy(iv2, iv2);
+    const f2 iv5 = dd_mul_lazy(iv4, iv), iv8 = dd_mul_lazy(iv4, iv4);
+    const f2 psi_pn = dd_add_lazy(dd_mul_lazy(P, iv5), dd_mul_lazy(lnv, dd_fma_lazy(w.cl6, v, w.cl5)));
     // t(f) = Psi'(f)/(2 pi) + t0 (the walker's d and dl6 carry the 1/(2 pi))
-    const f2 t = dd_add(dd_add(dd_mul(Q, iv8), dd_mul(dd_mul(lnv, w.dl6), iv2)), w.t0);
+    const f2 t = dd_add(dd_add_lazy(dd_mul_lazy(Q, iv8), dd_mul_lazy(dd_mul_lazy(lnv, w.dl6), iv2)), w.t0);
     const bool in = dd_le(q.f, w.fcut) && !dd_lt0(t) && dd_le(t, t_obs);
     if (!kAlways && !in) return false;
     // orbit angle alpha(t) = alpha(t_ref) + da, da from t - t_ref in float32
@@ -485,8 +486,8 @@ __device__ __forceinline__ bool phase_df(const WalkerDF& w, const WalkerF& wf, c
     const f2 sa_d = dd_add_f(w.sa_ref, wf.ca_ref * sd - wf.sa_ref * omc);
     const f2 ca_d = dd_add_f(w.ca_ref, -(wf.ca_ref * omc + wf.sa_ref * sd));
     // Phi = f (c1 + 2 pi (AU/c) k.c(t)) + Psi_PN(f) + c0 (kx, ky carry 2 pi AU/c)
-    const f2 S = dd_fma(w.ky, sa_d, dd_fma(w.kx, ca_d, w.c1));
-    Phi = dd_add(dd_mul(q.f, S), dd_add(psi_pn, w.c0));
+    const f2 S = dd_fma_lazy(w.ky, sa_d, dd_fma_lazy(w.kx, ca_d, w.c1));
+    Phi = dd_add(dd_mul_lazy(q.f, S), dd_add_lazy(psi_pn, w.c0));
     sa = dd_to_float(sa_d);
     ca = dd_to_float(ca_d);
     const float ff = q.f.hi;
