@@ -559,8 +559,12 @@ __device__ __forceinline__ float mode_vpow(const WalkerDF& w, const FreqDF& q2, 
 // phase modulo 2 pi in double-float, then float32
 __device__ __forceinline__ float reduce_phase(f2 p)
 {
+    // p - 2 pi n with 2 pi as a float pair (Cody-Waite): n is an integer of up to ~21 bits
+    // (|p| <~ 1e7), so p_hi - n (2 pi)_hi is exact in one FMA (its result needs no bits below
+    // 2^-21 and fits 24), and the low parts add the remaining ~1e-9 rad
     const float n = rintf(p.hi * (float)kInvTwoPi);
-    return dd_to_float(dd_sub(p, dd_mul_f(kTwoPiDF, n)));
+    const float r = fmaf(-n, kTwoPiDF.hi, p.hi);
+    return r + fmaf(-n, kTwoPiDF.lo, p.lo);
 }
 
 // Mixed template at one grid point: h = amp e^{-i Phi} T (float32 result, times `scale`).
@@ -1132,7 +1136,7 @@ __device__ __forceinline__ void het_mixed_body(const HetLaunch& L)
                 float sa, ca, amp;
                 if (phase_df<false, true>(wsd[lw], wsf[lw], q, tob, Phi, sa, ca, amp)) {
                     float sh, ch;
-                    sincos_small(0.5f * reduce_phase(dd_sub(Phi, ld_f2(me.phi0))), &sh, &ch);
+                    sincos_small(0.5f * reduce_phase(dd_add_lazy(Phi, {-me.phi0.x, -me.phi0.y})), &sh, &ch);
                     const cf em1 = {-2.0f * sh * sh, -2.0f * sh * ch};   // e^{-i dPhi} - 1
                     cf T[3];
                     transfer_f32<true>(wsf[lw], wsf[lw].Kp, wsf[lw].Kc, me.xs.w, sa, ca, 1.0f, me.xs.x, me.xs.y, T,
@@ -1243,7 +1247,8 @@ __global__ void __launch_bounds__(BLOCK)
                     float sa, ca, amp;
                     if (phase_df(wsd[lw], wsf[lw], q2, tob, Phi, sa, ca, amp)) {
                         float sh, ch;
-                        sincos_small(0.5f * reduce_phase(dd_sub(mode_phase(Phi, b), ld_f2(mm.phi0))), &sh, &ch);
+                        sincos_small(0.5f * reduce_phase(dd_add_lazy(mode_phase(Phi, b), {-mm.phi0.x, -mm.phi0.y})),
+                                     &sh, &ch);
                         const cf em1 = {-2.0f * sh * sh, -2.0f * sh * ch};   // e^{-i dPhi} - 1
                         cf T[3];
                         transfer_f32<false>(wsf[lw], &wsh[lw].hk[b][0], &wsh[lw].hk[b][2], me.xs.w, sa, ca,
@@ -1347,7 +1352,7 @@ __device__ __forceinline__ void het_mixed_pt_body(const HetLaunch& L)
                 float sa, ca, amp;
                 if (phase_df<false, true>(wsd[lw], wsf[lw], q, tob, Phi, sa, ca, amp)) {
                     float sh, ch;
-                    sincos_small(0.5f * reduce_phase(dd_sub(Phi, ld_f2(me.phi0))), &sh, &ch);
+                    sincos_small(0.5f * reduce_phase(dd_add_lazy(Phi, {-me.phi0.x, -me.phi0.y})), &sh, &ch);
                     const cf em1 = {-2.0f * sh * sh, -2.0f * sh * ch};
                     cf T[3];
                     transfer_f32<true>(wsf[lw], wsf[lw].Kp, wsf[lw].Kc, me.xs.w, sa, ca, 1.0f, me.xs.x, me.xs.y, T,
