@@ -39,20 +39,19 @@ __device__ __forceinline__ cf fscale(cf a, float s) { return {a.re * s, a.im * s
 
 // float32 copies of the response constants of a walker
 struct WalkerF {
-    float k[3], Pp[6], Pc[6], Kp[2], Kc[2];
+    // k/sqrt3; the polarisation basis u/sqrt3, v/sqrt3 (e+ = uu - vv, ex = uv + vu); the mode
+    // factors rotated by the polarisation angle, Ga = cos2psi K+ - sin2psi Kx and
+    // Gb = sin2psi K+ + cos2psi Kx, so that n.P+.n K+ + n.Px.n Kx = a Ga + b Gb with
+    // a = (u.n)^2 - (v.n)^2, b = 2 (u.n)(v.n); Glo: the float32 rounding of Ga, Gb (float pairs)
+    float k[3], eu[3], ev[3], Ga[2], Gb[2], Glo[4];
+    float eulo[2], evlo[3];   // the float32 rounding of eu (eu[2] = 0) and ev: float pairs
     float sa_ref, ca_ref, amp, inv_fc2;
     float amp76;   // amp (pi M)^{-7/6}: times f^{-7/6} of an edge table gives amp v^{-7/2}
     // relative rounding errors (exact/float - 1) of amp and amp76: a pure scale of the whole
     // template, which the heterodyne kernels undo exactly at the end (amp_fix)
     float eps_amp, eps_amp76;
-    float Klo[4];   // Kp, Kc - their float32 values (the (2,2) mode factors as float pairs)
 };
 
-__device__ __forceinline__ float nPnf(const float* P, const float* n)
-{
-    return P[0] * n[0] * n[0] + P[3] * n[1] * n[1] + P[5] * n[2] * n[2] +
-           2.0f * (P[1] * n[0] * n[1] + P[2] * n[0] * n[2] + P[4] * n[1] * n[2]);
-}
 
 // sin x / x as its Taylor series in u2 = x^2 to the term x^{2(N-1)}/(2N-1)!
 template <int N>
@@ -175,11 +174,12 @@ constexpr float kSincShortX = 0.1f;
 // X' = X/(1 - D^2) etc.  The heterodyne folds the rest, per edge and channel, into its
 // float64-formed 1/h0 (so that no float32 rounding of a per-edge or constant factor is shared
 // by every walker's template, which would bias the whole batch).
-// Klo (or nullptr): the low parts of Kp and Kc as float pairs (Kp_lo[2], Kc_lo[2]).
+// Ga, Gb: the walker's rotated mode factors (WalkerF, or a higher mode's); Glo (or nullptr):
+// their low parts as float pairs (Ga_lo[2], Gb_lo[2]).
 template <bool kRaw = false>
-__device__ inline void transfer_f32(const WalkerF& w, const float* Kp, const float* Kc, float x, float sa,
+__device__ inline void transfer_f32(const WalkerF& w, const float* Ga, const float* Gb, float x, float sa,
                                     float ca, float scale, float s1, float c1, cf T[3],
-                                    const float* Klo = nullptr)
+                                    const float* Glo = nullptr)
 {
     // sqrt3/2 as a float pair: its float32 rounding alone would shorten the arms by ~2e-8 for
     // every walker alike (a bias of the whole batch)
@@ -221,11 +221,16 @@ __device__ inline void transfer_f32(const WalkerF& w, const float* Kp, const flo
 #pragma unroll
         for (int q = 0; q < 3; ++q) d[q] = u[j][q] - u[i][q];
         const float kn = kap[j] - kap[i];
-        const float np = nPnf(w.Pp, d), nc = nPnf(w.Pc, d);
-        cf F = {np * Kp[0] + nc * Kc[0], np * Kp[1] + nc * Kc[1]};
-        if (Klo != nullptr) {   // the mode factors' float32 rounding is common to all edges
-            F.re += np * Klo[0] + nc * Klo[2];
-            F.im += np * Klo[1] + nc * Klo[3];
+        // n.P+.n K+ + n.Px.n Kx = a Ga + b Gb (n = d/sqrt3; eu, ev carry the 1/sqrt3)
+        // (u, v as float pairs: their rounding would otherwise be common to every edge)
+        const float un = fmaf(w.eu[0], d[0], fmaf(w.eu[1], d[1], w.eulo[0] * d[0] + w.eulo[1] * d[1]));
+        const float vn = fmaf(w.ev[0], d[0], fmaf(w.ev[1], d[1], fmaf(w.ev[2], d[2],
+                              w.evlo[0] * d[0] + w.evlo[1] * d[1] + w.evlo[2] * d[2])));
+        const float pa = fmaf(un, un, -vn * vn), pb = 2.0f * un * vn;
+        cf F = {pa * Ga[0] + pb * Gb[0], pa * Ga[1] + pb * Gb[1]};
+        if (Glo != nullptr) {   // the factors' float32 rounding is common to all edges
+            F.re += pa * Glo[0] + pb * Glo[2];
+            F.im += pa * Glo[1] + pb * Glo[3];
         }
         const cf g = fmul({-E[m].im, E[m].re}, F);   // i e^{i q_m} F
         // sinc(x(1 + k.n)) = sinc(x(1 - k.n)) + the difference (which T needs on its own);
@@ -265,13 +270,13 @@ __device__ inline void transfer_f32(const WalkerF& w, const float* Kp, const flo
 }
 
 // the same with sin x, cos x of the one-link phase x = pi f L/c computed here
-__device__ __forceinline__ void transfer_f32(const WalkerF& w, const float* Kp, const float* Kc, float f,
+__device__ __forceinline__ void transfer_f32(const WalkerF& w, const float* Ga, const float* Gb, float f,
                                              float sa, float ca, float scale, cf T[3])
 {
     const float x = (float)kPi * (float)kArmSec * f;
     float s1, c1;
     sincos_small(x, &s1, &c1);
-    transfer_f32<false>(w, Kp, Kc, x, sa, ca, scale, s1, c1, T);
+    transfer_f32<false>(w, Ga, Gb, x, sa, ca, scale, s1, c1, T);
 }
 
 constexpr f2 kTwoPiDF = df_const(kTwoPi);
@@ -409,32 +414,33 @@ __device__ inline void walker_setup_mixed(const double* __restrict__ theta, int6
     double s2p, c2p, s2f, c2f;
     sincos(2.0 * (double)pol, &s2p, &c2p);
     sincos(2.0 * (double)phi, &s2f, &c2f);
-    const double u[3] = {sl, -cl, 0.0};
-    const double vv[3] = {-sb * cl, -sb * sl, cbt};
-    // k/sqrt3 and P/3 (the response works with spacecraft offsets in units of L/sqrt3)
+    // k, u, v over sqrt3 (the response works with spacecraft offsets in units of L/sqrt3)
     constexpr double isq3 = 0.57735026918962576;
     wf.k[0] = (float)(-cbt * cl * isq3);
     wf.k[1] = (float)(-cbt * sl * isq3);
     wf.k[2] = (float)(-sb * isq3);
-    const int ii[6] = {0, 0, 0, 1, 1, 2}, jj[6] = {0, 1, 2, 1, 2, 2};
+    const double eu[2] = {sl * isq3, -cl * isq3};
+    const double ev[3] = {-sb * cl * isq3, -sb * sl * isq3, cbt * isq3};
 #pragma unroll
-    for (int n = 0; n < 6; ++n) {
-        const double ep = u[ii[n]] * u[jj[n]] - vv[ii[n]] * vv[jj[n]];
-        const double ec = u[ii[n]] * vv[jj[n]] + vv[ii[n]] * u[jj[n]];
-        wf.Pp[n] = (float)((c2p * ep + s2p * ec) * (1.0 / 3.0));
-        wf.Pc[n] = (float)((-s2p * ep + c2p * ec) * (1.0 / 3.0));
+    for (int j = 0; j < 3; ++j) {
+        wf.eu[j] = j < 2 ? (float)eu[j] : 0.0f;
+        wf.ev[j] = (float)ev[j];
+        wf.evlo[j] = (float)(ev[j] - (double)wf.ev[j]);
+        if (j < 2) wf.eulo[j] = (float)(eu[j] - (double)wf.eu[j]);
     }
     const double ylm = 0.15769578262626002 /* sqrt(5/(64 pi)) */;
     const double ci = cos((double)iota);
     const double ap = ylm * (1.0 + ci * ci), ac = 2.0 * ylm * ci;
-    wf.Kp[0] = (float)(ap * c2f);
-    wf.Kp[1] = (float)(ap * s2f);
-    wf.Kc[0] = (float)(-ac * s2f);
-    wf.Kc[1] = (float)(ac * c2f);
-    wf.Klo[0] = (float)(ap * c2f - (double)wf.Kp[0]);
-    wf.Klo[1] = (float)(ap * s2f - (double)wf.Kp[1]);
-    wf.Klo[2] = (float)(-ac * s2f - (double)wf.Kc[0]);
-    wf.Klo[3] = (float)(ac * c2f - (double)wf.Kc[1]);
+    // K+ = ap e^{2i phi}, Kx = i ac e^{2i phi}; Ga = cos2psi K+ - sin2psi Kx, Gb = sin2psi K+ + cos2psi Kx
+    const double g[4] = {c2p * ap * c2f + s2p * ac * s2f, c2p * ap * s2f - s2p * ac * c2f,
+                         s2p * ap * c2f - c2p * ac * s2f, s2p * ap * s2f + c2p * ac * c2f};
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        wf.Ga[j] = (float)g[j];
+        wf.Gb[j] = (float)g[2 + j];
+        wf.Glo[j] = (float)(g[j] - (double)wf.Ga[j]);
+        wf.Glo[2 + j] = (float)(g[2 + j] - (double)wf.Gb[j]);
+    }
 }
 
 // frequency tables of one grid point: f, f^{1/3}, f^{-1/3}, ln(f)/3 as float pairs
@@ -505,7 +511,7 @@ __device__ __forceinline__ bool phase_df(const WalkerDF& w, const WalkerF& wf, c
 // constants) with the phase scaled by m/2; the amplitude gains v^{p_lm} and the response uses
 // the mode's polarisation factors (float32, folded with H_lm's constant and sqrt(2/m)).
 struct WalkerHMF {
-    float hk[kHmModes][4];   // K+ (re, im), Kx (re, im) per mode
+    float hk[kHmModes][4];   // per mode Ga (re, im), Gb (re, im), as WalkerF's for the (2,2) mode
 };
 
 // tables of f2 = r f, r = 2/m: f2, f2^{1/3}, f2^{-1/3}, ln(f2)/3
@@ -538,12 +544,20 @@ __device__ inline void walker_setup_hm(const double* __restrict__ theta, int64_t
                                        WalkerHMF& h)
 {
     const double q = theta[kQ * W + i], iota = theta[kIota * W + i], phi = theta[kPhi * W + i];
+    const double pol = theta[kPsi * W + i];
     Walker tmp;
     hm_setup(tmp, q, iota, phi);
+    double s2p, c2p;
+    sincos(2.0 * pol, &s2p, &c2p);
+    // per mode (Ga, Gb) = (cos2psi K+ - sin2psi Kx, sin2psi K+ + cos2psi Kx) as transfer_f32 takes them
 #pragma unroll
     for (int b = 0; b < kHmModes; ++b)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) h.hk[b][j] = (float)tmp.hk[b][j];
+        for (int j = 0; j < 2; ++j) {
+            const double kp = tmp.hk[b][j], kc = tmp.hk[b][2 + j];
+            h.hk[b][j] = (float)(c2p * kp - s2p * kc);
+            h.hk[b][2 + j] = (float)(s2p * kp + c2p * kc);
+        }
 }
 
 // v^{p_lm} in float32 from f2^{1/3} and (pi M)^{1/3}
@@ -577,7 +591,7 @@ __device__ __forceinline__ bool point_mixed(const WalkerDF& w, const WalkerF& wf
     float sp, cp;
     sincos_small(reduce_phase(Phi), &sp, &cp);
     cf T[3];
-    transfer_f32(wf, wf.Kp, wf.Kc, q.f.hi, sa, ca, amp * scale, T);
+    transfer_f32(wf, wf.Ga, wf.Gb, q.f.hi, sa, ca, amp * scale, T);
     const cf e = {cp, -sp};
 #pragma unroll
     for (int c = 0; c < 3; ++c) h[c] = fmul(e, T[c]);
@@ -1139,8 +1153,8 @@ __device__ __forceinline__ void het_mixed_body(const HetLaunch& L)
                     sincos_small(0.5f * reduce_phase(dd_add_lazy(Phi, {-me.phi0.x, -me.phi0.y})), &sh, &ch);
                     const cf em1 = {-2.0f * sh * sh, -2.0f * sh * ch};   // e^{-i dPhi} - 1
                     cf T[3];
-                    transfer_f32<true>(wsf[lw], wsf[lw].Kp, wsf[lw].Kc, me.xs.w, sa, ca, 1.0f, me.xs.x, me.xs.y, T,
-                                       wsf[lw].Klo);
+                    transfer_f32<true>(wsf[lw], wsf[lw].Ga, wsf[lw].Gb, me.xs.w, sa, ca, 1.0f, me.xs.x, me.xs.y, T,
+                                       wsf[lw].Glo);
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         const cf rho = fmul(fscale(T[c], amp), {me.h0inv[c].x, me.h0inv[c].y});
@@ -1355,8 +1369,8 @@ __device__ __forceinline__ void het_mixed_pt_body(const HetLaunch& L)
                     sincos_small(0.5f * reduce_phase(dd_add_lazy(Phi, {-me.phi0.x, -me.phi0.y})), &sh, &ch);
                     const cf em1 = {-2.0f * sh * sh, -2.0f * sh * ch};
                     cf T[3];
-                    transfer_f32<true>(wsf[lw], wsf[lw].Kp, wsf[lw].Kc, me.xs.w, sa, ca, 1.0f, me.xs.x, me.xs.y, T,
-                                       wsf[lw].Klo);
+                    transfer_f32<true>(wsf[lw], wsf[lw].Ga, wsf[lw].Gb, me.xs.w, sa, ca, 1.0f, me.xs.x, me.xs.y, T,
+                                       wsf[lw].Glo);
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         const cf rho = fmul(fscale(T[c], amp), {me.h0inv[c].x, me.h0inv[c].y});
