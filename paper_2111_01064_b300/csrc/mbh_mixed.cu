@@ -943,13 +943,14 @@ __global__ void edge_mixed_kernel(const double* __restrict__ theta0, double t_ob
     }
 }
 
-// Higher-mode reference: per edge and mode the mode's large phase Phi0_lm (double-float,
-// defined also outside the mode's support), and per channel u = h0_lm/h0 and g = e^{-i Phi0_lm}/h0
-// (formed in float64 from the same mixed-precision chain as the walkers'); base = -1 where
-// h0 = 0 (r = 0 there).  A walker's delta = r - 1 is then
+// Higher-mode reference: per edge and mode the mode's large phase Phi0_lm from the walkers'
+// double-float chain (defined also outside the mode's support), and per channel
+// u = h0_lm/h0 and g = K f2^{-7/6} e^{-i Phi0_lm}/h0 in float64 from the exact float64 mode
+// templates h0_lm (h0 = their sum), K the frequency-only factors of the walkers' raw transfer
+// and f2 = 2f/m (whose f2^{-7/6} the walkers' amplitude leaves out); base = -1 where h0 = 0
+// (r = 0 there).  A walker's delta = r - 1 is then
 //   base + sum_lm [a + a (e^{-i dPhi_lm} - 1) + u (e^{-i dPhi_lm} - 1)],  a = H_lm g - u,
-// with H_lm its float32 mode template without the large phase; a mode outside the walker's
-// support contributes -u.
+// with H_lm its raw float32 mode template; a mode outside the walker's support contributes -u.
 __global__ void edge_mixed_hm_kernel(const double* __restrict__ theta0, double t_obs, uint32_t modes,
                                      const double* __restrict__ fe, int n_edges, MixEdge* __restrict__ out,
                                      MixModeHM* __restrict__ hm, float* __restrict__ base,
@@ -957,64 +958,70 @@ __global__ void edge_mixed_hm_kernel(const double* __restrict__ theta0, double t
 {
     __shared__ WalkerDF wd;
     __shared__ WalkerF wf;
-    __shared__ WalkerHMF wh;
+    __shared__ Walker w64;
     if (threadIdx.x == 0) {
         walker_setup_mixed(theta0, 1, 0, wd, wf);
-        walker_setup_hm(theta0, 1, 0, wh);
-        *eps0 = (double)wf.eps_amp;   // the mode records use amp (generic chain)
+        walker_setup(theta0, 1, 0, w64, modes);
+        *eps0 = 0.0;   // h0 is exact: no float32 amplitude on the reference side
     }
     __syncthreads();
     const f2 tob = split_d(t_obs);
     for (int e = threadIdx.x; e < n_edges; e += blockDim.x) {
-        const FreqDF q = freq_tables(fe[e]);
+        const double f = fe[e];
+        const FreqDF q = freq_tables(f);
         MixEdge me{};
         me.f = make_float2(q.f.hi, q.f.lo);
         me.f3 = make_float2(q.f3.hi, q.f3.lo);
         me.fm3 = make_float2(q.fm3.hi, q.fm3.lo);
         me.lnf3 = make_float2(q.lnf3.hi, q.lnf3.lo);
-        me.xs = edge_xs(fe[e]);
+        me.xs = edge_xs(f);
         out[e] = me;
-        double h0r[3] = {0, 0, 0}, h0i[3] = {0, 0, 0};
-        double hr[kHmModes][3], hi[kHmModes][3], er[kHmModes], ei[kHmModes];
+        // frequency-only factors (as the (2,2) records, without f^{-7/6}, which goes per mode)
+        const double x = kPi * kArmSec * f;
+        double s1, c1, s3, c3;
+        sincos(x, &s1, &c1);
+        sincos(3.0 * x, &s3, &c3);
+        const double wm = -2.0 * x * (2.0 * s1 * c1);
+        const double wr = wm * s3, wi = wm * c3;
+        const double ar = 2.0 * s1 * s1, ai = 2.0 * s1 * c1;
+        const double Kr[3] = {wr / kSqrt2, wr / kSqrt6, (wr * ar - wi * ai) / kSqrt3};
+        const double Ki[3] = {wi / kSqrt2, wi / kSqrt6, (wr * ai + wi * ar) / kSqrt3};
+        cd h0m[kHmModes][3], h0[3] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
+        double gr[kHmModes], gi[kHmModes];   // f2^{-7/6} e^{-i Phi0_lm}
         for (int b = 0; b < kHmModes; ++b) {
-            for (int c = 0; c < 3; ++c) hr[b][c] = hi[b][c] = 0.0;
-            er[b] = ei[b] = 0.0;
+            for (int c = 0; c < 3; ++c) h0m[b][c] = {0.0, 0.0};
+            gr[b] = gi[b] = 0.0;
             MixModeHM mm{};
             if (modes & (1u << b)) {
+                if (mode_point_f64(w64, b, f, t_obs, h0m[b]))
+                    for (int c = 0; c < 3; ++c) h0[c] = cadd(h0[c], h0m[b][c]);
                 const FreqDF q2 = mode_tables(q, b);
                 f2 Phi;
                 float sa, ca, amp;
-                const bool in = phase_df<true>(wd, wf, q2, tob, Phi, sa, ca, amp);
+                phase_df<true, true>(wd, wf, q2, tob, Phi, sa, ca, amp);
                 const f2 P = mode_phase(Phi, b);
                 mm.phi0 = make_float2(P.hi, P.lo);
-                const double ph = fmod((double)P.hi + (double)P.lo, kTwoPi);
-                sincos(-ph, &ei[b], &er[b]);   // e^{-i Phi0_lm}
-                if (in) {
-                    cf T[3];
-                    transfer_f32<false>(wf, &wh.hk[b][0], &wh.hk[b][2], me.xs.w, sa, ca, amp * mode_vpow(wd, q2, b),
-                                        me.xs.x, me.xs.y, T);
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        const double Hr = (double)T[c].re, Hi = (double)T[c].im;
-                        hr[b][c] = Hr * er[b] - Hi * ei[b];
-                        hi[b][c] = Hr * ei[b] + Hi * er[b];
-                        h0r[c] += hr[b][c];
-                        h0i[c] += hi[b][c];
-                    }
-                }
+                double sp, cp;
+                sincos((double)P.hi + (double)P.lo, &sp, &cp);
+                const double a = pow(2.0 * f / hm_m(b), -7.0 / 6.0);
+                gr[b] = a * cp;
+                gi[b] = -a * sp;
             }
             hm[(int64_t)e * kHmModes + b] = mm;
         }
         for (int c = 0; c < 3; ++c) {
-            const double m2 = h0r[c] * h0r[c] + h0i[c] * h0i[c];
+            const double m2 = h0[c].re * h0[c].re + h0[c].im * h0[c].im;
             base[e * 3 + c] = m2 > 0.0 ? 0.0f : -1.0f;
             if (!(m2 > 0.0)) continue;
-            const double ir = h0r[c] / m2, ii = -h0i[c] / m2;   // 1/h0
+            const double ir = h0[c].re / m2, ii = -h0[c].im / m2;   // 1/h0
             for (int b = 0; b < kHmModes; ++b) {
                 if (!(modes & (1u << b))) continue;
                 MixModeHM& mm = hm[(int64_t)e * kHmModes + b];
-                mm.u[c] = make_float2((float)(hr[b][c] * ir - hi[b][c] * ii), (float)(hr[b][c] * ii + hi[b][c] * ir));
-                mm.g[c] = make_float2((float)(er[b] * ir - ei[b] * ii), (float)(er[b] * ii + ei[b] * ir));
+                const cd hb = h0m[b][c];
+                mm.u[c] = make_float2((float)(hb.re * ir - hb.im * ii), (float)(hb.re * ii + hb.im * ir));
+                // K e'/h0, e' = f2^{-7/6} e^{-i Phi0_lm}
+                const double er = Kr[c] * gr[b] - Ki[c] * gi[b], ei = Kr[c] * gi[b] + Ki[c] * gr[b];
+                mm.g[c] = make_float2((float)(er * ir - ei * ii), (float)(er * ii + ei * ir));
             }
         }
     }
@@ -1259,18 +1266,19 @@ __global__ void __launch_bounds__(BLOCK)
                     const FreqDF q2 = mode_tables(q, b);
                     f2 Phi;
                     float sa, ca, amp;
-                    if (phase_df(wsd[lw], wsf[lw], q2, tob, Phi, sa, ca, amp)) {
+                    if (phase_df<false, true>(wsd[lw], wsf[lw], q2, tob, Phi, sa, ca, amp)) {
                         float sh, ch;
                         sincos_small(0.5f * reduce_phase(dd_add_lazy(mode_phase(Phi, b), {-mm.phi0.x, -mm.phi0.y})),
                                      &sh, &ch);
                         const cf em1 = {-2.0f * sh * sh, -2.0f * sh * ch};   // e^{-i dPhi} - 1
                         cf T[3];
-                        transfer_f32<false>(wsf[lw], &wsh[lw].hk[b][0], &wsh[lw].hk[b][2], me.xs.w, sa, ca,
-                                            amp * mode_vpow(wsd[lw], q2, b), me.xs.x, me.xs.y, T);
+                        transfer_f32<true>(wsf[lw], &wsh[lw].hk[b][0], &wsh[lw].hk[b][2], me.xs.w, sa, ca, 1.0f,
+                                           me.xs.x, me.xs.y, T);
+                        const float a = amp * mode_vpow(wsd[lw], q2, b);
 #pragma unroll
                         for (int c = 0; c < 3; ++c) {
                             const cf u = {mm.u[c].x, mm.u[c].y};
-                            const cf ac = fsub(fmul(T[c], {mm.g[c].x, mm.g[c].y}), u);
+                            const cf ac = fsub(fmul(fscale(T[c], a), {mm.g[c].x, mm.g[c].y}), u);
                             dl[c] = fadd(dl[c], fadd(fadd(ac, fmul(ac, em1)), fmul(u, em1)));
                         }
                     } else {
@@ -1303,7 +1311,7 @@ __global__ void __launch_bounds__(BLOCK)
             df_acc(ahh, ohh);
         }
         if (active && lane == 0) {
-            const double fix = amp_fix(wsf[lw].eps_amp, S.mix.amp_eps0);   // generic chain: amp
+            const double fix = amp_fix(wsf[lw].eps_amp76, S.mix.amp_eps0);
             const double dh = 4.0 * (S.mix.sumA0 + df_to_double(adh)) * fix;
             const double hh = 4.0 * (S.mix.sumB0 + df_to_double(ahh)) * (fix * fix);
             L.out[wi] = -0.5 * (S.dd + hh - 2.0 * dh);

@@ -362,34 +362,48 @@ __device__ inline bool point_f64(const Walker& w, double f, double t_obs, cd h[3
 // Template of the walker's modes at f, float64: per mode the (2,2) model at f2 = 2f/m (phase
 // scaled by m/2, amplitude by v^{p_lm}), the orbit and the transfer at t_lm(f), summed.
 // Returns false (and zeros) when no mode is in its support.
+// One mode (index b) of the walker's template at f, float64: the (2,2) model at f2 = 2f/m
+// (phase scaled by m/2, amplitude by v^{p_lm}), the orbit and the transfer at t_lm(f).
+// Returns false (and leaves h alone) outside the mode's support.
+__device__ inline bool mode_point_f64(const Walker& w, int b, double f, double t_obs, cd h[3])
+{
+    const int m = hm_m(b);
+    const double f2 = 2.0 * f / m;
+    const double v = cbrt(w.piM * f2);
+    double psi_pn, dpsi_pn;
+    pn_phase_f64(w, v, log(v), psi_pn, dpsi_pn);
+    const double t = w.tref + (dpsi_pn - w.dpsi_max) * kInvTwoPi;
+    if (!(f2 <= w.fcut) || t < 0.0 || t > t_obs) return false;
+    double amp = w.amp * exp(-f2 * f2 * w.inv_fc2) / (v * v * v * sqrt(v));
+    for (int j = 0; j < hm_vpow(b); ++j) amp *= v;
+    double sa, ca;
+    sincos(kTwoPi * t / kYear, &sa, &ca);
+    const double kc = kAUSec * (w.k[0] * ca + w.k[1] * sa);
+    const double Phi = 0.5 * m * (kTwoPi * f2 * w.tref + psi_pn - w.psi_max - (f2 - w.fmax) * w.dpsi_max) +
+                       kTwoPi * f * kc;
+    double sP, cP;
+    sincos(Phi, &sP, &cP);
+    cd T[3];
+    transfer_f64(w, f, sa, ca, &w.hk[b][0], &w.hk[b][2], T);
+    const cd e = {amp * cP, -amp * sP};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) h[c] = cmul(e, T[c]);
+    return true;
+}
+
+// Template of the walker's modes at f, float64: the modes of mode_point_f64, summed.
+// Returns false (and zeros) when no mode is in its support.
 __device__ inline bool point_hm_f64(const Walker& w, double f, double t_obs, cd h[3])
 {
     h[0] = h[1] = h[2] = {0.0, 0.0};
     bool any = false;
     for (int b = 0; b < kHmModes; ++b) {
         if (!(w.modes & (1u << b))) continue;
-        const int m = hm_m(b);
-        const double f2 = 2.0 * f / m;
-        const double v = cbrt(w.piM * f2);
-        double psi_pn, dpsi_pn;
-        pn_phase_f64(w, v, log(v), psi_pn, dpsi_pn);
-        const double t = w.tref + (dpsi_pn - w.dpsi_max) * kInvTwoPi;
-        if (!(f2 <= w.fcut) || t < 0.0 || t > t_obs) continue;
+        cd hb[3];
+        if (!mode_point_f64(w, b, f, t_obs, hb)) continue;
         any = true;
-        double amp = w.amp * exp(-f2 * f2 * w.inv_fc2) / (v * v * v * sqrt(v));
-        for (int j = 0; j < hm_vpow(b); ++j) amp *= v;
-        double sa, ca;
-        sincos(kTwoPi * t / kYear, &sa, &ca);
-        const double kc = kAUSec * (w.k[0] * ca + w.k[1] * sa);
-        const double Phi = 0.5 * m * (kTwoPi * f2 * w.tref + psi_pn - w.psi_max - (f2 - w.fmax) * w.dpsi_max) +
-                           kTwoPi * f * kc;
-        double sP, cP;
-        sincos(Phi, &sP, &cP);
-        cd T[3];
-        transfer_f64(w, f, sa, ca, &w.hk[b][0], &w.hk[b][2], T);
-        const cd e = {amp * cP, -amp * sP};
 #pragma unroll
-        for (int c = 0; c < 3; ++c) h[c] = cadd(h[c], cmul(e, T[c]));
+        for (int c = 0; c < 3; ++c) h[c] = cadd(h[c], hb[c]);
     }
     return any;
 }
