@@ -511,7 +511,8 @@ __device__ __forceinline__ bool phase_df(const WalkerDF& w, const WalkerF& wf, c
 // constants) with the phase scaled by m/2; the amplitude gains v^{p_lm} and the response uses
 // the mode's polarisation factors (float32, folded with H_lm's constant and sqrt(2/m)).
 struct WalkerHMF {
-    float hk[kHmModes][4];   // per mode Ga (re, im), Gb (re, im), as WalkerF's for the (2,2) mode
+    float hk[kHmModes][4];     // per mode Ga (re, im), Gb (re, im), as WalkerF's for the (2,2) mode
+    float hklo[kHmModes][4];   // their float32 rounding (float pairs)
 };
 
 // tables of f2 = r f, r = 2/m: f2, f2^{1/3}, f2^{-1/3}, ln(f2)/3
@@ -555,8 +556,11 @@ __device__ inline void walker_setup_hm(const double* __restrict__ theta, int64_t
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
             const double kp = tmp.hk[b][j], kc = tmp.hk[b][2 + j];
-            h.hk[b][j] = (float)(c2p * kp - s2p * kc);
-            h.hk[b][2 + j] = (float)(s2p * kp + c2p * kc);
+            const double ga = c2p * kp - s2p * kc, gb = s2p * kp + c2p * kc;
+            h.hk[b][j] = (float)ga;
+            h.hk[b][2 + j] = (float)gb;
+            h.hklo[b][j] = (float)(ga - (double)h.hk[b][j]);
+            h.hklo[b][2 + j] = (float)(gb - (double)h.hk[b][2 + j]);
         }
 }
 
@@ -1273,7 +1277,7 @@ __global__ void __launch_bounds__(BLOCK)
                         const cf em1 = {-2.0f * sh * sh, -2.0f * sh * ch};   // e^{-i dPhi} - 1
                         cf T[3];
                         transfer_f32<true>(wsf[lw], &wsh[lw].hk[b][0], &wsh[lw].hk[b][2], me.xs.w, sa, ca, 1.0f,
-                                           me.xs.x, me.xs.y, T);
+                                           me.xs.x, me.xs.y, T, &wsh[lw].hklo[b][0]);
                         const float a = amp * mode_vpow(wsd[lw], q2, b);
 #pragma unroll
                         for (int c = 0; c < 3; ++c) {
