@@ -321,11 +321,15 @@ __device__ inline void walker_setup_mixed(const double* __restrict__ theta, int6
 
     // few float64 divisions and transcendentals: on this path they cost 16 cycles of the SM's
     // float64 pipe per warp instruction, and the setup runs in every block before its edges
+    // one float64 division for four reciprocals: 1/(1+q), 1/q, 1/M and 1/D from 1/((1+q) q M D)
     const double opq = 1.0 + q;
-    const double x1 = 1.0 / opq, x2 = q * x1;
-    const double eta = x1 * x2;
     const double M = mt * kMsunSec;
-    const double iM = 1.0 / M;
+    const double dist = (double)dl * (1e9 * kParsec / kClight);
+    const double qM = q * M, od = opq * dist;
+    const double rr = 1.0 / (qM * od);
+    const double x1 = rr * qM * dist, iq = rr * M * od, iM = rr * q * od, idist = rr * qM * opq;
+    const double x2 = q * x1;
+    const double eta = x1 * x2;
     const double so = (113.0 / 12.0 * x1 * x1 + 25.0 / 4.0 * eta) * a1 +
                       (113.0 / 12.0 * x2 * x2 + 25.0 / 4.0 * eta) * a2;
     const double ss = 79.0 / 8.0 * eta * a1 * a2;
@@ -344,7 +348,7 @@ __device__ inline void walker_setup_mixed(const double* __restrict__ theta, int6
             127825.0 / 1296.0 * eta * eta * eta;
     const double alog6 = -6848.0 / 21.0;
     al[7] = kPi * (77096675.0 / 254016.0 + 378515.0 / 1512.0 * eta - 74045.0 / 756.0 * eta * eta);
-    const double pre = 3.0 / (128.0 * eta), dpre = pre * (kPi / 3.0) * M;
+    const double pre = (3.0 / 128.0) * opq * opq * iq, dpre = pre * (kPi / 3.0) * M;   // 3/(128 eta)
     double c[8], d[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
@@ -380,7 +384,7 @@ __device__ inline void walker_setup_mixed(const double* __restrict__ theta, int6
     m.dl6 = split_f64(dl6 * kInvTwoPi, 0);
     m.cbrt_piM = split_f64(cb, 0);
     m.icbrt_piM = split_f64(icb, 0);
-    m.ln_cbrt_piM = split_f64(log(piM) / 3.0, 0);
+    m.ln_cbrt_piM = split_f64(log(piM) * (1.0 / 3.0), 0);
     // the t_ref and f_max pinning folded into per-walker constants:
     //   t(f) = t_ref + (Psi'(f) - Psi'(f_max))/(2 pi) = Psi'(f)/(2 pi) + t0,
     //   Phi(f) = 2 pi f (t_ref + k.c(t)) + Psi_PN(f) - Psi_PN(f_max) - (f - f_max) Psi'(f_max)
@@ -401,8 +405,7 @@ __device__ inline void walker_setup_mixed(const double* __restrict__ theta, int6
     // so their rounding error enters the likelihood directly.
     // A = sqrt(2 pi/3) pi^{-2/3} M^{5/6} eta^{1/2} (pi M)^{7/6} / D v^{-7/2} exp(-(f/fc)^2)
     //   = pi sqrt(2/3) M^2 sqrt(eta) / D v^{-7/2} exp(-(f/fc)^2)
-    const double dist = (double)dl * (1e9 * kParsec / kClight);
-    const double ampd = kPi * 0.816496580927726 /* sqrt(2/3) */ * M * M * sqrt(eta) / dist;
+    const double ampd = kPi * 0.816496580927726 /* sqrt(2/3) */ * M * M * sqrt(eta) * idist;
     const double amp76d = ampd * (icb * icb * icb) * sqrt(icb);   // (pi M)^{-7/6} = icb^{7/2}
     wf.amp = (float)ampd;
     wf.amp76 = (float)amp76d;

@@ -298,9 +298,26 @@ def test_het_full_size_sampled(year, M, WL, oracle):
     err, scale = _lnl_err(omx[:, sample], out_o, ref_o["dd"])
     print("year het mixed sampled: abs p50/max", np.median(err), err.max(), "rel max", (err / scale).max())
     assert np.all(err <= 1e-6 * scale)
-    # every walker, mixed against the float64 kernel (itself held to the oracle above): the
-    # stated bound |dlnL| <= 1e-3 for at least 99.5 % of these far walkers, none beyond 5e-3
+    # every walker, mixed against the float64 kernel (itself held to the oracle above), relative
+    # to the likelihood's terms: float32 rounding makes |dlnL| grow with <h|h> (this source is
+    # louder than the benchmark's), so the SNR-free statement is relative
+    err, scale = _lnl_err(omx, o64, year["src"].data.dd)
+    print("year het mixed vs fp64: abs p50/max", np.median(err), err.max(), "rel max", (err / scale).max())
+    assert np.all(err <= 2e-8 * scale)
+
+
+def test_het_mixed_benchmark_accuracy(M, WL):
+    """The benchmark's heterodyne batch (workload 2: 16384 walkers 1e-3..1e-1 from the
+    injection, 256 bins, 1-yr grid): mixed precision within |dlnL| <= 1e-3 of the float64
+    kernel for at least 99.5 % of the walkers, none beyond 5e-3."""
+    g = I.grid_year()
+    src = WL.source_for(2, g)
+    ref = M.het_prepare_reference(src.data, src.theta_inj, 256)
+    W = 16384
+    th = WL.to_dev(WL.walkers(src.theta_inj, W, 2))
+    o64 = M.het_loglike_batch([ref], [0, W], th, "fp64").cpu().numpy()
+    omx = M.het_loglike_batch([ref], [0, W], th, "mixed").cpu().numpy()
     d = np.abs(omx[0] - o64[0])
-    print("year het mixed vs fp64: p50/p99/max", np.median(d), np.quantile(d, 0.99), d.max(),
+    print("workload 2 mixed vs fp64: p50/p99/max", np.median(d), np.quantile(d, 0.99), d.max(),
           "frac <= 1e-3", np.mean(d <= 1e-3))
     assert np.mean(d <= 1e-3) >= 0.995 and d.max() <= 5e-3
