@@ -1135,6 +1135,7 @@ __device__ __forceinline__ void het_mixed_body(const HetLaunch& L)
     constexpr int WPB = BLOCK / G;
     __shared__ WalkerDF wsd[WPB];
     __shared__ WalkerF wsf[WPB];
+    __shared__ float4 sums[WPB];   // per walker <d|h>, <h|h> partial sums (float pairs)
     const int lw = threadIdx.x / G, lane = threadIdx.x % G;
     for (int tile = blockIdx.x; tile < L.n_tiles; tile += gridDim.x) {
         int s = 0;
@@ -1203,14 +1204,20 @@ __device__ __forceinline__ void het_mixed_body(const HetLaunch& L)
             df_acc(adh, odh);
             df_acc(ahh, ohh);
         }
-        if (active && lane == 0) {
-            const double fix = amp_fix(wsf[lw].eps_amp76, S.mix.amp_eps0);
-            const double dh = 4.0 * (S.mix.sumA0 + df_to_double(adh)) * fix;
-            const double hh = 4.0 * (S.mix.sumB0 + df_to_double(ahh)) * (fix * fix);
-            L.out[wi] = -0.5 * (S.dd + hh - 2.0 * dh);
-            L.out[L.W + wi] = dh;
-            L.out[2 * L.W + wi] = hh;
-        }
+        // float64 epilogue on consecutive threads (as the setup: a float64 warp instruction costs
+        // the same for 32/G or 32 walkers)
+        if (lane == 0) sums[lw] = make_float4(adh.hi, adh.lo, ahh.hi, ahh.lo);
+        __syncthreads();
+        for (int j = threadIdx.x; j < WPB; j += BLOCK)
+            if (w0 + j < S.w_end) {
+                const float4 v = sums[j];
+                const double fix = amp_fix(wsf[j].eps_amp76, S.mix.amp_eps0);
+                const double dh = 4.0 * (S.mix.sumA0 + df_to_double({v.x, v.y})) * fix;
+                const double hh = 4.0 * (S.mix.sumB0 + df_to_double({v.z, v.w})) * (fix * fix);
+                L.out[w0 + j] = -0.5 * (S.dd + hh - 2.0 * dh);
+                L.out[L.W + w0 + j] = dh;
+                L.out[2 * L.W + w0 + j] = hh;
+            }
     }
 }
 
@@ -1238,6 +1245,7 @@ __global__ void __launch_bounds__(BLOCK)
     __shared__ WalkerDF wsd[WPB];
     __shared__ WalkerF wsf[WPB];
     __shared__ WalkerHMF wsh[WPB];
+    __shared__ float4 sums[WPB];   // per walker <d|h>, <h|h> partial sums (float pairs)
     const int lw = threadIdx.x / G, lane = threadIdx.x % G;
     for (int tile = blockIdx.x; tile < L.n_tiles; tile += gridDim.x) {
         int s = 0;
@@ -1317,14 +1325,20 @@ __global__ void __launch_bounds__(BLOCK)
             df_acc(adh, odh);
             df_acc(ahh, ohh);
         }
-        if (active && lane == 0) {
-            const double fix = amp_fix(wsf[lw].eps_amp76, S.mix.amp_eps0);
-            const double dh = 4.0 * (S.mix.sumA0 + df_to_double(adh)) * fix;
-            const double hh = 4.0 * (S.mix.sumB0 + df_to_double(ahh)) * (fix * fix);
-            L.out[wi] = -0.5 * (S.dd + hh - 2.0 * dh);
-            L.out[L.W + wi] = dh;
-            L.out[2 * L.W + wi] = hh;
-        }
+        // float64 epilogue on consecutive threads (as the setup: a float64 warp instruction costs
+        // the same for 32/G or 32 walkers)
+        if (lane == 0) sums[lw] = make_float4(adh.hi, adh.lo, ahh.hi, ahh.lo);
+        __syncthreads();
+        for (int j = threadIdx.x; j < WPB; j += BLOCK)
+            if (w0 + j < S.w_end) {
+                const float4 v = sums[j];
+                const double fix = amp_fix(wsf[j].eps_amp76, S.mix.amp_eps0);
+                const double dh = 4.0 * (S.mix.sumA0 + df_to_double({v.x, v.y})) * fix;
+                const double hh = 4.0 * (S.mix.sumB0 + df_to_double({v.z, v.w})) * (fix * fix);
+                L.out[w0 + j] = -0.5 * (S.dd + hh - 2.0 * dh);
+                L.out[L.W + w0 + j] = dh;
+                L.out[2 * L.W + w0 + j] = hh;
+            }
     }
 }
 
@@ -1343,6 +1357,7 @@ __device__ __forceinline__ void het_mixed_pt_body(const HetLaunch& L)
     __shared__ double ys[WPB][pt::kPar];
     __shared__ double facs[WPB];
     __shared__ int32_t flags[WPB];
+    __shared__ float4 sums[WPB];   // per walker <d|h>, <h|h> partial sums (float pairs)
     const pt::PtArgs& A = *static_cast<const pt::PtArgs*>(L.pt);
     const int half = L.pt_half;
     const int lw = threadIdx.x / G, lane = threadIdx.x % G;
@@ -1420,27 +1435,32 @@ __device__ __forceinline__ void het_mixed_pt_body(const HetLaunch& L)
             df_acc(adh, odh);
             df_acc(ahh, ohh);
         }
-        if (active && lane == 0) {
-            const double fix = amp_fix(wsf[lw].eps_amp76, S.mix.amp_eps0);
-            const double dh = 4.0 * (S.mix.sumA0 + df_to_double(adh)) * fix;
-            const double hh = 4.0 * (S.mix.sumB0 + df_to_double(ahh)) * (fix * fix);
-            const double lnl = -0.5 * (S.dd + hh - 2.0 * dh);
-            int32_t col;
-            int t, cb;
-            const int32_t flag = flags[lw];
-            const int kind = flag >> 1;
-            const bool acc = pt::accept_test(A, half, (int32_t)wi, lnl, facs[lw], flag, col, t, cb);
-            atomicAdd(&A.counters[cb + t * 4 + kind], 1ull);
-            if (acc) {
-                atomicAdd(&A.counters[cb + 4 * A.T + t * 4 + kind], 1ull);
-                const int64_t N = (int64_t)A.n_ens * A.T * A.W;
+        // float64 epilogue and acceptance on consecutive threads (full warps)
+        if (lane == 0) sums[lw] = make_float4(adh.hi, adh.lo, ahh.hi, ahh.lo);
+        __syncthreads();
+        for (int j = threadIdx.x; j < WPB; j += BLOCK)
+            if (w0 + j < S.w_end) {
+                const float4 v = sums[j];
+                const double fix = amp_fix(wsf[j].eps_amp76, S.mix.amp_eps0);
+                const double dh = 4.0 * (S.mix.sumA0 + df_to_double({v.x, v.y})) * fix;
+                const double hh = 4.0 * (S.mix.sumB0 + df_to_double({v.z, v.w})) * (fix * fix);
+                const double lnl = -0.5 * (S.dd + hh - 2.0 * dh);
+                int32_t col;
+                int t, cb;
+                const int32_t flag = flags[j];
+                const int kind = flag >> 1;
+                const bool acc = pt::accept_test(A, half, (int32_t)(w0 + j), lnl, facs[j], flag, col, t, cb);
+                atomicAdd(&A.counters[cb + t * 4 + kind], 1ull);
+                if (acc) {
+                    atomicAdd(&A.counters[cb + 4 * A.T + t * 4 + kind], 1ull);
+                    const int64_t N = (int64_t)A.n_ens * A.T * A.W;
 #pragma unroll
-                for (int p = 0; p < pt::kPar; ++p) A.x[p * N + col] = ys[lw][p];
-                A.out[col] = lnl;
-                A.out[N + col] = dh;
-                A.out[2 * N + col] = hh;
+                    for (int p = 0; p < pt::kPar; ++p) A.x[p * N + col] = ys[j][p];
+                    A.out[col] = lnl;
+                    A.out[N + col] = dh;
+                    A.out[2 * N + col] = hh;
+                }
             }
-        }
     }
 }
 
