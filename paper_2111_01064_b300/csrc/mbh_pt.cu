@@ -33,6 +33,7 @@
 #include <new>
 #include <vector>
 
+#include "mbh_df.cuh"
 #include "mbh_internal.cuh"
 #include "mbh_pt.cuh"
 
@@ -150,6 +151,28 @@ __global__ void __launch_bounds__(kSortThreads) pt_perm_kernel(const PtArgs A, i
         A.perm[((int64_t)e * A.T + i) * A.W + k] = (int32_t)(keys[k] & 0xFFFFull);
 }
 
+// The swap test cu < db (lh - lc) exactly as float64 decides it, without float64 instructions
+// in all but ~1e-7 of the cases (one SM's float64 pipe would otherwise bound the swap levels):
+// the operands as float pairs (integer splitting, 2^-48 relative), the difference and the
+// product in float32 with a bound on their error, float64 only inside that bound.
+__device__ __forceinline__ bool swap_test(double cu, double db, float dbf, double lh, double lc)
+{
+    const auto finite_small = [](double x) {   // |x| < 2^100 (and finite): the split is exact enough
+        return ((unsigned long long)__double_as_longlong(x) >> 52 & 0x7ffull) < 1023ull + 100ull;
+    };
+    if (finite_small(lh) && finite_small(lc) && finite_small(cu)) {
+        const f2 a = split_f64(lh, 0), b = split_f64(lc, 0), u = split_f64(cu, 0);
+        const float d = (a.hi - b.hi) + (a.lo - b.lo);
+        const float la = dbf * d, uf = u.hi + u.lo;
+        // float32 rounding of the difference, product and ln u (a few 1e-7 relative), the pairs'
+        // 2^-48 and the pair-split of db, with a factor ~4 of margin
+        const float err = 2e-6f * (fabsf(la) + fabsf(uf)) + 1e-13f * dbf * (fabsf(a.hi) + fabsf(b.hi)) + 1e-37f;
+        if (uf < la - err) return true;
+        if (uf > la + err) return false;
+    }
+    return cu < __dmul_rn(db, __dsub_rn(lh, lc));
+}
+
 // After the swap levels (thread 0 of an ensemble's block): ladder adaptation from this
 // iteration's swap acceptances, then the last ensemble block to finish advances the step.
 __device__ void swap_epilogue(const PtArgs& A, double* betas, const unsigned int* acc_now, uint64_t step)
@@ -250,14 +273,14 @@ __global__ void __launch_bounds__(kSortThreads) pt_swap_kernel(const PtArgs A)
             __syncthreads();
             if (i > 1) issue(i - 1);   // in flight while this level is decided
             const double db = __dsub_rn(betas[i - 1], betas[i]);
+            const float dbf = (float)db;
             unsigned int mine = 0;
 #pragma unroll
             for (int j = 0; j < J; ++j) {
                 const int k = threadIdx.x + j * blockDim.x;
                 if (k >= W) continue;
                 const int h = cp[j];
-                const double la = __dmul_rn(db, __dsub_rn(lnl[hot * W + h], lnl[cold * W + k]));
-                if (cu[j] < la) {
+                if (swap_test(cu[j], db, dbf, lnl[hot * W + h], lnl[cold * W + k])) {
                     const double l = lnl[hot * W + h];
                     lnl[hot * W + h] = lnl[cold * W + k];
                     lnl[cold * W + k] = l;
@@ -334,6 +357,7 @@ __global__ void __launch_bounds__(kSortThreads) pt_swap_resident_kernel(const Pt
         for (int i = T - 1; i >= 1; --i) {
             if (i > 1) load(i - 1, np, nu);   // in flight while this level is decided
             const double db = __dsub_rn(bs[i - 1], bs[i]);
+            const float dbf = (float)db;
             double* lh = lnl + i * W;
             double* lc = lnl + (i - 1) * W;
             int32_t* mh = mp + i * W;
@@ -344,8 +368,7 @@ __global__ void __launch_bounds__(kSortThreads) pt_swap_resident_kernel(const Pt
                 const int k = threadIdx.x + j * blockDim.x;
                 if (k >= W) continue;
                 const int h = cp[j];
-                const double la = __dmul_rn(db, __dsub_rn(lh[h], lc[k]));
-                if (cu[j] < la) {
+                if (swap_test(cu[j], db, dbf, lh[h], lc[k])) {
                     const double l = lh[h];
                     lh[h] = lc[k];
                     lc[k] = l;
