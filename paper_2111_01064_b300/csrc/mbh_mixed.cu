@@ -567,6 +567,13 @@ __device__ inline void walker_setup_hm(const double* __restrict__ theta, int64_t
         }
 }
 
+// modes (mask bits) of the four values of m: group 0 m = 2 ((2,2), (3,2)), 1 m = 3 ((3,3),
+// (4,3)), 2 m = 4 ((4,4)), 3 m = 1 ((2,1))
+__host__ __device__ constexpr uint32_t hm_group_mask(int grp)
+{
+    return grp == 0 ? 0x11u : grp == 1 ? 0x22u : grp == 2 ? 0x04u : 0x08u;
+}
+
 // v^{p_lm} in float32 from f2^{1/3} and (pi M)^{1/3}
 __device__ __forceinline__ float mode_vpow(const WalkerDF& w, const FreqDF& q2, int b)
 {
@@ -1021,13 +1028,22 @@ __global__ void edge_mixed_hm_kernel(const double* __restrict__ theta0, double t
             base[e * 3 + c] = m2 > 0.0 ? 0.0f : -1.0f;
             if (!(m2 > 0.0)) continue;
             const double ir = h0[c].re / m2, ii = -h0[c].im / m2;   // 1/h0
-            for (int b = 0; b < kHmModes; ++b) {
-                if (!(modes & (1u << b))) continue;
-                MixModeHM& mm = hm[(int64_t)e * kHmModes + b];
-                const cd hb = h0m[b][c];
-                mm.u[c] = make_float2((float)(hb.re * ir - hb.im * ii), (float)(hb.re * ii + hb.im * ir));
+            // per group of modes with the same m (same phase and g), the u summed into the
+            // record of its first mode, which the kernel reads for the whole group
+            for (int grp = 0; grp < 4; ++grp) {
+                const uint32_t gmask = modes & hm_group_mask(grp);
+                if (!gmask) continue;
+                const int b0 = __ffs(gmask) - 1;
+                double usr = 0.0, usi = 0.0;
+                for (uint32_t bm = gmask; bm; bm &= bm - 1) {
+                    const cd hb = h0m[__ffs(bm) - 1][c];
+                    usr += hb.re * ir - hb.im * ii;
+                    usi += hb.re * ii + hb.im * ir;
+                }
+                MixModeHM& mm = hm[(int64_t)e * kHmModes + b0];
+                mm.u[c] = make_float2((float)usr, (float)usi);
                 // K e'/h0, e' = f2^{-7/6} e^{-i Phi0_lm}
-                const double er = Kr[c] * gr[b] - Ki[c] * gi[b], ei = Kr[c] * gi[b] + Ki[c] * gr[b];
+                const double er = Kr[c] * gr[b0] - Ki[c] * gi[b0], ei = Kr[c] * gi[b0] + Ki[c] * gr[b0];
                 mm.g[c] = make_float2((float)(er * ir - ei * ii), (float)(er * ii + ei * ir));
             }
         }
@@ -1275,25 +1291,39 @@ __global__ void __launch_bounds__(BLOCK)
                 const FreqDF q = {ld_f2(me.f), ld_f2(me.f3), ld_f2(me.fm3), ld_f2(me.lnf3)};
 #pragma unroll
                 for (int c = 0; c < 3; ++c) dl[c].re = S.mix.hm_base[e * 3 + c];
-                for (int b = 0; b < kHmModes; ++b) {
-                    if (!(modes & (1u << b))) continue;
-                    const MixModeHM mm = S.mix.hm[(int64_t)e * kHmModes + b];
-                    const FreqDF q2 = mode_tables(q, b);
+                // Modes with the same m share f2 = 2f/m, so the phase chain, t(f2), the orbit, the
+                // reference's phase and g: one chain and one transfer per distinct m, with the
+                // modes' factors summed weighted by v^{p_lm} (the transfer is linear in them) and
+                // the group's u summed in its first mode's record (edge_mixed_hm_kernel).
+                for (int grp = 0; grp < 4; ++grp) {
+                    const uint32_t gmask = modes & hm_group_mask(grp);
+                    if (!gmask) continue;
+                    const int b0 = __ffs(gmask) - 1;   // the group's first mode
+                    const MixModeHM mm = S.mix.hm[(int64_t)e * kHmModes + b0];
+                    const FreqDF q2 = mode_tables(q, b0);
                     f2 Phi;
                     float sa, ca, amp;
                     if (phase_df<false, true>(wsd[lw], wsf[lw], q2, tob, Phi, sa, ca, amp)) {
                         float sh, ch;
-                        sincos_small(0.5f * reduce_phase(dd_add_lazy(mode_phase(Phi, b), {-mm.phi0.x, -mm.phi0.y})),
+                        sincos_small(0.5f * reduce_phase(dd_add_lazy(mode_phase(Phi, b0), {-mm.phi0.x, -mm.phi0.y})),
                                      &sh, &ch);
                         const cf em1 = {-2.0f * sh * sh, -2.0f * sh * ch};   // e^{-i dPhi} - 1
+                        float gk[4] = {0.f, 0.f, 0.f, 0.f}, gl[4] = {0.f, 0.f, 0.f, 0.f};
+                        for (uint32_t bm = gmask; bm; bm &= bm - 1) {
+                            const int b = __ffs(bm) - 1;
+                            const float vp = mode_vpow(wsd[lw], q2, b);
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                gk[j] = fmaf(vp, wsh[lw].hk[b][j], gk[j]);
+                                gl[j] = fmaf(vp, wsh[lw].hklo[b][j], gl[j]);
+                            }
+                        }
                         cf T[3];
-                        transfer_f32<true>(wsf[lw], &wsh[lw].hk[b][0], &wsh[lw].hk[b][2], me.xs.w, sa, ca, 1.0f,
-                                           me.xs.x, me.xs.y, T, &wsh[lw].hklo[b][0]);
-                        const float a = amp * mode_vpow(wsd[lw], q2, b);
+                        transfer_f32<true>(wsf[lw], &gk[0], &gk[2], me.xs.w, sa, ca, 1.0f, me.xs.x, me.xs.y, T, gl);
 #pragma unroll
                         for (int c = 0; c < 3; ++c) {
                             const cf u = {mm.u[c].x, mm.u[c].y};
-                            const cf ac = fsub(fmul(fscale(T[c], a), {mm.g[c].x, mm.g[c].y}), u);
+                            const cf ac = fsub(fmul(fscale(T[c], amp), {mm.g[c].x, mm.g[c].y}), u);
                             dl[c] = fadd(dl[c], fadd(fadd(ac, fmul(ac, em1)), fmul(u, em1)));
                         }
                     } else {
