@@ -621,17 +621,27 @@ __device__ __forceinline__ bool point_mixed_hm(const WalkerDF& w, const WalkerF&
 {
     h[0] = h[1] = h[2] = {0.0f, 0.0f};
     bool any = false;
-    for (int b = 0; b < kHmModes; ++b) {
-        if (!(modes & (1u << b))) continue;
-        const FreqDF q2 = mode_tables(q, b);
+    // one phase chain and one response per distinct m (as het_mixed_hm_kernel)
+    for (int grp = 0; grp < 4; ++grp) {
+        const uint32_t gmask = modes & hm_group_mask(grp);
+        if (!gmask) continue;
+        const int b0 = __ffs(gmask) - 1;
+        const FreqDF q2 = mode_tables(q, b0);
         f2 Phi;
         float sa, ca, amp;
         if (!phase_df(w, wf, q2, t_obs, Phi, sa, ca, amp)) continue;
         any = true;
         float sp, cp;
-        sincos_small(reduce_phase(mode_phase(Phi, b)), &sp, &cp);
+        sincos_small(reduce_phase(mode_phase(Phi, b0)), &sp, &cp);
+        float gk[4] = {0.f, 0.f, 0.f, 0.f};
+        for (uint32_t bm = gmask; bm; bm &= bm - 1) {
+            const int b = __ffs(bm) - 1;
+            const float vp = mode_vpow(w, q2, b);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) gk[j] = fmaf(vp, wh.hk[b][j], gk[j]);
+        }
         cf T[3];
-        transfer_f32(wf, &wh.hk[b][0], &wh.hk[b][2], q.f.hi, sa, ca, amp * mode_vpow(w, q2, b) * scale, T);
+        transfer_f32(wf, &gk[0], &gk[2], q.f.hi, sa, ca, amp * scale, T);
         const cf e = {cp, -sp};
 #pragma unroll
         for (int c = 0; c < 3; ++c) h[c] = fadd(h[c], fmul(e, T[c]));
