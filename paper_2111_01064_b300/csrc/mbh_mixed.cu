@@ -1199,8 +1199,8 @@ __device__ __forceinline__ void het_mixed_body(const HetLaunch& L)
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         const cf rho = fmul(fscale(T[c], amp), {me.h0inv[c].x, me.h0inv[c].y});
-                        const cf rm1 = {rho.re - 1.0f, rho.im};
-                        dl[c] = fadd(fadd(rm1, fmul(rm1, em1)), em1);
+                        // delta = rho e^{-i dPhi} - 1 = (rho - 1) + rho (e^{-i dPhi} - 1)
+                        dl[c] = fadd({rho.re - 1.0f, rho.im}, fmul(rho, em1));
                     }
                 } else {
 #pragma unroll
@@ -1444,8 +1444,8 @@ __device__ __forceinline__ void het_mixed_pt_body(const HetLaunch& L)
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         const cf rho = fmul(fscale(T[c], amp), {me.h0inv[c].x, me.h0inv[c].y});
-                        const cf rm1 = {rho.re - 1.0f, rho.im};
-                        dl[c] = fadd(fadd(rm1, fmul(rm1, em1)), em1);
+                        // delta = rho e^{-i dPhi} - 1 = (rho - 1) + rho (e^{-i dPhi} - 1)
+                        dl[c] = fadd({rho.re - 1.0f, rho.im}, fmul(rho, em1));
                     }
                 } else {
 #pragma unroll
