@@ -159,6 +159,9 @@ struct mbh_data {
     float2* vsp = nullptr;   // [3][n] float pair of 2^(2 shift) 4 df/S
     float4* ftab = nullptr;  // [n] (f hi, f lo, f^{1/3} hi, f^{1/3} lo) of the grid
     float4* ftab2 = nullptr; // [n] (f^{-1/3} hi, lo, ln(f)/3 hi, lo)
+    float4* ftab3 = nullptr; // [n] (sin x, cos x, 0, x), x = pi f L/c (the one-link phase)
+    float2* wdk = nullptr;   // [3][n] conj(K_c) sigma 4 df d/S: the fused mixed pass's data, with the
+    float* wvk = nullptr;    // [3][n] |K_c|^2 sigma^2 4 df/S  frequency-only factors K_c folded in
     double sigma = 1.0;      // scale of the float32 copies: h/sigma is O(1)
     int shift = 0;           // round(log2 sigma): templates are split as h 2^-shift
     double dd = 0.0;         // <d|d>

@@ -353,6 +353,9 @@ extern "C" void mbh_data_free(mbh_data* data)
     if (data->vsp) cudaFree(data->vsp);
     if (data->ftab) cudaFree(data->ftab);
     if (data->ftab2) cudaFree(data->ftab2);
+    if (data->ftab3) cudaFree(data->ftab3);
+    if (data->wdk) cudaFree(data->wdk);
+    if (data->wvk) cudaFree(data->wvk);
     delete data;
 }
 

@@ -595,6 +595,26 @@ __device__ __forceinline__ float reduce_phase(f2 p)
     return r + fmaf(-n, kTwoPiDF.lo, p.lo);
 }
 
+// Raw mixed template at one grid point (without the frequency-only factors K_c, which the
+// fused pass folds into its data): amp76 e^{-(f/f_c)^2} e^{-i Phi} T_raw, times `scale`; xs holds
+// sin x, cos x and x of the point (ftab3).
+__device__ __forceinline__ bool point_mixed_raw(const WalkerDF& w, const WalkerF& wf, const FreqDF& q,
+                                                float4 xs, f2 t_obs, float scale, cf h[3])
+{
+    f2 Phi;
+    float sa, ca, amp;
+    if (!phase_df<false, true>(w, wf, q, t_obs, Phi, sa, ca, amp)) return false;
+    float sp, cp;
+    sincos_small(reduce_phase(Phi), &sp, &cp);
+    cf T[3];
+    transfer_f32<true>(wf, wf.Ga, wf.Gb, xs.w, sa, ca, 1.0f, xs.x, xs.y, T, wf.Glo);
+    const float a = amp * scale;
+    const cf e = {a * cp, -a * sp};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) h[c] = fmul(e, T[c]);
+    return true;
+}
+
 // Mixed template at one grid point: h = amp e^{-i Phi} T (float32 result, times `scale`).
 __device__ __forceinline__ bool point_mixed(const WalkerDF& w, const WalkerF& wf, const FreqDF& q,
                                             f2 t_obs, float scale, cf h[3])
@@ -754,11 +774,14 @@ constexpr int kDirThreadsM = 256;
 // float64 sums in shared memory (a dynamically indexed register array would go to local
 // memory), reduced per walker at the end.  Data and templates are in units where h/sigma is
 // O(1) (float32 range); per-point products are float32, sums float64.
+constexpr int kDirFlush = 16;   // points per float32 partial sum in the fused mixed pass
+
 template <int T, bool kHM>
 __global__ void __launch_bounds__(kDirThreadsM, 2)
     direct_fused_mixed_kernel(const double* __restrict__ theta, int64_t W, const float4* __restrict__ ft1,
-                              const float4* __restrict__ ft2, double t_obs,
+                              const float4* __restrict__ ft2, const float4* __restrict__ ft3, double t_obs,
                               const float2* __restrict__ wd, const float* __restrict__ wv,
+                              const float2* __restrict__ wdk, const float* __restrict__ wvk,
                               int64_t n, int64_t chunk, int nchunks, float inv_sigma, uint32_t modes,
                               double2* __restrict__ part)
 {
@@ -766,6 +789,7 @@ __global__ void __launch_bounds__(kDirThreadsM, 2)
     __shared__ WalkerF wsf[T];
     __shared__ WalkerHMF wsh[kHM ? T : 1];
     __shared__ double2 acc[T][kDirThreadsM];
+    __shared__ float2 facc[T][kDirThreadsM];
     __shared__ double sm[32 * 2];
     const int64_t w0 = (int64_t)blockIdx.x * T;
     const int ch = blockIdx.y;
@@ -775,24 +799,33 @@ __global__ void __launch_bounds__(kDirThreadsM, 2)
         if (kHM) walker_setup_hm(theta, W, w0 + threadIdx.x, wsh[threadIdx.x]);
     }
 #pragma unroll
-    for (int t = 0; t < T; ++t) acc[t][threadIdx.x] = make_double2(0.0, 0.0);
+    for (int t = 0; t < T; ++t) {
+        acc[t][threadIdx.x] = make_double2(0.0, 0.0);
+        facc[t][threadIdx.x] = make_float2(0.0f, 0.0f);
+    }
     const f2 tob = split_d(t_obs);
     __syncthreads();
     const int64_t kb = (int64_t)ch * chunk, ke = std::min<int64_t>(n, kb + chunk);
+    int since = 0;
     for (int64_t k = kb + threadIdx.x; k < ke; k += kDirThreadsM) {
         const float4 a = __ldg(ft1 + k), b = __ldg(ft2 + k);
         const FreqDF q = {{a.x, a.y}, {a.z, a.w}, {b.x, b.y}, {b.z, b.w}};
+        // (2,2): raw templates against the folded data (folded_data_kernel); higher modes: full
+        // templates against the scaled data
+        const float2* wdc = kHM ? wd : wdk;
+        const float* wvc = kHM ? wv : wvk;
         float2 d[3];
         float v[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            d[c] = __ldg(wd + (int64_t)c * n + k);
-            v[c] = __ldg(wv + (int64_t)c * n + k);
+            d[c] = __ldg(wdc + (int64_t)c * n + k);
+            v[c] = __ldg(wvc + (int64_t)c * n + k);
         }
+        const float4 xs = kHM ? make_float4(0.f, 0.f, 0.f, 0.f) : __ldg(ft3 + k);
         for (int t = 0; t < nt; ++t) {
             cf h[3];
             const bool in = kHM ? point_mixed_hm(wsd[t], wsf[t], wsh[t], q, tob, inv_sigma, modes, h)
-                                : point_mixed(wsd[t], wsf[t], q, tob, inv_sigma, h);
+                                : point_mixed_raw(wsd[t], wsf[t], q, xs, tob, inv_sigma, h);
             if (in) {
                 float pd = 0.0f, ph = 0.0f;
 #pragma unroll
@@ -800,28 +833,94 @@ __global__ void __launch_bounds__(kDirThreadsM, 2)
                     pd += d[c].x * h[c].re + d[c].y * h[c].im;
                     ph += v[c] * (h[c].re * h[c].re + h[c].im * h[c].im);
                 }
+                float2 f = facc[t][threadIdx.x];
+                f.x += pd;
+                f.y += ph;
+                facc[t][threadIdx.x] = f;
+            }
+        }
+        // float32 partial sums of up to kDirFlush points go into the float64 accumulators (the
+        // conversions and adds run on the float64 pipe: once per kDirFlush points, not per point)
+        if (++since == kDirFlush) {
+            since = 0;
+            for (int t = 0; t < nt; ++t) {
+                const float2 f = facc[t][threadIdx.x];
                 double2 s2 = acc[t][threadIdx.x];
-                s2.x += (double)pd;
-                s2.y += (double)ph;
+                s2.x += (double)f.x;
+                s2.y += (double)f.y;
                 acc[t][threadIdx.x] = s2;
+                facc[t][threadIdx.x] = make_float2(0.0f, 0.0f);
             }
         }
     }
     for (int t = 0; t < nt; ++t) {
+        const float2 f = facc[t][threadIdx.x];
+        double2 s2 = acc[t][threadIdx.x];
+        s2.x += (double)f.x;
+        s2.y += (double)f.y;
+        acc[t][threadIdx.x] = s2;
+    }
+    for (int t = 0; t < nt; ++t) {
         double r[2] = {acc[t][threadIdx.x].x, acc[t][threadIdx.x].y};
         block_sum<2>(r, sm);
-        if (threadIdx.x == 0) part[(w0 + t) * nchunks + ch] = make_double2(r[0], r[1]);
+        if (threadIdx.x == 0) {
+            // the raw (2,2) templates used the float32 amp76: undo its rounding (a pure scale)
+            const double fix = kHM ? 1.0 : 1.0 + (double)wsf[t].eps_amp76;
+            part[(w0 + t) * nchunks + ch] = make_double2(r[0] * fix, r[1] * (fix * fix));
+        }
     }
 }
 
+// frequency-only inputs of an edge, rounded once from float64: sin and cos of the one-link
+// phase x = pi f L/c, and x
+__device__ __forceinline__ float4 edge_xs(double f)
+{
+    const double x = kPi * kArmSec * f;
+    double s, c;
+    sincos(x, &s, &c);
+    return make_float4((float)s, (float)c, 0.0f, (float)x);
+}
+
 __global__ void freq_table_kernel(double f0, double df, int64_t n, float4* __restrict__ t1,
-                                  float4* __restrict__ t2)
+                                  float4* __restrict__ t2, float4* __restrict__ t3)
 {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
          k += (int64_t)gridDim.x * blockDim.x) {
-        const FreqDF q = freq_tables(f0 + (double)k * df);
+        const double f = f0 + (double)k * df;
+        const FreqDF q = freq_tables(f);
         t1[k] = make_float4(q.f.hi, q.f.lo, q.f3.hi, q.f3.lo);
         t2[k] = make_float4(q.fm3.hi, q.fm3.lo, q.lnf3.hi, q.lnf3.lo);
+        t3[k] = edge_xs(f);
+    }
+}
+
+// The fused mixed pass's data with the template's frequency-only factors folded in (float64,
+// rounded once): with h_c = K_c H_c (H_c the raw float32 template of transfer_f32<true> and
+// phase_df<.., true>, K_c as in the heterodyne's edge records, including f^{-7/6}),
+// Re conj(D_c) h_c = Re conj(conj(K_c) D_c) H_c and |h_c|^2 V_c = |H_c|^2 |K_c|^2 V_c.
+__global__ void folded_data_kernel(double f0, double df, int64_t n, double sigma, const double2* __restrict__ wd,
+                                   const double* __restrict__ wv, float2* __restrict__ wdk,
+                                   float* __restrict__ wvk)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const double f = f0 + (double)k * df;
+        const double x = kPi * kArmSec * f;
+        double s1, c1, s3, c3;
+        sincos(x, &s1, &c1);
+        sincos(3.0 * x, &s3, &c3);
+        const double wm = -2.0 * x * (2.0 * s1 * c1) * pow(f, -7.0 / 6.0);
+        const double wr = wm * s3, wi = wm * c3;
+        const double ar = 2.0 * s1 * s1, ai = 2.0 * s1 * c1;
+        const double Kr[3] = {wr / kSqrt2, wr / kSqrt6, (wr * ar - wi * ai) / kSqrt3};
+        const double Ki[3] = {wi / kSqrt2, wi / kSqrt6, (wr * ai + wi * ar) / kSqrt3};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double2 d = wd[c * n + k];
+            const double dr = sigma * d.x, di = sigma * d.y;   // conj(K) D
+            wdk[c * n + k] = make_float2((float)(Kr[c] * dr + Ki[c] * di), (float)(Kr[c] * di - Ki[c] * dr));
+            wvk[c * n + k] = (float)(sigma * sigma * wv[c * n + k] * (Kr[c] * Kr[c] + Ki[c] * Ki[c]));
+        }
     }
 }
 
@@ -830,9 +929,13 @@ mbh_status mbh::make_freq_tables(mbh_data* D, cudaStream_t st)
     const int64_t n = D->grid.n;
     cudaError_t e = cudaMalloc(&D->ftab, sizeof(float4) * n);
     if (e == cudaSuccess) e = cudaMalloc(&D->ftab2, sizeof(float4) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&D->ftab3, sizeof(float4) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&D->wdk, sizeof(float2) * 3 * n);
+    if (e == cudaSuccess) e = cudaMalloc(&D->wvk, sizeof(float) * 3 * n);
     if (e != cudaSuccess) return cuda_fail(e, "frequency tables");
     const int blocks = (int)std::min<int64_t>((n + 255) / 256, 148 * 32);
-    freq_table_kernel<<<blocks, 256, 0, st>>>(D->grid.f0, D->grid.df, n, D->ftab, D->ftab2);
+    freq_table_kernel<<<blocks, 256, 0, st>>>(D->grid.f0, D->grid.df, n, D->ftab, D->ftab2, D->ftab3);
+    folded_data_kernel<<<blocks, 256, 0, st>>>(D->grid.f0, D->grid.df, n, D->sigma, D->wd, D->wv, D->wdk, D->wvk);
     e = cudaGetLastError();
     return e == cudaSuccess ? MBH_OK : cuda_fail(e, "frequency tables");
 }
@@ -852,12 +955,12 @@ mbh_status mbh::launch_direct_fused_mixed(const mbh_data* data, const double* th
     dim3 grid((unsigned)tiles, (unsigned)nchunks);
     if (modes == 1u)
         direct_fused_mixed_kernel<T, false><<<grid, kDirThreadsM, 0, st>>>(
-            theta, W, data->ftab, data->ftab2, data->grid.t_obs, data->wd32, data->wv32,
-            data->grid.n, chunk, nchunks, (float)(1.0 / data->sigma), modes, part);
+            theta, W, data->ftab, data->ftab2, data->ftab3, data->grid.t_obs, data->wd32, data->wv32,
+            data->wdk, data->wvk, data->grid.n, chunk, nchunks, (float)(1.0 / data->sigma), modes, part);
     else
         direct_fused_mixed_kernel<T, true><<<grid, kDirThreadsM, 0, st>>>(
-            theta, W, data->ftab, data->ftab2, data->grid.t_obs, data->wd32, data->wv32,
-            data->grid.n, chunk, nchunks, (float)(1.0 / data->sigma), modes, part);
+            theta, W, data->ftab, data->ftab2, data->ftab3, data->grid.t_obs, data->wd32, data->wv32,
+            data->wdk, data->wvk, data->grid.n, chunk, nchunks, (float)(1.0 / data->sigma), modes, part);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "direct_fused_mixed_kernel");
     return direct_finish(part, nchunks, W, data->dd, out, st);
@@ -896,15 +999,6 @@ void mbh::free_ref_tables(mbh_ref* R)
     if (R->mix_hm_base) cudaFree(R->mix_hm_base);
 }
 
-// frequency-only inputs of an edge, rounded once from float64: sin and cos of the one-link
-// phase x = pi f L/c, and x
-__device__ __forceinline__ float4 edge_xs(double f)
-{
-    const double x = kPi * kArmSec * f;
-    double s, c;
-    sincos(x, &s, &c);
-    return make_float4((float)s, (float)c, 0.0f, (float)x);
-}
 
 // Edge records of the reference: its large phase Phi0 from the same double-float chain and edge
 // tables as the walkers (so that Phi - Phi0 cancels exactly for the reference itself), and
