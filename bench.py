@@ -80,7 +80,7 @@ def fp64_peak_gflops(sm_mhz: float) -> float:
 # FP32 lanes x SM clock.
 HET_MIXED_FMA_INST_PER_EDGE = 821
 HET_KERNEL = "het_mixed_kernel_capped<8,224>"
-HET_MIXED_DRAM_BYTES = 1.5808e6            # read + write per 16384-walker launch (ncu)
+HET_MIXED_DRAM_BYTES = 1.571072e6          # read + write per 16384-walker launch (ncu)
 STORED_DATA_BYTES = 75.74e6                # data pairs, read once per launch (ncu: 883.66 MB
 STORED_BYTES_PER_TEMPLATE = 50.4945e6      # for 16 templates = 75.74 MB + 16 x 50.49 MB)
 
