@@ -48,7 +48,7 @@ struct MixTables {
     double sumA0;          // sum_b sum_c Re A0
     double sumB0;          // sum_b sum_c B0
     const MixModeHM* hm;   // [E+1][6] (higher-mode references)
-    const float* hm_base;  // [E+1][3]: -1 where h0 = 0, else 0
+    const float2* hm_base;  // [E+1][3]: -1 where h0 = 0, else sum u - 1 of the stored u
     double amp_eps0;       // relative rounding of the reference's float32 amplitude factor
 };
 
@@ -187,6 +187,6 @@ struct mbh_ref {
     mbh::MixBin* mix_bin = nullptr;
     double* mix_sums = nullptr;    // device [2]
     mbh::MixModeHM* mix_hm = nullptr;   // higher-mode references: [E+1][6]
-    float* mix_hm_base = nullptr;       // [E+1][3]
+    float2* mix_hm_base = nullptr;      // [E+1][3]
     mbh::MixTables mix{};
 };

@@ -577,7 +577,8 @@ __host__ __device__ constexpr uint32_t hm_group_mask(int grp)
 // v^{p_lm} in float32 from f2^{1/3} and (pi M)^{1/3}
 __device__ __forceinline__ float mode_vpow(const WalkerDF& w, const FreqDF& q2, int b)
 {
-    const float v = w.cbrt_piM.hi * q2.f3.hi;
+    const f2 vv = dd_mul_lazy(w.cbrt_piM, q2.f3);   // both parts: the high parts' rounding
+    const float v = vv.hi + vv.lo;                     // would bias v^p for every edge alike
     const int p = hm_vpow(b);
     return p == 0 ? 1.0f : p == 1 ? v : p == 2 ? v * v : v * v * v;
 }
@@ -1065,13 +1066,15 @@ __global__ void edge_mixed_kernel(const double* __restrict__ theta0, double t_ob
 // double-float chain (defined also outside the mode's support), and per channel
 // u = h0_lm/h0 and g = K f2^{-7/6} e^{-i Phi0_lm}/h0 in float64 from the exact float64 mode
 // templates h0_lm (h0 = their sum), K the frequency-only factors of the walkers' raw transfer
-// and f2 = 2f/m (whose f2^{-7/6} the walkers' amplitude leaves out); base = -1 where h0 = 0
-// (r = 0 there).  A walker's delta = r - 1 is then
+// and f2 = 2f/m (whose f2^{-7/6} the walkers' amplitude leaves out); base = sum u - 1 of the
+// float32 u (float64 sum, rounded once: the float32 u do not sum to 1 exactly, and the offset
+// would be shared by every walker), -1 where h0 = 0 (r = 0 there).  A walker's delta = r - 1
+// is then
 //   base + sum_lm [a + a (e^{-i dPhi_lm} - 1) + u (e^{-i dPhi_lm} - 1)],  a = H_lm g - u,
 // with H_lm its raw float32 mode template; a mode outside the walker's support contributes -u.
 __global__ void edge_mixed_hm_kernel(const double* __restrict__ theta0, double t_obs, uint32_t modes,
                                      const double* __restrict__ fe, int n_edges, MixEdge* __restrict__ out,
-                                     MixModeHM* __restrict__ hm, float* __restrict__ base,
+                                     MixModeHM* __restrict__ hm, float2* __restrict__ base,
                                      double* __restrict__ eps0)
 {
     __shared__ WalkerDF wd;
@@ -1129,8 +1132,9 @@ __global__ void edge_mixed_hm_kernel(const double* __restrict__ theta0, double t
         }
         for (int c = 0; c < 3; ++c) {
             const double m2 = h0[c].re * h0[c].re + h0[c].im * h0[c].im;
-            base[e * 3 + c] = m2 > 0.0 ? 0.0f : -1.0f;
+            base[e * 3 + c] = make_float2(-1.0f, 0.0f);
             if (!(m2 > 0.0)) continue;
+            double sur = -1.0, sui = 0.0;   // sum of the stored u, minus 1
             const double ir = h0[c].re / m2, ii = -h0[c].im / m2;   // 1/h0
             // per group of modes with the same m (same phase and g), the u summed into the
             // record of its first mode, which the kernel reads for the whole group
@@ -1146,10 +1150,13 @@ __global__ void edge_mixed_hm_kernel(const double* __restrict__ theta0, double t
                 }
                 MixModeHM& mm = hm[(int64_t)e * kHmModes + b0];
                 mm.u[c] = make_float2((float)usr, (float)usi);
+                sur += (double)mm.u[c].x;
+                sui += (double)mm.u[c].y;
                 // K e'/h0, e' = f2^{-7/6} e^{-i Phi0_lm}
                 const double er = Kr[c] * gr[b0] - Ki[c] * gi[b0], ei = Kr[c] * gi[b0] + Ki[c] * gr[b0];
                 mm.g[c] = make_float2((float)(er * ir - ei * ii), (float)(er * ii + ei * ir));
             }
+            base[e * 3 + c] = make_float2((float)sur, (float)sui);
         }
     }
 }
@@ -1190,7 +1197,7 @@ cudaError_t mbh::prepare_mixed_tables(mbh_ref* R, cudaStream_t st)
                                              R->mix_edge, R->mix_sums + 2);
     } else {
         cudaError_t e = cudaMalloc(&R->mix_hm, sizeof(MixModeHM) * kHmModes * (E + 1));
-        if (e == cudaSuccess) e = cudaMalloc(&R->mix_hm_base, sizeof(float) * 3 * (E + 1));
+        if (e == cudaSuccess) e = cudaMalloc(&R->mix_hm_base, sizeof(float2) * 3 * (E + 1));
         if (e != cudaSuccess) return e;
         edge_mixed_hm_kernel<<<1, 128, 0, st>>>(R->theta0_dev, R->grid.t_obs, R->modes, R->fe, E + 1,
                                                 R->mix_edge, R->mix_hm, R->mix_hm_base, R->mix_sums + 2);
@@ -1356,9 +1363,10 @@ __global__ void __launch_bounds__(BLOCK, 896 / BLOCK) het_mixed_kernel_capped(co
 
 // Higher-mode heterodyne (Sec. II B with the template of Eq. 9 summed over modes before the
 // ratio), mixed precision; layout and reductions as het_mixed_kernel, delta from the
-// per-mode reference tables (edge_mixed_hm_kernel).
+// per-mode reference tables (edge_mixed_hm_kernel).  The register cap (640 threads per SM,
+// 102 registers) fits five 128-thread blocks per SM against four uncapped, without spills.
 template <int G, int BLOCK>
-__global__ void __launch_bounds__(BLOCK)
+__global__ void __launch_bounds__(BLOCK, 640 / BLOCK)
     het_mixed_hm_kernel(const __grid_constant__ HetLaunch L)
 {
     constexpr int WPB = BLOCK / G;
@@ -1394,7 +1402,10 @@ __global__ void __launch_bounds__(BLOCK)
                 const MixEdge me = S.mix.edge[e];
                 const FreqDF q = {ld_f2(me.f), ld_f2(me.f3), ld_f2(me.fm3), ld_f2(me.lnf3)};
 #pragma unroll
-                for (int c = 0; c < 3; ++c) dl[c].re = S.mix.hm_base[e * 3 + c];
+                for (int c = 0; c < 3; ++c) {
+                    const float2 b = S.mix.hm_base[e * 3 + c];
+                    dl[c] = {b.x, b.y};
+                }
                 // Modes with the same m share f2 = 2f/m, so the phase chain, t(f2), the orbit, the
                 // reference's phase and g: one chain and one transfer per distinct m, with the
                 // modes' factors summed weighted by v^{p_lm} (the transfer is linear in them) and
