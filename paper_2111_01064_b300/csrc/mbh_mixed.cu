@@ -473,21 +473,57 @@ __device__ __forceinline__ bool phase_df(const WalkerDF& w, const WalkerF& wf, c
     const f2 v = dd_mul_lazy(w.cbrt_piM, q.f3);
     const f2 iv = dd_mul_lazy(w.icbrt_piM, q.fm3);
     const f2 lnv = dd_add_lazy(w.ln_cbrt_piM, q.lnf3);
-    f2 P = w.c[7], Q = w.d[7];
+    f2 P = w.c[7];
 #pragma unroll
-    for (int k = 6; k >= 0; --k) {
-        P = dd_fma_lazy(P, v, w.c[k]);
-        Q = dd_fma_lazy(Q, v, w.d[k]);
-    }
+    for (int k = 6; k >= 0; --k) P = dd_fma_lazy(P, v, w.c[k]);
     const f2 iv2 = dd_mul_lazy(iv, iv), iv4 = dd_mul_lazy(iv2, iv2);
-    const f2 iv5 = dd_mul_lazy(iv4, iv), iv8 = dd_mul_lazy(iv4, iv4);
+    const f2 iv5 = dd_mul_lazy(iv4, iv);
     const f2 psi_pn = dd_add_lazy(dd_mul_lazy(P, iv5), dd_mul_lazy(lnv, dd_fma_lazy(w.cl6, v, w.cl5)));
     // t(f) = Psi'(f)/(2 pi) + t0 (the walker's d and dl6 carry the 1/(2 pi))
-    const f2 t = dd_add(dd_add_lazy(dd_mul_lazy(Q, iv8), dd_mul_lazy(dd_mul_lazy(lnv, w.dl6), iv2)), w.t0);
-    const bool in = dd_le(q.f, w.fcut) && !dd_lt0(t) && dd_le(t, t_obs);
-    if (!kAlways && !in) return false;
-    // orbit angle alpha(t) = alpha(t_ref) + da, da from t - t_ref in float32
-    const float dt = __fadd_rn(__fsub_rn(t.hi, w.tref.hi), __fsub_rn(t.lo, w.tref.lo));
+    float dt;   // t - t_ref
+    bool in;
+    if (kAlways) {
+        const f2 iv8 = dd_mul_lazy(iv4, iv4);
+        f2 Q = w.d[7];
+#pragma unroll
+        for (int k = 6; k >= 0; --k) Q = dd_fma_lazy(Q, v, w.d[k]);
+        const f2 t = dd_add(dd_add_lazy(dd_mul_lazy(Q, iv8), dd_mul_lazy(dd_mul_lazy(lnv, w.dl6), iv2)), w.t0);
+        in = dd_le(q.f, w.fcut) && !dd_lt0(t) && dd_le(t, t_obs);
+        dt = __fadd_rn(__fsub_rn(t.hi, w.tref.hi), __fsub_rn(t.lo, w.tref.lo));
+    } else {
+        // t - t_ref in float32: it only turns the orbit (an error of 1e-6 |t - t_ref| moves
+        // the SSB delay phase by < 1e-7 rad at every frequency of the band), and the support
+        // test t in [0, t_obs] takes the double-float t only where the float32 value's error
+        // bound straddles a bound (rounding of the Horner sum, the float32 powers of v and ln v:
+        // < 3e-6 of the sum of |terms|; bound 1e-5)
+        const float vf = v.hi, i8 = iv4.hi * iv4.hi, i2 = iv2.hi;
+        float Qf = w.d[7].hi, Qa = fabsf(w.d[7].hi);
+#pragma unroll
+        for (int k = 6; k >= 0; --k) {
+            Qf = fmaf(Qf, vf, w.d[k].hi);
+            Qa = fmaf(Qa, vf, fabsf(w.d[k].hi));
+        }
+        const float t2 = lnv.hi * w.dl6.hi * i2;
+        const float dtc = __fadd_rn(__fsub_rn(w.t0.hi, w.tref.hi), __fsub_rn(w.t0.lo, w.tref.lo));
+        dt = fmaf(Qf, i8, t2) + dtc;
+        const float lo = (dt + w.tref.hi) + w.tref.lo;                          // t
+        const float hi = (dt + (w.tref.hi - t_obs.hi)) + (w.tref.lo - t_obs.lo);   // t - t_obs
+        const float err = 1e-5f * fmaf(Qa, i8, fabsf(t2)) + 3e-7f * (fabsf(dtc) + fabsf(lo) + fabsf(hi)) + 1e-6f;
+        in = dd_le(q.f, w.fcut);
+        if (lo >= err && hi <= -err) {
+            // inside
+        } else if (lo < -err || hi > err) {
+            in = false;
+        } else {   // within the bound of t = 0 or t = t_obs: the double-float t decides
+            const f2 iv8 = dd_mul_lazy(iv4, iv4);
+            f2 Q = w.d[7];
+#pragma unroll
+            for (int k = 6; k >= 0; --k) Q = dd_fma_lazy(Q, v, w.d[k]);
+            const f2 t = dd_add(dd_add_lazy(dd_mul_lazy(Q, iv8), dd_mul_lazy(dd_mul_lazy(lnv, w.dl6), iv2)), w.t0);
+            in = in && !dd_lt0(t) && dd_le(t, t_obs);
+        }
+        if (!in) return false;
+    }
     const float da = dt * (float)(kTwoPi / kYear);
     float sh, ch;
     sincos_small(0.5f * da, &sh, &ch);
