@@ -64,6 +64,7 @@ struct SrcDesc {
     const double* invw;      // [E]
     MixTables mix;
     double dd, t_obs;
+    float tob_hi, tob_lo;    // t_obs as a float pair (split on the host: no float64 work per edge)
     int64_t w_begin, w_end;  // walker range in theta/out
     int32_t E;
     int32_t tile_begin;      // first tile of this source

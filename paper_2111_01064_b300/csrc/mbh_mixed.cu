@@ -840,8 +840,12 @@ __global__ void __launch_bounds__(kDirThreadsM, 2)
         acc[t][threadIdx.x] = make_double2(0.0, 0.0);
         facc[t][threadIdx.x] = make_float2(0.0f, 0.0f);
     }
-    const f2 tob = split_d(t_obs);
+    // t_obs split once into shared memory: a register copy that the compiler rematerialises
+    // from the float64 parameter inside the point loop costs float64-pipe work at every point
+    __shared__ f2 s_tob;
+    if (threadIdx.x == 0) s_tob = split_d(t_obs);
     __syncthreads();
+    const f2 tob = s_tob;
     const int64_t kb = (int64_t)ch * chunk, ke = std::min<int64_t>(n, kb + chunk);
     int since = 0;
     for (int64_t k = kb + threadIdx.x; k < ke; k += kDirThreadsM) {
@@ -1314,7 +1318,7 @@ __device__ __forceinline__ void het_mixed_body(const HetLaunch& L)
             if (w0 + j < S.w_end) walker_setup_mixed(L.theta, L.W, w0 + j, wsd[j], wsf[j]);
         __syncthreads();
         const int E = S.E;
-        const f2 tob = split_d(S.t_obs);
+        const f2 tob = {S.tob_hi, S.tob_lo};
         f2 adh = {0.0f, 0.0f}, ahh = {0.0f, 0.0f};
         cf carry[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
         const int rounds = (E + 1 + G - 1) / G;
@@ -1427,7 +1431,7 @@ __global__ void __launch_bounds__(BLOCK, 640 / BLOCK)
         __syncthreads();
         const int E = S.E;
         const uint32_t modes = S.modes;
-        const f2 tob = split_d(S.t_obs);
+        const f2 tob = {S.tob_hi, S.tob_lo};
         f2 adh = {0.0f, 0.0f}, ahh = {0.0f, 0.0f};
         cf carry[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
         const int rounds = (E + 1 + G - 1) / G;
@@ -1563,7 +1567,7 @@ __device__ __forceinline__ void het_mixed_pt_body(const HetLaunch& L)
             }
         __syncthreads();
         const int E = S.E;
-        const f2 tob = split_d(S.t_obs);
+        const f2 tob = {S.tob_hi, S.tob_lo};
         f2 adh = {0.0f, 0.0f}, ahh = {0.0f, 0.0f};
         cf carry[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
         const int rounds = (E + 1 + G - 1) / G;

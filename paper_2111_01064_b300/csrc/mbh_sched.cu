@@ -140,6 +140,8 @@ mbh_status make_plan(const mbh_ref* const* refs, const int64_t* offsets, int32_t
                 S.mix = R->mix;
                 S.dd = R->dd;
                 S.t_obs = R->grid.t_obs;
+                S.tob_hi = (float)S.t_obs;
+                S.tob_lo = (float)(S.t_obs - (double)S.tob_hi);
                 S.E = R->E;
                 S.modes = R->modes;
                 S.w_begin = offsets[s];
@@ -374,6 +376,8 @@ mbh_status het_launch_fused_pt(const mbh_ref* const* refs, int n_ens, int64_t M,
             S.mix = R->mix;
             S.dd = R->dd;
             S.t_obs = R->grid.t_obs;
+            S.tob_hi = (float)S.t_obs;
+            S.tob_lo = (float)(S.t_obs - (double)S.tob_hi);
             S.E = R->E;
             S.modes = R->modes;
             S.w_begin = (int64_t)(first + q) * M;
