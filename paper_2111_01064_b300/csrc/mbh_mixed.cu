@@ -388,17 +388,18 @@ __device__ inline void walker_setup_mixed(const double* __restrict__ theta, int6
     // the t_ref and f_max pinning folded into per-walker constants:
     //   t(f) = t_ref + (Psi'(f) - Psi'(f_max))/(2 pi) = Psi'(f)/(2 pi) + t0,
     //   Phi(f) = 2 pi f (t_ref + k.c(t)) + Psi_PN(f) - Psi_PN(f_max) - (f - f_max) Psi'(f_max)
-    //          = f (c1 + 2 pi (AU/c) k.c(t)) + Psi_PN(f) + c0
+    //          = f (c1 + 2 pi (AU/c) k.(c(t) - c(t_ref))) + Psi_PN(f) + c0
     const double fmax = (0.05 * 0.6454972243679028) * iM;   // f_c sqrt(5/12)
     m.tref = split_f64(tref, 0);
     m.fcut = split_d(0.2 * iM);   // rounded to nearest: compared lexicographically (dd_le)
     m.t0 = split_f64(tref - dpsi_max * kInvTwoPi, 0);
     m.c0 = split_f64(fmax * dpsi_max - psi_max, 0);
-    m.c1 = split_f64(kTwoPi * tref - dpsi_max, 0);
+    const double kxd = kTwoPi * kAUSec * (-cbt * cl), kyd = kTwoPi * kAUSec * (-cbt * sl);
+    m.c1 = split_f64(kTwoPi * tref - dpsi_max + (kxd * ca + kyd * sa), 0);   // with k.c(t_ref)
     m.sa_ref = split_f64(sa, 0);
     m.ca_ref = split_f64(ca, 0);
-    m.kx = split_f64(kTwoPi * kAUSec * (-cbt * cl), 0);
-    m.ky = split_f64(kTwoPi * kAUSec * (-cbt * sl), 0);
+    m.kx = split_f64(kxd, 0);
+    m.ky = split_f64(kyd, 0);
 
     // Float32 constants (amplitude, taper, wave frame, mode factors), computed in float64 and
     // rounded once: the heterodyne ratio h/h0 of a nearby walker cancels their common part,
@@ -528,13 +529,20 @@ __device__ __forceinline__ bool phase_df(const WalkerDF& w, const WalkerF& wf, c
     float sh, ch;
     sincos_small(0.5f * da, &sh, &ch);
     const float sd = 2.0f * sh * ch, omc = 2.0f * sh * sh;   // sin da, 1 - cos da
-    const f2 sa_d = dd_add_f(w.sa_ref, wf.ca_ref * sd - wf.sa_ref * omc);
-    const f2 ca_d = dd_add_f(w.ca_ref, -(wf.ca_ref * omc + wf.sa_ref * sd));
-    // Phi = f (c1 + 2 pi (AU/c) k.c(t)) + Psi_PN(f) + c0 (kx, ky carry 2 pi AU/c)
-    const f2 S = dd_fma_lazy(w.ky, sa_d, dd_fma_lazy(w.kx, ca_d, w.c1));
+    const float ds = wf.ca_ref * sd - wf.sa_ref * omc;      // sin alpha - sin alpha(t_ref)
+    const float dc = -(wf.ca_ref * omc + wf.sa_ref * sd);   // cos alpha - cos alpha(t_ref)
+    // Phi = f (c1 + 2 pi (AU/c) k.c(t)) + Psi_PN(f) + c0 (kx, ky carry 2 pi AU/c); the walker's
+    // c1 holds k.c(t_ref), so only the orbit's change since t_ref is added here, in float32
+    // (its rounding, <= 1.2e-7 of f |k| |c(t) - c(t_ref)|, is below 1e-7 rad at every edge)
+    const float dk = fmaf(w.kx.hi, dc, fmaf(w.ky.hi, ds, fmaf(w.kx.lo, dc, w.ky.lo * ds)));
+    const f2 s1 = two_sum(w.c1.hi, dk);
+    const f2 S = {s1.hi, __fadd_rn(s1.lo, w.c1.lo)};   // unnormalised operand of dd_mul_lazy
     Phi = dd_add(dd_mul_lazy(q.f, S), dd_add_lazy(psi_pn, w.c0));
-    sa = dd_to_float(sa_d);
-    ca = dd_to_float(ca_d);
+    // sin, cos of the orbit angle rounded once from their exact sums (a double rounding here
+    // biases the response of a walker at every edge alike: p99 |dlnL| 6e-4 -> 1.2e-3)
+    const f2 ts = two_sum(w.sa_ref.hi, ds), tc = two_sum(w.ca_ref.hi, dc);
+    sa = __fadd_rn(ts.hi, __fadd_rn(ts.lo, w.sa_ref.lo));
+    ca = __fadd_rn(tc.hi, __fadd_rn(tc.lo, w.ca_ref.lo));
     const float ff = q.f.hi;
     if (kTab) {   // f^{-7/6} is folded into the edge table's 1/h0
         amp = wf.amp76 * expf(-ff * ff * wf.inv_fc2);
