@@ -476,7 +476,8 @@ __device__ __forceinline__ bool phase_df(const WalkerDF& w, const WalkerF& wf, c
     const f2 lnv = dd_add_lazy(w.ln_cbrt_piM, q.lnf3);
     f2 P = w.c[7];
 #pragma unroll
-    for (int k = 6; k >= 0; --k) P = dd_fma_lazy(P, v, w.c[k]);
+    for (int k = 6; k >= 0; --k)   // c_1 = 0 (no 0.5PN term): that step is a product
+        P = k == 1 ? dd_mul_lazy(P, v) : dd_fma_lazy(P, v, w.c[k]);
     const f2 iv2 = dd_mul_lazy(iv, iv), iv4 = dd_mul_lazy(iv2, iv2);
     const f2 iv5 = dd_mul_lazy(iv4, iv);
     const f2 psi_pn = dd_add_lazy(dd_mul_lazy(P, iv5), dd_mul_lazy(lnv, dd_fma_lazy(w.cl6, v, w.cl5)));
