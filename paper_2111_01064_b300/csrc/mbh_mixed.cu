@@ -1297,6 +1297,52 @@ __device__ __forceinline__ double amp_fix(float eps_walker, double eps_ref)
     return (1.0 + (double)eps_walker) / (1.0 + eps_ref);
 }
 
+// delta = h/h0 - 1 of one walker at one edge record (the (2,2) mixed ratio of Sec. II B):
+// rho = amp T h0inv (raw transfer, all frequency-only factors in h0inv), delta = (rho - 1) +
+// rho (e^{-i dPhi} - 1) with dPhi in double-float; -1 outside the walker's support (h = 0)
+__device__ __forceinline__ void edge_delta_mixed(const WalkerDF& wd, const WalkerF& wf, const MixEdge& me, f2 tob,
+                                                 cf dl[3])
+{
+    const FreqDF q = {ld_f2(me.f), ld_f2(me.f3), ld_f2(me.fm3), ld_f2(me.lnf3)};
+    f2 Phi;
+    float sa, ca, amp;
+    if (phase_df<false, true>(wd, wf, q, tob, Phi, sa, ca, amp)) {
+        float sh, ch;
+        sincos_small(0.5f * reduce_phase(dd_add_lazy(Phi, {-me.phi0.x, -me.phi0.y})), &sh, &ch);
+        const cf em1 = {-2.0f * sh * sh, -2.0f * sh * ch};   // e^{-i dPhi} - 1
+        cf T[3];
+        transfer_f32<true>(wf, wf.Ga, wf.Gb, me.xs.w, sa, ca, 1.0f, me.xs.x, me.xs.y, T, wf.Glo);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const cf rho = fmul(fscale(T[c], amp), {me.h0inv[c].x, me.h0inv[c].y});
+            dl[c] = fadd({rho.re - 1.0f, rho.im}, fmul(rho, em1));
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) dl[c] = {-1.0f, 0.0f};   // h = 0: r = 0
+    }
+}
+
+// A walker's <d|h>, <h|h> partial sums (float pairs) with the tail edge E, when the edge loop
+// left it out: evaluated here, its bin E - 1 contracted against the carried delta at E - 1 and
+// added last (the same order for every block size and launch mode)
+__device__ __forceinline__ float4 tail_sums(const SrcDesc& S, const WalkerDF& wd, const WalkerF& wf, f2 tob,
+                                            const cf dprev[3], bool tail, float4 v)
+{
+    if (!tail) return v;
+    const int E = S.E;
+    cf dl[3], dp[3];
+    edge_delta_mixed(wd, wf, S.mix.edge[E], tob, dl);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) dp[c] = dprev[c];
+    float bd, bh;
+    contract_bin(S.mix.bin[E - 1], dp, dl, bd, bh);
+    f2 adh = {v.x, v.y}, ahh = {v.z, v.w};
+    df_acc(adh, {bd, 0.0f});
+    df_acc(ahh, {bh, 0.0f});
+    return make_float4(adh.hi, adh.lo, ahh.hi, ahh.lo);
+}
+
 // ------------------------------------------------------------------------------------------
 // heterodyne likelihood, mixed precision
 // ------------------------------------------------------------------------------------------
@@ -1312,6 +1358,7 @@ __device__ __forceinline__ void het_mixed_body(const HetLaunch& L)
     __shared__ WalkerDF wsd[WPB];
     __shared__ WalkerF wsf[WPB];
     __shared__ float4 sums[WPB];   // per walker <d|h>, <h|h> partial sums (float pairs)
+    __shared__ cf tailc[WPB][3];   // per walker delta at edge E - 1, for the tail edge
     const int lw = threadIdx.x / G, lane = threadIdx.x % G;
     for (int tile = blockIdx.x; tile < L.n_tiles; tile += gridDim.x) {
         int s = 0;
@@ -1330,33 +1377,14 @@ __device__ __forceinline__ void het_mixed_body(const HetLaunch& L)
         const f2 tob = {S.tob_hi, S.tob_lo};
         f2 adh = {0.0f, 0.0f}, ahh = {0.0f, 0.0f};
         cf carry[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-        const int rounds = (E + 1 + G - 1) / G;
+        // (E + 1) % G == 1 leaves one edge per walker for a last round with one active lane per
+        // walker: that edge goes to the block-wide tail in the epilogue (consecutive threads)
+        const bool tail = G > 1 && E >= 1 && (E + 1) % G == 1;
+        const int rounds = tail ? E / G : (E + 1 + G - 1) / G;
         for (int r = 0; r < rounds; ++r) {
             const int e = r * G + lane;
             cf dl[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-            if (active && e <= E) {
-                const MixEdge me = S.mix.edge[e];
-                const FreqDF q = {ld_f2(me.f), ld_f2(me.f3), ld_f2(me.fm3), ld_f2(me.lnf3)};
-                f2 Phi;
-                float sa, ca, amp;
-                if (phase_df<false, true>(wsd[lw], wsf[lw], q, tob, Phi, sa, ca, amp)) {
-                    float sh, ch;
-                    sincos_small(0.5f * reduce_phase(dd_add_lazy(Phi, {-me.phi0.x, -me.phi0.y})), &sh, &ch);
-                    const cf em1 = {-2.0f * sh * sh, -2.0f * sh * ch};   // e^{-i dPhi} - 1
-                    cf T[3];
-                    transfer_f32<true>(wsf[lw], wsf[lw].Ga, wsf[lw].Gb, me.xs.w, sa, ca, 1.0f, me.xs.x, me.xs.y, T,
-                                       wsf[lw].Glo);
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        const cf rho = fmul(fscale(T[c], amp), {me.h0inv[c].x, me.h0inv[c].y});
-                        // delta = rho e^{-i dPhi} - 1 = (rho - 1) + rho (e^{-i dPhi} - 1)
-                        dl[c] = fadd({rho.re - 1.0f, rho.im}, fmul(rho, em1));
-                    }
-                } else {
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) dl[c] = {-1.0f, 0.0f};   // h = 0: r = 0
-                }
-            }
+            if (active && e <= E) edge_delta_mixed(wsd[lw], wsf[lw], S.mix.edge[e], tob, dl);
             cf dp[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -1382,11 +1410,15 @@ __device__ __forceinline__ void het_mixed_body(const HetLaunch& L)
         }
         // float64 epilogue on consecutive threads (as the setup: a float64 warp instruction costs
         // the same for 32/G or 32 walkers)
-        if (lane == 0) sums[lw] = make_float4(adh.hi, adh.lo, ahh.hi, ahh.lo);
+        if (lane == 0) {
+            sums[lw] = make_float4(adh.hi, adh.lo, ahh.hi, ahh.lo);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) tailc[lw][c] = carry[c];   // delta at edge E - 1 (tail)
+        }
         __syncthreads();
         for (int j = threadIdx.x; j < WPB; j += BLOCK)
             if (w0 + j < S.w_end) {
-                const float4 v = sums[j];
+                const float4 v = tail_sums(S, wsd[j], wsf[j], tob, tailc[j], tail, sums[j]);
                 const double fix = amp_fix(wsf[j].eps_amp76, S.mix.amp_eps0);
                 const double dh = 4.0 * (S.mix.sumA0 + df_to_double({v.x, v.y})) * fix;
                 const double hh = 4.0 * (S.mix.sumB0 + df_to_double({v.z, v.w})) * (fix * fix);
@@ -1552,6 +1584,7 @@ __device__ __forceinline__ void het_mixed_pt_body(const HetLaunch& L)
     __shared__ double facs[WPB];
     __shared__ int32_t flags[WPB];
     __shared__ float4 sums[WPB];   // per walker <d|h>, <h|h> partial sums (float pairs)
+    __shared__ cf tailc[WPB][3];   // per walker delta at edge E - 1, for the tail edge
     const pt::PtArgs& A = *static_cast<const pt::PtArgs*>(L.pt);
     const int half = L.pt_half;
     const int lw = threadIdx.x / G, lane = threadIdx.x % G;
@@ -1579,33 +1612,14 @@ __device__ __forceinline__ void het_mixed_pt_body(const HetLaunch& L)
         const f2 tob = {S.tob_hi, S.tob_lo};
         f2 adh = {0.0f, 0.0f}, ahh = {0.0f, 0.0f};
         cf carry[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-        const int rounds = (E + 1 + G - 1) / G;
+        // (E + 1) % G == 1 leaves one edge per walker for a last round with one active lane per
+        // walker: that edge goes to the block-wide tail in the epilogue (consecutive threads)
+        const bool tail = G > 1 && E >= 1 && (E + 1) % G == 1;
+        const int rounds = tail ? E / G : (E + 1 + G - 1) / G;
         for (int r = 0; r < rounds; ++r) {
             const int e = r * G + lane;
             cf dl[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-            if (active && e <= E) {
-                const MixEdge me = S.mix.edge[e];
-                const FreqDF q = {ld_f2(me.f), ld_f2(me.f3), ld_f2(me.fm3), ld_f2(me.lnf3)};
-                f2 Phi;
-                float sa, ca, amp;
-                if (phase_df<false, true>(wsd[lw], wsf[lw], q, tob, Phi, sa, ca, amp)) {
-                    float sh, ch;
-                    sincos_small(0.5f * reduce_phase(dd_add_lazy(Phi, {-me.phi0.x, -me.phi0.y})), &sh, &ch);
-                    const cf em1 = {-2.0f * sh * sh, -2.0f * sh * ch};
-                    cf T[3];
-                    transfer_f32<true>(wsf[lw], wsf[lw].Ga, wsf[lw].Gb, me.xs.w, sa, ca, 1.0f, me.xs.x, me.xs.y, T,
-                                       wsf[lw].Glo);
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        const cf rho = fmul(fscale(T[c], amp), {me.h0inv[c].x, me.h0inv[c].y});
-                        // delta = rho e^{-i dPhi} - 1 = (rho - 1) + rho (e^{-i dPhi} - 1)
-                        dl[c] = fadd({rho.re - 1.0f, rho.im}, fmul(rho, em1));
-                    }
-                } else {
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) dl[c] = {-1.0f, 0.0f};
-                }
-            }
+            if (active && e <= E) edge_delta_mixed(wsd[lw], wsf[lw], S.mix.edge[e], tob, dl);
             cf dp[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -1630,11 +1644,15 @@ __device__ __forceinline__ void het_mixed_pt_body(const HetLaunch& L)
             df_acc(ahh, ohh);
         }
         // float64 epilogue and acceptance on consecutive threads (full warps)
-        if (lane == 0) sums[lw] = make_float4(adh.hi, adh.lo, ahh.hi, ahh.lo);
+        if (lane == 0) {
+            sums[lw] = make_float4(adh.hi, adh.lo, ahh.hi, ahh.lo);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) tailc[lw][c] = carry[c];   // delta at edge E - 1 (tail)
+        }
         __syncthreads();
         for (int j = threadIdx.x; j < WPB; j += BLOCK)
             if (w0 + j < S.w_end) {
-                const float4 v = sums[j];
+                const float4 v = tail_sums(S, wsd[j], wsf[j], tob, tailc[j], tail, sums[j]);
                 const double fix = amp_fix(wsf[j].eps_amp76, S.mix.amp_eps0);
                 const double dh = 4.0 * (S.mix.sumA0 + df_to_double({v.x, v.y})) * fix;
                 const double hh = 4.0 * (S.mix.sumB0 + df_to_double({v.z, v.w})) * (fix * fix);
