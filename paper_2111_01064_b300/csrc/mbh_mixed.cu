@@ -474,18 +474,18 @@ __device__ __forceinline__ bool phase_df(const WalkerDF& w, const WalkerF& wf, c
     const f2 v = dd_mul_lazy(w.cbrt_piM, q.f3);
     const f2 iv = dd_mul_lazy(w.icbrt_piM, q.fm3);
     const f2 lnv = dd_add_lazy(w.ln_cbrt_piM, q.lnf3);
-    f2 P = w.c[7];
+    // Psi_PN = sum_k c_k v^{k-5} + ln v (cl5 + cl6 v): the powers v^-5..v^0 by Horner in 1/v
+    // (c_1 = 0, no 0.5PN term: the first step is the product c_0 / v), v and v^2 by Horner in v
+    f2 N = dd_mul_lazy(w.c[0], iv);
 #pragma unroll
-    for (int k = 6; k >= 0; --k)   // c_1 = 0 (no 0.5PN term): that step is a product
-        P = k == 1 ? dd_mul_lazy(P, v) : dd_fma_lazy(P, v, w.c[k]);
-    const f2 iv2 = dd_mul_lazy(iv, iv), iv4 = dd_mul_lazy(iv2, iv2);
-    const f2 iv5 = dd_mul_lazy(iv4, iv);
-    const f2 psi_pn = dd_add_lazy(dd_mul_lazy(P, iv5), dd_mul_lazy(lnv, dd_fma_lazy(w.cl6, v, w.cl5)));
+    for (int k = 2; k <= 5; ++k) N = dd_fma_lazy(N, iv, w.c[k]);
+    const f2 Pp = dd_mul_lazy(dd_fma_lazy(w.c[7], v, w.c[6]), v);
+    const f2 psi_pn = dd_add_lazy(dd_add_lazy(N, Pp), dd_mul_lazy(lnv, dd_fma_lazy(w.cl6, v, w.cl5)));
     // t(f) = Psi'(f)/(2 pi) + t0 (the walker's d and dl6 carry the 1/(2 pi))
     float dt;   // t - t_ref
     bool in;
     if (kAlways) {
-        const f2 iv8 = dd_mul_lazy(iv4, iv4);
+        const f2 iv2 = dd_mul_lazy(iv, iv), iv4 = dd_mul_lazy(iv2, iv2), iv8 = dd_mul_lazy(iv4, iv4);
         f2 Q = w.d[7];
 #pragma unroll
         for (int k = 6; k >= 0; --k) Q = dd_fma_lazy(Q, v, w.d[k]);
@@ -498,7 +498,7 @@ __device__ __forceinline__ bool phase_df(const WalkerDF& w, const WalkerF& wf, c
         // test t in [0, t_obs] takes the double-float t only where the float32 value's error
         // bound straddles a bound (rounding of the Horner sum, the float32 powers of v and ln v:
         // < 3e-6 of the sum of |terms|; bound 1e-5)
-        const float vf = v.hi, i8 = iv4.hi * iv4.hi, i2 = iv2.hi;
+        const float vf = v.hi, i2 = iv.hi * iv.hi, i4 = i2 * i2, i8 = i4 * i4;
         float Qf = w.d[7].hi, Qa = fabsf(w.d[7].hi);
 #pragma unroll
         for (int k = 6; k >= 0; --k) {
@@ -517,7 +517,7 @@ __device__ __forceinline__ bool phase_df(const WalkerDF& w, const WalkerF& wf, c
         } else if (lo < -err || hi > err) {
             in = false;
         } else {   // within the bound of t = 0 or t = t_obs: the double-float t decides
-            const f2 iv8 = dd_mul_lazy(iv4, iv4);
+            const f2 iv2 = dd_mul_lazy(iv, iv), iv4 = dd_mul_lazy(iv2, iv2), iv8 = dd_mul_lazy(iv4, iv4);
             f2 Q = w.d[7];
 #pragma unroll
             for (int k = 6; k >= 0; --k) Q = dd_fma_lazy(Q, v, w.d[k]);
