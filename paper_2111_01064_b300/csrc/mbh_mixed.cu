@@ -285,7 +285,7 @@ constexpr f2 kTwoPiDF = df_const(kTwoPi);
 struct WalkerDF {
     f2 c[8], d[8], cl5, cl6, dl6;
     f2 cbrt_piM, icbrt_piM, ln_cbrt_piM;
-    f2 tref, fcut, t0, c0, c1;
+    f2 tref, fcut, t0, c1;
     f2 sa_ref, ca_ref, kx, ky;
 };
 
@@ -374,9 +374,12 @@ __device__ inline void walker_setup_mixed(const double* __restrict__ theta, int6
     sincos(kTwoPi * tref / kYear, &sa, &ca);
     sincos(lam, &sl, &cl);
     sincos(bet, &sb, &cbt);
+    // Phi(f) = f (c1 + ...) + Psi_PN(f) + c0 (the pinning below): c0 joins the constant term c_5
+    const double fmax = (0.05 * 0.6454972243679028) * iM;   // f_c sqrt(5/12)
+    const double c0 = fmax * dpsi_max - psi_max;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        m.c[k] = split_f64(c[k], 0);
+        m.c[k] = split_f64(k == 5 ? c[5] + c0 : c[k], 0);
         m.d[k] = split_f64(d[k] * kInvTwoPi, 0);   // the derivative chain gives t(f) in seconds
     }
     m.cl5 = split_f64(cl5, 0);
@@ -389,11 +392,9 @@ __device__ inline void walker_setup_mixed(const double* __restrict__ theta, int6
     //   t(f) = t_ref + (Psi'(f) - Psi'(f_max))/(2 pi) = Psi'(f)/(2 pi) + t0,
     //   Phi(f) = 2 pi f (t_ref + k.c(t)) + Psi_PN(f) - Psi_PN(f_max) - (f - f_max) Psi'(f_max)
     //          = f (c1 + 2 pi (AU/c) k.(c(t) - c(t_ref))) + Psi_PN(f) + c0
-    const double fmax = (0.05 * 0.6454972243679028) * iM;   // f_c sqrt(5/12)
     m.tref = split_f64(tref, 0);
     m.fcut = split_d(0.2 * iM);   // rounded to nearest: compared lexicographically (dd_le)
     m.t0 = split_f64(tref - dpsi_max * kInvTwoPi, 0);
-    m.c0 = split_f64(fmax * dpsi_max - psi_max, 0);
     const double kxd = kTwoPi * kAUSec * (-cbt * cl), kyd = kTwoPi * kAUSec * (-cbt * sl);
     m.c1 = split_f64(kTwoPi * tref - dpsi_max + (kxd * ca + kyd * sa), 0);   // with k.c(t_ref)
     m.sa_ref = split_f64(sa, 0);
@@ -538,7 +539,7 @@ __device__ __forceinline__ bool phase_df(const WalkerDF& w, const WalkerF& wf, c
     const float dk = fmaf(w.kx.hi, dc, fmaf(w.ky.hi, ds, fmaf(w.kx.lo, dc, w.ky.lo * ds)));
     const f2 s1 = two_sum(w.c1.hi, dk);
     const f2 S = {s1.hi, __fadd_rn(s1.lo, w.c1.lo)};   // unnormalised operand of dd_mul_lazy
-    Phi = dd_add(dd_mul_lazy(q.f, S), dd_add_lazy(psi_pn, w.c0));
+    Phi = dd_add(dd_mul_lazy(q.f, S), psi_pn);   // c0 is in the walker's c_5
     // sin, cos of the orbit angle rounded once from their exact sums (a double rounding here
     // biases the response of a walker at every edge alike: p99 |dlnL| 6e-4 -> 1.2e-3)
     const f2 ts = two_sum(w.sa_ref.hi, ds), tc = two_sum(w.ca_ref.hi, dc);
