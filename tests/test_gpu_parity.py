@@ -88,6 +88,46 @@ def test_template(month, M, WL, oracle, prec, tol):
     np.testing.assert_array_equal(h_g[:, 0] == 0, h_o[:, 0] == 0)
 
 
+def _crossing(oracle, th, t_obs, target, a, b):
+    """f in [a, b] with t(f) = target (the oracle's time-frequency map), by bisection."""
+    ta = oracle.w0(th, np.array([a]), t_obs)[2][0] - target
+    for _ in range(200):
+        m = 0.5 * (a + b)
+        tm = oracle.w0(th, np.array([m]), t_obs)[2][0] - target
+        if (tm < 0) == (ta < 0):
+            a, ta = m, tm
+        else:
+            b = m
+    return 0.5 * (a + b)
+
+
+@pytest.mark.parametrize("bound", ["t=0", "t=t_obs"])
+def test_mixed_support_at_time_bounds(month, M, WL, oracle, bound):
+    """The support t(f) in [0, t_obs] (Sec. II A, the time-frequency map) decided by the
+    mixed templates point by point as by the oracle, on a grid of ~0.5 s steps in t across
+    each bound: the mixed chain forms t - t_ref in float32 and falls back to the double-float
+    t where the float32 value's rounding bound straddles a bound (here on most points)."""
+    g0 = month["g"]
+    th = month["th_o"].copy()
+    info = oracle.w0_info(th)
+    if bound == "t=0":
+        fs = _crossing(oracle, th, g0["t_obs"], 0.0, 1e-7, info["fmax"])
+    else:   # t_ref just past t_obs: t(f) crosses t_obs below f_max
+        th[I.I_TREF] = g0["t_obs"] + 20.0
+        fs = _crossing(oracle, th, g0["t_obs"], g0["t_obs"], 0.5 * info["fmax"], info["fmax"])
+    h = 1e-7 * fs
+    t2 = oracle.w0(th, np.array([fs - h, fs + h]), g0["t_obs"])[2]
+    slope = abs(t2[1] - t2[0]) / (2 * h)
+    step = 0.5 / slope
+    g = dict(f0=fs - 128.5 * step, df=step, n=257, t_obs=g0["t_obs"])
+    f = oracle.freqs(g)
+    h_o = oracle.template(th, f, g["t_obs"])
+    h_m = M.template_batch(g, WL.to_dev(th.reshape(11, 1)), "mixed").cpu().numpy()[0]
+    inside = h_o[0] != 0
+    assert 50 < inside.sum() < 207   # the bound lies inside the grid
+    np.testing.assert_array_equal(h_m[0] != 0, inside)
+
+
 def test_template_ragged_and_empty(month, M, WL, oracle):
     g = I.grid_small(n=1000 + 37)
     th = month["walk_o"][:, :3]
