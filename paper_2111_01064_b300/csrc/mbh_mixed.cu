@@ -397,8 +397,8 @@ __device__ inline void walker_setup_mixed(const double* __restrict__ theta, int6
     m.t0 = split_f64(tref - dpsi_max * kInvTwoPi, 0);
     const double kxd = kTwoPi * kAUSec * (-cbt * cl), kyd = kTwoPi * kAUSec * (-cbt * sl);
     m.c1 = split_f64(kTwoPi * tref - dpsi_max + (kxd * ca + kyd * sa), 0);   // with k.c(t_ref)
-    m.sa_ref = split_f64(sa, 0);
-    m.ca_ref = split_f64(ca, 0);
+    m.sa_ref = split_d(sa);   // high parts rounded to nearest (the orbit's sin, cos per point)
+    m.ca_ref = split_d(ca);
     m.kx = split_f64(kxd, 0);
     m.ky = split_f64(kyd, 0);
 
@@ -540,11 +540,13 @@ __device__ __forceinline__ bool phase_df(const WalkerDF& w, const WalkerF& wf, c
     const f2 s1 = two_sum(w.c1.hi, dk);
     const f2 S = {s1.hi, __fadd_rn(s1.lo, w.c1.lo)};   // unnormalised operand of dd_mul_lazy
     Phi = dd_add(dd_mul_lazy(q.f, S), psi_pn);   // c0 is in the walker's c_5
-    // sin, cos of the orbit angle rounded once from their exact sums (a double rounding here
-    // biases the response of a walker at every edge alike: p99 |dlnL| 6e-4 -> 1.2e-3)
-    const f2 ts = two_sum(w.sa_ref.hi, ds), tc = two_sum(w.ca_ref.hi, dc);
-    sa = __fadd_rn(ts.hi, __fadd_rn(ts.lo, w.sa_ref.lo));
-    ca = __fadd_rn(tc.hi, __fadd_rn(tc.lo, w.ca_ref.lo));
+    // sin, cos of the orbit angle: the reference's value rounded to nearest plus (the change
+    // since t_ref plus that rounding).  Near the merger, where the edges carry the weight, the
+    // change is small and the inner sum exact to far below an ulp of the result, so the one
+    // rounding left is unbiased; a rounding of the reference's value alone would be common to
+    // those edges (with a truncated high part, p99 |dlnL| 6e-4 -> 1.2e-3)
+    sa = __fadd_rn(w.sa_ref.hi, __fadd_rn(ds, w.sa_ref.lo));
+    ca = __fadd_rn(w.ca_ref.hi, __fadd_rn(dc, w.ca_ref.lo));
     const float ff = q.f.hi;
     if (kTab) {   // f^{-7/6} is folded into the edge table's 1/h0
         amp = wf.amp76 * expf(-ff * ff * wf.inv_fc2);
