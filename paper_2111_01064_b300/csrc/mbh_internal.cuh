@@ -29,7 +29,7 @@ struct MixEdge {
 };
 // Bin record of the mixed-precision heterodyne: float32 summary data per channel with the
 // contraction's factors folded in (q0/2, q1/2, q2/w, q3/w, q4/4, q5/w; w = f_hi - f_lo).
-struct MixBin {
+struct alignas(16) MixBin {   // 80 bytes, 16-byte aligned: five 128-bit loads per bin
     float q[18];
     float pad[2];
 };

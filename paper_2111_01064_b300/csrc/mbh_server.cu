@@ -78,7 +78,7 @@ size_t ref_bytes(const mbh_ref* R)
                (E + 1) * (sizeof(int64_t) + sizeof(double) + 2 * 3 * sizeof(double2) + sizeof(MixEdge)) +
                11 * sizeof(double) + 2 * sizeof(double);
     if (R->modes != 1u)   // per-mode reference tables of a higher-mode reference
-        b += (E + 1) * (kHmModes * sizeof(MixModeHM) + 3 * sizeof(float));
+        b += (E + 1) * (kHmModes * sizeof(MixModeHM) + 3 * sizeof(float2));
     return b;
 }
 
