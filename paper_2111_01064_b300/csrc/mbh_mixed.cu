@@ -1279,13 +1279,24 @@ cudaError_t mbh::prepare_mixed_tables(mbh_ref* R, cudaStream_t st)
 __device__ __forceinline__ void contract_bin(const MixBin& mb, const cf dp[3], const cf dl[3], float& bd,
                                              float& bh)
 {
+    // the record as five 128-bit loads (18 weights and 2 pad floats)
+    float qa[20];
+    const float4* q4 = reinterpret_cast<const float4*>(&mb);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const float4 t = q4[k];
+        qa[4 * k] = t.x;
+        qa[4 * k + 1] = t.y;
+        qa[4 * k + 2] = t.z;
+        qa[4 * k + 3] = t.w;
+    }
     bd = 0.0f;
     bh = 0.0f;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const float sr = dp[c].re + dl[c].re, si = dp[c].im + dl[c].im;
         const float tr = dl[c].re - dp[c].re, ti = dl[c].im - dp[c].im;
-        const float* q = mb.q + 6 * c;
+        const float* q = qa + 6 * c;
         bd = fmaf(q[0], sr, fmaf(q[1], si, fmaf(q[2], tr, fmaf(q[3], ti, bd))));
         bh = fmaf(q[4], fmaf(si, si, sr * (4.0f + sr)), fmaf(q[5], fmaf(si, ti, tr * (2.0f + sr)), bh));
     }
