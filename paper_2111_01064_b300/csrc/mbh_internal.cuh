@@ -27,12 +27,14 @@ struct MixEdge {
     float2 h0inv[3];
     float4 xs;   // sin x, cos x (x = pi f L/c, the one-link phase), 0, x
 };
+static_assert(sizeof(MixEdge) == 80 && alignof(MixEdge) == 16, "edge records are read as five float4");
 // Bin record of the mixed-precision heterodyne: float32 summary data per channel with the
 // contraction's factors folded in (q0/2, q1/2, q2/w, q3/w, q4/4, q5/w; w = f_hi - f_lo).
 struct alignas(16) MixBin {   // 80 bytes, 16-byte aligned: five 128-bit loads per bin
     float q[18];
     float pad[2];
 };
+static_assert(sizeof(MixBin) == 80 && alignof(MixBin) == 16, "bin records are read as five float4");
 
 // per (edge, mode) of a higher-mode reference: Phi0_lm (float pair), u = h0_lm/h0 and
 // g = e^{-i Phi0_lm}/h0 per channel (float32 complex)

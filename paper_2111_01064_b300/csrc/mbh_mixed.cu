@@ -1314,9 +1314,22 @@ __device__ __forceinline__ double amp_fix(float eps_walker, double eps_ref)
 // delta = h/h0 - 1 of one walker at one edge record (the (2,2) mixed ratio of Sec. II B):
 // rho = amp T h0inv (raw transfer, all frequency-only factors in h0inv), delta = (rho - 1) +
 // rho (e^{-i dPhi} - 1) with dPhi in double-float; -1 outside the walker's support (h = 0)
-__device__ __forceinline__ void edge_delta_mixed(const WalkerDF& wd, const WalkerF& wf, const MixEdge& me, f2 tob,
+__device__ __forceinline__ void edge_delta_mixed(const WalkerDF& wd, const WalkerF& wf, const MixEdge* pe, f2 tob,
                                                  cf dl[3])
 {
+    // the 80-byte record as five 128-bit loads
+    const float4* p4 = reinterpret_cast<const float4*>(pe);
+    const float4 r0 = p4[0], r1 = p4[1], r2 = p4[2], r3 = p4[3];
+    MixEdge me;
+    me.f = make_float2(r0.x, r0.y);
+    me.f3 = make_float2(r0.z, r0.w);
+    me.fm3 = make_float2(r1.x, r1.y);
+    me.lnf3 = make_float2(r1.z, r1.w);
+    me.phi0 = make_float2(r2.x, r2.y);
+    me.h0inv[0] = make_float2(r2.z, r2.w);
+    me.h0inv[1] = make_float2(r3.x, r3.y);
+    me.h0inv[2] = make_float2(r3.z, r3.w);
+    me.xs = p4[4];
     const FreqDF q = {ld_f2(me.f), ld_f2(me.f3), ld_f2(me.fm3), ld_f2(me.lnf3)};
     f2 Phi;
     float sa, ca, amp;
@@ -1346,7 +1359,7 @@ __device__ __forceinline__ float4 tail_sums(const SrcDesc& S, const WalkerDF& wd
     if (!tail) return v;
     const int E = S.E;
     cf dl[3], dp[3];
-    edge_delta_mixed(wd, wf, S.mix.edge[E], tob, dl);
+    edge_delta_mixed(wd, wf, S.mix.edge + E, tob, dl);
 #pragma unroll
     for (int c = 0; c < 3; ++c) dp[c] = dprev[c];
     float bd, bh;
@@ -1398,7 +1411,7 @@ __device__ __forceinline__ void het_mixed_body(const HetLaunch& L)
         for (int r = 0; r < rounds; ++r) {
             const int e = r * G + lane;
             cf dl[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-            if (active && e <= E) edge_delta_mixed(wsd[lw], wsf[lw], S.mix.edge[e], tob, dl);
+            if (active && e <= E) edge_delta_mixed(wsd[lw], wsf[lw], S.mix.edge + e, tob, dl);
             cf dp[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -1633,7 +1646,7 @@ __device__ __forceinline__ void het_mixed_pt_body(const HetLaunch& L)
         for (int r = 0; r < rounds; ++r) {
             const int e = r * G + lane;
             cf dl[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-            if (active && e <= E) edge_delta_mixed(wsd[lw], wsf[lw], S.mix.edge[e], tob, dl);
+            if (active && e <= E) edge_delta_mixed(wsd[lw], wsf[lw], S.mix.edge + e, tob, dl);
             cf dp[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
