@@ -74,13 +74,13 @@ def fp64_peak_gflops(sm_mhz: float) -> float:
 
 
 # The mixed heterodyne kernel is bound by the float32 (FMA) pipe: per edge evaluation it
-# issues 641 FMA-pipe thread instructions (double-float phase chain, float32 response,
+# issues 639 FMA-pipe thread instructions (double-float phase chain, float32 response,
 # ratio and contraction), counted by ncu on het_mixed_kernel_capped<8,224>, the default launch
 # at 16384 walkers (FMA-pipe utilisation x peak x elapsed cycles / edges).  Peak: 148 SMs x 128
 # FP32 lanes x SM clock.
-HET_MIXED_FMA_INST_PER_EDGE = 641
+HET_MIXED_FMA_INST_PER_EDGE = 639
 HET_KERNEL = "het_mixed_kernel_capped<8,224>"
-HET_MIXED_DRAM_BYTES = 1.596160e6          # read + write per 16384-walker launch (ncu)
+HET_MIXED_DRAM_BYTES = 1.593600e6          # read + write per 16384-walker launch (ncu)
 STORED_DATA_BYTES = 75.74e6                # data pairs, read once per launch (ncu: 883.66 MB
 STORED_BYTES_PER_TEMPLATE = 50.4945e6      # for 16 templates = 75.74 MB + 16 x 50.49 MB)
 
