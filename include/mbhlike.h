@@ -62,9 +62,22 @@ typedef enum {
 } mbh_status;
 
 typedef enum {
-    MBH_FP64 = 0,  /* every step in float64 */
-    MBH_MIXED = 1  /* large phases (Psi, 2 pi f k.c, t(f)) in float64, amplitudes,
-                      response, ratios and products in float32, sums in float64 */
+    MBH_FP64 = 0,      /* every step in float64 */
+    MBH_MIXED = 1,     /* float32-pipe arithmetic with float64-class results where needed.
+                          Templates and the direct likelihood: the large phase Phi (Psi +
+                          2 pi f k.c) in double-float (two floats, ~48 bits), t(f) in float32
+                          with a rounding bound (double-float near the support bounds),
+                          amplitude and response in float32, sums in float64.
+                          Heterodyne, (2,2) references: every edge value formed relative to
+                          the reference in double-float (phase, time and amplitude as
+                          differences of per-walker float64 coefficients, the response, the
+                          ratio delta = r - 1 and the contraction), |dlnL| against float64
+                          <= 1e-3 up to SNR ~1000.  Heterodyne, higher modes: as
+                          MBH_MIXED_F32. */
+    MBH_MIXED_F32 = 2  /* heterodyne only: double-float phase difference, float32 response,
+                          ratio delta = r - 1 and per-bin products, double-float sums.  About
+                          3x faster than MBH_MIXED; its |dlnL| grows with <h|h> (~1e-3 at
+                          SNR ~120, beyond it above). */
 } mbh_precision;
 
 typedef struct {

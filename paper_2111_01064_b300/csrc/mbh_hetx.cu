@@ -1,0 +1,688 @@
+// Heterodyned likelihood in extended (double-float) precision, the MBH_MIXED path for (2,2)
+// references (Katz, arXiv:2111.01064, Sec. II B, Eqs. 10-19; the batched evaluations of
+// Sec. III B-C).
+//
+// Why the ratio is formed relative to the reference.  lnL = -1/2 <d - h|d - h> + const has, for
+// a walker far from the data, a gradient of size ~<h|h> with respect to h: a relative error eps
+// of the edge values r = h/h0 reaches lnL as ~<h|h> eps / sqrt(N_eff) (N_eff ~ 70-80 bins carry
+// the weight of log-spaced bins).  At SNR 1000 (<h|h> = 1e6) |dlnL| <= 1e-3 for every walker of
+// a batch needs eps <~ 1.5e-9 per edge, ~25 times below the float32 rounding of a response
+// chain, and below what even a double-float phase Phi ~ 1e6 rad keeps (~5e-9 rad).  So no large
+// quantity is formed at all: per walker, in float64, the coefficients of the *differences* to
+// the reference are computed once,
+//   Psi_PN(f) - Psi_PN,0(f) = sum_k D_k v0^{k-5} + ln v0 (Dl5 + Dl6 v0),
+//   t(f) - t0(f)           = v0^{-8} sum_k E_k v0^k + v0^{-2} El6 ln v0 + dT0,
+// (v = s v0 with s = (M/M0)^{1/3}, v0 = (pi M0 f)^{1/3} of the reference, so every power of v
+// is a power of v0 times a walker constant), and the per-edge evaluation, in double-float on
+// the float32 pipe, only ever handles the (small) differences: the phase difference
+//   dPhi = f (C1 + 2 pi (AU/c) [k.c(t) - k0.c(t0)]) + dPsi_PN,
+// the orbit at t = t0(f) + dt from the reference's angle alpha0(f) and the increment 2 pi dt/yr,
+// the amplitude ratio R exp(-f^2 (1/fc^2 - 1/fc0^2)) (f^{-7/6} cancels), and the raw transfer of
+// the walker, which the edge record's G_c = K_c/T0_c (float64, from the reference's transfer at
+// alpha0(f) and the frequency-only factors K_c) turns into the response ratio.  All of these
+// vanish (or are exactly 1) at the reference itself.  Then
+//   delta_c = r_c - 1 = (rho_c - 1) + rho_c (e^{-i dPhi} - 1),   rho_c = R e^u T_c G_c,
+// and the contraction of Eqs. 14 and 17 is regrouped per edge (each edge's delta meets the
+// summary data of its two bins through five double-float weights per channel; the bin's cross
+// term needs the neighbouring edge's delta) and accumulated in double-float.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "mbh_dfx.cuh"
+#include "mbh_internal.cuh"
+#include "mbh_model.cuh"
+
+using namespace mbh;
+
+namespace mbh {
+
+// sin(k pi/16), cos(k pi/16) - 1 for k = 0..16 (40-digit values, rounded to float64)
+__device__ const double kSinTabD[17][2] = {
+    {0.0, 0.0},
+    {0.1950903220161282678482849, -0.01921471959676955087381776},
+    {0.38268343236508977172846, -0.07612046748871324387181681},
+    {0.5555702330196022247428308, -0.1685303876974547629212116},
+    {0.7071067811865475244008444, -0.2928932188134524755991556},
+    {0.8314696123025452370787884, -0.4444297669803977752571692},
+    {0.9238795325112867561281832, -0.61731656763491022827154},
+    {0.9807852804032304491261822, -0.8049096779838717321517151},
+    {1.0, -1.0},
+    {0.9807852804032304491261822, -1.195090322016128267848285},
+    {0.9238795325112867561281832, -1.38268343236508977172846},
+    {0.8314696123025452370787884, -1.555570233019602224742831},
+    {0.7071067811865475244008444, -1.707106781186547524400844},
+    {0.5555702330196022247428308, -1.831469612302545237078788},
+    {0.38268343236508977172846, -1.923879532511286756128183},
+    {0.1950903220161282678482849, -1.980785280403230449126182},
+    {0.0, -2.0},
+};
+
+__device__ __forceinline__ f2 split_rn(double x)
+{
+    const float hi = (float)x;
+    return {hi, (float)(x - (double)hi)};
+}
+
+__device__ __forceinline__ void load_sintab(SinTab& tab)
+{
+    for (int k = threadIdx.x; k < 17; k += blockDim.x) {
+        const f2 s = split_rn(kSinTabD[k][0]), c = split_rn(kSinTabD[k][1]);
+        tab.v[k] = make_float4(s.hi, s.lo, c.hi, c.lo);
+    }
+}
+
+// v and ln v at f_max: pi M f_max = 0.05 pi sqrt(5/12) for every mass (f_max = f_c sqrt(5/12),
+// f_c = 0.05/M), so v(f_max), ln v(f_max), v^-5 and v^-8 are constants (40-digit values).
+constexpr double kXVm = 0.4663064457284195;
+constexpr double kXLnVm = -0.7629122521271803;
+constexpr double kXVm5Inv = 45.35685218040481;
+constexpr double kXVm8Inv = 447.3306440422728;
+
+// float64 quantities of one parameter vector (Sec. II A parameter derivation): the one
+// derivation used for the reference and for the walkers, so that their differences vanish
+// exactly for the reference itself.
+__device__ inline void xderive(const double* __restrict__ theta, int64_t W, int64_t i, XDer& x)
+{
+    const double mt = theta[kMT * W + i], q = theta[kQ * W + i];
+    const double a1 = theta[kA1 * W + i], a2 = theta[kA2 * W + i];
+    const double tref = theta[kTref * W + i];
+    const double lam = theta[kLam * W + i], bet = theta[kBeta * W + i];
+    const double dl = theta[kDL * W + i], phi = theta[kPhi * W + i];
+    const double iota = theta[kIota * W + i], pol = theta[kPsi * W + i];
+    const double opq = 1.0 + q;
+    const double M = mt * kMsunSec;
+    const double dist = dl * (1e9 * kParsec / kClight);
+    const double x1 = 1.0 / opq, x2 = q * x1;
+    const double eta = x1 * x2;
+    const double so = (113.0 / 12.0 * x1 * x1 + 25.0 / 4.0 * eta) * a1 +
+                      (113.0 / 12.0 * x2 * x2 + 25.0 / 4.0 * eta) * a2;
+    const double ss = 79.0 / 8.0 * eta * a1 * a2;
+    const double pi2 = kPi * kPi;
+    double al[8];
+    al[0] = 1.0;
+    al[1] = 0.0;
+    al[2] = 3715.0 / 756.0 + 55.0 / 9.0 * eta;
+    al[3] = -16.0 * kPi + 4.0 * so;
+    al[4] = 15293365.0 / 508032.0 + 27145.0 / 504.0 * eta + 3085.0 / 72.0 * eta * eta - 10.0 * ss;
+    al[5] = kPi * (38645.0 / 756.0 - 65.0 / 9.0 * eta);
+    const double alog5 = 3.0 * al[5];
+    al[6] = 11583231236531.0 / 4694215680.0 - 640.0 / 3.0 * pi2 - 6848.0 / 21.0 * kEulerGamma -
+            6848.0 / 21.0 * 1.386294361119890618834464242916353136 +
+            eta * (-15737765635.0 / 3048192.0 + 2255.0 / 12.0 * pi2) + 76055.0 / 1728.0 * eta * eta -
+            127825.0 / 1296.0 * eta * eta * eta;
+    const double alog6 = -6848.0 / 21.0;
+    al[7] = kPi * (77096675.0 / 254016.0 + 378515.0 / 1512.0 * eta - 74045.0 / 756.0 * eta * eta);
+    const double pre = 3.0 / (128.0 * eta), dpre = pre * (kPi / 3.0) * M;
+    double c[8], d[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        c[k] = pre * al[k];
+        d[k] = dpre * ((k - 5) * al[k]);
+    }
+    d[5] += dpre * alog5;
+    d[6] += dpre * alog6;
+    const double cl5 = pre * alog5, cl6 = pre * alog6, dl6 = dpre * alog6;
+    double P = c[7], Q = d[7];
+#pragma unroll
+    for (int k = 6; k >= 0; --k) {
+        P = fma(P, kXVm, c[k]);
+        Q = fma(Q, kXVm, d[k]);
+    }
+    constexpr double vm5 = kXVm * kXVm * kXVm * kXVm * kXVm, vm6 = vm5 * kXVm;
+    const double psi_max = (P + kXLnVm * (cl5 * vm5 + cl6 * vm6)) * kXVm5Inv;
+    const double dpsi_max = (Q + kXLnVm * dl6 * vm6) * kXVm8Inv;
+    const double fmax = 0.05 * 0.6454972243679028 / M;   // f_c sqrt(5/12)
+    x.mt = mt;
+    x.eta = eta;
+    x.dist = dist;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        x.c[k] = c[k];
+        x.d[k] = d[k] * kInvTwoPi;
+    }
+    x.c[5] += fmax * dpsi_max - psi_max;   // the t_ref/f_max pinning's constant
+    x.cl5 = cl5;
+    x.cl6 = cl6;
+    x.dl6 = dl6 * kInvTwoPi;
+    x.t0 = tref - dpsi_max * kInvTwoPi;
+    x.c1 = kTwoPi * tref - dpsi_max;
+    x.fcut = 0.2 / M;
+    x.ifc2 = 400.0 * M * M;
+    double sl, cl, sb, cbt, s2p, c2p, s2f, c2f;
+    sincos(lam, &sl, &cl);
+    sincos(bet, &sb, &cbt);
+    sincos(2.0 * pol, &s2p, &c2p);
+    sincos(2.0 * phi, &s2f, &c2f);
+    x.kx = kTwoPi * kAUSec * (-cbt * cl);
+    x.ky = kTwoPi * kAUSec * (-cbt * sl);
+    constexpr double isq3 = 0.57735026918962576451;
+    x.k3[0] = -cbt * cl * isq3;
+    x.k3[1] = -cbt * sl * isq3;
+    x.k3[2] = -sb * isq3;
+    x.eu[0] = sl * isq3;
+    x.eu[1] = -cl * isq3;
+    x.ev[0] = -sb * cl * isq3;
+    x.ev[1] = -sb * sl * isq3;
+    x.ev[2] = cbt * isq3;
+    const double ylm = 0.15769578262626002 /* sqrt(5/(64 pi)) */;
+    const double ci = cos(iota);
+    const double ap = ylm * (1.0 + ci * ci), ac = 2.0 * ylm * ci;
+    // K+ = ap e^{2i phi}, Kx = i ac e^{2i phi}; Ga = cos2psi K+ - sin2psi Kx, Gb = sin2psi K+ + cos2psi Kx
+    x.G[0] = c2p * ap * c2f + s2p * ac * s2f;
+    x.G[1] = c2p * ap * s2f - s2p * ac * c2f;
+    x.G[2] = s2p * ap * c2f - c2p * ac * s2f;
+    x.G[3] = s2p * ap * s2f + c2p * ac * c2f;
+}
+
+// Walker constants relative to the reference (double-float, shared memory).
+struct XWalker {
+    f2 D[8], Dl5, Dl6;   // phase difference coefficients (D[1] = 0)
+    f2 E[8], El6, dT0;   // time difference coefficients
+    f2 C1;               // coefficient of f: 2 pi (t_ref - t_ref0) - (psi'_max - psi'_max,0)
+    f2 dkx, dky, kx, ky; // orbit phase: 2 pi AU/c (k - k0) and k of the walker (in-plane)
+    f2 fcut, R, difc2;   // f_cut; amplitude ratio; 1/fc^2 - 1/fc0^2
+    f2 k3[3], eu[2], ev[3], Ga[2], Gb[2];   // response constants (as the float32 path)
+};
+
+__device__ inline void xwalker_setup(const double* __restrict__ theta, int64_t W, int64_t i,
+                                     const XDer& r, XWalker& o)
+{
+    XDer w;
+    xderive(theta, W, i, w);
+    const double rm = w.mt / r.mt;
+    const double s = w.mt == r.mt ? 1.0 : cbrt(rm);
+    const double ls = w.mt == r.mt ? 0.0 : log(rm) * (1.0 / 3.0);
+    const double is = 1.0 / s;
+    double sp[16];   // s^{k}, k = -8..7, at sp[k + 8]
+    sp[8] = 1.0;
+    for (int k = 1; k < 8; ++k) sp[8 + k] = sp[7 + k] * s;
+    for (int k = 1; k <= 8; ++k) sp[8 - k] = sp[9 - k] * is;
+    double D[8], E[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        D[k] = w.c[k] * sp[8 + k - 5] - r.c[k];
+        E[k] = w.d[k] * sp[k] - r.d[k];   // s^{k - 8}
+    }
+    D[5] += w.cl5 * ls;
+    D[6] += w.cl6 * s * ls;
+    E[6] += w.dl6 * sp[6] * ls;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        o.D[k] = split_rn(D[k]);
+        o.E[k] = split_rn(E[k]);
+    }
+    o.Dl5 = split_rn(w.cl5 - r.cl5);
+    o.Dl6 = split_rn(w.cl6 * s - r.cl6);
+    o.El6 = split_rn(w.dl6 * sp[6] - r.dl6);
+    o.dT0 = split_rn(w.t0 - r.t0);
+    o.C1 = split_rn(w.c1 - r.c1);
+    o.dkx = split_rn(w.kx - r.kx);
+    o.dky = split_rn(w.ky - r.ky);
+    o.kx = split_rn(w.kx);
+    o.ky = split_rn(w.ky);
+    o.fcut = split_rn(w.fcut);
+    // A(f) = sqrt(2 pi/3) pi^{-2/3} M^{5/6} eta^{1/2} f^{-7/6} exp(-(f/f_c)^2) / D: the ratio of
+    // the f-independent factors is s^{5/2} (eta/eta0)^{1/2} D0/D
+    o.R = split_rn(s * s * sqrt(s * w.eta / r.eta) * (r.dist / w.dist));
+    o.difc2 = split_rn(w.ifc2 - r.ifc2);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        o.k3[j] = split_rn(w.k3[j]);
+        o.ev[j] = split_rn(w.ev[j]);
+    }
+    o.eu[0] = split_rn(w.eu[0]);
+    o.eu[1] = split_rn(w.eu[1]);
+    o.Ga[0] = split_rn(w.G[0]);
+    o.Ga[1] = split_rn(w.G[1]);
+    o.Gb[0] = split_rn(w.G[2]);
+    o.Gb[1] = split_rn(w.G[3]);
+}
+
+constexpr f2 kH3 = df_const(0.8660254037844386467637231707529361835);   // sqrt3/2
+constexpr f2 kOrbRate = df_const(6.283185307179586476925286766559005768 / 31557600.0);   // 2 pi / yr
+
+// sin(x(1 - kn)) and sinc(x(1 + kn)) - sinc(x(1 - kn)) of one arm (the one-link sinc factors
+// of the float32 path's transfer).  Below x = 0.3: sinc(b) = 1 - b^2/6 + b^4 (...) with the b^4
+// tail in float32 (< 1.1e-3, rounding < 7e-11), and the difference as 4 x^2 kn (-1/6 + S) with
+// S = sum_{j>=2} (-1)^j P_j/(2j+1)! (P_1 = 1, P_{j+1} = a^2 P_j + b^{2j}, a = x(1 + kn),
+// b = x(1 - kn)) in float32 (|S| < 6e-3); above, both sincs in double-float.
+__device__ __forceinline__ void arm_sincs(f2 x, f2 kn, const SinTab& tab, f2& sm, f2& sd)
+{
+    const f2 b = dd_mul_lazy(x, dd_add_f_lazy({-kn.hi, -kn.lo}, 1.0f));
+    if (x.hi < 0.3f) {
+        const f2 b2 = dd_sqr_lazy(b);
+        const float z = b2.hi;
+        const float tail = z * z * fmaf(z, fmaf(z, 1.0f / 362880.0f, -1.0f / 5040.0f), 1.0f / 120.0f);
+        sm = dd_add_f_lazy(dd_add_f_lazy(dd_mul_lazy(b2, kSc1), tail), 1.0f);
+        const float xa = x.hi * (1.0f + kn.hi), a2 = xa * xa;
+        float P = 1.0f, bp = 1.0f, S = 0.0f, sg = 1.0f;
+        constexpr float inv_fact[4] = {1.0f / 120.0f, 1.0f / 5040.0f, 1.0f / 362880.0f, 1.0f / 39916800.0f};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {   // P_{j+2} and the terms j + 2 = 2..5
+            bp *= z;
+            P = fmaf(a2, P, bp);
+            S = fmaf(sg * P, inv_fact[j], S);
+            sg = -sg;
+        }
+        const f2 k4 = dd_scale(dd_mul_lazy(dd_sqr_lazy(x), kn), 4.0f);
+        sd = dd_add_f_lazy(dd_mul_lazy(k4, kSc1), k4.hi * S);
+    } else {
+        const f2 a = dd_mul_lazy(x, dd_add_f_lazy(kn, 1.0f));
+        sm = dd_sinc(b, tab);
+        sd = dd_sub_lazy(dd_sinc(a, tab), sm);
+    }
+}
+
+// Raw transfer of the walker at orbit angle (sa, ca): the construction of the float32 path's
+// transfer_f32<raw> (spacecraft offsets u_i in units of L/sqrt3, arm phases x - q_m with
+// e^{i q_m}, q_m = x (k/sqrt3).u_m, polarisation response a Ga + b Gb, one-link sinc factors,
+// first-generation TDI with D = e^{-2ix} = (c2, -s2)) in double-float:
+//   T_A = P_A + D Q_A, T_E = P_E + D Q_E, T_T = z0 + z1 + z2 with, per arm, yf = g sinc(x(1-kn))
+//   and z = g [sinc(x(1+kn)) - sinc(x(1-kn))],
+//   P_A = U - z0, Q_A = U - z1, U = 2 yf2 + z2 - yf1 - yf0,
+//   P_E = V + z0 + z2 - 2 z1, Q_E = V + 2 z0 - z2 - z1, V = 3 (yf0 - yf1).
+__device__ inline void transfer_df(const XWalker& w, f2 x, f2 s2, f2 c2, f2 sa, f2 ca, const SinTab& tab,
+                                   c2f T[3])
+{
+    const f2 h3s = dd_mul_lazy(kH3, sa), h3c = dd_mul_lazy(kH3, ca);
+    const f2 hs = dd_scale(sa, 0.5f), hc = dd_scale(ca, 0.5f);
+    const f2 sp[3] = {sa, dd_sub_lazy({-hs.hi, -hs.lo}, h3c), dd_add_lazy({-hs.hi, -hs.lo}, h3c)};
+    const f2 cp[3] = {ca, dd_add_lazy({-hc.hi, -hc.lo}, h3s), dd_sub_lazy({-hc.hi, -hc.lo}, h3s)};
+    f2 u[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const f2 a0 = dd_mul_lazy(sp[i], sa), b0 = dd_mul_lazy(cp[i], hc);
+        u[i][0] = {-(a0.hi), -(a0.lo)};
+        u[i][0] = dd_sub_lazy(u[i][0], b0);
+        u[i][1] = dd_sub_lazy(dd_mul_lazy(sp[i], ca), dd_mul_lazy(cp[i], hs));
+        const f2 z = dd_mul_lazy(kH3, cp[i]);
+        u[i][2] = {-z.hi, -z.lo};
+    }
+    f2 kap[3];
+#pragma unroll
+    for (int m = 0; m < 2; ++m)
+        kap[m] = dd_add_lazy(dd_add_lazy(dd_mul_lazy(w.k3[0], u[m][0]), dd_mul_lazy(w.k3[1], u[m][1])),
+                             dd_mul_lazy(w.k3[2], u[m][2]));
+    kap[2] = dd_add_lazy(kap[0], kap[1]);
+    kap[2] = {-kap[2].hi, -kap[2].lo};
+    c2f E[3];   // e^{i q_m}
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+        f2 s, cm1;
+        dd_sincos_any(dd_mul_lazy(x, kap[m]), tab, s, cm1);
+        E[m] = {dd_add_f_lazy(cm1, 1.0f), s};
+    }
+    const c2f e01 = cd_mul(E[0], E[1]);
+    E[2] = {e01.re, {-e01.im.hi, -e01.im.lo}};
+    c2f yf[3], z[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int i = a, j = (a + 1) % 3, m = (a + 2) % 3;
+        f2 d[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) d[q] = dd_sub_lazy(u[j][q], u[i][q]);
+        const f2 kn = dd_sub_lazy(kap[j], kap[i]);
+        const f2 un = dd_add_lazy(dd_mul_lazy(w.eu[0], d[0]), dd_mul_lazy(w.eu[1], d[1]));
+        const f2 vn = dd_add_lazy(dd_add_lazy(dd_mul_lazy(w.ev[0], d[0]), dd_mul_lazy(w.ev[1], d[1])),
+                                  dd_mul_lazy(w.ev[2], d[2]));
+        const f2 pa = dd_sub_lazy(dd_sqr_lazy(un), dd_sqr_lazy(vn));
+        const f2 pb = dd_scale(dd_mul_lazy(un, vn), 2.0f);
+        const c2f F = {dd_add_lazy(dd_mul_lazy(pa, w.Ga[0]), dd_mul_lazy(pb, w.Gb[0])),
+                       dd_add_lazy(dd_mul_lazy(pa, w.Ga[1]), dd_mul_lazy(pb, w.Gb[1]))};
+        const c2f eF = cd_mul(E[m], F);
+        const c2f g = {{-eF.im.hi, -eF.im.lo}, eF.re};   // i e^{i q_m} F
+        f2 sm, sd;
+        arm_sincs(x, kn, tab, sm, sd);
+        yf[a] = cd_mul_r(g, sm);
+        z[a] = cd_mul_r(g, sd);
+    }
+    const c2f U = cd_sub(cd_sub(cd_add(cd_scale(yf[2], 2.0f), z[2]), yf[1]), yf[0]);
+    const c2f PA = cd_sub(U, z[0]), QA = cd_sub(U, z[1]);
+    const c2f d01 = cd_sub(yf[0], yf[1]);
+    const c2f V = cd_add(cd_scale(d01, 2.0f), d01);
+    const c2f PE = cd_sub(cd_add(cd_add(V, z[0]), z[2]), cd_scale(z[1], 2.0f));
+    const c2f QE = cd_sub(cd_sub(cd_add(V, cd_scale(z[0], 2.0f)), z[2]), z[1]);
+    const c2f D = {c2, {-s2.hi, -s2.lo}};
+    T[0] = cd_add(PA, cd_mul(D, QA));
+    T[1] = cd_add(PE, cd_mul(D, QE));
+    T[2] = cd_add(cd_add(z[0], z[1]), z[2]);
+}
+
+// delta = r - 1 of one walker at one edge record (Sec. II B, Eq. 10), double-float; -1 where the
+// walker's template or the reference's is zero.
+__device__ __forceinline__ void edge_delta_x(const XWalker& w, const XEdge* __restrict__ pe, f2 tob,
+                                             const SinTab& tab, c2f dl[3])
+{
+    const float4* p4 = reinterpret_cast<const float4*>(pe);
+    const float4 r0 = p4[0], r1 = p4[1], r2 = p4[2], r3 = p4[3], r4 = p4[4];
+    const f2 f = {r0.x, r0.y}, v0 = {r0.z, r0.w}, iv0 = {r1.x, r1.y}, lnv0 = {r1.z, r1.w};
+    const f2 t0 = {r2.x, r2.y}, ca0 = {r2.z, r2.w}, sa0 = {r3.x, r3.y}, x = {r3.z, r3.w};
+    const f2 s2 = {r4.x, r4.y}, c2 = {r4.z, r4.w};
+    // t(f) - t0(f) and the support test on t = t0 + dt, f <= f_cut
+    f2 Q = w.E[7];
+#pragma unroll
+    for (int k = 6; k >= 0; --k) Q = dd_fma_lazy(Q, v0, w.E[k]);
+    const f2 iv2 = dd_sqr_lazy(iv0), iv4 = dd_sqr_lazy(iv2), iv8 = dd_sqr_lazy(iv4);
+    const f2 dt = dd_add_lazy(dd_add_lazy(dd_mul_lazy(Q, iv8), dd_mul_lazy(dd_mul_lazy(w.El6, lnv0), iv2)), w.dT0);
+    const f2 t = dd_add(t0, dd_norm(dt));
+    if (!(dd_le(f, w.fcut) && !dd_lt0(t) && dd_le(t, tob))) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) dl[c] = {{-1.0f, 0.0f}, {0.0f, 0.0f}};
+        return;
+    }
+    // orbit angle alpha = alpha0 + 2 pi dt / yr
+    f2 sD, cD;
+    dd_sincos_any(dd_mul_lazy(dt, kOrbRate), tab, sD, cD);
+    const f2 sa = dd_add_lazy(sa0, dd_add_lazy(dd_mul_lazy(sa0, cD), dd_mul_lazy(ca0, sD)));
+    const f2 ca = dd_add_lazy(ca0, dd_sub_lazy(dd_mul_lazy(ca0, cD), dd_mul_lazy(sa0, sD)));
+    // 2 pi AU/c [k.c(t) - k0.c(t0)] = dk.c(t0) + (cos da - 1) k.c(t0) + sin da (k x c(t0))_z
+    const f2 kc0 = dd_add_lazy(dd_mul_lazy(w.kx, ca0), dd_mul_lazy(w.ky, sa0));
+    const f2 ks0 = dd_sub_lazy(dd_mul_lazy(w.ky, ca0), dd_mul_lazy(w.kx, sa0));
+    const f2 dorb = dd_add_lazy(dd_add_lazy(dd_mul_lazy(w.dkx, ca0), dd_mul_lazy(w.dky, sa0)),
+                                dd_add_lazy(dd_mul_lazy(cD, kc0), dd_mul_lazy(sD, ks0)));
+    // Psi_PN - Psi_PN,0 = sum_k D_k v0^{k-5} + ln v0 (Dl5 + Dl6 v0)
+    f2 N = dd_mul_lazy(w.D[0], iv0);
+#pragma unroll
+    for (int k = 2; k <= 5; ++k) N = dd_fma_lazy(N, iv0, w.D[k]);
+    const f2 Pp = dd_mul_lazy(dd_fma_lazy(w.D[7], v0, w.D[6]), v0);
+    const f2 L = dd_mul_lazy(lnv0, dd_fma_lazy(w.Dl6, v0, w.Dl5));
+    const f2 dphi = dd_norm(dd_add_lazy(dd_mul_lazy(f, dd_add_lazy(w.C1, dorb)), dd_add_lazy(dd_add_lazy(N, Pp), L)));
+    f2 sP, cP;
+    dd_sincos_any(dphi, tab, sP, cP);
+    const c2f em1 = {cP, {-sP.hi, -sP.lo}};   // e^{-i dPhi} - 1
+    // amplitude ratio R exp(-f^2 (1/fc^2 - 1/fc0^2))
+    const f2 ff = dd_sqr_lazy(f);
+    const f2 u = dd_mul_lazy(ff, w.difc2);
+    const f2 A = dd_mul_lazy(w.R, dd_exp({-u.hi, -u.lo}));
+    c2f T[3];
+    transfer_df(w, x, s2, c2, sa, ca, tab, T);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float4 g = p4[5 + c];
+        const c2f rho = cd_mul_r(cd_mul(T[c], {{g.x, g.y}, {g.z, g.w}}), A);
+        const c2f rm1 = {dd_add_f_lazy(rho.re, -1.0f), rho.im};
+        dl[c] = cd_norm(cd_add(rm1, cd_mul(rho, em1)));
+    }
+}
+
+// The edge's share of <d|h> and <h|h> (Eqs. 14 and 17 regrouped per edge, factor 4 included):
+//   <d|h>: war Re delta + wai Im delta,
+//   <h|h>: wbr Re delta + wq |delta|^2 + wc Re(delta_prev conj(delta)),
+// with delta_prev the previous edge's (its bin's cross term; wc = 0 at edge 0).
+__device__ __forceinline__ void contract_x(const XWeight* __restrict__ pw, const c2f dp[3], const c2f dl[3],
+                                           f2& adh, f2& ahh)
+{
+    const float4* p4 = reinterpret_cast<const float4*>(pw);
+    const float4 wc01 = p4[6], wc2 = p4[7];
+    const f2 wc[3] = {{wc01.x, wc01.y}, {wc01.z, wc01.w}, {wc2.x, wc2.y}};
+    f2 sdh = {0.0f, 0.0f}, shh = {0.0f, 0.0f};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float4 a = p4[2 * c], b = p4[2 * c + 1];
+        sdh = dd_add_lazy(sdh, dd_add_lazy(dd_mul_lazy({a.x, a.y}, dl[c].re), dd_mul_lazy({a.z, a.w}, dl[c].im)));
+        const f2 m2 = dd_add_lazy(dd_sqr_lazy(dl[c].re), dd_sqr_lazy(dl[c].im));
+        const f2 cr = dd_add_lazy(dd_mul_lazy(dp[c].re, dl[c].re), dd_mul_lazy(dp[c].im, dl[c].im));
+        shh = dd_add_lazy(shh, dd_add_lazy(dd_add_lazy(dd_mul_lazy({b.x, b.y}, dl[c].re), dd_mul_lazy({b.z, b.w}, m2)),
+                                           dd_mul_lazy(wc[c], cr)));
+    }
+    df_acc(adh, sdh);
+    df_acc(ahh, shh);
+}
+
+// ------------------------------------------------------------------------------------------
+// the kernel: layout and reductions as the float32 path's het_mixed_kernel (tiles of BLOCK/G
+// walkers of one source, G threads per walker dealing the edges round-robin, the previous
+// edge's delta from the neighbouring lane, lane sums reduced in a fixed order)
+// ------------------------------------------------------------------------------------------
+template <int G, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) het_x_kernel(const __grid_constant__ HetLaunch L)
+{
+    constexpr int WPB = BLOCK / G;
+    __shared__ XWalker xw[WPB];
+    __shared__ SinTab tab;
+    const int lw = threadIdx.x / G, lane = threadIdx.x % G;
+    load_sintab(tab);
+    for (int tile = blockIdx.x; tile < L.n_tiles; tile += gridDim.x) {
+        int s = 0;
+        while (s + 1 < L.n_src && L.src[s + 1].tile_begin <= tile) ++s;
+        const SrcDesc& S = L.src[s];
+        const int64_t w0 = S.w_begin + (int64_t)(tile - S.tile_begin) * WPB;
+        const bool active = w0 + lw < S.w_end;
+        __syncthreads();
+        for (int j = threadIdx.x; j < WPB; j += BLOCK)
+            if (w0 + j < S.w_end) xwalker_setup(L.theta, L.W, w0 + j, *S.mix.xder, xw[j]);
+        __syncthreads();
+        const int E = S.E;
+        const f2 tob = {S.tob_hi, S.tob_lo};
+        f2 adh = {0.0f, 0.0f}, ahh = {0.0f, 0.0f};
+        c2f carry[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) carry[c] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
+        const int rounds = (E + 1 + G - 1) / G;
+        for (int r = 0; r < rounds; ++r) {
+            const int e = r * G + lane;
+            c2f dl[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) dl[c] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
+            if (active && e <= E) edge_delta_x(xw[lw], S.mix.xedge + e, tob, tab, dl);
+            c2f dp[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                dp[c].re.hi = __shfl_up_sync(0xffffffffu, dl[c].re.hi, 1, G);
+                dp[c].re.lo = __shfl_up_sync(0xffffffffu, dl[c].re.lo, 1, G);
+                dp[c].im.hi = __shfl_up_sync(0xffffffffu, dl[c].im.hi, 1, G);
+                dp[c].im.lo = __shfl_up_sync(0xffffffffu, dl[c].im.lo, 1, G);
+                if (lane == 0) dp[c] = carry[c];
+                carry[c].re.hi = __shfl_sync(0xffffffffu, dl[c].re.hi, G - 1, G);
+                carry[c].re.lo = __shfl_sync(0xffffffffu, dl[c].re.lo, G - 1, G);
+                carry[c].im.hi = __shfl_sync(0xffffffffu, dl[c].im.hi, G - 1, G);
+                carry[c].im.lo = __shfl_sync(0xffffffffu, dl[c].im.lo, G - 1, G);
+            }
+            if (active && e <= E) contract_x(S.mix.xw + e, dp, dl, adh, ahh);
+        }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+            const f2 odh = {__shfl_down_sync(0xffffffffu, adh.hi, o, G), __shfl_down_sync(0xffffffffu, adh.lo, o, G)};
+            const f2 ohh = {__shfl_down_sync(0xffffffffu, ahh.hi, o, G), __shfl_down_sync(0xffffffffu, ahh.lo, o, G)};
+            df_acc(adh, odh);
+            df_acc(ahh, ohh);
+        }
+        if (lane == 0 && active) {
+            const int64_t wi = w0 + lw;
+            const double dh = S.mix.xsumA + df_to_double(adh);
+            const double hh = S.mix.xsumB + df_to_double(ahh);
+            L.out[wi] = -0.5 * (S.dd + hh - 2.0 * dh);
+            L.out[L.W + wi] = dh;
+            L.out[2 * L.W + wi] = hh;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// reference tables
+// ------------------------------------------------------------------------------------------
+__global__ void xref_kernel(const double* __restrict__ theta0, XDer* __restrict__ out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) xderive(theta0, 1, 0, *out);
+}
+
+// Edge records: the reference's v0, 1/v0, ln v0, t0(f), its orbit angle alpha0 = 2 pi t0/yr, the
+// one-link phase x = pi f L/c with sin 2x, cos 2x, and G_c = K_c/T0_c (float64: T0_c the
+// reference's full transfer at alpha0, K_c the frequency-only factors that the raw transfer
+// leaves out), 0 where h0 = 0.
+__global__ void xedge_kernel(const double* __restrict__ theta0, const XDer* __restrict__ xr, double t_obs,
+                             const double* __restrict__ fe, int n_edges, XEdge* __restrict__ out)
+{
+    __shared__ Walker w;
+    if (threadIdx.x == 0) walker_setup(theta0, 1, 0, w, 1u);
+    __syncthreads();
+    const XDer& r = *xr;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_edges; e += gridDim.x * blockDim.x) {
+        const double f = fe[e];
+        const double v0 = cbrt(kPi * r.mt * kMsunSec * f), iv0 = 1.0 / v0, lnv0 = log(v0);
+        double Q = r.d[7];
+        for (int k = 6; k >= 0; --k) Q = fma(Q, v0, r.d[k]);
+        const double iv2 = iv0 * iv0, iv8 = iv2 * iv2 * iv2 * iv2;
+        const double t0 = Q * iv8 + r.dl6 * lnv0 * iv2 + r.t0;
+        double sa0, ca0;
+        sincos(kTwoPi * t0 / kYear, &sa0, &ca0);
+        const double x = kPi * kArmSec * f;
+        double s1, c1, s2x, c2x, s3, c3;
+        sincos(x, &s1, &c1);
+        sincos(2.0 * x, &s2x, &c2x);
+        sincos(3.0 * x, &s3, &c3);
+        XEdge m;
+        const f2 vals[10] = {split_rn(f), split_rn(v0), split_rn(iv0), split_rn(lnv0), split_rn(t0),
+                             split_rn(ca0), split_rn(sa0), split_rn(x), split_rn(s2x), split_rn(c2x)};
+        float* p = reinterpret_cast<float*>(&m);
+        for (int j = 0; j < 10; ++j) {
+            p[2 * j] = vals[j].hi;
+            p[2 * j + 1] = vals[j].lo;
+        }
+        // the reference's support (as its float64 template): h0 = 0 outside
+        cd h0[3];
+        const bool in = point_f64(w, f, t_obs, h0);
+        cd T0[3];
+        transfer_f64(w, f, sa0, ca0, w.Kp, w.Kc, T0);
+        // K: W = (1 - D^2)(-x) e^{-ix} = -2 x sin2x (sin3x, cos3x), 1 - D = 2 sin x (sin x, cos x);
+        // K_A = W/sqrt2, K_E = W/sqrt6, K_T = W (1 - D)/sqrt3
+        const double wm = -2.0 * x * s2x;
+        const double wr = wm * s3, wi = wm * c3;
+        const double ar = 2.0 * s1 * s1, ai = 2.0 * s1 * c1;
+        const cd K[3] = {{wr / kSqrt2, wi / kSqrt2}, {wr / kSqrt6, wi / kSqrt6},
+                         {(wr * ar - wi * ai) / kSqrt3, (wr * ai + wi * ar) / kSqrt3}};
+        for (int c = 0; c < 3; ++c) {
+            const double m2 = T0[c].re * T0[c].re + T0[c].im * T0[c].im;
+            double gr = 0.0, gi = 0.0;
+            if (in && m2 > 0.0 && (h0[c].re != 0.0 || h0[c].im != 0.0)) {
+                gr = (K[c].re * T0[c].re + K[c].im * T0[c].im) / m2;
+                gi = (K[c].im * T0[c].re - K[c].re * T0[c].im) / m2;
+            }
+            const f2 a = split_rn(gr), b = split_rn(gi);
+            p[20 + 4 * c] = a.hi;
+            p[21 + 4 * c] = a.lo;
+            p[22 + 4 * c] = b.hi;
+            p[23 + 4 * c] = b.lo;
+        }
+        out[e] = m;
+    }
+}
+
+// Per-edge contraction weights (factor 4 included) from the summary data of the edge's two bins
+// (bin e as its lower edge, bin e - 1 as its upper edge), and the constant parts 4 sum Re A0,
+// 4 sum B0.
+__global__ void xweight_kernel(const double* __restrict__ summary, const double* __restrict__ invw, int E,
+                               XWeight* __restrict__ out, double* __restrict__ sums)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e <= E) {
+        XWeight m;
+        float* p = reinterpret_cast<float*>(&m);
+        for (int j = 0; j < 32; ++j) p[j] = 0.0f;
+        for (int c = 0; c < 3; ++c) {
+            double war = 0.0, wai = 0.0, wbr = 0.0, wq = 0.0, wc = 0.0;
+            if (e < E) {   // lower edge of bin e
+                const double* q = summary + ((int64_t)e * 3 + c) * 6;
+                const double iw = invw[e];
+                war += 0.5 * q[0] - q[2] * iw;
+                wai += 0.5 * q[1] - q[3] * iw;
+                wbr += q[4] - 2.0 * q[5] * iw;
+                wq += 0.25 * q[4] - q[5] * iw;
+            }
+            if (e >= 1) {   // upper edge of bin e - 1
+                const double* q = summary + ((int64_t)(e - 1) * 3 + c) * 6;
+                const double iw = invw[e - 1];
+                war += 0.5 * q[0] + q[2] * iw;
+                wai += 0.5 * q[1] + q[3] * iw;
+                wbr += q[4] + 2.0 * q[5] * iw;
+                wq += 0.25 * q[4] + q[5] * iw;
+                wc = 0.5 * q[4];
+            }
+            const f2 v[4] = {split_rn(4.0 * war), split_rn(4.0 * wai), split_rn(4.0 * wbr), split_rn(4.0 * wq)};
+            for (int j = 0; j < 4; ++j) {
+                p[8 * c + 2 * j] = v[j].hi;
+                p[8 * c + 2 * j + 1] = v[j].lo;
+            }
+            const f2 cc = split_rn(4.0 * wc);
+            p[24 + 2 * c] = cc.hi;
+            p[25 + 2 * c] = cc.lo;
+        }
+        out[e] = m;
+    }
+    if (e == 0) {
+        double a = 0.0, b = 0.0;
+        for (int i = 0; i < E; ++i)
+            for (int c = 0; c < 3; ++c) {
+                a += summary[((int64_t)i * 3 + c) * 6 + 0];
+                b += summary[((int64_t)i * 3 + c) * 6 + 4];
+            }
+        sums[0] = 4.0 * a;
+        sums[1] = 4.0 * b;
+    }
+}
+
+// Tables of the extended-precision heterodyne for a (2,2) reference: XDer of theta0, edge
+// records, edge weights and the constant parts (read back to the host into R->mix).
+cudaError_t prepare_x_tables(mbh_ref* R, cudaStream_t st)
+{
+    const int E = R->E;
+    cudaError_t e = cudaMalloc(&R->x_der, sizeof(XDer));
+    if (e == cudaSuccess) e = cudaMalloc(&R->x_edge, sizeof(XEdge) * (E + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&R->x_w, sizeof(XWeight) * (E + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&R->x_sums, sizeof(double) * 2);
+    if (e != cudaSuccess) return e;
+    xref_kernel<<<1, 32, 0, st>>>(R->theta0_dev, R->x_der);
+    xedge_kernel<<<(E + 1 + 127) / 128, 128, 0, st>>>(R->theta0_dev, R->x_der, R->grid.t_obs, R->fe, E + 1,
+                                                      R->x_edge);
+    xweight_kernel<<<(E + 1 + 127) / 128, 128, 0, st>>>(R->summary, R->invw, E, R->x_w, R->x_sums);
+    e = cudaGetLastError();
+    double sums[2];
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sums, R->x_sums, sizeof sums, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) {
+        R->mix.xder = R->x_der;
+        R->mix.xedge = R->x_edge;
+        R->mix.xw = R->x_w;
+        R->mix.xsumA = sums[0];
+        R->mix.xsumB = sums[1];
+    }
+    return e;
+}
+
+void free_x_tables(mbh_ref* R)
+{
+    if (R->x_der) cudaFree(R->x_der);
+    if (R->x_edge) cudaFree(R->x_edge);
+    if (R->x_w) cudaFree(R->x_w);
+    if (R->x_sums) cudaFree(R->x_sums);
+}
+
+}  // namespace mbh
+
+namespace {
+template <int G, int BLOCK>
+cudaError_t launch_het_x(const HetLaunch& L, int grid, cudaStream_t st)
+{
+    het_x_kernel<G, BLOCK><<<grid, BLOCK, 0, st>>>(L);
+    return cudaGetLastError();
+}
+}  // namespace
+
+namespace mbh {
+HetKernel het_kernel_x(int G, int block)
+{
+#define MBH_CASE(g, b) \
+    if (G == g && block == b) return {&launch_het_x<g, b>, (const void*)&het_x_kernel<g, b>};
+    MBH_CASE(1, 64) MBH_CASE(1, 128)
+    MBH_CASE(2, 64) MBH_CASE(2, 128)
+    MBH_CASE(4, 64) MBH_CASE(4, 128) MBH_CASE(4, 256)
+    MBH_CASE(8, 64) MBH_CASE(8, 128) MBH_CASE(8, 256)
+    MBH_CASE(16, 64) MBH_CASE(16, 128) MBH_CASE(16, 256)
+    MBH_CASE(32, 64) MBH_CASE(32, 128) MBH_CASE(32, 256)
+#undef MBH_CASE
+    return {nullptr, nullptr};
+}
+}  // namespace mbh

@@ -44,6 +44,30 @@ struct MixModeHM {
     float2 g[3];
 };
 
+// Extended-precision (double-float) heterodyne tables (mbh_hetx.cu).
+// float64 quantities of one parameter vector (Sec. II A), the same derivation for the reference
+// and the walkers: PN phase and time coefficients, pinning, cut and taper, amplitude factors, the
+// in-plane propagation components (times 2 pi AU/c) and the response constants.
+struct XDer {
+    double mt, eta, dist;
+    double c[8], cl5, cl6;   // Psi_PN = sum_k c_k v^{k-5} + ln v (cl5 + cl6 v); c[5] holds the pinning constant
+    double d[8], dl6;        // t(f) = sum_k d_k v^{k-8} + dl6 v^{-2} ln v + t0
+    double t0, c1;           // t0 = t_ref - psi'(f_max)/2 pi; c1 = 2 pi t_ref - psi'(f_max)
+    double fcut, ifc2;       // f_cut; 1/f_c^2
+    double kx, ky;           // 2 pi AU/c (k_x, k_y)
+    double k3[3], eu[2], ev[3], G[4];   // k/sqrt3, u/sqrt3, v/sqrt3; mode factors Ga, Gb (re, im)
+};
+// Edge record (8 x 128-bit loads): f, v0, 1/v0, ln v0, t0(f), cos alpha0, sin alpha0, x, sin 2x,
+// cos 2x as float pairs; G_c = K_c/T0_c (complex float pairs) per channel.
+struct alignas(16) XEdge {
+    float v[32];
+};
+// Edge weights (8 x 128-bit loads): per channel (war, wai), (wbr, wq) as float pairs; then the
+// cross-term weights wc of the three channels.
+struct alignas(16) XWeight {
+    float v[32];
+};
+
 struct MixTables {
     const MixEdge* edge;   // [E+1]
     const MixBin* bin;     // [E]
@@ -52,6 +76,10 @@ struct MixTables {
     const MixModeHM* hm;   // [E+1][6] (higher-mode references)
     const float2* hm_base;  // [E+1][3]: -1 where h0 = 0, else sum u - 1 of the stored u
     double amp_eps0;       // relative rounding of the reference's float32 amplitude factor
+    const XDer* xder;      // extended precision: the reference's float64 constants
+    const XEdge* xedge;    // [E+1]
+    const XWeight* xw;     // [E+1]
+    double xsumA, xsumB;   // 4 sum Re A0, 4 sum B0
 };
 
 struct PrepItem {
@@ -117,6 +145,9 @@ HetKernel het_kernel_f64(int G, int block);
 HetKernel het_kernel_mixed(int G, int block);
 HetKernel het_kernel_mixed_hm(int G, int block);
 HetKernel het_kernel_mixed_pt(int G, int block);
+HetKernel het_kernel_x(int G, int block);
+cudaError_t prepare_x_tables(mbh_ref* R, cudaStream_t st);
+void free_x_tables(mbh_ref* R);
 mbh_status het_launch_fused_pt(const mbh_ref* const* refs, int n_ens, int64_t M, const mbh_het_config& cfg,
                                const void* pt_dev, int half, cudaStream_t st);
 
@@ -191,5 +222,9 @@ struct mbh_ref {
     double* mix_sums = nullptr;    // device [2]
     mbh::MixModeHM* mix_hm = nullptr;   // higher-mode references: [E+1][6]
     float2* mix_hm_base = nullptr;      // [E+1][3]
+    mbh::XDer* x_der = nullptr;         // extended-precision tables ((2,2) references)
+    mbh::XEdge* x_edge = nullptr;
+    mbh::XWeight* x_w = nullptr;
+    double* x_sums = nullptr;
     mbh::MixTables mix{};
 };

@@ -1050,6 +1050,7 @@ void mbh::free_ref_tables(mbh_ref* R)
     cudaFree(R->mix_sums);
     if (R->mix_hm) cudaFree(R->mix_hm);
     if (R->mix_hm_base) cudaFree(R->mix_hm_base);
+    free_x_tables(R);
 }
 
 

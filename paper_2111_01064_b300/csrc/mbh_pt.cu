@@ -655,7 +655,9 @@ extern "C" mbh_status mbh_pt_create_multi(const mbh_pt_opts* o, const mbh_ref* c
     if ((int64_t)n_ens * o->ntemps * o->walkers > 0x3fffffff) return fail(MBH_EINVAL, "ensemble too large");
     for (int64_t t = 0; t < (int64_t)n_ens * o->ntemps; ++t)
         if (!(betas_host[t] >= 0.0) || !std::isfinite(betas_host[t])) return fail(MBH_EINVAL, "betas must be finite and >= 0");
-    if (o->precision != MBH_FP64 && o->precision != MBH_MIXED) return fail(MBH_EINVAL, "unknown precision");
+    if (o->precision != MBH_FP64 && o->precision != MBH_MIXED && o->precision != MBH_MIXED_F32)
+        return fail(MBH_EINVAL, "unknown precision");
+    if (data && o->precision == MBH_MIXED_F32) return fail(MBH_EINVAL, "MBH_MIXED_F32 is a heterodyne precision");
     const uint32_t modes = o->modes ? o->modes : 1u;
     if (data)
         if (mbh_status s = check_modes(modes, o->precision)) return s;
@@ -699,7 +701,7 @@ extern "C" mbh_status mbh_pt_create_multi(const mbh_pt_opts* o, const mbh_ref* c
     // about one wave of the register-capped 224-thread blocks (28 warps per SM): 16 threads per
     // walker up to 12288 moving walkers, 8 above (threads per walker fixes the summation order,
     // so a sampler keeps the one it was created with)
-    if (!o->het_config.threads_per_walker && P->precision == MBH_MIXED) P->cfg.threads_per_walker = M <= 12288 ? 16 : 8;
+    if (!o->het_config.threads_per_walker && P->precision == MBH_MIXED_F32) P->cfg.threads_per_walker = M <= 12288 ? 16 : 8;
     const int64_t NT = (int64_t)n_ens * A.T;
     cudaError_t e = cudaSuccess;
     auto alloc = [&](void** p, size_t bytes) {
@@ -752,7 +754,7 @@ extern "C" mbh_status mbh_pt_create_multi(const mbh_pt_opts* o, const mbh_ref* c
     if (e == cudaSuccess) e = cudaMemsetAsync(A.done, 0, sizeof(unsigned int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(A.perm, 0, sizeof(int32_t) * N, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(P->A_dev, &A, sizeof(PtArgs), cudaMemcpyHostToDevice, st);
-    P->fuse_ok = o->precision == MBH_MIXED && !o->no_fuse;
+    P->fuse_ok = o->precision == MBH_MIXED_F32 && !o->no_fuse;   // the fused half step is the float32-ratio kernel
     P->fused = P->fuse_ok && refs != nullptr && all22;
     if (e != cudaSuccess) {
         free_pt(P);

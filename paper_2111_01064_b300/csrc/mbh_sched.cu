@@ -82,25 +82,30 @@ mbh_status make_plan(const mbh_ref* const* refs, const int64_t* offsets, int32_t
                      const mbh_het_config& cfg, HetPlan& plan)
 {
     if (mbh_status s = check_cfg(cfg)) return s;
-    if (prec != MBH_FP64 && prec != MBH_MIXED) return fail(MBH_EINVAL, "unknown precision %d", (int)prec);
+    if (prec != MBH_FP64 && prec != MBH_MIXED && prec != MBH_MIXED_F32)
+        return fail(MBH_EINVAL, "unknown precision %d", (int)prec);
     const int64_t W = offsets[n_src];
-    // kernel per source: float64 (any modes), mixed (2,2), or mixed with higher modes;
-    // a launch holds sources of one kernel.  block 0 takes each kernel's default block.
+    // kernel per source: float64 (any modes); MBH_MIXED (2,2): the extended-precision kernel;
+    // MBH_MIXED_F32 (2,2): the float32-ratio kernel; mixed with higher modes: the float32-ratio
+    // higher-mode kernel.  A launch holds sources of one kernel; block 0 takes each kernel's
+    // default block.
     for (int group = 0; group < 2; ++group) {
         std::vector<int32_t> order;
         for (int32_t s = 0; s < n_src; ++s) {
-            const bool hm = prec == MBH_MIXED && refs[s]->modes != 1u;
+            const bool hm = prec != MBH_FP64 && refs[s]->modes != 1u;
             if ((group == 1) == hm) order.push_back(s);
         }
         if (order.empty()) continue;
-        const bool mixed22 = prec == MBH_MIXED && group == 0;
+        const bool f32_22 = prec == MBH_MIXED_F32 && group == 0;
+        const bool x22 = prec == MBH_MIXED && group == 0;
         int64_t wg = 0;
         for (int32_t s : order) wg += offsets[s + 1] - offsets[s];
         const int block = cfg.block ? cfg.block
-                                    : (mixed22 ? default_block_mixed(cfg.threads_per_walker, wg) : kDefaultBlock);
+                                    : (f32_22 ? default_block_mixed(cfg.threads_per_walker, wg) : kDefaultBlock);
         const int wpb = block / cfg.threads_per_walker;
         const HetKernel kernel = prec == MBH_FP64 ? het_kernel_f64(cfg.threads_per_walker, block)
-                                 : mixed22        ? het_kernel_mixed(cfg.threads_per_walker, block)
+                                 : x22            ? het_kernel_x(cfg.threads_per_walker, block)
+                                 : f32_22         ? het_kernel_mixed(cfg.threads_per_walker, block)
                                                   : het_kernel_mixed_hm(cfg.threads_per_walker, block);
         if (!kernel.launch) return fail(MBH_EINVAL, "no kernel for this configuration");
         if (cfg.persistent)   // largest bin counts first
@@ -176,9 +181,10 @@ mbh_status run_plan(const HetPlan& plan, cudaStream_t st)
 bool plan_has_kernels(const mbh_ref* const* refs, int32_t n_src, mbh_precision prec, const mbh_het_config& c)
 {
     for (int32_t s = 0; s < n_src; ++s) {
-        const HetKernel k = prec == MBH_FP64          ? het_kernel_f64(c.threads_per_walker, c.block)
-                            : refs[s]->modes == 1u ? het_kernel_mixed(c.threads_per_walker, c.block)
-                                                   : het_kernel_mixed_hm(c.threads_per_walker, c.block);
+        const HetKernel k = prec == MBH_FP64    ? het_kernel_f64(c.threads_per_walker, c.block)
+                            : refs[s]->modes != 1u ? het_kernel_mixed_hm(c.threads_per_walker, c.block)
+                            : prec == MBH_MIXED    ? het_kernel_x(c.threads_per_walker, c.block)
+                                                   : het_kernel_mixed(c.threads_per_walker, c.block);
         if (!k.launch) return false;
     }
     return true;

@@ -258,7 +258,7 @@ extern "C" mbh_status mbh_server_create(const mbh_server_opts* opts, mbh_server*
     *out = nullptr;
     if (opts->max_batch_walkers < 1 || opts->max_inflight_batches < 1 || opts->max_queue < 1)
         return fail(MBH_EINVAL, "max_batch_walkers, max_inflight_batches and max_queue must be >= 1");
-    if (opts->precision != MBH_FP64 && opts->precision != MBH_MIXED)
+    if (opts->precision != MBH_FP64 && opts->precision != MBH_MIXED && opts->precision != MBH_MIXED_F32)
         return fail(MBH_EINVAL, "unknown precision");
     if (mbh_status s = check_device()) return s;
     auto S = std::make_unique<mbh_server>();

@@ -16,8 +16,9 @@ import torch
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libmbhlike.so")
 
-FP64, MIXED = 0, 1
-_PREC = {"fp64": FP64, "mixed": MIXED, FP64: FP64, MIXED: MIXED}
+FP64, MIXED, MIXED_F32 = 0, 1, 2
+_PREC = {"fp64": FP64, "mixed": MIXED, "mixed_f32": MIXED_F32, FP64: FP64, MIXED: MIXED,
+         MIXED_F32: MIXED_F32}
 STATUS = {0: "MBH_OK", 1: "MBH_EINVAL", 2: "MBH_ENOMEM", 3: "MBH_ECUDA", 4: "MBH_ETIMEOUT",
           5: "MBH_EBUSY"}
 
