@@ -6,11 +6,17 @@
 One step = one heterodyned-likelihood batch (Sec. II B; the Module 2/3 workload of
 Sec. III B-C): 8 temperatures x 2048 walkers = 16384 templates perturbed
 1e-3..1e-1 per parameter around a reference on the 1-yr, 15-s grid
-(1,051,920 frequencies), 256 log-spaced bins x 3 channels, mixed precision.
-`value` = heterodyned lnL evaluations per second over all ranks.  The same run
-also measures the direct likelihood (Sec. II, Eqs. 2-3; Sec. III A): the stored-
-template streaming reduction against the HBM roofline and the fused
-generate-and-reduce pass over the 4096-template brute-force batch.
+(1,051,920 frequencies), 256 log-spaced bins x 3 channels, in the library's
+mixed precision (MBH_MIXED: edge values formed relative to the reference in
+double-float, |dlnL| <= 1e-3 against the float64 oracle).  `value` = heterodyned
+lnL evaluations per second over all ranks.  The same run reports the float64
+and float32-ratio heterodyne kernels on the same batch, an SNR-1000 variant of
+the batch, the 30-day workload 0 (direct and heterodyne, with the oracle timed
+on one core and on all cores), the direct likelihood (Sec. II, Eqs. 2-3;
+Sec. III A: the stored-template streaming reduction against the HBM roofline
+and the fused generate-and-reduce pass over the 4096-template brute-force
+batch, with the oracle's direct likelihood as its CPU baseline), the uneven
+multi-source batch and the serving loop, each with |dlnL| against the oracle.
 
 Inputs are synthetic and seeded (mbh_inputs): the LDC-1A data are not available,
 so an injection with SNR drawn in 100-1000, in Gaussian noise from the analytic
@@ -67,26 +73,35 @@ def _measured_peaks():
     return {"hbm_gbs": 6400.0, "sm_max_mhz": 2032.0}, "fallback"
 
 
-# FP64 peak of B300: 148 SMs x 2 DFMA per SM per clock (measured 566 G DFMA/s at 1935 MHz,
-# i.e. 1.98 per SM per clock) x 2 flop x max SM clock.
-def fp64_peak_gflops(sm_mhz: float) -> float:
-    return 148 * 2 * 2 * sm_mhz * 1e-3  # noqa: E501  (reported for the float64 kernel)
+def sm_count() -> int:
+    import torch
+    return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
 
 
-# The mixed heterodyne kernel is bound by the float32 (FMA) pipe: per edge evaluation it
-# issues 639 FMA-pipe thread instructions (double-float phase chain, float32 response,
-# ratio and contraction), counted by ncu on het_mixed_kernel_capped<8,224>, the default launch
-# at 16384 walkers (FMA-pipe utilisation x peak x elapsed cycles / edges).  Peak: 148 SMs x 128
-# FP32 lanes x SM clock.
-HET_MIXED_FMA_INST_PER_EDGE = 639
-HET_KERNEL = "het_mixed_kernel_capped<8,224>"
-HET_MIXED_DRAM_BYTES = 1.593600e6          # read + write per 16384-walker launch (ncu)
+# FP64 pipe of B300: 2 DFMA per SM per clock (measured 566 G DFMA/s at 1935 MHz on 148 SMs).
+def fp64_peak_tinst(sm_mhz: float) -> float:
+    return sm_count() * 2 * sm_mhz * 1e-6
+
+
+# FP32 (FMA) pipe: 128 lanes per SM per clock.
+def fma_peak_tinst(sm_mhz: float) -> float:
+    return sm_count() * 128 * sm_mhz * 1e-6
+
+
+# Work per unit of the ALU-bound kernels, counted by ncu (sm__inst_executed_pipe_fma /
+# _fp64 thread instructions of one launch divided by the units it processed; the profile
+# summaries name the launches):
+#  - het_x_kernel<4,128> (MBH_MIXED heterodyne): FMA-pipe instructions per edge evaluation
+#    (double-float phase/time differences, orbit, response, ratio, per-edge contraction);
+#  - direct_fused_mixed_kernel<8>: FMA-pipe instructions per (template, grid point);
+#  - direct_fused_f64_kernel<4>: FP64-pipe instructions per (template, grid point).
+HET_KERNEL = "het_x_kernel<4,128>"
+HET_X_FMA_INST_PER_EDGE = 2780.0
+HET_X_DRAM_BYTES = 1.62e6                  # read + write per 16384-walker launch (ncu)
+FUSED_MIXED_FMA_INST_PER_POINT = 0.0
+FUSED_F64_DFMA_INST_PER_POINT = 0.0
 STORED_DATA_BYTES = 75.74e6                # data pairs, read once per launch (ncu: 883.66 MB
 STORED_BYTES_PER_TEMPLATE = 50.4945e6      # for 16 templates = 75.74 MB + 16 x 50.49 MB)
-
-
-def fma_peak_tinst(sm_mhz: float) -> float:
-    return 148 * 128 * sm_mhz * 1e-6
 
 
 def max_over_ranks(value: float, device=None) -> float:
@@ -208,8 +223,8 @@ def run_ours(args) -> dict | None:
     offs = [0, nw]
     if args.only == "direct":
         return run_direct_only(args, M, WL, g, src, rank, dev, stream, peaks, peak_src)
-    if args.only == "fused":
-        return run_fused_only(args, M, WL, g, src, rank, dev, stream)
+    if args.only in ("fused", "fused64"):
+        return run_fused_only(args, M, WL, g, src, rank, dev, stream, "fp64" if args.only == "fused64" else "mixed")
     if args.only == "sampler":   # profiling case: sampler iterations alone
         r = run_sampler(M, WL, g, src, ref, stream, 1.0, iters=args.steps)
         return {"profile_case": "sampler", **r} if rank == 0 else None
@@ -268,6 +283,10 @@ def run_ours(args) -> dict | None:
     fp64_rate = nw / (statistics.median(f64_ms) * 1e-3)
     scale = 0.5 * (src.data.dd + np.abs(fp64_out[2]) + 2 * np.abs(fp64_out[1]))
     dmix = np.abs(mixed_out[0] - fp64_out[0])
+    # ---- float32-ratio heterodyne kernel on the same batch (MBH_MIXED_F32) ----
+    f32_ms = _time_launches(lambda: het_step("mixed_f32"), stream, 20, flush)
+    f32_out = out.cpu().numpy().copy()
+    f32_rate = nw / (f32_ms * 1e-3)
 
     # ---- e2e: host theta in, host lnL out, through the public API ----
     # Each step copies its theta from pinned host memory into the buffer of a captured
@@ -318,6 +337,9 @@ def run_ours(args) -> dict | None:
     del lanes
     e2e_value = weak_scaling_rate(ws, nw, args.steps, e2e_ms)
     e2e_serial_value = weak_scaling_rate(ws, nw, args.steps, e2e_ms_serial)
+
+    # ---- the same batch with its source at SNR 1000 ----
+    snr1000 = run_snr1000(M, WL, g, stream, flush) if args.only == "all" else None
 
     # ---- direct likelihood: stored templates (HBM roofline) ----
     del flush
@@ -386,24 +408,29 @@ def run_ours(args) -> dict | None:
     # ---- uneven multi-source batch: autotuned, one launch, CUDA-graph replay ----
     uneven = run_uneven(M, WL, stream) if args.only == "all" else None
     serving = run_serving(M, WL, cfg=None) if args.only == "all" else None
+    workload0 = run_workload0(M, WL, stream) if args.only == "all" else None
 
     clk.__exit__(None, None, None)
     clocks = clk.summary()
-    sm_for_peak = peaks.get("sm_max_mhz", 2032.0)
+    sm_for_peak = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2032.0)
     fma_peak = fma_peak_tinst(sm_for_peak)
+    fp64_peak = fp64_peak_tinst(sm_for_peak)
     E = ref.bins
-    inst = nw * (E + 1) * HET_MIXED_FMA_INST_PER_EDGE
+    inst = nw * (E + 1) * HET_X_FMA_INST_PER_EDGE
     achieved = inst / (ms_per_step * 1e-3) / 1e12
-    # DRAM traffic per launch from ncu captures (profiles/het_mixed_kernel_capped_16384w_256b_1yr.md,
-    # profiles/direct_stored_df_kernel_16tpl_1yr.md; the stored-template launch scaled from
-    # 16 to N_STORED templates by the templates processed)
-    roof_traffic = HET_MIXED_DRAM_BYTES if nw == N_WALKERS else None
+    # DRAM traffic per launch from ncu captures (the heterodyne launch at this batch; the
+    # stored-template launch scaled from 16 to N_STORED templates by the templates processed)
+    roof_traffic = HET_X_DRAM_BYTES if nw == N_WALKERS else None
     stored_traffic = STORED_DATA_BYTES + N_STORED * STORED_BYTES_PER_TEMPLATE
+    pts_mixed = N_DIRECT * n   # template points (one frequency of one template, 3 channels)
+    fused_mixed_tinst = FUSED_MIXED_FMA_INST_PER_POINT * pts_mixed / (fused_mixed_ms * 1e-3) / 1e12
+    fused_f64_tinst = FUSED_F64_DFMA_INST_PER_POINT * n64 * n / (fused_fp64_ms * 1e-3) / 1e12
 
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64 phases + f32 response (mixed)",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32x2 (double-float on the FP32 pipe) with f64 per-walker setup (MBH_MIXED)",
         "data": "synthetic (seeded injection in Gaussian noise from the analytic A/E/T PSD; LDC-1A "
                 "not available)",
         "config": {"workload": WORKLOAD, "walkers": nw, "temperatures": W_TEMPS,
@@ -416,11 +443,16 @@ def run_ours(args) -> dict | None:
         "p99_ms": float(np.percentile(step_ms, 99)),
         "wall_ms_per_step_incl_flush": t_wall * 1e3 / args.steps,
         "fp64_het": {"value": fp64_rate, "unit": UNIT, "speedup_mixed_over_fp64": value / ws / fp64_rate},
+        "mixed_f32_het": {"value": f32_rate, "unit": UNIT, "ms": f32_ms,
+                          "note": "float32-ratio kernel (MBH_MIXED_F32): faster, |dlnL| grows with <h|h>",
+                          "accuracy_vs_fp64_kernel": _acc(f32_out[0] - fp64_out[0])},
         "accuracy_mixed_vs_fp64_kernel": {
             "abs_dlnL_p50": float(np.median(dmix)), "abs_dlnL_p99": float(np.quantile(dmix, 0.99)),
             "abs_dlnL_max": float(dmix.max()), "frac_le_1e-3": float(np.mean(dmix <= 1e-3)),
             "rel_to_terms_max": float((dmix / scale).max()),
             "lnL_range": [float(fp64_out[0].min()), float(fp64_out[0].max())]},
+        "snr1000": snr1000,
+        "workload0": workload0,
         "direct": {
             "stored_fp64": {"templates": N_STORED, "ms": st_ms, "GB_per_s": stored_gbs,
                             "frac_of_hbm": stored_gbs / peaks["hbm_gbs"]},
@@ -441,8 +473,21 @@ def run_ours(args) -> dict | None:
         "roofline": {"bound": "alu", "pipe": "fp32 (FMA pipe)", "achieved": achieved, "peak": fma_peak,
                      "unit": "T fp32-pipe inst/s", "frac": achieved / fma_peak, "traffic": roof_traffic,
                      "kernel": HET_KERNEL,
-                     "peak_note": f"148 SM x 128 FP32 lanes x {sm_for_peak:.0f} MHz",
-                     "inst_per_edge": HET_MIXED_FMA_INST_PER_EDGE},
+                     "peak_note": f"{sm_count()} SM x 128 FP32 lanes x {sm_for_peak:.0f} MHz (median SM clock "
+                                  "sampled during the run)",
+                     "inst_per_edge": HET_X_FMA_INST_PER_EDGE,
+                     "ps_per_edge_evaluation": ms_per_step * 1e9 / (nw * (E + 1))},
+        "roofline_fused_mixed": {"bound": "alu", "pipe": "fp32 (FMA pipe)", "achieved": fused_mixed_tinst,
+                                 "peak": fma_peak, "unit": "T fp32-pipe inst/s",
+                                 "frac": fused_mixed_tinst / fma_peak, "traffic": None,
+                                 "kernel": "direct_fused_mixed_kernel<8>",
+                                 "inst_per_template_point": FUSED_MIXED_FMA_INST_PER_POINT},
+        "roofline_fused_fp64": {"bound": "alu", "pipe": "fp64", "achieved": fused_f64_tinst,
+                                "peak": fp64_peak, "unit": "T fp64-pipe inst/s",
+                                "frac": fused_f64_tinst / fp64_peak, "traffic": None,
+                                "kernel": "direct_fused_f64_kernel<4>",
+                                "inst_per_template_point": FUSED_F64_DFMA_INST_PER_POINT,
+                                "peak_note": f"{sm_count()} SM x 2 DFMA x {sm_for_peak:.0f} MHz"},
         "roofline_direct_stored": {"bound": "hbm", "achieved": stored_gbs, "peak": peaks["hbm_gbs"],
                                    "unit": "GB/s", "frac": stored_gbs / peaks["hbm_gbs"],
                                    "traffic": stored_traffic, "kernel": "direct_stored_df_kernel<4,4>",
@@ -457,10 +502,182 @@ def run_ours(args) -> dict | None:
         "clocks": clocks,
         "_mixed_lnl": mixed_out[0],
         "_fp64_lnl": fp64_out[0],
+        "_f32_lnl": f32_out[0],
+        "_direct_fused_mixed": dfused.cpu().numpy()[0],
     }
     if ws > 1:
         torch.distributed.barrier()
     return res if rank == 0 else None
+
+
+def _acc(d) -> dict:
+    d = np.abs(np.asarray(d))
+    return {"walkers": int(d.size), "abs_dlnL_p50": float(np.median(d)),
+            "abs_dlnL_p99": float(np.quantile(d, 0.99)), "abs_dlnL_max": float(d.max()),
+            "frac_le_1e-3": float(np.mean(d <= 1e-3))}
+
+
+def _time_launches(fn, stream, reps: int, flush=None) -> float:
+    """Median per-launch time (ms) with CUDA events on `stream`, L2 flushed between launches
+    (outside the events) when a flush buffer is given."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(reps):
+        if flush is not None:
+            flush_l2(flush)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    return statistics.median(ms)
+
+
+def run_snr1000(M, WL, g, stream, flush, reps: int = 20) -> dict:
+    """Workload 2 with its source made louder, SNR 1000 (the top of the workloads' range),
+    same 16384 walkers (1e-3..1e-1) and 256 bins: MBH_MIXED and the float32-ratio kernel
+    timed (L2 flushed between launches), |dlnL| against the float64 kernel on every walker
+    and against the oracle on 256 evenly spaced walkers."""
+    import torch
+    from oracle import oracle as O
+    th_raw, _ = WL.injection(2, g)
+    z = I.noise_normals(I.rng(2, 100), g["n"])
+    src = WL.build_source(g, th_raw, 1000.0, z)
+    ref = M.het_prepare_reference(src.data, src.theta_inj, N_BINS)
+    nw = N_WALKERS
+    theta = WL.to_dev(WL.walkers(src.theta_inj, nw, 2))
+    out = torch.empty((3, nw), dtype=torch.float64, device="cuda")
+    res = {"snr": 1000.0, "walkers": nw, "bins": ref.bins}
+    outs = {}
+    for prec, n in (("mixed", reps), ("mixed_f32", reps), ("fp64", 3)):
+        ms = _time_launches(lambda: M.het_loglike_batch([ref], [0, nw], theta, prec, out=out), stream, n, flush)
+        res[prec] = {"ms": ms, "lnL_evals_per_s": nw / (ms * 1e-3)}
+        outs[prec] = out.cpu().numpy().copy()
+    res["accuracy_mixed_vs_fp64_kernel"] = _acc(outs["mixed"][0] - outs["fp64"][0])
+    res["accuracy_mixed_f32_vs_fp64_kernel"] = _acc(outs["mixed_f32"][0] - outs["fp64"][0])
+    S = O.psd(O.freqs(g))
+    th_o = I.with_distance(th_raw, O.snr_distance(th_raw, g, 1000.0, S))
+    d_o, _ = O.make_data(th_o, g, z, S)
+    ref_o = O.het_prepare(th_o, g, d_o, S, N_BINS)
+    idx = np.linspace(0, nw - 1, 256).astype(int)
+    wo = np.ascontiguousarray(WL.walkers(th_o, nw, 2)[:, idx])
+    ora = O.het_loglike(wo, ref_o)
+    res["accuracy_mixed_vs_oracle"] = _acc(outs["mixed"][0, idx] - ora[0])
+    res["accuracy_mixed_f32_vs_oracle"] = _acc(outs["mixed_f32"][0, idx] - ora[0])
+    res["accuracy_fp64_vs_oracle"] = _acc(outs["fp64"][0, idx] - ora[0])
+    res["speedup_mixed_over_fp64"] = res["mixed"]["lnL_evals_per_s"] / res["fp64"]["lnL_evals_per_s"]
+    return res
+
+
+def _oracle_child(kind: str, threads: int) -> dict:
+    """Run the oracle timing `kind` in a fresh process with OMP_NUM_THREADS = threads (the
+    oracle's OpenMP team is fixed when it loads)."""
+    env = dict(os.environ, OMP_NUM_THREADS=str(threads))
+    p = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-time", kind],
+                       env=env, capture_output=True, text=True, timeout=900, cwd=ROOT)
+    if p.returncode != 0:
+        raise RuntimeError(f"oracle timing {kind} failed: {p.stderr[-800:]}")
+    return json.loads(p.stdout.strip().splitlines()[-1])
+
+
+def oracle_time(kind: str) -> dict:
+    """CPU side of the benchmark (child process, no GPU): the oracle, as it stands, timed with
+    time.perf_counter on the host cores its OpenMP team was given.
+      wl0:     workload 0 (30-day record, SNR-392 injection in noise, 64 walkers at 1e-3):
+               direct lnL of the 64 walkers and the 128-bin heterodyne (prepare not timed);
+      direct:  the direct lnL on the 1-yr grid for as many templates of the 4096-template
+               brute-force batch as there are threads (data built first, not timed)."""
+    from oracle import oracle as O
+    th_out = {"threads": O.threads()}
+    if kind == "wl0":
+        g = I.grid_month()
+        th_raw, snr = I.draw_source(I.rng(0, 0), g["t_obs"])
+        S = O.psd(O.freqs(g))
+        th = I.with_distance(th_raw, O.snr_distance(th_raw, g, snr, S))
+        z = I.noise_normals(I.rng(0, 100), g["n"])
+        d, _ = O.make_data(th, g, z, S)
+        ref = O.het_prepare(th, g, d, S, 128)
+        from paper_2111_01064_b300 import workloads as WL
+        wk = WL.walkers(th, 64, 0, lo=1e-3, hi=1e-3)
+        t0 = time.perf_counter()
+        dr = O.direct(wk, g, d, S)
+        t1 = time.perf_counter()
+        reps = 0
+        while True:
+            het = O.het_loglike(wk, ref)
+            reps += 1
+            if time.perf_counter() - t1 > 0.5:
+                break
+        t2 = time.perf_counter()
+        th_out.update({"walkers": 64, "direct_s": t1 - t0, "het_s": (t2 - t1) / reps,
+                       "lnl_direct": dr[0].tolist(), "lnl_het": het[0].tolist()})
+    elif kind == "direct":
+        g = I.grid_year()
+        th_raw, snr = I.draw_source(I.rng(2, 0), g["t_obs"])
+        S = O.psd(O.freqs(g))
+        th = I.with_distance(th_raw, O.snr_distance(th_raw, g, snr, S))
+        z = I.noise_normals(I.rng(2, 100), g["n"])
+        d, _ = O.make_data(th, g, z, S)
+        k = max(1, O.threads())
+        th_dir = np.ascontiguousarray(I.draw_prior_batch(I.rng(1, 300), N_DIRECT, g["t_obs"])[:, :k])
+        t0 = time.perf_counter()
+        out = O.direct(th_dir, g, d, S)
+        dt = time.perf_counter() - t0
+        th_out.update({"templates": k, "seconds": dt, "templates_per_s": k / dt, "lnl": out[0].tolist()})
+    else:
+        raise ValueError(kind)
+    return th_out
+
+
+def run_workload0(M, WL, stream, reps: int = 20) -> dict:
+    """Workload 0: the 30-day record (16384 bins from ~1e-4 Hz), one injection in noise, 64
+    walkers at 1e-3 from it; direct lnL (float64, mixed) and the 128-bin heterodyne (float64,
+    MBH_MIXED) on the GPU, against the oracle timed on one host core and on all of them."""
+    import torch
+    g = I.grid_month()
+    src = WL.source_for(0, g)
+    ref = M.het_prepare_reference(src.data, src.theta_inj, 128)
+    W = 64
+    th = WL.to_dev(WL.walkers(src.theta_inj, W, 0, lo=1e-3, hi=1e-3))
+    out = torch.empty((3, W), dtype=torch.float64, device="cuda")
+    res = {"grid_points": int(g["n"]), "walkers": W, "bins": ref.bins, "snr": float(src.snr)}
+    outs = {}
+    for name, fn in (("direct_fp64", lambda: M.direct_loglike_batch(src.data, th, "fp64", out=out)),
+                     ("direct_mixed", lambda: M.direct_loglike_batch(src.data, th, "mixed", out=out)),
+                     ("het_fp64", lambda: M.het_loglike_batch([ref], [0, W], th, "fp64", out=out)),
+                     ("het_mixed", lambda: M.het_loglike_batch([ref], [0, W], th, "mixed", out=out))):
+        ms = _time_launches(fn, stream, reps)
+        res[name] = {"ms": ms, "lnL_evals_per_s": W / (ms * 1e-3)}
+        outs[name] = out.cpu().numpy()[0].copy()
+    one = _oracle_child("wl0", 1)
+    allc = _oracle_child("wl0", os.cpu_count() or 1)
+    res["oracle_single_core"] = {"cores": one["threads"], "direct_lnL_per_s": W / one["direct_s"],
+                                 "het_lnL_per_s": W / one["het_s"]}
+    res["oracle_all_cores"] = {"cores": allc["threads"], "direct_lnL_per_s": W / allc["direct_s"],
+                               "het_lnL_per_s": W / allc["het_s"]}
+    od, oh = np.array(allc["lnl_direct"]), np.array(allc["lnl_het"])
+    res["accuracy_vs_oracle"] = {"direct_fp64": _acc(outs["direct_fp64"] - od),
+                                 "direct_mixed": _acc(outs["direct_mixed"] - od),
+                                 "het_fp64": _acc(outs["het_fp64"] - oh), "het_mixed": _acc(outs["het_mixed"] - oh)}
+    return res
+
+
+def direct_cpu_baseline() -> dict:
+    """The oracle's direct likelihood on the 1-yr grid (workload 1): one template on one core and
+    one template per core on all cores, extrapolated to the 4096-template batch."""
+    one = _oracle_child("direct", 1)
+    allc = _oracle_child("direct", os.cpu_count() or 1)
+    return {"kind": "oracle", "unit": "templates/s", "single_core": {"cores": 1, "value": one["templates_per_s"]},
+            "all_cores": {"cores": allc["threads"], "value": allc["templates_per_s"]},
+            "value": allc["templates_per_s"], "cores": allc["threads"],
+            "sample": f"{allc['templates']} templates of the 4096-template batch on {allc['threads']} "
+                      f"threads ({allc['seconds']:.1f} s) and 1 on one core ({one['seconds']:.1f} s); "
+                      "4096 templates extrapolated at that rate",
+            "extrapolated_4096_templates_s": N_DIRECT / allc["templates_per_s"],
+            "_lnl": allc["lnl"]}
 
 
 def run_higher_modes(M, WL, g, stream, reps: int = 5) -> dict:
@@ -534,8 +751,8 @@ def run_sampler(M, WL, g, src, ref, stream, het_rate: float, iters: int = 20) ->
     x = WL.to_dev(I.draw_pt_ensemble(I.rng(2, 300), x0, T, W, scale, lo, hi))
     betas = I.pt_betas(T, 100.0)
     res = {}
-    for name, cfg in (("default", None), ("threads_per_walker_8_block_128", M.het_config(8, 128, 0))):
-        pt = M.PTSampler(x, betas, lo, hi, ref=ref, walkers=W, seed=1, precision="mixed", cfg=cfg)
+    for name, prec in (("mixed", "mixed"), ("mixed_f32_fused", "mixed_f32")):
+        pt = M.PTSampler(x, betas, lo, hi, ref=ref, walkers=W, seed=1, precision=prec)
         pt.run(3)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -560,7 +777,7 @@ def run_sampler(M, WL, g, src, ref, stream, het_rate: float, iters: int = 20) ->
     refs = [ref] + [M.het_prepare_reference(src.data, t_, ref.bins) for t_ in ths[1:]]
     xs = [I.draw_pt_ensemble(I.rng(2, 310 + e), x0, T, W, scale, lo, hi) for e in range(n_ens)]
     pt = M.PTSampler(WL.to_dev(np.concatenate(xs, 1)), betas, lo, hi, refs=refs, walkers=W, seed=1,
-                     precision="mixed")
+                     precision="mixed_f32")
     pt.run(3)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -570,10 +787,11 @@ def run_sampler(M, WL, g, src, ref, stream, het_rate: float, iters: int = 20) ->
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / iters
     pt.close()
-    res["four_ensembles"] = {"ensembles": n_ens, "walkers": n_ens * T * W, "ms_per_iteration": ms,
+    res["four_ensembles_mixed_f32_fused"] = {"ensembles": n_ens, "walkers": n_ens * T * W, "ms_per_iteration": ms,
                              "iterations_per_s": 1e3 / ms, "lnL_evals_per_s": n_ens * T * W / (ms * 1e-3)}
-    return {"temperatures": T, "walkers_per_temperature": W, "bins": ref.bins,
-            "launches_per_iteration": 5, "fused_half_steps": True, "graph": True, **res}
+    return {"temperatures": T, "walkers_per_temperature": W, "bins": ref.bins, "graph": True,
+            "note": "mixed: proposal, likelihood (MBH_MIXED kernel) and acceptance as separate launches; "
+                    "mixed_f32: each half step one fused float32-ratio heterodyne launch", **res}
 
 
 def run_uneven(M, WL, stream, reps: int = 20) -> dict:
@@ -603,13 +821,49 @@ def run_uneven(M, WL, stream, reps: int = 20) -> dict:
     graph = M.HetGraph(ub.refs, ub.offsets, th, out, "mixed", cfg)
     ms_graph = timed(graph.launch)
     graph.close()
+    got = out.cpu().numpy()
     edges = int(np.sum(ub.walkers * (np.array([r.bins for r in ub.refs]) + 1)))
+    # |dlnL| against the oracle: 4 evenly spaced walkers of every source, each source rebuilt on
+    # the oracle side from the same draws
+    errs = _oracle_source_errors(WL, ub, 3, got[0], per_source=4, lo=1e-5, hi=1e-3)
     return {"sources": len(ub.refs), "walkers": W, "edge_evaluations": edges,
             "bins_range": [int(ub.bins.min()), int(ub.bins.max())],
             "walkers_range": [int(ub.walkers.min()), int(ub.walkers.max())],
             "autotuned": cfg.as_dict(), "ms_default_config": ms_default, "ms_autotuned": ms_tuned,
             "ms_graph_replay": ms_graph, "evals_per_s_graph": W / (ms_graph * 1e-3),
-            "evals_per_s_default": W / (ms_default * 1e-3)}
+            "evals_per_s_default": W / (ms_default * 1e-3),
+            "accuracy_vs_oracle": _acc(errs)}
+
+
+def _oracle_sources(ub, workload: int, sources) -> dict:
+    """The oracle's own copy of the listed sources of an uneven batch (30-day grid): injection
+    with its distance, data in noise and the reference with the source's bin count."""
+    from oracle import oracle as O
+    g = I.grid_month()
+    S = O.psd(O.freqs(g))
+    out = {}
+    for s in sources:
+        th_raw, snr = I.draw_source(I.rng(workload, s), g["t_obs"])
+        th0 = I.with_distance(th_raw, O.snr_distance(th_raw, g, snr, S))
+        z = I.noise_normals(I.rng(workload, 100 + s), g["n"])
+        d, _ = O.make_data(th0, g, z, S)
+        out[s] = (th0, O.het_prepare(th0, g, d, S, int(ub.bins[s])))
+    return out
+
+
+def _oracle_source_errors(WL, ub, workload, lnl, per_source, lo, hi) -> np.ndarray:
+    """|dlnL| of the batch's lnL (walkers grouped by source) against the oracle on
+    per_source evenly spaced walkers of every source."""
+    from oracle import oracle as O
+    srcs = _oracle_sources(ub, workload, range(len(ub.refs)))
+    errs = []
+    for s, (th0, ref_o) in srcs.items():
+        a, b = int(ub.offsets[s]), int(ub.offsets[s + 1])
+        wo = WL.walkers(th0, b - a, workload, s, lo, hi)
+        idx = np.unique(np.linspace(0, b - a - 1, per_source).astype(int))
+        ora = O.het_loglike(np.ascontiguousarray(wo[:, idx]), ref_o)
+        errs.append(np.abs(lnl[a + idx] - ora[0]))
+    return np.concatenate(errs)
 
 
 def run_serving(M, WL, cfg=None, n_sources: int = 32, seconds: float = 1.0,
@@ -661,13 +915,14 @@ def run_serving(M, WL, cfg=None, n_sources: int = 32, seconds: float = 1.0,
             th_.start()
         for th_ in threads:
             th_.join()
-        n_req = 0
+        n_req = n_kept = 0
         for lst in rids:
             for rid, s, st0, n in lst:
                 status, out = srv.wait(rid)
                 n_req += 1
-                if status == 0 and len(kept) < 64 and ri == 0:
-                    kept.append((s, st0, n, out))
+                if status == 0 and n_kept < 64:   # the first 64 completed requests of each rate
+                    kept.append((ri, s, st0, n, out))
+                    n_kept += 1
         wall = time.perf_counter() - t_start
         rep = srv.stats()
         steps.append({"offered_req_per_s": rate, "requests": n_req, "completed_req_per_s": n_req / wall,
@@ -676,13 +931,25 @@ def run_serving(M, WL, cfg=None, n_sources: int = 32, seconds: float = 1.0,
                       "mean_batch_walkers": rep["mean_batch_walkers"], "batches": rep["batches"]})
         if n_req / wall < 0.8 * rate or rep["p99_ms"] > 2000:
             break
-    # accuracy of served results against the float64 kernel on the same walkers
-    errs = []
-    for s, st0, n, out in kept:
+    # accuracy of served results: up to 64 requests of the lowest offered rate and 64 of the
+    # highest one run (the largest packed batches), against the float64 kernel on every walker
+    # of them and against the oracle on up to 8 walkers of each
+    last = max(k[0] for k in kept) if kept else 0
+    sel = [k for k in kept if k[0] == 0][:64] + ([k for k in kept if k[0] == last][:64] if last > 0 else [])
+    from oracle import oracle as O
+    osrc = _oracle_sources(ub, 4, sorted({k[1] for k in sel}))
+    errs, oerrs = [], []
+    for _, s, st0, n, out in sel:
         th = torch.from_numpy(pools[s][:, st0:st0 + n].copy()).cuda()
         ref = M.het_loglike_batch([ub.refs[s]], [0, n], th, "fp64").cpu().numpy()
         errs.append(np.abs(out[0] - ref[0]))
+        th0, ref_o = osrc[s]
+        wo = WL.walkers(th0, int(ub.walkers[s]), 4, s, 1e-5, 1e-3)[:, st0:st0 + n]
+        idx = np.unique(np.linspace(0, n - 1, min(8, n)).astype(int))
+        ora = O.het_loglike(np.ascontiguousarray(wo[:, idx]), ref_o)
+        oerrs.append(np.abs(out[0][idx] - ora[0]))
     e = np.concatenate(errs) if errs else np.zeros(1)
+    oe = np.concatenate(oerrs) if oerrs else np.zeros(1)
     # the same sources driven by native client threads (the server's own capacity: the Python
     # clients above saturate first)
     native = []
@@ -705,26 +972,28 @@ def run_serving(M, WL, cfg=None, n_sources: int = 32, seconds: float = 1.0,
             "native_clients": {"rates": native, "peak_walkers_per_s": best_native["walkers_per_s"],
                                "peak_completed_req_per_s": best_native["completed_per_s"]},
             "abs_dlnL_vs_fp64_kernel": {"p50": float(np.median(e)), "p99": float(np.quantile(e, 0.99)),
-                                        "max": float(e.max()), "walkers": int(e.size)}}
+                                        "max": float(e.max()), "walkers": int(e.size)},
+            "accuracy_vs_oracle": _acc(oe),
+            "accuracy_sampled_requests": f"{len(sel)} requests from the lowest and the highest offered rate"}
 
 
-def run_fused_only(args, M, WL, g, src, rank, dev, stream) -> dict | None:
-    """Profiling case: the fused generate-and-reduce direct path, mixed precision, on
+def run_fused_only(args, M, WL, g, src, rank, dev, stream, prec="mixed") -> dict | None:
+    """Profiling case: the fused generate-and-reduce direct path (mixed precision or float64) on
     args.stored prior templates of the 1-yr grid."""
     import torch
     th = WL.to_dev(I.draw_prior_batch(I.rng(1, 300 + rank), args.stored, g["t_obs"]))
     out = torch.empty((3, args.stored), dtype=torch.float64, device=dev)
     for _ in range(args.warmup):
-        M.direct_loglike_batch(src.data, th, "mixed", out=out)
+        M.direct_loglike_batch(src.data, th, prec, out=out)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        M.direct_loglike_batch(src.data, th, "mixed", out=out)
+        M.direct_loglike_batch(src.data, th, prec, out=out)
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
-    return {"profile_case": "fused", "templates": args.stored, "ms": ms,
+    return {"profile_case": "fused", "precision": prec, "templates": args.stored, "ms": ms,
             "templates_per_s": args.stored / (ms * 1e-3)} if rank == 0 else None
 
 
@@ -821,12 +1090,17 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="CPU work of the oracle baseline (0: skip)")
-    ap.add_argument("--only", default="all", choices=["all", "het", "direct", "fused", "sampler", "hm"],
+    ap.add_argument("--only", default="all", choices=["all", "het", "direct", "fused", "fused64", "sampler", "hm"],
                     help="profiling cases: time only the heterodyne steps, the direct path, the "
                          "sampler or the higher-mode heterodyne")
     ap.add_argument("--walkers", type=int, default=N_WALKERS, help="heterodyne batch (profiling)")
     ap.add_argument("--stored", type=int, default=N_STORED, help="stored templates (profiling)")
+    ap.add_argument("--oracle-time", default=None, choices=["wl0", "direct"],
+                    help="internal: time the oracle in this process (no GPU) and print JSON")
     args = ap.parse_args()
+    if args.oracle_time:
+        print(json.dumps(oracle_time(args.oracle_time)), flush=True)
+        return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
@@ -839,11 +1113,14 @@ def main():
             res["cpu_baseline"] = {k: v for k, v in cb.items() if not k.startswith("_")}
             idx, ora = cb["_idx"], cb["_out"][0]
             for key, name in (("_mixed_lnl", "accuracy_mixed_vs_oracle"),
-                              ("_fp64_lnl", "accuracy_fp64_vs_oracle")):
-                d = np.abs(res[key][idx] - ora)
-                res[name] = {"walkers": int(idx.size), "abs_dlnL_p50": float(np.median(d)),
-                             "abs_dlnL_p99": float(np.quantile(d, 0.99)),
-                             "abs_dlnL_max": float(d.max()), "frac_le_1e-3": float(np.mean(d <= 1e-3))}
+                              ("_fp64_lnl", "accuracy_fp64_vs_oracle"),
+                              ("_f32_lnl", "accuracy_mixed_f32_vs_oracle")):
+                res[name] = _acc(res[key][idx] - ora)
+            if args.only == "all":
+                dcb = direct_cpu_baseline()
+                lnl = np.array(dcb.pop("_lnl"))
+                dcb["accuracy_fused_mixed_vs_oracle"] = _acc(res["_direct_fused_mixed"][:lnl.size] - lnl)
+                res["direct"]["cpu_baseline"] = dcb
     if res is not None:
         for k in [k for k in res if k.startswith("_")]:
             res.pop(k)

@@ -58,7 +58,8 @@ typedef enum {
     MBH_ECUDA = 3,    /* CUDA error (no device, launch failure, ...) */
     MBH_ETIMEOUT = 4, /* a bounded wait gave up (serving loop) */
     MBH_EBUSY = 5,    /* admission refused: over the memory budget or queue full */
-    MBH_ECANCELED = 6 /* request cancelled before it was launched */
+    MBH_ECANCELED = 6, /* request cancelled before it was launched */
+    MBH_EDEVICE = 7    /* an in-kernel check failed (debug builds): see mbh_sync_status */
 } mbh_status;
 
 typedef enum {
@@ -92,6 +93,32 @@ typedef struct mbh_ref mbh_ref;   /* one heterodyne reference (summary data) */
 
 /* Message for the last failing call on this thread ("" if none). */
 MBH_API const char* mbh_last_error(void);
+
+/* ---- device-side status word -----------------------------------------------------
+ * The paper has no counterpart: this is the library's error channel for what only a
+ * kernel can see.  Every device holds one status word.  The heterodyne kernels of a build
+ * with MBH_DEBUG_CHECKS (libmbhlike_debug.so, built by `python -m
+ * paper_2111_01064_b300.build --debug`) check the index of every bin-edge record they read
+ * against the reference's logical edge range; the first failed check on a device records
+ * the kernel, the source slot, the index and its range, and the kernel skips that access
+ * (it never traps, faults or waits).  Release builds do no in-kernel checks.  Calls never
+ * read the word on their own (that would synchronise): mbh_sync_status does. */
+typedef struct {
+    int32_t code;     /* 0: no failure; 1: an index outside its logical range */
+    int32_t kernel;   /* 1: MBH_MIXED heterodyne, 2: MBH_MIXED_F32, 3: MBH_FP64 */
+    int32_t source;   /* launch slot of the failing walker's source */
+    int32_t reserved;
+    int64_t index;    /* the failing index and its range [0, limit) */
+    int64_t limit;
+} mbh_device_status;
+
+/* Synchronises `stream`, then reads and clears the current device's status word.
+ * MBH_OK if no check failed; MBH_EDEVICE (details in *info, if not NULL, and in
+ * mbh_last_error) if one did; MBH_ECUDA for an asynchronous CUDA error of the stream's
+ * work (cudaStreamSynchronize's).  info is zeroed when nothing failed. */
+MBH_API mbh_status mbh_sync_status(void* stream, mbh_device_status* info);
+/* 1 if this library was built with MBH_DEBUG_CHECKS, else 0. */
+MBH_API int32_t mbh_debug_checks(void);
 
 /* Analytic noise PSD S_n of A, E, T on the grid (Sec. II, remark under Eq. 3:
  * A and E identical, T different; acceleration 3e-15 m/s^2/rtHz, OMS
@@ -178,6 +205,12 @@ MBH_API uint32_t mbh_ref_modes(const mbh_ref* ref);
 MBH_API mbh_status mbh_ref_read(const mbh_ref* ref, int64_t* edges_host, double* summary_host,
                         double* h0_edges_host, double* dd_host);
 MBH_API void mbh_ref_free(mbh_ref* ref);
+/* Test support of debug builds: narrows the logical edge range that the in-kernel checks
+ * hold the reference's edge indices to, edges [0, e_check] (-1 restores [0, E]); the
+ * tables themselves and the kernels' loops are unchanged, so indices past e_check stay
+ * inside the allocated records and the checks, not the memory, decide.  MBH_EINVAL for
+ * e_check outside [-1, E], and in release builds (no in-kernel checks). */
+MBH_API mbh_status mbh_debug_ref_limit(mbh_ref* ref, int32_t e_check);
 
 /* Heterodyned likelihood for walkers of several sources in one launch
  * (Sec. II B, Eqs. 14 and 17): the template is evaluated at the E_s + 1 bin

@@ -15,6 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libmbhlike.so")
+DEBUG_LIB = os.path.join(HERE, "libmbhlike_debug.so")   # MBH_DEBUG_CHECKS: in-kernel index checks
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 
@@ -23,23 +24,28 @@ def sources() -> list[str]:
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib: str) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) \
         + glob.glob(os.path.join(INCLUDE, "*.h"))
     return any(os.path.getmtime(p) > t for p in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile every source to an object in parallel (one nvcc per file), then link."""
-    if not force and not _stale():
-        return LIB
-    objdir = os.path.join(HERE, "_build")
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    """Compile every source to an object in parallel (one nvcc per file), then link.
+    debug=True builds libmbhlike_debug.so with MBH_DEBUG_CHECKS (in-kernel index checks that
+    record into the device status word and skip the access)."""
+    lib = DEBUG_LIB if debug else LIB
+    if not force and not _stale(lib):
+        return lib
+    objdir = os.path.join(HERE, "_build_debug" if debug else "_build")
     os.makedirs(objdir, exist_ok=True)
     flags = [*ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden",
              "-I", INCLUDE, "--expt-relaxed-constexpr"]
+    if debug:
+        flags.append("-DMBH_DEBUG_CHECKS")
     if verbose:
         flags.insert(0, "-Xptxas=-v")
     jobs = []
@@ -49,10 +55,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
     failed = [obj for obj, p in jobs if p.wait() != 0]
     if failed:
         raise subprocess.CalledProcessError(1, f"nvcc ({', '.join(map(os.path.basename, failed))})")
-    subprocess.check_call([NVCC, *ARCH, "-shared", "-o", LIB + ".tmp", *[o for o, _ in jobs], "-lcudart"])
-    os.replace(LIB + ".tmp", LIB)
-    return LIB
+    subprocess.check_call([NVCC, *ARCH, "-shared", "-o", lib + ".tmp", *[o for o, _ in jobs], "-lcudart"])
+    os.replace(lib + ".tmp", lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="--verbose" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="--verbose" in sys.argv, debug="--debug" in sys.argv))

@@ -21,7 +21,7 @@
 // the walker, which the edge record's G_c = K_c/T0_c (float64, from the reference's transfer at
 // alpha0(f) and the frequency-only factors K_c) turns into the response ratio.  All of these
 // vanish (or are exactly 1) at the reference itself.  Then
-//   delta_c = r_c - 1 = (rho_c - 1) + rho_c (e^{-i dPhi} - 1),   rho_c = R e^u T_c G_c,
+//   delta_c = r_c - 1 = T_c (A e^{-i dPhi} G_c) - 1,   A = R e^u,
 // and the contraction of Eqs. 14 and 17 is regrouped per edge (each edge's delta meets the
 // summary data of its two bins through five double-float weights per channel; the bin's cross
 // term needs the neighbouring edge's delta) and accumulated in double-float.
@@ -241,6 +241,11 @@ __device__ inline void xwalker_setup(const double* __restrict__ theta, int64_t W
     o.Gb[1] = split_rn(w.G[3]);
 }
 
+// The per-arm body (three times per edge) and the double-float sine/cosine (four times per
+// edge) are compiled once and called: the inlined edge loop was ~45 KB of straight-line code,
+// and its instruction fetch stalled the warps.
+#define MBH_X_OUTLINE __noinline__
+
 constexpr f2 kH3 = df_const(0.8660254037844386467637231707529361835);   // sqrt3/2
 constexpr f2 kOrbRate = df_const(6.283185307179586476925286766559005768 / 31557600.0);   // 2 pi / yr
 
@@ -274,6 +279,41 @@ __device__ __forceinline__ void arm_sincs(f2 x, f2 kn, const SinTab& tab, f2& sm
         sm = dd_sinc(b, tab);
         sd = dd_sub_lazy(dd_sinc(a, tab), sm);
     }
+}
+
+struct SinCos {
+    f2 s, cm1;
+};
+
+__device__ MBH_X_OUTLINE SinCos sincos_df(f2 x, const SinTab& tab)
+{
+    SinCos r;
+    dd_sincos_any(x, tab, r.s, r.cm1);
+    return r;
+}
+
+struct ArmOut {
+    c2f yf, z;
+};
+
+// One arm (spacecraft i -> j, third spacecraft m) of the raw transfer: arm vector d = u_j - u_i,
+// kn = k.n, the polarisation response a Ga + b Gb, g = i e^{i q_m} F and the one-link sinc
+// factors: yf = g sinc(x(1 - kn)), z = g [sinc(x(1 + kn)) - sinc(x(1 - kn))].
+__device__ MBH_X_OUTLINE ArmOut arm_df(const XWalker& w, f2 x, f2 d0, f2 d1, f2 d2, f2 kn, c2f Em,
+                                       const SinTab& tab)
+{
+    const f2 un = dd_add_lazy(dd_mul_lazy(w.eu[0], d0), dd_mul_lazy(w.eu[1], d1));
+    const f2 vn = dd_add_lazy(dd_add_lazy(dd_mul_lazy(w.ev[0], d0), dd_mul_lazy(w.ev[1], d1)),
+                              dd_mul_lazy(w.ev[2], d2));
+    const f2 pa = dd_sub_lazy(dd_sqr_lazy(un), dd_sqr_lazy(vn));
+    const f2 pb = dd_scale(dd_mul_lazy(un, vn), 2.0f);
+    const c2f F = {dd_add_lazy(dd_mul_lazy(pa, w.Ga[0]), dd_mul_lazy(pb, w.Gb[0])),
+                   dd_add_lazy(dd_mul_lazy(pa, w.Ga[1]), dd_mul_lazy(pb, w.Gb[1]))};
+    const c2f eF = cd_mul(Em, F);
+    const c2f g = {{-eF.im.hi, -eF.im.lo}, eF.re};   // i e^{i q_m} F
+    f2 sm, sd;
+    arm_sincs(x, kn, tab, sm, sd);
+    return {cd_mul_r(g, sm), cd_mul_r(g, sd)};
 }
 
 // Raw transfer of the walker at orbit angle (sa, ca): the construction of the float32 path's
@@ -311,9 +351,8 @@ __device__ inline void transfer_df(const XWalker& w, f2 x, f2 s2, f2 c2, f2 sa, 
     c2f E[3];   // e^{i q_m}
 #pragma unroll
     for (int m = 0; m < 2; ++m) {
-        f2 s, cm1;
-        dd_sincos_any(dd_mul_lazy(x, kap[m]), tab, s, cm1);
-        E[m] = {dd_add_f_lazy(cm1, 1.0f), s};
+        const SinCos q = sincos_df(dd_mul_lazy(x, kap[m]), tab);
+        E[m] = {dd_add_f_lazy(q.cm1, 1.0f), q.s};
     }
     const c2f e01 = cd_mul(E[0], E[1]);
     E[2] = {e01.re, {-e01.im.hi, -e01.im.lo}};
@@ -324,20 +363,9 @@ __device__ inline void transfer_df(const XWalker& w, f2 x, f2 s2, f2 c2, f2 sa, 
         f2 d[3];
 #pragma unroll
         for (int q = 0; q < 3; ++q) d[q] = dd_sub_lazy(u[j][q], u[i][q]);
-        const f2 kn = dd_sub_lazy(kap[j], kap[i]);
-        const f2 un = dd_add_lazy(dd_mul_lazy(w.eu[0], d[0]), dd_mul_lazy(w.eu[1], d[1]));
-        const f2 vn = dd_add_lazy(dd_add_lazy(dd_mul_lazy(w.ev[0], d[0]), dd_mul_lazy(w.ev[1], d[1])),
-                                  dd_mul_lazy(w.ev[2], d[2]));
-        const f2 pa = dd_sub_lazy(dd_sqr_lazy(un), dd_sqr_lazy(vn));
-        const f2 pb = dd_scale(dd_mul_lazy(un, vn), 2.0f);
-        const c2f F = {dd_add_lazy(dd_mul_lazy(pa, w.Ga[0]), dd_mul_lazy(pb, w.Gb[0])),
-                       dd_add_lazy(dd_mul_lazy(pa, w.Ga[1]), dd_mul_lazy(pb, w.Gb[1]))};
-        const c2f eF = cd_mul(E[m], F);
-        const c2f g = {{-eF.im.hi, -eF.im.lo}, eF.re};   // i e^{i q_m} F
-        f2 sm, sd;
-        arm_sincs(x, kn, tab, sm, sd);
-        yf[a] = cd_mul_r(g, sm);
-        z[a] = cd_mul_r(g, sd);
+        const ArmOut o = arm_df(w, x, d[0], d[1], d[2], dd_sub_lazy(kap[j], kap[i]), E[m], tab);
+        yf[a] = o.yf;
+        z[a] = o.z;
     }
     const c2f U = cd_sub(cd_sub(cd_add(cd_scale(yf[2], 2.0f), z[2]), yf[1]), yf[0]);
     const c2f PA = cd_sub(U, z[0]), QA = cd_sub(U, z[1]);
@@ -374,8 +402,8 @@ __device__ __forceinline__ void edge_delta_x(const XWalker& w, const XEdge* __re
         return;
     }
     // orbit angle alpha = alpha0 + 2 pi dt / yr
-    f2 sD, cD;
-    dd_sincos_any(dd_mul_lazy(dt, kOrbRate), tab, sD, cD);
+    const SinCos oa = sincos_df(dd_mul_lazy(dt, kOrbRate), tab);
+    const f2 sD = oa.s, cD = oa.cm1;
     const f2 sa = dd_add_lazy(sa0, dd_add_lazy(dd_mul_lazy(sa0, cD), dd_mul_lazy(ca0, sD)));
     const f2 ca = dd_add_lazy(ca0, dd_sub_lazy(dd_mul_lazy(ca0, cD), dd_mul_lazy(sa0, sD)));
     // 2 pi AU/c [k.c(t) - k0.c(t0)] = dk.c(t0) + (cos da - 1) k.c(t0) + sin da (k x c(t0))_z
@@ -390,21 +418,22 @@ __device__ __forceinline__ void edge_delta_x(const XWalker& w, const XEdge* __re
     const f2 Pp = dd_mul_lazy(dd_fma_lazy(w.D[7], v0, w.D[6]), v0);
     const f2 L = dd_mul_lazy(lnv0, dd_fma_lazy(w.Dl6, v0, w.Dl5));
     const f2 dphi = dd_norm(dd_add_lazy(dd_mul_lazy(f, dd_add_lazy(w.C1, dorb)), dd_add_lazy(dd_add_lazy(N, Pp), L)));
-    f2 sP, cP;
-    dd_sincos_any(dphi, tab, sP, cP);
-    const c2f em1 = {cP, {-sP.hi, -sP.lo}};   // e^{-i dPhi} - 1
-    // amplitude ratio R exp(-f^2 (1/fc^2 - 1/fc0^2))
+    const SinCos ph = sincos_df(dphi, tab);
+    const c2f em1 = {ph.cm1, {-ph.s.hi, -ph.s.lo}};   // e^{-i dPhi} - 1
+    // amplitude ratio A = R exp(-f^2 (1/fc^2 - 1/fc0^2)), folded with e^{-i dPhi}:
+    // Z = A e^{-i dPhi} = A + A (e^{-i dPhi} - 1)
     const f2 ff = dd_sqr_lazy(f);
     const f2 u = dd_mul_lazy(ff, w.difc2);
     const f2 A = dd_mul_lazy(w.R, dd_exp({-u.hi, -u.lo}));
+    const c2f Z = {dd_add_lazy(A, dd_mul_lazy(A, em1.re)), dd_mul_lazy(A, em1.im)};
     c2f T[3];
     transfer_df(w, x, s2, c2, sa, ca, tab, T);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
+        // delta = r - 1 = T_c (Z G_c) - 1
         const float4 g = p4[5 + c];
-        const c2f rho = cd_mul_r(cd_mul(T[c], {{g.x, g.y}, {g.z, g.w}}), A);
-        const c2f rm1 = {dd_add_f_lazy(rho.re, -1.0f), rho.im};
-        dl[c] = cd_norm(cd_add(rm1, cd_mul(rho, em1)));
+        const c2f r = cd_mul(T[c], cd_mul(Z, {{g.x, g.y}, {g.z, g.w}}));
+        dl[c] = cd_norm({dd_add_f_lazy(r.re, -1.0f), r.im});
     }
 }
 
@@ -467,7 +496,10 @@ __global__ void __launch_bounds__(BLOCK) het_x_kernel(const __grid_constant__ He
             c2f dl[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) dl[c] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
-            if (active && e <= E) edge_delta_x(xw[lw], S.mix.xedge + e, tob, tab, dl);
+            // (debug builds: the edge index against the source's logical range; a failed
+            // check is recorded in the status word and the edge skipped)
+            const bool ok = active && e <= E && MBH_IN_RANGE(L.status, e, (long long)S.E_check + 1, kKernHetX, s);
+            if (ok) edge_delta_x(xw[lw], S.mix.xedge + e, tob, tab, dl);
             c2f dp[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -481,7 +513,7 @@ __global__ void __launch_bounds__(BLOCK) het_x_kernel(const __grid_constant__ He
                 carry[c].im.hi = __shfl_sync(0xffffffffu, dl[c].im.hi, G - 1, G);
                 carry[c].im.lo = __shfl_sync(0xffffffffu, dl[c].im.lo, G - 1, G);
             }
-            if (active && e <= E) contract_x(S.mix.xw + e, dp, dl, adh, ahh);
+            if (ok) contract_x(S.mix.xw + e, dp, dl, adh, ahh);
         }
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) {
@@ -676,8 +708,8 @@ HetKernel het_kernel_x(int G, int block)
 {
 #define MBH_CASE(g, b) \
     if (G == g && block == b) return {&launch_het_x<g, b>, (const void*)&het_x_kernel<g, b>};
-    MBH_CASE(1, 64) MBH_CASE(1, 128)
-    MBH_CASE(2, 64) MBH_CASE(2, 128)
+    MBH_CASE(1, 64) MBH_CASE(1, 128) MBH_CASE(1, 256)
+    MBH_CASE(2, 64) MBH_CASE(2, 128) MBH_CASE(2, 256)
     MBH_CASE(4, 64) MBH_CASE(4, 128) MBH_CASE(4, 256)
     MBH_CASE(8, 64) MBH_CASE(8, 128) MBH_CASE(8, 256)
     MBH_CASE(16, 64) MBH_CASE(16, 128) MBH_CASE(16, 256)

@@ -82,6 +82,38 @@ struct MixTables {
     double xsumA, xsumB;   // 4 sum Re A0, 4 sum B0
 };
 
+// Device-side status word (one per device): the first failed in-kernel check records what
+// failed and where; mbh_sync_status reads and clears it.  Kernels only check indices in builds
+// with MBH_DEBUG_CHECKS (libmbhlike_debug.so): a failed check records the index and skips the
+// access, so a wrong index can never fault or trap.
+struct DevStatus {
+    unsigned int code;     // 0 = no failure; kDevBounds
+    unsigned int kernel;   // kKern*
+    int32_t source, pad;   // source (launch slot) of the failing item
+    long long index, limit;   // the index and its logical range [0, limit)
+};
+enum : unsigned int { kDevBounds = 1u };
+enum : unsigned int { kKernHetX = 1u, kKernHetF32 = 2u, kKernHetF64 = 3u };
+DevStatus* dev_status();   // device address of the current device's status word
+
+#ifdef MBH_DEBUG_CHECKS
+__device__ __forceinline__ bool dbg_in_range(DevStatus* st, long long i, long long limit, unsigned kernel,
+                                             int src)
+{
+    if (i >= 0 && i < limit) return true;
+    if (st != nullptr && atomicCAS(&st->code, 0u, kDevBounds) == 0u) {
+        st->kernel = kernel;
+        st->source = src;
+        st->index = i;
+        st->limit = limit;
+    }
+    return false;
+}
+#define MBH_IN_RANGE(st, i, limit, kernel, src) mbh::dbg_in_range((st), (i), (limit), (kernel), (src))
+#else
+#define MBH_IN_RANGE(st, i, limit, kernel, src) true
+#endif
+
 struct PrepItem {
     int32_t bin;
     int64_t k0, k1;   // grid range [k0, k1)
@@ -97,6 +129,7 @@ struct SrcDesc {
     float tob_hi, tob_lo;    // t_obs as a float pair (split on the host: no float64 work per edge)
     int64_t w_begin, w_end;  // walker range in theta/out
     int32_t E;
+    int32_t E_check;         // logical edge range checked in debug builds: edges [0, E_check]
     int32_t tile_begin;      // first tile of this source
     uint32_t modes;          // mode mask of the reference (1 = (2,2) only)
 };
@@ -105,6 +138,7 @@ struct HetLaunch {
     const double* theta;
     double* out;
     const void* pt;          // fused sampler half step: the sampler's device state (else null)
+    DevStatus* status;       // device status word (in-kernel checks of debug builds)
     int32_t pt_half;
     int64_t W;
     int32_t n_src;
@@ -116,6 +150,7 @@ mbh_status fail(mbh_status s, const char* fmt, ...);
 mbh_status cuda_fail(cudaError_t e, const char* where);
 mbh_status check_grid(const mbh_grid* g);
 mbh_status check_device();
+int sm_count();   // multiprocessors of the current device (148 on B300; cached per device)
 mbh_status check_modes(uint32_t modes, mbh_precision precision);
 void direct_chunks(int64_t n, int64_t tiles, int64_t max_chunk, int64_t& chunk, int& nchunks);
 mbh_status direct_finish(double2* part, int nchunks, int64_t W, double dd, double* out,
@@ -206,6 +241,7 @@ struct mbh_ref {
     uint32_t modes = 1u;             // harmonics of h0 and of the walkers' templates
     mbh_grid grid;
     int32_t E = 0;
+    int32_t E_check = -1;            // debug builds: logical edge limit of the in-kernel checks (-1: E)
     int64_t band[2] = {0, 0};
     double theta0[11];
     double dd = 0.0;

@@ -127,7 +127,7 @@ __global__ void noise_kernel(double df, int64_t n, const double* __restrict__ z,
 static int grid_blocks(int64_t work, int threads)
 {
     int64_t b = (work + threads - 1) / threads;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(b, 148 * 64));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)sm_count() * 64));
 }
 
 extern "C" mbh_status mbh_psd_aet(const mbh_grid* grid, double* psd_dev, void* stream)
@@ -287,6 +287,7 @@ extern "C" mbh_status mbh_data_create(const mbh_grid* grid, const void* d_dev, c
     if (!d_dev || !psd_dev) return fail(MBH_EINVAL, "NULL buffer");
     if (mbh_status s = check_device()) return s;
     cudaStream_t st = (cudaStream_t)stream;
+    dev_status();   // resolve the status word's address here, outside any stream capture
     mbh_data* D = new mbh_data();
     D->grid = *grid;
     cudaGetDevice(&D->device);
@@ -435,7 +436,7 @@ namespace mbh {
 // several times over, chunks of at most max_chunk points.
 void direct_chunks(int64_t n, int64_t tiles, int64_t max_chunk, int64_t& chunk, int& nchunks)
 {
-    const int64_t target_blocks = 148 * 32;
+    const int64_t target_blocks = (int64_t)sm_count() * 32;
     int64_t nc = std::max<int64_t>(1, target_blocks / std::max<int64_t>(1, tiles));
     nc = std::max<int64_t>(nc, (n + max_chunk - 1) / max_chunk);
     nc = std::min<int64_t>(nc, (n + kDirThreads - 1) / kDirThreads);
@@ -676,6 +677,7 @@ extern "C" mbh_status het_prepare_reference_hm(const mbh_data* data, const doubl
         return fail(MBH_EINVAL, "theta0 needs M_T, q, D_L > 0");
     cudaStream_t st = (cudaStream_t)stream;
     const mbh_grid& g = data->grid;
+    dev_status();   // resolve the status word's address here, outside any stream capture
     mbh_ref* R = new mbh_ref();
     R->modes = modes;
     R->grid = g;
@@ -818,7 +820,8 @@ __global__ void __launch_bounds__(BLOCK)
         for (int r = 0; r < rounds; ++r) {
             const int e = r * G + lane;
             cd rr[3] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
-            if (active && e <= E) {
+            const bool ok = active && e <= E && MBH_IN_RANGE(L.status, e, (long long)S.E_check + 1, kKernHetF64, s);
+            if (ok) {
                 cd h[3];
                 if (point_model_f64(ws[lw], S.fe[e], S.t_obs, h)) {
 #pragma unroll
@@ -837,7 +840,7 @@ __global__ void __launch_bounds__(BLOCK)
                 carry[c].re = __shfl_sync(0xffffffffu, rr[c].re, G - 1, G);
                 carry[c].im = __shfl_sync(0xffffffffu, rr[c].im, G - 1, G);
             }
-            if (active && e >= 1 && e <= E) {
+            if (ok && e >= 1) {
                 const int b = e - 1;
                 const double iw = S.invw[b];
                 const double* sm = S.summary + (int64_t)b * 18;

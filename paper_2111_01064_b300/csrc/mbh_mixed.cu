@@ -754,7 +754,7 @@ extern "C" mbh_status mbh_selftest_math(int32_t kind, const float* x_dev, const 
     if (!x_dev || !o1_dev || (kind == 0 && !o2_dev) || ((kind == 2 || kind == 4) && !y_dev))
         return fail(MBH_EINVAL, "NULL buffer");
     if (mbh_status s = check_device()) return s;
-    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 148 * 32);
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 32);
     selftest_math_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(kind, x_dev, y_dev, n, o1_dev, o2_dev);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? MBH_OK : cuda_fail(e, "mbh_selftest_math");
@@ -986,7 +986,7 @@ mbh_status mbh::make_freq_tables(mbh_data* D, cudaStream_t st)
     if (e == cudaSuccess) e = cudaMalloc(&D->wdk, sizeof(float2) * 3 * n);
     if (e == cudaSuccess) e = cudaMalloc(&D->wvk, sizeof(float) * 3 * n);
     if (e != cudaSuccess) return cuda_fail(e, "frequency tables");
-    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 148 * 32);
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 32);
     freq_table_kernel<<<blocks, 256, 0, st>>>(D->grid.f0, D->grid.df, n, D->ftab, D->ftab2, D->ftab3);
     folded_data_kernel<<<blocks, 256, 0, st>>>(D->grid.f0, D->grid.df, n, D->sigma, D->wd, D->wv, D->wdk, D->wvk);
     e = cudaGetLastError();
@@ -1412,7 +1412,8 @@ __device__ __forceinline__ void het_mixed_body(const HetLaunch& L)
         for (int r = 0; r < rounds; ++r) {
             const int e = r * G + lane;
             cf dl[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-            if (active && e <= E) edge_delta_mixed(wsd[lw], wsf[lw], S.mix.edge + e, tob, dl);
+            const bool ok = active && e <= E && MBH_IN_RANGE(L.status, e, (long long)S.E_check + 1, kKernHetF32, s);
+            if (ok) edge_delta_mixed(wsd[lw], wsf[lw], S.mix.edge + e, tob, dl);
             cf dp[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -1422,7 +1423,7 @@ __device__ __forceinline__ void het_mixed_body(const HetLaunch& L)
                 carry[c].re = __shfl_sync(0xffffffffu, dl[c].re, G - 1, G);
                 carry[c].im = __shfl_sync(0xffffffffu, dl[c].im, G - 1, G);
             }
-            if (active && e >= 1 && e <= E) {
+            if (ok && e >= 1) {
                 float bd, bh;
                 contract_bin(S.mix.bin[e - 1], dp, dl, bd, bh);
                 df_acc(adh, {bd, 0.0f});
@@ -1647,7 +1648,8 @@ __device__ __forceinline__ void het_mixed_pt_body(const HetLaunch& L)
         for (int r = 0; r < rounds; ++r) {
             const int e = r * G + lane;
             cf dl[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-            if (active && e <= E) edge_delta_mixed(wsd[lw], wsf[lw], S.mix.edge + e, tob, dl);
+            const bool ok = active && e <= E && MBH_IN_RANGE(L.status, e, (long long)S.E_check + 1, kKernHetF32, s);
+            if (ok) edge_delta_mixed(wsd[lw], wsf[lw], S.mix.edge + e, tob, dl);
             cf dp[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -1657,7 +1659,7 @@ __device__ __forceinline__ void het_mixed_pt_body(const HetLaunch& L)
                 carry[c].re = __shfl_sync(0xffffffffu, dl[c].re, G - 1, G);
                 carry[c].im = __shfl_sync(0xffffffffu, dl[c].im, G - 1, G);
             }
-            if (active && e >= 1 && e <= E) {
+            if (ok && e >= 1) {
                 float bd, bh;
                 contract_bin(S.mix.bin[e - 1], dp, dl, bd, bh);
                 df_acc(adh, {bd, 0.0f});

@@ -702,6 +702,7 @@ extern "C" mbh_status mbh_pt_create_multi(const mbh_pt_opts* o, const mbh_ref* c
     // walker up to 12288 moving walkers, 8 above (threads per walker fixes the summation order,
     // so a sampler keeps the one it was created with)
     if (!o->het_config.threads_per_walker && P->precision == MBH_MIXED_F32) P->cfg.threads_per_walker = M <= 12288 ? 16 : 8;
+    if (!o->het_config.threads_per_walker && P->precision == MBH_MIXED) P->cfg.threads_per_walker = 4;
     const int64_t NT = (int64_t)n_ens * A.T;
     cudaError_t e = cudaSuccess;
     auto alloc = [&](void** p, size_t bytes) {

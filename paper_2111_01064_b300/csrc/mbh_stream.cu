@@ -196,7 +196,7 @@ mbh_status stored_plan(const mbh_data* data, int64_t W, int64_t& chunk, int& nch
     if (tiles > 0x7fffffff) return fail(MBH_EINVAL, "W too large");
     // about two waves of (tile, chunk) blocks, each thread reducing >= 16 points per channel
     const int64_t min_chunk = 16 * kStreamThreads;
-    int64_t nc = std::max<int64_t>(1, (148 * 16) / std::max<int64_t>(1, tiles));
+    int64_t nc = std::max<int64_t>(1, ((int64_t)sm_count() * 16) / std::max<int64_t>(1, tiles));
     nc = std::min<int64_t>(nc, std::max<int64_t>(1, data->grid.n / min_chunk));
     nc = std::max<int64_t>(nc, (data->grid.n + (1 << 18) - 1) / (1 << 18));
     nc = std::min<int64_t>(nc, 65535);

@@ -15,6 +15,7 @@ import torch
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libmbhlike.so")
+DEBUG_LIB_PATH = os.path.join(HERE, "libmbhlike_debug.so")
 
 FP64, MIXED, MIXED_F32 = 0, 1, 2
 _PREC = {"fp64": FP64, "mixed": MIXED, "mixed_f32": MIXED_F32, FP64: FP64, MIXED: MIXED,
@@ -88,6 +89,11 @@ class LoadgenReport(C.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class DeviceStatus(C.Structure):
+    _fields_ = [("code", C.c_int32), ("kernel", C.c_int32), ("source", C.c_int32), ("reserved", C.c_int32),
+                ("index", C.c_int64), ("limit", C.c_int64)]
+
+
 def grid_struct(g: dict) -> Grid:
     return Grid(float(g["f0"]), float(g["df"]), int(g["n"]), float(g["t_obs"]))
 
@@ -101,9 +107,12 @@ def lib() -> C.CDLL:
     global _lib
     if _lib is not None:
         return _lib
-    if not os.path.exists(LIB_PATH):
-        raise MBHError(3, f"{LIB_PATH} not built: run `python -m paper_2111_01064_b300.build`")
-    L = C.CDLL(LIB_PATH)
+    # MBH_DEBUG_CHECKS=1 selects the debug build (in-kernel index checks, see mbh_sync_status)
+    path = DEBUG_LIB_PATH if os.environ.get("MBH_DEBUG_CHECKS") == "1" else LIB_PATH
+    if not os.path.exists(path):
+        raise MBHError(3, f"{path} not built: run `python -m paper_2111_01064_b300.build`"
+                          f"{' --debug' if path == DEBUG_LIB_PATH else ''}")
+    L = C.CDLL(path)
     gp = C.POINTER(Grid)
     sigs = {
         "mbh_last_error": (C.c_char_p, []),
@@ -162,6 +171,9 @@ def lib() -> C.CDLL:
         "mbh_pt_counters": (C.c_int, [vp, C.POINTER(C.c_int64), C.POINTER(C.c_uint64), vp]),
         "mbh_pt_best": (C.c_int, [vp, i32, dp, dp, vp]),
         "mbh_pt_free": (None, [vp]),
+        "mbh_sync_status": (C.c_int, [vp, C.POINTER(DeviceStatus)]),
+        "mbh_debug_checks": (i32, []),
+        "mbh_debug_ref_limit": (C.c_int, [vp, i32]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(L, name)
@@ -663,3 +675,18 @@ class PTSampler:
             self.close()
         except Exception:
             pass
+
+
+def mbh_sync_status(stream=None) -> tuple[int, dict]:
+    """Synchronise the stream, read and clear the device status word: (status, details)."""
+    info = DeviceStatus()
+    st = lib().mbh_sync_status(_stream(stream), C.byref(info))
+    return st, {name: getattr(info, name) for name, _ in DeviceStatus._fields_}
+
+
+def mbh_debug_checks() -> bool:
+    return bool(lib().mbh_debug_checks())
+
+
+def mbh_debug_ref_limit(ref: "Ref", e_check: int):
+    _check(lib().mbh_debug_ref_limit(ref.handle, int(e_check)))

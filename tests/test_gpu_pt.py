@@ -93,15 +93,22 @@ def test_pt_fp64_matches_oracle(M, WL, oracle, case, n_iter):
     assert co[8 * case["T"] + 1:9 * case["T"]].sum() > 0   # some swaps accepted
 
 
-def test_pt_mixed_matches_oracle(M, WL, oracle, case):
-    _, xg, og, cg, _ = _gpu_run(M, WL, case, 3, precision="mixed")
+@pytest.mark.parametrize("precision", ["mixed", "mixed_f32"])
+def test_pt_mixed_matches_oracle(M, WL, oracle, case, precision):
+    """Mixed precisions against the oracle's float64 sampler: positions identical but where an
+    acceptance test sits within the likelihood's error of its threshold.  "mixed" (separate
+    launches, the extended-precision heterodyne): |dlnL| <= 1e-3 for every walker; "mixed_f32"
+    (fused half steps, float32 ratios): hot chains wander far from the reference, where that
+    path is held to 1e-6 of the terms, the cold chain stays near it."""
+    _, xg, og, cg, _ = _gpu_run(M, WL, case, 3, precision=precision)
     xo, oo, co = _oracle_run(oracle, case, 3)
     same = np.all(xg == xo, axis=0)
-    assert same.mean() >= 0.95, same.mean()
+    assert same.mean() >= (0.99 if precision == "mixed" else 0.95), same.mean()
     assert np.abs(cg - co).sum() <= 6
-    # hot chains wander far from the reference, where the mixed path is held to 1e-6 of the
-    # terms (as in the batch parity tests); the cold chain stays near it (|dlnL| ~ 1e-4)
     d = np.abs(og[0] - oo[0])
+    if precision == "mixed":
+        assert d[same].max() <= 1e-3
+        return
     scale = 0.5 * (case["ref_o"]["dd"] + np.abs(oo[2]) + 2 * np.abs(oo[1]))
     assert np.all((d / scale)[same] < 1e-6)
     cold = same & (np.arange(d.size) < case["W"])
@@ -232,7 +239,7 @@ def test_pt_ladder_adaptation_matches_oracle(M, WL, oracle, case):
 
 
 def test_pt_fused_half_steps_equal_separate_launches(M, WL, case):
-    """Mixed precision: a half step as one fused heterodyne launch (proposal in the walker
+    """Float32-ratio precision: a half step as one fused heterodyne launch (proposal in the walker
     setup, acceptance in the epilogue) against proposal, likelihood and acceptance as separate
     launches.  The likelihood arithmetic is the same; the walker constants are compiled into two
     kernels, so a last-bit difference may flip a decision sitting on its threshold."""
@@ -240,7 +247,7 @@ def test_pt_fused_half_steps_equal_separate_launches(M, WL, case):
     runs = []
     for fuse in (True, False):
         pt = M.PTSampler(WL.to_dev(c["x"]), c["betas"], c["lo"], c["hi"], ref=c["ref_g"], walkers=c["W"],
-                         probs=PROBS, seed=21, precision="mixed", fuse=fuse)
+                         probs=PROBS, seed=21, precision="mixed_f32", fuse=fuse)
         pt.run(4)
         x, out = (t.cpu().numpy() for t in pt.state())
         cnt, step = pt.counters()
@@ -294,20 +301,20 @@ def test_pt_multi_ensemble_matches_oracle(M, WL, oracle, case):
 
 
 def test_pt_multi_ensemble_fused_equals_alone(M, WL, oracle, case):
-    """Mixed precision, fused half steps: each ensemble of a joint run is bit-identical to the
+    """Float32-ratio precision, fused half steps: each ensemble of a joint run is bit-identical to the
     same ensemble run alone (its seed, its walkers, its reference)."""
     c = case
     n, T, W = 3, c["T"], c["W"]
     refs_g, _ = _ens_refs(M, oracle, c, n)
     xs = [I.draw_pt_ensemble(I.rng(69, e), c["x0"], T, W, c["scale"], c["lo"], c["hi"]) for e in range(n)]
     pt = M.PTSampler(WL.to_dev(np.concatenate(xs, 1)), c["betas"], c["lo"], c["hi"], refs=refs_g,
-                     walkers=W, probs=PROBS, seed=9, precision="mixed")
+                     walkers=W, probs=PROBS, seed=9, precision="mixed_f32")
     pt.run(3)
     xg = pt.state()[0].cpu().numpy()
     cg, _ = pt.counters()
     for e in range(n):
         one = M.PTSampler(WL.to_dev(xs[e]), c["betas"], c["lo"], c["hi"], ref=refs_g[e], walkers=W,
-                          probs=PROBS, seed=(9 + e * SEED_STEP) % (1 << 64), precision="mixed")
+                          probs=PROBS, seed=(9 + e * SEED_STEP) % (1 << 64), precision="mixed_f32")
         one.run(3)
         x1 = one.state()[0].cpu().numpy()
         c1, _ = one.counters()

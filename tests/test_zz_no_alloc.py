@@ -47,3 +47,25 @@ def test_noalloc_rejects_batches_beyond_its_buffer(case):
     assert st == 1
     msg = L.mbh_last_error().decode()
     assert "static buffer holds" in msg and str(8 << 20) in msg
+
+
+def test_noalloc_limit_on_the_year_grid(case):
+    """The documented limit on the 1-yr grid (1,051,920 points): large batches take
+    ceil(n / 2^18) = 5 grid chunks of partial sums, 16 bytes per (template, chunk), so the
+    8 MiB buffer holds W = 8 MiB / 80 B = 104857 templates.  Checked through the C ABI with
+    NULL buffers: W = 104857 passes the size check and stops at the NULL-buffer check (nothing
+    is queued), W = 104858 and 104861 are refused for their size."""
+    import torch
+    M, WL, g, src, th = case
+    gy = I.grid_year()
+    psd = M.mbh_psd_aet(gy)
+    data = M.Data(gy, torch.zeros((3, gy["n"]), dtype=torch.complex128, device="cuda"), psd)
+    L = M.lib()
+    w_max = (8 << 20) // (16 * 5)
+    assert w_max == 104857
+    assert L.direct_loglike_stored_noalloc(data.handle, None, w_max, 0, None, None) == 1
+    assert "NULL buffer" in L.mbh_last_error().decode()
+    for w in (w_max + 1, w_max + 4):
+        assert L.direct_loglike_stored_noalloc(data.handle, None, w, 0, None, None) == 1
+        msg = L.mbh_last_error().decode()
+        assert "static buffer holds" in msg and f"W={w}" in msg and "5 chunks" in msg, msg
