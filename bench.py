@@ -95,11 +95,14 @@ def fma_peak_tinst(sm_mhz: float) -> float:
 #    (double-float phase/time differences, orbit, response, ratio, per-edge contraction);
 #  - direct_fused_mixed_kernel<8>: FMA-pipe instructions per (template, grid point);
 #  - direct_fused_f64_kernel<4>: FP64-pipe instructions per (template, grid point).
+#    On workload 2 (SNR 122) 110 of the 257 edges take the float32 ratio and 147 the
+#    double-float chain: 1783 FMA-pipe instructions per edge on average (2536 with every edge
+#    double-float).
 HET_KERNEL = "het_x_kernel<4,128>"
-HET_X_FMA_INST_PER_EDGE = 2780.0
-HET_X_DRAM_BYTES = 1.62e6                  # read + write per 16384-walker launch (ncu)
-FUSED_MIXED_FMA_INST_PER_POINT = 0.0
-FUSED_F64_DFMA_INST_PER_POINT = 0.0
+HET_X_FMA_INST_PER_EDGE = 1783.2
+HET_X_DRAM_BYTES = 1.678e6                 # read + write per 16384-walker launch (ncu)
+FUSED_MIXED_FMA_INST_PER_POINT = 426.7
+FUSED_F64_DFMA_INST_PER_POINT = 590.5
 STORED_DATA_BYTES = 75.74e6                # data pairs, read once per launch (ncu: 883.66 MB
 STORED_BYTES_PER_TEMPLATE = 50.4945e6      # for 16 templates = 75.74 MB + 16 x 50.49 MB)
 
@@ -232,7 +235,7 @@ def run_ours(args) -> dict | None:
         r = run_higher_modes(M, WL, g, stream, reps=args.steps)
         return {"profile_case": "hm", **r} if rank == 0 else None
 
-    def het_step(prec="mixed"):
+    def het_step(prec=args.het_precision):
         M.het_loglike_batch([ref], offs, theta, prec, out=out)
 
     # ---- timed heterodyne steps ----
@@ -264,8 +267,8 @@ def run_ours(args) -> dict | None:
     mixed_out = out.cpu().numpy().copy()
     if args.only == "het":
         clk.__exit__(None, None, None)
-        return {"profile_case": "het", "walkers": nw, "value": value, "unit": UNIT,
-                "ms_per_step": ms_per_step} if rank == 0 else None
+        return {"profile_case": "het", "precision": args.het_precision, "walkers": nw, "value": value,
+                "unit": UNIT, "ms_per_step": ms_per_step} if rank == 0 else None
 
     # ---- float64 heterodyne kernel on the same batch (baseline) ----
     het_step("fp64")
@@ -435,7 +438,7 @@ def run_ours(args) -> dict | None:
                 "not available)",
         "config": {"workload": WORKLOAD, "walkers": nw, "temperatures": W_TEMPS,
                    "bins_requested": N_BINS, "bins": E, "channels": 3, "grid_points": n,
-                   "precision": "mixed", "l2": "flushed between steps (512 MiB write, outside the "
+                   "precision": args.het_precision, "l2": "flushed between steps (512 MiB write, outside the "
                    "timed events)", "parallelism": f"walker batches per rank x{ws}"},
         "gpu_launches": args.steps * 1,
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
@@ -1094,6 +1097,8 @@ def main():
                     help="profiling cases: time only the heterodyne steps, the direct path, the "
                          "sampler or the higher-mode heterodyne")
     ap.add_argument("--walkers", type=int, default=N_WALKERS, help="heterodyne batch (profiling)")
+    ap.add_argument("--het-precision", default="mixed", choices=["mixed", "mixed_f32", "fp64"],
+                    help="precision of the timed heterodyne steps (default: mixed, the library's MBH_MIXED)")
     ap.add_argument("--stored", type=int, default=N_STORED, help="stored templates (profiling)")
     ap.add_argument("--oracle-time", default=None, choices=["wl0", "direct"],
                     help="internal: time the oracle in this process (no GPU) and print JSON")

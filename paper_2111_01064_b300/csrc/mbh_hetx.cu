@@ -30,9 +30,11 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "mbh_dfx.cuh"
 #include "mbh_internal.cuh"
+#include "mbh_mixed.cuh"
 #include "mbh_model.cuh"
 
 using namespace mbh;
@@ -65,6 +67,15 @@ __device__ __forceinline__ f2 split_rn(double x)
     const float hi = (float)x;
     return {hi, (float)(x - (double)hi)};
 }
+
+// Per-edge precision.  On an edge that takes the float32 ratio (the float32-ratio path's
+// edge_delta_mixed: double-float phase, float32 response and ratio) delta is off by at most
+// kF32EdgeError for |delta| <= kDeltaMax (its measured error is a few 1e-8 typical, a few 1e-7
+// coherent over a walker's edges); with S_e >= |d lnL / d delta_e| the float32 edges add at most
+// kF32EdgeError sum S_e <= kF32Budget to |dlnL|.
+constexpr double kDeltaMax = 3.0;
+constexpr double kF32EdgeError = 1e-6;
+constexpr double kF32Budget = 1e-4;
 
 __device__ __forceinline__ void load_sintab(SinTab& tab)
 {
@@ -471,6 +482,8 @@ __global__ void __launch_bounds__(BLOCK) het_x_kernel(const __grid_constant__ He
 {
     constexpr int WPB = BLOCK / G;
     __shared__ XWalker xw[WPB];
+    __shared__ WalkerDF wsd[WPB];   // float32-ratio edges: the float32 path's walker constants
+    __shared__ WalkerF wsf[WPB];
     __shared__ SinTab tab;
     const int lw = threadIdx.x / G, lane = threadIdx.x % G;
     load_sintab(tab);
@@ -482,7 +495,10 @@ __global__ void __launch_bounds__(BLOCK) het_x_kernel(const __grid_constant__ He
         const bool active = w0 + lw < S.w_end;
         __syncthreads();
         for (int j = threadIdx.x; j < WPB; j += BLOCK)
-            if (w0 + j < S.w_end) xwalker_setup(L.theta, L.W, w0 + j, *S.mix.xder, xw[j]);
+            if (w0 + j < S.w_end) {
+                xwalker_setup(L.theta, L.W, w0 + j, *S.mix.xder, xw[j]);
+                if (S.mix.xn32 > 0) walker_setup_mixed(L.theta, L.W, w0 + j, wsd[j], wsf[j]);
+            }
         __syncthreads();
         const int E = S.E;
         const f2 tob = {S.tob_hi, S.tob_lo};
@@ -499,7 +515,16 @@ __global__ void __launch_bounds__(BLOCK) het_x_kernel(const __grid_constant__ He
             // (debug builds: the edge index against the source's logical range; a failed
             // check is recorded in the status word and the edge skipped)
             const bool ok = active && e <= E && MBH_IN_RANGE(L.status, e, (long long)S.E_check + 1, kKernHetX, s);
-            if (ok) edge_delta_x(xw[lw], S.mix.xedge + e, tob, tab, dl);
+            if (ok) {
+                if (S.mix.xw[e].v[30] != 0.0f) {   // low-weight edge: float32 ratio
+                    cf d32[3];
+                    edge_delta_mixed(wsd[lw], wsf[lw], S.mix.edge + e, tob, d32);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) dl[c] = {{d32[c].re, 0.0f}, {d32[c].im, 0.0f}};
+                } else {
+                    edge_delta_x(xw[lw], S.mix.xedge + e, tob, tab, dl);
+                }
+            }
             c2f dp[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -607,13 +632,14 @@ __global__ void xedge_kernel(const double* __restrict__ theta0, const XDer* __re
 // (bin e as its lower edge, bin e - 1 as its upper edge), and the constant parts 4 sum Re A0,
 // 4 sum B0.
 __global__ void xweight_kernel(const double* __restrict__ summary, const double* __restrict__ invw, int E,
-                               XWeight* __restrict__ out, double* __restrict__ sums)
+                               XWeight* __restrict__ out, double* __restrict__ sums, double* __restrict__ sens)
 {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e <= E) {
         XWeight m;
         float* p = reinterpret_cast<float*>(&m);
         for (int j = 0; j < 32; ++j) p[j] = 0.0f;
+        double S = 0.0;
         for (int c = 0; c < 3; ++c) {
             double war = 0.0, wai = 0.0, wbr = 0.0, wq = 0.0, wc = 0.0;
             if (e < E) {   // lower edge of bin e
@@ -641,8 +667,12 @@ __global__ void xweight_kernel(const double* __restrict__ summary, const double*
             const f2 cc = split_rn(4.0 * wc);
             p[24 + 2 * c] = cc.hi;
             p[25 + 2 * c] = cc.lo;
+            // |d lnL / d delta| bound for |delta|, |delta_prev| <= kDeltaMax: the linear weights,
+            // 2 kDeltaMax |wq| and kDeltaMax |wc| (lnL = <d|h> - <h|h>/2 + const)
+            S += 4.0 * (fabs(war) + fabs(wai) + 0.5 * fabs(wbr) + kDeltaMax * fabs(wq) + 0.5 * kDeltaMax * fabs(wc));
         }
         out[e] = m;
+        sens[e] = S;
     }
     if (e == 0) {
         double a = 0.0, b = 0.0;
@@ -657,7 +687,9 @@ __global__ void xweight_kernel(const double* __restrict__ summary, const double*
 }
 
 // Tables of the extended-precision heterodyne for a (2,2) reference: XDer of theta0, edge
-// records, edge weights and the constant parts (read back to the host into R->mix).
+// records, edge weights and the constant parts (read back to the host into R->mix), and the
+// edges that take the float32 ratio: the least sensitive ones, in ascending order of their
+// sensitivity S_e, while kF32EdgeError x (sum of their S_e) stays within kF32Budget.
 cudaError_t prepare_x_tables(mbh_ref* R, cudaStream_t st)
 {
     const int E = R->E;
@@ -665,14 +697,34 @@ cudaError_t prepare_x_tables(mbh_ref* R, cudaStream_t st)
     if (e == cudaSuccess) e = cudaMalloc(&R->x_edge, sizeof(XEdge) * (E + 1));
     if (e == cudaSuccess) e = cudaMalloc(&R->x_w, sizeof(XWeight) * (E + 1));
     if (e == cudaSuccess) e = cudaMalloc(&R->x_sums, sizeof(double) * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&R->x_sens, sizeof(double) * (E + 1));
     if (e != cudaSuccess) return e;
     xref_kernel<<<1, 32, 0, st>>>(R->theta0_dev, R->x_der);
     xedge_kernel<<<(E + 1 + 127) / 128, 128, 0, st>>>(R->theta0_dev, R->x_der, R->grid.t_obs, R->fe, E + 1,
                                                       R->x_edge);
-    xweight_kernel<<<(E + 1 + 127) / 128, 128, 0, st>>>(R->summary, R->invw, E, R->x_w, R->x_sums);
+    xweight_kernel<<<(E + 1 + 127) / 128, 128, 0, st>>>(R->summary, R->invw, E, R->x_w, R->x_sums, R->x_sens);
     e = cudaGetLastError();
     double sums[2];
+    std::vector<double> sens(E + 1);
     if (e == cudaSuccess) e = cudaMemcpyAsync(sums, R->x_sums, sizeof sums, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sens.data(), R->x_sens, sizeof(double) * (E + 1), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+    std::vector<int> order(E + 1);
+    for (int i = 0; i <= E; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return sens[a] < sens[b]; });
+    std::vector<float> flag(E + 1, 0.0f);
+    double acc = 0.0;
+    int n32 = 0;
+    for (int i : order) {
+        if (kF32EdgeError * (acc + sens[i]) > kF32Budget) break;
+        acc += sens[i];
+        flag[i] = 1.0f;
+        ++n32;
+    }
+    // v[30] of every record (pitch sizeof(XWeight))
+    e = cudaMemcpy2DAsync(reinterpret_cast<char*>(R->x_w) + 30 * sizeof(float), sizeof(XWeight), flag.data(),
+                          sizeof(float), sizeof(float), E + 1, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e == cudaSuccess) {
         R->mix.xder = R->x_der;
@@ -680,6 +732,7 @@ cudaError_t prepare_x_tables(mbh_ref* R, cudaStream_t st)
         R->mix.xw = R->x_w;
         R->mix.xsumA = sums[0];
         R->mix.xsumB = sums[1];
+        R->mix.xn32 = n32;
     }
     return e;
 }
@@ -690,6 +743,7 @@ void free_x_tables(mbh_ref* R)
     if (R->x_edge) cudaFree(R->x_edge);
     if (R->x_w) cudaFree(R->x_w);
     if (R->x_sums) cudaFree(R->x_sums);
+    if (R->x_sens) cudaFree(R->x_sens);
 }
 
 }  // namespace mbh

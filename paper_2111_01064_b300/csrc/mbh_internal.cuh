@@ -63,7 +63,7 @@ struct alignas(16) XEdge {
     float v[32];
 };
 // Edge weights (8 x 128-bit loads): per channel (war, wai), (wbr, wq) as float pairs; then the
-// cross-term weights wc of the three channels.
+// cross-term weights wc of the three channels; v[30] = 1 where the edge takes the float32 ratio.
 struct alignas(16) XWeight {
     float v[32];
 };
@@ -80,6 +80,7 @@ struct MixTables {
     const XEdge* xedge;    // [E+1]
     const XWeight* xw;     // [E+1]
     double xsumA, xsumB;   // 4 sum Re A0, 4 sum B0
+    int32_t xn32;          // edges that take the float32 ratio (flagged in their XWeight)
 };
 
 // Device-side status word (one per device): the first failed in-kernel check records what
@@ -262,5 +263,6 @@ struct mbh_ref {
     mbh::XEdge* x_edge = nullptr;
     mbh::XWeight* x_w = nullptr;
     double* x_sums = nullptr;
+    double* x_sens = nullptr;           // [E+1] per-edge sensitivity of lnL to delta
     mbh::MixTables mix{};
 };
