@@ -70,11 +70,12 @@ __device__ __forceinline__ f2 split_rn(double x)
 
 // Per-edge precision.  On an edge that takes the float32 ratio (the float32-ratio path's
 // edge_delta_mixed: double-float phase, float32 response and ratio) delta is off by at most
-// kF32EdgeError for |delta| <= kDeltaMax (its measured error is a few 1e-8 typical, a few 1e-7
-// coherent over a walker's edges); with S_e >= |d lnL / d delta_e| the float32 edges add at most
-// kF32EdgeError sum S_e <= kF32Budget to |dlnL|.
+// kF32EdgeError for |delta| <= kDeltaMax; with S_e >= |d lnL / d delta_e| the float32 edges add
+// at most kF32EdgeError sum S_e <= kF32Budget to |dlnL|.  kF32EdgeError is ten times the largest
+// error per unit of sensitivity that the float32 ratio shows with every edge in float32 (its
+// batch maximum |dlnL| over sum S_e: 1.4e-8 to 2.8e-8 on sources of SNR 122 to 1000).
 constexpr double kDeltaMax = 3.0;
-constexpr double kF32EdgeError = 1e-6;
+constexpr double kF32EdgeError = 3e-7;
 constexpr double kF32Budget = 1e-4;
 
 __device__ __forceinline__ void load_sintab(SinTab& tab)
@@ -196,7 +197,32 @@ struct XWalker {
     f2 dkx, dky, kx, ky; // orbit phase: 2 pi AU/c (k - k0) and k of the walker (in-plane)
     f2 fcut, R, difc2;   // f_cut; amplitude ratio; 1/fc^2 - 1/fc0^2
     f2 k3[3], eu[2], ev[3], Ga[2], Gb[2];   // response constants (as the float32 path)
+    f2 s;                // (M/M0)^{1/3}: v = s v0 (the higher modes' v^{p_lm})
 };
+
+// Higher modes: the walker's per-mode polarisation factors rotated by 2 psi, (Ga, Gb) as for the
+// (2,2) mode, folded with H_lm's constant and sqrt(2/m) (the float64 model's hm_setup).
+struct XWalkerHM {
+    f2 G[kHmModes][4];   // Ga (re, im), Gb (re, im)
+};
+
+__device__ inline void xwalker_setup_hm(const double* __restrict__ theta, int64_t W, int64_t i, XWalkerHM& h)
+{
+    const double q = theta[kQ * W + i], iota = theta[kIota * W + i], phi = theta[kPhi * W + i];
+    const double pol = theta[kPsi * W + i];
+    Walker tmp;
+    hm_setup(tmp, q, iota, phi);
+    double s2p, c2p;
+    sincos(2.0 * pol, &s2p, &c2p);
+#pragma unroll
+    for (int b = 0; b < kHmModes; ++b)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const double kp = tmp.hk[b][j], kc = tmp.hk[b][2 + j];
+            h.G[b][j] = split_rn(c2p * kp - s2p * kc);
+            h.G[b][2 + j] = split_rn(s2p * kp + c2p * kc);
+        }
+}
 
 __device__ inline void xwalker_setup(const double* __restrict__ theta, int64_t W, int64_t i,
                                      const XDer& r, XWalker& o)
@@ -250,6 +276,7 @@ __device__ inline void xwalker_setup(const double* __restrict__ theta, int64_t W
     o.Ga[1] = split_rn(w.G[1]);
     o.Gb[0] = split_rn(w.G[2]);
     o.Gb[1] = split_rn(w.G[3]);
+    o.s = split_rn(s);
 }
 
 // The per-arm body (three times per edge) and the double-float sine/cosine (four times per
@@ -310,16 +337,16 @@ struct ArmOut {
 // One arm (spacecraft i -> j, third spacecraft m) of the raw transfer: arm vector d = u_j - u_i,
 // kn = k.n, the polarisation response a Ga + b Gb, g = i e^{i q_m} F and the one-link sinc
 // factors: yf = g sinc(x(1 - kn)), z = g [sinc(x(1 + kn)) - sinc(x(1 - kn))].
-__device__ MBH_X_OUTLINE ArmOut arm_df(const XWalker& w, f2 x, f2 d0, f2 d1, f2 d2, f2 kn, c2f Em,
-                                       const SinTab& tab)
+__device__ MBH_X_OUTLINE ArmOut arm_df(const XWalker& w, const f2* Ga, const f2* Gb, f2 x, f2 d0, f2 d1, f2 d2,
+                                       f2 kn, c2f Em, const SinTab& tab)
 {
     const f2 un = dd_add_lazy(dd_mul_lazy(w.eu[0], d0), dd_mul_lazy(w.eu[1], d1));
     const f2 vn = dd_add_lazy(dd_add_lazy(dd_mul_lazy(w.ev[0], d0), dd_mul_lazy(w.ev[1], d1)),
                               dd_mul_lazy(w.ev[2], d2));
     const f2 pa = dd_sub_lazy(dd_sqr_lazy(un), dd_sqr_lazy(vn));
     const f2 pb = dd_scale(dd_mul_lazy(un, vn), 2.0f);
-    const c2f F = {dd_add_lazy(dd_mul_lazy(pa, w.Ga[0]), dd_mul_lazy(pb, w.Gb[0])),
-                   dd_add_lazy(dd_mul_lazy(pa, w.Ga[1]), dd_mul_lazy(pb, w.Gb[1]))};
+    const c2f F = {dd_add_lazy(dd_mul_lazy(pa, Ga[0]), dd_mul_lazy(pb, Gb[0])),
+                   dd_add_lazy(dd_mul_lazy(pa, Ga[1]), dd_mul_lazy(pb, Gb[1]))};
     const c2f eF = cd_mul(Em, F);
     const c2f g = {{-eF.im.hi, -eF.im.lo}, eF.re};   // i e^{i q_m} F
     f2 sm, sd;
@@ -335,8 +362,9 @@ __device__ MBH_X_OUTLINE ArmOut arm_df(const XWalker& w, f2 x, f2 d0, f2 d1, f2 
 //   and z = g [sinc(x(1+kn)) - sinc(x(1-kn))],
 //   P_A = U - z0, Q_A = U - z1, U = 2 yf2 + z2 - yf1 - yf0,
 //   P_E = V + z0 + z2 - 2 z1, Q_E = V + 2 z0 - z2 - z1, V = 3 (yf0 - yf1).
-__device__ inline void transfer_df(const XWalker& w, f2 x, f2 s2, f2 c2, f2 sa, f2 ca, const SinTab& tab,
-                                   c2f T[3])
+// Ga, Gb: the mode factors (the walker's (2,2) ones, or a higher-mode group's sum).
+__device__ inline void transfer_df(const XWalker& w, const f2* Ga, const f2* Gb, f2 x, f2 s2, f2 c2, f2 sa, f2 ca,
+                                   const SinTab& tab, c2f T[3])
 {
     const f2 h3s = dd_mul_lazy(kH3, sa), h3c = dd_mul_lazy(kH3, ca);
     const f2 hs = dd_scale(sa, 0.5f), hc = dd_scale(ca, 0.5f);
@@ -374,7 +402,7 @@ __device__ inline void transfer_df(const XWalker& w, f2 x, f2 s2, f2 c2, f2 sa, 
         f2 d[3];
 #pragma unroll
         for (int q = 0; q < 3; ++q) d[q] = dd_sub_lazy(u[j][q], u[i][q]);
-        const ArmOut o = arm_df(w, x, d[0], d[1], d[2], dd_sub_lazy(kap[j], kap[i]), E[m], tab);
+        const ArmOut o = arm_df(w, Ga, Gb, x, d[0], d[1], d[2], dd_sub_lazy(kap[j], kap[i]), E[m], tab);
         yf[a] = o.yf;
         z[a] = o.z;
     }
@@ -390,28 +418,25 @@ __device__ inline void transfer_df(const XWalker& w, f2 x, f2 s2, f2 c2, f2 sa, 
     T[2] = cd_add(cd_add(z[0], z[1]), z[2]);
 }
 
-// delta = r - 1 of one walker at one edge record (Sec. II B, Eq. 10), double-float; -1 where the
-// walker's template or the reference's is zero.
-__device__ __forceinline__ void edge_delta_x(const XWalker& w, const XEdge* __restrict__ pe, f2 tob,
-                                             const SinTab& tab, c2f dl[3])
+// One mode group's share of r = h/h0 at an edge (Sec. II B, Eq. 10), double-float: adds
+// T_c (A e^{-i dPhi} G_c) to acc[c] (c = A, E, T) and returns false, adding nothing, outside the
+// walker's support (f2 > f_cut or t outside [0, t_obs]).  The group's modes share f2 = 2f/m,
+// the phase chain (scaled by m/2), t(f2) and the orbit; the (2,2) mode alone is one group with
+// m = 2.  v0, 1/v0, ln v0 are the reference's at f2; t0, (ca0, sa0) its time and orbit angle
+// at f2; G4: the record's three G_c as float4 (re hi, re lo, im hi, im lo); Ga, Gb the mode
+// factors (summed over the group's modes with their v^{p_lm}).
+__device__ __forceinline__ bool group_term(const XWalker& w, const f2* Ga, const f2* Gb, f2 f, f2 fm, f2 v0, f2 iv0,
+                                           f2 lnv0, float half_m, f2 t0, f2 ca0, f2 sa0, f2 x, f2 s2, f2 c2,
+                                           const float4* G4, f2 tob, const SinTab& tab, c2f acc[3])
 {
-    const float4* p4 = reinterpret_cast<const float4*>(pe);
-    const float4 r0 = p4[0], r1 = p4[1], r2 = p4[2], r3 = p4[3], r4 = p4[4];
-    const f2 f = {r0.x, r0.y}, v0 = {r0.z, r0.w}, iv0 = {r1.x, r1.y}, lnv0 = {r1.z, r1.w};
-    const f2 t0 = {r2.x, r2.y}, ca0 = {r2.z, r2.w}, sa0 = {r3.x, r3.y}, x = {r3.z, r3.w};
-    const f2 s2 = {r4.x, r4.y}, c2 = {r4.z, r4.w};
-    // t(f) - t0(f) and the support test on t = t0 + dt, f <= f_cut
+    // t(f2) - t0(f2) and the support test on t = t0 + dt, f2 <= f_cut
     f2 Q = w.E[7];
 #pragma unroll
     for (int k = 6; k >= 0; --k) Q = dd_fma_lazy(Q, v0, w.E[k]);
     const f2 iv2 = dd_sqr_lazy(iv0), iv4 = dd_sqr_lazy(iv2), iv8 = dd_sqr_lazy(iv4);
     const f2 dt = dd_add_lazy(dd_add_lazy(dd_mul_lazy(Q, iv8), dd_mul_lazy(dd_mul_lazy(w.El6, lnv0), iv2)), w.dT0);
     const f2 t = dd_add(t0, dd_norm(dt));
-    if (!(dd_le(f, w.fcut) && !dd_lt0(t) && dd_le(t, tob))) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) dl[c] = {{-1.0f, 0.0f}, {0.0f, 0.0f}};
-        return;
-    }
+    if (!(dd_le(fm, w.fcut) && !dd_lt0(t) && dd_le(t, tob))) return false;
     // orbit angle alpha = alpha0 + 2 pi dt / yr
     const SinCos oa = sincos_df(dd_mul_lazy(dt, kOrbRate), tab);
     const f2 sD = oa.s, cD = oa.cm1;
@@ -422,30 +447,110 @@ __device__ __forceinline__ void edge_delta_x(const XWalker& w, const XEdge* __re
     const f2 ks0 = dd_sub_lazy(dd_mul_lazy(w.ky, ca0), dd_mul_lazy(w.kx, sa0));
     const f2 dorb = dd_add_lazy(dd_add_lazy(dd_mul_lazy(w.dkx, ca0), dd_mul_lazy(w.dky, sa0)),
                                 dd_add_lazy(dd_mul_lazy(cD, kc0), dd_mul_lazy(sD, ks0)));
-    // Psi_PN - Psi_PN,0 = sum_k D_k v0^{k-5} + ln v0 (Dl5 + Dl6 v0)
+    // Psi_PN - Psi_PN,0 = sum_k D_k v0^{k-5} + ln v0 (Dl5 + Dl6 v0) at f2
     f2 N = dd_mul_lazy(w.D[0], iv0);
 #pragma unroll
     for (int k = 2; k <= 5; ++k) N = dd_fma_lazy(N, iv0, w.D[k]);
     const f2 Pp = dd_mul_lazy(dd_fma_lazy(w.D[7], v0, w.D[6]), v0);
     const f2 L = dd_mul_lazy(lnv0, dd_fma_lazy(w.Dl6, v0, w.Dl5));
-    const f2 dphi = dd_norm(dd_add_lazy(dd_mul_lazy(f, dd_add_lazy(w.C1, dorb)), dd_add_lazy(dd_add_lazy(N, Pp), L)));
+    // dPhi = f (C1 + dorb) + (m/2) dPsi_PN(f2)  (the f2 t_ref terms of (m/2) Phi_22(f2) are f C1)
+    const f2 dpsi = dd_mul_f_lazy(dd_add_lazy(dd_add_lazy(N, Pp), L), half_m);
+    const f2 dphi = dd_norm(dd_add_lazy(dd_mul_lazy(f, dd_add_lazy(w.C1, dorb)), dpsi));
     const SinCos ph = sincos_df(dphi, tab);
-    const c2f em1 = {ph.cm1, {-ph.s.hi, -ph.s.lo}};   // e^{-i dPhi} - 1
-    // amplitude ratio A = R exp(-f^2 (1/fc^2 - 1/fc0^2)), folded with e^{-i dPhi}:
+    // amplitude ratio A = R exp(-f2^2 (1/fc^2 - 1/fc0^2)), folded with e^{-i dPhi}:
     // Z = A e^{-i dPhi} = A + A (e^{-i dPhi} - 1)
-    const f2 ff = dd_sqr_lazy(f);
-    const f2 u = dd_mul_lazy(ff, w.difc2);
+    const f2 u = dd_mul_lazy(dd_sqr_lazy(fm), w.difc2);
     const f2 A = dd_mul_lazy(w.R, dd_exp({-u.hi, -u.lo}));
-    const c2f Z = {dd_add_lazy(A, dd_mul_lazy(A, em1.re)), dd_mul_lazy(A, em1.im)};
+    const c2f Z = {dd_add_lazy(A, dd_mul_lazy(A, ph.cm1)), dd_mul_lazy(A, {-ph.s.hi, -ph.s.lo})};
     c2f T[3];
-    transfer_df(w, x, s2, c2, sa, ca, tab, T);
+    transfer_df(w, Ga, Gb, x, s2, c2, sa, ca, tab, T);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        // delta = r - 1 = T_c (Z G_c) - 1
-        const float4 g = p4[5 + c];
-        const c2f r = cd_mul(T[c], cd_mul(Z, {{g.x, g.y}, {g.z, g.w}}));
-        dl[c] = cd_norm({dd_add_f_lazy(r.re, -1.0f), r.im});
+        const float4 g = G4[c];
+        acc[c] = cd_add(acc[c], cd_mul(T[c], cd_mul(Z, {{g.x, g.y}, {g.z, g.w}})));
     }
+    return true;
+}
+
+// delta = r - 1 of one walker at one edge record of a (2,2) reference (Sec. II B, Eq. 10),
+// double-float; -1 where the walker's template or the reference's is zero.
+__device__ __forceinline__ void edge_delta_x(const XWalker& w, const XEdge* __restrict__ pe, f2 tob,
+                                             const SinTab& tab, c2f dl[3])
+{
+    const float4* p4 = reinterpret_cast<const float4*>(pe);
+    const float4 r0 = p4[0], r1 = p4[1], r2 = p4[2], r3 = p4[3], r4 = p4[4];
+    const f2 f = {r0.x, r0.y}, v0 = {r0.z, r0.w}, iv0 = {r1.x, r1.y}, lnv0 = {r1.z, r1.w};
+    const f2 t0 = {r2.x, r2.y}, ca0 = {r2.z, r2.w}, sa0 = {r3.x, r3.y}, x = {r3.z, r3.w};
+    const f2 s2 = {r4.x, r4.y}, c2 = {r4.z, r4.w};
+    c2f acc[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc[c] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
+    if (!group_term(w, w.Ga, w.Gb, f, f, v0, iv0, lnv0, 1.0f, t0, ca0, sa0, x, s2, c2, p4 + 5, tob, tab, acc)) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) dl[c] = {{-1.0f, 0.0f}, {0.0f, 0.0f}};   // h = 0: r = 0
+        return;
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) dl[c] = cd_norm({dd_add_f_lazy(acc[c].re, -1.0f), acc[c].im});
+}
+
+// Per group g = 0..3 (m = 2, 3, 4, 1): f2/f = 2/m, (2/m)^{1/3}, (m/2)^{1/3}, ln((2/m)^{1/3}), m/2
+__constant__ float kGrpHalfM[4] = {1.0f, 1.5f, 2.0f, 0.5f};
+__constant__ f2 kGrpR[4] = {df_const(1.0), df_const(2.0 / 3.0), df_const(0.5), df_const(2.0)};
+__constant__ f2 kGrpR3[4] = {df_const(1.0), df_const(0.87358046473629952), df_const(0.79370052598409974),
+                          df_const(1.2599210498948732)};
+__constant__ f2 kGrpRm3[4] = {df_const(1.0), df_const(1.1447142425533319), df_const(1.2599210498948732),
+                           df_const(0.79370052598409974)};
+__constant__ f2 kGrpLn3[4] = {df_const(0.0), df_const(-0.13515503603605479), df_const(-0.23104906018664842),
+                           df_const(0.23104906018664842)};
+
+// delta = r - 1 of one walker at one edge of a higher-mode reference (Sec. II B, Eq. 10, with the
+// template of Eq. 9 summed over the modes): r = sum over the reference's mode groups of the
+// group's share (group_term), the group's mode factors summed with v^{p_lm} = (s v0(f2))^{p_lm}.
+__device__ __forceinline__ void edge_delta_xhm(const XWalker& w, const XWalkerHM& wh, const XEdge* __restrict__ pe,
+                                               const XGrp* __restrict__ pg, uint32_t modes, f2 tob,
+                                               const SinTab& tab, c2f dl[3])
+{
+    const float4* p4 = reinterpret_cast<const float4*>(pe);
+    const float4 r0 = p4[0], r1 = p4[1], r3 = p4[3], r4 = p4[4];
+    const f2 f = {r0.x, r0.y}, v0 = {r0.z, r0.w}, iv0 = {r1.x, r1.y}, lnv0 = {r1.z, r1.w};
+    const f2 x = {r3.z, r3.w}, s2 = {r4.x, r4.y}, c2 = {r4.z, r4.w};
+    c2f acc[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc[c] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
+    bool any = false;
+#pragma unroll 1
+    for (int g = 0; g < 4; ++g) {
+        const uint32_t gmask = modes & hm_group_mask(g);
+        if (!gmask) continue;
+        const float4* q4 = reinterpret_cast<const float4*>(pg + g);
+        const float4 a = q4[0], b = q4[1];
+        const f2 t0 = {a.x, a.y}, ca0 = {a.z, a.w}, sa0 = {b.x, b.y};
+        const f2 v0m = dd_mul_lazy(v0, kGrpR3[g]), iv0m = dd_mul_lazy(iv0, kGrpRm3[g]);
+        const f2 lnv0m = dd_add_lazy(lnv0, kGrpLn3[g]), fm = dd_norm(dd_mul_lazy(f, kGrpR[g]));
+        // the group's mode factors: sum of v^{p_lm} (Ga, Gb)_lm, v = s v0(f2)
+        const f2 vm = dd_mul_lazy(w.s, v0m);
+        f2 G[4] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
+        for (uint32_t bm = gmask; bm; bm &= bm - 1) {
+            const int md = __ffs(bm) - 1;
+            const int pw = hm_vpow(md);
+            f2 vp = {1.0f, 0.0f};
+            for (int j = 0; j < pw; ++j) vp = dd_mul_lazy(vp, vm);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) G[j] = dd_add_lazy(G[j], dd_mul_lazy(vp, wh.G[md][j]));
+        }
+        // G4 of this group: float4 2, 3, 4 of the record are (G_A), (G_E), (G_T) after the 6
+        // floats of t0, ca0, sa0 and 2 of padding
+        any |= group_term(w, &G[0], &G[2], f, fm, v0m, iv0m, lnv0m, kGrpHalfM[g], t0, ca0, sa0, x, s2, c2, q4 + 2,
+                          tob, tab, acc);
+    }
+    if (!any) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) dl[c] = {{-1.0f, 0.0f}, {0.0f, 0.0f}};   // h = 0: r = 0
+        return;
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) dl[c] = cd_norm({dd_add_f_lazy(acc[c].re, -1.0f), acc[c].im});
 }
 
 // The edge's share of <d|h> and <h|h> (Eqs. 14 and 17 regrouped per edge, factor 4 included):
@@ -558,6 +663,77 @@ __global__ void __launch_bounds__(BLOCK) het_x_kernel(const __grid_constant__ He
     }
 }
 
+// Higher-mode references (Sec. II B with the template of Eq. 9): the layout of het_x_kernel, the
+// edge value from edge_delta_xhm (every edge double-float).
+template <int G, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) het_xhm_kernel(const __grid_constant__ HetLaunch L)
+{
+    constexpr int WPB = BLOCK / G;
+    __shared__ XWalker xw[WPB];
+    __shared__ XWalkerHM xh[WPB];
+    __shared__ SinTab tab;
+    const int lw = threadIdx.x / G, lane = threadIdx.x % G;
+    load_sintab(tab);
+    for (int tile = blockIdx.x; tile < L.n_tiles; tile += gridDim.x) {
+        int s = 0;
+        while (s + 1 < L.n_src && L.src[s + 1].tile_begin <= tile) ++s;
+        const SrcDesc& S = L.src[s];
+        const int64_t w0 = S.w_begin + (int64_t)(tile - S.tile_begin) * WPB;
+        const bool active = w0 + lw < S.w_end;
+        __syncthreads();
+        for (int j = threadIdx.x; j < WPB; j += BLOCK)
+            if (w0 + j < S.w_end) {
+                xwalker_setup(L.theta, L.W, w0 + j, *S.mix.xder, xw[j]);
+                xwalker_setup_hm(L.theta, L.W, w0 + j, xh[j]);
+            }
+        __syncthreads();
+        const int E = S.E;
+        const f2 tob = {S.tob_hi, S.tob_lo};
+        f2 adh = {0.0f, 0.0f}, ahh = {0.0f, 0.0f};
+        c2f carry[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) carry[c] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
+        const int rounds = (E + 1 + G - 1) / G;
+        for (int r = 0; r < rounds; ++r) {
+            const int e = r * G + lane;
+            c2f dl[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) dl[c] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
+            const bool ok = active && e <= E && MBH_IN_RANGE(L.status, e, (long long)S.E_check + 1, kKernHetX, s);
+            if (ok) edge_delta_xhm(xw[lw], xh[lw], S.mix.xedge + e, S.mix.xgrp + (int64_t)e * 4, S.modes, tob, tab, dl);
+            c2f dp[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                dp[c].re.hi = __shfl_up_sync(0xffffffffu, dl[c].re.hi, 1, G);
+                dp[c].re.lo = __shfl_up_sync(0xffffffffu, dl[c].re.lo, 1, G);
+                dp[c].im.hi = __shfl_up_sync(0xffffffffu, dl[c].im.hi, 1, G);
+                dp[c].im.lo = __shfl_up_sync(0xffffffffu, dl[c].im.lo, 1, G);
+                if (lane == 0) dp[c] = carry[c];
+                carry[c].re.hi = __shfl_sync(0xffffffffu, dl[c].re.hi, G - 1, G);
+                carry[c].re.lo = __shfl_sync(0xffffffffu, dl[c].re.lo, G - 1, G);
+                carry[c].im.hi = __shfl_sync(0xffffffffu, dl[c].im.hi, G - 1, G);
+                carry[c].im.lo = __shfl_sync(0xffffffffu, dl[c].im.lo, G - 1, G);
+            }
+            if (ok) contract_x(S.mix.xw + e, dp, dl, adh, ahh);
+        }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+            const f2 odh = {__shfl_down_sync(0xffffffffu, adh.hi, o, G), __shfl_down_sync(0xffffffffu, adh.lo, o, G)};
+            const f2 ohh = {__shfl_down_sync(0xffffffffu, ahh.hi, o, G), __shfl_down_sync(0xffffffffu, ahh.lo, o, G)};
+            df_acc(adh, odh);
+            df_acc(ahh, ohh);
+        }
+        if (lane == 0 && active) {
+            const int64_t wi = w0 + lw;
+            const double dh = S.mix.xsumA + df_to_double(adh);
+            const double hh = S.mix.xsumB + df_to_double(ahh);
+            L.out[wi] = -0.5 * (S.dd + hh - 2.0 * dh);
+            L.out[L.W + wi] = dh;
+            L.out[2 * L.W + wi] = hh;
+        }
+    }
+}
+
 // ------------------------------------------------------------------------------------------
 // reference tables
 // ------------------------------------------------------------------------------------------
@@ -623,6 +799,97 @@ __global__ void xedge_kernel(const double* __restrict__ theta0, const XDer* __re
             p[21 + 4 * c] = a.lo;
             p[22 + 4 * c] = b.hi;
             p[23 + 4 * c] = b.lo;
+        }
+        out[e] = m;
+    }
+}
+
+// Higher-mode reference: the edge records' shared part (f, v0, 1/v0, ln v0 at f, x, sin 2x,
+// cos 2x; the (2,2) slots t0, cos/sin alpha0 and G of group m = 2 are also filled) and per mode
+// group g (m = 2, 3, 4, 1) the group's t0(f2), orbit angle at it and
+//   G_gc = A0(f2) e^{-i Phi0_g(f)} K_c / h0_c,
+// float64: A0(f2) the reference's (2,2) amplitude at f2 = 2f/m, Phi0_g the group's large phase
+// ((m/2) times the (2,2) phase at f2, plus 2 pi f k0.c(t0(f2))), K_c the frequency-only factors
+// of the raw transfer and h0 the sum of the reference's modes; 0 where h0 = 0.
+__global__ void xedge_hm_kernel(const double* __restrict__ theta0, uint32_t modes, const XDer* __restrict__ xr,
+                                double t_obs, const double* __restrict__ fe, int n_edges, XEdge* __restrict__ out,
+                                XGrp* __restrict__ grp)
+{
+    __shared__ Walker w;
+    if (threadIdx.x == 0) walker_setup(theta0, 1, 0, w, modes);
+    __syncthreads();
+    const XDer& r = *xr;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_edges; e += gridDim.x * blockDim.x) {
+        const double f = fe[e];
+        const double x = kPi * kArmSec * f;
+        double s1, c1, s2x, c2x, s3, c3;
+        sincos(x, &s1, &c1);
+        sincos(2.0 * x, &s2x, &c2x);
+        sincos(3.0 * x, &s3, &c3);
+        const double wm = -2.0 * x * s2x;
+        const double wr = wm * s3, wi = wm * c3;
+        const double ar = 2.0 * s1 * s1, ai = 2.0 * s1 * c1;
+        const cd K[3] = {{wr / kSqrt2, wi / kSqrt2}, {wr / kSqrt6, wi / kSqrt6},
+                         {(wr * ar - wi * ai) / kSqrt3, (wr * ai + wi * ar) / kSqrt3}};
+        cd h0[3];
+        point_hm_f64(w, f, t_obs, h0);
+        XEdge m;
+        float* p = reinterpret_cast<float*>(&m);
+        for (int j = 0; j < 32; ++j) p[j] = 0.0f;
+        for (int g = 0; g < 4; ++g) {
+            float* q = reinterpret_cast<float*>(grp + (int64_t)e * 4 + g);
+            for (int j = 0; j < 20; ++j) q[j] = 0.0f;
+            const int mm = g == 0 ? 2 : g == 1 ? 3 : g == 2 ? 4 : 1;
+            const double f2v = 2.0 * f / mm;
+            const double v0 = cbrt(kPi * r.mt * kMsunSec * f2v), iv0 = 1.0 / v0, lnv0 = log(v0);
+            double Q = r.d[7];
+            for (int k = 6; k >= 0; --k) Q = fma(Q, v0, r.d[k]);
+            const double iv2 = iv0 * iv0, iv8 = iv2 * iv2 * iv2 * iv2;
+            const double t0 = Q * iv8 + r.dl6 * lnv0 * iv2 + r.t0;
+            double sa0, ca0;
+            sincos(kTwoPi * t0 / kYear, &sa0, &ca0);
+            if (g == 0) {   // shared part (at f: group m = 2)
+                const f2 vals[10] = {split_rn(f), split_rn(v0), split_rn(iv0), split_rn(lnv0), split_rn(t0),
+                                     split_rn(ca0), split_rn(sa0), split_rn(x), split_rn(s2x), split_rn(c2x)};
+                for (int j = 0; j < 10; ++j) {
+                    p[2 * j] = vals[j].hi;
+                    p[2 * j + 1] = vals[j].lo;
+                }
+            }
+            if (!(modes & hm_group_mask(g))) continue;
+            const f2 tv[3] = {split_rn(t0), split_rn(ca0), split_rn(sa0)};
+            for (int j = 0; j < 3; ++j) {
+                q[2 * j] = tv[j].hi;
+                q[2 * j + 1] = tv[j].lo;
+            }
+            // the reference's (2,2) amplitude at f2 and the group's phase, float64
+            const double vw = cbrt(w.piM * f2v);
+            double psi_pn, dpsi_pn;
+            pn_phase_f64(w, vw, log(vw), psi_pn, dpsi_pn);
+            const double tg = w.tref + (dpsi_pn - w.dpsi_max) * kInvTwoPi;
+            double sa, ca;
+            sincos(kTwoPi * tg / kYear, &sa, &ca);
+            const double kc = kAUSec * (w.k[0] * ca + w.k[1] * sa);
+            const double Phi = 0.5 * mm * (kTwoPi * f2v * w.tref + psi_pn - w.psi_max - (f2v - w.fmax) * w.dpsi_max) +
+                               kTwoPi * f * kc;
+            const double amp = w.amp * exp(-f2v * f2v * w.inv_fc2) / (vw * vw * vw * sqrt(vw));
+            double sP, cP;
+            sincos(Phi, &sP, &cP);
+            for (int c = 0; c < 3; ++c) {
+                const double m2 = h0[c].re * h0[c].re + h0[c].im * h0[c].im;
+                double gr = 0.0, gi = 0.0;
+                if (m2 > 0.0) {
+                    // amp e^{-i Phi} K_c / h0_c
+                    const double nr = amp * (cP * K[c].re + sP * K[c].im), ni = amp * (cP * K[c].im - sP * K[c].re);
+                    gr = (nr * h0[c].re + ni * h0[c].im) / m2;
+                    gi = (ni * h0[c].re - nr * h0[c].im) / m2;
+                }
+                const f2 a = split_rn(gr), b = split_rn(gi);
+                q[8 + 4 * c] = a.hi;
+                q[9 + 4 * c] = a.lo;
+                q[10 + 4 * c] = b.hi;
+                q[11 + 4 * c] = b.lo;
+            }
         }
         out[e] = m;
     }
@@ -737,6 +1004,39 @@ cudaError_t prepare_x_tables(mbh_ref* R, cudaStream_t st)
     return e;
 }
 
+// Tables of the extended-precision heterodyne for a higher-mode reference: XDer of theta0, the
+// edge records and the per-group records, the edge weights and the constant parts (every edge
+// double-float: no float32-ratio edges).
+cudaError_t prepare_x_tables_hm(mbh_ref* R, cudaStream_t st)
+{
+    const int E = R->E;
+    cudaError_t e = cudaMalloc(&R->x_der, sizeof(XDer));
+    if (e == cudaSuccess) e = cudaMalloc(&R->x_edge, sizeof(XEdge) * (E + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&R->x_grp, sizeof(XGrp) * 4 * (E + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&R->x_w, sizeof(XWeight) * (E + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&R->x_sums, sizeof(double) * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&R->x_sens, sizeof(double) * (E + 1));
+    if (e != cudaSuccess) return e;
+    xref_kernel<<<1, 32, 0, st>>>(R->theta0_dev, R->x_der);
+    xedge_hm_kernel<<<(E + 1 + 127) / 128, 128, 0, st>>>(R->theta0_dev, R->modes, R->x_der, R->grid.t_obs, R->fe,
+                                                         E + 1, R->x_edge, R->x_grp);
+    xweight_kernel<<<(E + 1 + 127) / 128, 128, 0, st>>>(R->summary, R->invw, E, R->x_w, R->x_sums, R->x_sens);
+    e = cudaGetLastError();
+    double sums[2];
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sums, R->x_sums, sizeof sums, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) {
+        R->mix.xder = R->x_der;
+        R->mix.xedge = R->x_edge;
+        R->mix.xgrp = R->x_grp;
+        R->mix.xw = R->x_w;
+        R->mix.xsumA = sums[0];
+        R->mix.xsumB = sums[1];
+        R->mix.xn32 = 0;
+    }
+    return e;
+}
+
 void free_x_tables(mbh_ref* R)
 {
     if (R->x_der) cudaFree(R->x_der);
@@ -744,6 +1044,7 @@ void free_x_tables(mbh_ref* R)
     if (R->x_w) cudaFree(R->x_w);
     if (R->x_sums) cudaFree(R->x_sums);
     if (R->x_sens) cudaFree(R->x_sens);
+    if (R->x_grp) cudaFree(R->x_grp);
 }
 
 }  // namespace mbh
@@ -755,6 +1056,13 @@ cudaError_t launch_het_x(const HetLaunch& L, int grid, cudaStream_t st)
     het_x_kernel<G, BLOCK><<<grid, BLOCK, 0, st>>>(L);
     return cudaGetLastError();
 }
+
+template <int G, int BLOCK>
+cudaError_t launch_het_xhm(const HetLaunch& L, int grid, cudaStream_t st)
+{
+    het_xhm_kernel<G, BLOCK><<<grid, BLOCK, 0, st>>>(L);
+    return cudaGetLastError();
+}
 }  // namespace
 
 namespace mbh {
@@ -762,6 +1070,22 @@ HetKernel het_kernel_x(int G, int block)
 {
 #define MBH_CASE(g, b) \
     if (G == g && block == b) return {&launch_het_x<g, b>, (const void*)&het_x_kernel<g, b>};
+    MBH_CASE(1, 64) MBH_CASE(1, 128) MBH_CASE(1, 256)
+    MBH_CASE(2, 64) MBH_CASE(2, 128) MBH_CASE(2, 256)
+    MBH_CASE(4, 64) MBH_CASE(4, 128) MBH_CASE(4, 256)
+    MBH_CASE(8, 64) MBH_CASE(8, 128) MBH_CASE(8, 256)
+    MBH_CASE(16, 64) MBH_CASE(16, 128) MBH_CASE(16, 256)
+    MBH_CASE(32, 64) MBH_CASE(32, 128) MBH_CASE(32, 256)
+#undef MBH_CASE
+    return {nullptr, nullptr};
+}
+}  // namespace mbh
+
+namespace mbh {
+HetKernel het_kernel_xhm(int G, int block)
+{
+#define MBH_CASE(g, b) \
+    if (G == g && block == b) return {&launch_het_xhm<g, b>, (const void*)&het_xhm_kernel<g, b>};
     MBH_CASE(1, 64) MBH_CASE(1, 128) MBH_CASE(1, 256)
     MBH_CASE(2, 64) MBH_CASE(2, 128) MBH_CASE(2, 256)
     MBH_CASE(4, 64) MBH_CASE(4, 128) MBH_CASE(4, 256)

@@ -67,6 +67,12 @@ struct alignas(16) XEdge {
 struct alignas(16) XWeight {
     float v[32];
 };
+// Per (edge, mode group) record of a higher-mode reference (5 x 128-bit loads): the group's
+// t0(f2) and orbit angle (cos, sin) as float pairs, and per channel G_gc = A0(f2) e^{-i Phi0_g}
+// K_c / h0_c (complex float pairs), 0 where h0 = 0; group g = 0..3 holds m = 2, 3, 4, 1.
+struct alignas(16) XGrp {
+    float v[20];
+};
 
 struct MixTables {
     const MixEdge* edge;   // [E+1]
@@ -79,6 +85,7 @@ struct MixTables {
     const XDer* xder;      // extended precision: the reference's float64 constants
     const XEdge* xedge;    // [E+1]
     const XWeight* xw;     // [E+1]
+    const XGrp* xgrp;      // [E+1][4] higher-mode references
     double xsumA, xsumB;   // 4 sum Re A0, 4 sum B0
     int32_t xn32;          // edges that take the float32 ratio (flagged in their XWeight)
 };
@@ -182,7 +189,9 @@ HetKernel het_kernel_mixed(int G, int block);
 HetKernel het_kernel_mixed_hm(int G, int block);
 HetKernel het_kernel_mixed_pt(int G, int block);
 HetKernel het_kernel_x(int G, int block);
+HetKernel het_kernel_xhm(int G, int block);
 cudaError_t prepare_x_tables(mbh_ref* R, cudaStream_t st);
+cudaError_t prepare_x_tables_hm(mbh_ref* R, cudaStream_t st);
 void free_x_tables(mbh_ref* R);
 mbh_status het_launch_fused_pt(const mbh_ref* const* refs, int n_ens, int64_t M, const mbh_het_config& cfg,
                                const void* pt_dev, int half, cudaStream_t st);
@@ -264,5 +273,6 @@ struct mbh_ref {
     mbh::XWeight* x_w = nullptr;
     double* x_sums = nullptr;
     double* x_sens = nullptr;           // [E+1] per-edge sensitivity of lnL to delta
+    mbh::XGrp* x_grp = nullptr;         // higher-mode references: [E+1][4]
     mbh::MixTables mix{};
 };

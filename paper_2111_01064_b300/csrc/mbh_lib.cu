@@ -754,7 +754,7 @@ extern "C" mbh_status het_prepare_reference_hm(const mbh_data* data, const doubl
     edge_ref_kernel<<<1, 256, 0, st>>>(R->theta0_dev, g.t_obs, R->fe, E + 1, modes, R->h0e, R->h0inv);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = prepare_mixed_tables(R, st);
-    if (e == cudaSuccess && modes == 1u) e = prepare_x_tables(R, st);
+    if (e == cudaSuccess) e = modes == 1u ? prepare_x_tables(R, st) : prepare_x_tables_hm(R, st);
     if (e == cudaSuccess) e = cudaFreeAsync(d_items, st);
     if (e == cudaSuccess) e = cudaFreeAsync(d_ib, st);
     if (e == cudaSuccess) e = cudaFreeAsync(d_fb, st);

@@ -98,6 +98,7 @@ mbh_status make_plan(const mbh_ref* const* refs, const int64_t* offsets, int32_t
         if (order.empty()) continue;
         const bool f32_22 = prec == MBH_MIXED_F32 && group == 0;
         const bool x22 = prec == MBH_MIXED && group == 0;
+        const bool xhm = prec == MBH_MIXED && group == 1;
         int64_t wg = 0;
         for (int32_t s : order) wg += offsets[s + 1] - offsets[s];
         const int block = cfg.block ? cfg.block
@@ -105,6 +106,7 @@ mbh_status make_plan(const mbh_ref* const* refs, const int64_t* offsets, int32_t
         const int wpb = block / cfg.threads_per_walker;
         const HetKernel kernel = prec == MBH_FP64 ? het_kernel_f64(cfg.threads_per_walker, block)
                                  : x22            ? het_kernel_x(cfg.threads_per_walker, block)
+                                 : xhm            ? het_kernel_xhm(cfg.threads_per_walker, block)
                                  : f32_22         ? het_kernel_mixed(cfg.threads_per_walker, block)
                                                   : het_kernel_mixed_hm(cfg.threads_per_walker, block);
         if (!kernel.launch) return fail(MBH_EINVAL, "no kernel for this configuration");
@@ -184,7 +186,8 @@ bool plan_has_kernels(const mbh_ref* const* refs, int32_t n_src, mbh_precision p
 {
     for (int32_t s = 0; s < n_src; ++s) {
         const HetKernel k = prec == MBH_FP64    ? het_kernel_f64(c.threads_per_walker, c.block)
-                            : refs[s]->modes != 1u ? het_kernel_mixed_hm(c.threads_per_walker, c.block)
+                            : refs[s]->modes != 1u ? (prec == MBH_MIXED ? het_kernel_xhm(c.threads_per_walker, c.block)
+                                                                        : het_kernel_mixed_hm(c.threads_per_walker, c.block))
                             : prec == MBH_MIXED    ? het_kernel_x(c.threads_per_walker, c.block)
                                                    : het_kernel_mixed(c.threads_per_walker, c.block);
         if (!k.launch) return false;
