@@ -91,17 +91,20 @@ def fma_peak_tinst(sm_mhz: float) -> float:
 # Work per unit of the ALU-bound kernels, counted by ncu (sm__inst_executed_pipe_fma /
 # _fp64 thread instructions of one launch divided by the units it processed; the profile
 # summaries name the launches):
-#  - het_x_kernel<4,128> (MBH_MIXED heterodyne): FMA-pipe instructions per edge evaluation
-#    (double-float phase/time differences, orbit, response, ratio, per-edge contraction);
-#  - direct_fused_mixed_kernel<8>: FMA-pipe instructions per (template, grid point);
+#  - het_x_kernel<4,256> (MBH_MIXED heterodyne): FMA-pipe instructions per edge evaluation
+#    (double-float phase/time differences, orbit, response, ratio, per-edge contraction).
+#    On workload 2 (SNR 122) 133 of the 257 edges take the float32 ratio and 124 the
+#    double-float chain: 1667 FMA-pipe instructions per edge on average (2536 with every edge
+#    double-float);
+#  - het_xhm_kernel<4,128> (MBH_MIXED, six modes, the higher-mode leg's batch): 5606 per edge;
+#  - direct_fused_mixed_kernel<8>: FMA-pipe instructions per (template, grid point), from a
+#    512-template launch (the 4096-template batch's block shape);
 #  - direct_fused_f64_kernel<4>: FP64-pipe instructions per (template, grid point).
-#    On workload 2 (SNR 122) 110 of the 257 edges take the float32 ratio and 147 the
-#    double-float chain: 1783 FMA-pipe instructions per edge on average (2536 with every edge
-#    double-float).
-HET_KERNEL = "het_x_kernel<4,128>"
-HET_X_FMA_INST_PER_EDGE = 1783.2
-HET_X_DRAM_BYTES = 1.678e6                 # read + write per 16384-walker launch (ncu)
-FUSED_MIXED_FMA_INST_PER_POINT = 426.7
+HET_KERNEL = "het_x_kernel<4,256>"
+HET_X_FMA_INST_PER_EDGE = 1667.1
+HET_X_DRAM_BYTES = 1.679e6                 # read + write per 16384-walker launch (ncu)
+HET_XHM_FMA_INST_PER_EDGE = 5605.8
+FUSED_MIXED_FMA_INST_PER_POINT = 471.9
 FUSED_F64_DFMA_INST_PER_POINT = 590.5
 STORED_DATA_BYTES = 75.74e6                # data pairs, read once per launch (ncu: 883.66 MB
 STORED_BYTES_PER_TEMPLATE = 50.4945e6      # for 16 templates = 75.74 MB + 16 x 50.49 MB)
@@ -438,7 +441,8 @@ def run_ours(args) -> dict | None:
                 "not available)",
         "config": {"workload": WORKLOAD, "walkers": nw, "temperatures": W_TEMPS,
                    "bins_requested": N_BINS, "bins": E, "channels": 3, "grid_points": n,
-                   "precision": args.het_precision, "l2": "flushed between steps (512 MiB write, outside the "
+                   "precision": args.het_precision, "float32_ratio_edges": ref.f32_edges,
+                   "l2": "flushed between steps (512 MiB write, outside the "
                    "timed events)", "parallelism": f"walker batches per rank x{ws}"},
         "gpu_launches": args.steps * 1,
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
@@ -480,6 +484,13 @@ def run_ours(args) -> dict | None:
                                   "sampled during the run)",
                      "inst_per_edge": HET_X_FMA_INST_PER_EDGE,
                      "ps_per_edge_evaluation": ms_per_step * 1e9 / (nw * (E + 1))},
+        "roofline_higher_modes": None if not higher_modes else {
+            "bound": "alu", "pipe": "fp32 (FMA pipe)", "peak": fma_peak, "unit": "T fp32-pipe inst/s",
+            "achieved": HET_XHM_FMA_INST_PER_EDGE * higher_modes["walkers"] * (higher_modes["bins"] + 1)
+            / (higher_modes["mixed"]["ms"] * 1e-3) / 1e12,
+            "frac": HET_XHM_FMA_INST_PER_EDGE * higher_modes["walkers"] * (higher_modes["bins"] + 1)
+            / (higher_modes["mixed"]["ms"] * 1e-3) / 1e12 / fma_peak,
+            "traffic": None, "kernel": "het_xhm_kernel<4,128>", "inst_per_edge": HET_XHM_FMA_INST_PER_EDGE},
         "roofline_fused_mixed": {"bound": "alu", "pipe": "fp32 (FMA pipe)", "achieved": fused_mixed_tinst,
                                  "peak": fma_peak, "unit": "T fp32-pipe inst/s",
                                  "frac": fused_mixed_tinst / fma_peak, "traffic": None,
@@ -553,7 +564,7 @@ def run_snr1000(M, WL, g, stream, flush, reps: int = 20) -> dict:
     nw = N_WALKERS
     theta = WL.to_dev(WL.walkers(src.theta_inj, nw, 2))
     out = torch.empty((3, nw), dtype=torch.float64, device="cuda")
-    res = {"snr": 1000.0, "walkers": nw, "bins": ref.bins}
+    res = {"snr": 1000.0, "walkers": nw, "bins": ref.bins, "float32_ratio_edges": ref.f32_edges}
     outs = {}
     for prec, n in (("mixed", reps), ("mixed_f32", reps), ("fp64", 3)):
         ms = _time_launches(lambda: M.het_loglike_batch([ref], [0, nw], theta, prec, out=out), stream, n, flush)
@@ -705,7 +716,7 @@ def run_higher_modes(M, WL, g, stream, reps: int = 5) -> dict:
     out = torch.empty((3, nw), dtype=torch.float64, device="cuda")
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     res = {"modes": "(2,2) (3,3) (4,4) (2,1) (3,2) (4,3)", "walkers": nw, "bins": ref.bins,
-           "q": float(th[I.I_Q])}
+           "q": float(th[I.I_Q]), "float32_ratio_edges": ref.f32_edges}
     outs = {}
     for prec, n in (("mixed", reps), ("mixed_f32", reps), ("fp64", 1)):
         M.het_loglike_batch([ref], [0, nw], theta, prec, out=out)

@@ -69,12 +69,14 @@ typedef enum {
                           2 pi f k.c) in double-float (two floats, ~48 bits), t(f) in float32
                           with a rounding bound (double-float near the support bounds),
                           amplitude and response in float32, sums in float64.
-                          Heterodyne, (2,2) references: every edge value formed relative to
-                          the reference in double-float (phase, time and amplitude as
-                          differences of per-walker float64 coefficients, the response, the
-                          ratio delta = r - 1 and the contraction), |dlnL| against float64
-                          <= 1e-3 up to SNR ~1000.  Heterodyne, higher modes: as
-                          MBH_MIXED_F32. */
+                          Heterodyne: every edge value formed relative to the reference in
+                          double-float (phase, time and amplitude as differences of
+                          per-walker float64 coefficients, the response, the ratio
+                          delta = r - 1 and the contraction; with higher modes per group of
+                          modes sharing m), except on edges of small contraction weight
+                          (mbh_ref_f32_edges), which take the MBH_MIXED_F32 ratio within an
+                          error budget of 1e-4 in lnL while |delta| <= 16; |dlnL| against
+                          float64 <= 1e-3 up to SNR ~1000. */
     MBH_MIXED_F32 = 2  /* heterodyne only: double-float phase difference, float32 response,
                           ratio delta = r - 1 and per-bin products, double-float sums.  About
                           3x faster than MBH_MIXED; its |dlnL| grows with <h|h> (~1e-3 at
@@ -199,6 +201,10 @@ MBH_API mbh_status het_prepare_reference(const mbh_data* data, const double* the
 MBH_API int32_t mbh_ref_bins(const mbh_ref* ref);
 /* Mode mask the reference was prepared with (see the higher-harmonic calls). */
 MBH_API uint32_t mbh_ref_modes(const mbh_ref* ref);
+/* Edges (of the E + 1) that MBH_MIXED evaluates with the float32 ratio instead of the
+ * double-float chain: the per-edge precision choice made at prepare from the contraction
+ * weights (Eqs. 14 and 17 regrouped per edge), see MBH_MIXED.  -1 for a NULL reference. */
+MBH_API int32_t mbh_ref_f32_edges(const mbh_ref* ref);
 /* Copies (host, blocking): edges int64 [E+1]; summary float64 [E][3][6] =
  * Re A0, Im A0, Re A1, Im A1, B0, B1; h0 at the edges complex128 [E+1][3];
  * any pointer may be NULL. */

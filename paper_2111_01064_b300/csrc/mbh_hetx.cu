@@ -73,10 +73,21 @@ __device__ __forceinline__ f2 split_rn(double x)
 // kF32EdgeError for |delta| <= kDeltaMax; with S_e >= |d lnL / d delta_e| the float32 edges add
 // at most kF32EdgeError sum S_e <= kF32Budget to |dlnL|.  kF32EdgeError is ten times the largest
 // error per unit of sensitivity that the float32 ratio shows with every edge in float32 (its
-// batch maximum |dlnL| over sum S_e: 1.4e-8 to 2.8e-8 on sources of SNR 122 to 1000).
+// batch maximum |dlnL| over sum S_e: 1.4e-8 to 2.8e-8 on sources of SNR 122 to 1000, whose
+// walkers reach |delta| ~ 4).  The float32 error grows with |1 + delta| and the sensitivity with
+// |delta|: a walker's float32 value is kept while every channel has |delta| <= kDeltaF32Max,
+// where the product is at most 18 times its value at |delta| = 4 (5e-7 per unit of S_e, so the
+// float32 edges add at most 1.7e-4 to |dlnL|); beyond that the edge takes the double-float
+// chain.  With higher modes the float32 terms are the modes' shares u_g = h0_g/h0 of the
+// reference, so near a zero of h0 (modes that cancel) the error grows by kappa = sum |u_g|:
+// the selection weighs S_e by kappa_e.  Edges are chosen in aligned groups of kF32Group: with
+// four threads per walker (the default) a group is one round of a warp's edges, so no warp
+// runs both paths for one round.
 constexpr double kDeltaMax = 3.0;
 constexpr double kF32EdgeError = 3e-7;
 constexpr double kF32Budget = 1e-4;
+constexpr float kDeltaF32Max = 16.0f;
+constexpr int kF32Group = 4;
 
 __device__ __forceinline__ void load_sintab(SinTab& tab)
 {
@@ -285,6 +296,8 @@ __device__ inline void xwalker_setup(const double* __restrict__ theta, int64_t W
 #define MBH_X_OUTLINE __noinline__
 
 constexpr f2 kH3 = df_const(0.8660254037844386467637231707529361835);   // sqrt3/2
+constexpr f2 kH3q = df_const(0.8660254037844386467637231707529361835 / 4.0);   // sqrt3/8
+constexpr f2 kH3x3q = df_const(0.8660254037844386467637231707529361835 * 0.75);   // 3 sqrt3/8
 constexpr f2 kOrbRate = df_const(6.283185307179586476925286766559005768 / 31557600.0);   // 2 pi / yr
 
 // sin(x(1 - kn)) and sinc(x(1 + kn)) - sinc(x(1 - kn)) of one arm (the one-link sinc factors
@@ -362,24 +375,23 @@ __device__ MBH_X_OUTLINE ArmOut arm_df(const XWalker& w, const f2* Ga, const f2*
 //   and z = g [sinc(x(1+kn)) - sinc(x(1-kn))],
 //   P_A = U - z0, Q_A = U - z1, U = 2 yf2 + z2 - yf1 - yf0,
 //   P_E = V + z0 + z2 - 2 z1, Q_E = V + 2 z0 - z2 - z1, V = 3 (yf0 - yf1).
-// Ga, Gb: the mode factors (the walker's (2,2) ones, or a higher-mode group's sum).
+// T is linear in (Ga, Gb): the mode factors (the walker's (2,2) ones, or a higher-mode group's
+// sum), here already multiplied by the amplitude and phase factor A e^{-i dPhi}.
 __device__ inline void transfer_df(const XWalker& w, const f2* Ga, const f2* Gb, f2 x, f2 s2, f2 c2, f2 sa, f2 ca,
                                    const SinTab& tab, c2f T[3])
 {
-    const f2 h3s = dd_mul_lazy(kH3, sa), h3c = dd_mul_lazy(kH3, ca);
-    const f2 hs = dd_scale(sa, 0.5f), hc = dd_scale(ca, 0.5f);
-    const f2 sp[3] = {sa, dd_sub_lazy({-hs.hi, -hs.lo}, h3c), dd_add_lazy({-hs.hi, -hs.lo}, h3c)};
-    const f2 cp[3] = {ca, dd_add_lazy({-hc.hi, -hc.lo}, h3s), dd_sub_lazy({-hc.hi, -hc.lo}, h3s)};
-    f2 u[3][3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        const f2 a0 = dd_mul_lazy(sp[i], sa), b0 = dd_mul_lazy(cp[i], hc);
-        u[i][0] = {-(a0.hi), -(a0.lo)};
-        u[i][0] = dd_sub_lazy(u[i][0], b0);
-        u[i][1] = dd_sub_lazy(dd_mul_lazy(sp[i], ca), dd_mul_lazy(cp[i], hs));
-        const f2 z = dd_mul_lazy(kH3, cp[i]);
-        u[i][2] = {-z.hi, -z.lo};
-    }
+    // spacecraft offsets from the double angle: with C = cos 2a, S = sin 2a, b_i = 2 pi i/3,
+    //   u_i = ((cos(2a - b_i) - 3 cos b_i)/4, (sin(2a - b_i) - 3 sin b_i)/4, -h3 cos(a - b_i))
+    const f2 S = dd_scale(dd_mul_lazy(sa, ca), 2.0f);
+    const f2 C = dd_sub_lazy(dd_sqr_lazy(ca), dd_sqr_lazy(sa));
+    const f2 hS = dd_mul_lazy(kH3q, S), hC = dd_mul_lazy(kH3q, C);   // (h3/4) S, (h3/4) C
+    const f2 x0 = dd_add_f_lazy(dd_scale(C, -0.125f), 0.375f);       // (3 - C)/8
+    const f2 y0 = dd_add_lazy(hC, kH3x3q);                            // (h3/4) C + 3 h3/4
+    const f2 sq = dd_scale(S, -0.125f);                               // -S/8
+    const f2 hca = dd_mul_lazy(kH3, ca), hca2 = dd_scale(hca, 0.5f), sa3 = dd_mul_f_lazy(sa, 0.75f);
+    const f2 u[3][3] = {{dd_add_f_lazy(dd_scale(C, 0.25f), -0.75f), dd_scale(S, 0.25f), {-hca.hi, -hca.lo}},
+                        {dd_add_lazy(x0, hS), dd_sub_lazy(sq, y0), dd_sub_lazy(hca2, sa3)},
+                        {dd_sub_lazy(x0, hS), dd_add_lazy(sq, y0), dd_add_lazy(hca2, sa3)}};
     f2 kap[3];
 #pragma unroll
     for (int m = 0; m < 2; ++m)
@@ -418,13 +430,14 @@ __device__ inline void transfer_df(const XWalker& w, const f2* Ga, const f2* Gb,
     T[2] = cd_add(cd_add(z[0], z[1]), z[2]);
 }
 
-// One mode group's share of r = h/h0 at an edge (Sec. II B, Eq. 10), double-float: adds
-// T_c (A e^{-i dPhi} G_c) to acc[c] (c = A, E, T) and returns false, adding nothing, outside the
-// walker's support (f2 > f_cut or t outside [0, t_obs]).  The group's modes share f2 = 2f/m,
+// One mode group's share of r = h/h0 at an edge (Sec. II B, Eq. 10), double-float: T_c G_c
+// (c = A, E, T) with T_c the raw transfer of the mode factors times A e^{-i dPhi}, added to
+// acc[c] (kAdd) or stored there; returns false, leaving acc unchanged, outside the walker's support (f2 > f_cut or t outside [0, t_obs]).  The group's modes share f2 = 2f/m,
 // the phase chain (scaled by m/2), t(f2) and the orbit; the (2,2) mode alone is one group with
 // m = 2.  v0, 1/v0, ln v0 are the reference's at f2; t0, (ca0, sa0) its time and orbit angle
 // at f2; G4: the record's three G_c as float4 (re hi, re lo, im hi, im lo); Ga, Gb the mode
 // factors (summed over the group's modes with their v^{p_lm}).
+template <bool kAdd>
 __device__ __forceinline__ bool group_term(const XWalker& w, const f2* Ga, const f2* Gb, f2 f, f2 fm, f2 v0, f2 iv0,
                                            f2 lnv0, float half_m, f2 t0, f2 ca0, f2 sa0, f2 x, f2 s2, f2 c2,
                                            const float4* G4, f2 tob, const SinTab& tab, c2f acc[3])
@@ -458,16 +471,19 @@ __device__ __forceinline__ bool group_term(const XWalker& w, const f2* Ga, const
     const f2 dphi = dd_norm(dd_add_lazy(dd_mul_lazy(f, dd_add_lazy(w.C1, dorb)), dpsi));
     const SinCos ph = sincos_df(dphi, tab);
     // amplitude ratio A = R exp(-f2^2 (1/fc^2 - 1/fc0^2)), folded with e^{-i dPhi}:
-    // Z = A e^{-i dPhi} = A + A (e^{-i dPhi} - 1)
+    // Z = A e^{-i dPhi} = A + A (e^{-i dPhi} - 1), and Z into the mode factors
     const f2 u = dd_mul_lazy(dd_sqr_lazy(fm), w.difc2);
     const f2 A = dd_mul_lazy(w.R, dd_exp({-u.hi, -u.lo}));
     const c2f Z = {dd_add_lazy(A, dd_mul_lazy(A, ph.cm1)), dd_mul_lazy(A, {-ph.s.hi, -ph.s.lo})};
+    const c2f za = cd_mul(Z, {Ga[0], Ga[1]}), zb = cd_mul(Z, {Gb[0], Gb[1]});
+    const f2 zGa[2] = {za.re, za.im}, zGb[2] = {zb.re, zb.im};
     c2f T[3];
-    transfer_df(w, Ga, Gb, x, s2, c2, sa, ca, tab, T);
+    transfer_df(w, zGa, zGb, x, s2, c2, sa, ca, tab, T);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const float4 g = G4[c];
-        acc[c] = cd_add(acc[c], cd_mul(T[c], cd_mul(Z, {{g.x, g.y}, {g.z, g.w}})));
+        const c2f p = cd_mul(T[c], {{g.x, g.y}, {g.z, g.w}});
+        acc[c] = kAdd ? cd_add(acc[c], p) : p;
     }
     return true;
 }
@@ -485,7 +501,7 @@ __device__ __forceinline__ void edge_delta_x(const XWalker& w, const XEdge* __re
     c2f acc[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) acc[c] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
-    if (!group_term(w, w.Ga, w.Gb, f, f, v0, iv0, lnv0, 1.0f, t0, ca0, sa0, x, s2, c2, p4 + 5, tob, tab, acc)) {
+    if (!group_term<false>(w, w.Ga, w.Gb, f, f, v0, iv0, lnv0, 1.0f, t0, ca0, sa0, x, s2, c2, p4 + 5, tob, tab, acc)) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) dl[c] = {{-1.0f, 0.0f}, {0.0f, 0.0f}};   // h = 0: r = 0
         return;
@@ -541,7 +557,7 @@ __device__ __forceinline__ void edge_delta_xhm(const XWalker& w, const XWalkerHM
         }
         // G4 of this group: float4 2, 3, 4 of the record are (G_A), (G_E), (G_T) after the 6
         // floats of t0, ca0, sa0 and 2 of padding
-        any |= group_term(w, &G[0], &G[2], f, fm, v0m, iv0m, lnv0m, kGrpHalfM[g], t0, ca0, sa0, x, s2, c2, q4 + 2,
+        any |= group_term<true>(w, &G[0], &G[2], f, fm, v0m, iv0m, lnv0m, kGrpHalfM[g], t0, ca0, sa0, x, s2, c2, q4 + 2,
                           tob, tab, acc);
     }
     if (!any) {
@@ -577,6 +593,25 @@ __device__ __forceinline__ void contract_x(const XWeight* __restrict__ pw, const
     df_acc(ahh, shh);
 }
 
+// The float32 value of an edge is kept while every channel has |delta| <= kDeltaF32Max.
+__device__ __forceinline__ bool f32_edge_small(const cf d[3])
+{
+    bool ok = true;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) ok &= d[c].re * d[c].re + d[c].im * d[c].im <= kDeltaF32Max * kDeltaF32Max;
+    return ok;
+}
+
+// A float32-ratio edge value as double-float, with the rounding of the float32 amplitude
+// factors removed: that rounding scales every float32 ratio of the walker alike (r' = r / fix,
+// amp_fix), so delta = (1 + d) fix - 1 = d + eta (1 + d) with eta = fix - 1 (~1e-7).
+__device__ __forceinline__ void f32_edge_df(const cf d[3], float eta, c2f dl[3])
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        dl[c] = {dd_add_f_lazy({d[c].re, 0.0f}, eta * (1.0f + d[c].re)), dd_add_f_lazy({d[c].im, 0.0f}, eta * d[c].im)};
+}
+
 // ------------------------------------------------------------------------------------------
 // the kernel: layout and reductions as the float32 path's het_mixed_kernel (tiles of BLOCK/G
 // walkers of one source, G threads per walker dealing the edges round-robin, the previous
@@ -589,6 +624,7 @@ __global__ void __launch_bounds__(BLOCK) het_x_kernel(const __grid_constant__ He
     __shared__ XWalker xw[WPB];
     __shared__ WalkerDF wsd[WPB];   // float32-ratio edges: the float32 path's walker constants
     __shared__ WalkerF wsf[WPB];
+    __shared__ float eta32[WPB];    // and its amplitude rounding (f32_edge_df)
     __shared__ SinTab tab;
     const int lw = threadIdx.x / G, lane = threadIdx.x % G;
     load_sintab(tab);
@@ -602,7 +638,10 @@ __global__ void __launch_bounds__(BLOCK) het_x_kernel(const __grid_constant__ He
         for (int j = threadIdx.x; j < WPB; j += BLOCK)
             if (w0 + j < S.w_end) {
                 xwalker_setup(L.theta, L.W, w0 + j, *S.mix.xder, xw[j]);
-                if (S.mix.xn32 > 0) walker_setup_mixed(L.theta, L.W, w0 + j, wsd[j], wsf[j]);
+                if (S.mix.xn32 > 0) {
+                    walker_setup_mixed(L.theta, L.W, w0 + j, wsd[j], wsf[j]);
+                    eta32[j] = (float)(amp_fix(wsf[j].eps_amp76, S.mix.amp_eps0) - 1.0);
+                }
             }
         __syncthreads();
         const int E = S.E;
@@ -621,14 +660,16 @@ __global__ void __launch_bounds__(BLOCK) het_x_kernel(const __grid_constant__ He
             // check is recorded in the status word and the edge skipped)
             const bool ok = active && e <= E && MBH_IN_RANGE(L.status, e, (long long)S.E_check + 1, kKernHetX, s);
             if (ok) {
+                bool done = false;
                 if (S.mix.xw[e].v[30] != 0.0f) {   // low-weight edge: float32 ratio
                     cf d32[3];
                     edge_delta_mixed(wsd[lw], wsf[lw], S.mix.edge + e, tob, d32);
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) dl[c] = {{d32[c].re, 0.0f}, {d32[c].im, 0.0f}};
-                } else {
-                    edge_delta_x(xw[lw], S.mix.xedge + e, tob, tab, dl);
+                    if (f32_edge_small(d32)) {
+                        f32_edge_df(d32, eta32[lw], dl);
+                        done = true;
+                    }
                 }
+                if (!done) edge_delta_x(xw[lw], S.mix.xedge + e, tob, tab, dl);
             }
             c2f dp[3];
 #pragma unroll
@@ -664,13 +705,18 @@ __global__ void __launch_bounds__(BLOCK) het_x_kernel(const __grid_constant__ He
 }
 
 // Higher-mode references (Sec. II B with the template of Eq. 9): the layout of het_x_kernel, the
-// edge value from edge_delta_xhm (every edge double-float).
+// edge value from edge_delta_xhm (double-float) or, on the edges flagged for it, the float32
+// ratio of the float32 higher-mode path (edge_delta_mixed_hm).
 template <int G, int BLOCK>
 __global__ void __launch_bounds__(BLOCK) het_xhm_kernel(const __grid_constant__ HetLaunch L)
 {
     constexpr int WPB = BLOCK / G;
     __shared__ XWalker xw[WPB];
     __shared__ XWalkerHM xh[WPB];
+    __shared__ WalkerDF wsd[WPB];   // float32-ratio edges: the float32 path's walker constants
+    __shared__ WalkerF wsf[WPB];
+    __shared__ WalkerHMF wsh[WPB];
+    __shared__ float eta32[WPB];
     __shared__ SinTab tab;
     const int lw = threadIdx.x / G, lane = threadIdx.x % G;
     load_sintab(tab);
@@ -685,6 +731,11 @@ __global__ void __launch_bounds__(BLOCK) het_xhm_kernel(const __grid_constant__ 
             if (w0 + j < S.w_end) {
                 xwalker_setup(L.theta, L.W, w0 + j, *S.mix.xder, xw[j]);
                 xwalker_setup_hm(L.theta, L.W, w0 + j, xh[j]);
+                if (S.mix.xn32 > 0) {
+                    walker_setup_mixed(L.theta, L.W, w0 + j, wsd[j], wsf[j]);
+                    walker_setup_hm(L.theta, L.W, w0 + j, wsh[j]);
+                    eta32[j] = (float)(amp_fix(wsf[j].eps_amp76, S.mix.amp_eps0) - 1.0);
+                }
             }
         __syncthreads();
         const int E = S.E;
@@ -700,7 +751,20 @@ __global__ void __launch_bounds__(BLOCK) het_xhm_kernel(const __grid_constant__ 
 #pragma unroll
             for (int c = 0; c < 3; ++c) dl[c] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
             const bool ok = active && e <= E && MBH_IN_RANGE(L.status, e, (long long)S.E_check + 1, kKernHetX, s);
-            if (ok) edge_delta_xhm(xw[lw], xh[lw], S.mix.xedge + e, S.mix.xgrp + (int64_t)e * 4, S.modes, tob, tab, dl);
+            if (ok) {
+                bool done = false;
+                if (S.mix.xw[e].v[30] != 0.0f) {   // low-weight edge: float32 ratio
+                    cf d32[3];
+                    edge_delta_mixed_hm(wsd[lw], wsf[lw], wsh[lw], S.mix, e, S.modes, tob, d32);
+                    if (f32_edge_small(d32)) {
+                        f32_edge_df(d32, eta32[lw], dl);
+                        done = true;
+                    }
+                }
+                if (!done)
+                    edge_delta_xhm(xw[lw], xh[lw], S.mix.xedge + e, S.mix.xgrp + (int64_t)e * 4, S.modes, tob, tab,
+                                   dl);
+            }
             c2f dp[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -934,9 +998,13 @@ __global__ void xweight_kernel(const double* __restrict__ summary, const double*
             const f2 cc = split_rn(4.0 * wc);
             p[24 + 2 * c] = cc.hi;
             p[25 + 2 * c] = cc.lo;
-            // |d lnL / d delta| bound for |delta|, |delta_prev| <= kDeltaMax: the linear weights,
-            // 2 kDeltaMax |wq| and kDeltaMax |wc| (lnL = <d|h> - <h|h>/2 + const)
-            S += 4.0 * (fabs(war) + fabs(wai) + 0.5 * fabs(wbr) + kDeltaMax * fabs(wq) + 0.5 * kDeltaMax * fabs(wc));
+            // |d lnL / d delta| bound for |delta| and its neighbours' <= kDeltaMax (lnL = <d|h> -
+            // <h|h>/2 + const): the linear weights, 2 kDeltaMax |wq|, kDeltaMax |wc| (the cross
+            // term with the previous edge) and kDeltaMax |wcn|, the next edge's cross term with
+            // this one (its wc: 0.5 B0 of bin e)
+            const double wcn = e < E ? 0.5 * summary[((int64_t)e * 3 + c) * 6 + 4] : 0.0;
+            S += 4.0 * (fabs(war) + fabs(wai) + 0.5 * fabs(wbr) + kDeltaMax * fabs(wq) +
+                        0.5 * kDeltaMax * (fabs(wc) + fabs(wcn)));
         }
         out[e] = m;
         sens[e] = S;
@@ -953,41 +1021,36 @@ __global__ void xweight_kernel(const double* __restrict__ summary, const double*
     }
 }
 
-// Tables of the extended-precision heterodyne for a (2,2) reference: XDer of theta0, edge
-// records, edge weights and the constant parts (read back to the host into R->mix), and the
-// edges that take the float32 ratio: the least sensitive ones, in ascending order of their
-// sensitivity S_e, while kF32EdgeError x (sum of their S_e) stays within kF32Budget.
-cudaError_t prepare_x_tables(mbh_ref* R, cudaStream_t st)
+// The edges that take the float32 ratio: the least sensitive groups of kF32Group aligned edges
+// (a group's sensitivity: the sum of its S_e (xweight_kernel) times kappa_e, 1 without higher
+// modes), in ascending order while kF32EdgeError x (sum of their sensitivities) stays within
+// kF32Budget; flagged in v[30] of their weight records.  Reads back the constant parts and sets
+// R->mix's extended-precision fields.
+static cudaError_t select_f32_edges(mbh_ref* R, cudaStream_t st, const std::vector<double>* kappa)
 {
     const int E = R->E;
-    cudaError_t e = cudaMalloc(&R->x_der, sizeof(XDer));
-    if (e == cudaSuccess) e = cudaMalloc(&R->x_edge, sizeof(XEdge) * (E + 1));
-    if (e == cudaSuccess) e = cudaMalloc(&R->x_w, sizeof(XWeight) * (E + 1));
-    if (e == cudaSuccess) e = cudaMalloc(&R->x_sums, sizeof(double) * 2);
-    if (e == cudaSuccess) e = cudaMalloc(&R->x_sens, sizeof(double) * (E + 1));
-    if (e != cudaSuccess) return e;
-    xref_kernel<<<1, 32, 0, st>>>(R->theta0_dev, R->x_der);
-    xedge_kernel<<<(E + 1 + 127) / 128, 128, 0, st>>>(R->theta0_dev, R->x_der, R->grid.t_obs, R->fe, E + 1,
-                                                      R->x_edge);
-    xweight_kernel<<<(E + 1 + 127) / 128, 128, 0, st>>>(R->summary, R->invw, E, R->x_w, R->x_sums, R->x_sens);
-    e = cudaGetLastError();
     double sums[2];
     std::vector<double> sens(E + 1);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(sums, R->x_sums, sizeof sums, cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaMemcpyAsync(sums, R->x_sums, sizeof sums, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(sens.data(), R->x_sens, sizeof(double) * (E + 1), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return e;
-    std::vector<int> order(E + 1);
-    for (int i = 0; i <= E; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return sens[a] < sens[b]; });
+    const int ng = (E + 1 + kF32Group - 1) / kF32Group;
+    std::vector<double> gs(ng, 0.0);
+    for (int i = 0; i <= E; ++i) gs[i / kF32Group] += sens[i] * (kappa ? (*kappa)[i] : 1.0);
+    std::vector<int> order(ng);
+    for (int i = 0; i < ng; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return gs[a] < gs[b]; });
     std::vector<float> flag(E + 1, 0.0f);
     double acc = 0.0;
     int n32 = 0;
-    for (int i : order) {
-        if (kF32EdgeError * (acc + sens[i]) > kF32Budget) break;
-        acc += sens[i];
-        flag[i] = 1.0f;
-        ++n32;
+    for (int gi : order) {
+        if (kF32EdgeError * (acc + gs[gi]) > kF32Budget) break;
+        acc += gs[gi];
+        for (int i = gi * kF32Group; i < std::min(E + 1, (gi + 1) * kF32Group); ++i) {
+            flag[i] = 1.0f;
+            ++n32;
+        }
     }
     // v[30] of every record (pitch sizeof(XWeight))
     e = cudaMemcpy2DAsync(reinterpret_cast<char*>(R->x_w) + 30 * sizeof(float), sizeof(XWeight), flag.data(),
@@ -1004,9 +1067,28 @@ cudaError_t prepare_x_tables(mbh_ref* R, cudaStream_t st)
     return e;
 }
 
+// Tables of the extended-precision heterodyne for a (2,2) reference: XDer of theta0, edge
+// records, edge weights and the constant parts, and the float32-ratio edges (select_f32_edges).
+cudaError_t prepare_x_tables(mbh_ref* R, cudaStream_t st)
+{
+    const int E = R->E;
+    cudaError_t e = cudaMalloc(&R->x_der, sizeof(XDer));
+    if (e == cudaSuccess) e = cudaMalloc(&R->x_edge, sizeof(XEdge) * (E + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&R->x_w, sizeof(XWeight) * (E + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&R->x_sums, sizeof(double) * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&R->x_sens, sizeof(double) * (E + 1));
+    if (e != cudaSuccess) return e;
+    xref_kernel<<<1, 32, 0, st>>>(R->theta0_dev, R->x_der);
+    xedge_kernel<<<(E + 1 + 127) / 128, 128, 0, st>>>(R->theta0_dev, R->x_der, R->grid.t_obs, R->fe, E + 1,
+                                                      R->x_edge);
+    xweight_kernel<<<(E + 1 + 127) / 128, 128, 0, st>>>(R->summary, R->invw, E, R->x_w, R->x_sums, R->x_sens);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? select_f32_edges(R, st, nullptr) : e;
+}
+
 // Tables of the extended-precision heterodyne for a higher-mode reference: XDer of theta0, the
-// edge records and the per-group records, the edge weights and the constant parts (every edge
-// double-float: no float32-ratio edges).
+// edge records and the per-group records, the edge weights and the constant parts, and the
+// float32-ratio edges (select_f32_edges; their ratio from the float32 higher-mode tables).
 cudaError_t prepare_x_tables_hm(mbh_ref* R, cudaStream_t st)
 {
     const int E = R->E;
@@ -1022,18 +1104,29 @@ cudaError_t prepare_x_tables_hm(mbh_ref* R, cudaStream_t st)
                                                          E + 1, R->x_edge, R->x_grp);
     xweight_kernel<<<(E + 1 + 127) / 128, 128, 0, st>>>(R->summary, R->invw, E, R->x_w, R->x_sums, R->x_sens);
     e = cudaGetLastError();
-    double sums[2];
-    if (e == cudaSuccess) e = cudaMemcpyAsync(sums, R->x_sums, sizeof sums, cudaMemcpyDeviceToHost, st);
+    // kappa_e = max over channels of sum over mode groups |u_g| (the float32 higher-mode records)
+    std::vector<MixModeHM> hm((size_t)(E + 1) * kHmModes);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hm.data(), R->mix_hm, sizeof(MixModeHM) * hm.size(), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e == cudaSuccess) {
-        R->mix.xder = R->x_der;
-        R->mix.xedge = R->x_edge;
-        R->mix.xgrp = R->x_grp;
-        R->mix.xw = R->x_w;
-        R->mix.xsumA = sums[0];
-        R->mix.xsumB = sums[1];
-        R->mix.xn32 = 0;
+    if (e != cudaSuccess) return e;
+    std::vector<double> kappa(E + 1, 1.0);
+    for (int i = 0; i <= E; ++i) {
+        double kmax = 1.0;
+        for (int c = 0; c < 3; ++c) {
+            double k = 0.0;
+            for (int g = 0; g < 4; ++g) {
+                const uint32_t gmask = R->modes & hm_group_mask(g);
+                if (!gmask) continue;
+                const float2 u = hm[(size_t)i * kHmModes + (__builtin_ctz(gmask))].u[c];
+                k += std::hypot((double)u.x, (double)u.y);
+            }
+            kmax = std::max(kmax, k);
+        }
+        kappa[i] = kmax;
     }
+    e = select_f32_edges(R, st, &kappa);
+    if (e == cudaSuccess) R->mix.xgrp = R->x_grp;
     return e;
 }
 
@@ -1072,7 +1165,7 @@ HetKernel het_kernel_x(int G, int block)
     if (G == g && block == b) return {&launch_het_x<g, b>, (const void*)&het_x_kernel<g, b>};
     MBH_CASE(1, 64) MBH_CASE(1, 128) MBH_CASE(1, 256)
     MBH_CASE(2, 64) MBH_CASE(2, 128) MBH_CASE(2, 256)
-    MBH_CASE(4, 64) MBH_CASE(4, 128) MBH_CASE(4, 256)
+    MBH_CASE(4, 64) MBH_CASE(4, 128) MBH_CASE(4, 256) MBH_CASE(4, 96) MBH_CASE(4, 160) MBH_CASE(4, 224)
     MBH_CASE(8, 64) MBH_CASE(8, 128) MBH_CASE(8, 256)
     MBH_CASE(16, 64) MBH_CASE(16, 128) MBH_CASE(16, 256)
     MBH_CASE(32, 64) MBH_CASE(32, 128) MBH_CASE(32, 256)
@@ -1086,7 +1179,7 @@ HetKernel het_kernel_xhm(int G, int block)
 {
 #define MBH_CASE(g, b) \
     if (G == g && block == b) return {&launch_het_xhm<g, b>, (const void*)&het_xhm_kernel<g, b>};
-    MBH_CASE(1, 64) MBH_CASE(1, 128) MBH_CASE(1, 256)
+    MBH_CASE(1, 64) MBH_CASE(1, 128)
     MBH_CASE(2, 64) MBH_CASE(2, 128) MBH_CASE(2, 256)
     MBH_CASE(4, 64) MBH_CASE(4, 128) MBH_CASE(4, 256)
     MBH_CASE(8, 64) MBH_CASE(8, 128) MBH_CASE(8, 256)

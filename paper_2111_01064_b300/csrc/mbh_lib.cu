@@ -768,6 +768,7 @@ extern "C" mbh_status het_prepare_reference_hm(const mbh_data* data, const doubl
 
 extern "C" int32_t mbh_ref_bins(const mbh_ref* ref) { return ref ? ref->E : -1; }
 extern "C" uint32_t mbh_ref_modes(const mbh_ref* ref) { return ref ? ref->modes : 0u; }
+extern "C" int32_t mbh_ref_f32_edges(const mbh_ref* ref) { return ref ? ref->mix.xn32 : -1; }
 
 extern "C" mbh_status mbh_ref_read(const mbh_ref* ref, int64_t* edges_host, double* summary_host,
                                    double* h0_edges_host, double* dd_host)

@@ -614,15 +614,6 @@ __device__ __forceinline__ void contract_bin(const MixBin& mb, const cf dp[3], c
     }
 }
 
-// The float32 amplitude factors of the walker and of the reference scale the whole of h and h0,
-// so their rounding is a common factor of every ratio r = h/h0: <d|h> (linear in r) is off by
-// amp_fix and <h|h> (quadratic) by its square, which the epilogue removes in float64.  Left in,
-// this coherent error dominates |dlnL| for walkers far from the reference.
-__device__ __forceinline__ double amp_fix(float eps_walker, double eps_ref)
-{
-    return (1.0 + (double)eps_walker) / (1.0 + eps_ref);
-}
-
 // A walker's <d|h>, <h|h> partial sums (float pairs) with the tail edge E, when the edge loop
 // left it out: evaluated here, its bin E - 1 contracted against the carried delta at E - 1 and
 // added last (the same order for every block size and launch mode)
@@ -780,55 +771,7 @@ __global__ void __launch_bounds__(BLOCK, 640 / BLOCK)
         for (int r = 0; r < rounds; ++r) {
             const int e = r * G + lane;
             cf dl[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-            if (active && e <= E) {
-                const MixEdge me = S.mix.edge[e];
-                const FreqDF q = {ld_f2(me.f), ld_f2(me.f3), ld_f2(me.fm3), ld_f2(me.lnf3)};
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const float2 b = S.mix.hm_base[e * 3 + c];
-                    dl[c] = {b.x, b.y};
-                }
-                // Modes with the same m share f2 = 2f/m, so the phase chain, t(f2), the orbit, the
-                // reference's phase and g: one chain and one transfer per distinct m, with the
-                // modes' factors summed weighted by v^{p_lm} (the transfer is linear in them) and
-                // the group's u summed in its first mode's record (edge_mixed_hm_kernel).
-                for (int grp = 0; grp < 4; ++grp) {
-                    const uint32_t gmask = modes & hm_group_mask(grp);
-                    if (!gmask) continue;
-                    const int b0 = __ffs(gmask) - 1;   // the group's first mode
-                    const MixModeHM mm = S.mix.hm[(int64_t)e * kHmModes + b0];
-                    const FreqDF q2 = mode_tables(q, b0);
-                    f2 Phi;
-                    float sa, ca, amp;
-                    if (phase_df<false, true>(wsd[lw], wsf[lw], q2, tob, Phi, sa, ca, amp)) {
-                        float sh, ch;
-                        sincos_small(0.5f * reduce_phase(dd_add_lazy(mode_phase(Phi, b0), {-mm.phi0.x, -mm.phi0.y})),
-                                     &sh, &ch);
-                        const cf em1 = {-2.0f * sh * sh, -2.0f * sh * ch};   // e^{-i dPhi} - 1
-                        float gk[4] = {0.f, 0.f, 0.f, 0.f}, gl[4] = {0.f, 0.f, 0.f, 0.f};
-                        for (uint32_t bm = gmask; bm; bm &= bm - 1) {
-                            const int b = __ffs(bm) - 1;
-                            const float vp = mode_vpow(wsd[lw], q2, b);
-#pragma unroll
-                            for (int j = 0; j < 4; ++j) {
-                                gk[j] = fmaf(vp, wsh[lw].hk[b][j], gk[j]);
-                                gl[j] = fmaf(vp, wsh[lw].hklo[b][j], gl[j]);
-                            }
-                        }
-                        cf T[3];
-                        transfer_f32<true>(wsf[lw], &gk[0], &gk[2], me.xs.w, sa, ca, 1.0f, me.xs.x, me.xs.y, T, gl);
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            const cf u = {mm.u[c].x, mm.u[c].y};
-                            const cf ac = fsub(fmul(fscale(T[c], amp), {mm.g[c].x, mm.g[c].y}), u);
-                            dl[c] = fadd(dl[c], fadd(fadd(ac, fmul(ac, em1)), fmul(u, em1)));
-                        }
-                    } else {
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) dl[c] = fsub(dl[c], {mm.u[c].x, mm.u[c].y});
-                    }
-                }
-            }
+            if (active && e <= E) edge_delta_mixed_hm(wsd[lw], wsf[lw], wsh[lw], S.mix, e, modes, tob, dl);
             cf dp[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {

@@ -429,6 +429,15 @@ __device__ inline void walker_setup_mixed(const double* __restrict__ theta, int6
     }
 }
 
+// The float32 amplitude factors of the walker and of the reference scale the whole of h and h0,
+// so their rounding is a common factor of every ratio r = h/h0: <d|h> (linear in r) is off by
+// amp_fix and <h|h> (quadratic) by its square, which the epilogue removes in float64.  Left in,
+// this coherent error dominates |dlnL| for walkers far from the reference.
+__device__ __forceinline__ double amp_fix(float eps_walker, double eps_ref)
+{
+    return (1.0 + (double)eps_walker) / (1.0 + eps_ref);
+}
+
 // frequency tables of one grid point: f, f^{1/3}, f^{-1/3}, ln(f)/3 as float pairs
 struct FreqDF {
     f2 f, f3, fm3, lnf3;
@@ -739,4 +748,59 @@ __device__ __forceinline__ void edge_delta_mixed(const WalkerDF& wd, const Walke
     }
 }
 
+// delta = h/h0 - 1 of one walker at edge e of a higher-mode reference, float32 ratio (Sec. II B
+// with the template of Eq. 9 summed over the modes before the ratio): from the per-mode
+// reference records (edge_mixed_hm_kernel), starting from the stored sum u - 1.  Modes with the
+// same m share f2 = 2f/m, so the phase chain, t(f2), the orbit, the reference's phase and g: one
+// chain and one transfer per distinct m, with the modes' factors summed weighted by v^{p_lm}
+// (the transfer is linear in them) and the group's u summed in its first mode's record.
+__device__ __forceinline__ void edge_delta_mixed_hm(const WalkerDF& wd, const WalkerF& wf, const WalkerHMF& wh,
+                                                    const MixTables& mix, int e, uint32_t modes, f2 tob,
+                                                    cf dl[3])
+{
+    const MixEdge me = mix.edge[e];
+    const FreqDF q = {ld_f2(me.f), ld_f2(me.f3), ld_f2(me.fm3), ld_f2(me.lnf3)};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float2 b = mix.hm_base[e * 3 + c];
+        dl[c] = {b.x, b.y};
+    }
+    for (int grp = 0; grp < 4; ++grp) {
+        const uint32_t gmask = modes & hm_group_mask(grp);
+        if (!gmask) continue;
+        const int b0 = __ffs(gmask) - 1;   // the group's first mode
+        const MixModeHM mm = mix.hm[(int64_t)e * kHmModes + b0];
+        const FreqDF q2 = mode_tables(q, b0);
+        f2 Phi;
+        float sa, ca, amp;
+        if (phase_df<false, true>(wd, wf, q2, tob, Phi, sa, ca, amp)) {
+            float sh, ch;
+            sincos_small(0.5f * reduce_phase(dd_add_lazy(mode_phase(Phi, b0), {-mm.phi0.x, -mm.phi0.y})), &sh, &ch);
+            const cf em1 = {-2.0f * sh * sh, -2.0f * sh * ch};   // e^{-i dPhi} - 1
+            float gk[4] = {0.f, 0.f, 0.f, 0.f}, gl[4] = {0.f, 0.f, 0.f, 0.f};
+            for (uint32_t bm = gmask; bm; bm &= bm - 1) {
+                const int b = __ffs(bm) - 1;
+                const float vp = mode_vpow(wd, q2, b);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    gk[j] = fmaf(vp, wh.hk[b][j], gk[j]);
+                    gl[j] = fmaf(vp, wh.hklo[b][j], gl[j]);
+                }
+            }
+            cf T[3];
+            transfer_f32<true>(wf, &gk[0], &gk[2], me.xs.w, sa, ca, 1.0f, me.xs.x, me.xs.y, T, gl);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const cf u = {mm.u[c].x, mm.u[c].y};
+                const cf ac = fsub(fmul(fscale(T[c], amp), {mm.g[c].x, mm.g[c].y}), u);
+                dl[c] = fadd(dl[c], fadd(fadd(ac, fmul(ac, em1)), fmul(u, em1)));
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) dl[c] = fsub(dl[c], {mm.u[c].x, mm.u[c].y});
+        }
+    }
+}
+
 }  // namespace mbh
+

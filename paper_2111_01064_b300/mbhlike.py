@@ -152,6 +152,7 @@ def lib() -> C.CDLL:
         "mbh_server_free": (None, [vp]),
         "mbh_selftest_math": (C.c_int, [i32, vp, vp, i64, vp, vp, vp]),
         "mbh_ref_modes": (C.c_uint32, [vp]),
+        "mbh_ref_f32_edges": (i32, [vp]),
         "template_batch_hm": (C.c_int, [gp, vp, i64, C.c_uint32, C.c_int, vp, vp]),
         "direct_loglike_batch_hm": (C.c_int, [vp, vp, i64, C.c_uint32, C.c_int, vp, vp]),
         "het_prepare_reference_hm": (C.c_int, [vp, dp, i32, C.c_uint32, vp, C.POINTER(vp)]),
@@ -361,6 +362,11 @@ class Ref:
     @property
     def modes(self) -> int:
         return int(lib().mbh_ref_modes(self.handle))
+
+    @property
+    def f32_edges(self) -> int:
+        """Edges that MBH_MIXED evaluates with the float32 ratio (per-edge precision)."""
+        return int(lib().mbh_ref_f32_edges(self.handle))
 
     def read(self) -> dict:
         E = self.bins

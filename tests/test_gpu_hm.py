@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import mbh_inputs as I
+from edge_rule import f32_edge_count
 
 pytestmark = pytest.mark.gpu
 ALL = 0x3F
@@ -135,6 +136,66 @@ def test_het_mixed_higher_modes(M, WL, oracle, which, request):
     out_m = M.het_loglike_batch([ref_g], [0, 1], WL.to_dev(c["th"].reshape(11, 1)), "mixed").cpu().numpy()
     out_f = M.het_loglike_batch([ref_g], [0, 1], WL.to_dev(c["th"].reshape(11, 1)), "fp64").cpu().numpy()
     assert abs(out_m[0, 0] - out_f[0, 0]) < 1e-5
+
+
+@pytest.fixture(scope="module")
+def year_case(oracle, M, WL):
+    """The benchmark's higher-mode source: workload 2's injection with q = min(q, 0.35) (odd-m
+    modes present) at its SNR (122), in noise on the 1-yr grid, 256 bins."""
+    import torch
+    g = I.grid_year()
+    th_raw, snr = WL.injection(2, g, 0)
+    th_raw = th_raw.copy()
+    th_raw[I.I_Q] = min(th_raw[I.I_Q], 0.35)
+    z = I.noise_normals(I.rng(2, 150), g["n"])
+    f = oracle.freqs(g)
+    S = oracle.psd(f)
+    th_o = I.with_distance(th_raw, oracle.snr_distance(th_raw, g, snr, S))
+    d_o = oracle.template_hm(th_o, f, g["t_obs"], ALL) + oracle.noise(S, g["df"], z)
+    psd = M.mbh_psd_aet(g)
+    d_g = M.template_batch(g, WL.to_dev(th_o.reshape(11, 1)), "fp64", modes=ALL)[0].contiguous()
+    M.mbh_noise_aet(g, torch.from_numpy(np.ascontiguousarray(z)).cuda(), psd, out=d_g, accumulate=True)
+    data = M.Data(g, d_g, psd)
+    ref_g = M.het_prepare_reference(data, th_o, 256, modes=ALL)
+    ref_o = oracle.het_prepare(th_o, g, d_o, S, 256, ALL)
+    return dict(g=g, th=th_o, ref_g=ref_g, ref_o=ref_o, snr=snr)
+
+
+def test_het_mixed_higher_modes_float32_edges(M, WL, oracle, year_case):
+    """Per-edge precision with six modes: on the benchmark's higher-mode source about half of
+    the 257 edges take the float32 ratio of the float32 higher-mode path (the rule recomputed
+    from the summary data and the modes' shares of h0), and MBH_MIXED stays within |dlnL| <= 1e-3 of the oracle (32 sampled
+    walkers) and of the float64 kernel (every walker), 1e-3..1e-1 and 1e-6..1e-3 from the
+    reference."""
+    c = year_case
+    ref_g, ref_o = c["ref_g"], c["ref_o"]
+    np.testing.assert_array_equal(ref_g.read()["edges"], ref_o["edges"])
+    # kappa_e: the reference's mode-group shares u_g = h0_g/h0 summed in modulus, per channel
+    g = c["g"]
+    fe = g["f0"] + ref_o["edges"] * g["df"]
+    h0 = oracle.template_hm(c["th"], fe, g["t_obs"], ALL)
+    share = np.zeros(h0.shape)
+    with np.errstate(all="ignore"):
+        for gmask in (0x11, 0x22, 0x04, 0x08):
+            hg = oracle.template_hm(c["th"], fe, g["t_obs"], gmask)
+            share += np.where(np.abs(h0) > 0, np.abs(hg / h0), 0.0)
+    kappa = np.maximum(1.0, share.max(axis=0))
+    lo, hi = f32_edge_count(ref_g, g, kappa, rtol=1e-5)   # the library's kappa: from float32 shares
+    print(f"six modes, SNR {c['snr']:.0f}: {ref_g.f32_edges} float32-ratio edges of {ref_g.bins + 1} "
+          f"(rule: {lo}..{hi})")
+    assert lo <= ref_g.f32_edges <= hi and ref_g.f32_edges >= 64
+    for lo_p, hi_p, W in ((1e-3, 1e-1, 16384), (1e-6, 1e-3, 4096)):
+        th = WL.walkers(c["th"], W, 2, source=9, lo=lo_p, hi=hi_p)
+        o64 = M.het_loglike_batch([ref_g], [0, W], WL.to_dev(th), "fp64").cpu().numpy()
+        omx = M.het_loglike_batch([ref_g], [0, W], WL.to_dev(th), "mixed").cpu().numpy()
+        d = np.abs(omx[0] - o64[0])
+        print(f"  {lo_p:g}..{hi_p:g}: mixed vs fp64 p50/p99/max", np.median(d), np.quantile(d, 0.99), d.max())
+        assert d.max() <= 1e-3
+        sample = np.arange(0, W, W // 32)
+        out_o = oracle.het_loglike(np.ascontiguousarray(th[:, sample]), ref_o)
+        err = np.abs(omx[0, sample] - out_o[0])
+        print("  mixed vs oracle sampled: p50/max", np.median(err), err.max())
+        assert err.max() <= 1e-3
 
 
 def test_het_mixed_f32_higher_modes(M, WL, oracle, case):

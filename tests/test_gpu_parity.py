@@ -22,6 +22,7 @@ import numpy as np
 import pytest
 
 import mbh_inputs as I
+from edge_rule import f32_edge_count
 
 pytestmark = pytest.mark.gpu
 
@@ -372,6 +373,24 @@ def test_het_mixed_benchmark_accuracy(M, WL):
     print("workload 2 mixed_f32 vs fp64: p50/p99/max", np.median(d), np.quantile(d, 0.99), d.max(),
           "frac <= 1e-3", np.mean(d <= 1e-3))
     assert np.mean(d <= 1e-3) >= 0.995 and d.max() <= 5e-3
+
+
+def test_f32_edge_choice(M, WL):
+    """The reference's float32-ratio edges follow the per-edge precision rule (recomputed on
+    the host from the summary data): on the benchmark's source (SNR 122) and on the same
+    source at SNR 1000, where fewer edges qualify."""
+    g = I.grid_year()
+    th_raw, snr = WL.injection(2, g)
+    z = I.noise_normals(I.rng(2, 100), g["n"])
+    counts = []
+    for target in (snr, 1000.0):
+        src = WL.build_source(g, th_raw, target, z)
+        ref = M.het_prepare_reference(src.data, src.theta_inj, 256)
+        lo, hi = f32_edge_count(ref, g)
+        print(f"SNR {target:.0f}: {ref.f32_edges} float32-ratio edges of {ref.bins + 1} (rule: {lo}..{hi})")
+        assert lo <= ref.f32_edges <= hi
+        counts.append(ref.f32_edges)
+    assert counts[0] > counts[1] > 0
 
 
 @pytest.mark.parametrize("lo,hi,W", [(1e-3, 1e-1, 16384), (1e-6, 1e-3, 4096)])
