@@ -837,14 +837,16 @@ def run_uneven(M, WL, stream, reps: int = 20) -> dict:
     edges = int(np.sum(ub.walkers * (np.array([r.bins for r in ub.refs]) + 1)))
     # |dlnL| against the oracle: 4 evenly spaced walkers of every source, each source rebuilt on
     # the oracle side from the same draws
-    errs = _oracle_source_errors(WL, ub, 3, got[0], per_source=4, lo=1e-5, hi=1e-3)
+    srcs = _oracle_sources(ub, 3, range(len(ub.refs)))
+    errs = _oracle_source_errors(WL, ub, 3, got[0], per_source=4, lo=1e-5, hi=1e-3, srcs=srcs)
+    cpu = _oracle_uneven_baseline(WL, ub, 3, srcs, lo=1e-5, hi=1e-3)
     return {"sources": len(ub.refs), "walkers": W, "edge_evaluations": edges,
             "bins_range": [int(ub.bins.min()), int(ub.bins.max())],
             "walkers_range": [int(ub.walkers.min()), int(ub.walkers.max())],
             "autotuned": cfg.as_dict(), "ms_default_config": ms_default, "ms_autotuned": ms_tuned,
             "ms_graph_replay": ms_graph, "evals_per_s_graph": W / (ms_graph * 1e-3),
             "evals_per_s_default": W / (ms_default * 1e-3),
-            "accuracy_vs_oracle": _acc(errs)}
+            "accuracy_vs_oracle": _acc(errs), "cpu_baseline": cpu}
 
 
 def _oracle_sources(ub, workload: int, sources) -> dict:
@@ -863,11 +865,35 @@ def _oracle_sources(ub, workload: int, sources) -> dict:
     return out
 
 
-def _oracle_source_errors(WL, ub, workload, lnl, per_source, lo, hi) -> np.ndarray:
+def _oracle_uneven_baseline(WL, ub, workload, srcs, lo, hi, per_source: int = 64) -> dict:
+    """The oracle on the uneven batch: per source, its heterodyne likelihood of up to
+    per_source of the source's walkers timed on the host cores (reference preparation not
+    timed, as on the GPU); the whole batch's time projected from each source's time per walker
+    and walker count."""
+    from oracle import oracle as O
+    projected, sample_s, n = 0.0, 0.0, 0
+    for s, (th0, ref_o) in srcs.items():
+        a, b = int(ub.offsets[s]), int(ub.offsets[s + 1])
+        k = min(per_source, b - a)
+        wo = np.ascontiguousarray(WL.walkers(th0, b - a, workload, s, lo, hi)[:, :k])
+        t0 = time.perf_counter()
+        O.het_loglike(wo, ref_o)
+        dt = time.perf_counter() - t0
+        projected += dt / k * (b - a)
+        sample_s += dt
+        n += k
+    W = int(ub.offsets[-1])
+    return {"value": W / projected, "unit": UNIT, "cores": O.threads(), "kind": "oracle",
+            "sample": f"{n} walkers ({per_source} or fewer per source) in {sample_s:.2f} s; the {W}-walker "
+                      f"batch's time projected per source from them"}
+
+
+def _oracle_source_errors(WL, ub, workload, lnl, per_source, lo, hi, srcs=None) -> np.ndarray:
     """|dlnL| of the batch's lnL (walkers grouped by source) against the oracle on
     per_source evenly spaced walkers of every source."""
     from oracle import oracle as O
-    srcs = _oracle_sources(ub, workload, range(len(ub.refs)))
+    if srcs is None:
+        srcs = _oracle_sources(ub, workload, range(len(ub.refs)))
     errs = []
     for s, (th0, ref_o) in srcs.items():
         a, b = int(ub.offsets[s]), int(ub.offsets[s + 1])

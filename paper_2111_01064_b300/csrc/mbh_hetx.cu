@@ -635,14 +635,19 @@ __global__ void __launch_bounds__(BLOCK) het_x_kernel(const __grid_constant__ He
         const int64_t w0 = S.w_begin + (int64_t)(tile - S.tile_begin) * WPB;
         const bool active = w0 + lw < S.w_end;
         __syncthreads();
-        for (int j = threadIdx.x; j < WPB; j += BLOCK)
-            if (w0 + j < S.w_end) {
+        // the walkers' two set-ups (float64 chains bound by latency, not by the float64 pipe's
+        // rate) on different warps where the block has them: slot t < WPB sets up walker t's
+        // double-float constants, slot WPB + t its float32-path constants
+        for (int t = threadIdx.x; t < 2 * WPB; t += BLOCK) {
+            const int j = t < WPB ? t : t - WPB;
+            if (w0 + j >= S.w_end) continue;
+            if (t < WPB) {
                 xwalker_setup(L.theta, L.W, w0 + j, *S.mix.xder, xw[j]);
-                if (S.mix.xn32 > 0) {
-                    walker_setup_mixed(L.theta, L.W, w0 + j, wsd[j], wsf[j]);
-                    eta32[j] = (float)(amp_fix(wsf[j].eps_amp76, S.mix.amp_eps0) - 1.0);
-                }
+            } else if (S.mix.xn32 > 0) {
+                walker_setup_mixed(L.theta, L.W, w0 + j, wsd[j], wsf[j]);
+                eta32[j] = (float)(amp_fix(wsf[j].eps_amp76, S.mix.amp_eps0) - 1.0);
             }
+        }
         __syncthreads();
         const int E = S.E;
         const f2 tob = {S.tob_hi, S.tob_lo};
@@ -727,16 +732,24 @@ __global__ void __launch_bounds__(BLOCK) het_xhm_kernel(const __grid_constant__ 
         const int64_t w0 = S.w_begin + (int64_t)(tile - S.tile_begin) * WPB;
         const bool active = w0 + lw < S.w_end;
         __syncthreads();
-        for (int j = threadIdx.x; j < WPB; j += BLOCK)
-            if (w0 + j < S.w_end) {
+        // the walkers' four set-ups on different warps where the block has them (slot
+        // k WPB + t: set-up k of walker t)
+        for (int t = threadIdx.x; t < 4 * WPB; t += BLOCK) {
+            const int k = t / WPB, j = t - k * WPB;
+            if (w0 + j >= S.w_end) continue;
+            if (k == 0) {
                 xwalker_setup(L.theta, L.W, w0 + j, *S.mix.xder, xw[j]);
+            } else if (k == 1) {
                 xwalker_setup_hm(L.theta, L.W, w0 + j, xh[j]);
-                if (S.mix.xn32 > 0) {
+            } else if (S.mix.xn32 > 0) {
+                if (k == 2) {
                     walker_setup_mixed(L.theta, L.W, w0 + j, wsd[j], wsf[j]);
-                    walker_setup_hm(L.theta, L.W, w0 + j, wsh[j]);
                     eta32[j] = (float)(amp_fix(wsf[j].eps_amp76, S.mix.amp_eps0) - 1.0);
+                } else {
+                    walker_setup_hm(L.theta, L.W, w0 + j, wsh[j]);
                 }
             }
+        }
         __syncthreads();
         const int E = S.E;
         const f2 tob = {S.tob_hi, S.tob_lo};
