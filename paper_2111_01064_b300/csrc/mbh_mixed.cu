@@ -133,11 +133,14 @@ constexpr int kDirThreadsM = 256;
 // grid point are loaded once and reused by the T walkers; each thread keeps its per-walker
 // float64 sums in shared memory (a dynamically indexed register array would go to local
 // memory), reduced per walker at the end.  Data and templates are in units where h/sigma is
-// O(1) (float32 range); per-point products are float32, sums float64.
+// O(1) (float32 range); per-point products are float32, sums float64.  Three blocks per SM
+// (80 registers, 52.5 KB of shared memory each; a few bytes of spills in the set-up): 5 %
+// faster than two (108 registers), the six-mode pass 7 %; four (64 registers) spill in the
+// point loop and run slower.
 constexpr int kDirFlush = 16;   // points per float32 partial sum in the fused mixed pass
 
 template <int T, bool kHM>
-__global__ void __launch_bounds__(kDirThreadsM, 2)
+__global__ void __launch_bounds__(kDirThreadsM, 3)
     direct_fused_mixed_kernel(const double* __restrict__ theta, int64_t W, const float4* __restrict__ ft1,
                               const float4* __restrict__ ft2, const float4* __restrict__ ft3, double t_obs,
                               const float2* __restrict__ wd, const float* __restrict__ wv,
