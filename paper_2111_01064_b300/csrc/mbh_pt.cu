@@ -702,7 +702,9 @@ extern "C" mbh_status mbh_pt_create_multi(const mbh_pt_opts* o, const mbh_ref* c
     // walker up to 12288 moving walkers, 8 above (threads per walker fixes the summation order,
     // so a sampler keeps the one it was created with)
     if (!o->het_config.threads_per_walker && P->precision == MBH_MIXED_F32) P->cfg.threads_per_walker = M <= 12288 ? 16 : 8;
-    if (!o->het_config.threads_per_walker && P->precision == MBH_MIXED) P->cfg.threads_per_walker = 4;
+    // MBH_MIXED: the extended-precision kernel; half steps of at most 12288 walkers fill the
+    // GPU better with 8 threads per walker (8192 walkers: 0.260 ms against 0.292 ms with 4)
+    if (!o->het_config.threads_per_walker && P->precision == MBH_MIXED) P->cfg.threads_per_walker = M <= 12288 ? 8 : 4;
     const int64_t NT = (int64_t)n_ens * A.T;
     cudaError_t e = cudaSuccess;
     auto alloc = [&](void** p, size_t bytes) {

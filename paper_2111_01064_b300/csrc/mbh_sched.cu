@@ -77,13 +77,16 @@ int default_block_mixed(int G, int64_t W)
     return 4 * tiles >= 3 * 4 * (int64_t)sms ? kDefaultBlockMixed : kDefaultBlock;
 }
 
-// Default block of the extended-precision (2,2) kernel (4 threads per walker, 128 registers):
-// 256 threads (64 walkers, two full warps of float64 walker set-up, 2 blocks per SM) once its
-// tiles fill one and a half blocks per SM, else 128 (32 walkers, 4 blocks per SM): 16384
-// walkers x 257 edges take 0.419 ms against 0.429 ms.  Blocks whose walkers do not fill
-// whole warps (64, 96, 160 threads) pay for idle lanes in the float64 set-up.
+// Default block of the extended-precision (2,2) kernel (128 registers): with 4 threads per
+// walker 256 threads (64 walkers, two full warps of float64 walker set-up, 2 blocks per SM) once
+// its tiles fill one and a half blocks per SM, else 128 (32 walkers, 4 blocks per SM): 16384
+// walkers x 257 edges take 0.404 ms against 0.414 ms.  Blocks whose walkers do not fill
+// whole warps (64, 96, 160 threads) pay for idle lanes in the float64 set-up.  With 8 or 16
+// threads per walker (the sampler's smaller half steps) 256 threads: 8192 walkers 0.260 ms
+// against 0.286 ms at 128.
 int default_block_x(int G, int64_t W)
 {
+    if (G == 8 || G == 16) return 256;
     if (G != 4) return kDefaultBlock;
     const int sms = sm_count();
     const int64_t tiles = (W + 63) / 64;
