@@ -232,7 +232,7 @@ def run_ours(args) -> dict | None:
     if args.only in ("fused", "fused64"):
         return run_fused_only(args, M, WL, g, src, rank, dev, stream, "fp64" if args.only == "fused64" else "mixed")
     if args.only == "sampler":   # profiling case: sampler iterations alone
-        r = run_sampler(M, WL, g, src, ref, stream, 1.0, iters=args.steps)
+        r = run_sampler(M, WL, g, src, ref, stream, None, iters=args.steps)
         return {"profile_case": "sampler", **r} if rank == 0 else None
     if args.only == "hm":        # profiling case: higher-mode heterodyne alone
         r = run_higher_modes(M, WL, g, stream, reps=args.steps)
@@ -406,7 +406,8 @@ def run_ours(args) -> dict | None:
     dscale = 0.5 * (src.data.dd + np.abs(d6[2]) + 2 * np.abs(d6[1]))
 
     # ---- device parallel-tempered sampler on the same source (Sec. III) ----
-    sampler = run_sampler(M, WL, g, src, ref, stream, value / ws) if args.only == "all" else None
+    sampler = run_sampler(M, WL, g, src, ref, stream, {"mixed": value / ws, "mixed_f32": f32_rate}) \
+        if args.only == "all" else None
 
     # ---- higher harmonics: the same batch shape with a six-mode reference ----
     higher_modes = run_higher_modes(M, WL, g, stream) if args.only == "all" else None
@@ -748,11 +749,13 @@ def run_higher_modes(M, WL, g, stream, reps: int = 5) -> dict:
     return res
 
 
-def run_sampler(M, WL, g, src, ref, stream, het_rate: float, iters: int = 20) -> dict:
+def run_sampler(M, WL, g, src, ref, stream, het_rates: dict | None, iters: int = 20) -> dict:
     """Parallel-tempered ensemble sampler iterations on the device (Sec. III) with the
     heterodyned likelihood of the benchmark's source: 8 temperatures x 2048 walkers, 256 bins,
     1-yr grid, mixed precision; one iteration = both half-step moves (2 x 8192 likelihood
-    evaluations), the acceptances and the temperature swaps, replayed from a CUDA graph."""
+    evaluations), the acceptances and the temperature swaps, replayed from a CUDA graph.
+    het_rates: the heterodyne batch's lnL/s per precision (the overhead of the sampler over
+    the likelihood alone), or None."""
     import torch
     T, W = W_TEMPS, N_WALKERS // W_TEMPS
     lo, hi = I.prior_box(g["t_obs"])
@@ -778,7 +781,8 @@ def run_sampler(M, WL, g, src, ref, stream, het_rate: float, iters: int = 20) ->
         prop, acc = cnt[:4 * T].reshape(T, 4), cnt[4 * T:8 * T].reshape(T, 4)
         res[name] = {"ms_per_iteration": ms, "iterations_per_s": 1e3 / ms,
                      "lnL_evals_per_s": T * W / (ms * 1e-3),
-                     "overhead_vs_het_only": 1.0 - (T * W / (ms * 1e-3)) / het_rate,
+                     "overhead_vs_het_only": None if not het_rates else
+                     1.0 - (T * W / (ms * 1e-3)) / het_rates[prec],
                      "acceptance_by_temperature": (acc.sum(1) / np.maximum(prop.sum(1), 1)).round(4).tolist(),
                      "swap_acceptance_by_level": (cnt[8 * T + 1:9 * T] / np.maximum(cnt[9 * T + 1:10 * T], 1)).round(4).tolist(),
                      "iterations_run": step}
