@@ -291,9 +291,9 @@ __device__ inline void xwalker_setup(const double* __restrict__ theta, int64_t W
 }
 
 // The per-arm body (three times per edge) and the double-float sine/cosine (four times per
-// edge) are compiled once and called: the inlined edge loop was ~45 KB of straight-line code,
-// and its instruction fetch stalled the warps.
-#define MBH_X_OUTLINE __noinline__
+// edge) come inlined (kInl, the (2,2) kernel: 2.4 % faster) or compiled once and called (the
+// higher-mode kernel, whose loop holds four mode groups and the float32 path: inlined there,
+// its instruction fetch stalls the warps and it runs 22 % slower).
 
 constexpr f2 kH3 = df_const(0.8660254037844386467637231707529361835);   // sqrt3/2
 constexpr f2 kH3q = df_const(0.8660254037844386467637231707529361835 / 4.0);   // sqrt3/8
@@ -336,11 +336,22 @@ struct SinCos {
     f2 s, cm1;
 };
 
-__device__ MBH_X_OUTLINE SinCos sincos_df(f2 x, const SinTab& tab)
+__device__ __forceinline__ SinCos sincos_df_body(f2 x, const SinTab& tab)
 {
     SinCos r;
     dd_sincos_any(x, tab, r.s, r.cm1);
     return r;
+}
+
+__device__ __noinline__ SinCos sincos_df_call(f2 x, const SinTab& tab) { return sincos_df_body(x, tab); }
+
+template <bool kInl>
+__device__ __forceinline__ SinCos sincos_df(f2 x, const SinTab& tab)
+{
+    if constexpr (kInl)
+        return sincos_df_body(x, tab);
+    else
+        return sincos_df_call(x, tab);
 }
 
 struct ArmOut {
@@ -350,8 +361,8 @@ struct ArmOut {
 // One arm (spacecraft i -> j, third spacecraft m) of the raw transfer: arm vector d = u_j - u_i,
 // kn = k.n, the polarisation response a Ga + b Gb, g = i e^{i q_m} F and the one-link sinc
 // factors: yf = g sinc(x(1 - kn)), z = g [sinc(x(1 + kn)) - sinc(x(1 - kn))].
-__device__ MBH_X_OUTLINE ArmOut arm_df(const XWalker& w, const f2* Ga, const f2* Gb, f2 x, f2 d0, f2 d1, f2 d2,
-                                       f2 kn, c2f Em, const SinTab& tab)
+__device__ __forceinline__ ArmOut arm_df_body(const XWalker& w, const f2* Ga, const f2* Gb, f2 x, f2 d0, f2 d1,
+                                              f2 d2, f2 kn, c2f Em, const SinTab& tab)
 {
     const f2 un = dd_add_lazy(dd_mul_lazy(w.eu[0], d0), dd_mul_lazy(w.eu[1], d1));
     const f2 vn = dd_add_lazy(dd_add_lazy(dd_mul_lazy(w.ev[0], d0), dd_mul_lazy(w.ev[1], d1)),
@@ -367,6 +378,22 @@ __device__ MBH_X_OUTLINE ArmOut arm_df(const XWalker& w, const f2* Ga, const f2*
     return {cd_mul_r(g, sm), cd_mul_r(g, sd)};
 }
 
+__device__ __noinline__ ArmOut arm_df_call(const XWalker& w, const f2* Ga, const f2* Gb, f2 x, f2 d0, f2 d1, f2 d2,
+                                           f2 kn, c2f Em, const SinTab& tab)
+{
+    return arm_df_body(w, Ga, Gb, x, d0, d1, d2, kn, Em, tab);
+}
+
+template <bool kInl>
+__device__ __forceinline__ ArmOut arm_df(const XWalker& w, const f2* Ga, const f2* Gb, f2 x, f2 d0, f2 d1, f2 d2,
+                                         f2 kn, c2f Em, const SinTab& tab)
+{
+    if constexpr (kInl)
+        return arm_df_body(w, Ga, Gb, x, d0, d1, d2, kn, Em, tab);
+    else
+        return arm_df_call(w, Ga, Gb, x, d0, d1, d2, kn, Em, tab);
+}
+
 // Raw transfer of the walker at orbit angle (sa, ca): the construction of the float32 path's
 // transfer_f32<raw> (spacecraft offsets u_i in units of L/sqrt3, arm phases x - q_m with
 // e^{i q_m}, q_m = x (k/sqrt3).u_m, polarisation response a Ga + b Gb, one-link sinc factors,
@@ -377,6 +404,7 @@ __device__ MBH_X_OUTLINE ArmOut arm_df(const XWalker& w, const f2* Ga, const f2*
 //   P_E = V + z0 + z2 - 2 z1, Q_E = V + 2 z0 - z2 - z1, V = 3 (yf0 - yf1).
 // T is linear in (Ga, Gb): the mode factors (the walker's (2,2) ones, or a higher-mode group's
 // sum), here already multiplied by the amplitude and phase factor A e^{-i dPhi}.
+template <bool kInl>
 __device__ inline void transfer_df(const XWalker& w, const f2* Ga, const f2* Gb, f2 x, f2 s2, f2 c2, f2 sa, f2 ca,
                                    const SinTab& tab, c2f T[3])
 {
@@ -402,7 +430,7 @@ __device__ inline void transfer_df(const XWalker& w, const f2* Ga, const f2* Gb,
     c2f E[3];   // e^{i q_m}
 #pragma unroll
     for (int m = 0; m < 2; ++m) {
-        const SinCos q = sincos_df(dd_mul_lazy(x, kap[m]), tab);
+        const SinCos q = sincos_df<kInl>(dd_mul_lazy(x, kap[m]), tab);
         E[m] = {dd_add_f_lazy(q.cm1, 1.0f), q.s};
     }
     const c2f e01 = cd_mul(E[0], E[1]);
@@ -414,7 +442,7 @@ __device__ inline void transfer_df(const XWalker& w, const f2* Ga, const f2* Gb,
         f2 d[3];
 #pragma unroll
         for (int q = 0; q < 3; ++q) d[q] = dd_sub_lazy(u[j][q], u[i][q]);
-        const ArmOut o = arm_df(w, Ga, Gb, x, d[0], d[1], d[2], dd_sub_lazy(kap[j], kap[i]), E[m], tab);
+        const ArmOut o = arm_df<kInl>(w, Ga, Gb, x, d[0], d[1], d[2], dd_sub_lazy(kap[j], kap[i]), E[m], tab);
         yf[a] = o.yf;
         z[a] = o.z;
     }
@@ -437,7 +465,7 @@ __device__ inline void transfer_df(const XWalker& w, const f2* Ga, const f2* Gb,
 // m = 2.  v0, 1/v0, ln v0 are the reference's at f2; t0, (ca0, sa0) its time and orbit angle
 // at f2; G4: the record's three G_c as float4 (re hi, re lo, im hi, im lo); Ga, Gb the mode
 // factors (summed over the group's modes with their v^{p_lm}).
-template <bool kAdd>
+template <bool kAdd, bool kInl>
 __device__ __forceinline__ bool group_term(const XWalker& w, const f2* Ga, const f2* Gb, f2 f, f2 fm, f2 v0, f2 iv0,
                                            f2 lnv0, float half_m, f2 t0, f2 ca0, f2 sa0, f2 x, f2 s2, f2 c2,
                                            const float4* G4, f2 tob, const SinTab& tab, c2f acc[3])
@@ -451,7 +479,7 @@ __device__ __forceinline__ bool group_term(const XWalker& w, const f2* Ga, const
     const f2 t = dd_add(t0, dd_norm(dt));
     if (!(dd_le(fm, w.fcut) && !dd_lt0(t) && dd_le(t, tob))) return false;
     // orbit angle alpha = alpha0 + 2 pi dt / yr
-    const SinCos oa = sincos_df(dd_mul_lazy(dt, kOrbRate), tab);
+    const SinCos oa = sincos_df<kInl>(dd_mul_lazy(dt, kOrbRate), tab);
     const f2 sD = oa.s, cD = oa.cm1;
     const f2 sa = dd_add_lazy(sa0, dd_add_lazy(dd_mul_lazy(sa0, cD), dd_mul_lazy(ca0, sD)));
     const f2 ca = dd_add_lazy(ca0, dd_sub_lazy(dd_mul_lazy(ca0, cD), dd_mul_lazy(sa0, sD)));
@@ -469,7 +497,7 @@ __device__ __forceinline__ bool group_term(const XWalker& w, const f2* Ga, const
     // dPhi = f (C1 + dorb) + (m/2) dPsi_PN(f2)  (the f2 t_ref terms of (m/2) Phi_22(f2) are f C1)
     const f2 dpsi = dd_mul_f_lazy(dd_add_lazy(dd_add_lazy(N, Pp), L), half_m);
     const f2 dphi = dd_norm(dd_add_lazy(dd_mul_lazy(f, dd_add_lazy(w.C1, dorb)), dpsi));
-    const SinCos ph = sincos_df(dphi, tab);
+    const SinCos ph = sincos_df<kInl>(dphi, tab);
     // amplitude ratio A = R exp(-f2^2 (1/fc^2 - 1/fc0^2)), folded with e^{-i dPhi}:
     // Z = A e^{-i dPhi} = A + A (e^{-i dPhi} - 1), and Z into the mode factors
     const f2 u = dd_mul_lazy(dd_sqr_lazy(fm), w.difc2);
@@ -478,7 +506,7 @@ __device__ __forceinline__ bool group_term(const XWalker& w, const f2* Ga, const
     const c2f za = cd_mul(Z, {Ga[0], Ga[1]}), zb = cd_mul(Z, {Gb[0], Gb[1]});
     const f2 zGa[2] = {za.re, za.im}, zGb[2] = {zb.re, zb.im};
     c2f T[3];
-    transfer_df(w, zGa, zGb, x, s2, c2, sa, ca, tab, T);
+    transfer_df<kInl>(w, zGa, zGb, x, s2, c2, sa, ca, tab, T);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const float4 g = G4[c];
@@ -501,7 +529,7 @@ __device__ __forceinline__ void edge_delta_x(const XWalker& w, const XEdge* __re
     c2f acc[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) acc[c] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
-    if (!group_term<false>(w, w.Ga, w.Gb, f, f, v0, iv0, lnv0, 1.0f, t0, ca0, sa0, x, s2, c2, p4 + 5, tob, tab, acc)) {
+    if (!group_term<false, true>(w, w.Ga, w.Gb, f, f, v0, iv0, lnv0, 1.0f, t0, ca0, sa0, x, s2, c2, p4 + 5, tob, tab, acc)) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) dl[c] = {{-1.0f, 0.0f}, {0.0f, 0.0f}};   // h = 0: r = 0
         return;
@@ -557,7 +585,7 @@ __device__ __forceinline__ void edge_delta_xhm(const XWalker& w, const XWalkerHM
         }
         // G4 of this group: float4 2, 3, 4 of the record are (G_A), (G_E), (G_T) after the 6
         // floats of t0, ca0, sa0 and 2 of padding
-        any |= group_term<true>(w, &G[0], &G[2], f, fm, v0m, iv0m, lnv0m, kGrpHalfM[g], t0, ca0, sa0, x, s2, c2, q4 + 2,
+        any |= group_term<true, false>(w, &G[0], &G[2], f, fm, v0m, iv0m, lnv0m, kGrpHalfM[g], t0, ca0, sa0, x, s2, c2, q4 + 2,
                           tob, tab, acc);
     }
     if (!any) {
