@@ -97,13 +97,15 @@ def fma_peak_tinst(sm_mhz: float) -> float:
 #    double-float chain: 1651 FMA-pipe instructions per edge on average (2536 with every edge
 #    double-float);
 #  - het_xhm_kernel<4,128> (MBH_MIXED, six modes, the higher-mode leg's batch): 5606 per edge;
-#  - direct_fused_mixed_kernel<8>: FMA-pipe instructions per (template, grid point), from a
-#    512-template launch (the 4096-template batch's block shape);
+#  - direct_fused_x_kernel<4> (MBH_MIXED direct, double-float template and products) and
+#    direct_fused_mixed_kernel<8> (MBH_MIXED_F32 direct): FMA-pipe instructions per (template,
+#    grid point), each from a 512-template launch (the 4096-template batch's block shape);
 #  - direct_fused_f64_kernel<4>: FP64-pipe instructions per (template, grid point).
 HET_KERNEL = "het_x_kernel<4,256>"
 HET_X_FMA_INST_PER_EDGE = 1650.6
 HET_X_DRAM_BYTES = 1.692e6                 # read + write per 16384-walker launch (ncu)
 HET_XHM_FMA_INST_PER_EDGE = 5605.8
+FUSED_X_FMA_INST_PER_POINT = 1851.6
 FUSED_MIXED_FMA_INST_PER_POINT = 480.3
 FUSED_F64_DFMA_INST_PER_POINT = 590.5
 STORED_DATA_BYTES = 75.74e6                # data pairs, read once per launch (ncu: 883.66 MB
@@ -229,8 +231,9 @@ def run_ours(args) -> dict | None:
     offs = [0, nw]
     if args.only == "direct":
         return run_direct_only(args, M, WL, g, src, rank, dev, stream, peaks, peak_src)
-    if args.only in ("fused", "fused64"):
-        return run_fused_only(args, M, WL, g, src, rank, dev, stream, "fp64" if args.only == "fused64" else "mixed")
+    if args.only in ("fused", "fused32", "fused64"):
+        prec = {"fused": "mixed", "fused32": "mixed_f32", "fused64": "fp64"}[args.only]
+        return run_fused_only(args, M, WL, g, src, rank, dev, stream, prec)
     if args.only == "sampler":   # profiling case: sampler iterations alone
         r = run_sampler(M, WL, g, src, ref, stream, None, iters=args.steps)
         return {"profile_case": "sampler", **r} if rank == 0 else None
@@ -387,13 +390,17 @@ def run_ours(args) -> dict | None:
 
     # ---- direct likelihood: fused generate + reduce over the brute-force batch ----
     dfused = torch.empty((3, N_DIRECT), dtype=torch.float64, device=dev)
-    M.direct_loglike_batch(src.data, th_dir_dev[:, :64].contiguous(), "mixed")
-    torch.cuda.synchronize()
-    e0.record(stream)
-    M.direct_loglike_batch(src.data, th_dir_dev, "mixed", out=dfused)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    fused_mixed_ms = e0.elapsed_time(e1)
+    dfused32 = torch.empty((3, N_DIRECT), dtype=torch.float64, device=dev)
+    fused_ms = {}
+    for prec, buf in (("mixed", dfused), ("mixed_f32", dfused32)):
+        M.direct_loglike_batch(src.data, th_dir_dev[:, :64].contiguous(), prec)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        M.direct_loglike_batch(src.data, th_dir_dev, prec, out=buf)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fused_ms[prec] = e0.elapsed_time(e1)
+    fused_mixed_ms, fused_f32_ms = fused_ms["mixed"], fused_ms["mixed_f32"]
     n64 = 256
     d64 = torch.empty((3, n64), dtype=torch.float64, device=dev)
     e0.record(stream)
@@ -402,6 +409,7 @@ def run_ours(args) -> dict | None:
     torch.cuda.synchronize()
     fused_fp64_ms = e0.elapsed_time(e1)
     dm = dfused[:, :n64].cpu().numpy()
+    dm32 = dfused32[:, :n64].cpu().numpy()
     d6 = d64.cpu().numpy()
     dscale = 0.5 * (src.data.dd + np.abs(d6[2]) + 2 * np.abs(d6[1]))
 
@@ -430,7 +438,8 @@ def run_ours(args) -> dict | None:
     roof_traffic = HET_X_DRAM_BYTES if nw == N_WALKERS else None
     stored_traffic = STORED_DATA_BYTES + N_STORED * STORED_BYTES_PER_TEMPLATE
     pts_mixed = N_DIRECT * n   # template points (one frequency of one template, 3 channels)
-    fused_mixed_tinst = FUSED_MIXED_FMA_INST_PER_POINT * pts_mixed / (fused_mixed_ms * 1e-3) / 1e12
+    fused_mixed_tinst = FUSED_X_FMA_INST_PER_POINT * pts_mixed / (fused_mixed_ms * 1e-3) / 1e12
+    fused_f32_tinst = FUSED_MIXED_FMA_INST_PER_POINT * pts_mixed / (fused_f32_ms * 1e-3) / 1e12
     fused_f64_tinst = FUSED_F64_DFMA_INST_PER_POINT * n64 * n / (fused_fp64_ms * 1e-3) / 1e12
 
     res = {
@@ -467,11 +476,17 @@ def run_ours(args) -> dict | None:
             "stored_fp32": {"templates": 2 * N_STORED, "ms": st32_ms, "GB_per_s": stored32_gbs,
                             "frac_of_hbm": stored32_gbs / peaks["hbm_gbs"]},
             "fused_mixed": {"templates": N_DIRECT, "ms": fused_mixed_ms,
-                            "templates_per_s": N_DIRECT / (fused_mixed_ms * 1e-3)},
+                            "templates_per_s": N_DIRECT / (fused_mixed_ms * 1e-3),
+                            "note": "MBH_MIXED: template and products in double-float"},
+            "fused_mixed_f32": {"templates": N_DIRECT, "ms": fused_f32_ms,
+                                "templates_per_s": N_DIRECT / (fused_f32_ms * 1e-3),
+                                "note": "MBH_MIXED_F32: double-float phase, float32 response and products"},
             "fused_fp64": {"templates": n64, "ms": fused_fp64_ms,
                            "templates_per_s": n64 / (fused_fp64_ms * 1e-3)},
             "fused_mixed_vs_fp64_rel_max": float((np.abs(dm[0] - d6[0]) / dscale).max()),
             "fused_mixed_vs_fp64_abs_max": float(np.abs(dm[0] - d6[0]).max()),
+            "fused_mixed_f32_vs_fp64_rel_max": float((np.abs(dm32[0] - d6[0]) / dscale).max()),
+            "fused_mixed_f32_vs_fp64_abs_max": float(np.abs(dm32[0] - d6[0]).max()),
         },
         "direct_hbm_gbs": stored_gbs,
         "sampler": sampler,
@@ -495,8 +510,13 @@ def run_ours(args) -> dict | None:
         "roofline_fused_mixed": {"bound": "alu", "pipe": "fp32 (FMA pipe)", "achieved": fused_mixed_tinst,
                                  "peak": fma_peak, "unit": "T fp32-pipe inst/s",
                                  "frac": fused_mixed_tinst / fma_peak, "traffic": None,
-                                 "kernel": "direct_fused_mixed_kernel<8>",
-                                 "inst_per_template_point": FUSED_MIXED_FMA_INST_PER_POINT},
+                                 "kernel": "direct_fused_x_kernel<4>",
+                                 "inst_per_template_point": FUSED_X_FMA_INST_PER_POINT},
+        "roofline_fused_mixed_f32": {"bound": "alu", "pipe": "fp32 (FMA pipe)", "achieved": fused_f32_tinst,
+                                     "peak": fma_peak, "unit": "T fp32-pipe inst/s",
+                                     "frac": fused_f32_tinst / fma_peak, "traffic": None,
+                                     "kernel": "direct_fused_mixed_kernel<8>",
+                                     "inst_per_template_point": FUSED_MIXED_FMA_INST_PER_POINT},
         "roofline_fused_fp64": {"bound": "alu", "pipe": "fp64", "achieved": fused_f64_tinst,
                                 "peak": fp64_peak, "unit": "T fp64-pipe inst/s",
                                 "frac": fused_f64_tinst / fp64_peak, "traffic": None,
@@ -519,6 +539,7 @@ def run_ours(args) -> dict | None:
         "_fp64_lnl": fp64_out[0],
         "_f32_lnl": f32_out[0],
         "_direct_fused_mixed": dfused.cpu().numpy()[0],
+        "_direct_fused_f32": dfused32.cpu().numpy()[0],
     }
     if ws > 1:
         torch.distributed.barrier()
@@ -649,7 +670,7 @@ def oracle_time(kind: str) -> dict:
 
 def run_workload0(M, WL, stream, reps: int = 20) -> dict:
     """Workload 0: the 30-day record (16384 bins from ~1e-4 Hz), one injection in noise, 64
-    walkers at 1e-3 from it; direct lnL (float64, mixed) and the 128-bin heterodyne (float64,
+    walkers at 1e-3 from it; direct lnL (float64, both mixed forms) and the 128-bin heterodyne (float64,
     MBH_MIXED) on the GPU, against the oracle timed on one host core and on all of them."""
     import torch
     g = I.grid_month()
@@ -662,6 +683,7 @@ def run_workload0(M, WL, stream, reps: int = 20) -> dict:
     outs = {}
     for name, fn in (("direct_fp64", lambda: M.direct_loglike_batch(src.data, th, "fp64", out=out)),
                      ("direct_mixed", lambda: M.direct_loglike_batch(src.data, th, "mixed", out=out)),
+                     ("direct_mixed_f32", lambda: M.direct_loglike_batch(src.data, th, "mixed_f32", out=out)),
                      ("het_fp64", lambda: M.het_loglike_batch([ref], [0, W], th, "fp64", out=out)),
                      ("het_mixed", lambda: M.het_loglike_batch([ref], [0, W], th, "mixed", out=out))):
         ms = _time_launches(fn, stream, reps)
@@ -676,6 +698,7 @@ def run_workload0(M, WL, stream, reps: int = 20) -> dict:
     od, oh = np.array(allc["lnl_direct"]), np.array(allc["lnl_het"])
     res["accuracy_vs_oracle"] = {"direct_fp64": _acc(outs["direct_fp64"] - od),
                                  "direct_mixed": _acc(outs["direct_mixed"] - od),
+                                 "direct_mixed_f32": _acc(outs["direct_mixed_f32"] - od),
                                  "het_fp64": _acc(outs["het_fp64"] - oh), "het_mixed": _acc(outs["het_mixed"] - oh)}
     return res
 
@@ -1020,8 +1043,8 @@ def run_serving(M, WL, cfg=None, n_sources: int = 32, seconds: float = 1.0,
 
 
 def run_fused_only(args, M, WL, g, src, rank, dev, stream, prec="mixed") -> dict | None:
-    """Profiling case: the fused generate-and-reduce direct path (mixed precision or float64) on
-    args.stored prior templates of the 1-yr grid."""
+    """Profiling case: the fused generate-and-reduce direct path (either mixed form or float64)
+    on args.stored prior templates of the 1-yr grid."""
     import torch
     th = WL.to_dev(I.draw_prior_batch(I.rng(1, 300 + rank), args.stored, g["t_obs"]))
     out = torch.empty((3, args.stored), dtype=torch.float64, device=dev)
@@ -1132,7 +1155,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="CPU work of the oracle baseline (0: skip)")
-    ap.add_argument("--only", default="all", choices=["all", "het", "direct", "fused", "fused64", "sampler", "hm"],
+    ap.add_argument("--only", default="all", choices=["all", "het", "direct", "fused", "fused32", "fused64", "sampler", "hm"],
                     help="profiling cases: time only the heterodyne steps, the direct path, the "
                          "sampler or the higher-mode heterodyne")
     ap.add_argument("--walkers", type=int, default=N_WALKERS, help="heterodyne batch (profiling)")
@@ -1164,6 +1187,7 @@ def main():
                 dcb = direct_cpu_baseline()
                 lnl = np.array(dcb.pop("_lnl"))
                 dcb["accuracy_fused_mixed_vs_oracle"] = _acc(res["_direct_fused_mixed"][:lnl.size] - lnl)
+                dcb["accuracy_fused_mixed_f32_vs_oracle"] = _acc(res["_direct_fused_f32"][:lnl.size] - lnl)
                 res["direct"]["cpu_baseline"] = dcb
     if res is not None:
         for k in [k for k in res if k.startswith("_")]:

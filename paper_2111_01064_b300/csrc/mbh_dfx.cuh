@@ -64,18 +64,24 @@ constexpr float kQ16a = (float)kPi16D;
 constexpr float kQ16b = (float)(kPi16D - (double)kQ16a);
 constexpr float kQ16c = (float)(kPi16D - (double)kQ16a - (double)kQ16b);
 
-// x - n 2 pi with n = round(x / 2 pi) (|n| < 2^22): |result| <= pi (1 + 2^-20).  The first
-// step x_hi - n P2a is exact: its exact value is a multiple of ulp(P2a) = 2^-21 (and of
-// ulp(x_hi) >= 2^-21 whenever n != 0) below 4 in magnitude.
-__device__ __forceinline__ f2 dd_reduce_2pi(f2 x)
+// x - n 2 pi with n = round(x / 2 pi) (|n| < 2^22).  The first step x_hi - n P2a is exact: its
+// exact value is a multiple of ulp(P2a) = 2^-21 (and of ulp(x_hi) >= 2^-21 whenever n != 0)
+// below 8 in magnitude.  n comes from a float32 product, whose rounding (~6e-8 |x|/2 pi) can
+// miss the nearest integer by one once |x| exceeds ~1e5; a second step with n2 in {-1, 0, 1}
+// (exact, and the identity when n2 = 0) brings the result within pi (1 + 2^-20).
+__device__ __forceinline__ f2 dd_reduce_2pi_step(f2 x)
 {
     const float n = rintf(x.hi * (float)(1.0 / kTwoPiD));
     const float r = __fmaf_rn(-n, kP2a, x.hi);
     const float p = __fmul_rn(n, kP2b);
     const float e = __fmaf_rn(n, kP2b, -p);
     const f2 s = two_sum(r, -p);
-    return {s.hi, __fadd_rn(__fadd_rn(s.lo, x.lo), __fmaf_rn(-n, kP2c, -e))};
+    // renormalised: x.lo (up to ulp(x.hi)/2, ~0.06 at |x| ~ 2e6) can exceed the reduced value's
+    // own ulp, and the small-angle forms below read only the high word
+    return two_sum(s.hi, __fadd_rn(__fadd_rn(s.lo, x.lo), __fmaf_rn(-n, kP2c, -e)));
 }
+
+__device__ __forceinline__ f2 dd_reduce_2pi(f2 x) { return dd_reduce_2pi_step(dd_reduce_2pi_step(x)); }
 
 // sin a and cos a - 1 for |a| <= ~0.2 (a double-float): sin a = a + a^3 (-1/6 + a^2/120 -
 // a^4/5040 + a^6/362880) with the a^3 term in float32 (its rounding <= 6e-8 |a|^3/6 < 1e-10),
@@ -105,12 +111,14 @@ __device__ __forceinline__ void dd_sincos(f2 r, const SinTab& tab, f2& s, f2& cm
 {
     const bool neg = r.hi < 0.0f;
     const f2 ar = neg ? f2{-r.hi, -r.lo} : r;
-    const float k = rintf(ar.hi * (float)(16.0 / 3.141592653589793238462643383279502884));
+    // k <= 16 for |r| <= pi (1 + 2^-20); the bound also keeps the table read in range for any
+    // input (a non-finite or unreduced argument gives a wrong value, never a stray read)
+    const float k = fminf(rintf(ar.hi * (float)(16.0 / 3.141592653589793238462643383279502884)), 16.0f);
     const float a0 = __fmaf_rn(-k, kQ16a, ar.hi);
     const float p = __fmul_rn(k, kQ16b);
     const float e = __fmaf_rn(k, kQ16b, -p);
     const f2 t = two_sum(a0, -p);
-    const f2 a = {t.hi, __fadd_rn(__fadd_rn(t.lo, ar.lo), __fmaf_rn(-k, kQ16c, -e))};
+    const f2 a = two_sum(t.hi, __fadd_rn(__fadd_rn(t.lo, ar.lo), __fmaf_rn(-k, kQ16c, -e)));
     f2 sa, ca;
     dd_sincos_small(a, sa, ca);
     const float4 T = tab.v[(int)k];
@@ -147,7 +155,7 @@ __device__ __forceinline__ f2 dd_exp(f2 u)
     const float p = __fmul_rn(n, kL2b);
     const float e = __fmaf_rn(n, kL2b, -p);
     const f2 t = two_sum(a0, -p);
-    const f2 a = {t.hi, __fadd_rn(__fadd_rn(t.lo, u.lo), __fmaf_rn(-n, kL2c, -e))};
+    const f2 a = two_sum(t.hi, __fadd_rn(__fadd_rn(t.lo, u.lo), __fmaf_rn(-n, kL2c, -e)));
     const float ah = a.hi;
     float tail = fmaf(ah, 1.0f / 479001600.0f, 1.0f / 39916800.0f);
     tail = fmaf(tail, ah, 1.0f / 3628800.0f);

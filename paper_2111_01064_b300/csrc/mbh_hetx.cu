@@ -840,6 +840,196 @@ __global__ void __launch_bounds__(BLOCK) het_xhm_kernel(const __grid_constant__ 
 }
 
 // ------------------------------------------------------------------------------------------
+// direct likelihood, fused, extended precision (MBH_MIXED, Sec. II Eqs. 2-3 over the full
+// grid): every template point in double-float on the FP32 pipe (phase and time chain, orbit at
+// t(f), amplitude, raw transfer), contracted in double-float with the data folded with the
+// frequency-only factors K_c (xdirect_data_kernel)
+// ------------------------------------------------------------------------------------------
+constexpr int kDirXThreads = 256;
+
+// Per-template constants: the float32 path's double-float phase and time chain (absolute), the
+// response constants (absolute k/sqrt3, polarisation basis, mode factors) in an XWalker (its
+// difference fields unused), the raw amplitude factor over sigma and 1/f_c^2.
+struct XDirect {
+    WalkerDF d;
+    XWalker r;
+    f2 amp, ifc2;
+};
+
+__device__ inline void xdirect_setup(const double* __restrict__ theta, int64_t W, int64_t i, double inv_sigma,
+                                     XDirect& o)
+{
+    WalkerF wf;   // the float32 constants of the float32 path's set-up are not used here
+    walker_setup_mixed(theta, W, i, o.d, wf);
+    XDer x;
+    xderive(theta, W, i, x);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        o.r.k3[j] = split_rn(x.k3[j]);
+        o.r.ev[j] = split_rn(x.ev[j]);
+    }
+    o.r.eu[0] = split_rn(x.eu[0]);
+    o.r.eu[1] = split_rn(x.eu[1]);
+    o.r.Ga[0] = split_rn(x.G[0]);
+    o.r.Ga[1] = split_rn(x.G[1]);
+    o.r.Gb[0] = split_rn(x.G[2]);
+    o.r.Gb[1] = split_rn(x.G[3]);
+    // amp (pi M)^{-7/6}, the factor of the raw template (f^{-7/6} is folded into the data):
+    // A = pi sqrt(2/3) M^2 sqrt(eta) / D v^{-7/2} exp(-(f/f_c)^2), v^{-7/2} = (pi M)^{-7/6} f^{-7/6}
+    const double M = x.mt * kMsunSec;
+    const double icb = rcbrt(kPi * M);
+    const double amp76 = kPi * 0.816496580927726 * M * M * sqrt(x.eta) / x.dist * (icb * icb * icb) * sqrt(icb);
+    o.amp = split_rn(amp76 * inv_sigma);
+    o.ifc2 = split_rn(x.ifc2);
+}
+
+// The raw template H_c of one template at one grid point (h_c = K_c H_c), double-float; false
+// outside its support (f > f_cut or t(f) outside [0, t_obs]).  q: f, f^{1/3}, f^{-1/3}, ln f/3;
+// x = pi f L/c with sin 2x, cos 2x.
+__device__ __forceinline__ bool point_x_direct(const XDirect& w, const FreqDF& q, f2 x, f2 s2, f2 c2, f2 tob,
+                                               const SinTab& tab, c2f H[3])
+{
+    const WalkerDF& d = w.d;
+    const f2 v = dd_mul_lazy(d.cbrt_piM, q.f3);
+    const f2 iv = dd_mul_lazy(d.icbrt_piM, q.fm3);
+    const f2 lnv = dd_add_lazy(d.ln_cbrt_piM, q.lnf3);
+    // Psi_PN = sum_k c_k v^{k-5} + ln v (cl5 + cl6 v) (c_1 = 0; the pinning constant in c_5)
+    f2 N = dd_mul_lazy(d.c[0], iv);
+#pragma unroll
+    for (int k = 2; k <= 5; ++k) N = dd_fma_lazy(N, iv, d.c[k]);
+    const f2 Pp = dd_mul_lazy(dd_fma_lazy(d.c[7], v, d.c[6]), v);
+    const f2 psi_pn = dd_add_lazy(dd_add_lazy(N, Pp), dd_mul_lazy(lnv, dd_fma_lazy(d.cl6, v, d.cl5)));
+    // t(f) = sum_k d_k v^{k-8} + dl6 v^{-2} ln v + t0 and the support test
+    const f2 iv2 = dd_sqr_lazy(iv), iv4 = dd_sqr_lazy(iv2), iv8 = dd_sqr_lazy(iv4);
+    f2 Q = d.d[7];
+#pragma unroll
+    for (int k = 6; k >= 0; --k) Q = dd_fma_lazy(Q, v, d.d[k]);
+    const f2 t = dd_add(dd_add_lazy(dd_mul_lazy(Q, iv8), dd_mul_lazy(dd_mul_lazy(lnv, d.dl6), iv2)), d.t0);
+    if (!(dd_le(q.f, d.fcut) && !dd_lt0(t) && dd_le(t, tob))) return false;
+    // orbit angle at t(f): alpha(t_ref) + 2 pi (t - t_ref)/yr
+    const SinCos oa = sincos_df<true>(dd_mul_lazy(dd_sub_lazy(t, d.tref), kOrbRate), tab);
+    const f2 ds = dd_add_lazy(dd_mul_lazy(d.sa_ref, oa.cm1), dd_mul_lazy(d.ca_ref, oa.s));   // sin a - sin a_ref
+    const f2 dc = dd_sub_lazy(dd_mul_lazy(d.ca_ref, oa.cm1), dd_mul_lazy(d.sa_ref, oa.s));   // cos a - cos a_ref
+    const f2 sa = dd_add_lazy(d.sa_ref, ds), ca = dd_add_lazy(d.ca_ref, dc);
+    // Phi = f (c1 + 2 pi AU/c k.(c(t) - c(t_ref))) + Psi_PN (c1 holds 2 pi t_ref - psi'(f_max) and
+    // 2 pi AU/c k.c(t_ref); kx, ky carry 2 pi AU/c)
+    const f2 dk = dd_add_lazy(dd_mul_lazy(d.kx, dc), dd_mul_lazy(d.ky, ds));
+    const f2 phi = dd_norm(dd_add_lazy(dd_mul_lazy(q.f, dd_add_lazy(d.c1, dk)), psi_pn));
+    const SinCos ph = sincos_df<true>(phi, tab);
+    // raw amplitude amp (pi M)^{-7/6} exp(-(f/f_c)^2)/sigma, Z = A e^{-i Phi} into the mode factors
+    const f2 u = dd_mul_lazy(dd_sqr_lazy(q.f), w.ifc2);
+    const f2 A = dd_mul_lazy(w.amp, dd_exp({-u.hi, -u.lo}));
+    const c2f Z = {dd_add_lazy(A, dd_mul_lazy(A, ph.cm1)), dd_mul_lazy(A, {-ph.s.hi, -ph.s.lo})};
+    const c2f za = cd_mul(Z, {w.r.Ga[0], w.r.Ga[1]}), zb = cd_mul(Z, {w.r.Gb[0], w.r.Gb[1]});
+    const f2 zGa[2] = {za.re, za.im}, zGb[2] = {zb.re, zb.im};
+    transfer_df<true>(w.r, zGa, zGb, x, s2, c2, sa, ca, tab, H);
+    return true;
+}
+
+// block (template tile of T, frequency chunk): the point's tables and folded data are loaded
+// once and reused by the T templates; each thread keeps per-template double-float sums in
+// shared memory, reduced per template at the end (float64) into part[template][chunk].
+template <int T>
+__global__ void __launch_bounds__(kDirXThreads)
+    direct_fused_x_kernel(const double* __restrict__ theta, int64_t W, const float4* __restrict__ ft1,
+                          const float4* __restrict__ ft2, const float4* __restrict__ ftx,
+                          const float2* __restrict__ ftx2, double t_obs, const float4* __restrict__ wdx,
+                          const float2* __restrict__ wvx, int64_t n, int64_t chunk, int nchunks, double inv_sigma,
+                          double2* __restrict__ part)
+{
+    __shared__ XDirect ws[T];
+    __shared__ SinTab tab;
+    __shared__ float4 acc[T][kDirXThreads];   // per template: <d|h> hi, lo, <h|h> hi, lo
+    __shared__ double sm[32 * 2];
+    __shared__ f2 s_tob;
+    const int64_t w0 = (int64_t)blockIdx.x * T;
+    const int ch = blockIdx.y;
+    const int nt = (int)std::min<int64_t>(T, W - w0);
+    load_sintab(tab);
+    if (threadIdx.x < nt) xdirect_setup(theta, W, w0 + threadIdx.x, inv_sigma, ws[threadIdx.x]);
+    if (threadIdx.x == 0) s_tob = split_rn(t_obs);
+#pragma unroll
+    for (int t = 0; t < T; ++t) acc[t][threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+    const f2 tob = s_tob;
+    const int64_t kb = (int64_t)ch * chunk, ke = std::min<int64_t>(n, kb + chunk);
+    for (int64_t k = kb + threadIdx.x; k < ke; k += kDirXThreads) {
+        const float4 a = __ldg(ft1 + k), b = __ldg(ft2 + k), xa = __ldg(ftx + k);
+        const float2 xb = __ldg(ftx2 + k);
+        const FreqDF q = {{a.x, a.y}, {a.z, a.w}, {b.x, b.y}, {b.z, b.w}};
+        const f2 x = {xa.x, xa.y}, s2 = {xa.z, xa.w}, c2 = {xb.x, xb.y};
+        c2f D[3];
+        f2 V[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float4 dv = __ldg(wdx + (int64_t)c * n + k);
+            const float2 vv = __ldg(wvx + (int64_t)c * n + k);
+            D[c] = {{dv.x, dv.y}, {dv.z, dv.w}};
+            V[c] = {vv.x, vv.y};
+        }
+        for (int t = 0; t < nt; ++t) {
+            c2f H[3];
+            if (!point_x_direct(ws[t], q, x, s2, c2, tob, tab, H)) continue;
+            f2 sd = {0.0f, 0.0f}, sh = {0.0f, 0.0f};
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                // Re conj(conj(K) D) H = Re conj(D) h; |H|^2 |K|^2 V = |h|^2 V
+                sd = dd_add_lazy(sd, dd_add_lazy(dd_mul_lazy(D[c].re, H[c].re), dd_mul_lazy(D[c].im, H[c].im)));
+                sh = dd_add_lazy(sh, dd_mul_lazy(V[c], dd_add_lazy(dd_sqr_lazy(H[c].re), dd_sqr_lazy(H[c].im))));
+            }
+            float4 s = acc[t][threadIdx.x];
+            f2 adh = {s.x, s.y}, ahh = {s.z, s.w};
+            df_acc(adh, sd);
+            df_acc(ahh, sh);
+            acc[t][threadIdx.x] = make_float4(adh.hi, adh.lo, ahh.hi, ahh.lo);
+        }
+    }
+    for (int t = 0; t < nt; ++t) {
+        const float4 s = acc[t][threadIdx.x];
+        double r[2] = {df_to_double({s.x, s.y}), df_to_double({s.z, s.w})};
+        block_sum<2>(r, sm);
+        if (threadIdx.x == 0) part[(w0 + t) * nchunks + ch] = make_double2(r[0], r[1]);
+    }
+}
+
+// The extended direct pass's tables of one data set: per grid point x = pi f L/c with sin 2x,
+// cos 2x, and per channel the data with the frequency-only factors folded in (float64, split
+// once): conj(K_c) sigma 4 df d/S and |K_c|^2 sigma^2 4 df/S, with K_c the factors that the raw
+// transfer leaves out (including f^{-7/6}, as the float32 pass's folded data).
+__global__ void xdirect_data_kernel(double f0, double df, int64_t n, double sigma, const double2* __restrict__ wd,
+                                    const double* __restrict__ wv, float4* __restrict__ ftx,
+                                    float2* __restrict__ ftx2, float4* __restrict__ wdx, float2* __restrict__ wvx)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const double f = f0 + (double)k * df;
+        const double x = kPi * kArmSec * f;
+        double s1, c1, s2x, c2x, s3, c3;
+        sincos(x, &s1, &c1);
+        sincos(2.0 * x, &s2x, &c2x);
+        sincos(3.0 * x, &s3, &c3);
+        const f2 xs = split_rn(x), ss = split_rn(s2x), cs = split_rn(c2x);
+        ftx[k] = make_float4(xs.hi, xs.lo, ss.hi, ss.lo);
+        ftx2[k] = make_float2(cs.hi, cs.lo);
+        // K: W = (1 - D^2)(-x) e^{-ix} f^{-7/6}, 1 - D = 2 sin x (sin x, cos x), D = e^{-2ix};
+        // K_A = W/sqrt2, K_E = W/sqrt6, K_T = W (1 - D)/sqrt3
+        const double wm = -2.0 * x * s2x * pow(f, -7.0 / 6.0);
+        const double wr = wm * s3, wi = wm * c3;
+        const double ar = 2.0 * s1 * s1, ai = 2.0 * s1 * c1;
+        const double Kr[3] = {wr / kSqrt2, wr / kSqrt6, (wr * ar - wi * ai) / kSqrt3};
+        const double Ki[3] = {wi / kSqrt2, wi / kSqrt6, (wr * ai + wi * ar) / kSqrt3};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double2 d = wd[c * n + k];
+            const double dr = sigma * d.x, di = sigma * d.y;
+            const f2 re = split_rn(Kr[c] * dr + Ki[c] * di), im = split_rn(Kr[c] * di - Ki[c] * dr);
+            wdx[c * n + k] = make_float4(re.hi, re.lo, im.hi, im.lo);
+            const f2 vv = split_rn(sigma * sigma * wv[c * n + k] * (Kr[c] * Kr[c] + Ki[c] * Ki[c]));
+            wvx[c * n + k] = make_float2(vv.hi, vv.lo);
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
 // reference tables
 // ------------------------------------------------------------------------------------------
 __global__ void xref_kernel(const double* __restrict__ theta0, XDer* __restrict__ out)
@@ -1169,6 +1359,45 @@ cudaError_t prepare_x_tables_hm(mbh_ref* R, cudaStream_t st)
     e = select_f32_edges(R, st, &kappa);
     if (e == cudaSuccess) R->mix.xgrp = R->x_grp;
     return e;
+}
+
+mbh_status make_x_direct_tables(mbh_data* D, cudaStream_t st)
+{
+    const int64_t n = D->grid.n;
+    cudaError_t e = cudaMalloc(&D->ftx, sizeof(float4) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&D->ftx2, sizeof(float2) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&D->wdx, sizeof(float4) * 3 * n);
+    if (e == cudaSuccess) e = cudaMalloc(&D->wvx, sizeof(float2) * 3 * n);
+    if (e != cudaSuccess) return cuda_fail(e, "extended direct tables");
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 32);
+    xdirect_data_kernel<<<blocks, 256, 0, st>>>(D->grid.f0, D->grid.df, n, D->sigma, D->wd, D->wv, D->ftx, D->ftx2,
+                                                 D->wdx, D->wvx);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? MBH_OK : cuda_fail(e, "extended direct tables");
+}
+
+mbh_status launch_direct_fused_x(const mbh_data* data, const double* theta, int64_t W, double* out,
+                                 cudaStream_t st)
+{
+    constexpr int T = 4;
+    const int64_t tiles = (W + T - 1) / T;
+    if (tiles > 0x7fffffff) return fail(MBH_EINVAL, "W too large");
+    int64_t chunk;
+    int nchunks;
+    direct_chunks(data->grid.n, tiles, 1 << 14, chunk, nchunks);
+    double2* part = nullptr;
+    cudaError_t e = cudaMallocAsync(&part, sizeof(double2) * W * nchunks, st);
+    if (e != cudaSuccess) return cuda_fail(e, "direct_loglike_batch alloc");
+    dim3 grid((unsigned)tiles, (unsigned)nchunks);
+    direct_fused_x_kernel<T><<<grid, kDirXThreads, 0, st>>>(theta, W, data->ftab, data->ftab2, data->ftx, data->ftx2,
+                                                            data->grid.t_obs, data->wdx, data->wvx, data->grid.n,
+                                                            chunk, nchunks, 1.0 / data->sigma, part);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        cudaFreeAsync(part, st);
+        return cuda_fail(e, "direct_fused_x_kernel");
+    }
+    return direct_finish(part, nchunks, W, data->dd, out, st);
 }
 
 void free_x_tables(mbh_ref* R)

@@ -176,6 +176,9 @@ mbh_status launch_direct_fused_mixed(const mbh_data* data, const double* theta, 
                                      double* out, cudaStream_t st, uint32_t modes = 1u);
 cudaError_t alloc_ref_tables(mbh_ref* R);
 mbh_status make_freq_tables(mbh_data* D, cudaStream_t st);
+mbh_status make_x_direct_tables(mbh_data* D, cudaStream_t st);
+mbh_status launch_direct_fused_x(const mbh_data* data, const double* theta, int64_t W, double* out,
+                                 cudaStream_t st);
 void free_ref_tables(mbh_ref* R);
 cudaError_t prepare_mixed_tables(mbh_ref* R, cudaStream_t st);
 // heterodyne kernel instantiations: launcher and kernel address (for occupancy queries)
@@ -241,6 +244,10 @@ struct mbh_data {
     float4* ftab3 = nullptr; // [n] (sin x, cos x, 0, x), x = pi f L/c (the one-link phase)
     float2* wdk = nullptr;   // [3][n] conj(K_c) sigma 4 df d/S: the fused mixed pass's data, with the
     float* wvk = nullptr;    // [3][n] |K_c|^2 sigma^2 4 df/S  frequency-only factors K_c folded in
+    float4* ftx = nullptr;   // [n] (x hi, x lo, sin 2x hi, lo), x = pi f L/c: the extended direct pass
+    float2* ftx2 = nullptr;  // [n] (cos 2x hi, lo)
+    float4* wdx = nullptr;   // [3][n] conj(K_c) sigma 4 df d/S as (re hi, re lo, im hi, im lo)
+    float2* wvx = nullptr;   // [3][n] |K_c|^2 sigma^2 4 df/S as a float pair
     double sigma = 1.0;      // scale of the float32 copies: h/sigma is O(1)
     int shift = 0;           // round(log2 sigma): templates are split as h 2^-shift
     double dd = 0.0;         // <d|d>

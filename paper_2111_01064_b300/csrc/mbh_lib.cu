@@ -328,6 +328,12 @@ extern "C" mbh_status mbh_data_create(const mbh_grid* grid, const void* d_dev, c
         mbh_data_free(D);
         return s;
     }
+    if (mbh_status s = make_x_direct_tables(D, st)) {
+        cudaFreeAsync(part, st);
+        cudaStreamSynchronize(st);
+        mbh_data_free(D);
+        return s;
+    }
     sum_partials_kernel<<<1, 32, 0, st>>>(part, nb, dd_dev);
     e = cudaMemcpyAsync(&D->dd, dd_dev, sizeof(double), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaFreeAsync(part, st);
@@ -357,6 +363,10 @@ extern "C" void mbh_data_free(mbh_data* data)
     if (data->ftab3) cudaFree(data->ftab3);
     if (data->wdk) cudaFree(data->wdk);
     if (data->wvk) cudaFree(data->wvk);
+    if (data->ftx) cudaFree(data->ftx);
+    if (data->ftx2) cudaFree(data->ftx2);
+    if (data->wdx) cudaFree(data->wdx);
+    if (data->wvx) cudaFree(data->wvx);
     delete data;
 }
 
@@ -477,13 +487,14 @@ extern "C" mbh_status direct_loglike_batch_hm(const mbh_data* data, const double
                                               uint32_t modes, mbh_precision precision, double* out_dev,
                                               void* stream)
 {
-    if (mbh_status s = check_modes(modes, precision)) return s;
+    // higher modes: MBH_MIXED and MBH_MIXED_F32 both take the float32-response pass
+    if (mbh_status s = check_modes(modes, precision == MBH_MIXED_F32 ? MBH_MIXED : precision)) return s;
     if (modes == 1u) return direct_loglike_batch(data, theta_dev, W, precision, out_dev, stream);
     if (!data) return fail(MBH_EINVAL, "data is NULL");
     if (W < 0) return fail(MBH_EINVAL, "W < 0");
     if (W == 0) return MBH_OK;
     if (!theta_dev || !out_dev) return fail(MBH_EINVAL, "NULL buffer");
-    if (precision == MBH_MIXED)
+    if (precision == MBH_MIXED || precision == MBH_MIXED_F32)
         return launch_direct_fused_mixed(data, theta_dev, W, out_dev, (cudaStream_t)stream, modes);
     return direct_f64(data, theta_dev, W, modes, out_dev, (cudaStream_t)stream);
 }
@@ -496,7 +507,10 @@ extern "C" mbh_status direct_loglike_batch(const mbh_data* data, const double* t
     if (W == 0) return MBH_OK;
     if (!theta_dev || !out_dev) return fail(MBH_EINVAL, "NULL buffer");
     cudaStream_t st = (cudaStream_t)stream;
-    if (precision == MBH_MIXED) return launch_direct_fused_mixed(data, theta_dev, W, out_dev, st);
+    // MBH_MIXED: the template in double-float at every point (extended-precision pass);
+    // MBH_MIXED_F32: double-float phase, float32 response and products
+    if (precision == MBH_MIXED) return launch_direct_fused_x(data, theta_dev, W, out_dev, st);
+    if (precision == MBH_MIXED_F32) return launch_direct_fused_mixed(data, theta_dev, W, out_dev, st);
     if (precision != MBH_FP64) return fail(MBH_EINVAL, "unknown precision %d", (int)precision);
     return direct_f64(data, theta_dev, W, 1u, out_dev, st);
 }

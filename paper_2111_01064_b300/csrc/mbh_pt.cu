@@ -657,10 +657,9 @@ extern "C" mbh_status mbh_pt_create_multi(const mbh_pt_opts* o, const mbh_ref* c
         if (!(betas_host[t] >= 0.0) || !std::isfinite(betas_host[t])) return fail(MBH_EINVAL, "betas must be finite and >= 0");
     if (o->precision != MBH_FP64 && o->precision != MBH_MIXED && o->precision != MBH_MIXED_F32)
         return fail(MBH_EINVAL, "unknown precision");
-    if (data && o->precision == MBH_MIXED_F32) return fail(MBH_EINVAL, "MBH_MIXED_F32 is a heterodyne precision");
     const uint32_t modes = o->modes ? o->modes : 1u;
     if (data)
-        if (mbh_status s = check_modes(modes, o->precision)) return s;
+        if (mbh_status s = check_modes(modes, o->precision == MBH_MIXED_F32 ? MBH_MIXED : o->precision)) return s;
     if (mbh_status s = check_device()) return s;
     int dev = -1;
     cudaGetDevice(&dev);
