@@ -77,15 +77,15 @@ __device__ __forceinline__ f2 split_rn(double x)
 // walkers reach |delta| ~ 4).  The float32 error grows with |1 + delta| and the sensitivity with
 // |delta|: a walker's float32 value is kept while every channel has |delta| <= kDeltaF32Max,
 // where the product is at most 18 times its value at |delta| = 4 (5e-7 per unit of S_e, so the
-// float32 edges add at most 1.7e-4 to |dlnL|); beyond that the edge takes the double-float
-// chain.  With higher modes the float32 terms are the modes' shares u_g = h0_g/h0 of the
+// float32 edges add at most 5e-7 kF32Budget / kF32EdgeError = 8.3e-4 to |dlnL|, the double-float
+// edges ~1e-5); beyond that the edge takes the double-float chain.  With higher modes the float32 terms are the modes' shares u_g = h0_g/h0 of the
 // reference, so near a zero of h0 (modes that cancel) the error grows by kappa = sum |u_g|:
 // the selection weighs S_e by kappa_e.  Edges are chosen in aligned groups of kF32Group: with
 // four threads per walker (the default) a group is one round of a warp's edges, so no warp
 // runs both paths for one round.
 constexpr double kDeltaMax = 3.0;
 constexpr double kF32EdgeError = 3e-7;
-constexpr double kF32Budget = 1e-4;
+constexpr double kF32Budget = 5e-4;
 constexpr float kDeltaF32Max = 16.0f;
 constexpr int kF32Group = 4;
 
@@ -649,6 +649,7 @@ template <int G, int BLOCK>
 __global__ void __launch_bounds__(BLOCK) het_x_kernel(const __grid_constant__ HetLaunch L)
 {
     constexpr int WPB = BLOCK / G;
+    constexpr int kSlot = (WPB + 31) / 32 * 32;
     __shared__ XWalker xw[WPB];
     __shared__ WalkerDF wsd[WPB];   // float32-ratio edges: the float32 path's walker constants
     __shared__ WalkerF wsf[WPB];
@@ -665,11 +666,12 @@ __global__ void __launch_bounds__(BLOCK) het_x_kernel(const __grid_constant__ He
         __syncthreads();
         // the walkers' two set-ups (float64 chains bound by latency, not by the float64 pipe's
         // rate) on different warps where the block has them: slot t < WPB sets up walker t's
-        // double-float constants, slot WPB + t its float32-path constants
-        for (int t = threadIdx.x; t < 2 * WPB; t += BLOCK) {
-            const int j = t < WPB ? t : t - WPB;
-            if (w0 + j >= S.w_end) continue;
-            if (t < WPB) {
+        // double-float constants, slot kSlot + t its float32-path constants (kSlot: WPB rounded
+        // up to whole warps, so that no warp runs both chains one after the other)
+        for (int t = threadIdx.x; t < 2 * kSlot; t += BLOCK) {
+            const int j = t < kSlot ? t : t - kSlot;
+            if (j >= WPB || w0 + j >= S.w_end) continue;
+            if (t < kSlot) {
                 xwalker_setup(L.theta, L.W, w0 + j, *S.mix.xder, xw[j]);
             } else if (S.mix.xn32 > 0) {
                 walker_setup_mixed(L.theta, L.W, w0 + j, wsd[j], wsf[j]);
@@ -744,6 +746,7 @@ template <int G, int BLOCK>
 __global__ void __launch_bounds__(BLOCK) het_xhm_kernel(const __grid_constant__ HetLaunch L)
 {
     constexpr int WPB = BLOCK / G;
+    constexpr int kSlot = (WPB + 31) / 32 * 32;
     __shared__ XWalker xw[WPB];
     __shared__ XWalkerHM xh[WPB];
     __shared__ WalkerDF wsd[WPB];   // float32-ratio edges: the float32 path's walker constants
@@ -761,10 +764,10 @@ __global__ void __launch_bounds__(BLOCK) het_xhm_kernel(const __grid_constant__ 
         const bool active = w0 + lw < S.w_end;
         __syncthreads();
         // the walkers' four set-ups on different warps where the block has them (slot
-        // k WPB + t: set-up k of walker t)
-        for (int t = threadIdx.x; t < 4 * WPB; t += BLOCK) {
-            const int k = t / WPB, j = t - k * WPB;
-            if (w0 + j >= S.w_end) continue;
+        // k kSlot + t: set-up k of walker t, kSlot = WPB rounded up to whole warps)
+        for (int t = threadIdx.x; t < 4 * kSlot; t += BLOCK) {
+            const int k = t / kSlot, j = t - k * kSlot;
+            if (j >= WPB || w0 + j >= S.w_end) continue;
             if (k == 0) {
                 xwalker_setup(L.theta, L.W, w0 + j, *S.mix.xder, xw[j]);
             } else if (k == 1) {
