@@ -753,19 +753,25 @@ def run_higher_modes(M, WL, g, stream, reps: int = 5) -> dict:
         ms = e0.elapsed_time(e1) / n
         res[prec] = {"ms": ms, "lnL_evals_per_s": nw / (ms * 1e-3)}
         outs[prec] = out.cpu().numpy().copy()
-    # brute-force (direct) likelihood with the six modes, mixed precision, full 1-yr grid
+    # brute-force (direct) likelihood with the six modes, both mixed forms, full 1-yr grid
     nd = 512
     thd = theta[:, :nd].contiguous()
-    outd = torch.empty((3, nd), dtype=torch.float64, device="cuda")
-    M.direct_loglike_batch_hm(data, thd[:, :8].contiguous(), 0x3F, "mixed")
-    torch.cuda.synchronize()
-    e0.record(stream)
-    M.direct_loglike_batch_hm(data, thd, 0x3F, "mixed", out=outd)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    msd = e0.elapsed_time(e1)
-    res["direct_mixed"] = {"templates": nd, "grid_points": int(g["n"]), "ms": msd,
-                           "templates_per_s": nd / (msd * 1e-3)}
+    outd = {}
+    for prec, key in (("mixed", "direct_mixed"), ("mixed_f32", "direct_mixed_f32")):
+        outd[prec] = torch.empty((3, nd), dtype=torch.float64, device="cuda")
+        M.direct_loglike_batch_hm(data, thd[:, :8].contiguous(), 0x3F, prec)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        M.direct_loglike_batch_hm(data, thd, 0x3F, prec, out=outd[prec])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        msd = e0.elapsed_time(e1)
+        res[key] = {"templates": nd, "grid_points": int(g["n"]), "ms": msd,
+                    "templates_per_s": nd / (msd * 1e-3)}
+    n64 = 16
+    o64 = M.direct_loglike_batch_hm(data, thd[:, :n64].contiguous(), 0x3F, "fp64").cpu().numpy()
+    for prec, key in (("mixed", "direct_mixed"), ("mixed_f32", "direct_mixed_f32")):
+        res[key]["accuracy_vs_fp64_kernel"] = _acc(outd[prec][0, :n64].cpu().numpy() - o64[0])
     res["accuracy_mixed_vs_fp64_kernel"] = _acc(outs["mixed"][0] - outs["fp64"][0])
     res["accuracy_mixed_f32_vs_fp64_kernel"] = _acc(outs["mixed_f32"][0] - outs["fp64"][0])
     res["speedup_mixed_over_fp64"] = res["mixed"]["lnL_evals_per_s"] / res["fp64"]["lnL_evals_per_s"]

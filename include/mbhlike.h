@@ -73,8 +73,8 @@ typedef enum {
                           double-float (phase, t(f), orbit, response, amplitude, taper) and
                           its products with the data, sums in float64; |dlnL| against float64
                           <= 1e-3 up to SNR ~1000 (<h|h> <= 1e6), beyond it ~1e-11 <h|h> (the
-                          ~1e6-rad phase carried to |Phi| 2^-48).  Higher modes: as
-                          MBH_MIXED_F32.
+                          ~1e6-rad phase carried to |Phi| 2^-48); with higher modes the same per
+                          distinct m (direct_loglike_batch_hm).
                           Heterodyne: every edge value formed relative to the reference in
                           double-float (phase, time and amplitude as differences of
                           per-walker float64 coefficients, the response, the ratio
@@ -403,10 +403,12 @@ MBH_API mbh_status mbh_server_loadgen(mbh_server* server, const int32_t* source_
  * H_lm(x), x = (pi M f2)^{2/3}; polarisations from the spin-weighted harmonics
  * -2Y_lm(iota, phi_ref).  Mode mask: bit 0 (2,2), bit 1 (3,3), bit 2 (4,4),
  * bit 3 (2,1), bit 4 (3,2), bit 5 (4,3); mask 1 is W0 and these calls then do
- * exactly what the (2,2) calls do.  Both precisions: the mixed path evaluates each
- * mode's large phase in double-float and its response in float32 (heterodyne: the
- * delta form per mode).  Layouts, ownership and errors as in the (2,2) calls (mixed
- * templates are complex64); an empty mask or bits above 5 return MBH_EINVAL. */
+ * exactly what the (2,2) calls do.  Mixed precisions: templates (complex64) and
+ * MBH_MIXED_F32 evaluate each mode's large phase in double-float and its response in
+ * float32; MBH_MIXED evaluates the direct likelihood's template and products in
+ * double-float, and the heterodyne ratio relative to the reference per group of modes
+ * sharing m (as for the (2,2) mode).  Layouts, ownership and errors as in the (2,2)
+ * calls; an empty mask or bits above 5 return MBH_EINVAL. */
 MBH_API mbh_status template_batch_hm(const mbh_grid* grid, const double* theta_dev, int64_t W,
                                      uint32_t modes, mbh_precision precision, void* h_out_dev,
                                      void* stream);

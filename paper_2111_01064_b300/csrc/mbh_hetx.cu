@@ -886,61 +886,127 @@ __device__ inline void xdirect_setup(const double* __restrict__ theta, int64_t W
     o.ifc2 = split_rn(x.ifc2);
 }
 
-// The raw template H_c of one template at one grid point (h_c = K_c H_c), double-float; false
-// outside its support (f > f_cut or t(f) outside [0, t_obs]).  q: f, f^{1/3}, f^{-1/3}, ln f/3;
-// x = pi f L/c with sin 2x, cos 2x.
-__device__ __forceinline__ bool point_x_direct(const XDirect& w, const FreqDF& q, f2 x, f2 s2, f2 c2, f2 tob,
-                                               const SinTab& tab, c2f H[3])
+// Amplitude factor (2/m)^{-7/6} of the m-groups (order of hm_group_mask: m = 2, 3, 4, 1): a
+// mode's v^{-7/2} at f2 = 2f/m is (pi M)^{-7/6} f^{-7/6} (2/m)^{-7/6}, and the folded data carry
+// f^{-7/6}.
+__constant__ f2 kGrpAmp[4] = {df_const(1.0), df_const(1.6048697909004944), df_const(2.2449240966187460),
+                              df_const(0.44544935907016965)};
+
+// One chain of the raw template H_c (h_c = K_c H_c) at one grid point, double-float: the (2,2)
+// model at f2 = q2.f (the grid's f for the (2,2) mode; 2f/m for a higher-mode group), i.e. the
+// phase and time chain at f2, the support test (f2 <= f_cut, t(f2) in [0, t_obs]), the orbit
+// at t(f2), Phi = (m/2) Phi_22(f2), the amplitude (pi M)^{-7/6} exp(-(f2/f_c)^2)/sigma times
+// ampr, and the raw transfer at the point's x of the mode factors times A e^{-i Phi}: the
+// walker's (2,2) factors, or with kHM the group's modes' factors weighted by v^{p_lm}.
+// q2: f2, f2^{1/3}, f2^{-1/3}, ln f2/3; x = pi f L/c with sin 2x, cos 2x (the grid's f).
+template <bool kInl, bool kHM>
+__device__ __forceinline__ bool x_direct_term(const XDirect& w, const XWalkerHM* wh, uint32_t gmask, const FreqDF& q2,
+                                              float half_m, f2 ampr, f2 x, f2 s2, f2 c2, f2 tob, const SinTab& tab,
+                                              c2f H[3])
 {
     const WalkerDF& d = w.d;
-    const f2 v = dd_mul_lazy(d.cbrt_piM, q.f3);
-    const f2 iv = dd_mul_lazy(d.icbrt_piM, q.fm3);
-    const f2 lnv = dd_add_lazy(d.ln_cbrt_piM, q.lnf3);
+    const f2 v = dd_mul_lazy(d.cbrt_piM, q2.f3);
+    const f2 iv = dd_mul_lazy(d.icbrt_piM, q2.fm3);
+    const f2 lnv = dd_add_lazy(d.ln_cbrt_piM, q2.lnf3);
     // Psi_PN = sum_k c_k v^{k-5} + ln v (cl5 + cl6 v) (c_1 = 0; the pinning constant in c_5)
     f2 N = dd_mul_lazy(d.c[0], iv);
 #pragma unroll
     for (int k = 2; k <= 5; ++k) N = dd_fma_lazy(N, iv, d.c[k]);
     const f2 Pp = dd_mul_lazy(dd_fma_lazy(d.c[7], v, d.c[6]), v);
     const f2 psi_pn = dd_add_lazy(dd_add_lazy(N, Pp), dd_mul_lazy(lnv, dd_fma_lazy(d.cl6, v, d.cl5)));
-    // t(f) = sum_k d_k v^{k-8} + dl6 v^{-2} ln v + t0 and the support test
+    // t(f2) = sum_k d_k v^{k-8} + dl6 v^{-2} ln v + t0 and the support test
     const f2 iv2 = dd_sqr_lazy(iv), iv4 = dd_sqr_lazy(iv2), iv8 = dd_sqr_lazy(iv4);
     f2 Q = d.d[7];
 #pragma unroll
     for (int k = 6; k >= 0; --k) Q = dd_fma_lazy(Q, v, d.d[k]);
     const f2 t = dd_add(dd_add_lazy(dd_mul_lazy(Q, iv8), dd_mul_lazy(dd_mul_lazy(lnv, d.dl6), iv2)), d.t0);
-    if (!(dd_le(q.f, d.fcut) && !dd_lt0(t) && dd_le(t, tob))) return false;
-    // orbit angle at t(f): alpha(t_ref) + 2 pi (t - t_ref)/yr
-    const SinCos oa = sincos_df<true>(dd_mul_lazy(dd_sub_lazy(t, d.tref), kOrbRate), tab);
+    if (!(dd_le(q2.f, d.fcut) && !dd_lt0(t) && dd_le(t, tob))) return false;
+    // orbit angle at t: alpha(t_ref) + 2 pi (t - t_ref)/yr
+    const SinCos oa = sincos_df<kInl>(dd_mul_lazy(dd_sub_lazy(t, d.tref), kOrbRate), tab);
     const f2 ds = dd_add_lazy(dd_mul_lazy(d.sa_ref, oa.cm1), dd_mul_lazy(d.ca_ref, oa.s));   // sin a - sin a_ref
     const f2 dc = dd_sub_lazy(dd_mul_lazy(d.ca_ref, oa.cm1), dd_mul_lazy(d.sa_ref, oa.s));   // cos a - cos a_ref
     const f2 sa = dd_add_lazy(d.sa_ref, ds), ca = dd_add_lazy(d.ca_ref, dc);
-    // Phi = f (c1 + 2 pi AU/c k.(c(t) - c(t_ref))) + Psi_PN (c1 holds 2 pi t_ref - psi'(f_max) and
-    // 2 pi AU/c k.c(t_ref); kx, ky carry 2 pi AU/c)
+    // Phi_22(f2) = f2 (c1 + 2 pi AU/c k.(c(t) - c(t_ref))) + Psi_PN (c1 holds 2 pi t_ref -
+    // psi'(f_max) and 2 pi AU/c k.c(t_ref); kx, ky carry 2 pi AU/c); a mode's phase is m/2 times
+    // it (its Doppler term (m/2) f2 ... = f ...)
     const f2 dk = dd_add_lazy(dd_mul_lazy(d.kx, dc), dd_mul_lazy(d.ky, ds));
-    const f2 phi = dd_norm(dd_add_lazy(dd_mul_lazy(q.f, dd_add_lazy(d.c1, dk)), psi_pn));
-    const SinCos ph = sincos_df<true>(phi, tab);
-    // raw amplitude amp (pi M)^{-7/6} exp(-(f/f_c)^2)/sigma, Z = A e^{-i Phi} into the mode factors
-    const f2 u = dd_mul_lazy(dd_sqr_lazy(q.f), w.ifc2);
-    const f2 A = dd_mul_lazy(w.amp, dd_exp({-u.hi, -u.lo}));
+    f2 phi = dd_norm(dd_add_lazy(dd_mul_lazy(q2.f, dd_add_lazy(d.c1, dk)), psi_pn));
+    if (kHM && half_m != 1.0f) phi = dd_norm(dd_mul_f_lazy(phi, half_m));
+    const SinCos ph = sincos_df<kInl>(phi, tab);
+    // raw amplitude amp (pi M)^{-7/6} exp(-(f2/f_c)^2)/sigma, Z = A e^{-i Phi} into the mode factors
+    const f2 u = dd_mul_lazy(dd_sqr_lazy(q2.f), w.ifc2);
+    f2 A = dd_mul_lazy(w.amp, dd_exp({-u.hi, -u.lo}));
+    if (kHM) A = dd_mul_lazy(A, ampr);
     const c2f Z = {dd_add_lazy(A, dd_mul_lazy(A, ph.cm1)), dd_mul_lazy(A, {-ph.s.hi, -ph.s.lo})};
-    const c2f za = cd_mul(Z, {w.r.Ga[0], w.r.Ga[1]}), zb = cd_mul(Z, {w.r.Gb[0], w.r.Gb[1]});
+    f2 G[4] = {w.r.Ga[0], w.r.Ga[1], w.r.Gb[0], w.r.Gb[1]};
+    if constexpr (kHM) {
+        // the group's mode factors: sum of v^{p_lm} (Ga, Gb)_lm
+#pragma unroll
+        for (int j = 0; j < 4; ++j) G[j] = {0.0f, 0.0f};
+        for (uint32_t bm = gmask; bm; bm &= bm - 1) {
+            const int md = __ffs(bm) - 1;
+            f2 vp = {1.0f, 0.0f};
+            for (int j = 0; j < hm_vpow(md); ++j) vp = dd_mul_lazy(vp, v);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) G[j] = dd_add_lazy(G[j], dd_mul_lazy(vp, wh->G[md][j]));
+        }
+    }
+    const c2f za = cd_mul(Z, {G[0], G[1]}), zb = cd_mul(Z, {G[2], G[3]});
     const f2 zGa[2] = {za.re, za.im}, zGb[2] = {zb.re, zb.im};
-    transfer_df<true>(w.r, zGa, zGb, x, s2, c2, sa, ca, tab, H);
+    transfer_df<kInl>(w.r, zGa, zGb, x, s2, c2, sa, ca, tab, H);
     return true;
+}
+
+// The raw template H_c of one template at one grid point, (2,2) mode (inlined bodies).
+__device__ __forceinline__ bool point_x_direct(const XDirect& w, const FreqDF& q, f2 x, f2 s2, f2 c2, f2 tob,
+                                               const SinTab& tab, c2f H[3])
+{
+    return x_direct_term<true, false>(w, nullptr, 0u, q, 1.0f, {1.0f, 0.0f}, x, s2, c2, tob, tab, H);
+}
+
+// The same summed over the modes of `modes` (Eq. 9): one chain and one transfer per distinct m
+// (modes sharing m share f2, t(f2) and the orbit), the sine/cosine and arm bodies called out of
+// line (the group loop's body would not fit the instruction cache inlined).  False when no
+// mode is in its support.
+__device__ __forceinline__ bool point_x_direct_hm(const XDirect& w, const XWalkerHM& wh, uint32_t modes,
+                                                  const FreqDF& q, f2 x, f2 s2, f2 c2, f2 tob, const SinTab& tab,
+                                                  c2f H[3])
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) H[c] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
+    bool any = false;
+#pragma unroll 1
+    for (int g = 0; g < 4; ++g) {
+        const uint32_t gmask = modes & hm_group_mask(g);
+        if (!gmask) continue;
+        FreqDF q2 = q;
+        if (g != 0)
+            q2 = {dd_norm(dd_mul_lazy(q.f, kGrpR[g])), dd_norm(dd_mul_lazy(q.f3, kGrpR3[g])),
+                  dd_norm(dd_mul_lazy(q.fm3, kGrpRm3[g])), dd_norm(dd_add_lazy(q.lnf3, kGrpLn3[g]))};
+        c2f Hg[3];
+        if (!x_direct_term<false, true>(w, &wh, gmask, q2, kGrpHalfM[g], kGrpAmp[g], x, s2, c2, tob, tab, Hg))
+            continue;
+        any = true;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) H[c] = cd_add(H[c], Hg[c]);
+    }
+    return any;
 }
 
 // block (template tile of T, frequency chunk): the point's tables and folded data are loaded
 // once and reused by the T templates; each thread keeps per-template double-float sums in
-// shared memory, reduced per template at the end (float64) into part[template][chunk].
-template <int T>
+// shared memory, reduced per template at the end (float64) into part[template][chunk].  kHM:
+// the templates of the modes of `modes` (point_x_direct_hm), else the (2,2) mode.
+template <int T, bool kHM>
 __global__ void __launch_bounds__(kDirXThreads)
     direct_fused_x_kernel(const double* __restrict__ theta, int64_t W, const float4* __restrict__ ft1,
                           const float4* __restrict__ ft2, const float4* __restrict__ ftx,
                           const float2* __restrict__ ftx2, double t_obs, const float4* __restrict__ wdx,
                           const float2* __restrict__ wvx, int64_t n, int64_t chunk, int nchunks, double inv_sigma,
-                          double2* __restrict__ part)
+                          uint32_t modes, double2* __restrict__ part)
 {
     __shared__ XDirect ws[T];
+    __shared__ XWalkerHM wsh[kHM ? T : 1];
     __shared__ SinTab tab;
     __shared__ float4 acc[T][kDirXThreads];   // per template: <d|h> hi, lo, <h|h> hi, lo
     __shared__ double sm[32 * 2];
@@ -950,6 +1016,8 @@ __global__ void __launch_bounds__(kDirXThreads)
     const int nt = (int)std::min<int64_t>(T, W - w0);
     load_sintab(tab);
     if (threadIdx.x < nt) xdirect_setup(theta, W, w0 + threadIdx.x, inv_sigma, ws[threadIdx.x]);
+    if (kHM && threadIdx.x >= 32 && threadIdx.x < 32 + nt)   // on another warp
+        xwalker_setup_hm(theta, W, w0 + threadIdx.x - 32, wsh[threadIdx.x - 32]);
     if (threadIdx.x == 0) s_tob = split_rn(t_obs);
 #pragma unroll
     for (int t = 0; t < T; ++t) acc[t][threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -972,7 +1040,9 @@ __global__ void __launch_bounds__(kDirXThreads)
         }
         for (int t = 0; t < nt; ++t) {
             c2f H[3];
-            if (!point_x_direct(ws[t], q, x, s2, c2, tob, tab, H)) continue;
+            if (kHM ? !point_x_direct_hm(ws[t], wsh[t], modes, q, x, s2, c2, tob, tab, H)
+                    : !point_x_direct(ws[t], q, x, s2, c2, tob, tab, H))
+                continue;
             f2 sd = {0.0f, 0.0f}, sh = {0.0f, 0.0f};
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -1380,7 +1450,7 @@ mbh_status make_x_direct_tables(mbh_data* D, cudaStream_t st)
 }
 
 mbh_status launch_direct_fused_x(const mbh_data* data, const double* theta, int64_t W, double* out,
-                                 cudaStream_t st)
+                                 cudaStream_t st, uint32_t modes)
 {
     constexpr int T = 4;
     const int64_t tiles = (W + T - 1) / T;
@@ -1392,9 +1462,14 @@ mbh_status launch_direct_fused_x(const mbh_data* data, const double* theta, int6
     cudaError_t e = cudaMallocAsync(&part, sizeof(double2) * W * nchunks, st);
     if (e != cudaSuccess) return cuda_fail(e, "direct_loglike_batch alloc");
     dim3 grid((unsigned)tiles, (unsigned)nchunks);
-    direct_fused_x_kernel<T><<<grid, kDirXThreads, 0, st>>>(theta, W, data->ftab, data->ftab2, data->ftx, data->ftx2,
-                                                            data->grid.t_obs, data->wdx, data->wvx, data->grid.n,
-                                                            chunk, nchunks, 1.0 / data->sigma, part);
+    if (modes == 1u)
+        direct_fused_x_kernel<T, false><<<grid, kDirXThreads, 0, st>>>(
+            theta, W, data->ftab, data->ftab2, data->ftx, data->ftx2, data->grid.t_obs, data->wdx, data->wvx,
+            data->grid.n, chunk, nchunks, 1.0 / data->sigma, modes, part);
+    else
+        direct_fused_x_kernel<T, true><<<grid, kDirXThreads, 0, st>>>(
+            theta, W, data->ftab, data->ftab2, data->ftx, data->ftx2, data->grid.t_obs, data->wdx, data->wvx,
+            data->grid.n, chunk, nchunks, 1.0 / data->sigma, modes, part);
     e = cudaGetLastError();
     if (e != cudaSuccess) {
         cudaFreeAsync(part, st);

@@ -178,7 +178,7 @@ cudaError_t alloc_ref_tables(mbh_ref* R);
 mbh_status make_freq_tables(mbh_data* D, cudaStream_t st);
 mbh_status make_x_direct_tables(mbh_data* D, cudaStream_t st);
 mbh_status launch_direct_fused_x(const mbh_data* data, const double* theta, int64_t W, double* out,
-                                 cudaStream_t st);
+                                 cudaStream_t st, uint32_t modes = 1u);
 void free_ref_tables(mbh_ref* R);
 cudaError_t prepare_mixed_tables(mbh_ref* R, cudaStream_t st);
 // heterodyne kernel instantiations: launcher and kernel address (for occupancy queries)

@@ -487,14 +487,15 @@ extern "C" mbh_status direct_loglike_batch_hm(const mbh_data* data, const double
                                               uint32_t modes, mbh_precision precision, double* out_dev,
                                               void* stream)
 {
-    // higher modes: MBH_MIXED and MBH_MIXED_F32 both take the float32-response pass
+    // higher modes: MBH_MIXED the double-float pass, MBH_MIXED_F32 the float32-response pass
     if (mbh_status s = check_modes(modes, precision == MBH_MIXED_F32 ? MBH_MIXED : precision)) return s;
     if (modes == 1u) return direct_loglike_batch(data, theta_dev, W, precision, out_dev, stream);
     if (!data) return fail(MBH_EINVAL, "data is NULL");
     if (W < 0) return fail(MBH_EINVAL, "W < 0");
     if (W == 0) return MBH_OK;
     if (!theta_dev || !out_dev) return fail(MBH_EINVAL, "NULL buffer");
-    if (precision == MBH_MIXED || precision == MBH_MIXED_F32)
+    if (precision == MBH_MIXED) return launch_direct_fused_x(data, theta_dev, W, out_dev, (cudaStream_t)stream, modes);
+    if (precision == MBH_MIXED_F32)
         return launch_direct_fused_mixed(data, theta_dev, W, out_dev, (cudaStream_t)stream, modes);
     return direct_f64(data, theta_dev, W, modes, out_dev, (cudaStream_t)stream);
 }

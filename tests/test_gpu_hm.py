@@ -227,9 +227,9 @@ def test_mixed_batch_of_both_kinds(M, WL, case):
 
 
 def test_mixed_templates_and_direct(M, WL, oracle, case):
-    """Mixed-precision higher-mode templates (complex64) and fused direct likelihood, with the
-    (2,2) mixed path's tolerances: templates within 2e-5 of max|h| per channel, lnL within
-    1e-5 of the terms; supports bit-exact."""
+    """Mixed-precision higher-mode templates (complex64) and the float32-response fused direct
+    likelihood (MBH_MIXED_F32), with the (2,2) float32-response tolerances: templates within
+    2e-5 of max|h| per channel, lnL within 1e-5 of the terms; supports bit-exact."""
     g, th = case["g"], case["walk"][:, :4]
     h_g = M.template_batch(g, WL.to_dev(th), "mixed", modes=ALL).cpu().numpy()
     h_o = oracle.template_batch(th, g, ALL)
@@ -238,9 +238,29 @@ def test_mixed_templates_and_direct(M, WL, oracle, case):
             ref = np.abs(h_o[w, c]).max()
             assert np.abs(h_g[w, c] - h_o[w, c]).max() <= 2e-5 * ref
     np.testing.assert_array_equal(h_g[:, 0] == 0, h_o[:, 0] == 0)
-    out_g = M.direct_loglike_batch_hm(case["data"], WL.to_dev(case["walk"]), ALL, "mixed").cpu().numpy()
+    out_g = M.direct_loglike_batch_hm(case["data"], WL.to_dev(case["walk"]), ALL, "mixed_f32").cpu().numpy()
     out_o = oracle.direct(case["walk"], g, case["d_o"], case["S"], ALL)
     _close(out_g, out_o, case["dd_o"], rel=1e-5)
+
+
+@pytest.mark.parametrize("loud", [False, True])
+def test_direct_mixed_higher_modes(M, WL, oracle, case, loud_case, loud):
+    """The double-float direct likelihood (MBH_MIXED) with the six modes on the 30-day source at
+    SNR 392 and 1000: |dlnL| <= 1e-3 absolute against the oracle (24 walkers 1e-5..1e-3), and
+    within 1e-6 of the terms of the float64 kernel; mode masks of one and of several groups."""
+    c = loud_case if loud else case
+    g, th = c["g"], WL.to_dev(c["walk"])
+    out_o = oracle.direct(c["walk"], g, c["d_o"], c["S"], ALL)
+    out_g = M.direct_loglike_batch_hm(c["data"], th, ALL, "mixed").cpu().numpy()
+    err = np.abs(out_g[0] - out_o[0])
+    print(f"six-mode direct MBH_MIXED, SNR {c['snr']:.0f}: abs p50/max", np.median(err), err.max())
+    assert err.max() <= 1e-3
+    for modes in (0x2, 0x9, ALL):
+        a = M.direct_loglike_batch_hm(c["data"], th, modes, "mixed").cpu().numpy()
+        b = M.direct_loglike_batch_hm(c["data"], th, modes, "fp64").cpu().numpy()
+        scale = 0.5 * (c["data"].dd + np.abs(b[2]) + 2 * np.abs(b[1]))
+        print(f"  modes 0x{modes:x}: vs float64 abs max", np.abs(a[0] - b[0]).max())
+        assert np.all(np.abs(a[0] - b[0]) <= 1e-6 * scale) and np.abs(a[0] - b[0]).max() <= 1e-3
 
 
 def test_invalid_mode_masks(M, WL, case):
