@@ -835,8 +835,8 @@ def run_sampler(M, WL, g, src, ref, stream, het_rates: dict | None, iters: int =
     res["four_ensembles_mixed_f32_fused"] = {"ensembles": n_ens, "walkers": n_ens * T * W, "ms_per_iteration": ms,
                              "iterations_per_s": 1e3 / ms, "lnL_evals_per_s": n_ens * T * W / (ms * 1e-3)}
     return {"temperatures": T, "walkers_per_temperature": W, "bins": ref.bins, "graph": True,
-            "note": "mixed: proposal, likelihood (MBH_MIXED kernel) and acceptance as separate launches; "
-                    "mixed_f32: each half step one fused float32-ratio heterodyne launch", **res}
+            "note": "each half step one fused launch (proposal, likelihood, acceptance): mixed the "
+                    "extended-precision MBH_MIXED kernel, mixed_f32 the float32-ratio kernel", **res}
 
 
 def run_uneven(M, WL, stream, reps: int = 20) -> dict:

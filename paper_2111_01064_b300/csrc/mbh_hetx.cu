@@ -36,6 +36,7 @@
 #include "mbh_internal.cuh"
 #include "mbh_mixed.cuh"
 #include "mbh_model.cuh"
+#include "mbh_pt.cuh"
 
 using namespace mbh;
 
@@ -643,18 +644,27 @@ __device__ __forceinline__ void f32_edge_df(const cf d[3], float eta, c2f dl[3])
 // ------------------------------------------------------------------------------------------
 // the kernel: layout and reductions as the float32 path's het_mixed_kernel (tiles of BLOCK/G
 // walkers of one source, G threads per walker dealing the edges round-robin, the previous
-// edge's delta from the neighbouring lane, lane sums reduced in a fixed order)
+// edge's delta from the neighbouring lane, lane sums reduced in a fixed order).  kPt: one
+// sampler half step (Sec. III) in the same launch, as the float32-ratio het_mixed_pt_kernel:
+// the walkers are the moving walkers' proposals (pt::propose_item in the set-up, kept in shared
+// memory) and the epilogue applies the tempered acceptance test (pt::accept_test) instead of
+// writing lnL.
 // ------------------------------------------------------------------------------------------
-template <int G, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) het_x_kernel(const __grid_constant__ HetLaunch L)
+template <int G, int BLOCK, bool kPt>
+__device__ __forceinline__ void het_x_body(const HetLaunch& L)
 {
     constexpr int WPB = BLOCK / G;
     constexpr int kSlot = (WPB + 31) / 32 * 32;
+    constexpr int PW = kPt ? WPB : 1;
     __shared__ XWalker xw[WPB];
     __shared__ WalkerDF wsd[WPB];   // float32-ratio edges: the float32 path's walker constants
     __shared__ WalkerF wsf[WPB];
     __shared__ float eta32[WPB];    // and its amplitude rounding (f32_edge_df)
     __shared__ SinTab tab;
+    __shared__ double ths[PW][pt::kPar];   // kPt: the proposals' theta (set-ups) and x (accepted)
+    __shared__ double ys[PW][pt::kPar];
+    __shared__ double facs[PW];
+    __shared__ int32_t flags[PW];
     const int lw = threadIdx.x / G, lane = threadIdx.x % G;
     load_sintab(tab);
     for (int tile = blockIdx.x; tile < L.n_tiles; tile += gridDim.x) {
@@ -664,6 +674,16 @@ __global__ void __launch_bounds__(BLOCK) het_x_kernel(const __grid_constant__ He
         const int64_t w0 = S.w_begin + (int64_t)(tile - S.tile_begin) * WPB;
         const bool active = w0 + lw < S.w_end;
         __syncthreads();
+        if constexpr (kPt) {
+            const pt::PtArgs& A = *static_cast<const pt::PtArgs*>(L.pt);
+            for (int j = threadIdx.x; j < WPB; j += BLOCK)
+                if (w0 + j < S.w_end) {
+                    int32_t flag;
+                    pt::propose_item(A, L.pt_half, (int32_t)(w0 + j), *A.step, ys[j], ths[j], facs[j], flag);
+                    flags[j] = flag;
+                }
+            __syncthreads();
+        }
         // the walkers' two set-ups (float64 chains bound by latency, not by the float64 pipe's
         // rate) on different warps where the block has them: slot t < WPB sets up walker t's
         // double-float constants, slot kSlot + t its float32-path constants (kSlot: WPB rounded
@@ -671,10 +691,12 @@ __global__ void __launch_bounds__(BLOCK) het_x_kernel(const __grid_constant__ He
         for (int t = threadIdx.x; t < 2 * kSlot; t += BLOCK) {
             const int j = t < kSlot ? t : t - kSlot;
             if (j >= WPB || w0 + j >= S.w_end) continue;
+            const double* th = kPt ? &ths[kPt ? j : 0][0] : L.theta;
+            const int64_t tw = kPt ? 1 : L.W, ti = kPt ? 0 : w0 + j;
             if (t < kSlot) {
-                xwalker_setup(L.theta, L.W, w0 + j, *S.mix.xder, xw[j]);
+                xwalker_setup(th, tw, ti, *S.mix.xder, xw[j]);
             } else if (S.mix.xn32 > 0) {
-                walker_setup_mixed(L.theta, L.W, w0 + j, wsd[j], wsf[j]);
+                walker_setup_mixed(th, tw, ti, wsd[j], wsf[j]);
                 eta32[j] = (float)(amp_fix(wsf[j].eps_amp76, S.mix.amp_eps0) - 1.0);
             }
         }
@@ -732,11 +754,44 @@ __global__ void __launch_bounds__(BLOCK) het_x_kernel(const __grid_constant__ He
             const int64_t wi = w0 + lw;
             const double dh = S.mix.xsumA + df_to_double(adh);
             const double hh = S.mix.xsumB + df_to_double(ahh);
-            L.out[wi] = -0.5 * (S.dd + hh - 2.0 * dh);
-            L.out[L.W + wi] = dh;
-            L.out[2 * L.W + wi] = hh;
+            const double lnl = -0.5 * (S.dd + hh - 2.0 * dh);
+            if constexpr (kPt) {
+                const pt::PtArgs& A = *static_cast<const pt::PtArgs*>(L.pt);
+                int32_t col;
+                int t, cb;
+                const int32_t flag = flags[lw];
+                const int kind = flag >> 1;
+                const bool acc = pt::accept_test(A, L.pt_half, (int32_t)wi, lnl, facs[lw], flag, col, t, cb);
+                atomicAdd(&A.counters[cb + t * 4 + kind], 1ull);
+                if (acc) {
+                    atomicAdd(&A.counters[cb + 4 * A.T + t * 4 + kind], 1ull);
+                    const int64_t N = (int64_t)A.n_ens * A.T * A.W;
+#pragma unroll
+                    for (int p = 0; p < pt::kPar; ++p) A.x[p * N + col] = ys[lw][p];
+                    A.out[col] = lnl;
+                    A.out[N + col] = dh;
+                    A.out[2 * N + col] = hh;
+                }
+            } else {
+                L.out[wi] = lnl;
+                L.out[L.W + wi] = dh;
+                L.out[2 * L.W + wi] = hh;
+            }
         }
     }
+}
+
+template <int G, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) het_x_kernel(const __grid_constant__ HetLaunch L)
+{
+    het_x_body<G, BLOCK, false>(L);
+}
+
+// one fused sampler half step (blocks of at most 32 walkers: the proposals' shared arrays)
+template <int G, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) het_x_pt_kernel(const __grid_constant__ HetLaunch L)
+{
+    het_x_body<G, BLOCK, true>(L);
 }
 
 // Higher-mode references (Sec. II B with the template of Eq. 9): the layout of het_x_kernel, the
@@ -1499,6 +1554,13 @@ cudaError_t launch_het_x(const HetLaunch& L, int grid, cudaStream_t st)
 }
 
 template <int G, int BLOCK>
+cudaError_t launch_het_x_pt(const HetLaunch& L, int grid, cudaStream_t st)
+{
+    het_x_pt_kernel<G, BLOCK><<<grid, BLOCK, 0, st>>>(L);
+    return cudaGetLastError();
+}
+
+template <int G, int BLOCK>
 cudaError_t launch_het_xhm(const HetLaunch& L, int grid, cudaStream_t st)
 {
     het_xhm_kernel<G, BLOCK><<<grid, BLOCK, 0, st>>>(L);
@@ -1523,6 +1585,17 @@ HetKernel het_kernel_x(int G, int block)
 }  // namespace mbh
 
 namespace mbh {
+// fused sampler half steps of the extended kernel: blocks of at most 32 walkers
+HetKernel het_kernel_x_pt(int G, int block)
+{
+#define MBH_CASE(g, b) \
+    if (G == g && block == b) return {&launch_het_x_pt<g, b>, (const void*)&het_x_pt_kernel<g, b>};
+    MBH_CASE(2, 64) MBH_CASE(4, 64) MBH_CASE(4, 128) MBH_CASE(8, 128) MBH_CASE(8, 256)
+    MBH_CASE(16, 256) MBH_CASE(32, 256)
+#undef MBH_CASE
+    return {nullptr, nullptr};
+}
+
 HetKernel het_kernel_xhm(int G, int block)
 {
 #define MBH_CASE(g, b) \

@@ -192,12 +192,14 @@ HetKernel het_kernel_mixed(int G, int block);
 HetKernel het_kernel_mixed_hm(int G, int block);
 HetKernel het_kernel_mixed_pt(int G, int block);
 HetKernel het_kernel_x(int G, int block);
+HetKernel het_kernel_x_pt(int G, int block);
 HetKernel het_kernel_xhm(int G, int block);
 cudaError_t prepare_x_tables(mbh_ref* R, cudaStream_t st);
 cudaError_t prepare_x_tables_hm(mbh_ref* R, cudaStream_t st);
 void free_x_tables(mbh_ref* R);
 mbh_status het_launch_fused_pt(const mbh_ref* const* refs, int n_ens, int64_t M, const mbh_het_config& cfg,
-                               const void* pt_dev, int half, cudaStream_t st);
+                               mbh_precision prec, const void* pt_dev, int half, cudaStream_t st);
+int fused_pt_block(mbh_precision prec, int G, int64_t M);   // 0: no fused kernel for this shape
 
 // ------------------------------------------------------------------------------------------
 // reductions

@@ -561,7 +561,7 @@ mbh_status queue_iteration(mbh_pt* P, cudaStream_t st)
         if (P->fused) {   // proposal, likelihood and acceptance in one launch
             if (half == 0 && (e = cudaStreamWaitEvent(st, P->join_draws, 0)) != cudaSuccess)
                 return cuda_fail(e, "join");
-            if (mbh_status s = het_launch_fused_pt(P->refs.data(), (int)P->refs.size(), M / A.n_ens, P->cfg,
+            if (mbh_status s = het_launch_fused_pt(P->refs.data(), (int)P->refs.size(), M / A.n_ens, P->cfg, P->precision,
                                                    P->A_dev, half, st))
                 return s;
             continue;
@@ -756,7 +756,15 @@ extern "C" mbh_status mbh_pt_create_multi(const mbh_pt_opts* o, const mbh_ref* c
     if (e == cudaSuccess) e = cudaMemsetAsync(A.done, 0, sizeof(unsigned int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(A.perm, 0, sizeof(int32_t) * N, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(P->A_dev, &A, sizeof(PtArgs), cudaMemcpyHostToDevice, st);
-    P->fuse_ok = o->precision == MBH_MIXED_F32 && !o->no_fuse;   // the fused half step is the float32-ratio kernel
+    // fused half steps: the float32-ratio kernel (MBH_MIXED_F32) or the extended kernel
+    // (MBH_MIXED), where a kernel exists for the launch shape
+    {
+        const int G = P->cfg.threads_per_walker;
+        const int blk = P->cfg.block ? P->cfg.block : fused_pt_block(o->precision, G, M);
+        const bool shape = o->precision == MBH_MIXED ? het_kernel_x_pt(G, blk).launch != nullptr
+                                                     : het_kernel_mixed_pt(G, blk).launch != nullptr;
+        P->fuse_ok = (o->precision == MBH_MIXED_F32 || o->precision == MBH_MIXED) && !o->no_fuse && shape;
+    }
     P->fused = P->fuse_ok && refs != nullptr && all22;
     if (e != cudaSuccess) {
         free_pt(P);

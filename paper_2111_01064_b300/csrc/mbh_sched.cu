@@ -368,15 +368,25 @@ extern "C" void mbh_het_graph_free(mbh_het_graph* g)
 }
 
 namespace mbh {
-// One fused sampler half step (het_mixed_pt_kernel) over the moving walkers of n_ens ensembles,
-// M of each, ensemble e against refs[e] ((2,2) references): multi-source launches (up to
-// kMaxSrc ensembles each) whose walker constants come from the sampler's proposals.
+// Block of a fused half step: the float32-ratio kernel's default, or for the extended kernel
+// (whose proposals take shared memory per walker) 32 walkers per block, at most 256 threads.
+int fused_pt_block(mbh_precision prec, int G, int64_t M)
+{
+    if (prec == MBH_MIXED) return std::min(256, 32 * G);
+    return default_block_mixed(G, M);
+}
+
+// One fused sampler half step (het_mixed_pt_kernel for MBH_MIXED_F32, het_x_pt_kernel for
+// MBH_MIXED) over the moving walkers of n_ens ensembles, M of each, ensemble e against refs[e]
+// ((2,2) references): multi-source launches (up to kMaxSrc ensembles each) whose walker
+// constants come from the sampler's proposals.
 mbh_status het_launch_fused_pt(const mbh_ref* const* refs, int n_ens, int64_t M, const mbh_het_config& cfg,
-                               const void* pt_dev, int half, cudaStream_t st)
+                               mbh_precision prec, const void* pt_dev, int half, cudaStream_t st)
 {
     if (mbh_status s = check_cfg(cfg)) return s;
-    const int block = cfg.block ? cfg.block : default_block_mixed(cfg.threads_per_walker, M * n_ens);
-    const HetKernel k = het_kernel_mixed_pt(cfg.threads_per_walker, block);
+    const int block = cfg.block ? cfg.block : fused_pt_block(prec, cfg.threads_per_walker, M * n_ens);
+    const HetKernel k = prec == MBH_MIXED ? het_kernel_x_pt(cfg.threads_per_walker, block)
+                                          : het_kernel_mixed_pt(cfg.threads_per_walker, block);
     if (!k.launch) return fail(MBH_EINVAL, "no kernel for this configuration");
     const int wpb = block / cfg.threads_per_walker;
     std::unique_ptr<HetLaunch> L(new (std::nothrow) HetLaunch);

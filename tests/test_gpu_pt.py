@@ -96,8 +96,8 @@ def test_pt_fp64_matches_oracle(M, WL, oracle, case, n_iter):
 @pytest.mark.parametrize("precision", ["mixed", "mixed_f32"])
 def test_pt_mixed_matches_oracle(M, WL, oracle, case, precision):
     """Mixed precisions against the oracle's float64 sampler: positions identical but where an
-    acceptance test sits within the likelihood's error of its threshold.  "mixed" (separate
-    launches, the extended-precision heterodyne): |dlnL| <= 1e-3 for every walker; "mixed_f32"
+    acceptance test sits within the likelihood's error of its threshold.  "mixed" (fused half
+    steps, the extended-precision heterodyne): |dlnL| <= 1e-3 for every walker; "mixed_f32"
     (fused half steps, float32 ratios): hot chains wander far from the reference, where that
     path is held to 1e-6 of the terms, the cold chain stays near it."""
     _, xg, og, cg, _ = _gpu_run(M, WL, case, 3, precision=precision)
@@ -238,16 +238,18 @@ def test_pt_ladder_adaptation_matches_oracle(M, WL, oracle, case):
     assert not np.allclose(bo, b0) and bo[0] == 1.0 and bo[-1] == 0.0
 
 
-def test_pt_fused_half_steps_equal_separate_launches(M, WL, case):
-    """Float32-ratio precision: a half step as one fused heterodyne launch (proposal in the walker
-    setup, acceptance in the epilogue) against proposal, likelihood and acceptance as separate
-    launches.  The likelihood arithmetic is the same; the walker constants are compiled into two
-    kernels, so a last-bit difference may flip a decision sitting on its threshold."""
+@pytest.mark.parametrize("precision", ["mixed_f32", "mixed"])
+def test_pt_fused_half_steps_equal_separate_launches(M, WL, case, precision):
+    """A half step as one fused heterodyne launch (proposal in the walker setup, acceptance in
+    the epilogue; the float32-ratio kernel, or the extended kernel for "mixed") against
+    proposal, likelihood and acceptance as separate launches.  The likelihood arithmetic is the
+    same; the walker constants are compiled into two kernels, so a last-bit difference may flip
+    a decision sitting on its threshold."""
     c = case
     runs = []
     for fuse in (True, False):
         pt = M.PTSampler(WL.to_dev(c["x"]), c["betas"], c["lo"], c["hi"], ref=c["ref_g"], walkers=c["W"],
-                         probs=PROBS, seed=21, precision="mixed_f32", fuse=fuse)
+                         probs=PROBS, seed=21, precision=precision, fuse=fuse)
         pt.run(4)
         x, out = (t.cpu().numpy() for t in pt.state())
         cnt, step = pt.counters()
