@@ -106,6 +106,8 @@ HET_X_FMA_INST_PER_EDGE = 1497.1
 HET_X_DRAM_BYTES = 1.693e6                 # read + write per 16384-walker launch (ncu)
 HET_XHM_FMA_INST_PER_EDGE = 5111.4
 FUSED_X_FMA_INST_PER_POINT = 1851.6
+HET_F32_KERNEL = "het_mixed_kernel_capped<8,224>"
+HET_F32_FMA_INST_PER_EDGE = 639.0          # MBH_MIXED_F32 heterodyne (ncu, workload 2)
 FUSED_MIXED_FMA_INST_PER_POINT = 480.3
 FUSED_F64_DFMA_INST_PER_POINT = 590.5
 STORED_DATA_BYTES = 75.74e6                # data pairs, read once per launch (ncu: 883.66 MB
@@ -500,6 +502,12 @@ def run_ours(args) -> dict | None:
                                   "sampled during the run)",
                      "inst_per_edge": HET_X_FMA_INST_PER_EDGE,
                      "ps_per_edge_evaluation": ms_per_step * 1e9 / (nw * (E + 1))},
+        "roofline_mixed_f32": {"bound": "alu", "pipe": "fp32 (FMA pipe)", "peak": fma_peak,
+                               "unit": "T fp32-pipe inst/s",
+                               "achieved": HET_F32_FMA_INST_PER_EDGE * nw * (E + 1) / (f32_ms * 1e-3) / 1e12,
+                               "frac": HET_F32_FMA_INST_PER_EDGE * nw * (E + 1) / (f32_ms * 1e-3) / 1e12 / fma_peak,
+                               "traffic": None, "kernel": HET_F32_KERNEL,
+                               "inst_per_edge": HET_F32_FMA_INST_PER_EDGE},
         "roofline_higher_modes": None if not higher_modes else {
             "bound": "alu", "pipe": "fp32 (FMA pipe)", "peak": fma_peak, "unit": "T fp32-pipe inst/s",
             "achieved": HET_XHM_FMA_INST_PER_EDGE * higher_modes["walkers"] * (higher_modes["bins"] + 1)
