@@ -105,7 +105,7 @@ HET_KERNEL = "het_x_kernel<4,256>"
 HET_X_FMA_INST_PER_EDGE = 1497.1
 HET_X_DRAM_BYTES = 1.693e6                 # read + write per 16384-walker launch (ncu)
 HET_XHM_FMA_INST_PER_EDGE = 5111.4
-FUSED_X_FMA_INST_PER_POINT = 1851.6
+FUSED_X_FMA_INST_PER_POINT = 1893.2
 HET_F32_KERNEL = "het_mixed_kernel_capped<8,224>"
 HET_F32_FMA_INST_PER_EDGE = 639.0          # MBH_MIXED_F32 heterodyne (ncu, workload 2)
 FUSED_MIXED_FMA_INST_PER_POINT = 480.3

@@ -37,6 +37,29 @@ __device__ __forceinline__ f2 dd_sqr_lazy(f2 a)
     return {p, __fmaf_rn(2.0f * a.hi, a.lo, __fmaf_rn(a.hi, a.hi, -p))};
 }
 __device__ __forceinline__ f2 dd_norm(f2 a) { return fast_two_sum(a.hi, a.lo); }
+// a b + c and a b keeping the a.lo b.lo term: along a chain of products of correlated
+// operands (a Horner evaluation of c_0 v^-5) the dropped terms share a sign and add up to a
+// bias of ~(lo/hi)^2 per step, ~1e-9 rad at |Psi| ~ 1e6
+__device__ __forceinline__ f2 dd_fma_full(f2 a, f2 b, f2 c)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.lo, b.lo, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e)));
+    const f2 s = two_sum(p, c.hi);
+    return {s.hi, __fadd_rn(s.lo, __fadd_rn(e, c.lo))};
+}
+__device__ __forceinline__ f2 dd_mul_full(f2 a, f2 b)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    return {p, __fmaf_rn(a.lo, b.lo, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, __fmaf_rn(a.hi, b.hi, -p))))};
+}
+
+// a^2 with the lo^2 term (for operands that may be unnormalised)
+__device__ __forceinline__ f2 dd_sqr_full(f2 a)
+{
+    const float p = __fmul_rn(a.hi, a.hi);
+    return {p, __fmaf_rn(a.lo, a.lo, __fmaf_rn(2.0f * a.hi, a.lo, __fmaf_rn(a.hi, a.hi, -p)))};
+}
 __device__ __forceinline__ f2 dd_from(float a) { return {a, 0.0f}; }
 
 __device__ __forceinline__ c2f cd_add(c2f a, c2f b) { return {dd_add_lazy(a.re, b.re), dd_add_lazy(a.im, b.im)}; }
@@ -82,6 +105,36 @@ __device__ __forceinline__ f2 dd_reduce_2pi_step(f2 x)
 }
 
 __device__ __forceinline__ f2 dd_reduce_2pi(f2 x) { return dd_reduce_2pi_step(dd_reduce_2pi_step(x)); }
+
+// a b - n 2 pi for a double-float a and a triple-float b = b.hi + b.lo + bx, |a b| < 2^22 pi
+// (n = round(a.hi b.hi / 2 pi); the result lies within ~pi + 1.5 of zero, as a normalised
+// double-float good to ~1e-14).  At |a b| ~ 1e6-1e7 the low word of a plain double-float
+// product resolves ~|a b| 2^-48 ~ 1e-8: the product's small terms (a.lo b.lo, a.hi bx, the
+// residuals of the partial products) fall below it and round away, alike at every a for a
+// constant b.  Here the leading product is taken exactly, reduced first (exactly, as in
+// dd_reduce_2pi_step), and the O(1) partial products and the small terms are added after.
+__device__ __forceinline__ f2 dd_mul_mod2pi(f2 a, f2 b, float bx)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    const float e = __fmaf_rn(a.hi, b.hi, -p);           // p + e = a.hi b.hi
+    const float n = rintf(p * (float)(1.0 / kTwoPiD));
+    const float r = __fmaf_rn(-n, kP2a, p);              // exact
+    const float q = __fmul_rn(n, kP2b);
+    const float qe = __fmaf_rn(n, kP2b, -q);             // q + qe = n P2b
+    const float t1 = __fmul_rn(a.hi, b.lo);
+    const float t1e = __fmaf_rn(a.hi, b.lo, -t1);        // t1 + t1e = a.hi b.lo
+    const float t2 = __fmul_rn(a.lo, b.hi);
+    const float t2e = __fmaf_rn(a.lo, b.hi, -t2);        // t2 + t2e = a.lo b.hi
+    const f2 s0 = two_sum(r, -q);
+    const f2 s1 = two_sum(s0.hi, e);
+    const f2 s2 = two_sum(s1.hi, t1);
+    const f2 s3 = two_sum(s2.hi, t2);
+    // the words below: the two-sums' residuals (each below ulp(~pi)/2) and the small terms
+    float lo = __fadd_rn(__fadd_rn(s0.lo, s1.lo), __fadd_rn(s2.lo, s3.lo));
+    float sm = __fmaf_rn(a.lo, b.lo, __fmaf_rn(a.hi, bx, __fadd_rn(t1e, t2e)));
+    sm = __fsub_rn(sm, __fmaf_rn(n, kP2c, qe));
+    return two_sum(s3.hi, __fadd_rn(lo, sm));
+}
 
 // sin a and cos a - 1 for |a| <= ~0.2 (a double-float): sin a = a + a^3 (-1/6 + a^2/120 -
 // a^4/5040 + a^6/362880) with the a^3 term in float32 (its rounding <= 6e-8 |a|^3/6 < 1e-10),
@@ -129,8 +182,12 @@ __device__ __forceinline__ void dd_sincos(f2 r, const SinTab& tab, f2& s, f2& cm
 }
 
 // sin x and cos x - 1 of any double-float |x| < 2^22 pi (reduction by 2 pi, then dd_sincos).
+// x is renormalised first: arguments from lazy arithmetic after a cancellation (an orbit angle
+// (t - t_ref) 2 pi/yr with t ~ t_ref ~ 3e7 s) can carry a low word of many ulps of the high
+// word, which the small-angle series would miss in its cubic term (~a^2/2 lo, 4e-9 at 0.2).
 __device__ __forceinline__ void dd_sincos_any(f2 x, const SinTab& tab, f2& s, f2& cm1)
 {
+    x = two_sum(x.hi, x.lo);
     if (fabsf(x.hi) <= 0.19f) {
         dd_sincos_small(x, s, cm1);
         return;

@@ -912,13 +912,21 @@ struct XDirect {
     WalkerDF d;
     XWalker r;
     f2 amp, ifc2;
+    float c1x;   // c1's third part: c1 ~ 2 pi t_ref reaches ~2e8, whose float pair is off by ~1e-6
+    float c0x;   // c_0's third part and the relative residual of (pi M)^{-1/3}'s float pair:
+    float icbr;  // Psi_PN ~ c_0 v^-5 reaches ~1e5 rad, where ~4e-15 of it is ~4e-10 rad
 };
 
 __device__ inline void xdirect_setup(const double* __restrict__ theta, int64_t W, int64_t i, double inv_sigma,
                                      XDirect& o)
 {
     WalkerF wf;   // the float32 constants of the float32 path's set-up are not used here
-    walker_setup_mixed(theta, W, i, o.d, wf);
+    WalkerDFFull full;
+    walker_setup_mixed(theta, W, i, o.d, wf, &full);
+    // beyond the float pairs (both differences exact)
+    o.c1x = (float)((full.c1 - (double)o.d.c1.hi) - (double)o.d.c1.lo);
+    o.c0x = (float)((full.c0 - (double)o.d.c[0].hi) - (double)o.d.c[0].lo);
+    o.icbr = (float)(((full.icb - (double)o.d.icbrt_piM.hi) - (double)o.d.icbrt_piM.lo) / full.icb);
     XDer x;
     xderive(theta, W, i, x);
 #pragma unroll
@@ -953,20 +961,23 @@ __constant__ f2 kGrpAmp[4] = {df_const(1.0), df_const(1.6048697909004944), df_co
 // at t(f2), Phi = (m/2) Phi_22(f2), the amplitude (pi M)^{-7/6} exp(-(f2/f_c)^2)/sigma times
 // ampr, and the raw transfer at the point's x of the mode factors times A e^{-i Phi}: the
 // walker's (2,2) factors, or with kHM the group's modes' factors weighted by v^{p_lm}.
-// q2: f2, f2^{1/3}, f2^{-1/3}, ln f2/3; x = pi f L/c with sin 2x, cos 2x (the grid's f).
+// q2: f2, f2^{1/3}, f2^{-1/3}, ln f2/3; fg the grid's f; x = pi f L/c with sin 2x, cos 2x.
+// Phi = f c1 + f dk + (m/2) Psi_PN(f2) ((m/2) f2 = f): lin = f c1 mod 2 pi (x_direct_lin),
+// the same for every mode.
 template <bool kInl, bool kHM>
 __device__ __forceinline__ bool x_direct_term(const XDirect& w, const XWalkerHM* wh, uint32_t gmask, const FreqDF& q2,
-                                              float half_m, f2 ampr, f2 x, f2 s2, f2 c2, f2 tob, const SinTab& tab,
-                                              c2f H[3])
+                                              f2 fg, f2 lin, float half_m, f2 ampr, f2 x, f2 s2, f2 c2, f2 tob,
+                                              const SinTab& tab, c2f H[3])
 {
     const WalkerDF& d = w.d;
     const f2 v = dd_mul_lazy(d.cbrt_piM, q2.f3);
     const f2 iv = dd_mul_lazy(d.icbrt_piM, q2.fm3);
     const f2 lnv = dd_add_lazy(d.ln_cbrt_piM, q2.lnf3);
-    // Psi_PN = sum_k c_k v^{k-5} + ln v (cl5 + cl6 v) (c_1 = 0; the pinning constant in c_5)
-    f2 N = dd_mul_lazy(d.c[0], iv);
+    // Psi_PN = sum_k c_k v^{k-5} + ln v (cl5 + cl6 v) (c_1 = 0; the pinning constant in c_5), the
+    // v^-k chain with its products' lo lo terms (dd_fma_full)
+    f2 N = dd_mul_full(d.c[0], iv);
 #pragma unroll
-    for (int k = 2; k <= 5; ++k) N = dd_fma_lazy(N, iv, d.c[k]);
+    for (int k = 2; k <= 5; ++k) N = dd_fma_full(N, iv, d.c[k]);
     const f2 Pp = dd_mul_lazy(dd_fma_lazy(d.c[7], v, d.c[6]), v);
     const f2 psi_pn = dd_add_lazy(dd_add_lazy(N, Pp), dd_mul_lazy(lnv, dd_fma_lazy(d.cl6, v, d.cl5)));
     // t(f2) = sum_k d_k v^{k-8} + dl6 v^{-2} ln v + t0 and the support test
@@ -976,6 +987,19 @@ __device__ __forceinline__ bool x_direct_term(const XDirect& w, const XWalkerHM*
     for (int k = 6; k >= 0; --k) Q = dd_fma_lazy(Q, v, d.d[k]);
     const f2 t = dd_add(dd_add_lazy(dd_mul_lazy(Q, iv8), dd_mul_lazy(dd_mul_lazy(lnv, d.dl6), iv2)), d.t0);
     if (!(dd_le(q2.f, d.fcut) && !dd_lt0(t) && dd_le(t, tob))) return false;
+    // the residuals of c_0 and of (pi M)^{-1/3} beyond their float pairs, to first order: c0x v^-5
+    // + icbr sum_k (5 - k) c_k v^{k-5}, k = 0..4 (float32; ~1e-8 rad at |Psi| ~ 1e6, the same
+    // at every point: added once the phase is reduced, where it is not rounded away)
+    float corr;
+    {
+        const float ivf = iv.hi;
+        float dn = 5.0f * d.c[0].hi * ivf;
+        dn = __fmaf_rn(dn, ivf, 3.0f * d.c[2].hi);
+        dn = __fmaf_rn(dn, ivf, 2.0f * d.c[3].hi);
+        dn = __fmaf_rn(dn, ivf, d.c[4].hi) * ivf;
+        const float iv2f = ivf * ivf;
+        corr = __fmaf_rn(w.c0x, iv2f * iv2f * ivf, w.icbr * dn);
+    }
     // orbit angle at t: alpha(t_ref) + 2 pi (t - t_ref)/yr
     const SinCos oa = sincos_df<kInl>(dd_mul_lazy(dd_sub_lazy(t, d.tref), kOrbRate), tab);
     const f2 ds = dd_add_lazy(dd_mul_lazy(d.sa_ref, oa.cm1), dd_mul_lazy(d.ca_ref, oa.s));   // sin a - sin a_ref
@@ -985,9 +1009,11 @@ __device__ __forceinline__ bool x_direct_term(const XDirect& w, const XWalkerHM*
     // psi'(f_max) and 2 pi AU/c k.c(t_ref); kx, ky carry 2 pi AU/c); a mode's phase is m/2 times
     // it (its Doppler term (m/2) f2 ... = f ...)
     const f2 dk = dd_add_lazy(dd_mul_lazy(d.kx, dc), dd_mul_lazy(d.ky, ds));
-    f2 phi = dd_norm(dd_add_lazy(dd_mul_lazy(q2.f, dd_add_lazy(d.c1, dk)), psi_pn));
-    if (kHM && half_m != 1.0f) phi = dd_norm(dd_mul_f_lazy(phi, half_m));
-    const SinCos ph = sincos_df<kInl>(phi, tab);
+    const f2 pp = kHM && half_m != 1.0f ? dd_mul_f_lazy(psi_pn, half_m) : psi_pn;
+    f2 phi = dd_add_lazy(dd_add_lazy(lin, dd_mul_lazy(fg, dk)), pp);
+    if (fabsf(phi.hi) > 3.14f) phi = dd_reduce_2pi(phi);
+    phi.lo = __fmaf_rn(kHM ? half_m : 1.0f, corr, phi.lo);
+    const SinCos ph = sincos_df<kInl>(dd_norm(phi), tab);
     // raw amplitude amp (pi M)^{-7/6} exp(-(f2/f_c)^2)/sigma, Z = A e^{-i Phi} into the mode factors
     const f2 u = dd_mul_lazy(dd_sqr_lazy(q2.f), w.ifc2);
     f2 A = dd_mul_lazy(w.amp, dd_exp({-u.hi, -u.lo}));
@@ -1012,11 +1038,15 @@ __device__ __forceinline__ bool x_direct_term(const XDirect& w, const XWalkerHM*
     return true;
 }
 
+// f c1 modulo 2 pi with c1 as a triple-float (c1 ~ 2 pi t_ref reaches ~2e8, and f c1 ~1e7 rad)
+__device__ __forceinline__ f2 x_direct_lin(const XDirect& w, f2 f) { return dd_mul_mod2pi(f, w.d.c1, w.c1x); }
+
 // The raw template H_c of one template at one grid point, (2,2) mode (inlined bodies).
 __device__ __forceinline__ bool point_x_direct(const XDirect& w, const FreqDF& q, f2 x, f2 s2, f2 c2, f2 tob,
                                                const SinTab& tab, c2f H[3])
 {
-    return x_direct_term<true, false>(w, nullptr, 0u, q, 1.0f, {1.0f, 0.0f}, x, s2, c2, tob, tab, H);
+    return x_direct_term<true, false>(w, nullptr, 0u, q, q.f, x_direct_lin(w, q.f), 1.0f, {1.0f, 0.0f}, x, s2, c2,
+                                      tob, tab, H);
 }
 
 // The same summed over the modes of `modes` (Eq. 9): one chain and one transfer per distinct m
@@ -1030,6 +1060,7 @@ __device__ __forceinline__ bool point_x_direct_hm(const XDirect& w, const XWalke
 #pragma unroll
     for (int c = 0; c < 3; ++c) H[c] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
     bool any = false;
+    const f2 lin = x_direct_lin(w, q.f);
 #pragma unroll 1
     for (int g = 0; g < 4; ++g) {
         const uint32_t gmask = modes & hm_group_mask(g);
@@ -1039,7 +1070,7 @@ __device__ __forceinline__ bool point_x_direct_hm(const XDirect& w, const XWalke
             q2 = {dd_norm(dd_mul_lazy(q.f, kGrpR[g])), dd_norm(dd_mul_lazy(q.f3, kGrpR3[g])),
                   dd_norm(dd_mul_lazy(q.fm3, kGrpRm3[g])), dd_norm(dd_add_lazy(q.lnf3, kGrpLn3[g]))};
         c2f Hg[3];
-        if (!x_direct_term<false, true>(w, &wh, gmask, q2, kGrpHalfM[g], kGrpAmp[g], x, s2, c2, tob, tab, Hg))
+        if (!x_direct_term<false, true>(w, &wh, gmask, q2, q.f, lin, kGrpHalfM[g], kGrpAmp[g], x, s2, c2, tob, tab, Hg))
             continue;
         any = true;
 #pragma unroll
@@ -1101,9 +1132,11 @@ __global__ void __launch_bounds__(kDirXThreads)
             f2 sd = {0.0f, 0.0f}, sh = {0.0f, 0.0f};
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                // Re conj(conj(K) D) H = Re conj(D) h; |H|^2 |K|^2 V = |h|^2 V
+                // Re conj(conj(K) D) H = Re conj(D) h; |H|^2 |K|^2 V = |h|^2 V.  The squares keep
+                // lo^2: after the transfer's cancellations H's parts can be unnormalised (|lo|
+                // well above ulp(hi)), and a dropped lo^2 (never negative) biases <h|h> low
                 sd = dd_add_lazy(sd, dd_add_lazy(dd_mul_lazy(D[c].re, H[c].re), dd_mul_lazy(D[c].im, H[c].im)));
-                sh = dd_add_lazy(sh, dd_mul_lazy(V[c], dd_add_lazy(dd_sqr_lazy(H[c].re), dd_sqr_lazy(H[c].im))));
+                sh = dd_add_lazy(sh, dd_mul_lazy(V[c], dd_add_lazy(dd_sqr_full(H[c].re), dd_sqr_full(H[c].im))));
             }
             float4 s = acc[t][threadIdx.x];
             f2 adh = {s.x, s.y}, ahh = {s.z, s.w};

@@ -284,6 +284,12 @@ constexpr double kLnVm = -0.7629122521271803;
 constexpr double kVmPow5Inv = 45.35685218040481;
 constexpr double kVmPow8Inv = 447.3306440422728;
 
+// float64 values of constants that WalkerDF carries as float pairs, for callers that need
+// them beyond the pairs' ~48 bits (the extended direct pass)
+struct WalkerDFFull {
+    double c1, c0, icb;   // c1; c_0 (the 0PN phase coefficient); (pi M)^{-1/3}
+};
+
 // Per-walker constants of the mixed path (Sec. II A parameter derivation), in float64: the
 // large-phase constants (PN coefficients, the v and ln v scales, t_ref and the f_max
 // references, the orbital angle at t_ref, the in-plane propagation components) are split
@@ -291,7 +297,7 @@ constexpr double kVmPow8Inv = 447.3306440422728;
 // factors are rounded once to float32.  One thread per walker; the caller spreads walkers
 // over full warps (a float64 warp instruction costs the same with 4 or 32 active lanes).
 __device__ inline void walker_setup_mixed(const double* __restrict__ theta, int64_t W, int64_t i,
-                                          WalkerDF& m, WalkerF& wf)
+                                          WalkerDF& m, WalkerF& wf, WalkerDFFull* full = nullptr)
 {
     const double mt = theta[kMT * W + i], q = theta[kQ * W + i];
     const double a1 = theta[kA1 * W + i], a2 = theta[kA2 * W + i];
@@ -377,7 +383,13 @@ __device__ inline void walker_setup_mixed(const double* __restrict__ theta, int6
     m.fcut = split_d(0.2 * iM);   // rounded to nearest: compared lexicographically (dd_le)
     m.t0 = split_f64(tref - dpsi_max * kInvTwoPi, 0);
     const double kxd = kTwoPi * kAUSec * (-cbt * cl), kyd = kTwoPi * kAUSec * (-cbt * sl);
-    m.c1 = split_f64(kTwoPi * tref - dpsi_max + (kxd * ca + kyd * sa), 0);   // with k.c(t_ref)
+    const double c1d = kTwoPi * tref - dpsi_max + (kxd * ca + kyd * sa);   // with k.c(t_ref)
+    m.c1 = split_f64(c1d, 0);
+    if (full) {
+        full->c1 = c1d;
+        full->c0 = c[0];
+        full->icb = icb;
+    }
     m.sa_ref = split_d(sa);   // high parts rounded to nearest (the orbit's sin, cos per point)
     m.ca_ref = split_d(ca);
     m.kx = split_f64(kxd, 0);
