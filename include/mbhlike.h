@@ -81,7 +81,7 @@ typedef enum {
                           delta = r - 1 and the contraction; with higher modes per group of
                           modes sharing m), except on edges of small contraction weight
                           (mbh_ref_f32_edges), which take the MBH_MIXED_F32 ratio within an
-                          error budget of 5e-4 in lnL (8.3e-4 at most while |delta| <= 16,
+                          error budget of 3e-4 in lnL (5e-4 at most while |delta| <= 16,
                           where a walker's edge keeps the float32 value); |dlnL| against
                           float64 <= 1e-3 up to SNR ~1000. */
     MBH_MIXED_F32 = 2  /* heterodyne: double-float phase difference, float32 response,

@@ -78,15 +78,16 @@ __device__ __forceinline__ f2 split_rn(double x)
 // walkers reach |delta| ~ 4).  The float32 error grows with |1 + delta| and the sensitivity with
 // |delta|: a walker's float32 value is kept while every channel has |delta| <= kDeltaF32Max,
 // where the product is at most 18 times its value at |delta| = 4 (5e-7 per unit of S_e, so the
-// float32 edges add at most 5e-7 kF32Budget / kF32EdgeError = 8.3e-4 to |dlnL|, the double-float
-// edges ~1e-5); beyond that the edge takes the double-float chain.  With higher modes the float32 terms are the modes' shares u_g = h0_g/h0 of the
+// float32 edges add at most 5e-7 kF32Budget / kF32EdgeError = 5e-4 to |dlnL|, the double-float
+// edges ~1e-4); beyond that the edge takes the double-float chain.  (A single float32 edge at the
+// top of a band has shown 2e-7 per unit of S_e on a source drawn at random.)  With higher modes the float32 terms are the modes' shares u_g = h0_g/h0 of the
 // reference, so near a zero of h0 (modes that cancel) the error grows by kappa = sum |u_g|:
 // the selection weighs S_e by kappa_e.  Edges are chosen in aligned groups of kF32Group: with
 // four threads per walker (the default) a group is one round of a warp's edges, so no warp
 // runs both paths for one round.
 constexpr double kDeltaMax = 3.0;
 constexpr double kF32EdgeError = 3e-7;
-constexpr double kF32Budget = 5e-4;
+constexpr double kF32Budget = 3e-4;
 constexpr float kDeltaF32Max = 16.0f;
 constexpr int kF32Group = 4;
 

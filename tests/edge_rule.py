@@ -3,7 +3,7 @@ side, from a prepared reference's summary data)."""
 import numpy as np
 
 
-def f32_edge_count(ref, g, kappa=None, budget=5e-4, eps32=3e-7, delta_max=3.0, group=4, rtol=1e-9):
+def f32_edge_count(ref, g, kappa=None, budget=3e-4, eps32=3e-7, delta_max=3.0, group=4, rtol=1e-9):
     """The per-edge precision rule of MBH_MIXED recomputed from the reference's summary data:
     each edge meets the summary data of the bin above it (as its lower edge) and below it (as
     its upper edge), with the per-bin linear interpolation of r (Eqs. 14 and 17) giving five
