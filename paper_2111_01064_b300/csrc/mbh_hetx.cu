@@ -692,8 +692,13 @@ __device__ __forceinline__ void het_x_body(const HetLaunch& L)
         for (int t = threadIdx.x; t < 2 * kSlot; t += BLOCK) {
             const int j = t < kSlot ? t : t - kSlot;
             if (j >= WPB || w0 + j >= S.w_end) continue;
-            const double* th = kPt ? &ths[kPt ? j : 0][0] : L.theta;
-            const int64_t tw = kPt ? 1 : L.W, ti = kPt ? 0 : w0 + j;
+            const double* th = L.theta;   // the batch's theta, or the proposal in shared memory
+            int64_t tw = L.W, ti = w0 + j;
+            if constexpr (kPt) {
+                th = &ths[j][0];
+                tw = 1;
+                ti = 0;
+            }
             if (t < kSlot) {
                 xwalker_setup(th, tw, ti, *S.mix.xder, xw[j]);
             } else if (S.mix.xn32 > 0) {
