@@ -96,7 +96,7 @@ def fma_peak_tinst(sm_mhz: float) -> float:
 #    On workload 2 (SNR 122) 149 of the 257 edges take the float32 ratio and 108 the
 #    double-float chain: 1581 FMA-pipe instructions per edge on average (2536 with every edge
 #    double-float);
-#  - het_xhm_kernel<4,128> (MBH_MIXED, six modes, the higher-mode leg's batch): 5330 per edge;
+#  - het_xhm_kernel<4,256> (MBH_MIXED, six modes, the higher-mode leg's batch): 5330 per edge;
 #  - direct_fused_x_kernel<4> (MBH_MIXED direct, double-float template and products) and
 #    direct_fused_mixed_kernel<8> (MBH_MIXED_F32 direct): FMA-pipe instructions per (template,
 #    grid point), each from a 512-template launch (the 4096-template batch's block shape);
@@ -514,7 +514,7 @@ def run_ours(args) -> dict | None:
             / (higher_modes["mixed"]["ms"] * 1e-3) / 1e12,
             "frac": HET_XHM_FMA_INST_PER_EDGE * higher_modes["walkers"] * (higher_modes["bins"] + 1)
             / (higher_modes["mixed"]["ms"] * 1e-3) / 1e12 / fma_peak,
-            "traffic": None, "kernel": "het_xhm_kernel<4,128>", "inst_per_edge": HET_XHM_FMA_INST_PER_EDGE},
+            "traffic": None, "kernel": "het_xhm_kernel<4,256>", "inst_per_edge": HET_XHM_FMA_INST_PER_EDGE},
         "roofline_fused_mixed": {"bound": "alu", "pipe": "fp32 (FMA pipe)", "achieved": fused_mixed_tinst,
                                  "peak": fma_peak, "unit": "T fp32-pipe inst/s",
                                  "frac": fused_mixed_tinst / fma_peak, "traffic": None,
