@@ -248,7 +248,11 @@ MBH_API mbh_status het_loglike_batch(const mbh_ref* const* refs, const int64_t* 
  * Taylor polynomials, |x| up to ~100); kind 1: sin(x)/x (o1); kind 2:
  * sinc(x(1+y)) - sinc(x(1-y)) without cancellation (o1); kinds 3 and 4: the
  * four-term forms of kinds 1 and 2 that the response uses below x = 0.1 (valid for
- * |x| < 0.2, and x < 0.1 with |y| <= 1).  MBH_EINVAL for another kind. */
+ * |x| < 0.2, and x < 0.1 with |y| <= 1).  The double-float (two-float) math of the
+ * extended-precision kernels, n values as (hi, lo) pairs (x: 2n floats; o1, o2: 2n
+ * floats): kind 5: sin and cos - 1 of x (o1, o2; any |x| < 2^22 pi, the pairs need not
+ * be normalised); kind 6: x y - n 2 pi with y three floats per value (3n floats, a
+ * triple-float), n = round(x.hi y.hi / 2 pi) (o1).  MBH_EINVAL for another kind. */
 MBH_API mbh_status mbh_selftest_math(int32_t kind, const float* x_dev, const float* y_dev, int64_t n,
                              float* o1_dev, float* o2_dev, void* stream);
 

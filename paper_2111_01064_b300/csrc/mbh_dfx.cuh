@@ -79,9 +79,12 @@ __device__ __forceinline__ c2f cd_norm(c2f a) { return {dd_norm(a.re), dd_norm(a
 // below are exact inside an FMA (see dd_reduce_2pi and dd_sincos), the second enters through an
 // exact two-product.
 constexpr double kTwoPiD = 6.283185307179586476925286766559005768;
-constexpr float kP2a = (float)kTwoPiD;
-constexpr float kP2b = (float)(kTwoPiD - (double)kP2a);
-constexpr float kP2c = (float)(kTwoPiD - (double)kP2a - (double)kP2b);
+// 2 pi = P2a + P2b + P2c to ~4e-23, the three parts rounded from a 60-digit value of 2 pi (the
+// float64 value of 2 pi is itself 2.4e-16 off, which over the ~1e6 turns of a 1e7-rad phase would
+// be a systematic 5e-10 rad)
+constexpr float kP2a = 0x1.921fb6p+2f;
+constexpr float kP2b = -0x1.777a5cp-23f;
+constexpr float kP2c = -0x1.ee59dap-48f;
 constexpr double kPi16D = 0.196349540849362077403915211455980405;
 constexpr float kQ16a = (float)kPi16D;
 constexpr float kQ16b = (float)(kPi16D - (double)kQ16a);
@@ -136,8 +139,9 @@ __device__ __forceinline__ f2 dd_mul_mod2pi(f2 a, f2 b, float bx)
     return two_sum(s3.hi, __fadd_rn(lo, sm));
 }
 
-// sin a and cos a - 1 for |a| <= ~0.2 (a double-float): sin a = a + a^3 (-1/6 + a^2/120 -
-// a^4/5040 + a^6/362880) with the a^3 term in float32 (its rounding <= 6e-8 |a|^3/6 < 1e-10),
+// sin a and cos a - 1 for |a| <= 0.1 (a double-float): sin a = a + a^3 (-1/6 + a^2/120 -
+// a^4/5040 + a^6/362880) with the a^3 term in float32 (its four float32 roundings, ~2e-7 of
+// |a|^3/6, are below 3.5e-11 at 0.1; at 0.19 they reached 1.7e-10),
 // cos a - 1 = -a^2/2 (double-float) + a^4 (1/24 - a^2/720 + a^4/40320) (float32 tail < 4e-5).
 __device__ __forceinline__ void dd_sincos_small(f2 a, f2& s, f2& cm1)
 {
@@ -188,7 +192,7 @@ __device__ __forceinline__ void dd_sincos(f2 r, const SinTab& tab, f2& s, f2& cm
 __device__ __forceinline__ void dd_sincos_any(f2 x, const SinTab& tab, f2& s, f2& cm1)
 {
     x = two_sum(x.hi, x.lo);
-    if (fabsf(x.hi) <= 0.19f) {
+    if (fabsf(x.hi) <= 0.1f) {
         dd_sincos_small(x, s, cm1);
         return;
     }

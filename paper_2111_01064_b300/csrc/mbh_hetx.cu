@@ -1572,6 +1572,40 @@ mbh_status launch_direct_fused_x(const mbh_data* data, const double* theta, int6
     return direct_finish(part, nchunks, W, data->dd, out, st);
 }
 
+// Test support (mbh_selftest_math kinds 5 and 6): the double-float sine/cosine of (x[2i],
+// x[2i+1]) as given (normalised or not) into o1 (sin) and o2 (cos - 1) as (hi, lo) pairs; the
+// exactly reduced product (x[2i], x[2i+1]) (y[3i], y[3i+1], y[3i+2]) mod 2 pi into o1.
+__global__ void selftest_df_kernel(int kind, const float* __restrict__ x, const float* __restrict__ y, int64_t n,
+                                   float* __restrict__ o1, float* __restrict__ o2)
+{
+    __shared__ SinTab tab;
+    load_sintab(tab);
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const f2 a = {x[2 * i], x[2 * i + 1]};
+        if (kind == 5) {
+            f2 sn, cm;
+            dd_sincos_any(a, tab, sn, cm);
+            o1[2 * i] = sn.hi;
+            o1[2 * i + 1] = sn.lo;
+            o2[2 * i] = cm.hi;
+            o2[2 * i + 1] = cm.lo;
+        } else {
+            const f2 r = dd_mul_mod2pi(a, {y[3 * i], y[3 * i + 1]}, y[3 * i + 2]);
+            o1[2 * i] = r.hi;
+            o1[2 * i + 1] = r.lo;
+        }
+    }
+}
+
+mbh_status selftest_df(int kind, const float* x, const float* y, int64_t n, float* o1, float* o2, cudaStream_t st)
+{
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 32);
+    selftest_df_kernel<<<blocks, 256, 0, st>>>(kind, x, y, n, o1, o2);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MBH_OK : cuda_fail(e, "mbh_selftest_math");
+}
+
 void free_x_tables(mbh_ref* R)
 {
     if (R->x_der) cudaFree(R->x_der);

@@ -193,6 +193,8 @@ HetKernel het_kernel_mixed_hm(int G, int block);
 HetKernel het_kernel_mixed_pt(int G, int block);
 HetKernel het_kernel_x(int G, int block);
 HetKernel het_kernel_x_pt(int G, int block);
+mbh_status selftest_df(int kind, const float* x, const float* y, int64_t n, float* o1, float* o2,
+                       cudaStream_t st);   // mbh_selftest_math kinds 5, 6
 HetKernel het_kernel_xhm(int G, int block);
 cudaError_t prepare_x_tables(mbh_ref* R, cudaStream_t st);
 cudaError_t prepare_x_tables_hm(mbh_ref* R, cudaStream_t st);

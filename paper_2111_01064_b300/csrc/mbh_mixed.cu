@@ -59,12 +59,13 @@ __global__ void selftest_math_kernel(int kind, const float* __restrict__ x, cons
 extern "C" mbh_status mbh_selftest_math(int32_t kind, const float* x_dev, const float* y_dev, int64_t n,
                                         float* o1_dev, float* o2_dev, void* stream)
 {
-    if (kind < 0 || kind > 4) return fail(MBH_EINVAL, "kind must be 0..4");
+    if (kind < 0 || kind > 6) return fail(MBH_EINVAL, "kind must be 0..6");
     if (n < 0) return fail(MBH_EINVAL, "n < 0");
     if (n == 0) return MBH_OK;
-    if (!x_dev || !o1_dev || (kind == 0 && !o2_dev) || ((kind == 2 || kind == 4) && !y_dev))
+    if (!x_dev || !o1_dev || ((kind == 0 || kind == 5) && !o2_dev) || ((kind == 2 || kind == 4 || kind == 6) && !y_dev))
         return fail(MBH_EINVAL, "NULL buffer");
     if (mbh_status s = check_device()) return s;
+    if (kind >= 5) return selftest_df(kind, x_dev, y_dev, n, o1_dev, o2_dev, (cudaStream_t)stream);
     const int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 32);
     selftest_math_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(kind, x_dev, y_dev, n, o1_dev, o2_dev);
     cudaError_t e = cudaGetLastError();

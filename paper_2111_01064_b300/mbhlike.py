@@ -572,16 +572,18 @@ class Server:
 
 def mbh_selftest_math(kind: int, x: torch.Tensor, y: torch.Tensor | None = None, stream=None):
     """Library float32 device math on x (and y): kind 0 -> (sin, cos), 1 -> sinc,
-    2 -> sinc(x(1+y)) - sinc(x(1-y)); 3, 4: the four-term forms of 1 and 2 (small x)."""
-    n = x.numel()
+    2 -> sinc(x(1+y)) - sinc(x(1-y)); 3, 4: the four-term forms of 1 and 2 (small x).
+    Double-float math, x as (hi, lo) pairs of shape (n, 2): kind 5 -> (sin, cos - 1) as pairs;
+    kind 6 -> x y mod 2 pi as pairs, y of shape (n, 3) (triple-floats)."""
+    n = x.numel() // 2 if kind >= 5 else x.numel()
     o1 = torch.empty_like(x)
-    o2 = torch.empty_like(x) if kind == 0 else None
+    o2 = torch.empty_like(x) if kind in (0, 5) else None
     _check(lib().mbh_selftest_math(int(kind), _dev(x, torch.float32, None, "x"),
                                    _dev(y, torch.float32, None, "y") if y is not None else None, n,
                                    _dev(o1, torch.float32, None, "o1"),
                                    _dev(o2, torch.float32, None, "o2") if o2 is not None else None,
                                    _stream(stream)))
-    return (o1, o2) if kind == 0 else o1
+    return (o1, o2) if kind in (0, 5) else o1
 
 
 class PTSampler:

@@ -83,4 +83,68 @@ def test_short_sinc_forms(M):
         assert abs(got[i] - ref) <= 1e-6 * abs(ref) + 1e-14, (xs[i], ks[i], got[i], ref)
         assert abs(got[i] - full[i]) <= 1e-6 * abs(ref) + 1e-14
     with pytest.raises(M.MBHError):
-        M.mbh_selftest_math(5, torch.from_numpy(xs).cuda())
+        M.mbh_selftest_math(7, torch.from_numpy(xs).cuda())
+
+
+def _split2(v):
+    hi = v.astype(np.float32)
+    return hi, (v - hi.astype(np.float64)).astype(np.float32)
+
+
+def test_df_sincos_unnormalised(M):
+    """The double-float sine and cosine - 1 of the extended kernels (kind 5) against 40-digit
+    values of the same inputs: small angles, |x| <= pi and |x| ~ 1e6, with low words of up to 8
+    ulps of the high word (lazy arithmetic after a cancellation leaves such pairs).  Bound: 5e-11
+    (the series' float32 a^3 term at |a| <= 0.1, directly or after the reduction to within pi/32)
+    plus |x| 2^-46 at large |x| (the reduction's rounding of the argument's low word)."""
+    import mpmath as mp
+    import torch
+    rng = np.random.default_rng(7)
+    hi = np.concatenate([rng.uniform(-0.19, 0.19, 400), rng.uniform(-3.2, 3.2, 400),
+                         rng.uniform(-2e6, 2e6, 400)]).astype(np.float32)
+    ulp = np.spacing(np.abs(hi)).astype(np.float64)
+    lo = (rng.integers(-16, 17, hi.size) * 0.5 * ulp).astype(np.float32)
+    x = np.ascontiguousarray(np.stack([hi, lo], 1))
+    s, c = M.mbh_selftest_math(5, torch.from_numpy(x).cuda())
+    s, c = s.cpu().numpy(), c.cpu().numpy()
+    mp.mp.dps = 40
+    worst = 0.0
+    for i in range(hi.size):
+        xv = mp.mpf(float(hi[i])) + mp.mpf(float(lo[i]))
+        es = abs(mp.mpf(float(s[i, 0])) + mp.mpf(float(s[i, 1])) - mp.sin(xv))
+        ec = abs(mp.mpf(float(c[i, 0])) + mp.mpf(float(c[i, 1])) - (mp.cos(xv) - 1))
+        bound = 5e-11 + abs(float(xv)) * 2.0 ** -46
+        worst = max(worst, float(max(es, ec)) / bound)
+        assert es <= bound and ec <= bound, (float(xv), float(es), float(ec))
+    print("df sincos worst error / bound", worst)
+
+
+def test_df_mul_mod2pi(M):
+    """x y mod 2 pi (kind 6) for a double-float x (frequencies 1e-5..0.05 Hz) and a
+    triple-float y (1e6..3e8: the time coefficient 2 pi t_ref of the absolute phase) against
+    the exact product: within 1e-13 after the whole turns are removed, with no bias."""
+    import mpmath as mp
+    import torch
+    rng = np.random.default_rng(8)
+    n = 2000
+    a = np.exp(rng.uniform(np.log(1e-5), np.log(0.05), n))
+    b = np.exp(rng.uniform(np.log(1e6), np.log(3e8), n))
+    ahi, alo = _split2(a)
+    bhi, blo = _split2(b)
+    bx = (b - bhi.astype(np.float64) - blo.astype(np.float64)).astype(np.float32)
+    x = np.ascontiguousarray(np.stack([ahi, alo], 1))
+    y = np.ascontiguousarray(np.stack([bhi, blo, bx], 1))
+    r = M.mbh_selftest_math(6, torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()).cpu().numpy()
+    mp.mp.dps = 50
+    two_pi = 2 * mp.pi
+    errs = np.empty(n)
+    for i in range(n):
+        exact = (mp.mpf(float(ahi[i])) + mp.mpf(float(alo[i]))) * (mp.mpf(float(bhi[i])) + mp.mpf(float(blo[i]))
+                                                                    + mp.mpf(float(bx[i])))
+        got = mp.mpf(float(r[i, 0])) + mp.mpf(float(r[i, 1]))
+        turns = mp.nint((exact - got) / two_pi)
+        errs[i] = float(got - (exact - turns * two_pi))
+        assert abs(got) < 8
+    print("mod 2 pi product: max error", np.abs(errs).max(), "mean", errs.mean())
+    assert np.abs(errs).max() <= 1e-13
+    assert abs(errs.mean()) <= 1e-14
