@@ -94,7 +94,7 @@ def fma_peak_tinst(sm_mhz: float) -> float:
 #  - het_x_kernel<4,256> (MBH_MIXED heterodyne): FMA-pipe instructions per edge evaluation
 #    (double-float phase/time differences, orbit, response, ratio, per-edge contraction).
 #    On workload 2 (SNR 122) 149 of the 257 edges take the float32 ratio and 108 the
-#    double-float chain: 1581 FMA-pipe instructions per edge on average (2536 with every edge
+#    double-float chain: 1586 FMA-pipe instructions per edge on average (2536 with every edge
 #    double-float);
 #  - het_xhm_kernel<4,256> (MBH_MIXED, six modes, the higher-mode leg's batch): 5330 per edge;
 #  - direct_fused_x_kernel<4> (MBH_MIXED direct, double-float template and products) and
@@ -102,10 +102,10 @@ def fma_peak_tinst(sm_mhz: float) -> float:
 #    grid point), each from a 512-template launch (the 4096-template batch's block shape);
 #  - direct_fused_f64_kernel<4>: FP64-pipe instructions per (template, grid point).
 HET_KERNEL = "het_x_kernel<4,256>"
-HET_X_FMA_INST_PER_EDGE = 1580.7
+HET_X_FMA_INST_PER_EDGE = 1585.7
 HET_X_DRAM_BYTES = 1.693e6                 # read + write per 16384-walker launch (ncu)
 HET_XHM_FMA_INST_PER_EDGE = 5330.2
-FUSED_X_FMA_INST_PER_POINT = 1893.2
+FUSED_X_FMA_INST_PER_POINT = 1921.7
 HET_F32_KERNEL = "het_mixed_kernel_capped<8,224>"
 HET_F32_FMA_INST_PER_EDGE = 639.0          # MBH_MIXED_F32 heterodyne (ncu, workload 2)
 FUSED_MIXED_FMA_INST_PER_POINT = 480.3
