@@ -96,7 +96,7 @@ def fma_peak_tinst(sm_mhz: float) -> float:
 #    On workload 2 (SNR 122) 149 of the 257 edges take the float32 ratio and 108 the
 #    double-float chain: 1586 FMA-pipe instructions per edge on average (2536 with every edge
 #    double-float);
-#  - het_xhm_kernel<4,256> (MBH_MIXED, six modes, the higher-mode leg's batch): 5330 per edge;
+#  - het_xhm_kernel<4,256> (MBH_MIXED, six modes, the higher-mode leg's batch): 5344 per edge;
 #  - direct_fused_x_kernel<4> (MBH_MIXED direct, double-float template and products) and
 #    direct_fused_mixed_kernel<8> (MBH_MIXED_F32 direct): FMA-pipe instructions per (template,
 #    grid point), each from a 512-template launch (the 4096-template batch's block shape);
@@ -104,7 +104,7 @@ def fma_peak_tinst(sm_mhz: float) -> float:
 HET_KERNEL = "het_x_kernel<4,256>"
 HET_X_FMA_INST_PER_EDGE = 1585.7
 HET_X_DRAM_BYTES = 1.693e6                 # read + write per 16384-walker launch (ncu)
-HET_XHM_FMA_INST_PER_EDGE = 5330.2
+HET_XHM_FMA_INST_PER_EDGE = 5344.0
 FUSED_X_FMA_INST_PER_POINT = 1921.7
 HET_F32_KERNEL = "het_mixed_kernel_capped<8,224>"
 HET_F32_FMA_INST_PER_EDGE = 639.0          # MBH_MIXED_F32 heterodyne (ncu, workload 2)
