@@ -1551,7 +1551,9 @@ mbh_status launch_direct_fused_x(const mbh_data* data, const double* theta, int6
     if (tiles > 0x7fffffff) return fail(MBH_EINVAL, "W too large");
     int64_t chunk;
     int nchunks;
-    direct_chunks(data->grid.n, tiles, 1 << 14, chunk, nchunks);
+    // one wave of blocks (2 per SM) at least: each block's float64 set-up of its 4 templates is
+    // worth ~1000 points of their double-float work
+    direct_chunks(data->grid.n, tiles, 1 << 14, chunk, nchunks, 2);
     double2* part = nullptr;
     cudaError_t e = cudaMallocAsync(&part, sizeof(double2) * W * nchunks, st);
     if (e != cudaSuccess) return cuda_fail(e, "direct_loglike_batch alloc");

@@ -160,7 +160,8 @@ mbh_status check_grid(const mbh_grid* g);
 mbh_status check_device();
 int sm_count();   // multiprocessors of the current device (148 on B300; cached per device)
 mbh_status check_modes(uint32_t modes, mbh_precision precision);
-void direct_chunks(int64_t n, int64_t tiles, int64_t max_chunk, int64_t& chunk, int& nchunks);
+void direct_chunks(int64_t n, int64_t tiles, int64_t max_chunk, int64_t& chunk, int& nchunks,
+                   int blocks_per_sm = 32);
 mbh_status direct_finish(double2* part, int nchunks, int64_t W, double dd, double* out,
                          cudaStream_t st);
 mbh_status launch_direct_finalize(const double2* part, int nchunks, int64_t W, double dd, double* out,

@@ -442,11 +442,13 @@ __global__ void direct_finalize_kernel(const double2* __restrict__ part, int nch
 }
 
 namespace mbh {
-// Chunking of the grid for the direct kernels: enough (tile, chunk) blocks to fill the GPU
-// several times over, chunks of at most max_chunk points.
-void direct_chunks(int64_t n, int64_t tiles, int64_t max_chunk, int64_t& chunk, int& nchunks)
+// Chunking of the grid for the direct kernels: enough (tile, chunk) blocks for blocks_per_sm
+// blocks per SM, chunks of at most max_chunk points.  Every block sets its templates up again,
+// so a kernel whose set-up is heavy against a chunk's work (the double-float pass) asks for
+// fewer, larger chunks.
+void direct_chunks(int64_t n, int64_t tiles, int64_t max_chunk, int64_t& chunk, int& nchunks, int blocks_per_sm)
 {
-    const int64_t target_blocks = (int64_t)sm_count() * 32;
+    const int64_t target_blocks = (int64_t)sm_count() * blocks_per_sm;
     int64_t nc = std::max<int64_t>(1, target_blocks / std::max<int64_t>(1, tiles));
     nc = std::max<int64_t>(nc, (n + max_chunk - 1) / max_chunk);
     nc = std::min<int64_t>(nc, (n + kDirThreads - 1) / kDirThreads);
