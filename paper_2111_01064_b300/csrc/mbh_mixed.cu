@@ -316,7 +316,7 @@ mbh_status mbh::launch_direct_fused_mixed(const mbh_data* data, const double* th
     if (tiles > 0x7fffffff) return fail(MBH_EINVAL, "W too large");
     int64_t chunk;
     int nchunks;
-    direct_chunks(data->grid.n, tiles, 1 << 14, chunk, nchunks);
+    direct_chunks(data->grid.n, tiles, 1 << 14, chunk, nchunks, 2);   // as the double-float pass
     double2* part = nullptr;
     cudaError_t e = cudaMallocAsync(&part, sizeof(double2) * W * nchunks, st);
     if (e != cudaSuccess) return cuda_fail(e, "direct_loglike_batch alloc");
